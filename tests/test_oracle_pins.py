@@ -1,0 +1,331 @@
+"""Pins of the CPU oracle against facts fixed by the paper and by mathematics (no GPU).
+
+Each test checks the oracle against something other than itself: closed forms, exact
+reproduction properties of the discretisation, brute force on tiny inputs, library
+routines for special cases, and numbers printed in the paper (tests/golden/).
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+import scipy.linalg as sla
+import scipy.sparse.linalg as spla
+
+import workloads as W
+from oracle import geometry as G
+from oracle import krylov as K
+from oracle import multigrid as MG
+from oracle import quadrature as Q
+from oracle.dgsbm import Discretisation
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+# ------------------------------------------------------------------ quadrature and basis
+@pytest.mark.parametrize("n", [1, 2, 3, 4, 6])
+def test_gauss_legendre_degree_of_exactness(n):
+    x, w = Q.gauss_legendre(n)
+    for k in range(2 * n):
+        assert abs(np.sum(w * x ** k) - 1.0 / (k + 1)) < 1e-14
+    assert abs(np.sum(w * x ** (2 * n)) - 1.0 / (2 * n + 1)) > 1e-10    # not exact beyond 2n-1
+
+
+@pytest.mark.parametrize("p", [1, 2, 3])
+def test_lagrange_basis_interpolates_polynomials(p):
+    nodes, _ = Q.gauss_legendre(p + 1)
+    assert np.allclose(Q.lagrange_values(nodes, nodes), np.eye(p + 1), atol=1e-14)
+    xs = np.linspace(-0.3, 1.4, 17)
+    V, D = Q.lagrange_values(nodes, xs), Q.lagrange_derivs(nodes, xs)
+    rng = np.random.default_rng(p)
+    c = rng.normal(size=p + 1)
+    poly = np.polynomial.Polynomial(c)
+    assert np.allclose(poly(nodes) @ V, poly(xs), atol=1e-12)
+    assert np.allclose(poly(nodes) @ D, poly.deriv()(xs), atol=1e-11)
+    # degree-1 case against the closed form l_0(x) = (x - x1) / (x0 - x1)
+    if p == 1:
+        assert np.allclose(V[0], (xs - nodes[1]) / (nodes[0] - nodes[1]))
+        assert np.allclose(nodes, [0.5 - 0.5 / math.sqrt(3), 0.5 + 0.5 / math.sqrt(3)])
+
+
+# ------------------------------------------------------------------ geometry
+def test_box_kappa_exact_and_disk_area():
+    prob = W.Problem(dim=2, n=16, p=1, shape=W.box(0.5))
+    kap = G.volume_fractions(prob, 16)
+    # box [-0.5,0.5]^2 on a 16^2 grid over [-1,1]^2: cells 4..11 inside, others outside
+    expect = np.zeros((16, 16))
+    expect[4:12, 4:12] = 1.0
+    assert np.array_equal(kap, expect)
+    # disk area from kappa: sampling error O(h * perimeter / s)
+    prob = W.disk2d_p1(64, 3)
+    kap = G.volume_fractions(prob, 64)
+    h = 2.0 / 64
+    assert abs(kap.sum() * h * h - math.pi * 0.49) < 2 * math.pi * 0.7 * h / 16
+
+
+def test_disk_shift_closed_form():
+    prob = W.disk2d_p1(16, 5)
+    g = G.LevelGeometry(prob, 16, 2)
+    c = np.array(prob.shape.center[:2])
+    for xt, d in zip(g.face_xt, g.face_d):
+        x = xt + d
+        assert np.allclose(np.linalg.norm(x - c, axis=1), 0.7, atol=1e-14)
+        cross = (x - c)[:, 0] * d[:, 1] - (x - c)[:, 1] * d[:, 0]      # d parallel to the radius
+        assert np.allclose(cross, 0.0, atol=1e-14)
+
+
+@pytest.mark.parametrize("shape", [W.star(1), W.random_star(1007), W.complex2d()])
+def test_newton_closest_point_2d_brute_force(shape):
+    """Newton on Eqs. 21-22 against a dense sampling of the boundary curve in polar form."""
+    rng = np.random.default_rng(0)
+    th = np.linspace(0, 2 * np.pi, 400001)[:-1]
+    if shape.kind == W.SHAPE_STAR:
+        r = shape.radius * (1 + shape.amp * np.sin(shape.freq * th + shape.phase))
+    else:   # complex2d: (1 - 3/4 sin^2(pi x)) r^2 = 1/5 along each ray, solved by bisection in r
+        lo_, hi_ = np.zeros_like(th), np.full_like(th, 2.0)
+        for _ in range(60):
+            mid = 0.5 * (lo_ + hi_)
+            X = np.stack([mid * np.cos(th), mid * np.sin(th)], axis=1)
+            inside = G.phi(shape, X) < 0
+            lo_ = np.where(inside, mid, lo_)
+            hi_ = np.where(inside, hi_, mid)
+        r = 0.5 * (lo_ + hi_)
+    curve = np.stack([r * np.cos(th), r * np.sin(th)], axis=1) + np.array(shape.center[:2])
+    for _ in range(25):
+        ang = rng.uniform(0, 2 * np.pi)
+        rad = np.interp(ang, th, r) * (1 + rng.uniform(-0.08, 0.08))
+        xt = np.array([rad * np.cos(ang), rad * np.sin(ang)]) + np.array(shape.center[:2])
+        x = G.closest_point(shape, xt)
+        assert abs(G.phi(shape, x)) < 1e-12
+        dist_brute = np.min(np.linalg.norm(curve - xt, axis=1))
+        assert np.linalg.norm(x - xt) <= dist_brute + 1e-6
+        assert np.linalg.norm(x - xt) >= dist_brute - 2e-5
+
+
+def test_newton_closest_point_ellipsoid():
+    shape = W.ellipsoid(4)
+    rng = np.random.default_rng(1)
+    R = np.array(shape.rot).reshape(3, 3)
+    semi = np.array(shape.semi)
+    u, v = np.meshgrid(np.linspace(0, np.pi, 801), np.linspace(0, 2 * np.pi, 1601), indexing="ij")
+    loc = np.stack([np.sin(u) * np.cos(v), np.sin(u) * np.sin(v), np.cos(u)], axis=-1).reshape(-1, 3) * semi
+    surf = loc @ R.T
+    for _ in range(15):
+        dirn = rng.normal(size=3)
+        dirn /= np.linalg.norm(dirn)
+        s = 1.0 / np.linalg.norm((R.T @ dirn) / semi)          # boundary along this ray
+        xt = dirn * s * (1 + rng.uniform(-0.1, 0.1))
+        x = G.closest_point(shape, xt)
+        assert abs(G.phi(shape, x)) < 1e-12
+        g, _ = G.grad_hess(shape, x)
+        assert np.linalg.norm(np.cross(g, x - xt)) < 1e-10 * np.linalg.norm(g)   # normal to the surface
+        dist_brute = np.min(np.linalg.norm(surf - xt, axis=1))
+        assert np.linalg.norm(x - xt) <= dist_brute + 1e-9
+        assert np.linalg.norm(x - xt) >= dist_brute - 5e-3
+
+
+def _golden(name):
+    rows = []
+    with open(os.path.join(GOLDEN, name)) as fh:
+        for line in fh:
+            if line.strip() and not line.startswith("#"):
+                rows.append([float(v) for v in line.split()])
+    return rows
+
+
+def test_paper_shift_ranges_golden():
+    """Sec. 5, figure shift_distribution: min/max normalised shifts, unit disk, p = 3."""
+    cache = {}
+    for lam, level, mn, mx in _golden("paper_shift_range.txt"):
+        key = (lam, int(level))
+        if key not in cache:
+            prob = W.paper_disk(int(level), 3, lam)
+            g = G.LevelGeometry(prob, prob.n, 3)
+            vals = []
+            for (_a, dr, side), d in zip(g.faces, g.face_d):
+                nt = np.zeros(2)
+                nt[dr] = 1.0 if side == 1 else -1.0
+                vals.append(np.sign(d @ nt) * np.linalg.norm(d, axis=1) / g.h)
+            vals = np.concatenate(vals)
+            cache[key] = (vals.min(), vals.max())
+        omin, omax = cache[key]
+        assert abs(omax - mx) < 6e-4, (lam, level, omax, mx)
+        if not math.isnan(mn):
+            assert abs(omin - mn) < 6e-4, (lam, level, omin, mn)
+
+
+# ------------------------------------------------------------------ the discrete operator
+CASES_LINEAR = [
+    (W.disk2d_p1(16, 1), 1), (W.disk2d_p1(16, 1), 2), (W.disk2d_p1(8, 2), 3),
+    (W.star2d_p2(16, 3), 2), (W.star2d_p2(16, 3), 3),
+    (W.sphere3d(8, 1, 4), 1), (W.sphere3d(6, 2, 4), 2), (W.ellipsoid3d_p3(6, 5), 3),
+]
+
+
+@pytest.mark.parametrize("prob,p", CASES_LINEAR, ids=lambda v: getattr(v, "name", str(v)))
+def test_linear_solution_reproduced(prob, p):
+    """The Taylor extension is exact for linear u (Eqs. 5-7), so A u_I = b with f = 0, g = u
+    for any shift d; the solve returns u_I.  A dropped/mis-signed consistency or SBM term fails."""
+    prob = prob.replace(p=p, exact=W.EXACT_LINEAR)
+    g = G.LevelGeometry(prob, prob.n, p)
+    D = Discretisation(prob, g)
+    uI, b = D.interpolate(W.EXACT_LINEAR), D.rhs()
+    assert len(g.faces) > 0 and np.abs(np.concatenate(g.face_d)).max() > 0.01 * g.h
+    assert np.linalg.norm(D.A @ uI - b) <= 1e-12 * np.linalg.norm(b)
+    x = spla.spsolve(D.A.tocsc(), b)
+    assert np.linalg.norm(x - uI) <= 1e-10 * np.linalg.norm(uI)
+
+
+@pytest.mark.parametrize("dim,n,p", [(2, 16, 1), (2, 8, 2), (2, 8, 3), (3, 4, 1), (3, 4, 2)])
+def test_box_symmetric_positive_definite(dim, n, p):
+    """d = 0 on a body-fitted box: the form is symmetric for alpha = 1 (Sec. 2, Eq. 3) and SPD."""
+    prob = W.Problem(dim=dim, n=n, p=p, shape=W.box(0.5))
+    g = G.LevelGeometry(prob, n, p)
+    assert np.abs(np.concatenate(g.face_d)).max() == 0.0
+    A = Discretisation(prob, g).A.toarray()
+    assert np.abs(A - A.T).max() <= 1e-14 * np.abs(A).max()
+    sla.cholesky(A)                                        # raises if not positive definite
+
+
+@pytest.mark.parametrize("p,kind", [(2, W.EXACT_QUADRATIC), (3, W.EXACT_QUADRATIC)])
+def test_box_polynomial_solution_exact(p, kind):
+    """Galerkin consistency on a fitted boundary: u in V_h is reproduced exactly (tests the
+    volume source quadrature and every consistency term)."""
+    for dim, n in ((2, 8), (3, 4)):
+        prob = W.Problem(dim=dim, n=n, p=p, shape=W.box(0.5), exact=kind)
+        g = G.LevelGeometry(prob, n, p)
+        D = Discretisation(prob, g)
+        x = spla.spsolve(D.A.tocsc(), D.rhs())
+        uI = D.interpolate(kind)
+        assert np.linalg.norm(x - uI) <= 1e-11 * np.linalg.norm(uI)
+        assert D.l2_error(x) < 1e-11
+
+
+def test_h_convergence_taylor_extension():
+    """First-order Taylor shift (Eq. 6): O(h^2) L2 convergence on the disk for p = 1."""
+    errs = []
+    for n in (16, 32, 64):
+        prob = W.disk2d_p1(n, 0)
+        g = G.LevelGeometry(prob, n, 1)
+        D = Discretisation(prob, g)
+        errs.append(D.l2_error(spla.spsolve(D.A.tocsc(), D.rhs())))
+    rates = np.log2(np.array(errs[:-1]) / np.array(errs[1:]))
+    assert np.all(np.abs(rates - 2.0) < 0.35), (errs, rates)
+
+
+@pytest.mark.slow
+def test_paper_l2_bands_golden():
+    """Sec. 5.1 figure convergence_results_l2: with the polynomial extension the errors over
+    lambda in {1, .75, .5, .25} sit within a factor 4 of the paper's band (geometric means),
+    and fall at the optimal rate p + 1."""
+    rows = [r for r in _golden("paper_l2_bands.txt") if r[1] <= 3]
+    ours = {}
+    for p, level, up, lo in rows:
+        errs = []
+        for lam in (1.0, 0.75, 0.5, 0.25):
+            prob = W.paper_disk(int(level), int(p), lam)
+            g = G.LevelGeometry(prob, prob.n, int(p))
+            D = Discretisation(prob, g)
+            errs.append(D.l2_error(spla.spsolve(D.A.tocsc(), D.rhs())))
+        gm = math.exp(np.mean(np.log(errs)))
+        ours[(p, level)] = gm
+        assert gm / math.sqrt(up * lo) < 4.0 and math.sqrt(up * lo) / gm < 4.0, (p, level, errs, up, lo)
+    for p in (1, 2, 3):
+        rate = math.log2(ours[(p, 1.0)] / ours[(p, 3.0)]) / 2
+        assert abs(rate - (p + 1)) < 0.6, (p, rate)
+
+
+# ------------------------------------------------------------------ multigrid pieces
+@pytest.mark.parametrize("dim,n,pf,pc", [(2, 8, 1, 1), (2, 8, 3, 1), (2, 8, 3, 2), (3, 8, 1, 1), (3, 4, 2, 1)])
+def test_prolongation_reproduces_coarse_polynomials(dim, n, pf, pc):
+    """Eq. 17: the embedding reproduces every coarse polynomial exactly on the fine cells."""
+    prob = W.Problem(dim=dim, n=n, p=pf, shape=W.disk(dim, 0, radius=0.8), exact=W.EXACT_QUADRATIC)
+    if pf == pc:       # h-transfer
+        coarse, fine = MG.Level(prob, n // 2, pc), MG.Level(prob, n, pf)
+        kind = W.EXACT_LINEAR
+    else:              # p-transfer
+        coarse, fine = MG.Level(prob, n, pc), MG.Level(prob, n, pf)
+        kind = W.EXACT_QUADRATIC if pc >= 2 else W.EXACT_LINEAR
+    P = MG.prolongation(coarse, fine)
+    uc, uf = coarse.disc.interpolate(kind), fine.disc.interpolate(kind)
+    # compare on fine cells whose parent is active (masked reading)
+    hit = np.asarray(P.sum(axis=1)).reshape(-1) != 0
+    assert hit.sum() > 0
+    assert np.abs((P @ uc - uf)[hit]).max() < 1e-13
+    # partition of unity of the coarse basis: row sums are 1 on hit rows
+    assert np.allclose(np.asarray(P.sum(axis=1)).reshape(-1)[hit], 1.0, atol=1e-13)
+
+
+def test_coloured_sweep_equals_sequential_block_gs():
+    """Cells of one colour share no face, so the per-colour update equals the cell-by-cell
+    successive correction of Eq. 16 in colour order; natural order gives a different map."""
+    for prob in (W.disk2d_p1(16, 2).replace(p=2), W.sphere3d(6, 1, 1)):
+        lev = MG.Level(prob, prob.n, prob.p)
+        rng = np.random.default_rng(3)
+        f = rng.normal(size=lev.N)
+        u0 = rng.normal(size=lev.N)
+        a = lev.coloured_sweep(u0.copy(), f)
+        b = lev.block_gs_sequential(u0.copy(), f, lev.colour_order())
+        c = lev.block_gs_sequential(u0.copy(), f, np.arange(lev.geom.n_active))
+        assert np.linalg.norm(a - b) <= 1e-12 * np.linalg.norm(b)
+        assert np.linalg.norm(a - c) > 1e-6 * np.linalg.norm(b)
+        a = lev.coloured_sweep(u0.copy(), f, reverse=True)
+        b = lev.block_gs_sequential(u0.copy(), f, lev.colour_order(reverse=True))
+        assert np.linalg.norm(a - b) <= 1e-12 * np.linalg.norm(b)
+
+
+def test_block_gs_converges_to_solution():
+    """Repeated symmetric block Gauss-Seidel on an SPD system converges to A^{-1} f."""
+    prob = W.Problem(dim=2, n=8, p=2, shape=W.box(0.5))
+    lev = MG.Level(prob, 8, 2)
+    f = np.random.default_rng(0).normal(size=lev.N)
+    x = spla.spsolve(lev.A.tocsc(), f)
+    u = np.zeros(lev.N)
+    for _ in range(3000):
+        lev.coloured_sweep(u, f)
+        lev.coloured_sweep(u, f, reverse=True)
+    assert np.linalg.norm(u - x) <= 1e-8 * np.linalg.norm(x)
+
+
+def test_vcycle_symmetric_on_spd_box():
+    """Forward pre-smoothing, backward post-smoothing and R = P^T make the V-cycle a symmetric
+    operator when A is symmetric (Secs. 3.1-3.2)."""
+    prob = W.Problem(dim=2, n=32, p=2, shape=W.box(0.5), coarsest_n=4)
+    H = MG.Hierarchy(prob)
+    rng = np.random.default_rng(0)
+    r1, r2 = rng.normal(size=H.finest.N), rng.normal(size=H.finest.N)
+    a, b = H.vcycle(r1) @ r2, r1 @ H.vcycle(r2)
+    assert abs(a - b) <= 1e-12 * abs(a)
+
+
+def test_vcycle_is_linear_and_exact_on_single_level():
+    prob = W.disk2d_p1(8, 0)
+    H = MG.Hierarchy(prob, levels=[(8, 1)])
+    r = np.random.default_rng(1).normal(size=H.finest.N)
+    x = np.linalg.solve(H.finest.A.toarray(), r)
+    assert np.linalg.norm(H.vcycle(r) - x) <= 1e-12 * np.linalg.norm(x)
+
+
+# ------------------------------------------------------------------ Krylov
+def test_fgmres_matches_direct_solve_tiny():
+    prob = W.disk2d_p1(16, 0)
+    H = MG.Hierarchy(prob)
+    A, b = H.finest.A, H.finest.disc.rhs()
+    x, info = K.fgmres(lambda v: A @ v, H.vcycle, b, tol=1e-12, m=30, max_it=400)
+    xd = np.linalg.solve(A.toarray(), b)
+    assert info.converged and info.true_rel_residual <= 1e-12
+    assert np.linalg.norm(x - xd) <= 1e-10 * np.linalg.norm(xd)
+
+
+def test_unpreconditioned_gmres_terminates_in_n_steps():
+    """Full GMRES (m >= N) reaches the exact solution in at most N steps (Krylov dimension)."""
+    rng = np.random.default_rng(2)
+    N = 12
+    A = rng.normal(size=(N, N)) + N * np.eye(N)
+    b = rng.normal(size=N)
+    x, info = K.fgmres(lambda v: A @ v, lambda v: v, b, tol=1e-13, m=N, max_it=N)
+    assert info.iterations <= N
+    assert np.linalg.norm(A @ x - b) <= 1e-12 * np.linalg.norm(b)
+    # with m = 3 it restarts, and still converges
+    x, info = K.fgmres(lambda v: A @ v, lambda v: v, b, tol=1e-10, m=3, max_it=500)
+    assert info.converged and info.restarts > 1
