@@ -1,0 +1,199 @@
+/*
+ * sbm.h - C ABI of the GB300 DG-SBM solver library (libsbm.so).
+ *
+ * The library solves the Poisson problem -Laplace(u) = f in Omega, u = g on Gamma
+ * (arXiv 2506.12899, Sec. 2, Eq. 1) with the interior-penalty discontinuous Galerkin
+ * discretisation of the Shifted Boundary Method (Sec. 2.2, Eqs. 7, 10, 11) on an unfitted
+ * Cartesian background mesh, by flexible GMRES preconditioned with one hp-multigrid
+ * V-cycle (Sec. 3).  Every step of the solve runs in the library's own CUDA kernels on one
+ * GPU; the host computes only the one-time set-up (geometry, element matrices, block
+ * factorisations, the coarse inverse, the right-hand side).
+ *
+ * Conventions for every call:
+ *   - Return value: SBM_OK (0) or a negative SBM_ERR_* code.  sbm_last_error() returns a
+ *     message for the last failure on the calling thread.  No C++ exception crosses the ABI.
+ *   - "_dev" pointers are device pointers owned by the caller (e.g. torch CUDA tensors),
+ *     contiguous, 16-byte aligned.  "_host" pointers are host memory owned by the caller.
+ *   - All device work is enqueued on the stream given in sbm_setup_desc.stream (a
+ *     cudaStream_t, NULL for the legacy default stream).  Calls return once the work is
+ *     enqueued, except where a call says it synchronises.
+ *   - Vector layout ("compact layout"): only active cells carry degrees of freedom.  On each
+ *     level, active cells are ordered by colour c = sum_k (i_k mod 2) 2^k (c = 0 .. 2^d-1);
+ *     within a colour, cells owning a surrogate face come first, then the others, each group
+ *     in lexicographic background order (x index fastest).  The (p_l+1)^d degrees of freedom
+ *     of a cell are contiguous, lexicographic (x fastest), and are the values of u at the
+ *     tensor Gauss-Legendre nodes of the cell.  sbm_layout() returns the background index of
+ *     every compact cell.
+ *   - Levels are numbered 0 (coarsest) .. L (finest); level -1 means the finest.
+ *   - dtype: SBM_F64 (double) or SBM_F32 (float) for the vectors of that call.
+ */
+#ifndef SBM_H
+#define SBM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+  SBM_OK = 0,
+  SBM_ERR_ARG = -1,             /* invalid argument or descriptor                               */
+  SBM_ERR_CUDA = -2,            /* a CUDA runtime call failed                                   */
+  SBM_ERR_SINGULAR_BLOCK = -3,  /* a cell block or the coarse matrix has pivot ratio < 1e-13    */
+  SBM_ERR_NOT_CONVERGED = -4,   /* FGMRES reached max_it without the requested tolerance        */
+  SBM_ERR_NAN = -5,             /* a non-finite residual or Hessenberg entry was detected       */
+  SBM_ERR_GEOMETRY = -6,        /* closest-point Newton failed or the finest level is empty     */
+  SBM_ERR_ALLOC = -7            /* out of device or host memory                                 */
+};
+
+enum { SBM_F64 = 0, SBM_F32 = 1 };
+
+/* Level-set shapes (Sec. 4.1: Omega = {phi < 0}). */
+enum { SBM_SHAPE_DISK = 0, SBM_SHAPE_STAR = 1, SBM_SHAPE_ELLIPSOID = 2, SBM_SHAPE_BOX = 3,
+       SBM_SHAPE_COMPLEX2D = 4 };
+/* Manufactured solutions: f = -Laplace(u), g = u (Sec. 5.1, Eq. 23 for COSSIN). */
+enum { SBM_U_SINPROD = 0, SBM_U_EXPCOS = 1, SBM_U_LINEAR = 2, SBM_U_COSSIN = 3, SBM_U_PHIP1 = 4,
+       SBM_U_QUADRATIC = 5 };
+
+typedef struct {
+  int kind;              /* SBM_SHAPE_*                                                         */
+  double center[3];
+  double radius;         /* disk/sphere radius; star base radius r0; box half-width             */
+  double amp, freq, phase; /* star: r(theta) = r0 (1 + amp sin(freq theta + phase))           */
+  double semi[3];        /* ellipsoid semi-axes                                                 */
+  double rot[9];         /* ellipsoid rotation R, row-major: phi = |S^-1 R^T (x - c)| - 1        */
+} sbm_shape;
+
+typedef struct {
+  int dim;               /* 2 or 3                                                              */
+  int n;                 /* background cells per direction on the finest level (even)          */
+  int p;                 /* polynomial degree on the finest level, 1..3                          */
+  double lo[3], hi[3];   /* background box; cells must be square: (hi-lo) equal in every dir     */
+  sbm_shape shape;
+  int exact;             /* SBM_U_*                                                             */
+  double lambda;         /* volume-fraction threshold (Sec. 2.1)                                 */
+  int lambda_inclusive;  /* 1: active iff kappa >= lambda; 0: kappa > lambda                      */
+  double sigma_face_c;   /* sigma_F = c (p_l+1)^2 / h_l                                          */
+  double sigma_bnd_c;    /* sigma_Gamma = c (p_l+1)^2 / h_l                                      */
+  double alpha;          /* 1: quasi-symmetric Nitsche (Eq. 7); -1: penalty-free variant          */
+  int extension;         /* 0: u(x~) + d.grad u(x~) (Eq. 6); 1: cell polynomial at x~ + d          */
+  int coarsest_n;        /* h-coarsening stops at this many cells per direction                 */
+  int pre_smooth, post_smooth;
+  double omega;          /* block-smoother relaxation on levels with p_l <= 2                    */
+  double omega_p3;       /* relaxation on levels with p_l = 3                                    */
+  int vf_samples;        /* kappa sub-samples per direction; 0: 16 in 2D, 8 in 3D                 */
+  int precision;         /* V-cycle precision inside sbm_solve: SBM_F64 or SBM_F32                */
+  void* stream;          /* cudaStream_t for every launch of this context                        */
+} sbm_setup_desc;
+
+typedef struct {
+  int n;                 /* cells per direction                                                 */
+  int p;                 /* degree                                                              */
+  double h;              /* cell size                                                           */
+  int n_active;          /* active cells                                                        */
+  int n_dof;             /* n_active * (p+1)^dim                                                */
+  int n_boundary;        /* active cells owning at least one surrogate face                     */
+  int n_sface;           /* surrogate faces                                                     */
+  int colour_start[9];   /* compact index of the first cell of each colour; [2^d] = n_active    */
+  int colour_nbnd[8];    /* boundary cells at the start of each colour                          */
+} sbm_level_info;
+
+typedef struct {
+  int converged;         /* 1 if ||b - A x|| <= tol ||b|| in FP64                                */
+  int iterations;        /* Arnoldi steps (= V-cycle applications)                               */
+  int restarts;          /* completed Arnoldi cycles                                             */
+  double true_rel_residual; /* ||b - A x|| / ||b|| recomputed in FP64 at the end                  */
+  double history[512];   /* |g_{j+1}| / ||b|| after each step (first 512)                        */
+  double ms_total;       /* device time of the whole call (CUDA events)                          */
+} sbm_solve_info;
+
+/* Create a context: builds every level's geometry (Sec. 2.1, Sec. 4.2), element data, block
+ * inverses (Eq. 14), transfer tables (Eqs. 17-18), the coarse inverse and the right-hand side,
+ * and copies them to the device.  Synchronises.  *out is NULL on failure. */
+int sbm_setup(const sbm_setup_desc* desc, void** out);
+
+/* Host-only context for checking the set-up without a GPU: builds the same levels, element data
+ * and right-hand side as sbm_setup but allocates no device memory.  Only sbm_num_levels,
+ * sbm_info, sbm_layout, sbm_export_geometry, sbm_host_apply, sbm_host_rhs and sbm_destroy
+ * accept it; the device calls return SBM_ERR_ARG. */
+int sbm_setup_host(const sbm_setup_desc* desc, void** out);
+
+/* Host FP64 evaluation of y = A_l x (Eq. 11) with the same element data the kernels use;
+ * x_host, y_host hold n_dof doubles in compact layout. */
+int sbm_host_apply(const void* ctx, int level, const double* x_host, double* y_host);
+
+/* Right-hand side of Eq. 11 into a host buffer of n_dof doubles (compact layout). */
+int sbm_host_rhs(const void* ctx, double* b_host);
+
+/* Release the context and all device memory it owns.  Safe on NULL. */
+void sbm_destroy(void* ctx);
+
+/* Message of the last failing call on this thread (static storage, never NULL). */
+const char* sbm_last_error(void);
+
+/* Number of multigrid levels L+1. */
+int sbm_num_levels(const void* ctx, int* out);
+
+/* Sizes and colour ranges of one level. */
+int sbm_info(const void* ctx, int level, sbm_level_info* out);
+
+/* Background multi-index of every compact cell: coords_host[3*a + k] = i_k (i_2 = 0 in 2D). */
+int sbm_layout(const void* ctx, int level, int* coords_host);
+
+/* Surrogate faces of a level, in compact-cell order then face slot 2*direction + side:
+ * cell_host[f], slot_host[f] and shifts d_host[f][(p+1)^(d-1)][3] (FP64, zero third component
+ * in 2D).  Pass NULL to query the count through *n_faces only. */
+int sbm_export_geometry(const void* ctx, int level, int* n_faces, int* cell_host, int* slot_host,
+                        double* d_host);
+
+/* Right-hand side b of Eq. 11 on the finest level, FP64, into the caller's device buffer. */
+int sbm_rhs(void* ctx, double* b_dev);
+
+/* y = A_l x: matrix-free operator of Eq. 11 on level l (volume, interior-penalty faces of
+ * Eq. 10, Nitsche-SBM surrogate faces of Eq. 7).  x and y hold n_dof values of `dtype`;
+ * x and y must not overlap. */
+int sbm_apply(void* ctx, int level, int dtype, const void* x_dev, void* y_dev);
+
+/* r = f - A_l u on level l (same operator as sbm_apply). */
+int sbm_residual(void* ctx, int level, int dtype, const void* f_dev, const void* u_dev, void* r_dev);
+
+/* One coloured block Gauss-Seidel sweep on level l (Eq. 16 with A_i of Eq. 14):
+ * for c = 0 .. 2^d-1 (reverse = 1: 2^d-1 .. 0), for every cell K of colour c,
+ * u_K <- u_K + omega_l A_KK^{-1} (f - A u)_K.  u is updated in place. */
+int sbm_smooth(void* ctx, int level, int dtype, int reverse, const void* f_dev, void* u_dev);
+
+/* Restriction (Eq. 18): rc = P^T rf from level l to level l-1 (l >= 1), masked to active cells. */
+int sbm_restrict(void* ctx, int level, int dtype, const void* rf_dev, void* rc_dev);
+
+/* Prolongation (Eq. 17): uf += P ec from level l-1 to level l (l >= 1), masked to active cells. */
+int sbm_prolong_add(void* ctx, int level, int dtype, const void* ec_dev, void* uf_dev);
+
+/* Coarse direct solve on level 0: e = A_0^{-1} r, always computed in FP64 (dense inverse of
+ * the LU-factored coarse matrix); r and e are of `dtype`. */
+int sbm_coarse_solve(void* ctx, int dtype, const void* r_dev, void* e_dev);
+
+/* One V-cycle z = M^{-1} r on the finest level (Sec. 3): zero initial guess, pre-smoothing
+ * (forward colours), residual, restriction, recursion, prolongation, post-smoothing (reverse
+ * colours); coarse direct solve.  dtype selects the V-cycle precision (FP32: every level
+ * operation in FP32 except the FP64 coarse solve). */
+int sbm_vcycle(void* ctx, int dtype, const void* r_dev, void* z_dev);
+
+/* Solve A x = b by FGMRES(restart), right-preconditioned by one V-cycle in the precision of
+ * sbm_setup_desc.precision; Arnoldi, Gram-Schmidt (two classical passes), the update of x and
+ * the true residual are FP64.  x_dev holds the initial guess on entry.  Stops when the
+ * Hessenberg residual estimate <= tol ||b|| and the recomputed ||b - A x|| <= tol ||b||, or
+ * at max_it Arnoldi steps (SBM_ERR_NOT_CONVERGED).  Synchronises; fills *info if non-NULL. */
+int sbm_solve(void* ctx, const double* b_dev, double* x_dev, double tol, int restart, int max_it,
+              sbm_solve_info* info);
+
+/* sbm_solve with host buffers: copies b_host to the device, solves from x = 0, copies x back
+ * into x_host.  The copies are part of the call. */
+int sbm_solve_host(void* ctx, const double* b_host, double* x_host, double tol, int restart,
+                   int max_it, sbm_solve_info* info);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SBM_H */

@@ -49,7 +49,7 @@ def _face_points(p: int, dim: int, direction: int, side: int):
 class Discretisation:
     """Element matrices, the assembled sparse matrix A and the RHS b on one level."""
 
-    def __init__(self, prob: W.Problem, geom: LevelGeometry):
+    def __init__(self, prob: W.Problem, geom: LevelGeometry, assemble: bool = True):
         self.prob, self.geom = prob, geom
         p, dim, h = geom.p, geom.dim, geom.h
         self.p, self.dim, self.h = p, dim, h
@@ -91,7 +91,11 @@ class Discretisation:
             self.F_blocks.append(blocks)
 
         self.sbm_blocks = [self.surrogate_face_matrix(f) for f in range(len(geom.faces))]
-        self._assemble()
+        self._faces_of = {}
+        for f, (a, _d, _s) in enumerate(geom.faces):
+            self._faces_of.setdefault(a, []).append(f)
+        if assemble:                       # assemble=False: blocks on demand only (large meshes)
+            self._assemble()
 
     # ------------------------------------------------------------------ surrogate faces
     def surrogate_face_matrix(self, f: int) -> np.ndarray:
@@ -144,9 +148,6 @@ class Discretisation:
     def _assemble(self):
         geom, nb = self.geom, self.nb
         nact = geom.n_active
-        self._faces_of = {}
-        for f, (a, _d, _s) in enumerate(geom.faces):
-            self._faces_of.setdefault(a, []).append(f)
         loc = np.arange(nb)
         Ri = np.repeat(loc, nb)
         Cj = np.tile(loc, nb)

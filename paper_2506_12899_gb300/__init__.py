@@ -1,0 +1,324 @@
+"""Python binding of libsbm, the GB300 DG-SBM hp-multigrid FGMRES solver.
+
+Argument marshalling only: every step of the solver runs in libsbm's CUDA kernels.  PyTorch
+provides the caller's device buffers and the CUDA stream.  There is no CPU fallback: if
+libsbm.so is missing or no CUDA device is present, the calls raise.
+
+Example:
+    import workloads as W, paper_2506_12899_gb300 as sbm
+    solver = sbm.Solver(W.disk2d_p1(32, 0), precision="f32")
+    b = solver.rhs(); x = torch.zeros_like(b)
+    info = solver.solve(b, x, tol=1e-8)
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libsbm.so")
+
+SBM_F64, SBM_F32 = 0, 1
+ERRORS = {-1: "SBM_ERR_ARG", -2: "SBM_ERR_CUDA", -3: "SBM_ERR_SINGULAR_BLOCK", -4: "SBM_ERR_NOT_CONVERGED",
+          -5: "SBM_ERR_NAN", -6: "SBM_ERR_GEOMETRY", -7: "SBM_ERR_ALLOC"}
+
+# exported C symbols (checked by the tests against include/sbm.h)
+SYMBOLS = ("sbm_setup", "sbm_setup_host", "sbm_host_apply", "sbm_host_rhs", "sbm_destroy", "sbm_last_error", "sbm_num_levels", "sbm_info", "sbm_layout",
+           "sbm_export_geometry", "sbm_rhs", "sbm_apply", "sbm_residual", "sbm_smooth", "sbm_restrict",
+           "sbm_prolong_add", "sbm_coarse_solve", "sbm_vcycle", "sbm_solve", "sbm_solve_host")
+
+
+class SbmError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{ERRORS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class _Shape(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("center", ctypes.c_double * 3), ("radius", ctypes.c_double),
+                ("amp", ctypes.c_double), ("freq", ctypes.c_double), ("phase", ctypes.c_double),
+                ("semi", ctypes.c_double * 3), ("rot", ctypes.c_double * 9)]
+
+
+class _Desc(ctypes.Structure):
+    _fields_ = [("dim", ctypes.c_int), ("n", ctypes.c_int), ("p", ctypes.c_int),
+                ("lo", ctypes.c_double * 3), ("hi", ctypes.c_double * 3), ("shape", _Shape),
+                ("exact", ctypes.c_int), ("lam", ctypes.c_double), ("lam_inclusive", ctypes.c_int),
+                ("sigma_face_c", ctypes.c_double), ("sigma_bnd_c", ctypes.c_double), ("alpha", ctypes.c_double),
+                ("extension", ctypes.c_int), ("coarsest_n", ctypes.c_int), ("pre_smooth", ctypes.c_int),
+                ("post_smooth", ctypes.c_int), ("omega", ctypes.c_double), ("omega_p3", ctypes.c_double),
+                ("vf_samples", ctypes.c_int), ("precision", ctypes.c_int), ("stream", ctypes.c_void_p)]
+
+
+class _LevelInfo(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int), ("p", ctypes.c_int), ("h", ctypes.c_double), ("n_active", ctypes.c_int),
+                ("n_dof", ctypes.c_int), ("n_boundary", ctypes.c_int), ("n_sface", ctypes.c_int),
+                ("colour_start", ctypes.c_int * 9), ("colour_nbnd", ctypes.c_int * 8)]
+
+
+class _SolveInfo(ctypes.Structure):
+    _fields_ = [("converged", ctypes.c_int), ("iterations", ctypes.c_int), ("restarts", ctypes.c_int),
+                ("true_rel_residual", ctypes.c_double), ("history", ctypes.c_double * 512),
+                ("ms_total", ctypes.c_double)]
+
+
+@dataclass
+class SolveInfo:
+    converged: bool
+    iterations: int
+    restarts: int
+    true_rel_residual: float
+    history: list
+    ms_total: float
+    status: int
+
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
+    """Load libsbm.so (built by `python -m paper_2506_12899_gb300.build`); raises if absent."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"libsbm.so not found at {path}: build it with "
+                           "`python -c 'import __graft_entry__ as g; g.build()'`")
+    import torch  # noqa: F401  (loads the CUDA runtime that libsbm shares)
+    lib = ctypes.CDLL(path)
+    vp, ip, dp = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+    lib.sbm_setup.argtypes = [ctypes.POINTER(_Desc), ctypes.POINTER(ctypes.c_void_p)]
+    lib.sbm_setup_host.argtypes = [ctypes.POINTER(_Desc), ctypes.POINTER(ctypes.c_void_p)]
+    lib.sbm_host_apply.argtypes = [vp, ip, vp, vp]
+    lib.sbm_host_rhs.argtypes = [vp, vp]
+    lib.sbm_destroy.argtypes = [vp]
+    lib.sbm_destroy.restype = None
+    lib.sbm_last_error.restype = ctypes.c_char_p
+    lib.sbm_num_levels.argtypes = [vp, ctypes.POINTER(ctypes.c_int)]
+    lib.sbm_info.argtypes = [vp, ip, ctypes.POINTER(_LevelInfo)]
+    lib.sbm_layout.argtypes = [vp, ip, vp]
+    lib.sbm_export_geometry.argtypes = [vp, ip, ctypes.POINTER(ctypes.c_int), vp, vp, vp]
+    lib.sbm_rhs.argtypes = [vp, vp]
+    lib.sbm_apply.argtypes = [vp, ip, ip, vp, vp]
+    lib.sbm_residual.argtypes = [vp, ip, ip, vp, vp, vp]
+    lib.sbm_smooth.argtypes = [vp, ip, ip, ip, vp, vp]
+    lib.sbm_restrict.argtypes = [vp, ip, ip, vp, vp]
+    lib.sbm_prolong_add.argtypes = [vp, ip, ip, vp, vp]
+    lib.sbm_coarse_solve.argtypes = [vp, ip, vp, vp]
+    lib.sbm_vcycle.argtypes = [vp, ip, vp, vp]
+    lib.sbm_solve.argtypes = [vp, vp, vp, dp, ip, ip, ctypes.POINTER(_SolveInfo)]
+    lib.sbm_solve_host.argtypes = [vp, vp, vp, dp, ip, ip, ctypes.POINTER(_SolveInfo)]
+    for name in SYMBOLS:
+        if name not in ("sbm_destroy", "sbm_last_error"):
+            getattr(lib, name).restype = ctypes.c_int
+    _lib = lib
+    return lib
+
+
+def _check(code: int):
+    if code != 0:
+        raise SbmError(code, _lib.sbm_last_error().decode())
+
+
+def make_desc(prob, precision: int = SBM_F64, stream: int = 0) -> _Desc:
+    d = _Desc()
+    d.dim, d.n, d.p = prob.dim, prob.n, prob.p
+    d.lo[:] = [float(v) for v in prob.lo]
+    d.hi[:] = [float(v) for v in prob.hi]
+    s = prob.shape
+    d.shape.kind = s.kind
+    d.shape.center[:] = [float(v) for v in s.center]
+    d.shape.radius, d.shape.amp, d.shape.freq, d.shape.phase = s.radius, s.amp, s.freq, s.phase
+    d.shape.semi[:] = [float(v) for v in s.semi]
+    d.shape.rot[:] = [float(v) for v in s.rot]
+    d.exact, d.lam, d.lam_inclusive = prob.exact, prob.lam, prob.lam_inclusive
+    d.sigma_face_c, d.sigma_bnd_c, d.alpha = prob.sigma_face_c, prob.sigma_bnd_c, prob.alpha
+    d.extension, d.coarsest_n = prob.extension, prob.coarsest_n
+    d.pre_smooth, d.post_smooth, d.omega, d.omega_p3 = prob.pre_smooth, prob.post_smooth, prob.omega, prob.omega_p3
+    d.vf_samples, d.precision, d.stream = prob.vf_samples, precision, stream
+    return d
+
+
+class Solver:
+    """One DG-SBM problem set up on the current CUDA device (a libsbm context)."""
+
+    def __init__(self, prob, precision: str = "f64", stream=None):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("libsbm needs a CUDA device; no CPU fallback exists")
+        self._torch = torch
+        self.lib = load_library()
+        self.prob = prob
+        self.precision = SBM_F32 if precision == "f32" else SBM_F64
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        desc = make_desc(prob, self.precision, self.stream.cuda_stream)
+        ctx = ctypes.c_void_p()
+        _check(self.lib.sbm_setup(ctypes.byref(desc), ctypes.byref(ctx)))
+        self.ctx = ctx
+        n = ctypes.c_int()
+        _check(self.lib.sbm_num_levels(self.ctx, ctypes.byref(n)))
+        self.num_levels = n.value
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            self.lib.sbm_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ------------------------------------------------------------------ layout / geometry
+    def info(self, level: int = -1) -> dict:
+        li = _LevelInfo()
+        _check(self.lib.sbm_info(self.ctx, level, ctypes.byref(li)))
+        return dict(n=li.n, p=li.p, h=li.h, n_active=li.n_active, n_dof=li.n_dof, n_boundary=li.n_boundary,
+                    n_sface=li.n_sface, colour_start=list(li.colour_start), colour_nbnd=list(li.colour_nbnd))
+
+    def layout(self, level: int = -1) -> np.ndarray:
+        """(n_active, 3) background multi-index of each compact cell."""
+        na = self.info(level)["n_active"]
+        out = np.zeros((na, 3), dtype=np.int32)
+        _check(self.lib.sbm_layout(self.ctx, level, out.ctypes.data))
+        return out
+
+    def export_geometry(self, level: int = -1):
+        nf = ctypes.c_int()
+        _check(self.lib.sbm_export_geometry(self.ctx, level, ctypes.byref(nf), None, None, None))
+        nq = (self.info(level)["p"] + 1) ** (self.prob.dim - 1)
+        cell = np.zeros(nf.value, dtype=np.int32)
+        slot = np.zeros(nf.value, dtype=np.int32)
+        d = np.zeros((nf.value, nq, 3))
+        _check(self.lib.sbm_export_geometry(self.ctx, level, ctypes.byref(nf), cell.ctypes.data,
+                                            slot.ctypes.data, d.ctypes.data))
+        return cell, slot, d
+
+    # ------------------------------------------------------------------ device operations
+    def _vec(self, t, dtype=None):
+        torch = self._torch
+        if not (t.is_cuda and t.is_contiguous()):
+            raise ValueError("expected a contiguous CUDA tensor")
+        if dtype is not None and t.dtype != dtype:
+            raise ValueError(f"expected dtype {dtype}, got {t.dtype}")
+        if t.dtype not in (torch.float64, torch.float32):
+            raise ValueError("vectors must be float64 or float32")
+        return ctypes.c_void_p(t.data_ptr())
+
+    def _dt(self, t):
+        return SBM_F64 if t.dtype == self._torch.float64 else SBM_F32
+
+    def n_dof(self, level: int = -1) -> int:
+        return self.info(level)["n_dof"]
+
+    def rhs(self):
+        b = self._torch.empty(self.n_dof(), dtype=self._torch.float64, device="cuda")
+        _check(self.lib.sbm_rhs(self.ctx, self._vec(b)))
+        return b
+
+    def apply(self, x, y=None, level: int = -1):
+        y = self._torch.empty_like(x) if y is None else y
+        _check(self.lib.sbm_apply(self.ctx, level, self._dt(x), self._vec(x), self._vec(y, x.dtype)))
+        return y
+
+    def residual(self, f, u, r=None, level: int = -1):
+        r = self._torch.empty_like(u) if r is None else r
+        _check(self.lib.sbm_residual(self.ctx, level, self._dt(u), self._vec(f, u.dtype), self._vec(u),
+                                     self._vec(r, u.dtype)))
+        return r
+
+    def smooth(self, f, u, level: int = -1, reverse: bool = False):
+        _check(self.lib.sbm_smooth(self.ctx, level, self._dt(u), int(reverse), self._vec(f, u.dtype), self._vec(u)))
+        return u
+
+    def restrict(self, rf, level: int = -1):
+        level = self.num_levels - 1 if level < 0 else level
+        rc = self._torch.empty(self.n_dof(level - 1), dtype=rf.dtype, device="cuda")
+        _check(self.lib.sbm_restrict(self.ctx, level, self._dt(rf), self._vec(rf), self._vec(rc)))
+        return rc
+
+    def prolong_add(self, ec, uf, level: int = -1):
+        _check(self.lib.sbm_prolong_add(self.ctx, level, self._dt(uf), self._vec(ec, uf.dtype), self._vec(uf)))
+        return uf
+
+    def coarse_solve(self, r, e=None):
+        e = self._torch.empty_like(r) if e is None else e
+        _check(self.lib.sbm_coarse_solve(self.ctx, self._dt(r), self._vec(r), self._vec(e, r.dtype)))
+        return e
+
+    def vcycle(self, r, z=None):
+        z = self._torch.empty_like(r) if z is None else z
+        _check(self.lib.sbm_vcycle(self.ctx, self._dt(r), self._vec(r), self._vec(z, r.dtype)))
+        return z
+
+    def solve(self, b, x, tol: float = 1e-8, restart: int = 30, max_it: int = 300, check: bool = True) -> SolveInfo:
+        inf = _SolveInfo()
+        code = self.lib.sbm_solve(self.ctx, self._vec(b, self._torch.float64), self._vec(x, self._torch.float64),
+                                  tol, restart, max_it, ctypes.byref(inf))
+        if check and code not in (0, -4):
+            _check(code)
+        return _info(inf, code)
+
+    def solve_host(self, b_host: np.ndarray, x_host: np.ndarray, tol: float = 1e-8, restart: int = 30,
+                   max_it: int = 300) -> SolveInfo:
+        """Host-buffer solve: the host->device copy of b and the copy of x back are part of the call."""
+        for a in (b_host, x_host):
+            if a.dtype != np.float64 or not a.flags["C_CONTIGUOUS"]:
+                raise ValueError("host buffers must be contiguous float64")
+        inf = _SolveInfo()
+        code = self.lib.sbm_solve_host(self.ctx, ctypes.c_void_p(b_host.ctypes.data),
+                                       ctypes.c_void_p(x_host.ctypes.data), tol, restart, max_it, ctypes.byref(inf))
+        if code not in (0, -4):
+            _check(code)
+        return _info(inf, code)
+
+
+class HostSetup:
+    """Host-only libsbm context (no GPU needed): the set-up of every level and a host FP64
+    evaluation of the operator with the same element data the kernels use."""
+
+    def __init__(self, prob):
+        self.lib = load_library()
+        self.prob = prob
+        desc = make_desc(prob, SBM_F64, 0)
+        ctx = ctypes.c_void_p()
+        _check(self.lib.sbm_setup_host(ctypes.byref(desc), ctypes.byref(ctx)))
+        self.ctx = ctx
+        n = ctypes.c_int()
+        _check(self.lib.sbm_num_levels(self.ctx, ctypes.byref(n)))
+        self.num_levels = n.value
+
+    info = Solver.info
+    layout = Solver.layout
+    export_geometry = Solver.export_geometry
+    close = Solver.close
+    __del__ = Solver.__del__
+
+    def host_apply(self, x: np.ndarray, level: int = -1) -> np.ndarray:
+        x = np.ascontiguousarray(x, dtype=np.float64)
+        y = np.zeros_like(x)
+        _check(self.lib.sbm_host_apply(self.ctx, level, x.ctypes.data, y.ctypes.data))
+        return y
+
+    def host_rhs(self) -> np.ndarray:
+        b = np.zeros(self.info(-1)["n_dof"])
+        _check(self.lib.sbm_host_rhs(self.ctx, b.ctypes.data))
+        return b
+
+
+def _info(inf: _SolveInfo, code: int) -> SolveInfo:
+    n = min(inf.iterations, 512)
+    return SolveInfo(bool(inf.converged), inf.iterations, inf.restarts, inf.true_rel_residual,
+                     list(inf.history[:n]), inf.ms_total, code)
+
+
+def compact_to_natural(coords: np.ndarray, n: int, dim: int) -> np.ndarray:
+    """Background linear id (x fastest) of each compact cell, from `Solver.layout()`."""
+    lin = coords[:, 0].astype(np.int64) + n * coords[:, 1].astype(np.int64)
+    if dim == 3:
+        lin += n * n * coords[:, 2].astype(np.int64)
+    return lin

@@ -1,0 +1,723 @@
+// C ABI of libsbm: context set-up, level operations, the V-cycle (Sec. 3) and FGMRES.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstring>
+#include <memory>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "ops.h"
+
+namespace sbm {
+namespace {
+
+thread_local std::string g_last_error;
+
+int set_error(int code, const std::string& msg) {
+  g_last_error = msg;
+  return code;
+}
+
+#define CUDA_TRY(expr)                                                                             \
+  do {                                                                                             \
+    cudaError_t e_ = (expr);                                                                       \
+    if (e_ != cudaSuccess) throw SetupError{SBM_ERR_CUDA, std::string(#expr) + ": " + cudaGetErrorString(e_)}; \
+  } while (0)
+
+template <typename R>
+constexpr int prec_index() {
+  return sizeof(R) == 8 ? 0 : 1;
+}
+
+struct DevLevel {
+  HostLevel H;
+  int* nbr = nullptr;
+  double* dhat64 = nullptr;
+  float* dhat32 = nullptr;
+  double* binv64 = nullptr;
+  float* binv32 = nullptr;
+  int* parent_code = nullptr;
+  int* children = nullptr;
+  double* coarse_inv = nullptr;
+  LevelParams<double> P64{};
+  LevelParams<float> P32{};
+  TransferParams<double> T64{};   // transfer between level l-1 (coarse) and this level
+  TransferParams<float> T32{};
+  void* z[2] = {nullptr, nullptr};
+  void* rhs[2] = {nullptr, nullptr};
+  void* res[2] = {nullptr, nullptr};
+};
+
+struct Context {
+  sbm_setup_desc desc{};
+  cudaStream_t stream = nullptr;
+  std::vector<DevLevel> lv;
+  std::vector<double> rhs_host;
+  std::vector<void*> allocs;
+  bool work_ready[2] = {false, false};
+  // FGMRES workspace
+  int ws_m = 0, ws_prec = -1;
+  double* V = nullptr;
+  void* Z = nullptr;
+  double* w = nullptr;
+  float* r32 = nullptr;
+  double* partial = nullptr;
+  double* dots = nullptr;          // [0,32) h1, [32,64) h2, [64] norm, [96, 128) Hessenberg column
+  double* ydev = nullptr;
+  double* bbuf = nullptr;
+  double* xbuf = nullptr;
+  double* host_pinned = nullptr;   // 64 doubles
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  bool host_only = false;
+
+  ~Context() {
+    for (void* p : allocs) cudaFree(p);
+    if (host_pinned) cudaFreeHost(host_pinned);
+    if (ev0) cudaEventDestroy(ev0);
+    if (ev1) cudaEventDestroy(ev1);
+  }
+
+  template <typename T>
+  T* dalloc(size_t n) {
+    void* p = nullptr;
+    if (n == 0) n = 1;
+    cudaError_t e = cudaMalloc(&p, n * sizeof(T));
+    if (e != cudaSuccess) throw SetupError{SBM_ERR_ALLOC, std::string("cudaMalloc: ") + cudaGetErrorString(e)};
+    allocs.push_back(p);
+    return static_cast<T*>(p);
+  }
+  template <typename T>
+  T* upload(const std::vector<T>& v) {
+    T* p = dalloc<T>(v.size());
+    if (!v.empty()) CUDA_TRY(cudaMemcpy(p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice));
+    return p;
+  }
+  int finest() const { return (int)lv.size() - 1; }
+};
+
+template <typename R>
+const LevelParams<R>& params(const DevLevel& L);
+template <>
+const LevelParams<double>& params<double>(const DevLevel& L) { return L.P64; }
+template <>
+const LevelParams<float>& params<float>(const DevLevel& L) { return L.P32; }
+template <typename R>
+const TransferParams<R>& tparams(const DevLevel& L);
+template <>
+const TransferParams<double>& tparams<double>(const DevLevel& L) { return L.T64; }
+template <>
+const TransferParams<float>& tparams<float>(const DevLevel& L) { return L.T32; }
+
+template <typename R>
+LevelParams<R> make_params(const DevLevel& D, const R* dhat, const R* binv) {
+  const HostLevel& H = D.H;
+  LevelParams<R> P;
+  std::memset(&P, 0, sizeof(P));
+  P.n_act = H.n_act;
+  for (int c = 0; c < 9; ++c) P.colour_start[c] = H.colour_start[c];
+  for (int c = 0; c < 8; ++c) {
+    P.colour_nbnd[c] = H.colour_nbnd[c];
+    P.bstart[c] = H.bstart[c];
+  }
+  P.nbr = D.nbr;
+  P.dhat = dhat;
+  P.binvT = binv;
+  P.hscale = (R)std::pow(H.h, H.dim - 2);
+  P.sigG = (R)H.sigG_hat;
+  P.alpha = (R)H.alpha;
+  P.omega = (R)H.omega;
+  P.extension = H.extension;
+  const int n1 = H.n1;
+  for (int m = 0; m < 4; ++m)
+    for (int ij = 0; ij < n1 * n1; ++ij) P.k.L[m][ij] = (R)H.L[m][ij];
+  for (int ij = 0; ij < n1 * n1; ++ij) {
+    P.k.Bmp[ij] = (R)H.Bmp[ij];
+    P.k.Bpm[ij] = (R)H.Bpm[ij];
+    P.k.Dm[ij] = (R)H.B.Dm[ij];
+    P.k.S[ij] = (R)H.S[ij];
+  }
+  for (int k = 0; k < n1; ++k) {
+    P.k.w[k] = (R)H.B.w[k];
+    P.k.e0[k] = (R)H.B.e0[k];
+    P.k.e1[k] = (R)H.B.e1[k];
+    P.k.d0[k] = (R)H.B.d0[k];
+    P.k.d1[k] = (R)H.B.d1[k];
+    P.k.x[k] = (R)H.B.x[k];
+    double den = 1.0;
+    for (int j = 0; j < n1; ++j)
+      if (j != k) den *= H.B.x[k] - H.B.x[j];
+    P.k.inv_denom[k] = (R)(1.0 / den);
+    P.k.lam[k] = (R)H.lam[k];
+  }
+  return P;
+}
+
+template <typename R>
+TransferParams<R> make_transfer(const DevLevel& C, const DevLevel& F) {
+  TransferParams<R> T;
+  std::memset(&T, 0, sizeof(T));
+  T.n_act_f = F.H.n_act;
+  T.n_act_c = C.H.n_act;
+  T.hmode = C.H.n != F.H.n;
+  T.parent_code = F.parent_code;
+  T.children = C.children;
+  const int nf = F.H.n1, nc = C.H.n1;
+  double v[kMaxN1];
+  for (int o = 0; o < 2; ++o)
+    for (int i = 0; i < nf; ++i) {
+      lagrange_eval(nc, C.H.B.x, 0.5 * (o + F.H.B.x[i]), v, nullptr);
+      for (int j = 0; j < nc; ++j) T.Ph[o][i * nc + j] = (R)v[j];
+    }
+  for (int i = 0; i < nf; ++i) {
+    lagrange_eval(nc, C.H.B.x, F.H.B.x[i], v, nullptr);
+    for (int j = 0; j < nc; ++j) T.Pp[i * nc + j] = (R)v[j];
+  }
+  return T;
+}
+
+template <typename T>
+std::vector<float> to_f32(const std::vector<T>& v) {
+  return std::vector<float>(v.begin(), v.end());
+}
+
+void validate(const sbm_setup_desc& d) {
+  auto bad = [](const std::string& m) { throw SetupError{SBM_ERR_ARG, m}; };
+  if (d.dim != 2 && d.dim != 3) bad("dim must be 2 or 3");
+  if (d.p < 1 || d.p > 3) bad("p must be 1, 2 or 3");
+  if (d.n < 1 || d.n > 4096) bad("n out of range");
+  if (d.coarsest_n < 1) bad("coarsest_n must be >= 1");
+  if (!(d.lambda >= 0.0 && d.lambda <= 1.0)) bad("lambda must lie in [0,1]");
+  if (d.pre_smooth < 0 || d.post_smooth < 0 || d.pre_smooth > 16 || d.post_smooth > 16) bad("smoothing steps");
+  if (d.precision != SBM_F64 && d.precision != SBM_F32) bad("precision must be SBM_F64 or SBM_F32");
+  if (d.extension != 0 && d.extension != 1) bad("extension must be 0 or 1");
+  const double w0 = d.hi[0] - d.lo[0];
+  if (!(w0 > 0) || !std::isfinite(w0)) bad("empty or non-finite box");
+  for (int k = 1; k < d.dim; ++k)
+    if (!(std::fabs((d.hi[k] - d.lo[k]) - w0) <= 1e-12 * w0)) bad("cells must be square: equal box extents");
+  if (!(d.sigma_face_c > 0 && d.sigma_bnd_c >= 0)) bad("penalty constants");
+  if (d.shape.kind < 0 || d.shape.kind > 4) bad("unknown shape");
+  if (d.shape.kind == SBM_SHAPE_STAR && d.dim != 2) bad("star shape is 2D");
+  if (d.shape.kind == SBM_SHAPE_COMPLEX2D && d.dim != 2) bad("complex2d shape is 2D");
+  if (d.shape.kind == SBM_SHAPE_ELLIPSOID && d.dim != 3) bad("ellipsoid shape is 3D");
+}
+
+Context* build_context(const sbm_setup_desc& d, bool device) {
+  validate(d);
+  auto C = std::make_unique<Context>();
+  C->desc = d;
+  C->stream = static_cast<cudaStream_t>(d.stream);
+  std::vector<int> ns{d.n};
+  while (ns.back() % 2 == 0 && ns.back() / 2 >= d.coarsest_n) ns.push_back(ns.back() / 2);
+  std::vector<std::pair<int, int>> seq;
+  for (auto it = ns.rbegin(); it != ns.rend(); ++it) seq.emplace_back(*it, 1);
+  for (int q = 2; q <= d.p; ++q) seq.emplace_back(d.n, q);
+  for (auto& np : seq) {
+    DevLevel L;
+    L.H = build_level(d, np.first, np.second);
+    if (L.H.n_act == 0) {
+      C->lv.clear();                       // an empty level: everything coarser is dropped
+      continue;
+    }
+    C->lv.push_back(std::move(L));
+  }
+  if (C->lv.empty()) throw SetupError{SBM_ERR_GEOMETRY, "finest level has no active cells"};
+  for (size_t l = 1; l < C->lv.size(); ++l) link_levels(C->lv[l - 1].H, C->lv[l].H);
+  build_coarse_inverse(C->lv[0].H);
+  C->rhs_host = build_rhs(d, C->lv.back().H);
+  if (!device) return C.release();
+  for (auto& L : C->lv) {
+    L.nbr = C->upload(L.H.nbr);
+    L.dhat64 = C->upload(L.H.dhat);
+    L.dhat32 = C->upload(to_f32(L.H.dhat));
+    L.binv64 = C->upload(L.H.binvT);
+    L.binv32 = C->upload(to_f32(L.H.binvT));
+    if (!L.H.parent_code.empty()) L.parent_code = C->upload(L.H.parent_code);
+    if (!L.H.children.empty()) L.children = C->upload(L.H.children);
+    if (!L.H.coarse_inv.empty()) L.coarse_inv = C->upload(L.H.coarse_inv);
+    L.P64 = make_params<double>(L, L.dhat64, L.binv64);
+    L.P32 = make_params<float>(L, L.dhat32, L.binv32);
+  }
+  for (size_t l = 1; l < C->lv.size(); ++l) {
+    C->lv[l].T64 = make_transfer<double>(C->lv[l - 1], C->lv[l]);
+    C->lv[l].T32 = make_transfer<float>(C->lv[l - 1], C->lv[l]);
+  }
+  CUDA_TRY(cudaMallocHost(&C->host_pinned, 64 * sizeof(double)));
+  CUDA_TRY(cudaEventCreate(&C->ev0));
+  CUDA_TRY(cudaEventCreate(&C->ev1));
+  CUDA_TRY(cudaDeviceSynchronize());
+  return C.release();
+}
+
+template <typename R>
+void ensure_work(Context& C) {
+  const int pi = prec_index<R>();
+  if (C.work_ready[pi]) return;
+  for (auto& L : C.lv) {
+    size_t N = L.H.n_dof();
+    L.z[pi] = C.dalloc<R>(N);
+    L.rhs[pi] = C.dalloc<R>(N);
+    L.res[pi] = C.dalloc<R>(N);
+  }
+  C.work_ready[pi] = true;
+}
+
+// One V-cycle on level l (Sec. 3): zero initial guess, pre-smoothing with forward colour order,
+// residual, restriction (Eq. 18), recursion, prolongation (Eq. 17), post-smoothing with reverse
+// colour order; level 0 is solved with the dense coarse inverse.
+template <typename R>
+void vcycle_rec(Context& C, int l, const R* r, R* z) {
+  DevLevel& L = C.lv[l];
+  const int pi = prec_index<R>();
+  const cudaStream_t s = C.stream;
+  if (l == 0) {
+    CUDA_TRY(launch_coarse<R>(L.coarse_inv, L.H.n_dof(), r, z, s));
+    return;
+  }
+  const int dim = L.H.dim;
+  const LevelParams<R>& P = params<R>(L);
+  CUDA_TRY(cudaMemsetAsync(z, 0, (size_t)L.H.n_dof() * sizeof(R), s));
+  for (int k = 0; k < C.desc.pre_smooth; ++k) CUDA_TRY(launch_smooth<R>(dim, L.H.p, P, 0, r, z, s));
+  R* res = static_cast<R*>(L.res[pi]);
+  CUDA_TRY((launch_apply<R, R>(dim, L.H.p, P, z, r, res, 1, s)));
+  DevLevel& Lc = C.lv[l - 1];
+  R* rc = static_cast<R*>(Lc.rhs[pi]);
+  R* zc = static_cast<R*>(Lc.z[pi]);
+  CUDA_TRY(launch_restrict<R>(dim, L.H.p, Lc.H.p, tparams<R>(L), res, rc, s));
+  vcycle_rec<R>(C, l - 1, rc, zc);
+  CUDA_TRY(launch_prolong<R>(dim, L.H.p, Lc.H.p, tparams<R>(L), zc, z, s));
+  for (int k = 0; k < C.desc.post_smooth; ++k) CUDA_TRY(launch_smooth<R>(dim, L.H.p, P, 1, r, z, s));
+}
+
+void ensure_krylov(Context& C, int m) {
+  const int prec = C.desc.precision;
+  if (C.ws_m >= m && C.ws_prec == prec) return;
+  const size_t N = C.lv.back().H.n_dof();
+  C.V = C.dalloc<double>((size_t)(m + 1) * N);
+  C.Z = prec == SBM_F32 ? (void*)C.dalloc<float>((size_t)m * N) : (void*)C.dalloc<double>((size_t)m * N);
+  C.w = C.dalloc<double>(N);
+  if (prec == SBM_F32) C.r32 = C.dalloc<float>(N);
+  C.partial = C.dalloc<double>((size_t)dot_blocks(N) * 32);
+  C.dots = C.dalloc<double>(128);
+  C.ydev = C.dalloc<double>(32);
+  C.ws_m = m;
+  C.ws_prec = prec;
+}
+
+double device_norm(Context& C, const double* v, size_t N, double* out_dev) {
+  CUDA_TRY(launch_multi_dot(v, N, 1, v, N, C.partial, out_dev, 1, C.stream));
+  CUDA_TRY(cudaMemcpyAsync(C.host_pinned, out_dev, sizeof(double), cudaMemcpyDeviceToHost, C.stream));
+  CUDA_TRY(cudaStreamSynchronize(C.stream));
+  return C.host_pinned[0];
+}
+
+// Right-preconditioned flexible GMRES(m) with two classical Gram-Schmidt passes, FP64.
+int solve_impl(Context& C, const double* b, double* x, double tol, int m, int max_it, sbm_solve_info* info) {
+  if (m < 1 || m > 31) throw SetupError{SBM_ERR_ARG, "restart must be in 1..31"};
+  if (!(tol > 0)) throw SetupError{SBM_ERR_ARG, "tol must be > 0"};
+  ensure_krylov(C, m);
+  const int prec = C.desc.precision;
+  if (prec == SBM_F32) ensure_work<float>(C); else ensure_work<double>(C);
+  const int Lf = C.finest();
+  DevLevel& F = C.lv[Lf];
+  const size_t N = F.H.n_dof();
+  const cudaStream_t s = C.stream;
+  const int dim = F.H.dim, p = F.H.p;
+  double* h1 = C.dots;
+  double* h2 = C.dots + 32;
+  double* hn = C.dots + 64;
+  double* col = C.dots + 96;
+  sbm_solve_info loc{};
+  CUDA_TRY(cudaEventRecord(C.ev0, s));
+  const double bnorm = device_norm(C, b, N, hn);
+  if (!std::isfinite(bnorm)) throw SetupError{SBM_ERR_NAN, "non-finite ||b||"};
+  int status = SBM_OK;
+  if (bnorm == 0.0) {
+    CUDA_TRY(cudaMemsetAsync(x, 0, N * sizeof(double), s));
+    loc.converged = 1;
+    loc.true_rel_residual = 0.0;
+  } else {
+    std::vector<double> H((size_t)(m + 1) * m), cs(m), sn(m), g(m + 1), y(m);
+    while (true) {
+      double* V0 = C.V;
+      CUDA_TRY((launch_apply<double, double>(dim, p, F.P64, x, b, V0, 1, s)));
+      const double beta = device_norm(C, V0, N, hn);
+      loc.true_rel_residual = beta / bnorm;
+      if (!std::isfinite(beta)) {
+        status = SBM_ERR_NAN;
+        break;
+      }
+      if (beta <= tol * bnorm) {
+        loc.converged = 1;
+        break;
+      }
+      if (loc.iterations >= max_it) {
+        status = SBM_ERR_NOT_CONVERGED;
+        break;
+      }
+      CUDA_TRY(launch_div_scalar(V0, hn, V0, N, s));
+      std::fill(H.begin(), H.end(), 0.0);
+      std::fill(g.begin(), g.end(), 0.0);
+      g[0] = beta;
+      int k = 0;
+      bool nan = false;
+      for (int j = 0; j < m; ++j) {
+        double* Vj = C.V + (size_t)j * N;
+        if (prec == SBM_F32) {
+          float* Zj = static_cast<float*>(C.Z) + (size_t)j * N;
+          CUDA_TRY((launch_cast<double, float>(Vj, C.r32, N, s)));
+          vcycle_rec<float>(C, Lf, C.r32, Zj);
+          CUDA_TRY((launch_apply<float, double>(dim, p, F.P64, Zj, nullptr, C.w, 0, s)));
+        } else {
+          double* Zj = static_cast<double*>(C.Z) + (size_t)j * N;
+          vcycle_rec<double>(C, Lf, Vj, Zj);
+          CUDA_TRY((launch_apply<double, double>(dim, p, F.P64, Zj, nullptr, C.w, 0, s)));
+        }
+        CUDA_TRY(launch_multi_dot(C.V, N, j + 1, C.w, N, C.partial, h1, 0, s));
+        CUDA_TRY(launch_multi_axpy<double>(C.V, N, j + 1, h1, -1.0, C.w, N, s));
+        CUDA_TRY(launch_multi_dot(C.V, N, j + 1, C.w, N, C.partial, h2, 0, s));
+        CUDA_TRY(launch_multi_axpy<double>(C.V, N, j + 1, h2, -1.0, C.w, N, s));
+        CUDA_TRY(launch_multi_dot(C.w, N, 1, C.w, N, C.partial, hn, 1, s));
+        CUDA_TRY(launch_div_scalar(C.w, hn, C.V + (size_t)(j + 1) * N, N, s));
+        CUDA_TRY(launch_hess_column(h1, h2, hn, j + 1, col, s));
+        CUDA_TRY(cudaMemcpyAsync(C.host_pinned, col, (j + 2) * sizeof(double), cudaMemcpyDeviceToHost, s));
+        CUDA_TRY(cudaStreamSynchronize(s));
+        for (int i = 0; i <= j + 1; ++i) {
+          H[(size_t)i * m + j] = C.host_pinned[i];
+          if (!std::isfinite(C.host_pinned[i])) nan = true;
+        }
+        const double hnorm = C.host_pinned[j + 1];
+        for (int i = 0; i < j; ++i) {              // previous Givens rotations
+          const double t = cs[i] * H[(size_t)i * m + j] + sn[i] * H[(size_t)(i + 1) * m + j];
+          H[(size_t)(i + 1) * m + j] = -sn[i] * H[(size_t)i * m + j] + cs[i] * H[(size_t)(i + 1) * m + j];
+          H[(size_t)i * m + j] = t;
+        }
+        const double rr = std::hypot(H[(size_t)j * m + j], H[(size_t)(j + 1) * m + j]);
+        cs[j] = H[(size_t)j * m + j] / rr;
+        sn[j] = H[(size_t)(j + 1) * m + j] / rr;
+        H[(size_t)j * m + j] = rr;
+        H[(size_t)(j + 1) * m + j] = 0.0;
+        g[j + 1] = -sn[j] * g[j];
+        g[j] = cs[j] * g[j];
+        k = j + 1;
+        if (loc.iterations < 512) loc.history[loc.iterations] = std::fabs(g[j + 1]) / bnorm;
+        loc.iterations += 1;
+        if (nan || !std::isfinite(g[j + 1])) {
+          nan = true;
+          break;
+        }
+        if (std::fabs(g[j + 1]) <= tol * bnorm || loc.iterations >= max_it || hnorm == 0.0) break;
+      }
+      if (nan) {
+        status = SBM_ERR_NAN;
+        break;
+      }
+      for (int i = k - 1; i >= 0; --i) {           // back substitution H y = g
+        double acc = g[i];
+        for (int q = i + 1; q < k; ++q) acc -= H[(size_t)i * m + q] * y[q];
+        y[i] = acc / H[(size_t)i * m + i];
+      }
+      for (int i = 0; i < k; ++i) C.host_pinned[i] = y[i];
+      CUDA_TRY(cudaMemcpyAsync(C.ydev, C.host_pinned, k * sizeof(double), cudaMemcpyHostToDevice, s));
+      if (prec == SBM_F32)
+        CUDA_TRY(launch_multi_axpy<float>(static_cast<float*>(C.Z), N, k, C.ydev, 1.0, x, N, s));
+      else
+        CUDA_TRY(launch_multi_axpy<double>(static_cast<double*>(C.Z), N, k, C.ydev, 1.0, x, N, s));
+      CUDA_TRY(cudaStreamSynchronize(s));          // host_pinned is reused by the next norm
+      loc.restarts += 1;
+    }
+  }
+  CUDA_TRY(cudaEventRecord(C.ev1, s));
+  CUDA_TRY(cudaEventSynchronize(C.ev1));
+  float ms = 0;
+  CUDA_TRY(cudaEventElapsedTime(&ms, C.ev0, C.ev1));
+  loc.ms_total = ms;
+  if (info) *info = loc;
+  if (status == SBM_ERR_NAN) return set_error(status, "non-finite value in FGMRES");
+  if (status == SBM_ERR_NOT_CONVERGED) return set_error(status, "FGMRES did not reach the tolerance");
+  return SBM_OK;
+}
+
+Context* ctx_of(void* p) { return static_cast<Context*>(p); }
+
+int check_level(const Context* C, int& level) {
+  if (!C) return set_error(SBM_ERR_ARG, "null context");
+  if (C->lv.empty()) return set_error(SBM_ERR_ARG, "context has no levels");
+  if (level < 0) level = (int)C->lv.size() - 1;
+  if (level >= (int)C->lv.size()) return set_error(SBM_ERR_ARG, "level out of range");
+  return SBM_OK;
+}
+
+template <typename F>
+int guarded(F&& f) {
+  try {
+    return f();
+  } catch (const SetupError& e) {
+    return set_error(e.code, e.msg);
+  } catch (const std::bad_alloc&) {
+    return set_error(SBM_ERR_ALLOC, "host allocation failed");
+  } catch (const std::exception& e) {
+    return set_error(SBM_ERR_ARG, e.what());
+  }
+}
+
+}  // namespace
+}  // namespace sbm
+
+using namespace sbm;
+
+extern "C" {
+
+int sbm_setup(const sbm_setup_desc* desc, void** out) {
+  if (out) *out = nullptr;
+  if (!desc || !out) return set_error(SBM_ERR_ARG, "null argument");
+  return guarded([&]() -> int {
+    *out = build_context(*desc, true);
+    return SBM_OK;
+  });
+}
+
+int sbm_setup_host(const sbm_setup_desc* desc, void** out) {
+  if (out) *out = nullptr;
+  if (!desc || !out) return set_error(SBM_ERR_ARG, "null argument");
+  return guarded([&]() -> int {
+    *out = build_context(*desc, false);
+    static_cast<Context*>(*out)->host_only = true;
+    return SBM_OK;
+  });
+}
+
+int sbm_host_apply(const void* ctx, int level, const double* x_host, double* y_host) {
+  const Context* C = static_cast<const Context*>(ctx);
+  if (int e = check_level(C, level)) return e;
+  if (!x_host || !y_host || x_host == y_host) return set_error(SBM_ERR_ARG, "bad vector pointers");
+  return guarded([&]() -> int {
+    host_apply_level(C->lv[level].H, x_host, y_host);
+    return SBM_OK;
+  });
+}
+
+int sbm_host_rhs(const void* ctx, double* b_host) {
+  const Context* C = static_cast<const Context*>(ctx);
+  if (!C || !b_host) return set_error(SBM_ERR_ARG, "null argument");
+  std::memcpy(b_host, C->rhs_host.data(), C->rhs_host.size() * sizeof(double));
+  return SBM_OK;
+}
+
+void sbm_destroy(void* ctx) { delete ctx_of(ctx); }
+
+const char* sbm_last_error(void) { return g_last_error.c_str(); }
+
+int sbm_num_levels(const void* ctx, int* out) {
+  if (!ctx || !out) return set_error(SBM_ERR_ARG, "null argument");
+  *out = (int)static_cast<const Context*>(ctx)->lv.size();
+  return SBM_OK;
+}
+
+int sbm_info(const void* ctx, int level, sbm_level_info* out) {
+  const Context* C = static_cast<const Context*>(ctx);
+  if (int e = check_level(C, level)) return e;
+  if (!out) return set_error(SBM_ERR_ARG, "null output");
+  const HostLevel& H = C->lv[level].H;
+  std::memset(out, 0, sizeof(*out));
+  out->n = H.n;
+  out->p = H.p;
+  out->h = H.h;
+  out->n_active = H.n_act;
+  out->n_dof = H.n_dof();
+  out->n_boundary = H.n_bnd;
+  out->n_sface = H.n_sface;
+  for (int c = 0; c < 9; ++c) out->colour_start[c] = H.colour_start[c];
+  for (int c = 0; c < 8; ++c) out->colour_nbnd[c] = H.colour_nbnd[c];
+  return SBM_OK;
+}
+
+int sbm_layout(const void* ctx, int level, int* coords_host) {
+  const Context* C = static_cast<const Context*>(ctx);
+  if (int e = check_level(C, level)) return e;
+  if (!coords_host) return set_error(SBM_ERR_ARG, "null output");
+  const HostLevel& H = C->lv[level].H;
+  std::memcpy(coords_host, H.cell.data(), H.cell.size() * sizeof(int));
+  return SBM_OK;
+}
+
+int sbm_export_geometry(const void* ctx, int level, int* n_faces, int* cell_host, int* slot_host, double* d_host) {
+  const Context* C = static_cast<const Context*>(ctx);
+  if (int e = check_level(C, level)) return e;
+  const HostLevel& H = C->lv[level].H;
+  if (n_faces) *n_faces = H.n_sface;
+  if (cell_host) std::memcpy(cell_host, H.sf_cell.data(), H.sf_cell.size() * sizeof(int));
+  if (slot_host) std::memcpy(slot_host, H.sf_slot.data(), H.sf_slot.size() * sizeof(int));
+  if (d_host) std::memcpy(d_host, H.sf_d.data(), H.sf_d.size() * sizeof(double));
+  return SBM_OK;
+}
+
+int sbm_rhs(void* ctx, double* b_dev) {
+  Context* C = ctx_of(ctx);
+  if (C && C->host_only) return set_error(SBM_ERR_ARG, "host-only context");
+  if (!C || !b_dev) return set_error(SBM_ERR_ARG, "null argument");
+  return guarded([&]() -> int {
+    CUDA_TRY(cudaMemcpyAsync(b_dev, C->rhs_host.data(), C->rhs_host.size() * sizeof(double),
+                             cudaMemcpyHostToDevice, C->stream));
+    CUDA_TRY(cudaStreamSynchronize(C->stream));
+    return SBM_OK;
+  });
+}
+
+int sbm_apply(void* ctx, int level, int dtype, const void* x_dev, void* y_dev) {
+  Context* C = ctx_of(ctx);
+  if (C && C->host_only) return set_error(SBM_ERR_ARG, "host-only context");
+  if (int e = check_level(C, level)) return e;
+  if (!x_dev || !y_dev || x_dev == y_dev) return set_error(SBM_ERR_ARG, "bad vector pointers");
+  return guarded([&]() -> int {
+    DevLevel& L = C->lv[level];
+    if (dtype == SBM_F64)
+      CUDA_TRY((launch_apply<double, double>(L.H.dim, L.H.p, L.P64, (const double*)x_dev, nullptr, (double*)y_dev, 0,
+                                             C->stream)));
+    else if (dtype == SBM_F32)
+      CUDA_TRY((launch_apply<float, float>(L.H.dim, L.H.p, L.P32, (const float*)x_dev, nullptr, (float*)y_dev, 0,
+                                           C->stream)));
+    else
+      return set_error(SBM_ERR_ARG, "dtype");
+    return SBM_OK;
+  });
+}
+
+int sbm_residual(void* ctx, int level, int dtype, const void* f_dev, const void* u_dev, void* r_dev) {
+  Context* C = ctx_of(ctx);
+  if (C && C->host_only) return set_error(SBM_ERR_ARG, "host-only context");
+  if (int e = check_level(C, level)) return e;
+  if (!f_dev || !u_dev || !r_dev || u_dev == r_dev) return set_error(SBM_ERR_ARG, "bad vector pointers");
+  return guarded([&]() -> int {
+    DevLevel& L = C->lv[level];
+    if (dtype == SBM_F64)
+      CUDA_TRY((launch_apply<double, double>(L.H.dim, L.H.p, L.P64, (const double*)u_dev, (const double*)f_dev,
+                                             (double*)r_dev, 1, C->stream)));
+    else if (dtype == SBM_F32)
+      CUDA_TRY((launch_apply<float, float>(L.H.dim, L.H.p, L.P32, (const float*)u_dev, (const float*)f_dev,
+                                           (float*)r_dev, 1, C->stream)));
+    else
+      return set_error(SBM_ERR_ARG, "dtype");
+    return SBM_OK;
+  });
+}
+
+int sbm_smooth(void* ctx, int level, int dtype, int reverse, const void* f_dev, void* u_dev) {
+  Context* C = ctx_of(ctx);
+  if (C && C->host_only) return set_error(SBM_ERR_ARG, "host-only context");
+  if (int e = check_level(C, level)) return e;
+  if (!f_dev || !u_dev || f_dev == u_dev) return set_error(SBM_ERR_ARG, "bad vector pointers");
+  return guarded([&]() -> int {
+    DevLevel& L = C->lv[level];
+    if (dtype == SBM_F64)
+      CUDA_TRY(launch_smooth<double>(L.H.dim, L.H.p, L.P64, reverse, (const double*)f_dev, (double*)u_dev, C->stream));
+    else if (dtype == SBM_F32)
+      CUDA_TRY(launch_smooth<float>(L.H.dim, L.H.p, L.P32, reverse, (const float*)f_dev, (float*)u_dev, C->stream));
+    else
+      return set_error(SBM_ERR_ARG, "dtype");
+    return SBM_OK;
+  });
+}
+
+int sbm_restrict(void* ctx, int level, int dtype, const void* rf_dev, void* rc_dev) {
+  Context* C = ctx_of(ctx);
+  if (C && C->host_only) return set_error(SBM_ERR_ARG, "host-only context");
+  if (int e = check_level(C, level)) return e;
+  if (level < 1) return set_error(SBM_ERR_ARG, "restriction needs level >= 1");
+  if (!rf_dev || !rc_dev) return set_error(SBM_ERR_ARG, "null vector");
+  return guarded([&]() -> int {
+    DevLevel& L = C->lv[level];
+    const int pc = C->lv[level - 1].H.p;
+    if (dtype == SBM_F64)
+      CUDA_TRY(launch_restrict<double>(L.H.dim, L.H.p, pc, L.T64, (const double*)rf_dev, (double*)rc_dev, C->stream));
+    else if (dtype == SBM_F32)
+      CUDA_TRY(launch_restrict<float>(L.H.dim, L.H.p, pc, L.T32, (const float*)rf_dev, (float*)rc_dev, C->stream));
+    else
+      return set_error(SBM_ERR_ARG, "dtype");
+    return SBM_OK;
+  });
+}
+
+int sbm_prolong_add(void* ctx, int level, int dtype, const void* ec_dev, void* uf_dev) {
+  Context* C = ctx_of(ctx);
+  if (C && C->host_only) return set_error(SBM_ERR_ARG, "host-only context");
+  if (int e = check_level(C, level)) return e;
+  if (level < 1) return set_error(SBM_ERR_ARG, "prolongation needs level >= 1");
+  if (!ec_dev || !uf_dev) return set_error(SBM_ERR_ARG, "null vector");
+  return guarded([&]() -> int {
+    DevLevel& L = C->lv[level];
+    const int pc = C->lv[level - 1].H.p;
+    if (dtype == SBM_F64)
+      CUDA_TRY(launch_prolong<double>(L.H.dim, L.H.p, pc, L.T64, (const double*)ec_dev, (double*)uf_dev, C->stream));
+    else if (dtype == SBM_F32)
+      CUDA_TRY(launch_prolong<float>(L.H.dim, L.H.p, pc, L.T32, (const float*)ec_dev, (float*)uf_dev, C->stream));
+    else
+      return set_error(SBM_ERR_ARG, "dtype");
+    return SBM_OK;
+  });
+}
+
+int sbm_coarse_solve(void* ctx, int dtype, const void* r_dev, void* e_dev) {
+  Context* C = ctx_of(ctx);
+  if (C && C->host_only) return set_error(SBM_ERR_ARG, "host-only context");
+  if (!C || !r_dev || !e_dev || r_dev == e_dev) return set_error(SBM_ERR_ARG, "bad argument");
+  return guarded([&]() -> int {
+    DevLevel& L = C->lv[0];
+    if (dtype == SBM_F64)
+      CUDA_TRY(launch_coarse<double>(L.coarse_inv, L.H.n_dof(), (const double*)r_dev, (double*)e_dev, C->stream));
+    else if (dtype == SBM_F32)
+      CUDA_TRY(launch_coarse<float>(L.coarse_inv, L.H.n_dof(), (const float*)r_dev, (float*)e_dev, C->stream));
+    else
+      return set_error(SBM_ERR_ARG, "dtype");
+    return SBM_OK;
+  });
+}
+
+int sbm_vcycle(void* ctx, int dtype, const void* r_dev, void* z_dev) {
+  Context* C = ctx_of(ctx);
+  if (C && C->host_only) return set_error(SBM_ERR_ARG, "host-only context");
+  if (!C || !r_dev || !z_dev || r_dev == z_dev) return set_error(SBM_ERR_ARG, "bad argument");
+  return guarded([&]() -> int {
+    if (dtype == SBM_F64) {
+      ensure_work<double>(*C);
+      vcycle_rec<double>(*C, C->finest(), (const double*)r_dev, (double*)z_dev);
+    } else if (dtype == SBM_F32) {
+      ensure_work<float>(*C);
+      vcycle_rec<float>(*C, C->finest(), (const float*)r_dev, (float*)z_dev);
+    } else {
+      return set_error(SBM_ERR_ARG, "dtype");
+    }
+    return SBM_OK;
+  });
+}
+
+int sbm_solve(void* ctx, const double* b_dev, double* x_dev, double tol, int restart, int max_it,
+              sbm_solve_info* info) {
+  Context* C = ctx_of(ctx);
+  if (C && C->host_only) return set_error(SBM_ERR_ARG, "host-only context");
+  if (!C || !b_dev || !x_dev || (const void*)b_dev == (void*)x_dev) return set_error(SBM_ERR_ARG, "bad argument");
+  return guarded([&]() -> int { return solve_impl(*C, b_dev, x_dev, tol, restart, max_it, info); });
+}
+
+int sbm_solve_host(void* ctx, const double* b_host, double* x_host, double tol, int restart, int max_it,
+                   sbm_solve_info* info) {
+  Context* C = ctx_of(ctx);
+  if (C && C->host_only) return set_error(SBM_ERR_ARG, "host-only context");
+  if (!C || !b_host || !x_host) return set_error(SBM_ERR_ARG, "bad argument");
+  return guarded([&]() -> int {
+    const size_t N = C->lv.back().H.n_dof();
+    if (!C->bbuf) {
+      C->bbuf = C->dalloc<double>(N);
+      C->xbuf = C->dalloc<double>(N);
+    }
+    CUDA_TRY(cudaMemcpyAsync(C->bbuf, b_host, N * sizeof(double), cudaMemcpyHostToDevice, C->stream));
+    CUDA_TRY(cudaMemsetAsync(C->xbuf, 0, N * sizeof(double), C->stream));
+    int rc = solve_impl(*C, C->bbuf, C->xbuf, tol, restart, max_it, info);
+    CUDA_TRY(cudaMemcpyAsync(x_host, C->xbuf, N * sizeof(double), cudaMemcpyDeviceToHost, C->stream));
+    CUDA_TRY(cudaStreamSynchronize(C->stream));
+    return rc;
+  });
+}
+
+}  // extern "C"

@@ -1,0 +1,151 @@
+// FP64 building blocks of FGMRES (Sec. 3: GMRES preconditioned by one V-cycle): multi-vector
+// dot products with a deterministic two-stage reduction (warp shuffles, then a fixed-order sum
+// of per-block partials), multi-vector AXPY, scaling and precision casts.
+#include <cuda_runtime.h>
+
+#include "ops.h"
+
+namespace sbm {
+
+namespace {
+
+constexpr int kDotThreads = 256;
+constexpr int kMaxVec = 32;
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+  return v;
+}
+
+// partial[block][k] = sum over this block's grid-stride share of V_k . w
+__global__ void __launch_bounds__(kDotThreads) k_multi_dot(const double* __restrict__ V, size_t ldv, int nv,
+                                                           const double* __restrict__ w, size_t N,
+                                                           double* __restrict__ partial) {
+  double acc[kMaxVec];
+#pragma unroll
+  for (int k = 0; k < kMaxVec; ++k) acc[k] = 0.0;
+  const size_t stride = (size_t)gridDim.x * blockDim.x;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += stride) {
+    const double wi = w[i];
+#pragma unroll
+    for (int k = 0; k < kMaxVec; ++k)
+      if (k < nv) acc[k] += V[k * ldv + i] * wi;
+  }
+  __shared__ double red[kDotThreads / 32][kMaxVec];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll
+  for (int k = 0; k < kMaxVec; ++k) {
+    if (k < nv) {
+      const double s = warp_sum(acc[k]);
+      if (lane == 0) red[warp][k] = s;
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x < nv) {
+    double s = 0.0;
+#pragma unroll
+    for (int q = 0; q < kDotThreads / 32; ++q) s += red[q][threadIdx.x];
+    partial[(size_t)blockIdx.x * kMaxVec + threadIdx.x] = s;
+  }
+}
+
+__global__ void k_reduce_partials(const double* __restrict__ partial, int nblk, int nv, double* __restrict__ out,
+                                  int take_sqrt) {
+  const int k = threadIdx.x;
+  if (k >= nv) return;
+  double s = 0.0;
+  for (int b = 0; b < nblk; ++b) s += partial[(size_t)b * kMaxVec + k];
+  out[k] = take_sqrt ? sqrt(s) : s;
+}
+
+template <typename TZ>
+__global__ void __launch_bounds__(256) k_multi_axpy(const TZ* __restrict__ Z, size_t ldz, int nv,
+                                                    const double* __restrict__ coef, double sign,
+                                                    double* __restrict__ w, size_t N) {
+  __shared__ double cf[kMaxVec];
+  if (threadIdx.x < nv) cf[threadIdx.x] = sign * coef[threadIdx.x];
+  __syncthreads();
+  const size_t stride = (size_t)gridDim.x * blockDim.x;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += stride) {
+    double s = w[i];
+    for (int k = 0; k < nv; ++k) s += cf[k] * (double)Z[k * ldz + i];
+    w[i] = s;
+  }
+}
+
+__global__ void k_div_scalar(const double* __restrict__ w, const double* __restrict__ s, double* __restrict__ v,
+                             size_t N) {
+  const double inv = 1.0 / s[0];
+  const size_t stride = (size_t)gridDim.x * blockDim.x;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += stride) v[i] = w[i] * inv;
+}
+
+template <typename TI, typename TO>
+__global__ void k_cast(const TI* __restrict__ x, TO* __restrict__ y, size_t N) {
+  const size_t stride = (size_t)gridDim.x * blockDim.x;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += stride) y[i] = (TO)x[i];
+}
+
+__global__ void k_hess_column(const double* h1, const double* h2, const double* hn, int k, double* col) {
+  const int i = threadIdx.x;
+  if (i < k) col[i] = h1[i] + h2[i];
+  if (i == k) col[k] = hn[0];
+}
+
+unsigned grid_for(size_t N) {
+  size_t g = (N + 255) / 256;
+  return (unsigned)(g < 1 ? 1 : (g > 152 * 8 ? 152 * 8 : g));
+}
+
+}  // namespace
+
+int dot_blocks(size_t N) {
+  size_t g = (N + kDotThreads * 4 - 1) / (kDotThreads * 4);
+  if (g < 1) g = 1;
+  if (g > 152 * 4) g = 152 * 4;
+  return (int)g;
+}
+
+cudaError_t launch_multi_dot(const double* V, size_t ldv, int nv, const double* w, size_t N, double* partial,
+                             double* out, int take_sqrt, cudaStream_t s) {
+  if (nv < 1 || nv > kMaxVec) return cudaErrorInvalidValue;
+  const int nblk = dot_blocks(N);
+  k_multi_dot<<<nblk, kDotThreads, 0, s>>>(V, ldv, nv, w, N, partial);
+  k_reduce_partials<<<1, kMaxVec, 0, s>>>(partial, nblk, nv, out, take_sqrt);
+  return cudaGetLastError();
+}
+
+template <typename TZ>
+cudaError_t launch_multi_axpy(const TZ* Z, size_t ldz, int nv, const double* coef, double sign, double* w,
+                              size_t N, cudaStream_t s) {
+  if (nv < 1 || nv > kMaxVec) return cudaErrorInvalidValue;
+  k_multi_axpy<TZ><<<grid_for(N), 256, 0, s>>>(Z, ldz, nv, coef, sign, w, N);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_div_scalar(const double* w, const double* sc, double* v, size_t N, cudaStream_t s) {
+  k_div_scalar<<<grid_for(N), 256, 0, s>>>(w, sc, v, N);
+  return cudaGetLastError();
+}
+
+template <typename TI, typename TO>
+cudaError_t launch_cast(const TI* x, TO* y, size_t N, cudaStream_t s) {
+  k_cast<TI, TO><<<grid_for(N), 256, 0, s>>>(x, y, N);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_hess_column(const double* h1, const double* h2, const double* hn, int k, double* col,
+                               cudaStream_t s) {
+  k_hess_column<<<1, 64, 0, s>>>(h1, h2, hn, k, col);
+  return cudaGetLastError();
+}
+
+template cudaError_t launch_multi_axpy<double>(const double*, size_t, int, const double*, double, double*, size_t,
+                                               cudaStream_t);
+template cudaError_t launch_multi_axpy<float>(const float*, size_t, int, const double*, double, double*, size_t,
+                                              cudaStream_t);
+template cudaError_t launch_cast<double, float>(const double*, float*, size_t, cudaStream_t);
+template cudaError_t launch_cast<float, double>(const float*, double*, size_t, cudaStream_t);
+
+}  // namespace sbm

@@ -1,0 +1,553 @@
+// CUDA kernels of one multigrid level (sm_103a): matrix-free DG-SBM operator, coloured block
+// Gauss-Seidel smoother, h- and p-transfers, coarse dense solve.
+//
+// Paper: arXiv 2506.12899.  Operator: Eqs. 7, 10, 11 (Sec. 2.2).  Smoother: Eqs. 14, 16 (Sec. 3.1).
+// Transfers: Eqs. 17, 18 (Sec. 3.2).
+//
+// Thread mapping: one thread per degree of freedom, CPB = floor(256 / (p+1)^d) cells per block.
+// A block stages its cells and their 2d face neighbours in shared memory with coalesced loads
+// (each cell's (p+1)^d values are contiguous), then every thread contracts the 1D element
+// matrices along each direction (sum factorisation on the Cartesian cell).
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "ops.h"
+
+namespace sbm {
+
+namespace {
+
+template <int D, int N1>
+struct Dims {
+  static constexpr int NP = D == 2 ? N1 * N1 : N1 * N1 * N1;
+  static constexpr int NQ = D == 2 ? N1 : N1 * N1;
+  static constexpr int NS = 2 * D;
+  static constexpr int CPB = 256 / NP > 0 ? 256 / NP : 1;
+  static constexpr int NT = CPB * NP;
+};
+
+template <int N1>
+__device__ __forceinline__ int stride_of(int dir) {
+  return dir == 0 ? 1 : (dir == 1 ? N1 : N1 * N1);
+}
+
+template <int D, int N1>
+__device__ __forceinline__ void decompose(int i, int (&ii)[3]) {
+  ii[0] = i % N1;
+  ii[1] = (i / N1) % N1;
+  ii[2] = D == 3 ? i / (N1 * N1) : 0;
+}
+
+// Tangential index t (tangential dims ascending, first fastest) and weight of dof ii on the
+// faces normal to dir.
+template <int D, int N1, typename R>
+__device__ __forceinline__ int tang(const int (&ii)[3], int dir, const R* w, R& wt) {
+  if (D == 2) {
+    const int k = ii[1 - dir];
+    wt = w[k];
+    return k;
+  }
+  const int a = dir == 0 ? 1 : 0, b = dir == 2 ? 1 : 2;
+  wt = w[ii[a]] * w[ii[b]];
+  return ii[a] + N1 * ii[b];
+}
+
+template <typename R>
+__device__ __forceinline__ void load_consts(const LevelConsts<R>& src, LevelConsts<R>& dst) {
+  constexpr int n = sizeof(LevelConsts<R>) / sizeof(R);
+  const R* s = reinterpret_cast<const R*>(&src);
+  R* d = reinterpret_cast<R*>(&dst);
+  for (int i = threadIdx.x; i < n; i += blockDim.x) d[i] = s[i];
+}
+
+// Index of cell a among boundary cells (cells owning a surrogate face), or -1.
+template <typename R>
+__device__ __forceinline__ int bnd_index(const LevelParams<R>& P, int a, int ncol) {
+  int c = 0;
+#pragma unroll
+  for (int k = 1; k < 8; ++k)
+    if (k < ncol && a >= P.colour_start[k]) c = k;
+  const int off = a - P.colour_start[c];
+  return off < P.colour_nbnd[c] ? P.bstart[c] + off : -1;
+}
+
+// Nitsche-SBM surrogate-face terms of Eq. 7 for the dofs of one block (reference form; the
+// caller multiplies by h^(d-2)).  Per face point t: trace U_t, normal derivative G_t,
+// extended value E_t = U_t + d^.grad^u (extension 0) or the cell polynomial at x~ + d
+// (extension 1); dof (k, t) receives w_t [ e_s[k] (-s G_t + sigma^ E_t) - alpha s d_s[k] E_t ].
+// Every thread of the block must call this (it contains barriers).  smask bit s marks slot s
+// (= 2 * direction + side) as a surrogate face of this thread's cell.
+template <int D, int N1, typename R>
+__device__ __forceinline__ R sbm_face_terms(const LevelParams<R>& P, const LevelConsts<R>& C, int bidx,
+                                            unsigned smask, int c, int i, const int (&ii)[3], const R* sU, R* sA,
+                                            R* sB, R* sE) {
+  using Dm = Dims<D, N1>;
+  constexpr int NP = Dm::NP, NQ = Dm::NQ, NS = Dm::NS;
+  R acc = 0;
+#pragma unroll 1
+  for (int slot = 0; slot < NS; ++slot) {
+    const int dir = slot >> 1, side = slot & 1;
+    const bool sf = bidx >= 0 && ((smask >> slot) & 1u);
+    const int st = stride_of<N1>(dir), id = ii[dir], base = i - id * st;
+    R wt;
+    const int t = tang<D, N1>(ii, dir, C.w, wt);
+    const R* es = side ? C.e1 : C.e0;
+    const R* ds = side ? C.d1 : C.d0;
+    if (sf && id == 0) {
+      R su = 0, sd = 0;
+#pragma unroll
+      for (int k = 0; k < N1; ++k) {
+        const R v = sU[c * NP + base + k * st];
+        su += es[k] * v;
+        sd += ds[k] * v;
+      }
+      sA[c * NQ + t] = su;
+      sB[c * NQ + t] = sd;
+    }
+    __syncthreads();
+    if (sf && id == 0) {
+      const R* dh = P.dhat + ((size_t)bidx * NS + slot) * D * NQ;
+      R E;
+      if (P.extension == 0) {
+        E = sA[c * NQ + t] + dh[dir * NQ + t] * sB[c * NQ + t];
+        if (D == 2) {
+          const int m = 1 - dir;
+          R g = 0;
+#pragma unroll
+          for (int q = 0; q < N1; ++q) g += C.Dm[t * N1 + q] * sA[c * NQ + q];
+          E += dh[m * NQ + t] * g;
+        } else {
+          const int ma = dir == 0 ? 1 : 0, mb = dir == 2 ? 1 : 2;
+          const int ta = t % N1, tb = t / N1;
+          R ga = 0, gb = 0;
+#pragma unroll
+          for (int q = 0; q < N1; ++q) {
+            ga += C.Dm[ta * N1 + q] * sA[c * NQ + q + N1 * tb];
+            gb += C.Dm[tb * N1 + q] * sA[c * NQ + ta + N1 * q];
+          }
+          E += dh[ma * NQ + t] * ga + dh[mb * NQ + t] * gb;
+        }
+      } else {
+        R lv[3][N1];
+#pragma unroll
+        for (int m = 0; m < D; ++m) {
+          const R y = (m == dir ? R(side) : C.x[ii[m]]) + dh[m * NQ + t];
+#pragma unroll
+          for (int k = 0; k < N1; ++k) {
+            R v = C.inv_denom[k];
+#pragma unroll
+            for (int j = 0; j < N1; ++j)
+              if (j != k) v *= (y - C.x[j]);
+            lv[m][k] = v;
+          }
+        }
+        E = 0;
+#pragma unroll
+        for (int j = 0; j < NP; ++j) {
+          R ph = lv[0][j % N1] * lv[1][(j / N1) % N1];
+          if (D == 3) ph *= lv[2][j / (N1 * N1)];
+          E += ph * sU[c * NP + j];
+        }
+      }
+      sE[c * NQ + t] = E;
+    }
+    __syncthreads();
+    if (sf) {
+      const R sg = side ? R(1) : R(-1);
+      const R E = sE[c * NQ + t], G = sB[c * NQ + t];
+      acc += wt * (es[id] * (-sg * G + P.sigG * E) - P.alpha * sg * ds[id] * E);
+    }
+    __syncthreads();
+  }
+  return acc;
+}
+
+// y = A x  (MODE 0)  or  y = f - A x  (MODE 1).
+template <int D, int N1, typename TI, typename R, int MODE>
+__global__ void __launch_bounds__(256) k_apply(const __grid_constant__ LevelParams<R> P, const TI* __restrict__ x,
+                                               const R* __restrict__ f, R* __restrict__ y) {
+  using Dm = Dims<D, N1>;
+  constexpr int NP = Dm::NP, NQ = Dm::NQ, NS = Dm::NS, CPB = Dm::CPB;
+  __shared__ LevelConsts<R> C;
+  __shared__ R sU[CPB * NP];
+  __shared__ R sN[CPB * NS * NP];
+  __shared__ R sA[CPB * NQ], sB[CPB * NQ], sE[CPB * NQ];
+  load_consts(P.k, C);
+  const int c = threadIdx.x / NP, i = threadIdx.x - c * NP;
+  const int a = blockIdx.x * CPB + c;
+  const bool valid = threadIdx.x < CPB * NP && a < P.n_act;
+  int nb[NS];
+#pragma unroll
+  for (int s = 0; s < NS; ++s) nb[s] = -1;
+  if (valid) {
+    sU[c * NP + i] = (R)x[(size_t)a * NP + i];
+#pragma unroll
+    for (int s = 0; s < NS; ++s) {
+      nb[s] = P.nbr[(size_t)s * P.n_act + a];
+      sN[(c * NS + s) * NP + i] = nb[s] >= 0 ? (R)x[(size_t)nb[s] * NP + i] : R(0);
+    }
+  }
+  __syncthreads();
+  int ii[3];
+  decompose<D, N1>(i, ii);
+  R acc = 0;
+  if (valid) {
+#pragma unroll
+    for (int dir = 0; dir < D; ++dir) {
+      const int st = stride_of<N1>(dir), id = ii[dir], base = i - id * st;
+      R wt;
+      tang<D, N1>(ii, dir, C.w, wt);
+      const int mask = (nb[2 * dir] >= 0) + 2 * (nb[2 * dir + 1] >= 0);
+      const R* Lm = C.L[mask];
+      R s = 0;
+#pragma unroll
+      for (int k = 0; k < N1; ++k) s += Lm[id * N1 + k] * sU[c * NP + base + k * st];
+      if (nb[2 * dir] >= 0) {
+#pragma unroll
+        for (int k = 0; k < N1; ++k) s += C.Bpm[id * N1 + k] * sN[(c * NS + 2 * dir) * NP + base + k * st];
+      }
+      if (nb[2 * dir + 1] >= 0) {
+#pragma unroll
+        for (int k = 0; k < N1; ++k) s += C.Bmp[id * N1 + k] * sN[(c * NS + 2 * dir + 1) * NP + base + k * st];
+      }
+      acc += wt * s;
+    }
+  }
+  const int bidx = valid ? bnd_index(P, a, 1 << D) : -1;
+  unsigned smask = 0;                               // bit s: face slot s is a surrogate face
+#pragma unroll
+  for (int s = 0; s < NS; ++s) smask |= (nb[s] < 0 ? 1u : 0u) << s;
+  if (__syncthreads_or(bidx >= 0)) acc += sbm_face_terms<D, N1, R>(P, C, bidx, smask, c, i, ii, sU, sA, sB, sE);
+  if (valid) {
+    R v = P.hscale * acc;
+    if (MODE == 1) v = f[(size_t)a * NP + i] - v;
+    y[(size_t)a * NP + i] = v;
+  }
+}
+
+// One colour of the block Gauss-Seidel sweep (Eq. 16): for each cell K of the colour,
+//   t_K = f_K - sum_{N != K} A_KN u_N  (interior-face couplings only; the SBM terms lie in A_KK),
+//   u_K <- (1 - omega) u_K + omega A_KK^{-1} t_K,
+// which equals u_K + omega A_KK^{-1}(f - A u)_K.  Blocks [0, nblk_b) take the colour's boundary
+// cells (dense inverse), the remaining blocks its interior cells (fast diagonalisation
+// A_KK^{-1} = h^(2-d) S^(x d) diag(1 / sum lambda) (S^T)^(x d)).
+template <int D, int N1, typename R>
+__global__ void __launch_bounds__(256) k_smooth(const __grid_constant__ LevelParams<R> P, int cs, int nbnd, int ce,
+                                                int nblk_b, int b0, const R* __restrict__ f, R* __restrict__ u) {
+  using Dm = Dims<D, N1>;
+  constexpr int NP = Dm::NP, NS = Dm::NS, CPB = Dm::CPB;
+  __shared__ LevelConsts<R> C;
+  __shared__ R sN[CPB * NS * NP];
+  __shared__ R sT[CPB * NP], sW[CPB * NP];
+  load_consts(P.k, C);
+  const bool isB = (int)blockIdx.x < nblk_b;
+  const int first = isB ? cs + blockIdx.x * CPB : cs + nbnd + (blockIdx.x - nblk_b) * CPB;
+  const int last = isB ? cs + nbnd : ce;
+  const int c = threadIdx.x / NP, i = threadIdx.x - c * NP;
+  const int a = first + c;
+  const bool valid = threadIdx.x < CPB * NP && a < last;
+  int nb[NS];
+  R uold = 0;
+  if (valid) {
+#pragma unroll
+    for (int s = 0; s < NS; ++s) {
+      nb[s] = P.nbr[(size_t)s * P.n_act + a];
+      sN[(c * NS + s) * NP + i] = nb[s] >= 0 ? u[(size_t)nb[s] * NP + i] : R(0);
+    }
+    if (P.omega != R(1)) uold = u[(size_t)a * NP + i];
+  }
+  __syncthreads();
+  int ii[3];
+  decompose<D, N1>(i, ii);
+  R t = 0;
+  if (valid) {
+    R acc = 0;
+#pragma unroll
+    for (int dir = 0; dir < D; ++dir) {
+      const int st = stride_of<N1>(dir), id = ii[dir], base = i - id * st;
+      R wt;
+      tang<D, N1>(ii, dir, C.w, wt);
+      R s = 0;
+      if (nb[2 * dir] >= 0) {
+#pragma unroll
+        for (int k = 0; k < N1; ++k) s += C.Bpm[id * N1 + k] * sN[(c * NS + 2 * dir) * NP + base + k * st];
+      }
+      if (nb[2 * dir + 1] >= 0) {
+#pragma unroll
+        for (int k = 0; k < N1; ++k) s += C.Bmp[id * N1 + k] * sN[(c * NS + 2 * dir + 1) * NP + base + k * st];
+      }
+      acc += wt * s;
+    }
+    t = f[(size_t)a * NP + i] - P.hscale * acc;
+  }
+  sT[c * NP + i] = t;
+  __syncthreads();
+  R yv = 0;
+  if (isB) {
+    if (valid) {
+      const R* Bi = P.binvT + (size_t)(b0 + (a - cs)) * NP * NP;
+#pragma unroll 8
+      for (int j = 0; j < NP; ++j) yv += Bi[(size_t)j * NP + i] * sT[c * NP + j];
+    }
+  } else {
+    R* src = sT;
+    R* dst = sW;
+#pragma unroll
+    for (int dir = 0; dir < D; ++dir) {              // (S^T)^(x d) t
+      const int st = stride_of<N1>(dir), id = ii[dir], base = i - id * st;
+      R v = 0;
+#pragma unroll
+      for (int m = 0; m < N1; ++m) v += C.S[m * N1 + id] * src[c * NP + base + m * st];
+      yv = v;
+      dst[c * NP + i] = v;
+      __syncthreads();
+      R* tmp = src;
+      src = dst;
+      dst = tmp;
+    }
+    R lsum = C.lam[ii[0]] + C.lam[ii[1]];
+    if (D == 3) lsum += C.lam[ii[2]];
+    yv = yv / (P.hscale * lsum);
+    dst[c * NP + i] = yv;
+    __syncthreads();
+    {
+      R* tmp = src;
+      src = dst;
+      dst = tmp;
+    }
+#pragma unroll
+    for (int dir = 0; dir < D; ++dir) {              // S^(x d) v
+      const int st = stride_of<N1>(dir), id = ii[dir], base = i - id * st;
+      R v = 0;
+#pragma unroll
+      for (int m = 0; m < N1; ++m) v += C.S[id * N1 + m] * src[c * NP + base + m * st];
+      yv = v;
+      if (dir + 1 < D) {
+        dst[c * NP + i] = v;
+        __syncthreads();
+        R* tmp = src;
+        src = dst;
+        dst = tmp;
+      }
+    }
+  }
+  if (valid) u[(size_t)a * NP + i] = P.omega == R(1) ? yv : (R(1) - P.omega) * uold + P.omega * yv;
+}
+
+// Restriction rc = P^T rf (Eq. 18), gathered per coarse dof.
+template <int D, int NF, int NC, typename R>
+__global__ void __launch_bounds__(256) k_restrict(const __grid_constant__ TransferParams<R> T,
+                                                  const R* __restrict__ rf, R* __restrict__ rc) {
+  constexpr int NPF = D == 2 ? NF * NF : NF * NF * NF;
+  constexpr int NPC = D == 2 ? NC * NC : NC * NC * NC;
+  const size_t gid = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int cc = (int)(gid / NPC), j = (int)(gid % NPC);
+  if (cc >= T.n_act_c) return;
+  const int j0 = j % NC, j1 = (j / NC) % NC, j2 = D == 3 ? j / (NC * NC) : 0;
+  R sum = 0;
+  const int nchild = T.hmode ? (1 << D) : 1;
+  for (int o = 0; o < nchild; ++o) {
+    int src;
+    const R *P0, *P1, *P2;
+    if (T.hmode) {
+      src = T.children[(size_t)o * T.n_act_c + cc];
+      if (src < 0) continue;
+      P0 = T.Ph[o & 1];
+      P1 = T.Ph[(o >> 1) & 1];
+      P2 = T.Ph[(o >> 2) & 1];
+    } else {
+      src = cc;
+      P0 = P1 = P2 = T.Pp;
+    }
+    const R* r = rf + (size_t)src * NPF;
+    R s2 = 0;
+#pragma unroll
+    for (int i2 = 0; i2 < (D == 3 ? NF : 1); ++i2) {
+      R s1 = 0;
+#pragma unroll
+      for (int i1 = 0; i1 < NF; ++i1) {
+        R s0 = 0;
+#pragma unroll
+        for (int i0 = 0; i0 < NF; ++i0) s0 += P0[i0 * NC + j0] * r[i0 + NF * i1 + NF * NF * i2];
+        s1 += P1[i1 * NC + j1] * s0;
+      }
+      s2 += (D == 3 ? P2[i2 * NC + j2] : R(1)) * s1;
+    }
+    sum += s2;
+  }
+  rc[(size_t)cc * NPC + j] = sum;
+}
+
+// Prolongation uf += P ec (Eq. 17) per fine dof; fine cells without an active parent get 0.
+template <int D, int NF, int NC, typename R>
+__global__ void __launch_bounds__(256) k_prolong(const __grid_constant__ TransferParams<R> T,
+                                                 const R* __restrict__ ec, R* __restrict__ uf) {
+  constexpr int NPF = D == 2 ? NF * NF : NF * NF * NF;
+  constexpr int NPC = D == 2 ? NC * NC : NC * NC * NC;
+  const size_t gid = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int a = (int)(gid / NPF), i = (int)(gid % NPF);
+  if (a >= T.n_act_f) return;
+  int par;
+  const R *P0, *P1, *P2;
+  if (T.hmode) {
+    const int code = T.parent_code[a];
+    if (code < 0) return;
+    par = code >> 3;
+    P0 = T.Ph[code & 1];
+    P1 = T.Ph[(code >> 1) & 1];
+    P2 = T.Ph[(code >> 2) & 1];
+  } else {
+    par = a;
+    P0 = P1 = P2 = T.Pp;
+  }
+  const int i0 = i % NF, i1 = (i / NF) % NF, i2 = D == 3 ? i / (NF * NF) : 0;
+  const R* e = ec + (size_t)par * NPC;
+  R s2 = 0;
+#pragma unroll
+  for (int j2 = 0; j2 < (D == 3 ? NC : 1); ++j2) {
+    R s1 = 0;
+#pragma unroll
+    for (int j1 = 0; j1 < NC; ++j1) {
+      R s0 = 0;
+#pragma unroll
+      for (int j0 = 0; j0 < NC; ++j0) s0 += P0[i0 * NC + j0] * e[j0 + NC * j1 + NC * NC * j2];
+      s1 += P1[i1 * NC + j1] * s0;
+    }
+    s2 += (D == 3 ? P2[i2 * NC + j2] : R(1)) * s1;
+  }
+  uf[(size_t)a * NPF + i] += s2;
+}
+
+// e = Ainv r in FP64; one warp per row.
+template <typename T>
+__global__ void __launch_bounds__(256) k_coarse(const double* __restrict__ Ainv, int N, const T* __restrict__ r,
+                                                T* __restrict__ e) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int row = blockIdx.x * (blockDim.x >> 5) + warp;
+  if (row >= N) return;
+  double s = 0;
+  for (int col = lane; col < N; col += 32) s += Ainv[(size_t)row * N + col] * (double)r[col];
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+  if (lane == 0) e[row] = (T)s;
+}
+
+inline unsigned ceil_div(size_t a, size_t b) { return (unsigned)((a + b - 1) / b); }
+
+}  // namespace
+
+// ------------------------------------------------------------------------------------ launchers
+#define SBM_DISPATCH_DP(dim, p, MACRO)                 \
+  do {                                                 \
+    if (dim == 2 && p == 1) { MACRO(2, 2); }           \
+    else if (dim == 2 && p == 2) { MACRO(2, 3); }      \
+    else if (dim == 2 && p == 3) { MACRO(2, 4); }      \
+    else if (dim == 3 && p == 1) { MACRO(3, 2); }      \
+    else if (dim == 3 && p == 2) { MACRO(3, 3); }      \
+    else if (dim == 3 && p == 3) { MACRO(3, 4); }      \
+    else return cudaErrorInvalidValue;                 \
+  } while (0)
+
+template <typename TI, typename R>
+cudaError_t launch_apply(int dim, int p, const LevelParams<R>& P, const TI* x, const R* f, R* y, int mode,
+                         cudaStream_t s) {
+  if (P.n_act == 0) return cudaSuccess;
+#define SBM_APPLY(D, N1)                                                                 \
+  {                                                                                      \
+    using Dm = Dims<D, N1>;                                                              \
+    const unsigned grid = ceil_div(P.n_act, Dm::CPB);                                    \
+    if (mode == 0) k_apply<D, N1, TI, R, 0><<<grid, Dm::NT, 0, s>>>(P, x, f, y);         \
+    else k_apply<D, N1, TI, R, 1><<<grid, Dm::NT, 0, s>>>(P, x, f, y);                   \
+  }
+  SBM_DISPATCH_DP(dim, p, SBM_APPLY);
+#undef SBM_APPLY
+  return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t launch_smooth(int dim, int p, const LevelParams<R>& P, int reverse, const R* f, R* u, cudaStream_t s) {
+  const int ncol = 1 << dim;
+  for (int q = 0; q < ncol; ++q) {
+    const int col = reverse ? ncol - 1 - q : q;
+    const int cs = P.colour_start[col], ce = P.colour_start[col + 1], nbnd = P.colour_nbnd[col];
+#define SBM_SMOOTH(D, N1)                                                                          \
+  {                                                                                                \
+    using Dm = Dims<D, N1>;                                                                        \
+    const int nblk_b = (int)ceil_div(nbnd, Dm::CPB);                                               \
+    const int nblk_i = (int)ceil_div(ce - cs - nbnd, Dm::CPB);                                     \
+    if (nblk_b + nblk_i > 0)                                                                       \
+      k_smooth<D, N1, R><<<nblk_b + nblk_i, Dm::NT, 0, s>>>(P, cs, nbnd, ce, nblk_b, P.bstart[col], f, u); \
+  }
+    SBM_DISPATCH_DP(dim, p, SBM_SMOOTH);
+#undef SBM_SMOOTH
+  }
+  return cudaGetLastError();
+}
+
+#define SBM_DISPATCH_T(dim, pf, pc, MACRO)                          \
+  do {                                                              \
+    if (dim == 2 && pf == 1 && pc == 1) { MACRO(2, 2, 2); }         \
+    else if (dim == 2 && pf == 2 && pc == 1) { MACRO(2, 3, 2); }    \
+    else if (dim == 2 && pf == 3 && pc == 2) { MACRO(2, 4, 3); }    \
+    else if (dim == 3 && pf == 1 && pc == 1) { MACRO(3, 2, 2); }    \
+    else if (dim == 3 && pf == 2 && pc == 1) { MACRO(3, 3, 2); }    \
+    else if (dim == 3 && pf == 3 && pc == 2) { MACRO(3, 4, 3); }    \
+    else return cudaErrorInvalidValue;                              \
+  } while (0)
+
+template <typename R>
+cudaError_t launch_restrict(int dim, int pf, int pc, const TransferParams<R>& T, const R* rf, R* rc, cudaStream_t s) {
+  if (T.n_act_c == 0) return cudaSuccess;
+#define SBM_RESTRICT(D, NF, NC)                                                   \
+  {                                                                               \
+    const size_t n = (size_t)T.n_act_c * (D == 2 ? NC * NC : NC * NC * NC);       \
+    k_restrict<D, NF, NC, R><<<ceil_div(n, 256), 256, 0, s>>>(T, rf, rc);         \
+  }
+  SBM_DISPATCH_T(dim, pf, pc, SBM_RESTRICT);
+#undef SBM_RESTRICT
+  return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t launch_prolong(int dim, int pf, int pc, const TransferParams<R>& T, const R* ec, R* uf, cudaStream_t s) {
+  if (T.n_act_f == 0) return cudaSuccess;
+#define SBM_PROLONG(D, NF, NC)                                                    \
+  {                                                                               \
+    const size_t n = (size_t)T.n_act_f * (D == 2 ? NF * NF : NF * NF * NF);       \
+    k_prolong<D, NF, NC, R><<<ceil_div(n, 256), 256, 0, s>>>(T, ec, uf);          \
+  }
+  SBM_DISPATCH_T(dim, pf, pc, SBM_PROLONG);
+#undef SBM_PROLONG
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_coarse(const double* Ainv, int N, const T* r, T* e, cudaStream_t s) {
+  if (N == 0) return cudaSuccess;
+  k_coarse<T><<<ceil_div(N, 8), 256, 0, s>>>(Ainv, N, r, e);
+  return cudaGetLastError();
+}
+
+template cudaError_t launch_apply<double, double>(int, int, const LevelParams<double>&, const double*, const double*,
+                                                  double*, int, cudaStream_t);
+template cudaError_t launch_apply<float, float>(int, int, const LevelParams<float>&, const float*, const float*,
+                                                float*, int, cudaStream_t);
+template cudaError_t launch_apply<float, double>(int, int, const LevelParams<double>&, const float*, const double*,
+                                                 double*, int, cudaStream_t);
+template cudaError_t launch_smooth<double>(int, int, const LevelParams<double>&, int, const double*, double*,
+                                           cudaStream_t);
+template cudaError_t launch_smooth<float>(int, int, const LevelParams<float>&, int, const float*, float*,
+                                          cudaStream_t);
+template cudaError_t launch_restrict<double>(int, int, int, const TransferParams<double>&, const double*, double*,
+                                             cudaStream_t);
+template cudaError_t launch_restrict<float>(int, int, int, const TransferParams<float>&, const float*, float*,
+                                            cudaStream_t);
+template cudaError_t launch_prolong<double>(int, int, int, const TransferParams<double>&, const double*, double*,
+                                            cudaStream_t);
+template cudaError_t launch_prolong<float>(int, int, int, const TransferParams<float>&, const float*, float*,
+                                           cudaStream_t);
+template cudaError_t launch_coarse<double>(const double*, int, const double*, double*, cudaStream_t);
+template cudaError_t launch_coarse<float>(const double*, int, const float*, float*, cudaStream_t);
+
+}  // namespace sbm

@@ -1,0 +1,49 @@
+// Host-side launchers of the libsbm CUDA kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "sbm_internal.h"
+
+namespace sbm {
+
+// y = A x (mode 0) or y = f - A x (mode 1) on one level; TI is the input precision, R the
+// compute / output precision.
+template <typename TI, typename R>
+cudaError_t launch_apply(int dim, int p, const LevelParams<R>& P, const TI* x, const R* f, R* y, int mode,
+                         cudaStream_t s);
+
+// One coloured block Gauss-Seidel sweep (all colours, forward or reverse).
+template <typename R>
+cudaError_t launch_smooth(int dim, int p, const LevelParams<R>& P, int reverse, const R* f, R* u, cudaStream_t s);
+
+// rc = P^T rf (restriction) and uf += P ec (prolongation) between level l-1 and l.
+template <typename R>
+cudaError_t launch_restrict(int dim, int pf, int pc, const TransferParams<R>& T, const R* rf, R* rc, cudaStream_t s);
+template <typename R>
+cudaError_t launch_prolong(int dim, int pf, int pc, const TransferParams<R>& T, const R* ec, R* uf, cudaStream_t s);
+
+// e = Ainv r, dense FP64 matrix, N x N row-major.
+template <typename T>
+cudaError_t launch_coarse(const double* Ainv, int N, const T* r, T* e, cudaStream_t s);
+
+// ---------------------------------------------------------------- FGMRES building blocks (FP64)
+// Number of partial-sum blocks used for vectors of length N (fixed per N: deterministic sums).
+int dot_blocks(size_t N);
+// out[k] = sum_i V[k*ldv + i] w[i], k < nv (nv <= 32); partial holds dot_blocks(N)*32 doubles.
+cudaError_t launch_multi_dot(const double* V, size_t ldv, int nv, const double* w, size_t N, double* partial,
+                             double* out, int take_sqrt, cudaStream_t s);
+// w[i] += sign * sum_k coef[k] Z[k*ldz + i]
+template <typename TZ>
+cudaError_t launch_multi_axpy(const TZ* Z, size_t ldz, int nv, const double* coef, double sign, double* w,
+                              size_t N, cudaStream_t s);
+// v = w / (*s)
+cudaError_t launch_div_scalar(const double* w, const double* s, double* v, size_t N, cudaStream_t st);
+// y = (TO) x
+template <typename TI, typename TO>
+cudaError_t launch_cast(const TI* x, TO* y, size_t N, cudaStream_t s);
+// c = a + b (k <= 32 entries), c[k] = hn at index k
+cudaError_t launch_hess_column(const double* h1, const double* h2, const double* hn, int k, double* col,
+                               cudaStream_t s);
+
+}  // namespace sbm

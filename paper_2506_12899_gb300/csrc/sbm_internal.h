@@ -1,0 +1,115 @@
+// Internal data structures of libsbm: host-side level set-up and the device parameter blocks.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "sbm.h"
+
+namespace sbm {
+
+constexpr int kMaxN1 = 4;          // p + 1 <= 4
+constexpr int kMaxLevels = 16;
+
+// ---------------------------------------------------------------------------------------------
+// One-dimensional reference data of the nodal Gauss-Legendre Lagrange basis of degree p on [0,1].
+struct Basis1D {
+  int p = 1, n1 = 2;
+  double x[kMaxN1] = {}, w[kMaxN1] = {};          // nodes and weights
+  double Dm[kMaxN1 * kMaxN1] = {};                // Dm[i*n1+k] = l_k'(x_i)
+  double e0[kMaxN1] = {}, e1[kMaxN1] = {};        // l_k(0), l_k(1)
+  double d0[kMaxN1] = {}, d1[kMaxN1] = {};        // l_k'(0), l_k'(1)
+  double Khat[kMaxN1 * kMaxN1] = {};              // sum_q w_q l_i'(x_q) l_j'(x_q)
+};
+
+void gauss_legendre01(int n, double* x, double* w);
+void lagrange_eval(int n1, const double* nodes, double y, double* val, double* der);
+Basis1D make_basis(int p);
+
+// ---------------------------------------------------------------------------------------------
+// Host copy of everything one multigrid level needs.
+struct HostLevel {
+  int dim = 2, n = 0, p = 1, n1 = 2, np = 4, nq = 2, nslot = 4, ncol = 4;
+  double h = 0, lo[3] = {0, 0, 0};
+  double sigF_hat = 0, sigG_hat = 0, alpha = 1, omega = 1;
+  int extension = 0;
+  int n_act = 0, n_bnd = 0, n_sface = 0;
+  std::vector<int> cell;            // [n_act][3] background multi-index, compact order
+  std::vector<int> bg2act;          // [n^dim] compact index or -1
+  std::vector<int> nbr;             // [nslot][n_act] neighbour compact index or -1 (slot = 2*dir+side)
+  int colour_start[9] = {}, colour_nbnd[8] = {}, bstart[8] = {};
+  std::vector<double> dhat;         // [n_bnd][nslot][dim][nq]  d / h (zero on non-surrogate slots)
+  std::vector<double> binvT;        // [n_bnd][np][np]  (A_KK^{-1})^T: element (j, i) at j*np + i
+  std::vector<int> parent_code;     // [n_act] (parent compact index << 3) | child bits, or -1
+  std::vector<int> children;        // [2^dim][n_act] compact index of child in the next finer level
+  std::vector<int> sf_cell, sf_slot;
+  std::vector<double> sf_d;         // [n_sface][nq][3]
+  Basis1D B;
+  double L[4][kMaxN1 * kMaxN1] = {}; // self 1D matrices by neighbour mask (left active) + 2*(right active)
+  double Bmp[kMaxN1 * kMaxN1] = {};  // coupling to the right neighbour (this cell is K-)
+  double Bpm[kMaxN1 * kMaxN1] = {};  // coupling to the left neighbour (this cell is K+)
+  double S[kMaxN1 * kMaxN1] = {}, lam[kMaxN1] = {};   // W-orthonormal eigenvectors / values of L[3]
+  std::vector<double> coarse_inv;   // [N*N] on the coarsest level only
+  int n_dof() const { return n_act * np; }
+  bool is_boundary(int a, int* bidx) const;
+};
+
+struct SetupError {
+  int code;
+  std::string msg;
+};
+
+// Builds one level; throws SetupError.  (Geometry of Sec. 2.1 / Sec. 4.2, element data of Eq. 11.)
+HostLevel build_level(const sbm_setup_desc& d, int n, int p);
+// Links a coarse and the next finer level (parent / children tables for h-transfers).
+void link_levels(HostLevel& coarse, HostLevel& fine);
+// Dense coarse inverse (host LU with partial pivoting).
+void build_coarse_inverse(HostLevel& L0);
+// Finest-level right-hand side of Eq. 11 in compact layout.
+std::vector<double> build_rhs(const sbm_setup_desc& d, const HostLevel& L);
+// Host evaluation of y = A x on a whole level (set-up checks without a GPU).
+void host_apply_level(const HostLevel& L, const double* x, double* y);
+// Host evaluation of A_KK applied to one local vector (used for the dense cell blocks).
+void cell_self_apply(const HostLevel& L, int a, int bidx, const double* u, double* y);
+
+// ---------------------------------------------------------------------------------------------
+// Small 1D element matrices of one level (copied to shared memory by every kernel block).
+template <typename R>
+struct LevelConsts {
+  R L[4][kMaxN1 * kMaxN1];          // self matrices by neighbour mask
+  R Bmp[kMaxN1 * kMaxN1], Bpm[kMaxN1 * kMaxN1];
+  R Dm[kMaxN1 * kMaxN1];
+  R S[kMaxN1 * kMaxN1];             // fast-diagonalisation eigenvectors (columns)
+  R w[kMaxN1], e0[kMaxN1], e1[kMaxN1], d0[kMaxN1], d1[kMaxN1];
+  R x[kMaxN1], inv_denom[kMaxN1];   // nodes and 1 / prod_{j != k}(x_k - x_j)
+  R lam[kMaxN1];
+};
+
+// Device parameter block of one level for one precision (passed by value to the kernels).
+template <typename R>
+struct LevelParams {
+  int n_act;
+  int colour_start[9], colour_nbnd[8], bstart[8];
+  const int* nbr;
+  const R* dhat;
+  const R* binvT;
+  R hscale;                        // h^(dim-2)
+  R sigG, alpha, omega;
+  int extension;
+  LevelConsts<R> k;
+};
+
+// Transfer parameter block between level l-1 (coarse) and l (fine).
+template <typename R>
+struct TransferParams {
+  int n_act_f, n_act_c;
+  int hmode;                       // 1: h-transfer (both p = 1), 0: p-transfer on the same mesh
+  const int* parent_code;          // fine [n_act_f]
+  const int* children;             // coarse [2^d][n_act_c]
+  R Ph[2][kMaxN1 * kMaxN1];        // h: Ph[o][i*nc + j] = l^c_j((o + x^f_i)/2)
+  R Pp[kMaxN1 * kMaxN1];           // p: Pp[i*nc + j] = l^c_j(x^f_i)
+};
+
+}  // namespace sbm
