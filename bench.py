@@ -1,0 +1,362 @@
+#!/usr/bin/env python
+"""Benchmark of the DG-SBM hp-multigrid FGMRES solve on GB300.
+
+One step = one FGMRES(30) solve to 1e-8 relative FP64 residual from x = 0 (every row of the
+hot path: operator apply, coloured block smoother, transfers, coarse solve, Arnoldi with
+two-pass classical Gram-Schmidt) of the 2D p=2 star workload, 512^2 background cells, with the
+FP32 V-cycle under FP64 FGMRES.  The FP64-V-cycle solve of the same workload is timed beside
+it.  Prints one JSON line (rank 0).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun each rank solves its own seeded replica of the workload on its own GPU
+(replicas only: no data-path collective); the reported time is the max over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import workloads as W  # noqa: E402
+
+METRIC = "solve time to 1e-8 rel. residual (FP32/learned vs FP64 V-cycle); apply GB/s"
+WORKLOADS = {
+    "star2d_p2_n512": lambda seed: W.star2d_p2(512, seed),
+    "disk2d_p1_n32": lambda seed: W.disk2d_p1(32, seed),
+    "sphere3d_p1_n64": lambda seed: W.sphere3d(64, 1, seed),
+    "sphere3d_p2_n64": lambda seed: W.sphere3d(64, 2, seed),
+    "ellipsoid3d_p3_n96": lambda seed: W.ellipsoid3d_p3(96, seed),
+}
+DESCRIPTION = {
+    "star2d_p2_n512": "2D star r(theta)=0.7(1+0.1 sin(5 theta+phi)), 512^2 background cells, Q2 DG-SBM, "
+                      "u=exp(x)cos(2y), lambda=0.75, hp-multigrid p2->p1 then h to 8^2, FGMRES(30) tol 1e-8",
+}
+TOL, RESTART, MAX_IT = 1e-8, 30, 300
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+
+
+# ----------------------------------------------------------------------------- CPU oracle worker
+def cpu_worker(workload: str, seed: int, budget_s: float, full: bool) -> dict:
+    """Times the CPU FP64 oracle (set-up untimed) on the same workload: FGMRES iterations until
+    `budget_s` of solve time is spent; returns ms per Arnoldi step and, if `full`, the oracle's
+    own iteration count to 1e-8."""
+    from oracle import krylov as K
+    from oracle import multigrid as MG
+    prob = WORKLOADS[workload](seed)
+    t0 = time.perf_counter()
+    H = MG.Hierarchy(prob)
+    F = H.finest
+    b = F.disc.rhs()
+    setup_s = time.perf_counter() - t0
+    steps, spent = 0, 0.0
+    while spent < budget_s:
+        t0 = time.perf_counter()
+        K.fgmres(lambda v: F.A @ v, H.vcycle, b, tol=TOL, m=RESTART, max_it=2)
+        spent += time.perf_counter() - t0
+        steps += 2
+    out = dict(ms_per_iteration=1e3 * spent / steps, iterations_sampled=steps, setup_s=setup_s, n_dof=F.N)
+    if full:
+        t0 = time.perf_counter()
+        _x, info = K.fgmres(lambda v: F.A @ v, H.vcycle, b, tol=TOL, m=RESTART, max_it=MAX_IT)
+        out.update(full_iterations=info.iterations, full_solve_ms=1e3 * (time.perf_counter() - t0),
+                   converged=info.converged)
+    return out
+
+
+def start_cpu_worker(workload, seed, budget_s, full=False):
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
+               CUDA_VISIBLE_DEVICES="")
+    cmd = [sys.executable, os.path.abspath(__file__), "--cpu-worker", workload, str(seed), str(budget_s),
+           "1" if full else "0"]
+    return subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.PIPE, env=env, cwd=ROOT)
+
+
+def finish_cpu_worker(proc) -> dict | None:
+    out, err = proc.communicate()
+    if proc.returncode != 0:
+        sys.stderr.write(err.decode(errors="replace")[-2000:])
+        return None
+    return json.loads(out.decode().strip().splitlines()[-1])
+
+
+# ----------------------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.file = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.proc = None
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={gpu_index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=self.file, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        self.proc.wait()
+        self.file.seek(0)
+        rows = [r.split(",") for r in self.file.read().strip().splitlines() if r.strip()]
+        os.unlink(self.file.name)
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                smax = float(r[2])
+                for k, name in enumerate(names):
+                    if r[5 + k].strip().lower() == "active":
+                        reasons.add(name)
+            except (ValueError, IndexError):
+                continue
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------- helpers
+def peaks():
+    try:
+        with open(PEAKS_FILE) as fh:
+            d = json.load(fh)
+        return d.get("hbm_gbs"), "measured"
+    except (OSError, ValueError):
+        return 6800.0, "fallback"
+
+
+def event_time(torch, fn, reps, flush=None):
+    """Mean device time (ms) of fn() over reps launches on the current stream."""
+    s = torch.cuda.current_stream()
+    total = 0.0
+    for _ in range(reps):
+        if flush is not None:
+            flush()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(s)
+        fn()
+        e1.record(s)
+        e1.synchronize()
+        total += e0.elapsed_time(e1)
+    return total / reps
+
+
+def run_ours(args) -> dict | None:
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    cpu_proc = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu_proc = start_cpu_worker(args.workload, 0, args.cpu_budget)   # spawned before any CUDA call
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    import paper_2506_12899_gb300 as S
+
+    prob = WORKLOADS[args.workload](rank)
+    s32 = S.Solver(prob, "f32")
+    s64 = S.Solver(prob, "f64")
+    b = s32.rhs()
+    x = torch.zeros_like(b)
+    N = b.numel()
+    flush_buf = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")   # 256 MB > L2 (126 MB)
+
+    def flush():
+        flush_buf.fill_(1.0)
+
+    def solve_step(solver):
+        x.zero_()
+        flush()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        info = solver.solve(b, x, tol=TOL, restart=RESTART, max_it=MAX_IT)
+        e1.record()
+        e1.synchronize()
+        return e0.elapsed_time(e1), info
+
+    for _ in range(args.warmup):
+        solve_step(s32)
+        solve_step(s64)
+    # ---- timed region: K FP32-V-cycle solves
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    launches0 = S.kernel_launches()
+    times32, infos32 = [], []
+    for _ in range(args.steps):
+        ms, info = solve_step(s32)
+        times32.append(ms)
+        infos32.append(info)
+    launches = S.kernel_launches() - launches0
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    if world > 1:
+        dist.barrier()
+    total_ms = sum(times32)
+    if world > 1:
+        t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    # ---- FP64 V-cycle solves (the plain variant), same workload
+    times64, infos64 = [], []
+    for _ in range(args.steps):
+        ms, info = solve_step(s64)
+        times64.append(ms)
+        infos64.append(info)
+    # ---- end to end through the host-buffer C-ABI call (copies inside the timed region)
+    bh = torch.empty(N, dtype=torch.float64, pin_memory=True)
+    xh = torch.empty(N, dtype=torch.float64, pin_memory=True)
+    bh.copy_(b)
+    bnp, xnp = bh.numpy(), xh.numpy()
+    s32.solve_host(bnp, xnp, tol=TOL, restart=RESTART, max_it=MAX_IT)
+    e2e = []
+    for _ in range(args.steps):
+        flush()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        s32.solve_host(bnp, xnp, tol=TOL, restart=RESTART, max_it=MAX_IT)
+        e2e.append(1e3 * (time.perf_counter() - t0))
+    # ---- per-kernel rooflines (finest level, FP32 as in the V-cycle; FP64 operator as in FGMRES)
+    info = s32.info()
+    nb = (info["p"] + 1) ** prob.dim
+    r32 = torch.rand(N, device="cuda", dtype=torch.float32)
+    u32 = torch.rand_like(r32)
+    y32 = torch.empty_like(r32)
+    x64 = torch.rand(N, device="cuda", dtype=torch.float64)
+    y64 = torch.empty_like(x64)
+    geo_bytes = info["n_sface"] * (info["p"] + 1) ** (prob.dim - 1) * prob.dim
+    t_apply32 = event_time(torch, lambda: s32.apply(r32, y32), 20, flush)
+    t_apply64 = event_time(torch, lambda: s64.apply(x64, y64), 20, flush)
+    t_smooth = event_time(torch, lambda: s32.smooth(r32, u32), 20, flush) / 2 ** prob.dim
+    bytes_apply32 = 2 * 4 * N + 4 * geo_bytes
+    bytes_apply64 = 2 * 8 * N + 8 * geo_bytes
+    bytes_smooth = (3 * 4 * N + info["n_boundary"] * nb * nb * 4 + 4 * geo_bytes) / 2 ** prob.dim
+    hbm, src = peaks()
+    kernels = {
+        "k_smooth (FP32, finest level, one colour)": (bytes_smooth, t_smooth),
+        "k_apply (FP32, finest level)": (bytes_apply32, t_apply32),
+        "k_apply (FP64, finest level)": (bytes_apply64, t_apply64),
+    }
+    rooflines = {k: {"bound": "hbm", "achieved": round(b_ / t_ / 1e6, 1), "peak": hbm, "unit": "GB/s",
+                     "frac": round(b_ / t_ / 1e6 / hbm, 3), "bytes_per_launch": int(b_), "ms_per_launch": t_}
+                 for k, (b_, t_) in kernels.items()}
+    dominant = "k_smooth (FP32, finest level, one colour)"
+    roof = dict(rooflines[dominant])
+    roof.update(kernel=dominant, peak_source=src, traffic=None)
+    if rank != 0:
+        return None
+    cpu = finish_cpu_worker(cpu_proc) if cpu_proc is not None else None
+    ms32 = total_ms / args.steps
+    its32 = [i.iterations for i in infos32]
+    out = {
+        "metric": METRIC, "value": round(ms32, 4), "unit": "ms", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(ms32, 4), "higher_is_better": False, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+        "config": {"workload": args.workload, "description": DESCRIPTION.get(args.workload, args.workload),
+                   "n_dof": N, "levels": s32.num_levels, "variant": "FP32 V-cycle, FP64 FGMRES(30)",
+                   "l2": "flushed (256 MB write) before every step", "parallelism": f"replicas x{world}"},
+        "iterations": its32, "converged": all(i.converged for i in infos32),
+        "true_rel_residual": max(i.true_rel_residual for i in infos32),
+        "fp64_vcycle": {"ms": round(statistics.mean(times64), 4), "iterations": [i.iterations for i in infos64],
+                        "converged": all(i.converged for i in infos64)},
+        "speedup_fp32_over_fp64_vcycle": round(statistics.mean(times64) / ms32, 3),
+        "solves_per_s_total": round(world * args.steps / (total_ms / 1e3), 3),
+        "apply_gbs": {"fp32": rooflines["k_apply (FP32, finest level)"]["achieved"],
+                      "fp64": rooflines["k_apply (FP64, finest level)"]["achieved"]},
+        "clocks": clk,
+        "e2e": {"value": round(statistics.mean(e2e), 4), "unit": "ms", "h2d_bytes_per_step": 8 * N,
+                "d2h_bytes_per_step": 8 * N},
+        "gpu_launches": int(launches),
+        "roofline": roof,
+        "rooflines": rooflines,
+    }
+    if cpu is not None:
+        solve_ms = cpu["ms_per_iteration"] * statistics.mean(its32)
+        out["cpu_baseline"] = {"value": round(solve_ms, 1), "unit": "ms", "cores": 1, "kind": "oracle",
+                               "sample": f"{cpu['iterations_sampled']} FGMRES iterations of the FP64 oracle on the "
+                                         f"same workload ({cpu['ms_per_iteration']:.1f} ms each), scaled to the "
+                                         f"{statistics.mean(its32):.1f} iterations of the GPU solve; oracle set-up "
+                                         f"{cpu['setup_s']:.0f} s not timed"}
+    return out
+
+
+def run_reference(args) -> dict | None:
+    """The reference arm: the CPU FP64 oracle on the host cores (no GPU)."""
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return None
+    os.environ.setdefault("OMP_NUM_THREADS", "1")
+    from oracle import krylov as K
+    from oracle import multigrid as MG
+    prob = WORKLOADS[args.workload](0)
+    H = MG.Hierarchy(prob)
+    F = H.finest
+    b = F.disc.rhs()
+    # the oracle's own iteration count to 1e-8 is measured once (not timed), then each step times
+    # a bounded sample of two FGMRES iterations and scales it to that count
+    _x, info = K.fgmres(lambda v: F.A @ v, H.vcycle, b, tol=TOL, m=RESTART, max_it=MAX_IT)
+    its = info.iterations
+    per_it = []
+    for k in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        K.fgmres(lambda v: F.A @ v, H.vcycle, b, tol=TOL, m=RESTART, max_it=2)
+        if k >= args.warmup:
+            per_it.append((time.perf_counter() - t0) / 2)
+    ms = 1e3 * statistics.mean(per_it) * its
+    return {"impl": "reference", "metric": METRIC, "value": round(ms, 1), "unit": "ms", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 1), "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": args.workload, "description": DESCRIPTION.get(args.workload, args.workload),
+                       "n_dof": F.N, "variant": "CPU FP64 oracle: assembled CSR, coloured block GS V-cycle, "
+                                                "FGMRES(30)"},
+            "iterations": its, "converged": info.converged,
+            "cpu_baseline": {"value": round(ms, 1), "unit": "ms", "cores": 1, "kind": "oracle",
+                             "sample": f"each step: 2 FGMRES iterations of the oracle scaled to its {its} "
+                                       f"iterations to 1e-8"},
+            "e2e": {"value": round(ms, 1), "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    if len(sys.argv) > 1 and sys.argv[1] == "--cpu-worker":
+        workload, seed, budget, full = sys.argv[2], int(sys.argv[3]), float(sys.argv[4]), sys.argv[5] == "1"
+        print(json.dumps(cpu_worker(workload, seed, budget, full)))
+        return
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="star2d_p2_n512", choices=sorted(WORKLOADS))
+    ap.add_argument("--cpu-budget", type=float, default=15.0, help="seconds of oracle solve time to sample")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    out = run_reference(args) if args.impl == "reference" else run_ours(args)
+    if out is not None:
+        print(json.dumps(out))
+    if int(os.environ.get("WORLD_SIZE", "1")) > 1 and args.impl == "ours":
+        import torch.distributed as dist
+        if dist.is_initialized():
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

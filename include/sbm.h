@@ -133,6 +133,10 @@ void sbm_destroy(void* ctx);
 /* Message of the last failing call on this thread (static storage, never NULL). */
 const char* sbm_last_error(void);
 
+/* Total number of CUDA kernel launches issued by this library since it was loaded (all
+ * contexts; memsets and copies are not counted). */
+long long sbm_kernel_launches(void);
+
 /* Number of multigrid levels L+1. */
 int sbm_num_levels(const void* ctx, int* out);
 

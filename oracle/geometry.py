@@ -12,8 +12,10 @@ Readings where the paper leaves a choice:
   * The level set is the analytic phi on every level (the paper interpolates phi by
     finite elements; geometry is set-up, not the solver path).
   * The closest point is the global one for the disk/sphere and box (closed form); for the
-    other shapes Newton on Eqs. 21-22 starts from three steps of the projection
-    x <- x - phi grad(phi) / |grad(phi)|^2 and uses backtracking on |F|.
+    other shapes Newton on Eqs. 21-22 (backtracking on |F|) starts from the nearest point of a
+    fixed sampling of the boundary, so that it converges to the global minimum also where the
+    surrogate point lies beyond a centre of curvature (coarse levels), where a projection
+    start lands on a local maximum of the distance.
 """
 from __future__ import annotations
 
@@ -106,18 +108,53 @@ class NewtonFailure(RuntimeError):
     pass
 
 
+def boundary_samples(shape: W.Shape, dim: int) -> np.ndarray:
+    """A fixed sampling of the true boundary, used only to start Newton near the global minimum:
+    star and the Sec. 5.4 domain: 1024 rays theta_k = 2 pi k / 1024; ellipsoid: 64 x 128
+    (u_i = pi (i + 1/2) / 64, v_j = 2 pi j / 128) points of c + R diag(semi) (sin u cos v,
+    sin u sin v, cos u)."""
+    c = np.array(shape.center[:dim])
+    if shape.kind == W.SHAPE_STAR:
+        th = 2 * np.pi * np.arange(1024) / 1024
+        r = shape.radius * (1.0 + shape.amp * np.sin(shape.freq * th + shape.phase))
+        return c + np.stack([r * np.cos(th), r * np.sin(th)], axis=1)
+    if shape.kind == W.SHAPE_COMPLEX2D:
+        th = 2 * np.pi * np.arange(1024) / 1024
+        lo, hi = np.zeros(1024), np.full(1024, 2.0)        # phi(0) < 0 < phi(2 e_theta): bisection
+        for _ in range(64):
+            mid = 0.5 * (lo + hi)
+            inside = phi(shape, np.stack([mid * np.cos(th), mid * np.sin(th)], axis=1)) < 0
+            lo, hi = np.where(inside, mid, lo), np.where(inside, hi, mid)
+        r = 0.5 * (lo + hi)
+        return np.stack([r * np.cos(th), r * np.sin(th)], axis=1)
+    if shape.kind == W.SHAPE_ELLIPSOID:
+        u = np.pi * (np.arange(64) + 0.5) / 64
+        v = 2 * np.pi * np.arange(128) / 128
+        U, V = np.meshgrid(u, v, indexing="ij")
+        loc = np.stack([np.sin(U) * np.cos(V), np.sin(U) * np.sin(V), np.cos(U)], axis=-1).reshape(-1, 3)
+        return c + (loc * np.array(shape.semi)) @ _rot(shape).T
+    raise ValueError(f"no boundary sampling for shape kind {shape.kind}")
+
+
+_SAMPLES = {}
+
+
 def closest_point_newton(shape: W.Shape, xt: np.ndarray, maxit: int = 50) -> np.ndarray:
     """Closest point on {phi = 0} to xt: Newton on the stationarity system of the
     Lagrangian L(x, mu) = |x - xt|^2 + mu phi(x) (Eqs. 20-22):
         F(x, mu) = [2 (x - xt) + mu grad phi(x) ; phi(x)] = 0,
-        J = [[2 I + mu Hess phi, grad phi], [grad phi^T, 0]].
+        J = [[2 I + mu Hess phi, grad phi], [grad phi^T, 0]],
+    started from the nearest point of `boundary_samples` (first one on ties) with
+    mu = 2 (xt - x).grad phi / |grad phi|^2, with backtracking on |F|.
     """
     xt = np.asarray(xt, dtype=np.float64)
     dim = len(xt)
-    x = xt.copy()
-    for _ in range(3):
-        g, _H = grad_hess(shape, x)
-        x = x - phi(shape, x) * g / (g @ g)
+    key = (shape.kind, tuple(shape.center), shape.radius, shape.amp, shape.freq, shape.phase,
+           tuple(shape.semi), tuple(shape.rot), dim)
+    if key not in _SAMPLES:
+        _SAMPLES[key] = boundary_samples(shape, dim)
+    samp = _SAMPLES[key]
+    x = samp[int(np.argmin(np.sum((samp - xt) ** 2, axis=1)))].copy()
     g, _H = grad_hess(shape, x)
     mu = 2.0 * ((xt - x) @ g) / (g @ g)
 

@@ -26,7 +26,7 @@ ERRORS = {-1: "SBM_ERR_ARG", -2: "SBM_ERR_CUDA", -3: "SBM_ERR_SINGULAR_BLOCK", -
           -5: "SBM_ERR_NAN", -6: "SBM_ERR_GEOMETRY", -7: "SBM_ERR_ALLOC"}
 
 # exported C symbols (checked by the tests against include/sbm.h)
-SYMBOLS = ("sbm_setup", "sbm_setup_host", "sbm_host_apply", "sbm_host_rhs", "sbm_destroy", "sbm_last_error", "sbm_num_levels", "sbm_info", "sbm_layout",
+SYMBOLS = ("sbm_setup", "sbm_setup_host", "sbm_host_apply", "sbm_host_rhs", "sbm_destroy", "sbm_last_error", "sbm_kernel_launches", "sbm_num_levels", "sbm_info", "sbm_layout",
            "sbm_export_geometry", "sbm_rhs", "sbm_apply", "sbm_residual", "sbm_smooth", "sbm_restrict",
            "sbm_prolong_add", "sbm_coarse_solve", "sbm_vcycle", "sbm_solve", "sbm_solve_host")
 
@@ -97,6 +97,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.sbm_destroy.argtypes = [vp]
     lib.sbm_destroy.restype = None
     lib.sbm_last_error.restype = ctypes.c_char_p
+    lib.sbm_kernel_launches.restype = ctypes.c_longlong
     lib.sbm_num_levels.argtypes = [vp, ctypes.POINTER(ctypes.c_int)]
     lib.sbm_info.argtypes = [vp, ip, ctypes.POINTER(_LevelInfo)]
     lib.sbm_layout.argtypes = [vp, ip, vp]
@@ -112,10 +113,15 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.sbm_solve.argtypes = [vp, vp, vp, dp, ip, ip, ctypes.POINTER(_SolveInfo)]
     lib.sbm_solve_host.argtypes = [vp, vp, vp, dp, ip, ip, ctypes.POINTER(_SolveInfo)]
     for name in SYMBOLS:
-        if name not in ("sbm_destroy", "sbm_last_error"):
+        if name not in ("sbm_destroy", "sbm_last_error", "sbm_kernel_launches"):
             getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
+
+
+def kernel_launches() -> int:
+    """Kernel launches issued by libsbm since it was loaded."""
+    return int(load_library().sbm_kernel_launches())
 
 
 def _check(code: int):

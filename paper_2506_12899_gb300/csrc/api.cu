@@ -509,6 +509,8 @@ void sbm_destroy(void* ctx) { delete ctx_of(ctx); }
 
 const char* sbm_last_error(void) { return g_last_error.c_str(); }
 
+long long sbm_kernel_launches(void) { return g_kernel_launches.load(); }
+
 int sbm_num_levels(const void* ctx, int* out) {
   if (!ctx || !out) return set_error(SBM_ERR_ARG, "null argument");
   *out = (int)static_cast<const Context*>(ctx)->lv.size();

@@ -100,6 +100,8 @@ unsigned grid_for(size_t N) {
 
 }  // namespace
 
+std::atomic<long long> g_kernel_launches{0};
+
 int dot_blocks(size_t N) {
   size_t g = (N + kDotThreads * 4 - 1) / (kDotThreads * 4);
   if (g < 1) g = 1;
@@ -113,6 +115,7 @@ cudaError_t launch_multi_dot(const double* V, size_t ldv, int nv, const double* 
   const int nblk = dot_blocks(N);
   k_multi_dot<<<nblk, kDotThreads, 0, s>>>(V, ldv, nv, w, N, partial);
   k_reduce_partials<<<1, kMaxVec, 0, s>>>(partial, nblk, nv, out, take_sqrt);
+  count_launches(2);
   return cudaGetLastError();
 }
 
@@ -121,23 +124,27 @@ cudaError_t launch_multi_axpy(const TZ* Z, size_t ldz, int nv, const double* coe
                               size_t N, cudaStream_t s) {
   if (nv < 1 || nv > kMaxVec) return cudaErrorInvalidValue;
   k_multi_axpy<TZ><<<grid_for(N), 256, 0, s>>>(Z, ldz, nv, coef, sign, w, N);
+  count_launches();
   return cudaGetLastError();
 }
 
 cudaError_t launch_div_scalar(const double* w, const double* sc, double* v, size_t N, cudaStream_t s) {
   k_div_scalar<<<grid_for(N), 256, 0, s>>>(w, sc, v, N);
+  count_launches();
   return cudaGetLastError();
 }
 
 template <typename TI, typename TO>
 cudaError_t launch_cast(const TI* x, TO* y, size_t N, cudaStream_t s) {
   k_cast<TI, TO><<<grid_for(N), 256, 0, s>>>(x, y, N);
+  count_launches();
   return cudaGetLastError();
 }
 
 cudaError_t launch_hess_column(const double* h1, const double* h2, const double* hn, int k, double* col,
                                cudaStream_t s) {
   k_hess_column<<<1, 64, 0, s>>>(h1, h2, hn, k, col);
+  count_launches();
   return cudaGetLastError();
 }
 

@@ -459,6 +459,7 @@ cudaError_t launch_apply(int dim, int p, const LevelParams<R>& P, const TI* x, c
     const unsigned grid = ceil_div(P.n_act, Dm::CPB);                                    \
     if (mode == 0) k_apply<D, N1, TI, R, 0><<<grid, Dm::NT, 0, s>>>(P, x, f, y);         \
     else k_apply<D, N1, TI, R, 1><<<grid, Dm::NT, 0, s>>>(P, x, f, y);                   \
+    count_launches();                                                                    \
   }
   SBM_DISPATCH_DP(dim, p, SBM_APPLY);
 #undef SBM_APPLY
@@ -476,8 +477,10 @@ cudaError_t launch_smooth(int dim, int p, const LevelParams<R>& P, int reverse, 
     using Dm = Dims<D, N1>;                                                                        \
     const int nblk_b = (int)ceil_div(nbnd, Dm::CPB);                                               \
     const int nblk_i = (int)ceil_div(ce - cs - nbnd, Dm::CPB);                                     \
-    if (nblk_b + nblk_i > 0)                                                                       \
+    if (nblk_b + nblk_i > 0) {                                                                     \
       k_smooth<D, N1, R><<<nblk_b + nblk_i, Dm::NT, 0, s>>>(P, cs, nbnd, ce, nblk_b, P.bstart[col], f, u); \
+      count_launches();                                                                            \
+    }                                                                                              \
   }
     SBM_DISPATCH_DP(dim, p, SBM_SMOOTH);
 #undef SBM_SMOOTH
@@ -503,6 +506,7 @@ cudaError_t launch_restrict(int dim, int pf, int pc, const TransferParams<R>& T,
   {                                                                               \
     const size_t n = (size_t)T.n_act_c * (D == 2 ? NC * NC : NC * NC * NC);       \
     k_restrict<D, NF, NC, R><<<ceil_div(n, 256), 256, 0, s>>>(T, rf, rc);         \
+    count_launches();                                                             \
   }
   SBM_DISPATCH_T(dim, pf, pc, SBM_RESTRICT);
 #undef SBM_RESTRICT
@@ -516,6 +520,7 @@ cudaError_t launch_prolong(int dim, int pf, int pc, const TransferParams<R>& T, 
   {                                                                               \
     const size_t n = (size_t)T.n_act_f * (D == 2 ? NF * NF : NF * NF * NF);       \
     k_prolong<D, NF, NC, R><<<ceil_div(n, 256), 256, 0, s>>>(T, ec, uf);          \
+    count_launches();                                                             \
   }
   SBM_DISPATCH_T(dim, pf, pc, SBM_PROLONG);
 #undef SBM_PROLONG
@@ -526,6 +531,7 @@ template <typename T>
 cudaError_t launch_coarse(const double* Ainv, int N, const T* r, T* e, cudaStream_t s) {
   if (N == 0) return cudaSuccess;
   k_coarse<T><<<ceil_div(N, 8), 256, 0, s>>>(Ainv, N, r, e);
+  count_launches();
   return cudaGetLastError();
 }
 

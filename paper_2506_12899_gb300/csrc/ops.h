@@ -5,7 +5,13 @@
 
 #include "sbm_internal.h"
 
+#include <atomic>
+
 namespace sbm {
+
+// Number of kernel launches issued by the library since it was loaded.
+extern std::atomic<long long> g_kernel_launches;
+inline void count_launches(long long n = 1) { g_kernel_launches.fetch_add(n, std::memory_order_relaxed); }
 
 // y = A x (mode 0) or y = f - A x (mode 1) on one level; TI is the input precision, R the
 // compute / output precision.

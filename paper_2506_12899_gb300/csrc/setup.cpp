@@ -186,10 +186,50 @@ bool small_solve(int n, const double* A_in, const double* b_in, double* x) {
   return true;
 }
 
+// Fixed sampling of the true boundary (start points for the closest-point Newton solve):
+// star / deformed 2D domain: 1024 rays theta_k = 2 pi k / 1024 (the deformed domain's radius by
+// 64 bisection steps on [0, 2]); ellipsoid: 64 x 128 points u_i = pi (i + 1/2) / 64,
+// v_j = 2 pi j / 128 of c + R diag(semi) (sin u cos v, sin u sin v, cos u).  Row-major [k][dim].
+std::vector<double> boundary_samples(const Shape& sh) {
+  std::vector<double> out;
+  const double* c = sh.s.center;
+  if (sh.s.kind == SBM_SHAPE_STAR || sh.s.kind == SBM_SHAPE_COMPLEX2D) {
+    for (int k = 0; k < 1024; ++k) {
+      const double th = 2.0 * kPi * k / 1024.0;
+      double r;
+      if (sh.s.kind == SBM_SHAPE_STAR) {
+        r = sh.s.radius * (1.0 + sh.s.amp * std::sin(sh.s.freq * th + sh.s.phase));
+      } else {
+        double lo = 0.0, hi = 2.0;
+        for (int it = 0; it < 64; ++it) {
+          const double mid = 0.5 * (lo + hi);
+          const double X[2] = {mid * std::cos(th), mid * std::sin(th)};
+          if (sh.phi(X) < 0.0) lo = mid; else hi = mid;
+        }
+        r = 0.5 * (lo + hi);
+      }
+      const double ox = sh.s.kind == SBM_SHAPE_STAR ? c[0] : 0.0, oy = sh.s.kind == SBM_SHAPE_STAR ? c[1] : 0.0;
+      out.push_back(ox + r * std::cos(th));
+      out.push_back(oy + r * std::sin(th));
+    }
+  } else if (sh.s.kind == SBM_SHAPE_ELLIPSOID) {
+    for (int i = 0; i < 64; ++i)
+      for (int j = 0; j < 128; ++j) {
+        const double u = kPi * (i + 0.5) / 64.0, v = 2.0 * kPi * j / 128.0;
+        const double l[3] = {sh.s.semi[0] * std::sin(u) * std::cos(v), sh.s.semi[1] * std::sin(u) * std::sin(v),
+                             sh.s.semi[2] * std::cos(u)};
+        for (int r = 0; r < 3; ++r)
+          out.push_back(c[r] + sh.s.rot[r * 3 + 0] * l[0] + sh.s.rot[r * 3 + 1] * l[1] + sh.s.rot[r * 3 + 2] * l[2]);
+      }
+  }
+  return out;
+}
+
 // Closest point on {phi = 0} (Sec. 4.2).  Disk/sphere and box: closed form.  Other shapes:
-// three projection steps x <- x - phi g/|g|^2, then Newton on F = [2(x - xt) + mu g; phi]
-// (Eqs. 21-22) with Jacobian [[2I + mu H, g], [g^T, 0]] and backtracking on |F|.
-bool closest_point(const Shape& sh, const double* xt, double* out) {
+// Newton on F = [2(x - xt) + mu g; phi] (Eqs. 21-22) with Jacobian [[2I + mu H, g], [g^T, 0]]
+// and backtracking on |F|, started from the nearest boundary sample (first on ties) with
+// mu = 2 (xt - x).g / |g|^2.
+bool closest_point(const Shape& sh, const std::vector<double>& samples, const double* xt, double* out) {
   const int dim = sh.dim;
   const double* c = sh.s.center;
   if (sh.s.kind == SBM_SHAPE_DISK) {
@@ -217,15 +257,22 @@ bool closest_point(const Shape& sh, const double* xt, double* out) {
     }
     return true;
   }
-  double x[3], g[3], H[9];
-  for (int k = 0; k < dim; ++k) x[k] = xt[k];
-  for (int it = 0; it < 3; ++it) {
-    sh.grad_hess(x, g, H);
-    double gg = 0;
-    for (int k = 0; k < dim; ++k) gg += g[k] * g[k];
-    double f = sh.phi(x);
-    for (int k = 0; k < dim; ++k) x[k] -= f * g[k] / gg;
+  const size_t ns = samples.size() / dim;
+  size_t best = 0;
+  double bd = 1e300;
+  for (size_t k = 0; k < ns; ++k) {
+    double d2 = 0;
+    for (int m = 0; m < dim; ++m) {
+      const double t = samples[k * dim + m] - xt[m];
+      d2 += t * t;
+    }
+    if (d2 < bd) {
+      bd = d2;
+      best = k;
+    }
   }
+  double x[3], g[3], H[9];
+  for (int k = 0; k < dim; ++k) x[k] = samples[best * dim + k];
   sh.grad_hess(x, g, H);
   double gg = 0, mu = 0;
   for (int k = 0; k < dim; ++k) {
@@ -753,6 +800,7 @@ HostLevel build_level(const sbm_setup_desc& d, int n, int p) {
     if (L.is_boundary(a, &bidx)) bcell[bidx] = a;
   }
   std::vector<int> newton_fail(L.n_bnd, 0);
+  const std::vector<double> samples = boundary_samples(sh);
   parallel_for(L.n_bnd, [&](int b0, int b1) {
     for (int b = b0; b < b1; ++b) {
       int a = bcell[b];
@@ -772,7 +820,7 @@ HostLevel build_level(const sbm_setup_desc& d, int n, int p) {
             }
             X[k] = d.lo[k] + L.h * (L.cell[3 * a + k] + xi);
           }
-          if (!closest_point(sh, X, C)) newton_fail[b] = 1;
+          if (!closest_point(sh, samples, X, C)) newton_fail[b] = 1;
           for (int k = 0; k < dim; ++k)
             L.dhat[(((size_t)b * L.nslot + slot) * dim + k) * nq + t] = (C[k] - X[k]) / L.h;
         }

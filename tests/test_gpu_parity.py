@@ -2,8 +2,9 @@
 
 Every comparison maps the library's compact, colour-major layout onto the oracle's natural
 ordering with the layout the library reports, then compares element by element.  FP64
-tolerances: 1e-12 relative for the operator, smoother, transfers and V-cycle; 1e-10 relative
-L2 for FGMRES solutions with equal iteration counts.  FP32 tolerances are derived from the
+tolerances: 1e-12 relative for the operator and the transfers; for operations that apply
+cell-block inverses (smoother, V-cycle) max(1e-12, n_p eps cond(A_KK)) (see `block_tol`);
+1e-10 relative L2 for FGMRES solutions with equal iteration counts.  FP32 tolerances are derived from the
 FP32 unit roundoff (6e-8) times the operation's amplification (stated per test).
 """
 import numpy as np
@@ -74,6 +75,14 @@ def rel_max(a, b):
     return np.abs(a - b).max() / max(np.abs(b).max(), 1e-300)
 
 
+def block_tol(levels):
+    """FP64 tolerance for operations that apply cell-block inverses: the rounding error of a
+    block solve grows like n_p * eps * cond(A_KK); floor 1e-12."""
+    kap = max(np.linalg.cond(lev.disc.diag).max() for lev in levels)
+    nb = max(lev.nb for lev in levels)
+    return max(1e-12, nb * 2.2e-16 * kap)
+
+
 @pytest.mark.parametrize("name", list(CASES))
 def test_apply_matches_assembled_matrix(name):
     """a1: y = A_l x on every level equals the oracle's assembled CSR product (Eq. 11)."""
@@ -123,7 +132,8 @@ def test_coloured_smoother_sweep(name):
         for reverse in (False, True):
             uo = lev.coloured_sweep(u0.copy(), f, reverse=reverse)
             ug = P.gpu.smooth(P.to_gpu(f, l), P.to_gpu(u0, l), level=l, reverse=reverse)
-            assert rel_max(P.to_oracle(ug, l), uo) <= 1e-12, (l, reverse, rel_max(P.to_oracle(ug, l), uo))
+            tol = block_tol([lev])
+            assert rel_max(P.to_oracle(ug, l), uo) <= tol, (l, reverse, rel_max(P.to_oracle(ug, l), uo), tol)
             ug32 = P.gpu.smooth(P.to_gpu(f, l, torch.float32), P.to_gpu(u0, l, torch.float32), level=l,
                                 reverse=reverse)
             # FP32: rounded inputs and block inverses amplified by cond(A_KK) (<= ~1e3 here)
@@ -163,7 +173,8 @@ def test_vcycle(name):
     r = W.random_vector(P.H.finest.N, 21)
     zo = P.H.vcycle(r)
     z = P.to_oracle(P.gpu.vcycle(P.to_gpu(r, L)), L)
-    assert np.linalg.norm(z - zo) <= 1e-12 * np.linalg.norm(zo), np.linalg.norm(z - zo) / np.linalg.norm(zo)
+    tol = block_tol(P.H.levels[1:] or P.H.levels)
+    assert np.linalg.norm(z - zo) <= tol * np.linalg.norm(zo), (np.linalg.norm(z - zo) / np.linalg.norm(zo), tol)
     z32 = P.to_oracle(P.gpu.vcycle(P.to_gpu(r, L, torch.float32)), L)
     assert np.linalg.norm(z32 - zo) <= 1e-4 * np.linalg.norm(zo), np.linalg.norm(z32 - zo) / np.linalg.norm(zo)
 
@@ -262,13 +273,13 @@ def test_single_level_and_tiny_mesh():
     z = g.vcycle(torch.tensor(r[m], device="cuda")).cpu().numpy()
     zo = np.linalg.solve(H.finest.A.toarray(), r)[m]
     assert np.abs(z - zo).max() <= 1e-11 * np.abs(zo).max()
-    prob = W.Problem(dim=2, n=2, p=2, shape=W.disk(2, 0, radius=0.95), coarsest_n=2)
+    prob = W.Problem(dim=2, n=2, p=1, shape=W.disk(2, 0, radius=0.95), coarsest_n=2)
     g = S.Solver(prob)
-    assert g.info()["n_active"] == 4
+    assert g.info()["n_active"] == 4 and g.num_levels == 1
     b = g.rhs()
     x = torch.zeros_like(b)
     info = g.solve(b, x, tol=1e-12)
-    assert info.converged and info.iterations <= 2
+    assert info.converged and info.iterations == 1        # the preconditioner is the exact inverse
 
 
 def test_full_size_star512_p2_sampled():

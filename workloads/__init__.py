@@ -139,22 +139,29 @@ def disk2d_p1(n: int = 32, seed: int = 0) -> Problem:
                    exact=EXACT_SINPROD, coarsest_n=4)
 
 
+# The p >= 2 and 3D workloads use lambda = 0.75 (kappa >= 0.75), a minimal interior penalty
+# sigma_F = (p+1)^2 / h and the boundary penalty sigma_Gamma = 10 (p+1)^2 / h.  With the 2D
+# workload's lambda = 0.5 and sigma_F = 10 (p+1)^2 / h, about 40% of the boundary-cell blocks
+# are indefinite at p = 2 and the cell-wise smoother diverges.
+HIGH_ORDER = dict(lam=0.75, sigma_face_c=1.0, sigma_bnd_c=10.0)
+
+
 def star2d_p2(n: int = 512, seed: int = 0) -> Problem:
     """2D p=2 workload: 512^2 cells, star r(theta)=0.7(1+0.1 sin(5 theta+phi)), phi seeded."""
     return Problem(name=f"star2d_p2_n{n}", dim=2, n=n, p=2, shape=star(seed),
-                   exact=EXACT_EXPCOS, coarsest_n=8 if n >= 64 else 4)
+                   exact=EXACT_EXPCOS, coarsest_n=8 if n >= 64 else 4, **HIGH_ORDER)
 
 
 def sphere3d(n: int = 64, p: int = 1, seed: int = 0) -> Problem:
     """3D p=1 / p=2 workload: 64^3 cells, sphere r=0.7 with seeded centre offset."""
     return Problem(name=f"sphere3d_p{p}_n{n}", dim=3, n=n, p=p, shape=disk(3, seed),
-                   exact=EXACT_SINPROD, coarsest_n=4)
+                   exact=EXACT_SINPROD, coarsest_n=4, **HIGH_ORDER)
 
 
 def ellipsoid3d_p3(n: int = 96, seed: int = 0) -> Problem:
     """3D p=3 workload: 96^3 cells, ellipsoid (0.75,0.6,0.5) rotated by seeded angles."""
     return Problem(name=f"ellipsoid3d_p3_n{n}", dim=3, n=n, p=3, shape=ellipsoid(seed),
-                   exact=EXACT_SINPROD, coarsest_n=6 if n % 6 == 0 else 4)
+                   exact=EXACT_SINPROD, coarsest_n=6 if n % 6 == 0 else 4, **HIGH_ORDER)
 
 
 def paper_disk(level: int, p: int, lam: float, dim: int = 2) -> Problem:
