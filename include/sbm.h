@@ -184,6 +184,14 @@ int sbm_coarse_solve(void* ctx, int dtype, const void* r_dev, void* e_dev);
  * operation in FP32 except the FP64 coarse solve). */
 int sbm_vcycle(void* ctx, int dtype, const void* r_dev, void* z_dev);
 
+/* Gram-Schmidt projections of the FGMRES Arnoldi step (Sec. 3): out[k] = sum_i V[k*ldv + i] w[i]
+ * for k < nv (1 <= nv <= 32), FP64, with the deterministic two-stage reduction used inside
+ * sbm_solve (warp shuffles, per-block partial sums in a context-owned buffer allocated on first
+ * use, then a fixed-order sum).  V holds nv vectors of length n with leading dimension ldv >= n;
+ * out_dev holds nv doubles. */
+int sbm_dots(void* ctx, const double* V_dev, long long ldv, int nv, const double* w_dev, long long n,
+             double* out_dev);
+
 /* Solve A x = b by FGMRES(restart), right-preconditioned by one V-cycle in the precision of
  * sbm_setup_desc.precision; Arnoldi, Gram-Schmidt (two classical passes), the update of x and
  * the true residual are FP64.  x_dev holds the initial guess on entry.  Stops when the

@@ -28,7 +28,7 @@ ERRORS = {-1: "SBM_ERR_ARG", -2: "SBM_ERR_CUDA", -3: "SBM_ERR_SINGULAR_BLOCK", -
 # exported C symbols (checked by the tests against include/sbm.h)
 SYMBOLS = ("sbm_setup", "sbm_setup_host", "sbm_host_apply", "sbm_host_rhs", "sbm_destroy", "sbm_last_error", "sbm_kernel_launches", "sbm_num_levels", "sbm_info", "sbm_layout",
            "sbm_export_geometry", "sbm_rhs", "sbm_apply", "sbm_residual", "sbm_smooth", "sbm_restrict",
-           "sbm_prolong_add", "sbm_coarse_solve", "sbm_vcycle", "sbm_solve", "sbm_solve_host")
+           "sbm_prolong_add", "sbm_coarse_solve", "sbm_vcycle", "sbm_dots", "sbm_solve", "sbm_solve_host")
 
 
 class SbmError(RuntimeError):
@@ -110,6 +110,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.sbm_prolong_add.argtypes = [vp, ip, ip, vp, vp]
     lib.sbm_coarse_solve.argtypes = [vp, ip, vp, vp]
     lib.sbm_vcycle.argtypes = [vp, ip, vp, vp]
+    lib.sbm_dots.argtypes = [vp, vp, ctypes.c_longlong, ip, vp, ctypes.c_longlong, vp]
     lib.sbm_solve.argtypes = [vp, vp, vp, dp, ip, ip, ctypes.POINTER(_SolveInfo)]
     lib.sbm_solve_host.argtypes = [vp, vp, vp, dp, ip, ip, ctypes.POINTER(_SolveInfo)]
     for name in SYMBOLS:
@@ -260,6 +261,16 @@ class Solver:
         z = self._torch.empty_like(r) if z is None else z
         _check(self.lib.sbm_vcycle(self.ctx, self._dt(r), self._vec(r), self._vec(z, r.dtype)))
         return z
+
+    def dots(self, V, w, out=None):
+        """out[k] = V[k] . w (FP64), V: (nv, n) contiguous CUDA tensor, w: (n,)."""
+        torch = self._torch
+        if V.dim() != 2 or V.dtype != torch.float64 or not V.is_contiguous() or not V.is_cuda:
+            raise ValueError("V must be a contiguous (nv, n) float64 CUDA tensor")
+        out = torch.empty(V.shape[0], dtype=torch.float64, device="cuda") if out is None else out
+        _check(self.lib.sbm_dots(self.ctx, self._vec(V), V.shape[1], V.shape[0], self._vec(w, torch.float64),
+                                 w.numel(), self._vec(out, torch.float64)))
+        return out
 
     def solve(self, b, x, tol: float = 1e-8, restart: int = 30, max_it: int = 300, check: bool = True) -> SolveInfo:
         inf = _SolveInfo()

@@ -71,8 +71,30 @@ struct Context {
   double* host_pinned = nullptr;   // 64 doubles
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   bool host_only = false;
+  double* dots_scratch = nullptr;  // partial sums of sbm_dots
+  size_t dots_scratch_len = 0;
+  // FGMRES runs on an internal non-blocking stream (the legacy default stream cannot be captured
+  // into a graph), joined to the caller's stream with events.  Each Arnoldi step j of each
+  // V-cycle precision is captured once into a CUDA graph and replayed.
+  cudaStream_t ws = nullptr;
+  cudaEvent_t join_in = nullptr, join_out = nullptr;
+  cudaGraphExec_t arnoldi[2][32] = {};
+  long long arnoldi_kernels[2][32] = {};
+
+  void drop_graphs() {
+    for (auto& row : arnoldi)
+      for (auto& g : row)
+        if (g) {
+          cudaGraphExecDestroy(g);
+          g = nullptr;
+        }
+  }
 
   ~Context() {
+    drop_graphs();
+    if (ws) cudaStreamDestroy(ws);
+    if (join_in) cudaEventDestroy(join_in);
+    if (join_out) cudaEventDestroy(join_out);
     for (void* p : allocs) cudaFree(p);
     if (host_pinned) cudaFreeHost(host_pinned);
     if (ev0) cudaEventDestroy(ev0);
@@ -246,6 +268,9 @@ Context* build_context(const sbm_setup_desc& d, bool device) {
   CUDA_TRY(cudaMallocHost(&C->host_pinned, 64 * sizeof(double)));
   CUDA_TRY(cudaEventCreate(&C->ev0));
   CUDA_TRY(cudaEventCreate(&C->ev1));
+  CUDA_TRY(cudaStreamCreateWithFlags(&C->ws, cudaStreamNonBlocking));
+  CUDA_TRY(cudaEventCreateWithFlags(&C->join_in, cudaEventDisableTiming));
+  CUDA_TRY(cudaEventCreateWithFlags(&C->join_out, cudaEventDisableTiming));
   CUDA_TRY(cudaDeviceSynchronize());
   return C.release();
 }
@@ -267,32 +292,32 @@ void ensure_work(Context& C) {
 // residual, restriction (Eq. 18), recursion, prolongation (Eq. 17), post-smoothing with reverse
 // colour order; level 0 is solved with the dense coarse inverse.
 template <typename R>
-void vcycle_rec(Context& C, int l, const R* r, R* z) {
+void vcycle_rec(Context& C, int l, const R* r, R* z, cudaStream_t s) {
   DevLevel& L = C.lv[l];
   const int pi = prec_index<R>();
-  const cudaStream_t s = C.stream;
   if (l == 0) {
     CUDA_TRY(launch_coarse<R>(L.coarse_inv, L.H.n_dof(), r, z, s));
     return;
   }
   const int dim = L.H.dim;
   const LevelParams<R>& P = params<R>(L);
-  CUDA_TRY(cudaMemsetAsync(z, 0, (size_t)L.H.n_dof() * sizeof(R), s));
-  for (int k = 0; k < C.desc.pre_smooth; ++k) CUDA_TRY(launch_smooth<R>(dim, L.H.p, P, 0, r, z, s));
+  if (C.desc.pre_smooth == 0) CUDA_TRY(cudaMemsetAsync(z, 0, (size_t)L.H.n_dof() * sizeof(R), s));
+  for (int k = 0; k < C.desc.pre_smooth; ++k) CUDA_TRY(launch_smooth<R>(dim, L.H.p, P, 0, k == 0, r, z, s));
   R* res = static_cast<R*>(L.res[pi]);
   CUDA_TRY((launch_apply<R, R>(dim, L.H.p, P, z, r, res, 1, s)));
   DevLevel& Lc = C.lv[l - 1];
   R* rc = static_cast<R*>(Lc.rhs[pi]);
   R* zc = static_cast<R*>(Lc.z[pi]);
   CUDA_TRY(launch_restrict<R>(dim, L.H.p, Lc.H.p, tparams<R>(L), res, rc, s));
-  vcycle_rec<R>(C, l - 1, rc, zc);
+  vcycle_rec<R>(C, l - 1, rc, zc, s);
   CUDA_TRY(launch_prolong<R>(dim, L.H.p, Lc.H.p, tparams<R>(L), zc, z, s));
-  for (int k = 0; k < C.desc.post_smooth; ++k) CUDA_TRY(launch_smooth<R>(dim, L.H.p, P, 1, r, z, s));
+  for (int k = 0; k < C.desc.post_smooth; ++k) CUDA_TRY(launch_smooth<R>(dim, L.H.p, P, 1, 0, r, z, s));
 }
 
 void ensure_krylov(Context& C, int m) {
   const int prec = C.desc.precision;
   if (C.ws_m >= m && C.ws_prec == prec) return;
+  C.drop_graphs();                                  // captured pointers change
   const size_t N = C.lv.back().H.n_dof();
   C.V = C.dalloc<double>((size_t)(m + 1) * N);
   C.Z = prec == SBM_F32 ? (void*)C.dalloc<float>((size_t)m * N) : (void*)C.dalloc<double>((size_t)m * N);
@@ -305,11 +330,72 @@ void ensure_krylov(Context& C, int m) {
   C.ws_prec = prec;
 }
 
-double device_norm(Context& C, const double* v, size_t N, double* out_dev) {
-  CUDA_TRY(launch_multi_dot(v, N, 1, v, N, C.partial, out_dev, 1, C.stream));
-  CUDA_TRY(cudaMemcpyAsync(C.host_pinned, out_dev, sizeof(double), cudaMemcpyDeviceToHost, C.stream));
-  CUDA_TRY(cudaStreamSynchronize(C.stream));
+double device_norm(Context& C, const double* v, size_t N, double* out_dev, cudaStream_t s) {
+  CUDA_TRY(launch_multi_dot(v, N, 1, v, N, C.partial, out_dev, 1, s));
+  CUDA_TRY(cudaMemcpyAsync(C.host_pinned, out_dev, sizeof(double), cudaMemcpyDeviceToHost, s));
+  CUDA_TRY(cudaStreamSynchronize(s));
   return C.host_pinned[0];
+}
+
+// All device work of Arnoldi step j (Sec. 3: one V-cycle, then the FP64 operator and two
+// classical Gram-Schmidt passes), ending with the copy of Hessenberg column j to pinned memory.
+void arnoldi_step_work(Context& C, int j, cudaStream_t s) {
+  const int prec = C.desc.precision;
+  const int Lf = C.finest();
+  DevLevel& F = C.lv[Lf];
+  const size_t N = F.H.n_dof();
+  const int dim = F.H.dim, p = F.H.p;
+  double* h1 = C.dots;
+  double* h2 = C.dots + 32;
+  double* hn = C.dots + 64;
+  double* col = C.dots + 96;
+  double* Vj = C.V + (size_t)j * N;
+  if (prec == SBM_F32) {
+    float* Zj = static_cast<float*>(C.Z) + (size_t)j * N;
+    CUDA_TRY((launch_cast<double, float>(Vj, C.r32, N, s)));
+    vcycle_rec<float>(C, Lf, C.r32, Zj, s);
+    CUDA_TRY((launch_apply<float, double>(dim, p, F.P64, Zj, nullptr, C.w, 0, s)));
+  } else {
+    double* Zj = static_cast<double*>(C.Z) + (size_t)j * N;
+    vcycle_rec<double>(C, Lf, Vj, Zj, s);
+    CUDA_TRY((launch_apply<double, double>(dim, p, F.P64, Zj, nullptr, C.w, 0, s)));
+  }
+  CUDA_TRY(launch_multi_dot(C.V, N, j + 1, C.w, N, C.partial, h1, 0, s));
+  CUDA_TRY(launch_multi_axpy<double>(C.V, N, j + 1, h1, -1.0, C.w, N, s));
+  CUDA_TRY(launch_multi_dot(C.V, N, j + 1, C.w, N, C.partial, h2, 0, s));
+  CUDA_TRY(launch_multi_axpy<double>(C.V, N, j + 1, h2, -1.0, C.w, N, s));
+  CUDA_TRY(launch_multi_dot(C.w, N, 1, C.w, N, C.partial, hn, 1, s));
+  CUDA_TRY(launch_div_scalar(C.w, hn, C.V + (size_t)(j + 1) * N, N, s));
+  CUDA_TRY(launch_hess_column(h1, h2, hn, j + 1, col, s));
+  CUDA_TRY(cudaMemcpyAsync(C.host_pinned, col, (j + 2) * sizeof(double), cudaMemcpyDeviceToHost, s));
+}
+
+// Runs step j from its captured graph (captured on first use).
+void run_arnoldi_step(Context& C, int j, cudaStream_t s) {
+  const int pi = C.desc.precision == SBM_F32 ? 1 : 0;
+  if (!C.arnoldi[pi][j]) {
+    const long long before = g_kernel_launches.load();
+    CUDA_TRY(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+    try {
+      arnoldi_step_work(C, j, s);
+    } catch (...) {
+      cudaGraph_t g = nullptr;
+      cudaStreamEndCapture(s, &g);
+      if (g) cudaGraphDestroy(g);
+      throw;
+    }
+    cudaGraph_t g = nullptr;
+    CUDA_TRY(cudaStreamEndCapture(s, &g));
+    cudaGraphExec_t ge = nullptr;
+    const cudaError_t e = cudaGraphInstantiate(&ge, g, 0);
+    cudaGraphDestroy(g);
+    CUDA_TRY(e);
+    C.arnoldi[pi][j] = ge;
+    C.arnoldi_kernels[pi][j] = g_kernel_launches.load() - before;
+    g_kernel_launches.fetch_sub(C.arnoldi_kernels[pi][j]);   // captured, not executed
+  }
+  CUDA_TRY(cudaGraphLaunch(C.arnoldi[pi][j], s));
+  count_launches(C.arnoldi_kernels[pi][j]);
 }
 
 // Right-preconditioned flexible GMRES(m) with two classical Gram-Schmidt passes, FP64.
@@ -322,15 +408,14 @@ int solve_impl(Context& C, const double* b, double* x, double tol, int m, int ma
   const int Lf = C.finest();
   DevLevel& F = C.lv[Lf];
   const size_t N = F.H.n_dof();
-  const cudaStream_t s = C.stream;
+  const cudaStream_t s = C.ws;
   const int dim = F.H.dim, p = F.H.p;
-  double* h1 = C.dots;
-  double* h2 = C.dots + 32;
   double* hn = C.dots + 64;
-  double* col = C.dots + 96;
   sbm_solve_info loc{};
+  CUDA_TRY(cudaEventRecord(C.join_in, C.stream));   // b and x are ready on the caller's stream
+  CUDA_TRY(cudaStreamWaitEvent(s, C.join_in, 0));
   CUDA_TRY(cudaEventRecord(C.ev0, s));
-  const double bnorm = device_norm(C, b, N, hn);
+  const double bnorm = device_norm(C, b, N, hn, s);
   if (!std::isfinite(bnorm)) throw SetupError{SBM_ERR_NAN, "non-finite ||b||"};
   int status = SBM_OK;
   if (bnorm == 0.0) {
@@ -342,7 +427,7 @@ int solve_impl(Context& C, const double* b, double* x, double tol, int m, int ma
     while (true) {
       double* V0 = C.V;
       CUDA_TRY((launch_apply<double, double>(dim, p, F.P64, x, b, V0, 1, s)));
-      const double beta = device_norm(C, V0, N, hn);
+      const double beta = device_norm(C, V0, N, hn, s);
       loc.true_rel_residual = beta / bnorm;
       if (!std::isfinite(beta)) {
         status = SBM_ERR_NAN;
@@ -363,25 +448,7 @@ int solve_impl(Context& C, const double* b, double* x, double tol, int m, int ma
       int k = 0;
       bool nan = false;
       for (int j = 0; j < m; ++j) {
-        double* Vj = C.V + (size_t)j * N;
-        if (prec == SBM_F32) {
-          float* Zj = static_cast<float*>(C.Z) + (size_t)j * N;
-          CUDA_TRY((launch_cast<double, float>(Vj, C.r32, N, s)));
-          vcycle_rec<float>(C, Lf, C.r32, Zj);
-          CUDA_TRY((launch_apply<float, double>(dim, p, F.P64, Zj, nullptr, C.w, 0, s)));
-        } else {
-          double* Zj = static_cast<double*>(C.Z) + (size_t)j * N;
-          vcycle_rec<double>(C, Lf, Vj, Zj);
-          CUDA_TRY((launch_apply<double, double>(dim, p, F.P64, Zj, nullptr, C.w, 0, s)));
-        }
-        CUDA_TRY(launch_multi_dot(C.V, N, j + 1, C.w, N, C.partial, h1, 0, s));
-        CUDA_TRY(launch_multi_axpy<double>(C.V, N, j + 1, h1, -1.0, C.w, N, s));
-        CUDA_TRY(launch_multi_dot(C.V, N, j + 1, C.w, N, C.partial, h2, 0, s));
-        CUDA_TRY(launch_multi_axpy<double>(C.V, N, j + 1, h2, -1.0, C.w, N, s));
-        CUDA_TRY(launch_multi_dot(C.w, N, 1, C.w, N, C.partial, hn, 1, s));
-        CUDA_TRY(launch_div_scalar(C.w, hn, C.V + (size_t)(j + 1) * N, N, s));
-        CUDA_TRY(launch_hess_column(h1, h2, hn, j + 1, col, s));
-        CUDA_TRY(cudaMemcpyAsync(C.host_pinned, col, (j + 2) * sizeof(double), cudaMemcpyDeviceToHost, s));
+        run_arnoldi_step(C, j, s);
         CUDA_TRY(cudaStreamSynchronize(s));
         for (int i = 0; i <= j + 1; ++i) {
           H[(size_t)i * m + j] = C.host_pinned[i];
@@ -429,6 +496,8 @@ int solve_impl(Context& C, const double* b, double* x, double tol, int m, int ma
     }
   }
   CUDA_TRY(cudaEventRecord(C.ev1, s));
+  CUDA_TRY(cudaEventRecord(C.join_out, s));
+  CUDA_TRY(cudaStreamWaitEvent(C.stream, C.join_out, 0));
   CUDA_TRY(cudaEventSynchronize(C.ev1));
   float ms = 0;
   CUDA_TRY(cudaEventElapsedTime(&ms, C.ev0, C.ev1));
@@ -613,9 +682,11 @@ int sbm_smooth(void* ctx, int level, int dtype, int reverse, const void* f_dev, 
   return guarded([&]() -> int {
     DevLevel& L = C->lv[level];
     if (dtype == SBM_F64)
-      CUDA_TRY(launch_smooth<double>(L.H.dim, L.H.p, L.P64, reverse, (const double*)f_dev, (double*)u_dev, C->stream));
+      CUDA_TRY(launch_smooth<double>(L.H.dim, L.H.p, L.P64, reverse, 0, (const double*)f_dev, (double*)u_dev,
+                                     C->stream));
     else if (dtype == SBM_F32)
-      CUDA_TRY(launch_smooth<float>(L.H.dim, L.H.p, L.P32, reverse, (const float*)f_dev, (float*)u_dev, C->stream));
+      CUDA_TRY(launch_smooth<float>(L.H.dim, L.H.p, L.P32, reverse, 0, (const float*)f_dev, (float*)u_dev,
+                                    C->stream));
     else
       return set_error(SBM_ERR_ARG, "dtype");
     return SBM_OK;
@@ -683,13 +754,30 @@ int sbm_vcycle(void* ctx, int dtype, const void* r_dev, void* z_dev) {
   return guarded([&]() -> int {
     if (dtype == SBM_F64) {
       ensure_work<double>(*C);
-      vcycle_rec<double>(*C, C->finest(), (const double*)r_dev, (double*)z_dev);
+      vcycle_rec<double>(*C, C->finest(), (const double*)r_dev, (double*)z_dev, C->stream);
     } else if (dtype == SBM_F32) {
       ensure_work<float>(*C);
-      vcycle_rec<float>(*C, C->finest(), (const float*)r_dev, (float*)z_dev);
+      vcycle_rec<float>(*C, C->finest(), (const float*)r_dev, (float*)z_dev, C->stream);
     } else {
       return set_error(SBM_ERR_ARG, "dtype");
     }
+    return SBM_OK;
+  });
+}
+
+int sbm_dots(void* ctx, const double* V_dev, long long ldv, int nv, const double* w_dev, long long n,
+             double* out_dev) {
+  Context* C = ctx_of(ctx);
+  if (C && C->host_only) return set_error(SBM_ERR_ARG, "host-only context");
+  if (!C || !V_dev || !w_dev || !out_dev || nv < 1 || nv > 32 || n < 0 || ldv < n)
+    return set_error(SBM_ERR_ARG, "bad argument");
+  return guarded([&]() -> int {
+    const size_t need = (size_t)dot_blocks((size_t)n) * 32;
+    if (C->dots_scratch_len < need) {
+      C->dots_scratch = C->dalloc<double>(need);
+      C->dots_scratch_len = need;
+    }
+    CUDA_TRY(launch_multi_dot(V_dev, (size_t)ldv, nv, w_dev, (size_t)n, C->dots_scratch, out_dev, 0, C->stream));
     return SBM_OK;
   });
 }

@@ -18,31 +18,31 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
-// partial[block][k] = sum over this block's grid-stride share of V_k . w
-__global__ void __launch_bounds__(kDotThreads) k_multi_dot(const double* __restrict__ V, size_t ldv, int nv,
+// partial[block][k] = sum over this block's grid-stride share of V_k . w, k < NV.  NV is a
+// compile-time constant so that no predicated FP64 FMA is issued: the FP64 pipe (about 2 FMA per
+// clock per SM on GB300) is the limit of this kernel.
+template <int NV>
+__global__ void __launch_bounds__(kDotThreads) k_multi_dot(const double* __restrict__ V, size_t ldv,
                                                            const double* __restrict__ w, size_t N,
                                                            double* __restrict__ partial) {
-  double acc[kMaxVec];
+  double acc[NV];
 #pragma unroll
-  for (int k = 0; k < kMaxVec; ++k) acc[k] = 0.0;
+  for (int k = 0; k < NV; ++k) acc[k] = 0.0;
   const size_t stride = (size_t)gridDim.x * blockDim.x;
   for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += stride) {
     const double wi = w[i];
 #pragma unroll
-    for (int k = 0; k < kMaxVec; ++k)
-      if (k < nv) acc[k] += V[k * ldv + i] * wi;
+    for (int k = 0; k < NV; ++k) acc[k] = fma(V[k * ldv + i], wi, acc[k]);
   }
-  __shared__ double red[kDotThreads / 32][kMaxVec];
+  __shared__ double red[kDotThreads / 32][NV];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 #pragma unroll
-  for (int k = 0; k < kMaxVec; ++k) {
-    if (k < nv) {
-      const double s = warp_sum(acc[k]);
-      if (lane == 0) red[warp][k] = s;
-    }
+  for (int k = 0; k < NV; ++k) {
+    const double s = warp_sum(acc[k]);
+    if (lane == 0) red[warp][k] = s;
   }
   __syncthreads();
-  if (threadIdx.x < nv) {
+  if (threadIdx.x < NV) {
     double s = 0.0;
 #pragma unroll
     for (int q = 0; q < kDotThreads / 32; ++q) s += red[q][threadIdx.x];
@@ -50,13 +50,16 @@ __global__ void __launch_bounds__(kDotThreads) k_multi_dot(const double* __restr
   }
 }
 
-__global__ void k_reduce_partials(const double* __restrict__ partial, int nblk, int nv, double* __restrict__ out,
-                                  int take_sqrt) {
-  const int k = threadIdx.x;
+// out[k] = sum_b partial[b][k]: warp k sums a fixed lane-strided share and shuffles, so the
+// order of the additions is fixed for a given number of blocks (deterministic results).
+__global__ void __launch_bounds__(1024) k_reduce_partials(const double* __restrict__ partial, int nblk, int nv,
+                                                          double* __restrict__ out, int take_sqrt) {
+  const int k = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (k >= nv) return;
   double s = 0.0;
-  for (int b = 0; b < nblk; ++b) s += partial[(size_t)b * kMaxVec + k];
-  out[k] = take_sqrt ? sqrt(s) : s;
+  for (int b = lane; b < nblk; b += 32) s += partial[(size_t)b * kMaxVec + k];
+  s = warp_sum(s);
+  if (lane == 0) out[k] = take_sqrt ? sqrt(s) : s;
 }
 
 template <typename TZ>
@@ -113,8 +116,18 @@ cudaError_t launch_multi_dot(const double* V, size_t ldv, int nv, const double* 
                              double* out, int take_sqrt, cudaStream_t s) {
   if (nv < 1 || nv > kMaxVec) return cudaErrorInvalidValue;
   const int nblk = dot_blocks(N);
-  k_multi_dot<<<nblk, kDotThreads, 0, s>>>(V, ldv, nv, w, N, partial);
-  k_reduce_partials<<<1, kMaxVec, 0, s>>>(partial, nblk, nv, out, take_sqrt);
+  switch (nv) {
+#define SBM_DOT_CASE(K) \
+  case K: k_multi_dot<K><<<nblk, kDotThreads, 0, s>>>(V, ldv, w, N, partial); break;
+    SBM_DOT_CASE(1) SBM_DOT_CASE(2) SBM_DOT_CASE(3) SBM_DOT_CASE(4) SBM_DOT_CASE(5) SBM_DOT_CASE(6)
+    SBM_DOT_CASE(7) SBM_DOT_CASE(8) SBM_DOT_CASE(9) SBM_DOT_CASE(10) SBM_DOT_CASE(11) SBM_DOT_CASE(12)
+    SBM_DOT_CASE(13) SBM_DOT_CASE(14) SBM_DOT_CASE(15) SBM_DOT_CASE(16) SBM_DOT_CASE(17) SBM_DOT_CASE(18)
+    SBM_DOT_CASE(19) SBM_DOT_CASE(20) SBM_DOT_CASE(21) SBM_DOT_CASE(22) SBM_DOT_CASE(23) SBM_DOT_CASE(24)
+    SBM_DOT_CASE(25) SBM_DOT_CASE(26) SBM_DOT_CASE(27) SBM_DOT_CASE(28) SBM_DOT_CASE(29) SBM_DOT_CASE(30)
+    SBM_DOT_CASE(31) SBM_DOT_CASE(32)
+#undef SBM_DOT_CASE
+  }
+  k_reduce_partials<<<1, 32 * nv, 0, s>>>(partial, nblk, nv, out, take_sqrt);
   count_launches(2);
   return cudaGetLastError();
 }

@@ -232,9 +232,13 @@ __global__ void __launch_bounds__(256) k_apply(const __grid_constant__ LevelPara
 // which equals u_K + omega A_KK^{-1}(f - A u)_K.  Blocks [0, nblk_b) take the colour's boundary
 // cells (dense inverse), the remaining blocks its interior cells (fast diagonalisation
 // A_KK^{-1} = h^(2-d) S^(x d) diag(1 / sum lambda) (S^T)^(x d)).
+//
+// zero_start: u is the zero vector before this forward sweep; cells of colours not yet visited
+// (neighbour colour > col) are read as zero and u itself is not read, so no memset is needed.
 template <int D, int N1, typename R>
-__global__ void __launch_bounds__(256) k_smooth(const __grid_constant__ LevelParams<R> P, int cs, int nbnd, int ce,
-                                                int nblk_b, int b0, const R* __restrict__ f, R* __restrict__ u) {
+__global__ void __launch_bounds__(256) k_smooth(const __grid_constant__ LevelParams<R> P, int col, int zero_start,
+                                                int cs, int nbnd, int ce, int nblk_b, int b0,
+                                                const R* __restrict__ f, R* __restrict__ u) {
   using Dm = Dims<D, N1>;
   constexpr int NP = Dm::NP, NS = Dm::NS, CPB = Dm::CPB;
   __shared__ LevelConsts<R> C;
@@ -253,9 +257,10 @@ __global__ void __launch_bounds__(256) k_smooth(const __grid_constant__ LevelPar
 #pragma unroll
     for (int s = 0; s < NS; ++s) {
       nb[s] = P.nbr[(size_t)s * P.n_act + a];
+      if (zero_start && (col ^ (1 << (s >> 1))) > col) nb[s] = -1;   // unvisited colour: zero
       sN[(c * NS + s) * NP + i] = nb[s] >= 0 ? u[(size_t)nb[s] * NP + i] : R(0);
     }
-    if (P.omega != R(1)) uold = u[(size_t)a * NP + i];
+    if (P.omega != R(1) && !zero_start) uold = u[(size_t)a * NP + i];
   }
   __syncthreads();
   int ii[3];
@@ -467,7 +472,9 @@ cudaError_t launch_apply(int dim, int p, const LevelParams<R>& P, const TI* x, c
 }
 
 template <typename R>
-cudaError_t launch_smooth(int dim, int p, const LevelParams<R>& P, int reverse, const R* f, R* u, cudaStream_t s) {
+cudaError_t launch_smooth(int dim, int p, const LevelParams<R>& P, int reverse, int zero_start, const R* f, R* u,
+                          cudaStream_t s) {
+  if (reverse) zero_start = 0;
   const int ncol = 1 << dim;
   for (int q = 0; q < ncol; ++q) {
     const int col = reverse ? ncol - 1 - q : q;
@@ -478,7 +485,8 @@ cudaError_t launch_smooth(int dim, int p, const LevelParams<R>& P, int reverse, 
     const int nblk_b = (int)ceil_div(nbnd, Dm::CPB);                                               \
     const int nblk_i = (int)ceil_div(ce - cs - nbnd, Dm::CPB);                                     \
     if (nblk_b + nblk_i > 0) {                                                                     \
-      k_smooth<D, N1, R><<<nblk_b + nblk_i, Dm::NT, 0, s>>>(P, cs, nbnd, ce, nblk_b, P.bstart[col], f, u); \
+      k_smooth<D, N1, R><<<nblk_b + nblk_i, Dm::NT, 0, s>>>(P, col, zero_start, cs, nbnd, ce, nblk_b,   \
+                                                            P.bstart[col], f, u);                    \
       count_launches();                                                                            \
     }                                                                                              \
   }
@@ -541,9 +549,9 @@ template cudaError_t launch_apply<float, float>(int, int, const LevelParams<floa
                                                 float*, int, cudaStream_t);
 template cudaError_t launch_apply<float, double>(int, int, const LevelParams<double>&, const float*, const double*,
                                                  double*, int, cudaStream_t);
-template cudaError_t launch_smooth<double>(int, int, const LevelParams<double>&, int, const double*, double*,
+template cudaError_t launch_smooth<double>(int, int, const LevelParams<double>&, int, int, const double*, double*,
                                            cudaStream_t);
-template cudaError_t launch_smooth<float>(int, int, const LevelParams<float>&, int, const float*, float*,
+template cudaError_t launch_smooth<float>(int, int, const LevelParams<float>&, int, int, const float*, float*,
                                           cudaStream_t);
 template cudaError_t launch_restrict<double>(int, int, int, const TransferParams<double>&, const double*, double*,
                                              cudaStream_t);

@@ -19,9 +19,11 @@ template <typename TI, typename R>
 cudaError_t launch_apply(int dim, int p, const LevelParams<R>& P, const TI* x, const R* f, R* y, int mode,
                          cudaStream_t s);
 
-// One coloured block Gauss-Seidel sweep (all colours, forward or reverse).
+// One coloured block Gauss-Seidel sweep (all colours, forward or reverse).  zero_start (forward
+// only): u holds zeros on entry and is not read or cleared beforehand.
 template <typename R>
-cudaError_t launch_smooth(int dim, int p, const LevelParams<R>& P, int reverse, const R* f, R* u, cudaStream_t s);
+cudaError_t launch_smooth(int dim, int p, const LevelParams<R>& P, int reverse, int zero_start, const R* f, R* u,
+                          cudaStream_t s);
 
 // rc = P^T rf (restriction) and uf += P ec (prolongation) between level l-1 and l.
 template <typename R>

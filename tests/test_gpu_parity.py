@@ -223,6 +223,20 @@ def test_fgmres_fp32_vcycle(name):
     assert abs(info.iterations - oi.iterations) <= max(2, oi.iterations // 5)
 
 
+@pytest.mark.parametrize("n,nv", [(1, 1), (1000, 5), (912582, 31), (4097, 32)])
+def test_gram_schmidt_dots(n, nv):
+    """a6: the FGMRES projections V^T w (deterministic two-stage reduction) against NumPy FP64,
+    within the dot-product rounding bound n eps sum_i |V_ki w_i|; bitwise repeatable."""
+    P = pair("disk2d_p1_n32")
+    rng = np.random.default_rng(n)
+    V, w = rng.normal(size=(nv, n)), rng.normal(size=n)
+    Vt, wt = torch.tensor(V, device="cuda"), torch.tensor(w, device="cuda")
+    out = P.gpu.dots(Vt, wt).cpu().numpy()
+    bound = n * 2.2e-16 * (np.abs(V) @ np.abs(w))
+    assert np.all(np.abs(out - V @ w) <= bound + 1e-300)
+    assert np.array_equal(out, P.gpu.dots(Vt, wt).cpu().numpy())
+
+
 def test_solve_host_buffers():
     P = pair("disk2d_p1_n32")
     b = P.gpu.rhs()
