@@ -50,7 +50,8 @@ class _Desc(ctypes.Structure):
                 ("sigma_face_c", ctypes.c_double), ("sigma_bnd_c", ctypes.c_double), ("alpha", ctypes.c_double),
                 ("extension", ctypes.c_int), ("coarsest_n", ctypes.c_int), ("pre_smooth", ctypes.c_int),
                 ("post_smooth", ctypes.c_int), ("omega", ctypes.c_double), ("omega_p3", ctypes.c_double),
-                ("vf_samples", ctypes.c_int), ("precision", ctypes.c_int), ("stream", ctypes.c_void_p)]
+                ("vf_samples", ctypes.c_int), ("precision", ctypes.c_int), ("tail_max_cells", ctypes.c_int),
+                ("stream", ctypes.c_void_p)]
 
 
 class _LevelInfo(ctypes.Structure):
@@ -130,7 +131,7 @@ def _check(code: int):
         raise SbmError(code, _lib.sbm_last_error().decode())
 
 
-def make_desc(prob, precision: int = SBM_F64, stream: int = 0) -> _Desc:
+def make_desc(prob, precision: int = SBM_F64, stream: int = 0, tail_max_cells: int = 0) -> _Desc:
     d = _Desc()
     d.dim, d.n, d.p = prob.dim, prob.n, prob.p
     d.lo[:] = [float(v) for v in prob.lo]
@@ -146,13 +147,15 @@ def make_desc(prob, precision: int = SBM_F64, stream: int = 0) -> _Desc:
     d.extension, d.coarsest_n = prob.extension, prob.coarsest_n
     d.pre_smooth, d.post_smooth, d.omega, d.omega_p3 = prob.pre_smooth, prob.post_smooth, prob.omega, prob.omega_p3
     d.vf_samples, d.precision, d.stream = prob.vf_samples, precision, stream
+    d.tail_max_cells = tail_max_cells
     return d
 
 
 class Solver:
     """One DG-SBM problem set up on the current CUDA device (a libsbm context)."""
 
-    def __init__(self, prob, precision: str = "f64", stream=None):
+    def __init__(self, prob, precision: str = "f64", stream=None, tail_max_cells: int = 0):
+        """tail_max_cells: small p = 1 levels run as one cluster launch (0: default, < 0: never)."""
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("libsbm needs a CUDA device; no CPU fallback exists")
@@ -161,7 +164,7 @@ class Solver:
         self.prob = prob
         self.precision = SBM_F32 if precision == "f32" else SBM_F64
         self.stream = stream if stream is not None else torch.cuda.current_stream()
-        desc = make_desc(prob, self.precision, self.stream.cuda_stream)
+        desc = make_desc(prob, self.precision, self.stream.cuda_stream, tail_max_cells)
         ctx = ctypes.c_void_p()
         _check(self.lib.sbm_setup(ctypes.byref(desc), ctypes.byref(ctx)))
         self.ctx = ctx

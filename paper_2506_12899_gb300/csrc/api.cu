@@ -57,6 +57,8 @@ struct Context {
   std::vector<double> rhs_host;
   std::vector<void*> allocs;
   bool work_ready[2] = {false, false};
+  int tail_top = -1;                 // levels 0..tail_top form the cluster tail (-1: none)
+  void* tail[2] = {nullptr, nullptr};  // TailLevel<double> / TailLevel<float> arrays
   // FGMRES workspace
   int ws_m = 0, ws_prec = -1;
   double* V = nullptr;
@@ -157,6 +159,9 @@ LevelParams<R> make_params(const DevLevel& D, const R* dhat, const R* binv) {
   for (int ij = 0; ij < n1 * n1; ++ij) {
     P.k.Bmp[ij] = (R)H.Bmp[ij];
     P.k.Bpm[ij] = (R)H.Bpm[ij];
+    P.k.Kh[ij] = (R)H.B.Khat[ij];
+    P.k.Bmm[ij] = (R)H.Bmm[ij];
+    P.k.Bpp[ij] = (R)H.Bpp[ij];
     P.k.Dm[ij] = (R)H.B.Dm[ij];
     P.k.S[ij] = (R)H.S[ij];
   }
@@ -265,6 +270,18 @@ Context* build_context(const sbm_setup_desc& d, bool device) {
     C->lv[l].T64 = make_transfer<double>(C->lv[l - 1], C->lv[l]);
     C->lv[l].T32 = make_transfer<float>(C->lv[l - 1], C->lv[l]);
   }
+  {
+    const int cap = d.tail_max_cells == 0 ? 40000 : d.tail_max_cells;
+    int top = -1;
+    for (int l = 0; l < (int)C->lv.size(); ++l) {
+      const HostLevel& H = C->lv[l].H;
+      const bool h_level = l == 0 || (H.n == 2 * C->lv[l - 1].H.n && H.p == 1);
+      if (H.p != 1 || !h_level || H.n_act > cap) break;
+      top = l;
+    }
+    C->tail_top = (cap > 0 && top >= 1 && tail_cluster_size(d.dim, 0) > 0 && tail_cluster_size(d.dim, 1) > 0)
+                      ? top : -1;
+  }
   CUDA_TRY(cudaMallocHost(&C->host_pinned, 64 * sizeof(double)));
   CUDA_TRY(cudaEventCreate(&C->ev0));
   CUDA_TRY(cudaEventCreate(&C->ev1));
@@ -285,6 +302,19 @@ void ensure_work(Context& C) {
     L.rhs[pi] = C.dalloc<R>(N);
     L.res[pi] = C.dalloc<R>(N);
   }
+  if (C.tail_top >= 1) {
+    std::vector<TailLevel<R>> tl(C.tail_top + 1);
+    for (int l = 0; l <= C.tail_top; ++l) {
+      std::memset(&tl[l], 0, sizeof(TailLevel<R>));
+      tl[l].P = params<R>(C.lv[l]);
+      if (l >= 1) tl[l].T = tparams<R>(C.lv[l]);
+      tl[l].z = static_cast<R*>(C.lv[l].z[pi]);
+      tl[l].rhs = static_cast<R*>(C.lv[l].rhs[pi]);
+    }
+    TailLevel<R>* d = C.dalloc<TailLevel<R>>(tl.size());
+    CUDA_TRY(cudaMemcpy(d, tl.data(), tl.size() * sizeof(TailLevel<R>), cudaMemcpyHostToDevice));
+    C.tail[pi] = d;
+  }
   C.work_ready[pi] = true;
 }
 
@@ -299,16 +329,23 @@ void vcycle_rec(Context& C, int l, const R* r, R* z, cudaStream_t s) {
     CUDA_TRY(launch_coarse<R>(L.coarse_inv, L.H.n_dof(), r, z, s));
     return;
   }
+  if (l == C.tail_top) {                          // levels 0..l in one cluster launch
+    CUDA_TRY(launch_vcycle_tail<R>(L.H.dim, static_cast<const TailLevel<R>*>(C.tail[pi]), l, r, z,
+                                   C.lv[0].coarse_inv, C.desc.pre_smooth, C.desc.post_smooth, s));
+    return;
+  }
   const int dim = L.H.dim;
   const LevelParams<R>& P = params<R>(L);
   if (C.desc.pre_smooth == 0) CUDA_TRY(cudaMemsetAsync(z, 0, (size_t)L.H.n_dof() * sizeof(R), s));
   for (int k = 0; k < C.desc.pre_smooth; ++k) CUDA_TRY(launch_smooth<R>(dim, L.H.p, P, 0, k == 0, r, z, s));
-  R* res = static_cast<R*>(L.res[pi]);
-  CUDA_TRY((launch_apply<R, R>(dim, L.H.p, P, z, r, res, 1, s)));
   DevLevel& Lc = C.lv[l - 1];
   R* rc = static_cast<R*>(Lc.rhs[pi]);
   R* zc = static_cast<R*>(Lc.z[pi]);
-  CUDA_TRY(launch_restrict<R>(dim, L.H.p, Lc.H.p, tparams<R>(L), res, rc, s));
+  if (Lc.H.n == L.H.n) {                          // p-transfer: residual restricted in the same kernel
+    CUDA_TRY(launch_resid_restrict_p<R>(dim, L.H.p, P, tparams<R>(L), z, r, rc, s));
+  } else {                                        // h-transfer: coarse cells gather their children
+    CUDA_TRY(launch_resid_restrict_h<R>(dim, P, tparams<R>(L), z, r, rc, s));
+  }
   vcycle_rec<R>(C, l - 1, rc, zc, s);
   CUDA_TRY(launch_prolong<R>(dim, L.H.p, Lc.H.p, tparams<R>(L), zc, z, s));
   for (int k = 0; k < C.desc.post_smooth; ++k) CUDA_TRY(launch_smooth<R>(dim, L.H.p, P, 1, 0, r, z, s));
@@ -360,11 +397,10 @@ void arnoldi_step_work(Context& C, int j, cudaStream_t s) {
     vcycle_rec<double>(C, Lf, Vj, Zj, s);
     CUDA_TRY((launch_apply<double, double>(dim, p, F.P64, Zj, nullptr, C.w, 0, s)));
   }
+  // CGS2 in three sweeps over V: h1 = V^T w; w -= V h1 and h2 = V^T w; w -= V h2 and |w|
   CUDA_TRY(launch_multi_dot(C.V, N, j + 1, C.w, N, C.partial, h1, 0, s));
-  CUDA_TRY(launch_multi_axpy<double>(C.V, N, j + 1, h1, -1.0, C.w, N, s));
-  CUDA_TRY(launch_multi_dot(C.V, N, j + 1, C.w, N, C.partial, h2, 0, s));
-  CUDA_TRY(launch_multi_axpy<double>(C.V, N, j + 1, h2, -1.0, C.w, N, s));
-  CUDA_TRY(launch_multi_dot(C.w, N, 1, C.w, N, C.partial, hn, 1, s));
+  CUDA_TRY(launch_axpy_dot(C.V, N, j + 1, h1, C.w, N, C.partial, h2, s));
+  CUDA_TRY(launch_axpy_norm(C.V, N, j + 1, h2, C.w, N, C.partial, hn, s));
   CUDA_TRY(launch_div_scalar(C.w, hn, C.V + (size_t)(j + 1) * N, N, s));
   CUDA_TRY(launch_hess_column(h1, h2, hn, j + 1, col, s));
   CUDA_TRY(cudaMemcpyAsync(C.host_pinned, col, (j + 2) * sizeof(double), cudaMemcpyDeviceToHost, s));
@@ -532,6 +568,7 @@ int guarded(F&& f) {
 }
 
 }  // namespace
+
 }  // namespace sbm
 
 using namespace sbm;

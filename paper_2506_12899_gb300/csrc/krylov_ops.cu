@@ -18,22 +18,9 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
-// partial[block][k] = sum over this block's grid-stride share of V_k . w, k < NV.  NV is a
-// compile-time constant so that no predicated FP64 FMA is issued: the FP64 pipe (about 2 FMA per
-// clock per SM on GB300) is the limit of this kernel.
+// Block-level reduction of NV per-thread sums into partial[blockIdx][k].
 template <int NV>
-__global__ void __launch_bounds__(kDotThreads) k_multi_dot(const double* __restrict__ V, size_t ldv,
-                                                           const double* __restrict__ w, size_t N,
-                                                           double* __restrict__ partial) {
-  double acc[NV];
-#pragma unroll
-  for (int k = 0; k < NV; ++k) acc[k] = 0.0;
-  const size_t stride = (size_t)gridDim.x * blockDim.x;
-  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += stride) {
-    const double wi = w[i];
-#pragma unroll
-    for (int k = 0; k < NV; ++k) acc[k] = fma(V[k * ldv + i], wi, acc[k]);
-  }
+__device__ __forceinline__ void block_partials(const double (&acc)[NV], double* __restrict__ partial) {
   __shared__ double red[kDotThreads / 32][NV];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 #pragma unroll
@@ -48,6 +35,79 @@ __global__ void __launch_bounds__(kDotThreads) k_multi_dot(const double* __restr
     for (int q = 0; q < kDotThreads / 32; ++q) s += red[q][threadIdx.x];
     partial[(size_t)blockIdx.x * kMaxVec + threadIdx.x] = s;
   }
+}
+
+constexpr int kDotE = 4;                        // elements per thread per chunk
+constexpr size_t kDotChunk = (size_t)kDotThreads * kDotE;
+
+// partial[block][k] = this block's share of V_k . w, k < NV.  A block sweeps chunks of
+// kDotChunk consecutive elements; within a chunk it reads each vector V_k as one contiguous
+// 8 KB run (DRAM-friendly) while w stays in registers.  NV is a compile-time constant so that
+// no predicated FP64 FMA is issued: the FP64 pipe (about 2 FMA per clock per SM on GB300) and
+// HBM are the two limits of this kernel.
+template <int NV>
+__global__ void __launch_bounds__(kDotThreads) k_multi_dot(const double* __restrict__ V, size_t ldv,
+                                                           const double* __restrict__ w, size_t N,
+                                                           double* __restrict__ partial) {
+  double acc[NV];
+#pragma unroll
+  for (int k = 0; k < NV; ++k) acc[k] = 0.0;
+  for (size_t base = (size_t)blockIdx.x * kDotChunk; base < N; base += (size_t)gridDim.x * kDotChunk) {
+    double wv[kDotE];
+#pragma unroll
+    for (int e = 0; e < kDotE; ++e) {
+      const size_t i = base + (size_t)e * kDotThreads + threadIdx.x;
+      wv[e] = i < N ? w[i] : 0.0;
+    }
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+      const double* row = V + k * ldv;
+      double sk = 0.0;
+#pragma unroll
+      for (int e = 0; e < kDotE; ++e) {
+        const size_t i = base + (size_t)e * kDotThreads + threadIdx.x;
+        sk = fma(i < N ? row[i] : 0.0, wv[e], sk);
+      }
+      acc[k] += sk;
+    }
+  }
+  block_partials<NV>(acc, partial);
+}
+
+// Second Gram-Schmidt pass fused with the first update: w <- w - sum_k h[k] V_k, then
+// partial sums of V_k . w (new w) for k < NV, and of |w|^2 when NORM (then NV = 0 dots).
+template <int NV, bool NORM>
+__global__ void __launch_bounds__(kDotThreads) k_axpy_dot(const double* __restrict__ V, size_t ldv,
+                                                          const double* __restrict__ h, double* __restrict__ w,
+                                                          size_t N, int nv, double* __restrict__ partial) {
+  constexpr int NA = NORM ? 1 : NV;            // accumulators
+  __shared__ double hs[kMaxVec];
+  if (threadIdx.x < nv) hs[threadIdx.x] = h[threadIdx.x];
+  __syncthreads();
+  double acc[NA];
+#pragma unroll
+  for (int k = 0; k < NA; ++k) acc[k] = 0.0;
+  const size_t stride = (size_t)gridDim.x * kDotThreads;
+  for (size_t i = (size_t)blockIdx.x * kDotThreads + threadIdx.x; i < N; i += stride) {
+    if (NORM) {
+      double wi = w[i];
+      for (int k = 0; k < nv; ++k) wi = fma(-hs[k], V[k * ldv + i], wi);
+      w[i] = wi;
+      acc[0] = fma(wi, wi, acc[0]);
+    } else {
+      double v[NV > 0 ? NV : 1];
+      double wi = w[i];
+#pragma unroll
+      for (int k = 0; k < NV; ++k) {
+        v[k] = V[k * ldv + i];
+        wi = fma(-hs[k], v[k], wi);
+      }
+      w[i] = wi;
+#pragma unroll
+      for (int k = 0; k < NV; ++k) acc[k] = fma(v[k], wi, acc[k]);
+    }
+  }
+  block_partials<NA>(acc, partial);
 }
 
 // out[k] = sum_b partial[b][k]: warp k sums a fixed lane-strided share and shuffles, so the
@@ -106,7 +166,7 @@ unsigned grid_for(size_t N) {
 std::atomic<long long> g_kernel_launches{0};
 
 int dot_blocks(size_t N) {
-  size_t g = (N + kDotThreads * 4 - 1) / (kDotThreads * 4);
+  size_t g = (N + kDotChunk - 1) / kDotChunk;
   if (g < 1) g = 1;
   if (g > 152 * 4) g = 152 * 4;
   return (int)g;
@@ -128,6 +188,36 @@ cudaError_t launch_multi_dot(const double* V, size_t ldv, int nv, const double* 
 #undef SBM_DOT_CASE
   }
   k_reduce_partials<<<1, 32 * nv, 0, s>>>(partial, nblk, nv, out, take_sqrt);
+  count_launches(2);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_axpy_dot(const double* V, size_t ldv, int nv, const double* h, double* w, size_t N,
+                            double* partial, double* out, cudaStream_t s) {
+  if (nv < 1 || nv > kMaxVec) return cudaErrorInvalidValue;
+  const int nblk = dot_blocks(N);
+  switch (nv) {
+#define SBM_AD_CASE(K) \
+  case K: k_axpy_dot<K, false><<<nblk, kDotThreads, 0, s>>>(V, ldv, h, w, N, nv, partial); break;
+    SBM_AD_CASE(1) SBM_AD_CASE(2) SBM_AD_CASE(3) SBM_AD_CASE(4) SBM_AD_CASE(5) SBM_AD_CASE(6)
+    SBM_AD_CASE(7) SBM_AD_CASE(8) SBM_AD_CASE(9) SBM_AD_CASE(10) SBM_AD_CASE(11) SBM_AD_CASE(12)
+    SBM_AD_CASE(13) SBM_AD_CASE(14) SBM_AD_CASE(15) SBM_AD_CASE(16) SBM_AD_CASE(17) SBM_AD_CASE(18)
+    SBM_AD_CASE(19) SBM_AD_CASE(20) SBM_AD_CASE(21) SBM_AD_CASE(22) SBM_AD_CASE(23) SBM_AD_CASE(24)
+    SBM_AD_CASE(25) SBM_AD_CASE(26) SBM_AD_CASE(27) SBM_AD_CASE(28) SBM_AD_CASE(29) SBM_AD_CASE(30)
+    SBM_AD_CASE(31) SBM_AD_CASE(32)
+#undef SBM_AD_CASE
+  }
+  k_reduce_partials<<<1, 32 * nv, 0, s>>>(partial, nblk, nv, out, 0);
+  count_launches(2);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_axpy_norm(const double* V, size_t ldv, int nv, const double* h, double* w, size_t N,
+                             double* partial, double* out, cudaStream_t s) {
+  if (nv < 1 || nv > kMaxVec) return cudaErrorInvalidValue;
+  const int nblk = dot_blocks(N);
+  k_axpy_dot<0, true><<<nblk, kDotThreads, 0, s>>>(V, ldv, h, w, N, nv, partial);
+  k_reduce_partials<<<1, 32, 0, s>>>(partial, nblk, 1, out, 1);
   count_launches(2);
   return cudaGetLastError();
 }

@@ -163,20 +163,13 @@ __device__ __forceinline__ R sbm_face_terms(const LevelParams<R>& P, const Level
   return acc;
 }
 
-// y = A x  (MODE 0)  or  y = f - A x  (MODE 1).
-template <int D, int N1, typename TI, typename R, int MODE>
-__global__ void __launch_bounds__(256) k_apply(const __grid_constant__ LevelParams<R> P, const TI* __restrict__ x,
-                                               const R* __restrict__ f, R* __restrict__ y) {
+// (A x) at dof i of the block's cell slot c (cell a) on one level; every thread of the block calls
+// this (it contains barriers).  Stages the block's cells and their face neighbours in shared memory.
+template <int D, int N1, typename TI, typename R>
+__device__ __forceinline__ R apply_dof(const LevelParams<R>& P, const LevelConsts<R>& C, const TI* __restrict__ x,
+                                       int c, int i, int a, bool valid, R* sU, R* sN, R* sA, R* sB, R* sE) {
   using Dm = Dims<D, N1>;
-  constexpr int NP = Dm::NP, NQ = Dm::NQ, NS = Dm::NS, CPB = Dm::CPB;
-  __shared__ LevelConsts<R> C;
-  __shared__ R sU[CPB * NP];
-  __shared__ R sN[CPB * NS * NP];
-  __shared__ R sA[CPB * NQ], sB[CPB * NQ], sE[CPB * NQ];
-  load_consts(P.k, C);
-  const int c = threadIdx.x / NP, i = threadIdx.x - c * NP;
-  const int a = blockIdx.x * CPB + c;
-  const bool valid = threadIdx.x < CPB * NP && a < P.n_act;
+  constexpr int NP = Dm::NP, NS = Dm::NS;
   int nb[NS];
 #pragma unroll
   for (int s = 0; s < NS; ++s) nb[s] = -1;
@@ -219,10 +212,71 @@ __global__ void __launch_bounds__(256) k_apply(const __grid_constant__ LevelPara
 #pragma unroll
   for (int s = 0; s < NS; ++s) smask |= (nb[s] < 0 ? 1u : 0u) << s;
   if (__syncthreads_or(bidx >= 0)) acc += sbm_face_terms<D, N1, R>(P, C, bidx, smask, c, i, ii, sU, sA, sB, sE);
+  return P.hscale * acc;
+}
+
+// y = A x  (MODE 0)  or  y = f - A x  (MODE 1).
+template <int D, int N1, typename TI, typename R, int MODE>
+__global__ void __launch_bounds__(256) k_apply(const __grid_constant__ LevelParams<R> P, const TI* __restrict__ x,
+                                               const R* __restrict__ f, R* __restrict__ y) {
+  using Dm = Dims<D, N1>;
+  constexpr int NP = Dm::NP, NQ = Dm::NQ, NS = Dm::NS, CPB = Dm::CPB;
+  __shared__ LevelConsts<R> C;
+  __shared__ R sU[CPB * NP];
+  __shared__ R sN[CPB * NS * NP];
+  __shared__ R sA[CPB * NQ], sB[CPB * NQ], sE[CPB * NQ];
+  load_consts(P.k, C);
+  const int c = threadIdx.x / NP, i = threadIdx.x - c * NP;
+  const int a = blockIdx.x * CPB + c;
+  const bool valid = threadIdx.x < CPB * NP && a < P.n_act;
+  R v = apply_dof<D, N1, TI, R>(P, C, x, c, i, a, valid, sU, sN, sA, sB, sE);
   if (valid) {
-    R v = P.hscale * acc;
     if (MODE == 1) v = f[(size_t)a * NP + i] - v;
     y[(size_t)a * NP + i] = v;
+  }
+}
+
+// Residual and p-restriction fused (Eqs. 11, 18; same mesh, degree N1-1 -> NC-1):
+//   rc_K = (Pp^T (x) Pp^T) (f - A u)_K, the residual kept in shared memory.
+template <int D, int N1, int NC, typename R>
+__global__ void __launch_bounds__(256) k_resid_restrict_p(const __grid_constant__ LevelParams<R> P,
+                                                          const __grid_constant__ TransferParams<R> T,
+                                                          const R* __restrict__ u, const R* __restrict__ f,
+                                                          R* __restrict__ rc) {
+  using Dm = Dims<D, N1>;
+  constexpr int NP = Dm::NP, NQ = Dm::NQ, NS = Dm::NS, CPB = Dm::CPB;
+  constexpr int NPC = D == 2 ? NC * NC : NC * NC * NC;
+  __shared__ LevelConsts<R> C;
+  __shared__ R sU[CPB * NP];
+  __shared__ R sN[CPB * NS * NP];
+  __shared__ R sA[CPB * NQ], sB[CPB * NQ], sE[CPB * NQ];
+  __shared__ R sPp[N1 * NC];
+  load_consts(P.k, C);
+  for (int q = threadIdx.x; q < N1 * NC; q += blockDim.x) sPp[q] = T.Pp[q];
+  const int c = threadIdx.x / NP, i = threadIdx.x - c * NP;
+  const int a = blockIdx.x * CPB + c;
+  const bool valid = threadIdx.x < CPB * NP && a < P.n_act;
+  R v = apply_dof<D, N1, R, R>(P, C, u, c, i, a, valid, sU, sN, sA, sB, sE);
+  __syncthreads();                                   // sU is reused for the residual
+  sU[c * NP + i] = valid ? f[(size_t)a * NP + i] - v : R(0);
+  __syncthreads();
+  if (valid && i < NPC) {
+    const int j0 = i % NC, j1 = (i / NC) % NC, j2 = D == 3 ? i / (NC * NC) : 0;
+    const R* r = sU + c * NP;
+    R s2 = 0;
+#pragma unroll
+    for (int i2 = 0; i2 < (D == 3 ? N1 : 1); ++i2) {
+      R s1 = 0;
+#pragma unroll
+      for (int i1 = 0; i1 < N1; ++i1) {
+        R s0 = 0;
+#pragma unroll
+        for (int i0 = 0; i0 < N1; ++i0) s0 += sPp[i0 * NC + j0] * r[i0 + N1 * i1 + N1 * N1 * i2];
+        s1 += sPp[i1 * NC + j1] * s0;
+      }
+      s2 += (D == 3 ? sPp[i2 * NC + j2] : R(1)) * s1;
+    }
+    rc[(size_t)a * NPC + i] = s2;
   }
 }
 
@@ -458,6 +512,7 @@ template <typename TI, typename R>
 cudaError_t launch_apply(int dim, int p, const LevelParams<R>& P, const TI* x, const R* f, R* y, int mode,
                          cudaStream_t s) {
   if (P.n_act == 0) return cudaSuccess;
+  if (cell_kernels(dim, p)) return launch_apply_cell<TI, R>(dim, p, P, x, f, y, mode, s);
 #define SBM_APPLY(D, N1)                                                                 \
   {                                                                                      \
     using Dm = Dims<D, N1>;                                                              \
@@ -474,6 +529,7 @@ cudaError_t launch_apply(int dim, int p, const LevelParams<R>& P, const TI* x, c
 template <typename R>
 cudaError_t launch_smooth(int dim, int p, const LevelParams<R>& P, int reverse, int zero_start, const R* f, R* u,
                           cudaStream_t s) {
+  if (cell_kernels(dim, p)) return launch_smooth_cell<R>(dim, p, P, reverse, zero_start, f, u, s);
   if (reverse) zero_start = 0;
   const int ncol = 1 << dim;
   for (int q = 0; q < ncol; ++q) {
@@ -506,6 +562,32 @@ cudaError_t launch_smooth(int dim, int p, const LevelParams<R>& P, int reverse, 
     else if (dim == 3 && pf == 3 && pc == 2) { MACRO(3, 4, 3); }    \
     else return cudaErrorInvalidValue;                              \
   } while (0)
+
+template <typename R>
+cudaError_t launch_resid_restrict_p(int dim, int pf, const LevelParams<R>& P, const TransferParams<R>& T, const R* u,
+                                   const R* f, R* rc, cudaStream_t s) {
+  if (P.n_act == 0) return cudaSuccess;
+  if (cell_kernels(dim, pf)) return launch_resid_restrict_p_cell<R>(dim, pf, P, T, u, f, rc, s);
+#define SBM_RRP(D, N1, NC)                                                                         \
+  {                                                                                                \
+    using Dm = Dims<D, N1>;                                                                        \
+    k_resid_restrict_p<D, N1, NC, R><<<ceil_div(P.n_act, Dm::CPB), Dm::NT, 0, s>>>(P, T, u, f, rc); \
+    count_launches();                                                                              \
+  }
+  if (dim == 2 && pf == 2) { SBM_RRP(2, 3, 2); }
+  else if (dim == 2 && pf == 3) { SBM_RRP(2, 4, 3); }
+  else if (dim == 3 && pf == 2) { SBM_RRP(3, 3, 2); }
+  else if (dim == 3 && pf == 3) { SBM_RRP(3, 4, 3); }
+  else return cudaErrorInvalidValue;
+#undef SBM_RRP
+  return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t launch_resid_restrict_h(int dim, const LevelParams<R>& P, const TransferParams<R>& T, const R* u,
+                                   const R* f, R* rc, cudaStream_t s) {
+  return launch_resid_restrict_h_cell<R>(dim, P, T, u, f, rc, s);   // h-levels have p = 1
+}
 
 template <typename R>
 cudaError_t launch_restrict(int dim, int pf, int pc, const TransferParams<R>& T, const R* rf, R* rc, cudaStream_t s) {
@@ -553,6 +635,15 @@ template cudaError_t launch_smooth<double>(int, int, const LevelParams<double>&,
                                            cudaStream_t);
 template cudaError_t launch_smooth<float>(int, int, const LevelParams<float>&, int, int, const float*, float*,
                                           cudaStream_t);
+template cudaError_t launch_resid_restrict_p<double>(int, int, const LevelParams<double>&,
+                                                     const TransferParams<double>&, const double*, const double*,
+                                                     double*, cudaStream_t);
+template cudaError_t launch_resid_restrict_p<float>(int, int, const LevelParams<float>&, const TransferParams<float>&,
+                                                    const float*, const float*, float*, cudaStream_t);
+template cudaError_t launch_resid_restrict_h<double>(int, const LevelParams<double>&, const TransferParams<double>&,
+                                                     const double*, const double*, double*, cudaStream_t);
+template cudaError_t launch_resid_restrict_h<float>(int, const LevelParams<float>&, const TransferParams<float>&,
+                                                    const float*, const float*, float*, cudaStream_t);
 template cudaError_t launch_restrict<double>(int, int, int, const TransferParams<double>&, const double*, double*,
                                              cudaStream_t);
 template cudaError_t launch_restrict<float>(int, int, int, const TransferParams<float>&, const float*, float*,

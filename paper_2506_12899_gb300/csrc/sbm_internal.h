@@ -50,6 +50,8 @@ struct HostLevel {
   double L[4][kMaxN1 * kMaxN1] = {}; // self 1D matrices by neighbour mask (left active) + 2*(right active)
   double Bmp[kMaxN1 * kMaxN1] = {};  // coupling to the right neighbour (this cell is K-)
   double Bpm[kMaxN1 * kMaxN1] = {};  // coupling to the left neighbour (this cell is K+)
+  double Bmm[kMaxN1 * kMaxN1] = {};  // own half of the right interior face (this cell is K-)
+  double Bpp[kMaxN1 * kMaxN1] = {};  // own half of the left interior face (this cell is K+)
   double S[kMaxN1 * kMaxN1] = {}, lam[kMaxN1] = {};   // W-orthonormal eigenvectors / values of L[3]
   std::vector<double> coarse_inv;   // [N*N] on the coarsest level only
   int n_dof() const { return n_act * np; }
@@ -80,6 +82,8 @@ template <typename R>
 struct LevelConsts {
   R L[4][kMaxN1 * kMaxN1];          // self matrices by neighbour mask
   R Bmp[kMaxN1 * kMaxN1], Bpm[kMaxN1 * kMaxN1];
+  R Kh[kMaxN1 * kMaxN1];            // volume stiffness alone
+  R Bmm[kMaxN1 * kMaxN1], Bpp[kMaxN1 * kMaxN1];   // own halves of the right / left interior face
   R Dm[kMaxN1 * kMaxN1];
   R S[kMaxN1 * kMaxN1];             // fast-diagonalisation eigenvectors (columns)
   R w[kMaxN1], e0[kMaxN1], e1[kMaxN1], d0[kMaxN1], d1[kMaxN1];
@@ -110,6 +114,16 @@ struct TransferParams {
   const int* children;             // coarse [2^d][n_act_c]
   R Ph[2][kMaxN1 * kMaxN1];        // h: Ph[o][i*nc + j] = l^c_j((o + x^f_i)/2)
   R Pp[kMaxN1 * kMaxN1];           // p: Pp[i*nc + j] = l^c_j(x^f_i)
+};
+
+// One level of the cluster V-cycle tail (device memory): parameters, the transfer to the next
+// coarser level, and the level's work vectors.
+template <typename R>
+struct TailLevel {
+  LevelParams<R> P;
+  TransferParams<R> T;
+  R* z;
+  R* rhs;
 };
 
 }  // namespace sbm

@@ -773,6 +773,10 @@ HostLevel build_level(const sbm_setup_desc& d, int n, int p) {
   for (int mask = 0; mask < 4; ++mask)
     for (int ij = 0; ij < n1 * n1; ++ij)
       L.L[mask][ij] = B.Khat[ij] + ((mask & 2) ? Bmm[ij] : 0.0) + ((mask & 1) ? Bpp[ij] : 0.0);
+  for (int ij = 0; ij < n1 * n1; ++ij) {
+    L.Bmm[ij] = Bmm[ij];
+    L.Bpp[ij] = Bpp[ij];
+  }
 
   // fast diagonalisation of the interior block: L[3] s = lambda W s
   {
