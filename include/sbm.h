@@ -194,6 +194,22 @@ int sbm_vcycle(void* ctx, int dtype, const void* r_dev, void* z_dev);
 int sbm_dots(void* ctx, const double* V_dev, long long ldv, int nv, const double* w_dev, long long n,
              double* out_dev);
 
+/* sbm_dots without any allocation, for callers that cannot call cudaMalloc: for example a
+ * process whose caching allocator has already reserved the device memory (a cudaMalloc would
+ * fail), or a latency-critical loop that cannot accept the device-wide synchronisation a
+ * cudaMalloc may cause.  It needs no context: out[k] = sum_i V[k*ldv + i] w[i] for k < nv,
+ * computed by the same kernels and in the same order as sbm_dots, on `stream` (a cudaStream_t,
+ * NULL for the legacy default stream, current device).  The per-block partial sums live in a
+ * file-scope __device__ array of 608 x 32 doubles (152 KiB) that every GPU loading the library
+ * holds until the process exits.  The first call on a device looks up that array's device
+ * address (cudaGetSymbolAddress) and should come before any stream capture.  Every call reuses
+ * the same array: each call overwrites the partial sums it reads, so nothing carries over, but
+ * calls that overlap on the GPU (other streams, other host threads) race on the array.
+ * Errors: SBM_ERR_ARG for null pointers, nv outside 1..32, n < 0 or ldv < n; SBM_ERR_CUDA if
+ * the address lookup or the launch fails.  The paper has no counterpart to this entry point. */
+int sbm_dots_noalloc(const double* V_dev, long long ldv, int nv, const double* w_dev, long long n,
+                     double* out_dev, void* stream);
+
 /* Solve A x = b by FGMRES(restart), right-preconditioned by one V-cycle in the precision of
  * sbm_setup_desc.precision; Arnoldi, Gram-Schmidt (two classical passes), the update of x and
  * the true residual are FP64.  x_dev holds the initial guess on entry.  Stops when the

@@ -28,7 +28,8 @@ ERRORS = {-1: "SBM_ERR_ARG", -2: "SBM_ERR_CUDA", -3: "SBM_ERR_SINGULAR_BLOCK", -
 # exported C symbols (checked by the tests against include/sbm.h)
 SYMBOLS = ("sbm_setup", "sbm_setup_host", "sbm_host_apply", "sbm_host_rhs", "sbm_destroy", "sbm_last_error", "sbm_kernel_launches", "sbm_num_levels", "sbm_info", "sbm_layout",
            "sbm_export_geometry", "sbm_rhs", "sbm_apply", "sbm_residual", "sbm_smooth", "sbm_restrict",
-           "sbm_prolong_add", "sbm_coarse_solve", "sbm_vcycle", "sbm_dots", "sbm_solve", "sbm_solve_host")
+           "sbm_prolong_add", "sbm_coarse_solve", "sbm_vcycle", "sbm_dots", "sbm_dots_noalloc", "sbm_solve",
+           "sbm_solve_host")
 
 
 class SbmError(RuntimeError):
@@ -112,6 +113,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.sbm_coarse_solve.argtypes = [vp, ip, vp, vp]
     lib.sbm_vcycle.argtypes = [vp, ip, vp, vp]
     lib.sbm_dots.argtypes = [vp, vp, ctypes.c_longlong, ip, vp, ctypes.c_longlong, vp]
+    lib.sbm_dots_noalloc.argtypes = [vp, ctypes.c_longlong, ip, vp, ctypes.c_longlong, vp, vp]
     lib.sbm_solve.argtypes = [vp, vp, vp, dp, ip, ip, ctypes.POINTER(_SolveInfo)]
     lib.sbm_solve_host.argtypes = [vp, vp, vp, dp, ip, ip, ctypes.POINTER(_SolveInfo)]
     for name in SYMBOLS:

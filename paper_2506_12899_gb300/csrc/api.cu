@@ -569,6 +569,8 @@ int guarded(F&& f) {
 
 }  // namespace
 
+int record_error(int code, const std::string& msg) { return set_error(code, msg); }
+
 }  // namespace sbm
 
 using namespace sbm;

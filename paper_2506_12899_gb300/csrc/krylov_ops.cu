@@ -3,6 +3,8 @@
 // of per-block partials), multi-vector AXPY, scaling and precision casts.
 #include <cuda_runtime.h>
 
+#include <mutex>
+
 #include "ops.h"
 
 namespace sbm {
@@ -156,6 +158,14 @@ __global__ void k_hess_column(const double* h1, const double* h2, const double* 
   if (i == k) col[k] = hn[0];
 }
 
+// Scratch of sbm_dots_noalloc: room for the per-block partial sums of the largest grid the dot
+// kernel uses (dot_blocks() never exceeds kNoAllocBlocks) times 32 vectors: 152 KiB per device,
+// held by every GPU that loads the library until the process exits.
+constexpr int kNoAllocBlocks = 152 * 4;
+static __device__ __align__(256) double g_dots_scratch[kNoAllocBlocks * kMaxVec];
+std::mutex g_dots_scratch_mu;
+double* g_dots_scratch_dev[256] = {};      // device address of g_dots_scratch, per device ordinal
+
 unsigned grid_for(size_t N) {
   size_t g = (N + 255) / 256;
   return (unsigned)(g < 1 ? 1 : (g > 152 * 8 ? 152 * 8 : g));
@@ -251,6 +261,33 @@ cudaError_t launch_hess_column(const double* h1, const double* h2, const double*
   return cudaGetLastError();
 }
 
+int dots_noalloc(const double* V, long long ldv, int nv, const double* w, long long n, double* out,
+                 cudaStream_t stream) {
+  if (!V || !w || !out || nv < 1 || nv > kMaxVec || n < 0 || ldv < n)
+    return record_error(SBM_ERR_ARG, "sbm_dots_noalloc: need non-null pointers, 1 <= nv <= 32, 0 <= n <= ldv");
+  if (dot_blocks((size_t)n) > kNoAllocBlocks)
+    return record_error(SBM_ERR_ARG, "sbm_dots_noalloc: grid exceeds the static scratch");
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return record_error(SBM_ERR_CUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
+  if (dev < 0 || dev >= 256) return record_error(SBM_ERR_ARG, "sbm_dots_noalloc: device ordinal out of range");
+  double* scratch = nullptr;
+  {
+    std::lock_guard<std::mutex> lock(g_dots_scratch_mu);
+    if (!g_dots_scratch_dev[dev]) {          // first call on this device: resolve the array's address
+      void* p = nullptr;
+      e = cudaGetSymbolAddress(&p, g_dots_scratch);
+      if (e != cudaSuccess)
+        return record_error(SBM_ERR_CUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+      g_dots_scratch_dev[dev] = static_cast<double*>(p);
+    }
+    scratch = g_dots_scratch_dev[dev];
+  }
+  e = launch_multi_dot(V, (size_t)ldv, nv, w, (size_t)n, scratch, out, 0, stream);
+  if (e != cudaSuccess) return record_error(SBM_ERR_CUDA, std::string("sbm_dots_noalloc: ") + cudaGetErrorString(e));
+  return SBM_OK;
+}
+
 template cudaError_t launch_multi_axpy<double>(const double*, size_t, int, const double*, double, double*, size_t,
                                                cudaStream_t);
 template cudaError_t launch_multi_axpy<float>(const float*, size_t, int, const double*, double, double*, size_t,
@@ -259,3 +296,8 @@ template cudaError_t launch_cast<double, float>(const double*, float*, size_t, c
 template cudaError_t launch_cast<float, double>(const float*, double*, size_t, cudaStream_t);
 
 }  // namespace sbm
+
+extern "C" int sbm_dots_noalloc(const double* V_dev, long long ldv, int nv, const double* w_dev, long long n,
+                                double* out_dev, void* stream) {
+  return sbm::dots_noalloc(V_dev, ldv, nv, w_dev, n, out_dev, static_cast<cudaStream_t>(stream));
+}

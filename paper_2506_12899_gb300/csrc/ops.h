@@ -6,12 +6,20 @@
 #include "sbm_internal.h"
 
 #include <atomic>
+#include <string>
 
 namespace sbm {
 
 // Number of kernel launches issued by the library since it was loaded.
 extern std::atomic<long long> g_kernel_launches;
 inline void count_launches(long long n = 1) { g_kernel_launches.fetch_add(n, std::memory_order_relaxed); }
+
+// Sets the calling thread's sbm_last_error() message and returns code.
+int record_error(int code, const std::string& msg);
+
+// Body of sbm_dots_noalloc (static scratch, no allocation).
+int dots_noalloc(const double* V, long long ldv, int nv, const double* w, long long n, double* out,
+                 cudaStream_t stream);
 
 // Thread-per-cell kernels (cell_ops.cu) serve levels with (p+1)^d <= 16: 2D, and 3D with p = 1.
 bool cell_kernels(int dim, int p);
