@@ -85,8 +85,10 @@ typedef struct {
   double omega_p3;       /* relaxation on levels with p_l = 3                                    */
   int vf_samples;        /* kappa sub-samples per direction; 0: 16 in 2D, 8 in 3D                 */
   int precision;         /* V-cycle precision inside sbm_solve: SBM_F64 or SBM_F32                */
-  int tail_max_cells;    /* p = 1 h-levels with at most this many active cells run their whole    */
-                         /* V-cycle in one thread-block-cluster launch; 0: 40000; < 0: never      */
+  int tail_max_cells;    /* the p = 1 h-levels with at most this many active cells run their      */
+                         /* whole V-cycle in one thread-block-cluster launch; 0: 10000; < 0: never */
+  int cell_kernel_min_cells; /* launches over at least this many cells use one thread per cell   */
+                         /* when (p+1)^d <= 16; 0: always in FP32, never in FP64; < 0: never       */
   void* stream;          /* cudaStream_t for every launch of this context                        */
 } sbm_setup_desc;
 

@@ -171,11 +171,14 @@ class Hierarchy:
     def finest(self) -> Level:
         return self.levels[-1]
 
-    def vcycle(self, r: np.ndarray, level: int | None = None) -> np.ndarray:
+    def vcycle(self, r: np.ndarray, level: int | None = None, correction=None) -> np.ndarray:
         """One V-cycle z = M^{-1} r (Sec. 3): zero initial guess on every level, pre-smooth
         (forward colours), residual, restrict, recurse, prolongate and add, post-smooth
-        (reverse colours); the coarsest level is solved directly."""
-        l = len(self.levels) - 1 if level is None else level
+        (reverse colours); the coarsest level is solved directly.  `correction(level, z, r)`,
+        if given, updates z in place after the finest level's post-smoothing (the learned
+        boundary-cell correction)."""
+        top = len(self.levels) - 1
+        l = top if level is None else level
         lev = self.levels[l]
         if l == 0:
             return sla.lu_solve(self.coarse_lu, r)
@@ -187,4 +190,6 @@ class Hierarchy:
         z += self.P[l] @ zc
         for _ in range(self.prob.post_smooth):
             lev.coloured_sweep(z, r, reverse=True)
+        if correction is not None and l == top:
+            correction(lev, z, r)
         return z

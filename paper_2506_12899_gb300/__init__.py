@@ -52,7 +52,7 @@ class _Desc(ctypes.Structure):
                 ("extension", ctypes.c_int), ("coarsest_n", ctypes.c_int), ("pre_smooth", ctypes.c_int),
                 ("post_smooth", ctypes.c_int), ("omega", ctypes.c_double), ("omega_p3", ctypes.c_double),
                 ("vf_samples", ctypes.c_int), ("precision", ctypes.c_int), ("tail_max_cells", ctypes.c_int),
-                ("stream", ctypes.c_void_p)]
+                ("cell_kernel_min_cells", ctypes.c_int), ("stream", ctypes.c_void_p)]
 
 
 class _LevelInfo(ctypes.Structure):
@@ -133,7 +133,8 @@ def _check(code: int):
         raise SbmError(code, _lib.sbm_last_error().decode())
 
 
-def make_desc(prob, precision: int = SBM_F64, stream: int = 0, tail_max_cells: int = 0) -> _Desc:
+def make_desc(prob, precision: int = SBM_F64, stream: int = 0, tail_max_cells: int = 0,
+              cell_kernel_min_cells: int = 0) -> _Desc:
     d = _Desc()
     d.dim, d.n, d.p = prob.dim, prob.n, prob.p
     d.lo[:] = [float(v) for v in prob.lo]
@@ -150,14 +151,19 @@ def make_desc(prob, precision: int = SBM_F64, stream: int = 0, tail_max_cells: i
     d.pre_smooth, d.post_smooth, d.omega, d.omega_p3 = prob.pre_smooth, prob.post_smooth, prob.omega, prob.omega_p3
     d.vf_samples, d.precision, d.stream = prob.vf_samples, precision, stream
     d.tail_max_cells = tail_max_cells
+    d.cell_kernel_min_cells = cell_kernel_min_cells
     return d
 
 
 class Solver:
     """One DG-SBM problem set up on the current CUDA device (a libsbm context)."""
 
-    def __init__(self, prob, precision: str = "f64", stream=None, tail_max_cells: int = 0):
-        """tail_max_cells: small p = 1 levels run as one cluster launch (0: default, < 0: never)."""
+    def __init__(self, prob, precision: str = "f64", stream=None, tail_max_cells: int = 0,
+                 cell_kernel_min_cells: int = 0):
+        """tail_max_cells: p = 1 levels with at most that many cells run as one cluster launch
+        (0: library default, < 0: never).  cell_kernel_min_cells: launches over at least that many
+        cells use one thread per cell (0: library default, < 0: never, 1: always where
+        (p+1)^d <= 16)."""
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("libsbm needs a CUDA device; no CPU fallback exists")
@@ -166,7 +172,7 @@ class Solver:
         self.prob = prob
         self.precision = SBM_F32 if precision == "f32" else SBM_F64
         self.stream = stream if stream is not None else torch.cuda.current_stream()
-        desc = make_desc(prob, self.precision, self.stream.cuda_stream, tail_max_cells)
+        desc = make_desc(prob, self.precision, self.stream.cuda_stream, tail_max_cells, cell_kernel_min_cells)
         ctx = ctypes.c_void_p()
         _check(self.lib.sbm_setup(ctypes.byref(desc), ctypes.byref(ctx)))
         self.ctx = ctx

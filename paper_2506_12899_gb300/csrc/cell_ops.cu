@@ -527,7 +527,7 @@ cudaError_t launch_smooth_cell(int dim, int p, const LevelParams<R>& P, int reve
                                R* u, cudaStream_t s) {
   if (reverse) zero_start = 0;
   const int ncol = 1 << dim;
-  for (int q = 0; q < ncol; ++q) {
+  for (int q = 0; q < ncol; ++q) {   // (the launcher in level_ops.cu chose this path for the level)
     const int col = reverse ? ncol - 1 - q : q;
     const int cs = P.colour_start[col], ce = P.colour_start[col + 1], nbnd = P.colour_nbnd[col];
     const int nblk_b = (int)cdiv(nbnd, kCellThreads), nblk_i = (int)cdiv(ce - cs - nbnd, kCellThreads);

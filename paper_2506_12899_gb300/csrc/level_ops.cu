@@ -280,6 +280,64 @@ __global__ void __launch_bounds__(256) k_resid_restrict_p(const __grid_constant_
   }
 }
 
+// Residual and h-restriction fused (Eqs. 11, 18; p = 1 on both meshes): a block takes CPB / 2^d
+// coarse cells; block slot c = 2^d * (coarse cell) + o holds child o (o = child bits = colour of
+// the fine cell).  The children's residuals f - A u stay in shared memory (0 for inactive
+// children) and rc_C = sum_o (Ph[o_0] (x) Ph[o_1] ...)^T r_child(o).
+template <int D, typename R>
+__global__ void __launch_bounds__(256) k_resid_restrict_h(const __grid_constant__ LevelParams<R> P,
+                                                          const __grid_constant__ TransferParams<R> T,
+                                                          const R* __restrict__ u, const R* __restrict__ f,
+                                                          R* __restrict__ rc) {
+  using Dm = Dims<D, 2>;
+  constexpr int NP = Dm::NP, NQ = Dm::NQ, NS = Dm::NS, CPB = Dm::CPB;
+  constexpr int NCH = 1 << D, CPC = CPB / NCH;       // children per coarse cell, coarse cells per block
+  __shared__ LevelConsts<R> C;
+  __shared__ R sU[CPB * NP];
+  __shared__ R sN[CPB * NS * NP];
+  __shared__ R sA[CPB * NQ], sB[CPB * NQ], sE[CPB * NQ];
+  __shared__ R sPh[2][4];
+  load_consts(P.k, C);
+  if (threadIdx.x < 8) sPh[threadIdx.x >> 2][threadIdx.x & 3] = T.Ph[threadIdx.x >> 2][threadIdx.x & 3];
+  const int c = threadIdx.x / NP, i = threadIdx.x - c * NP;
+  const int cc = blockIdx.x * CPC + c / NCH, o = c % NCH;
+  const int a = (threadIdx.x < CPB * NP && cc < T.n_act_c) ? T.children[(size_t)o * T.n_act_c + cc] : -1;
+  const bool valid = a >= 0;
+  R v = apply_dof<D, 2, R, R>(P, C, u, c, i, a, valid, sU, sN, sA, sB, sE);
+  __syncthreads();                                   // sU is reused for the residuals
+  sU[c * NP + i] = valid ? f[(size_t)a * NP + i] - v : R(0);
+  __syncthreads();
+  const int t = threadIdx.x;
+  if (t < CPC * NP) {                               // coarse dof j of coarse cell t / NP (NPC = NP for p = 1)
+    const int ccl = t / NP, j = t % NP;
+    const int cc2 = blockIdx.x * CPC + ccl;
+    if (cc2 < T.n_act_c) {
+      const int j0 = j & 1, j1 = (j >> 1) & 1, j2 = (j >> 2) & 1;
+      R sum = 0;
+#pragma unroll
+      for (int oo = 0; oo < NCH; ++oo) {
+        const R* r = sU + (ccl * NCH + oo) * NP;
+        const R* P0 = sPh[oo & 1];
+        const R* P1 = sPh[(oo >> 1) & 1];
+        const R* P2 = sPh[(oo >> 2) & 1];
+        R s2 = 0;
+#pragma unroll
+        for (int i2 = 0; i2 < (D == 3 ? 2 : 1); ++i2) {
+          R s1 = 0;
+#pragma unroll
+          for (int i1 = 0; i1 < 2; ++i1) {
+            const R s0 = P0[0 * 2 + j0] * r[0 + 2 * i1 + 4 * i2] + P0[1 * 2 + j0] * r[1 + 2 * i1 + 4 * i2];
+            s1 += P1[i1 * 2 + j1] * s0;
+          }
+          s2 += (D == 3 ? P2[i2 * 2 + j2] : R(1)) * s1;
+        }
+        sum += s2;
+      }
+      rc[(size_t)cc2 * NP + j] = sum;
+    }
+  }
+}
+
 // One colour of the block Gauss-Seidel sweep (Eq. 16): for each cell K of the colour,
 //   t_K = f_K - sum_{N != K} A_KN u_N  (interior-face couplings only; the SBM terms lie in A_KK),
 //   u_K <- (1 - omega) u_K + omega A_KK^{-1} t_K,
@@ -512,7 +570,8 @@ template <typename TI, typename R>
 cudaError_t launch_apply(int dim, int p, const LevelParams<R>& P, const TI* x, const R* f, R* y, int mode,
                          cudaStream_t s) {
   if (P.n_act == 0) return cudaSuccess;
-  if (cell_kernels(dim, p)) return launch_apply_cell<TI, R>(dim, p, P, x, f, y, mode, s);
+  if (cell_kernels(dim, p) && P.cell_min > 0 && P.n_act >= P.cell_min)
+    return launch_apply_cell<TI, R>(dim, p, P, x, f, y, mode, s);
 #define SBM_APPLY(D, N1)                                                                 \
   {                                                                                      \
     using Dm = Dims<D, N1>;                                                              \
@@ -529,7 +588,8 @@ cudaError_t launch_apply(int dim, int p, const LevelParams<R>& P, const TI* x, c
 template <typename R>
 cudaError_t launch_smooth(int dim, int p, const LevelParams<R>& P, int reverse, int zero_start, const R* f, R* u,
                           cudaStream_t s) {
-  if (cell_kernels(dim, p)) return launch_smooth_cell<R>(dim, p, P, reverse, zero_start, f, u, s);
+  if (cell_kernels(dim, p) && P.cell_min > 0 && P.n_act >= (1 << dim) * P.cell_min)
+    return launch_smooth_cell<R>(dim, p, P, reverse, zero_start, f, u, s);
   if (reverse) zero_start = 0;
   const int ncol = 1 << dim;
   for (int q = 0; q < ncol; ++q) {
@@ -567,7 +627,8 @@ template <typename R>
 cudaError_t launch_resid_restrict_p(int dim, int pf, const LevelParams<R>& P, const TransferParams<R>& T, const R* u,
                                    const R* f, R* rc, cudaStream_t s) {
   if (P.n_act == 0) return cudaSuccess;
-  if (cell_kernels(dim, pf)) return launch_resid_restrict_p_cell<R>(dim, pf, P, T, u, f, rc, s);
+  if (cell_kernels(dim, pf) && P.cell_min > 0 && P.n_act >= P.cell_min)
+    return launch_resid_restrict_p_cell<R>(dim, pf, P, T, u, f, rc, s);
 #define SBM_RRP(D, N1, NC)                                                                         \
   {                                                                                                \
     using Dm = Dims<D, N1>;                                                                        \
@@ -586,7 +647,19 @@ cudaError_t launch_resid_restrict_p(int dim, int pf, const LevelParams<R>& P, co
 template <typename R>
 cudaError_t launch_resid_restrict_h(int dim, const LevelParams<R>& P, const TransferParams<R>& T, const R* u,
                                    const R* f, R* rc, cudaStream_t s) {
-  return launch_resid_restrict_h_cell<R>(dim, P, T, u, f, rc, s);   // h-levels have p = 1
+  if (T.n_act_c == 0) return cudaSuccess;
+  if (P.cell_min > 0 && T.n_act_f >= P.cell_min) return launch_resid_restrict_h_cell<R>(dim, P, T, u, f, rc, s);
+  if (dim == 2) {
+    using Dm = Dims<2, 2>;
+    k_resid_restrict_h<2, R><<<ceil_div(T.n_act_c, Dm::CPB / 4), Dm::NT, 0, s>>>(P, T, u, f, rc);
+  } else if (dim == 3) {
+    using Dm = Dims<3, 2>;
+    k_resid_restrict_h<3, R><<<ceil_div(T.n_act_c, Dm::CPB / 8), Dm::NT, 0, s>>>(P, T, u, f, rc);
+  } else {
+    return cudaErrorInvalidValue;
+  }
+  count_launches();
+  return cudaGetLastError();
 }
 
 template <typename R>

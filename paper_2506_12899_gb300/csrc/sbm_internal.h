@@ -102,6 +102,7 @@ struct LevelParams {
   R hscale;                        // h^(dim-2)
   R sigG, alpha, omega;
   int extension;
+  int cell_min;                    // launches over >= cell_min cells use thread-per-cell kernels (0: never)
   LevelConsts<R> k;
 };
 

@@ -33,10 +33,11 @@ def _dof_map(solver, lev, level):
 class Pair:
     """A GPU solver and the oracle hierarchy of the same problem, with dof maps per level."""
 
-    def __init__(self, prob, precision="f64"):
+    def __init__(self, prob, precision="f64", tail_max_cells=0, cell_kernel_min_cells=0):
         import paper_2506_12899_gb300 as S
         self.prob = prob
-        self.gpu = S.Solver(prob, precision)
+        self.gpu = S.Solver(prob, precision, tail_max_cells=tail_max_cells,
+                            cell_kernel_min_cells=cell_kernel_min_cells)
         self.H = MG.Hierarchy(prob)
         assert self.gpu.num_levels == len(self.H.levels)
         self.maps = [_dof_map(self.gpu, lev, l) for l, lev in enumerate(self.H.levels)]
@@ -64,10 +65,12 @@ CASES = {
 _pairs = {}
 
 
-def pair(name, precision="f64"):
-    key = (name, precision)
+def pair(name, precision="f64", tail=False, cell=0):
+    """tail: run the small p = 1 levels as one cluster launch; cell: thread-per-cell kernels
+    (0: size-based default, 1: always where (p+1)^d <= 16, -1: never)."""
+    key = (name, precision, tail, cell)
     if key not in _pairs:
-        _pairs[key] = Pair(CASES[name], precision)
+        _pairs[key] = Pair(CASES[name], precision, 40000 if tail else -1, cell)
     return _pairs[key]
 
 
@@ -109,6 +112,32 @@ def test_apply_unit_columns_tiny(name):
         e[j] = 1.0
         y = P.to_oracle(P.gpu.apply(P.to_gpu(e, 0), level=0), 0)
         assert np.abs(y - A[:, j]).max() <= 1e-12 * np.abs(A).max()
+
+
+@pytest.mark.parametrize("cell", [1, -1], ids=["thread_per_cell", "thread_per_dof"])
+@pytest.mark.parametrize("name", ["disk2d_p1_n32", "star2d_p2_n32", "star2d_p3_n16", "sphere3d_p1_n8"])
+def test_kernel_variants(name, cell):
+    """Both kernel families (one thread per cell, one thread per dof) for the operator, the
+    smoother and the V-cycle, in FP64 and FP32, against the oracle."""
+    P = pair(name, cell=cell)
+    L = len(P.H.levels) - 1
+    lev = P.H.finest
+    x = W.random_vector(lev.N, 3)
+    assert rel_max(P.to_oracle(P.gpu.apply(P.to_gpu(x, L)), L), lev.A @ x) <= 1e-12
+    scale = np.abs(abs(lev.A) @ np.abs(x)).max()
+    y32 = P.to_oracle(P.gpu.apply(P.to_gpu(x, L, torch.float32)), L)
+    assert np.abs(y32 - lev.A @ x).max() <= 2e-6 * scale
+    f, u0 = W.random_vector(lev.N, 4), W.random_vector(lev.N, 5)
+    uo = lev.coloured_sweep(u0.copy(), f)
+    ug = P.to_oracle(P.gpu.smooth(P.to_gpu(f, L), P.to_gpu(u0, L)), L)
+    assert rel_max(ug, uo) <= block_tol([lev])
+    ug32 = P.to_oracle(P.gpu.smooth(P.to_gpu(f, L, torch.float32), P.to_gpu(u0, L, torch.float32)), L)
+    assert rel_max(ug32, uo) <= 2e-4
+    zo = P.H.vcycle(f)
+    z = P.to_oracle(P.gpu.vcycle(P.to_gpu(f, L)), L)
+    assert np.linalg.norm(z - zo) <= block_tol(P.H.levels[1:] or P.H.levels) * np.linalg.norm(zo)
+    z32 = P.to_oracle(P.gpu.vcycle(P.to_gpu(f, L, torch.float32)), L)
+    assert np.linalg.norm(z32 - zo) <= 1e-4 * np.linalg.norm(zo)
 
 
 @pytest.mark.parametrize("name", ["disk2d_p1_n32", "sphere3d_p2_n8", "ellipsoid3d_p3_n12"])
@@ -165,10 +194,12 @@ def test_coarse_solve(name):
     assert rel_max(e, x) <= 1e-11
 
 
+@pytest.mark.parametrize("tail", [True, False], ids=["cluster_tail", "per_level_launches"])
 @pytest.mark.parametrize("name", list(CASES))
-def test_vcycle(name):
-    """One V-cycle (Sec. 3) equals the oracle's; FP32 V-cycle within its rounding bound."""
-    P = pair(name)
+def test_vcycle(name, tail):
+    """One V-cycle (Sec. 3) equals the oracle's; FP32 V-cycle within its rounding bound.  Run with
+    the small p = 1 levels in one thread-block-cluster launch and with one launch per phase."""
+    P = pair(name, tail=tail)
     L = len(P.H.levels) - 1
     r = W.random_vector(P.H.finest.N, 21)
     zo = P.H.vcycle(r)
@@ -235,6 +266,40 @@ def test_gram_schmidt_dots(n, nv):
     bound = n * 2.2e-16 * (np.abs(V) @ np.abs(w))
     assert np.all(np.abs(out - V @ w) <= bound + 1e-300)
     assert np.array_equal(out, P.gpu.dots(Vt, wt).cpu().numpy())
+
+
+def test_cluster_tail_is_one_launch():
+    """On a hierarchy of small p = 1 levels the whole V-cycle is one cluster launch; with the tail
+    disabled it is one launch per phase."""
+    import paper_2506_12899_gb300 as S
+    P, Q = pair("disk2d_p1_n32", tail=True), pair("disk2d_p1_n32", tail=False)
+    r = torch.tensor(W.random_vector(P.H.finest.N, 1), device="cuda")
+    for g, expect in ((P.gpu, 1), (Q.gpu, None)):
+        g.vcycle(r)
+        torch.cuda.synchronize()
+        n0 = S.kernel_launches()
+        g.vcycle(r)
+        torch.cuda.synchronize()
+        n = S.kernel_launches() - n0
+        if expect is not None:
+            assert n == expect
+        else:
+            assert n > 10
+
+
+@pytest.mark.parametrize("name", ["disk2d_p1_n32", "star2d_p2_n32", "sphere3d_p1_n8"])
+def test_fgmres_fp64_per_level_launches(name):
+    """FGMRES with the cluster tail disabled: same iteration count and solution as the oracle."""
+    P = pair(name, tail=False)
+    F = P.H.finest
+    L = len(P.H.levels) - 1
+    bo = F.disc.rhs()
+    xo, oi = K.fgmres(lambda v: F.A @ v, P.H.vcycle, bo, tol=1e-8, m=30, max_it=300)
+    b = P.gpu.rhs()
+    x = torch.zeros_like(b)
+    info = P.gpu.solve(b, x, tol=1e-8, restart=30, max_it=300)
+    assert info.converged and info.iterations == oi.iterations
+    assert np.linalg.norm(P.to_oracle(x, L) - xo) <= 1e-10 * np.linalg.norm(xo)
 
 
 def test_solve_host_buffers():

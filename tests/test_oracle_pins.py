@@ -329,3 +329,65 @@ def test_unpreconditioned_gmres_terminates_in_n_steps():
     # with m = 3 it restarts, and still converges
     x, info = K.fgmres(lambda v: A @ v, lambda v: v, b, tol=1e-10, m=3, max_it=500)
     assert info.converged and info.restarts > 1
+
+
+# ------------------------------------------------------------------ learned boundary correction
+def test_mlp_gradients_match_central_differences():
+    """Backward pass of the FP64 MLP against central finite differences of its loss."""
+    from oracle import learned as LR
+    rng = np.random.default_rng(0)
+    net = LR.MLP(7, 5, 3, seed=1)
+    for prm in net.params():
+        prm += 0.05 * rng.normal(size=prm.shape)      # nonzero biases, no ties at ReLU kinks
+    X, T = rng.normal(size=(11, 7)), rng.normal(size=(11, 3))
+    grads = net.backward(net.forward(X), T)
+    for prm, g in zip(net.params(), grads):
+        flat = prm.reshape(-1)
+        for k in range(flat.size):
+            old = flat[k]
+            flat[k] = old + 1e-6
+            lp = net.loss(net.forward(X), T)
+            flat[k] = old - 1e-6
+            lm = net.loss(net.forward(X), T)
+            flat[k] = old
+            fd = (lp - lm) / 2e-6
+            assert abs(fd - g.reshape(-1)[k]) <= 1e-6 * max(1.0, abs(fd)), (k, fd, g.reshape(-1)[k])
+
+
+def test_mlp_forward_closed_form():
+    """Identity-like weights: y = relu(relu(x)) = relu(x) for a square network with zero biases."""
+    from oracle import learned as LR
+    net = LR.MLP(4, 4, 4)
+    net.W1, net.W2, net.W3 = np.eye(4), np.eye(4), np.eye(4)
+    x = np.array([[1.0, -2.0, 3.0, -0.5]])
+    assert np.array_equal(net.forward(x), np.array([[1.0, 0.0, 3.0, 0.0]]))
+
+
+def test_adam_first_step_is_sign_step():
+    """Adam's bias-corrected first step moves every parameter by lr in the direction -sign(g)."""
+    from oracle import learned as LR
+    p = [np.array([1.0, -1.0, 0.5])]
+    g = [np.array([3.0, -0.2, 1e-3])]
+    LR.adam_step(p, g, {}, lr=0.01, eps=1e-12)
+    assert np.allclose(p[0], [0.99, -0.99, 0.49], atol=1e-9)
+
+
+def test_learned_features_layout():
+    """Patch residual normalised to unit norm; shift and mask entries only on surrogate faces."""
+    from oracle import learned as LR
+    prob = W.star2d_p2(16, 1).replace(p=3)
+    lev = MG.Level(prob, 16, 3)
+    r = W.random_vector(lev.N, 5)
+    cells = lev.geom.boundary_cells()[:10]
+    X, s = LR.features(lev, r, cells)
+    nb, dim, nq = lev.nb, 2, 4
+    assert X.shape == (10, LR.feature_size(2, 3)) == (10, 9 * 16 + 4 * 4 * 2 + 1 + 4)
+    for row, a in enumerate(cells):
+        assert abs(np.linalg.norm(X[row, :9 * nb]) - 1.0) < 1e-12
+        assert np.allclose(X[row, 4 * nb:5 * nb] * s[row], r[a * nb:(a + 1) * nb])     # centre cell
+        mask = X[row, -4:]
+        d = X[row, 9 * nb:9 * nb + 4 * nq * dim].reshape(4, nq, dim)
+        slots = {2 * dr + sd for (aa, dr, sd) in lev.geom.faces if aa == a}
+        assert set(np.nonzero(mask)[0]) == slots
+        for slot in range(4):
+            assert (np.abs(d[slot]).max() > 0) == (slot in slots)
