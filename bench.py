@@ -8,6 +8,7 @@ FP32 V-cycle under FP64 FGMRES.  The FP64-V-cycle solve of the same workload is 
 it.  Prints one JSON line (rank 0).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+  python bench.py --profile solve|kernels [--profile-n N]   (fixed launches for ncu, no JSON)
 
 Under torchrun each rank solves its own seeded replica of the workload on its own GPU
 (replicas only: no data-path collective); the reported time is the max over ranks.
@@ -298,6 +299,41 @@ def run_ours(args) -> dict | None:
     return out
 
 
+def run_profile(args) -> None:
+    """Fixed launch sequences for ncu captures (numbers printed under ncu are not bench values).
+    solve:   one warm-up and one FP32-V-cycle FGMRES solve of --workload; prints how many of the
+             library's kernels the warm-up launched (the ncu skip count) and how many the solve did.
+    kernels: 2D p=2 star at --profile-n^2 cells (vectors larger than L2): one FP32 operator apply,
+             one finest-level smoother sweep (2^d colour launches) and one V-cycle."""
+    import torch
+    import paper_2506_12899_gb300 as S
+    if args.profile == "solve":
+        g = S.Solver(WORKLOADS[args.workload](0), "f32")
+        b = g.rhs()
+        x = torch.zeros_like(b)
+        l0 = S.kernel_launches()
+        g.solve(b, x, tol=TOL, restart=RESTART, max_it=MAX_IT)
+        l1 = S.kernel_launches()
+        x.zero_()
+        info = g.solve(b, x, tol=TOL, restart=RESTART, max_it=MAX_IT)
+        torch.cuda.synchronize()
+        print("WARM_LAUNCHES", l1 - l0, flush=True)
+        print("SOLVE_LAUNCHES", S.kernel_launches() - l1, flush=True)
+        print("ITERATIONS", info.iterations, "CONVERGED", info.converged, flush=True)
+    else:
+        g = S.Solver(W.star2d_p2(args.profile_n, 0), "f32")
+        N = g.n_dof()
+        gen = torch.Generator(device="cuda").manual_seed(0)
+        f = torch.rand(N, device="cuda", generator=gen)
+        u = torch.rand(N, device="cuda", generator=gen)
+        y = torch.empty_like(f)
+        g.apply(f, y)
+        g.smooth(f, u)
+        g.vcycle(f, y)
+        torch.cuda.synchronize()
+        print("N", N, "LEVELS", g.num_levels, flush=True)
+
+
 def run_reference(args) -> dict | None:
     """The reference arm: the CPU FP64 oracle on the host cores (no GPU)."""
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -348,7 +384,12 @@ def main():
     ap.add_argument("--workload", default="star2d_p2_n512", choices=sorted(WORKLOADS))
     ap.add_argument("--cpu-budget", type=float, default=15.0, help="seconds of oracle solve time to sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile", choices=["solve", "kernels"], help="fixed launches for an ncu capture")
+    ap.add_argument("--profile-n", type=int, default=2048, help="cells per direction for --profile kernels")
     args = ap.parse_args()
+    if args.profile:
+        run_profile(args)
+        return
     out = run_reference(args) if args.impl == "reference" else run_ours(args)
     if out is not None:
         print(json.dumps(out))
