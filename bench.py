@@ -140,6 +140,22 @@ def peaks():
         return 6800.0, "fallback"
 
 
+def committed_traffic(workload: str, kernel: str):
+    """dram__bytes_read.sum + dram__bytes_write.sum per launch of `kernel` on `workload` from the
+    committed ncu summary profiles/<kernel family>_<workload>_traffic.txt (one line
+    'traffic_bytes_per_launch <B>'), or None when there is none."""
+    name = kernel.split("<")[0]
+    path = os.path.join(ROOT, "profiles", f"{name}_{workload}_traffic.txt")
+    try:
+        with open(path) as fh:
+            for line in fh:
+                if line.startswith("traffic_bytes_per_launch"):
+                    return int(float(line.split()[1]))
+    except OSError:
+        pass
+    return None
+
+
 def event_time(torch, fn, reps, flush=None):
     """Mean device time (ms) of fn() over reps launches on the current stream."""
     s = torch.cuda.current_stream()
@@ -235,7 +251,9 @@ def run_ours(args) -> dict | None:
         t0 = time.perf_counter()
         s32.solve_host(bnp, xnp, tol=TOL, restart=RESTART, max_it=MAX_IT)
         e2e.append(1e3 * (time.perf_counter() - t0))
-    # ---- per-kernel rooflines (finest level, FP32 as in the V-cycle; FP64 operator as in FGMRES)
+    # ---- per-kernel rooflines, each kernel timed alone with CUDA events on the solver's stream
+    # after an L2 flush (finest level: FP32 as in the V-cycle; FP64 operator and Gram-Schmidt as in
+    # FGMRES).  Algorithmic bytes count every vector once; flops are the method's FMAs x 2.
     info = s32.info()
     nb = (info["p"] + 1) ** prob.dim
     r32 = torch.rand(N, device="cuda", dtype=torch.float32)
@@ -243,25 +261,42 @@ def run_ours(args) -> dict | None:
     y32 = torch.empty_like(r32)
     x64 = torch.rand(N, device="cuda", dtype=torch.float64)
     y64 = torch.empty_like(x64)
+    nv = 27                                      # Gram-Schmidt width at the last step of the bench solve
+    V64 = torch.rand((nv, N), device="cuda", dtype=torch.float64)
     geo_bytes = info["n_sface"] * (info["p"] + 1) ** (prob.dim - 1) * prob.dim
+    ncol = 2 ** prob.dim
     t_apply32 = event_time(torch, lambda: s32.apply(r32, y32), 20, flush)
     t_apply64 = event_time(torch, lambda: s64.apply(x64, y64), 20, flush)
-    t_smooth = event_time(torch, lambda: s32.smooth(r32, u32), 20, flush) / 2 ** prob.dim
-    bytes_apply32 = 2 * 4 * N + 4 * geo_bytes
-    bytes_apply64 = 2 * 8 * N + 8 * geo_bytes
-    bytes_smooth = (3 * 4 * N + info["n_boundary"] * nb * nb * 4 + 4 * geo_bytes) / 2 ** prob.dim
+    t_smooth = event_time(torch, lambda: s32.smooth(r32, u32), 20, flush) / ncol
+    t_dots = event_time(torch, lambda: s64.dots(V64, x64), 20, flush)
     hbm, src = peaks()
+    fp64_tflops = 152 * 2.07e9 * 2 * 2 / 1e12    # SMs x max clock x 2 FP64 FMA/clk/SM x 2 flop
     kernels = {
-        "k_smooth (FP32, finest level, one colour)": (bytes_smooth, t_smooth),
-        "k_apply (FP32, finest level)": (bytes_apply32, t_apply32),
-        "k_apply (FP64, finest level)": (bytes_apply64, t_apply64),
+        # one colour of the finest-level (p) block Gauss-Seidel sweep: f of the colour, u of the
+        # neighbouring colours, u written, dense inverses of the colour's boundary cells, face data
+        f"k_smooth_cell<{prob.dim},{info['p'] + 1},float> (finest level, one colour)":
+            ("hbm", (4 * N + info["n_boundary"] * nb * nb * 4 + 4 * geo_bytes) / ncol, t_smooth),
+        f"k_apply_cell<{prob.dim},{info['p'] + 1},float> (FP32 operator, finest level)":
+            ("hbm", 2 * 4 * N + 4 * geo_bytes, t_apply32),
+        f"k_apply<{prob.dim},{info['p'] + 1},double> (FP64 operator, finest level)":
+            ("hbm", 2 * 8 * N + 8 * geo_bytes, t_apply64),
+        # first Gram-Schmidt sweep h = V^T w at width 27, plus its partial-sum reduction
+        "k_multi_dot<27> (FP64 Gram-Schmidt sweep)": ("alu", 2 * nv * N, t_dots),
     }
-    rooflines = {k: {"bound": "hbm", "achieved": round(b_ / t_ / 1e6, 1), "peak": hbm, "unit": "GB/s",
-                     "frac": round(b_ / t_ / 1e6 / hbm, 3), "bytes_per_launch": int(b_), "ms_per_launch": t_}
-                 for k, (b_, t_) in kernels.items()}
-    dominant = "k_smooth (FP32, finest level, one colour)"
+    rooflines = {}
+    for k, (bound, amount, t_) in kernels.items():
+        if bound == "hbm":
+            ach = amount / t_ / 1e6
+            rooflines[k] = {"bound": "hbm", "achieved": round(ach, 1), "peak": hbm, "unit": "GB/s",
+                            "frac": round(ach / hbm, 3), "bytes_per_launch": int(amount), "ms_per_launch": t_}
+        else:
+            ach = amount / t_ / 1e9
+            rooflines[k] = {"bound": "alu", "achieved": round(ach, 4), "peak": round(fp64_tflops, 4),
+                            "unit": "TFLOP/s", "frac": round(ach / fp64_tflops, 3), "flops_per_launch": int(amount),
+                            "ms_per_launch": t_, "bytes_per_launch": 8 * (nv + 1) * N}
+    dominant = next(iter(kernels))
     roof = dict(rooflines[dominant])
-    roof.update(kernel=dominant, peak_source=src, traffic=None)
+    roof.update(kernel=dominant, peak_source=src, traffic=committed_traffic(args.workload, dominant))
     if rank != 0:
         return None
     cpu = finish_cpu_worker(cpu_proc) if cpu_proc is not None else None
@@ -280,8 +315,8 @@ def run_ours(args) -> dict | None:
                         "converged": all(i.converged for i in infos64)},
         "speedup_fp32_over_fp64_vcycle": round(statistics.mean(times64) / ms32, 3),
         "solves_per_s_total": round(world * args.steps / (total_ms / 1e3), 3),
-        "apply_gbs": {"fp32": rooflines["k_apply (FP32, finest level)"]["achieved"],
-                      "fp64": rooflines["k_apply (FP64, finest level)"]["achieved"]},
+        "apply_gbs": {"fp32": list(rooflines.values())[1]["achieved"],
+                      "fp64": list(rooflines.values())[2]["achieved"]},
         "clocks": clk,
         "e2e": {"value": round(statistics.mean(e2e), 4), "unit": "ms", "h2d_bytes_per_step": 8 * N,
                 "d2h_bytes_per_step": 8 * N},

@@ -86,7 +86,10 @@ typedef struct {
   int vf_samples;        /* kappa sub-samples per direction; 0: 16 in 2D, 8 in 3D                 */
   int precision;         /* V-cycle precision inside sbm_solve: SBM_F64 or SBM_F32                */
   int tail_max_cells;    /* the p = 1 h-levels with at most this many active cells run their      */
-                         /* whole V-cycle in one thread-block-cluster launch; 0: 10000; < 0: never */
+                         /* whole V-cycle in one thread-block-cluster launch with the level       */
+                         /* vectors in shared memory (the largest such level that fits starts    */
+                         /* it); 0: library default (none); < 0: never                            */
+  int tail_cluster_ctas; /* CTAs of that cluster: 1, 2, 4, 8 or 16; 0: 16, else 8                  */
   int cell_kernel_min_cells; /* launches over at least this many cells use one thread per cell   */
                          /* when (p+1)^d <= 16; 0: always in FP32, never in FP64; < 0: never       */
   void* stream;          /* cudaStream_t for every launch of this context                        */
@@ -111,6 +114,8 @@ typedef struct {
   double true_rel_residual; /* ||b - A x|| / ||b|| recomputed in FP64 at the end                  */
   double history[512];   /* |g_{j+1}| / ||b|| after each step (first 512)                        */
   double ms_total;       /* device time of the whole call (CUDA events)                          */
+  int learned;           /* 1 if the solve started with the learned correction attached and on   */
+  int learned_fallback;  /* 1 if the fallback rule switched it off during this solve             */
 } sbm_solve_info;
 
 /* Create a context: builds every level's geometry (Sec. 2.1, Sec. 4.2), element data, block
@@ -224,6 +229,73 @@ int sbm_solve(void* ctx, const double* b_dev, double* x_dev, double tol, int res
  * into x_host.  The copies are part of the call. */
 int sbm_solve_host(void* ctx, const double* b_host, double* x_host, double tol, int restart,
                    int max_it, sbm_solve_info* info);
+
+/* ---------------------------------------------------------------------------------------------
+ * Learned boundary-cell correction.  The paper has no learned component; this is a learned
+ * variant of the V-cycle smoother built on its method (the p = 3 smoother weakens near the
+ * surrogate boundary, Sec. 5.3).  After the finest level's post-smoothing every boundary cell K
+ * (a cell owning a surrogate face) gets u_K += scale * s_K * MLP(x_K), where
+ *   x_K = [ patch residual / s_K, d / h at every face point, kappa(K), surrogate-face mask ],
+ *   s_K = |patch residual|_2 (1 if zero),
+ * the patch being the 3^d cells K + o, o in {-1,0,1}^d (x fastest), their residual r - A u with
+ * zeros for inactive or missing cells; d / h is given per face slot s = 2 dir + side, face point
+ * t (first tangential dimension fastest) and component, zero on slots that are not surrogate
+ * faces.  F = 3^d (p+1)^d + 2d (p+1)^(d-1) d + 1 + 2d features.  The MLP is
+ * y = W3^T relu(W2^T relu(W1^T x + b1) + b2) + b3 with hidden width H and O = (p+1)^d
+ * outputs; FP32 master parameters, BF16 weights and activations on the tensor cores, FP32
+ * accumulation.  Parameters travel packed as FP32 [W1 (F x H, input-major) | b1 | W2 (H x H) |
+ * b2 | W3 (H x O) | b3].  An MLP handle is independent of a context and owned by the caller;
+ * it must outlive every context it is attached to.  All MLP calls run on the stream given at
+ * creation; the correction itself runs on the context's streams inside sbm_vcycle/sbm_solve.
+ * ------------------------------------------------------------------------------------------- */
+
+/* Create an MLP for dimension dim and degree p with hidden width `hidden` (8..1024): He-normal
+ * weights from a splitmix64/Box-Muller stream seeded by `seed`, zero biases.  `stream` is a
+ * cudaStream_t (NULL: legacy default stream).  SBM_ERR_ARG for a bad shape. */
+int sbm_mlp_create(int dim, int p, int hidden, unsigned long long seed, void* stream, void** out);
+void sbm_mlp_destroy(void* mlp);
+/* F features, Fpad (F rounded up to 32, the device row length), H, O and the packed parameter
+ * count. */
+int sbm_mlp_shape(const void* mlp, int* F, int* Fpad, int* H, int* O, long long* nparam);
+/* Host FP32 packed parameters in / out; setting them also resets the Adam state. */
+int sbm_mlp_set_params(void* mlp, const float* params_host);
+int sbm_mlp_get_params(const void* mlp, float* params_host);
+/* Y_dev[rows][O] = MLP(X_dev[rows][F]) (device FP32 buffers; X is rounded to BF16). */
+int sbm_mlp_forward(void* mlp, const float* X_dev, int rows, float* Y_dev);
+/* Gradient of the mean squared error mean((MLP(X) - T)^2) over the rows x O entries, in the
+ * packed layout (host), and the loss.  X_dev [rows][F], T_dev [rows][O] device FP32. */
+int sbm_mlp_gradients(void* mlp, const float* X_dev, const float* T_dev, int rows, float* grad_host,
+                      double* loss);
+/* The MLP's training set (filled by sbm_collect): number of stored rows; empty it. */
+int sbm_mlp_num_samples(const void* mlp, long long* n);
+int sbm_mlp_clear_samples(void* mlp);
+/* Adam (lr, beta = 0.9 / 0.999, eps 1e-8) on the mean squared error of the stored set for
+ * `epochs` passes in minibatches of `batch` rows, shuffled each epoch by a splitmix64
+ * Fisher-Yates permutation seeded by `seed`; *loss = mean batch loss of the last epoch.
+ * SBM_ERR_ARG if the set is empty. */
+int sbm_mlp_train(void* mlp, int epochs, int batch, float lr, unsigned long long seed, double* loss);
+/* Checkpoint: "SBMMLP\0\0", int32 {version 1, dim, p, F, H, O}, packed FP32 parameters, CRC-32
+ * (IEEE) of everything before it.  Load checks the shape and the checksum (SBM_ERR_ARG). */
+int sbm_mlp_save(const void* mlp, const char* path);
+int sbm_mlp_load(void* mlp, const char* path);
+
+/* Finest-level features of every boundary cell from a residual res_dev (dtype SBM_F64 or
+ * SBM_F32, compact layout): X_dev [n_bnd][F] FP32 (the BF16 values the MLP sees) and s_dev
+ * [n_bnd].  Boundary cells are ordered as sbm_learned_cells lists them. */
+int sbm_learned_features(void* ctx, int dtype, const void* res_dev, float* X_dev, float* s_dev);
+/* Number of finest-level boundary cells and (if cells_host is non-NULL) their compact indices. */
+int sbm_learned_cells(void* ctx, int* n_bnd, int* cells_host);
+/* Training pairs: from each of the n_starts initial vectors u0_dev[k][N] (dtype, the V-cycle
+ * precision used), run n_cycles steps of u <- u + V(-A u) on A u = 0 (plain V-cycles, exact
+ * solution 0) and after each step append, for every boundary cell, (x_K from r = -A u,
+ * target -u_K / s_K) to the MLP's training set.  *n_added = rows appended. */
+int sbm_collect(void* ctx, void* mlp, int dtype, const void* u0_dev, int n_starts, int n_cycles,
+                long long* n_added);
+/* Attach (mlp non-NULL) or detach (NULL) the correction to the context's V-cycle with the given
+ * scale.  fallback_rate > 0: a solve whose mean residual reduction per step over its first three
+ * steps is worse (larger) than fallback_rate switches the correction off for the rest of that
+ * solve (reported in sbm_solve_info.learned_fallback); 0 disables the rule. */
+int sbm_attach_mlp(void* ctx, void* mlp, float scale, double fallback_rate);
 
 #ifdef __cplusplus
 }

@@ -29,7 +29,10 @@ ERRORS = {-1: "SBM_ERR_ARG", -2: "SBM_ERR_CUDA", -3: "SBM_ERR_SINGULAR_BLOCK", -
 SYMBOLS = ("sbm_setup", "sbm_setup_host", "sbm_host_apply", "sbm_host_rhs", "sbm_destroy", "sbm_last_error", "sbm_kernel_launches", "sbm_num_levels", "sbm_info", "sbm_layout",
            "sbm_export_geometry", "sbm_rhs", "sbm_apply", "sbm_residual", "sbm_smooth", "sbm_restrict",
            "sbm_prolong_add", "sbm_coarse_solve", "sbm_vcycle", "sbm_dots", "sbm_dots_noalloc", "sbm_solve",
-           "sbm_solve_host")
+           "sbm_solve_host", "sbm_mlp_create", "sbm_mlp_destroy", "sbm_mlp_shape", "sbm_mlp_set_params",
+           "sbm_mlp_get_params", "sbm_mlp_forward", "sbm_mlp_gradients", "sbm_mlp_num_samples",
+           "sbm_mlp_clear_samples", "sbm_mlp_train", "sbm_mlp_save", "sbm_mlp_load", "sbm_learned_features",
+           "sbm_learned_cells", "sbm_collect", "sbm_attach_mlp")
 
 
 class SbmError(RuntimeError):
@@ -52,7 +55,7 @@ class _Desc(ctypes.Structure):
                 ("extension", ctypes.c_int), ("coarsest_n", ctypes.c_int), ("pre_smooth", ctypes.c_int),
                 ("post_smooth", ctypes.c_int), ("omega", ctypes.c_double), ("omega_p3", ctypes.c_double),
                 ("vf_samples", ctypes.c_int), ("precision", ctypes.c_int), ("tail_max_cells", ctypes.c_int),
-                ("cell_kernel_min_cells", ctypes.c_int), ("stream", ctypes.c_void_p)]
+                ("tail_cluster_ctas", ctypes.c_int), ("cell_kernel_min_cells", ctypes.c_int), ("stream", ctypes.c_void_p)]
 
 
 class _LevelInfo(ctypes.Structure):
@@ -64,7 +67,7 @@ class _LevelInfo(ctypes.Structure):
 class _SolveInfo(ctypes.Structure):
     _fields_ = [("converged", ctypes.c_int), ("iterations", ctypes.c_int), ("restarts", ctypes.c_int),
                 ("true_rel_residual", ctypes.c_double), ("history", ctypes.c_double * 512),
-                ("ms_total", ctypes.c_double)]
+                ("ms_total", ctypes.c_double), ("learned", ctypes.c_int), ("learned_fallback", ctypes.c_int)]
 
 
 @dataclass
@@ -76,6 +79,8 @@ class SolveInfo:
     history: list
     ms_total: float
     status: int
+    learned: bool = False
+    learned_fallback: bool = False
 
 
 _lib = None
@@ -116,8 +121,26 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.sbm_dots_noalloc.argtypes = [vp, ctypes.c_longlong, ip, vp, ctypes.c_longlong, vp, vp]
     lib.sbm_solve.argtypes = [vp, vp, vp, dp, ip, ip, ctypes.POINTER(_SolveInfo)]
     lib.sbm_solve_host.argtypes = [vp, vp, vp, dp, ip, ip, ctypes.POINTER(_SolveInfo)]
+    llp = ctypes.POINTER(ctypes.c_longlong)
+    lib.sbm_mlp_create.argtypes = [ip, ip, ip, ctypes.c_ulonglong, vp, ctypes.POINTER(ctypes.c_void_p)]
+    lib.sbm_mlp_destroy.argtypes = [vp]
+    lib.sbm_mlp_destroy.restype = None
+    lib.sbm_mlp_shape.argtypes = [vp, vp, vp, vp, vp, llp]
+    lib.sbm_mlp_set_params.argtypes = [vp, vp]
+    lib.sbm_mlp_get_params.argtypes = [vp, vp]
+    lib.sbm_mlp_forward.argtypes = [vp, vp, ip, vp]
+    lib.sbm_mlp_gradients.argtypes = [vp, vp, vp, ip, vp, ctypes.POINTER(ctypes.c_double)]
+    lib.sbm_mlp_num_samples.argtypes = [vp, llp]
+    lib.sbm_mlp_clear_samples.argtypes = [vp]
+    lib.sbm_mlp_train.argtypes = [vp, ip, ip, ctypes.c_float, ctypes.c_ulonglong, ctypes.POINTER(ctypes.c_double)]
+    lib.sbm_mlp_save.argtypes = [vp, ctypes.c_char_p]
+    lib.sbm_mlp_load.argtypes = [vp, ctypes.c_char_p]
+    lib.sbm_learned_features.argtypes = [vp, ip, vp, vp, vp]
+    lib.sbm_learned_cells.argtypes = [vp, ctypes.POINTER(ctypes.c_int), vp]
+    lib.sbm_collect.argtypes = [vp, vp, ip, vp, ip, ip, llp]
+    lib.sbm_attach_mlp.argtypes = [vp, vp, ctypes.c_float, dp]
     for name in SYMBOLS:
-        if name not in ("sbm_destroy", "sbm_last_error", "sbm_kernel_launches"):
+        if name not in ("sbm_destroy", "sbm_last_error", "sbm_kernel_launches", "sbm_mlp_destroy"):
             getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -134,7 +157,7 @@ def _check(code: int):
 
 
 def make_desc(prob, precision: int = SBM_F64, stream: int = 0, tail_max_cells: int = 0,
-              cell_kernel_min_cells: int = 0) -> _Desc:
+              cell_kernel_min_cells: int = 0, tail_cluster_ctas: int = 0) -> _Desc:
     d = _Desc()
     d.dim, d.n, d.p = prob.dim, prob.n, prob.p
     d.lo[:] = [float(v) for v in prob.lo]
@@ -151,6 +174,7 @@ def make_desc(prob, precision: int = SBM_F64, stream: int = 0, tail_max_cells: i
     d.pre_smooth, d.post_smooth, d.omega, d.omega_p3 = prob.pre_smooth, prob.post_smooth, prob.omega, prob.omega_p3
     d.vf_samples, d.precision, d.stream = prob.vf_samples, precision, stream
     d.tail_max_cells = tail_max_cells
+    d.tail_cluster_ctas = tail_cluster_ctas
     d.cell_kernel_min_cells = cell_kernel_min_cells
     return d
 
@@ -159,9 +183,9 @@ class Solver:
     """One DG-SBM problem set up on the current CUDA device (a libsbm context)."""
 
     def __init__(self, prob, precision: str = "f64", stream=None, tail_max_cells: int = 0,
-                 cell_kernel_min_cells: int = 0):
+                 cell_kernel_min_cells: int = 0, tail_cluster_ctas: int = 0):
         """tail_max_cells: p = 1 levels with at most that many cells run as one cluster launch
-        (0: library default, < 0: never).  cell_kernel_min_cells: launches over at least that many
+        (0: library default, < 0: never) of tail_cluster_ctas CTAs (0: 16, else 8).  cell_kernel_min_cells: launches over at least that many
         cells use one thread per cell (0: library default, < 0: never, 1: always where
         (p+1)^d <= 16)."""
         import torch
@@ -172,7 +196,8 @@ class Solver:
         self.prob = prob
         self.precision = SBM_F32 if precision == "f32" else SBM_F64
         self.stream = stream if stream is not None else torch.cuda.current_stream()
-        desc = make_desc(prob, self.precision, self.stream.cuda_stream, tail_max_cells, cell_kernel_min_cells)
+        desc = make_desc(prob, self.precision, self.stream.cuda_stream, tail_max_cells, cell_kernel_min_cells,
+                         tail_cluster_ctas)
         ctx = ctypes.c_void_p()
         _check(self.lib.sbm_setup(ctypes.byref(desc), ctypes.byref(ctx)))
         self.ctx = ctx
@@ -305,6 +330,138 @@ class Solver:
         return _info(inf, code)
 
 
+    # ------------------------------------------------------------------ learned correction
+    def learned_cells(self) -> np.ndarray:
+        """Compact indices of the finest-level boundary cells (the rows of learned_features)."""
+        n = ctypes.c_int()
+        _check(self.lib.sbm_learned_cells(self.ctx, ctypes.byref(n), None))
+        out = np.zeros(n.value, dtype=np.int32)
+        _check(self.lib.sbm_learned_cells(self.ctx, ctypes.byref(n), out.ctypes.data))
+        return out
+
+    def learned_features(self, res, F: int):
+        """(X [n_bnd][F] float32, s [n_bnd]) from a finest-level residual."""
+        torch = self._torch
+        nb = len(self.learned_cells())
+        X = torch.empty((nb, F), dtype=torch.float32, device="cuda")
+        s = torch.empty(nb, dtype=torch.float32, device="cuda")
+        _check(self.lib.sbm_learned_features(self.ctx, self._dt(res), self._vec(res), ctypes.c_void_p(X.data_ptr()),
+                                             ctypes.c_void_p(s.data_ptr())))
+        return X, s
+
+    def collect(self, mlp: "Mlp", u0, n_cycles: int) -> int:
+        """Training pairs from n_cycles stationary V-cycle steps on A u = 0 from each row of u0
+        ((n_starts, N), the V-cycle precision); returns the rows appended to mlp's set."""
+        if u0.dim() != 2 or u0.shape[1] != self.n_dof() or not u0.is_contiguous() or not u0.is_cuda:
+            raise ValueError("u0 must be a contiguous (n_starts, N) CUDA tensor")
+        n = ctypes.c_longlong()
+        _check(self.lib.sbm_collect(self.ctx, mlp.h, self._dt(u0), ctypes.c_void_p(u0.data_ptr()), u0.shape[0],
+                                    n_cycles, ctypes.byref(n)))
+        return n.value
+
+    def attach_mlp(self, mlp: "Mlp | None", scale: float = 1.0, fallback_rate: float = 0.0) -> None:
+        """Attach (or detach with None) the learned correction to this solver's V-cycle."""
+        self._mlp = mlp                                   # keeps the MLP alive while attached
+        _check(self.lib.sbm_attach_mlp(self.ctx, mlp.h if mlp is not None else None, scale, fallback_rate))
+
+
+class Mlp:
+    """The learned boundary-cell correction's MLP (FP32 master parameters, BF16 tensor-core
+    forward/backward, Adam) and its device training set.  See sbm_mlp_* in include/sbm.h."""
+
+    def __init__(self, dim: int, p: int, hidden: int = 128, seed: int = 0, stream=None):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("libsbm needs a CUDA device; no CPU fallback exists")
+        self._torch = torch
+        self.lib = load_library()
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        h = ctypes.c_void_p()
+        _check(self.lib.sbm_mlp_create(dim, p, hidden, seed, ctypes.c_void_p(self.stream.cuda_stream),
+                                       ctypes.byref(h)))
+        self.h = h
+        F, Fp, H, O = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        n = ctypes.c_longlong()
+        _check(self.lib.sbm_mlp_shape(self.h, ctypes.byref(F), ctypes.byref(Fp), ctypes.byref(H), ctypes.byref(O),
+                                      ctypes.byref(n)))
+        self.F, self.Fpad, self.H, self.O, self.nparam = F.value, Fp.value, H.value, O.value, n.value
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.sbm_mlp_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _f32(self, t, shape):
+        if not (t.is_cuda and t.is_contiguous() and t.dtype == self._torch.float32) or tuple(t.shape) != shape:
+            raise ValueError(f"expected a contiguous float32 CUDA tensor of shape {shape}")
+        return ctypes.c_void_p(t.data_ptr())
+
+    def split(self, flat: np.ndarray):
+        """(W1, b1, W2, b2, W3, b3) views of a packed parameter vector."""
+        F, H, O = self.F, self.H, self.O
+        sizes = [F * H, H, H * H, H, H * O, O]
+        shapes = [(F, H), (H,), (H, H), (H,), (H, O), (O,)]
+        out, o = [], 0
+        for n, sh in zip(sizes, shapes):
+            out.append(flat[o:o + n].reshape(sh))
+            o += n
+        return out
+
+    def get_params(self) -> np.ndarray:
+        out = np.zeros(self.nparam, dtype=np.float32)
+        _check(self.lib.sbm_mlp_get_params(self.h, out.ctypes.data))
+        return out
+
+    def set_params(self, params) -> None:
+        """params: packed vector, or the list (W1, b1, W2, b2, W3, b3) (input-major weights)."""
+        if isinstance(params, (list, tuple)):
+            params = np.concatenate([np.asarray(a, dtype=np.float64).reshape(-1) for a in params])
+        flat = np.ascontiguousarray(params, dtype=np.float32)
+        if flat.size != self.nparam:
+            raise ValueError(f"expected {self.nparam} parameters, got {flat.size}")
+        _check(self.lib.sbm_mlp_set_params(self.h, flat.ctypes.data))
+
+    def forward(self, X):
+        rows = X.shape[0]
+        Y = self._torch.empty((rows, self.O), dtype=self._torch.float32, device="cuda")
+        _check(self.lib.sbm_mlp_forward(self.h, self._f32(X, (rows, self.F)), rows, self._f32(Y, (rows, self.O))))
+        return Y
+
+    def gradients(self, X, T):
+        """(loss, packed gradient) of mean((MLP(X) - T)^2)."""
+        rows = X.shape[0]
+        g = np.zeros(self.nparam, dtype=np.float32)
+        loss = ctypes.c_double()
+        _check(self.lib.sbm_mlp_gradients(self.h, self._f32(X, (rows, self.F)), self._f32(T, (rows, self.O)), rows,
+                                          g.ctypes.data, ctypes.byref(loss)))
+        return loss.value, g
+
+    def num_samples(self) -> int:
+        n = ctypes.c_longlong()
+        _check(self.lib.sbm_mlp_num_samples(self.h, ctypes.byref(n)))
+        return n.value
+
+    def clear_samples(self) -> None:
+        _check(self.lib.sbm_mlp_clear_samples(self.h))
+
+    def train(self, epochs: int = 20, batch: int = 4096, lr: float = 1e-3, seed: int = 0) -> float:
+        loss = ctypes.c_double()
+        _check(self.lib.sbm_mlp_train(self.h, epochs, batch, lr, seed, ctypes.byref(loss)))
+        return loss.value
+
+    def save(self, path: str) -> None:
+        _check(self.lib.sbm_mlp_save(self.h, os.fsencode(path)))
+
+    def load(self, path: str) -> None:
+        _check(self.lib.sbm_mlp_load(self.h, os.fsencode(path)))
+
+
 class HostSetup:
     """Host-only libsbm context (no GPU needed): the set-up of every level and a host FP64
     evaluation of the operator with the same element data the kernels use."""
@@ -341,7 +498,7 @@ class HostSetup:
 def _info(inf: _SolveInfo, code: int) -> SolveInfo:
     n = min(inf.iterations, 512)
     return SolveInfo(bool(inf.converged), inf.iterations, inf.restarts, inf.true_rel_residual,
-                     list(inf.history[:n]), inf.ms_total, code)
+                     list(inf.history[:n]), inf.ms_total, code, bool(inf.learned), bool(inf.learned_fallback))
 
 
 def compact_to_natural(coords: np.ndarray, n: int, dim: int) -> np.ndarray:

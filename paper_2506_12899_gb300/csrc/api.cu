@@ -50,6 +50,115 @@ struct DevLevel {
   void* res[2] = {nullptr, nullptr};
 };
 
+
+// The learned boundary-cell correction: a two-hidden-layer ReLU MLP (FP32 master parameters,
+// BF16 copies for the tensor-core GEMMs), its Adam state, a device training set and the
+// per-batch activation buffers.  Parameters are packed W1[Fpad][H] b1[H] W2[H][H] b2[H]
+// W3[H][O] b3[O] (input-major); rows F..Fpad-1 of W1 are zero and stay zero (their gradient
+// is zero because the padded feature columns are zero).
+struct Mlp {
+  int dim = 2, p = 1, np = 4, npatch = 9, nstat = 0, F = 0, Fpad = 0, H = 128, O = 4;
+  size_t nparam = 0, oW1 = 0, ob1 = 0, oW2 = 0, ob2 = 0, oW3 = 0, ob3 = 0;
+  cudaStream_t s = nullptr;
+  std::vector<void*> allocs;
+  float* P = nullptr;                // master parameters
+  float* G = nullptr;                // gradients
+  float* Am = nullptr;               // Adam first moments
+  float* Av = nullptr;               // Adam second moments
+  __nv_bfloat16* Pb = nullptr;       // BF16 copy of the parameters
+  int adam_t = 0;
+  size_t cap = 0, count = 0;         // training set rows
+  __nv_bfloat16* Xd = nullptr;       // [cap][Fpad]
+  float* Td = nullptr;               // [cap][O]
+  int* idx_all = nullptr;            // [cap] epoch permutation
+  int bcap = 0;                      // batch buffers
+  __nv_bfloat16 *Xb = nullptr, *H1 = nullptr, *H2 = nullptr, *dYb = nullptr, *dZ2b = nullptr, *dZ1b = nullptr;
+  float *Tb = nullptr, *Y = nullptr, *dYf = nullptr, *dH2 = nullptr, *dH1 = nullptr, *loss_part = nullptr,
+        *loss_tmp = nullptr, *loss_acc = nullptr;
+  ~Mlp() {
+    for (void* q : allocs) cudaFree(q);
+  }
+  template <typename T>
+  T* alloc(size_t n) {
+    void* q = nullptr;
+    cudaError_t e = cudaMalloc(&q, (n ? n : 1) * sizeof(T));
+    if (e != cudaSuccess) throw SetupError{SBM_ERR_ALLOC, std::string("cudaMalloc: ") + cudaGetErrorString(e)};
+    allocs.push_back(q);
+    return static_cast<T*>(q);
+  }
+  void release(void* q) {
+    if (!q) return;
+    for (auto it = allocs.begin(); it != allocs.end(); ++it)
+      if (*it == q) {
+        cudaFree(q);
+        allocs.erase(it);
+        return;
+      }
+  }
+  const __nv_bfloat16* W1b() const { return Pb + oW1; }
+  const __nv_bfloat16* W2b() const { return Pb + oW2; }
+  const __nv_bfloat16* W3b() const { return Pb + oW3; }
+  void ensure_batch(int B) {
+    if (B <= bcap) return;
+    for (void* q : {(void*)Xb, (void*)H1, (void*)H2, (void*)dYb, (void*)dZ2b, (void*)dZ1b, (void*)Tb, (void*)Y,
+                    (void*)dYf, (void*)dH2, (void*)dH1})
+      release(q);
+    Xb = alloc<__nv_bfloat16>((size_t)B * Fpad);
+    H1 = alloc<__nv_bfloat16>((size_t)B * H);
+    H2 = alloc<__nv_bfloat16>((size_t)B * H);
+    dYb = alloc<__nv_bfloat16>((size_t)B * O);
+    dZ2b = alloc<__nv_bfloat16>((size_t)B * H);
+    dZ1b = alloc<__nv_bfloat16>((size_t)B * H);
+    Tb = alloc<float>((size_t)B * O);
+    Y = alloc<float>((size_t)B * O);
+    dYf = alloc<float>((size_t)B * O);
+    dH2 = alloc<float>((size_t)B * H);
+    dH1 = alloc<float>((size_t)B * H);
+    bcap = B;
+  }
+  // Training-set capacity for `rows` rows, keeping the stored ones.
+  void reserve(size_t rows) {
+    if (rows <= cap) return;
+    const size_t ncap = std::max(rows, cap * 2);
+    __nv_bfloat16* nX = alloc<__nv_bfloat16>(ncap * Fpad);
+    float* nT = alloc<float>(ncap * O);
+    if (count) {
+      CUDA_TRY(cudaMemcpyAsync(nX, Xd, count * Fpad * sizeof(__nv_bfloat16), cudaMemcpyDeviceToDevice, s));
+      CUDA_TRY(cudaMemcpyAsync(nT, Td, count * O * sizeof(float), cudaMemcpyDeviceToDevice, s));
+      CUDA_TRY(cudaStreamSynchronize(s));
+    }
+    release(Xd);
+    release(Td);
+    release(idx_all);
+    Xd = nX;
+    Td = nT;
+    idx_all = alloc<int>(ncap);
+    cap = ncap;
+  }
+  // Yout[rows][O] = MLP(X) with the BF16 weights, hidden activations into h1, h2 ([rows][H]).
+  void forward(const __nv_bfloat16* X, int rows, float* Yout, __nv_bfloat16* h1, __nv_bfloat16* h2,
+               cudaStream_t st) const {
+    CUDA_TRY(launch_gemm_bf16(rows, H, Fpad, 0, 0, X, Fpad, W1b(), H, P + ob1, 1, nullptr, h1, H, st));
+    CUDA_TRY(launch_gemm_bf16(rows, H, H, 0, 0, h1, H, W2b(), H, P + ob2, 1, nullptr, h2, H, st));
+    CUDA_TRY(launch_gemm_bf16(rows, O, H, 0, 0, h2, H, W3b(), O, P + ob3, 0, Yout, nullptr, O, st));
+  }
+  // G = gradient of the mean squared error over the rows of (X, T), after forward(X, rows, Y,
+  // H1, H2); loss_part receives per-block partial sums of the squared errors.
+  void backward(const __nv_bfloat16* X, const float* T, int rows) {
+    CUDA_TRY(launch_mse_grad(rows, O, Y, T, dYf, dYb, 1.0f / ((float)rows * O), loss_part, 152, s));
+    CUDA_TRY(launch_gemm_bf16(H, O, rows, 1, 0, H2, H, dYb, O, nullptr, 0, G + oW3, nullptr, O, s));
+    CUDA_TRY(launch_colsum(rows, O, dYf, G + ob3, s));
+    CUDA_TRY(launch_gemm_bf16(rows, H, O, 0, 1, dYb, O, W3b(), O, nullptr, 0, dH2, nullptr, H, s));
+    CUDA_TRY(launch_relu_mask(rows * H, dH2, H2, dZ2b, s));
+    CUDA_TRY(launch_gemm_bf16(H, H, rows, 1, 0, H1, H, dZ2b, H, nullptr, 0, G + oW2, nullptr, H, s));
+    CUDA_TRY(launch_colsum(rows, H, dH2, G + ob2, s));
+    CUDA_TRY(launch_gemm_bf16(rows, H, H, 0, 1, dZ2b, H, W2b(), H, nullptr, 0, dH1, nullptr, H, s));
+    CUDA_TRY(launch_relu_mask(rows * H, dH1, H1, dZ1b, s));
+    CUDA_TRY(launch_gemm_bf16(Fpad, H, rows, 1, 0, X, Fpad, dZ1b, H, nullptr, 0, G + oW1, nullptr, H, s));
+    CUDA_TRY(launch_colsum(rows, H, dH1, G + ob1, s));
+  }
+};
+
 struct Context {
   sbm_setup_desc desc{};
   cudaStream_t stream = nullptr;
@@ -57,7 +166,8 @@ struct Context {
   std::vector<double> rhs_host;
   std::vector<void*> allocs;
   bool work_ready[2] = {false, false};
-  int tail_top = -1;                 // levels 0..tail_top form the cluster tail (-1: none)
+  int tail_cand = -1;                // highest level the cluster tail may start at (-1: none)
+  TailPlan tail_plan[2];             // per precision: levels 0..top in one cluster launch
   void* tail[2] = {nullptr, nullptr};  // TailLevel<double> / TailLevel<float> arrays
   // FGMRES workspace
   int ws_m = 0, ws_prec = -1;
@@ -80,16 +190,34 @@ struct Context {
   // V-cycle precision is captured once into a CUDA graph and replayed.
   cudaStream_t ws = nullptr;
   cudaEvent_t join_in = nullptr, join_out = nullptr;
-  cudaGraphExec_t arnoldi[2][32] = {};
-  long long arnoldi_kernels[2][32] = {};
+  cudaGraphExec_t arnoldi[2][2][32] = {};   // [precision][learned correction on][j]
+  long long arnoldi_kernels[2][2][32] = {};
+  // learned boundary-cell correction attached to this context (not owned)
+  Mlp* mlp = nullptr;
+  bool mlp_on = false;                 // correction active in the next V-cycles
+  float mlp_scale = 1.f;
+  double mlp_rate_ref = 0.0;           // fallback when the per-step rate is worse than this (0: never)
+  // finest-level feature data (uploaded on first use) and inference buffers
+  int lf_F = 0, lf_Fpad = 0, lf_npatch = 0, lf_nstat = 0, lf_nb = 0;
+  int* mlp_cells = nullptr;            // [n_bnd] compact cell of each boundary cell (finest level)
+  int* mlp_patch = nullptr;            // [n_bnd][3^d]
+  float* mlp_stat = nullptr;           // [n_bnd][nstat]
+  __nv_bfloat16* mlp_X = nullptr;      // [n_bnd][Fpad] inference features
+  float* mlp_s = nullptr;              // [n_bnd]
+  int mlp_bufH = 0, mlp_bufO = 0;      // sizes of the buffers below
+  float* mlp_Y = nullptr;              // [n_bnd][O]
+  __nv_bfloat16* mlp_H1 = nullptr;     // [n_bnd][H]
+  __nv_bfloat16* mlp_H2 = nullptr;
+  void* col_vec[2][4] = {};            // training-data collection: u, rhs, z, zero (per precision)
 
   void drop_graphs() {
-    for (auto& row : arnoldi)
-      for (auto& g : row)
-        if (g) {
-          cudaGraphExecDestroy(g);
-          g = nullptr;
-        }
+    for (auto& a : arnoldi)
+      for (auto& row : a)
+        for (auto& g : row)
+          if (g) {
+            cudaGraphExecDestroy(g);
+            g = nullptr;
+          }
   }
 
   ~Context() {
@@ -219,6 +347,8 @@ void validate(const sbm_setup_desc& d) {
   if (d.pre_smooth < 0 || d.post_smooth < 0 || d.pre_smooth > 16 || d.post_smooth > 16) bad("smoothing steps");
   if (d.precision != SBM_F64 && d.precision != SBM_F32) bad("precision must be SBM_F64 or SBM_F32");
   if (d.extension != 0 && d.extension != 1) bad("extension must be 0 or 1");
+  if (d.tail_cluster_ctas < 0 || d.tail_cluster_ctas > 16 || (d.tail_cluster_ctas & (d.tail_cluster_ctas - 1)))
+    bad("tail_cluster_ctas must be 0, 1, 2, 4, 8 or 16");
   const double w0 = d.hi[0] - d.lo[0];
   if (!(w0 > 0) || !std::isfinite(w0)) bad("empty or non-finite box");
   for (int k = 1; k < d.dim; ++k)
@@ -279,7 +409,7 @@ Context* build_context(const sbm_setup_desc& d, bool device) {
     C->lv[l].T32 = make_transfer<float>(C->lv[l - 1], C->lv[l]);
   }
   {
-    const int cap = d.tail_max_cells == 0 ? 10000 : d.tail_max_cells;
+    const long long cap = d.tail_max_cells == 0 ? -1 : d.tail_max_cells;
     int top = -1;
     for (int l = 0; l < (int)C->lv.size(); ++l) {
       const HostLevel& H = C->lv[l].H;
@@ -287,8 +417,7 @@ Context* build_context(const sbm_setup_desc& d, bool device) {
       if (H.p != 1 || !h_level || H.n_act > cap) break;
       top = l;
     }
-    C->tail_top = (cap > 0 && top >= 1 && tail_cluster_size(d.dim, 0) > 0 && tail_cluster_size(d.dim, 1) > 0)
-                      ? top : -1;
+    C->tail_cand = cap > 0 && top >= 1 ? top : -1;
   }
   CUDA_TRY(cudaMallocHost(&C->host_pinned, 64 * sizeof(double)));
   CUDA_TRY(cudaEventCreate(&C->ev0));
@@ -310,20 +439,89 @@ void ensure_work(Context& C) {
     L.rhs[pi] = C.dalloc<R>(N);
     L.res[pi] = C.dalloc<R>(N);
   }
-  if (C.tail_top >= 1) {
-    std::vector<TailLevel<R>> tl(C.tail_top + 1);
-    for (int l = 0; l <= C.tail_top; ++l) {
-      std::memset(&tl[l], 0, sizeof(TailLevel<R>));
-      tl[l].P = params<R>(C.lv[l]);
-      if (l >= 1) tl[l].T = tparams<R>(C.lv[l]);
-      tl[l].z = static_cast<R*>(C.lv[l].z[pi]);
-      tl[l].rhs = static_cast<R*>(C.lv[l].rhs[pi]);
+  // cluster tail: the highest candidate level whose vectors (levels 0..top) fit in the shared
+  // memory of a resident cluster of 16, else 8, CTAs
+  C.tail_plan[pi] = TailPlan{};
+  const int NP = C.lv[0].H.dim == 2 ? 4 : 8;
+  std::vector<int> sizes = {16, 8};
+  if (C.desc.tail_cluster_ctas > 0) sizes = {C.desc.tail_cluster_ctas};
+  for (int size : sizes) {
+    if (C.tail_plan[pi].top >= 1) break;
+    for (int top = C.tail_cand; top >= 1; --top) {
+      std::vector<TailLevel<R>> tl(top + 1);
+      size_t elems = 0;
+      for (int l = 0; l <= top; ++l) {
+        std::memset(&tl[l], 0, sizeof(TailLevel<R>));
+        tl[l].P = params<R>(C.lv[l]);
+        if (l >= 1) tl[l].T = tparams<R>(C.lv[l]);
+        int ncell = 0;
+        for (int c = 0; c < (1 << C.lv[l].H.dim); ++c) {
+          const int cnt = tl[l].P.colour_start[c + 1] - tl[l].P.colour_start[c];
+          tl[l].m[c] = (cnt + size - 1) / size;
+          tl[l].off[c] = ncell;
+          ncell += tl[l].m[c];
+        }
+        tl[l].ncell = ncell;
+        tl[l].zoff = (int)elems;
+        tl[l].roff = (int)(elems + (size_t)ncell * NP);
+        elems += 2 * (size_t)ncell * NP;
+      }
+      const int gather_off = (int)elems;
+      elems += (size_t)C.lv[0].H.n_act * NP;
+      const size_t smem = elems * sizeof(R);
+      if (!tail_cluster_fits(C.lv[0].H.dim, pi, size, smem)) continue;
+      TailLevel<R>* d = C.dalloc<TailLevel<R>>(tl.size());
+      CUDA_TRY(cudaMemcpy(d, tl.data(), tl.size() * sizeof(TailLevel<R>), cudaMemcpyHostToDevice));
+      C.tail[pi] = d;
+      C.tail_plan[pi].top = top;
+      C.tail_plan[pi].cluster = size;
+      C.tail_plan[pi].smem_bytes = smem;
+      C.tail_plan[pi].gather_off = gather_off;
+      break;
     }
-    TailLevel<R>* d = C.dalloc<TailLevel<R>>(tl.size());
-    CUDA_TRY(cudaMemcpy(d, tl.data(), tl.size() * sizeof(TailLevel<R>), cudaMemcpyHostToDevice));
-    C.tail[pi] = d;
   }
   C.work_ready[pi] = true;
+}
+
+// Feature layout of the finest level: F = 3^d (p+1)^d patch values + 2d (p+1)^(d-1) d face
+// components + kappa + 2d face mask, padded to a multiple of 32; uploads the patch table, the
+// static features and the boundary-cell list on first use.
+void ensure_learned(Context& C) {
+  if (C.lf_F > 0) return;
+  const HostLevel& H = C.lv[C.finest()].H;
+  const int dim = H.dim, np = H.np, nq = H.nq;
+  C.lf_npatch = dim == 2 ? 9 : 27;
+  C.lf_nstat = 2 * dim * nq * dim + 1 + 2 * dim;
+  C.lf_F = C.lf_npatch * np + C.lf_nstat;
+  C.lf_Fpad = (C.lf_F + 31) / 32 * 32;
+  C.lf_nb = H.n_bnd;
+  const int nb = H.n_bnd;
+  C.mlp_cells = C.dalloc<int>(nb);
+  C.mlp_patch = C.dalloc<int>((size_t)nb * C.lf_npatch);
+  C.mlp_stat = C.dalloc<float>((size_t)nb * C.lf_nstat);
+  C.mlp_X = C.dalloc<__nv_bfloat16>((size_t)nb * C.lf_Fpad);
+  C.mlp_s = C.dalloc<float>(nb);
+  std::vector<float> st(H.mlp_static.begin(), H.mlp_static.end());
+  if (nb) {
+    CUDA_TRY(cudaMemcpy(C.mlp_cells, H.bnd_cell.data(), nb * sizeof(int), cudaMemcpyHostToDevice));
+    CUDA_TRY(cudaMemcpy(C.mlp_patch, H.patch.data(), H.patch.size() * sizeof(int), cudaMemcpyHostToDevice));
+    CUDA_TRY(cudaMemcpy(C.mlp_stat, st.data(), st.size() * sizeof(float), cudaMemcpyHostToDevice));
+  }
+}
+
+// Learned boundary-cell correction after the finest-level post-smoothing: features from the
+// residual r - A z, then z_K += scale * s_K * MLP(x_K) on every boundary cell.
+template <typename R>
+void apply_learned(Context& C, DevLevel& L, const R* r, R* z, cudaStream_t s) {
+  const Mlp& M = *C.mlp;
+  const int pi = prec_index<R>();
+  R* res = static_cast<R*>(L.res[pi]);
+  CUDA_TRY((launch_apply<R, R>(L.H.dim, L.H.p, params<R>(L), z, r, res, 1, s)));
+  const int nb = C.lf_nb;
+  CUDA_TRY(launch_mlp_features<R>(nb, C.lf_npatch, L.H.np, C.lf_nstat, C.lf_Fpad, C.mlp_patch, C.mlp_stat, res,
+                                  C.mlp_X, C.mlp_s, s));
+  M.forward(C.mlp_X, nb, C.mlp_Y, C.mlp_H1, C.mlp_H2, s);
+  CUDA_TRY(launch_mlp_scatter<R>(nb, M.np, M.O, C.mlp_cells, C.mlp_Y, C.mlp_s, C.mlp_scale, z, s));
 }
 
 // One V-cycle on level l (Sec. 3): zero initial guess, pre-smoothing with forward colour order,
@@ -337,9 +535,9 @@ void vcycle_rec(Context& C, int l, const R* r, R* z, cudaStream_t s) {
     CUDA_TRY(launch_coarse<R>(L.coarse_inv, L.H.n_dof(), r, z, s));
     return;
   }
-  if (l == C.tail_top) {                          // levels 0..l in one cluster launch
+  if (l == C.tail_plan[pi].top && !(C.mlp_on && l == C.finest())) {   // levels 0..l in one cluster launch
     CUDA_TRY(launch_vcycle_tail<R>(L.H.dim, static_cast<const TailLevel<R>*>(C.tail[pi]), l, r, z,
-                                   C.lv[0].coarse_inv, C.desc.pre_smooth, C.desc.post_smooth, s));
+                                   C.lv[0].coarse_inv, C.desc.pre_smooth, C.desc.post_smooth, C.tail_plan[pi], s));
     return;
   }
   const int dim = L.H.dim;
@@ -357,6 +555,7 @@ void vcycle_rec(Context& C, int l, const R* r, R* z, cudaStream_t s) {
   vcycle_rec<R>(C, l - 1, rc, zc, s);
   CUDA_TRY(launch_prolong<R>(dim, L.H.p, Lc.H.p, tparams<R>(L), zc, z, s));
   for (int k = 0; k < C.desc.post_smooth; ++k) CUDA_TRY(launch_smooth<R>(dim, L.H.p, P, 1, 0, r, z, s));
+  if (C.mlp_on && l == C.finest()) apply_learned<R>(C, L, r, z, s);
 }
 
 void ensure_krylov(Context& C, int m) {
@@ -417,7 +616,10 @@ void arnoldi_step_work(Context& C, int j, cudaStream_t s) {
 // Runs step j from its captured graph (captured on first use).
 void run_arnoldi_step(Context& C, int j, cudaStream_t s) {
   const int pi = C.desc.precision == SBM_F32 ? 1 : 0;
-  if (!C.arnoldi[pi][j]) {
+  const int li = C.mlp_on ? 1 : 0;
+  auto& graph = C.arnoldi[pi][li][j];
+  auto& nkern = C.arnoldi_kernels[pi][li][j];
+  if (!graph) {
     const long long before = g_kernel_launches.load();
     CUDA_TRY(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
     try {
@@ -434,12 +636,12 @@ void run_arnoldi_step(Context& C, int j, cudaStream_t s) {
     const cudaError_t e = cudaGraphInstantiate(&ge, g, 0);
     cudaGraphDestroy(g);
     CUDA_TRY(e);
-    C.arnoldi[pi][j] = ge;
-    C.arnoldi_kernels[pi][j] = g_kernel_launches.load() - before;
-    g_kernel_launches.fetch_sub(C.arnoldi_kernels[pi][j]);   // captured, not executed
+    graph = ge;
+    nkern = g_kernel_launches.load() - before;
+    g_kernel_launches.fetch_sub(nkern);             // captured, not executed
   }
-  CUDA_TRY(cudaGraphLaunch(C.arnoldi[pi][j], s));
-  count_launches(C.arnoldi_kernels[pi][j]);
+  CUDA_TRY(cudaGraphLaunch(graph, s));
+  count_launches(nkern);
 }
 
 // Right-preconditioned flexible GMRES(m) with two classical Gram-Schmidt passes, FP64.
@@ -456,6 +658,13 @@ int solve_impl(Context& C, const double* b, double* x, double tol, int m, int ma
   const int dim = F.H.dim, p = F.H.p;
   double* hn = C.dots + 64;
   sbm_solve_info loc{};
+  const bool mlp_was_on = C.mlp_on;
+  loc.learned = C.mlp_on ? 1 : 0;
+  struct Restore {                                  // the fallback lasts for this solve only
+    Context& C;
+    bool on;
+    ~Restore() { C.mlp_on = on; }
+  } restore{C, mlp_was_on};
   CUDA_TRY(cudaEventRecord(C.join_in, C.stream));   // b and x are ready on the caller's stream
   CUDA_TRY(cudaStreamWaitEvent(s, C.join_in, 0));
   CUDA_TRY(cudaEventRecord(C.ev0, s));
@@ -514,6 +723,14 @@ int solve_impl(Context& C, const double* b, double* x, double tol, int m, int ma
         k = j + 1;
         if (loc.iterations < 512) loc.history[loc.iterations] = std::fabs(g[j + 1]) / bnorm;
         loc.iterations += 1;
+        // learned-correction fallback: after 3 steps of the first cycle, a mean residual reduction
+        // per step worse than the reference rate switches the correction off; FGMRES tolerates
+        // the change of preconditioner (every z_j is stored)
+        if (C.mlp_on && C.mlp_rate_ref > 0 && loc.restarts == 0 && loc.iterations == 3 &&
+            std::pow(std::fabs(g[j + 1]) / beta, 1.0 / 3.0) > C.mlp_rate_ref) {
+          C.mlp_on = false;
+          loc.learned_fallback = 1;
+        }
         if (nan || !std::isfinite(g[j + 1])) {
           nan = true;
           break;
@@ -552,7 +769,106 @@ int solve_impl(Context& C, const double* b, double* x, double tol, int m, int ma
   return SBM_OK;
 }
 
+// Training pairs from the stationary iteration u <- u + V(-A u) on A u = 0 (exact solution 0):
+// after each V-cycle (the finest post-smoothing is its last step) the error of the iterate is -u,
+// so every boundary cell K gives features x_K from r = -A u and the target -u_K / s_K.
+template <typename R>
+long long collect_impl(Context& C, Mlp& M, const R* u0, int n_starts, int n_cycles) {
+  ensure_work<R>(C);
+  ensure_learned(C);
+  const int pi = prec_index<R>();
+  const int Lf = C.finest();
+  DevLevel& F = C.lv[Lf];
+  const size_t N = F.H.n_dof();
+  const int nb = C.lf_nb;
+  const cudaStream_t s = C.stream;
+  for (int k = 0; k < 4; ++k)
+    if (!C.col_vec[pi][k]) C.col_vec[pi][k] = C.dalloc<R>(N);
+  R* u = static_cast<R*>(C.col_vec[pi][0]);
+  R* rhs = static_cast<R*>(C.col_vec[pi][1]);
+  R* z = static_cast<R*>(C.col_vec[pi][2]);
+  R* zero = static_cast<R*>(C.col_vec[pi][3]);
+  CUDA_TRY(cudaMemsetAsync(zero, 0, N * sizeof(R), s));
+  M.reserve(M.count + (size_t)n_starts * n_cycles * nb);
+  const bool was_on = C.mlp_on;
+  C.mlp_on = false;                                 // plain V-cycles
+  const LevelParams<R>& P = params<R>(F);
+  for (int k = 0; k < n_starts; ++k) {
+    CUDA_TRY(cudaMemcpyAsync(u, u0 + (size_t)k * N, N * sizeof(R), cudaMemcpyDeviceToDevice, s));
+    for (int c = 0; c < n_cycles; ++c) {
+      CUDA_TRY((launch_apply<R, R>(F.H.dim, F.H.p, P, u, zero, rhs, 1, s)));     // rhs = -A u
+      vcycle_rec<R>(C, Lf, rhs, z, s);
+      CUDA_TRY(launch_add<R>(N, z, u, s));
+      CUDA_TRY((launch_apply<R, R>(F.H.dim, F.H.p, P, u, zero, rhs, 1, s)));     // r = -A u
+      __nv_bfloat16* X = M.Xd + M.count * M.Fpad;
+      CUDA_TRY(launch_mlp_features<R>(nb, C.lf_npatch, F.H.np, C.lf_nstat, C.lf_Fpad, C.mlp_patch, C.mlp_stat, rhs, X,
+                                      C.mlp_s, s));
+      CUDA_TRY(launch_mlp_targets<R>(nb, F.H.np, C.mlp_cells, u, C.mlp_s, M.Td + M.count * M.O, s));
+      M.count += nb;
+    }
+  }
+  C.mlp_on = was_on;
+  CUDA_TRY(cudaStreamSynchronize(s));
+  return (long long)nb * n_starts * n_cycles;
+}
+
+// splitmix64 (Steele, Lea, Flood 2014): the seeded generator of the host-side MLP set-up.
+uint64_t splitmix64(uint64_t& x) {
+  uint64_t z = (x += 0x9E3779B97F4A7C15ull);
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+double uniform01(uint64_t& x) { return ((splitmix64(x) >> 11) + 0.5) * (1.0 / 9007199254740992.0); }
+double normal01(uint64_t& x) {                      // Box-Muller
+  const double u1 = uniform01(x), u2 = uniform01(x);
+  return std::sqrt(-2.0 * std::log(u1)) * std::cos(6.283185307179586 * u2);
+}
+
+// CRC-32 (IEEE 802.3, reflected polynomial 0xEDB88320), bitwise.
+uint32_t crc32(const unsigned char* p, size_t n) {
+  uint32_t c = 0xFFFFFFFFu;
+  for (size_t i = 0; i < n; ++i) {
+    c ^= p[i];
+    for (int k = 0; k < 8; ++k) c = (c >> 1) ^ (0xEDB88320u & (0u - (c & 1u)));
+  }
+  return c ^ 0xFFFFFFFFu;
+}
+
+// Packed unpadded parameter vector (W1 F x H, b1, W2, b2, W3, b3) <-> the padded device layout.
+size_t packed_size(const Mlp& M) { return M.nparam - (size_t)(M.Fpad - M.F) * M.H; }
+
+void set_params(Mlp& M, const float* host) {
+  std::vector<float> full(M.nparam, 0.f);
+  std::memcpy(full.data(), host, (size_t)M.F * M.H * sizeof(float));
+  std::memcpy(full.data() + M.ob1, host + (size_t)M.F * M.H, (M.nparam - M.ob1) * sizeof(float));
+  CUDA_TRY(cudaMemcpy(M.P, full.data(), M.nparam * sizeof(float), cudaMemcpyHostToDevice));
+  CUDA_TRY(launch_to_bf16((int)M.nparam, M.P, M.Pb, M.s));
+  CUDA_TRY(cudaMemsetAsync(M.Am, 0, M.nparam * sizeof(float), M.s));
+  CUDA_TRY(cudaMemsetAsync(M.Av, 0, M.nparam * sizeof(float), M.s));
+  CUDA_TRY(cudaStreamSynchronize(M.s));
+  M.adam_t = 0;
+}
+
+void get_packed(const Mlp& M, const float* dev, float* host) {
+  std::vector<float> full(M.nparam);
+  CUDA_TRY(cudaMemcpy(full.data(), dev, M.nparam * sizeof(float), cudaMemcpyDeviceToHost));
+  std::memcpy(host, full.data(), (size_t)M.F * M.H * sizeof(float));
+  std::memcpy(host + (size_t)M.F * M.H, full.data() + M.ob1, (M.nparam - M.ob1) * sizeof(float));
+}
+
+// Sum of the squared-error partials of the last backward pass, on the host.
+double read_loss(Mlp& M, int rows) {
+  float part[152];
+  CUDA_TRY(cudaMemcpyAsync(part, M.loss_part, sizeof(part), cudaMemcpyDeviceToHost, M.s));
+  CUDA_TRY(cudaStreamSynchronize(M.s));
+  double t = 0;
+  for (float v : part) t += v;
+  return t / ((double)rows * M.O);
+}
+
 Context* ctx_of(void* p) { return static_cast<Context*>(p); }
+Mlp* mlp_of(void* p) { return static_cast<Mlp*>(p); }
 
 int check_level(const Context* C, int& level) {
   if (!C) return set_error(SBM_ERR_ARG, "null context");
@@ -854,6 +1170,293 @@ int sbm_solve_host(void* ctx, const double* b_host, double* x_host, double tol, 
     CUDA_TRY(cudaMemcpyAsync(x_host, C->xbuf, N * sizeof(double), cudaMemcpyDeviceToHost, C->stream));
     CUDA_TRY(cudaStreamSynchronize(C->stream));
     return rc;
+  });
+}
+
+
+// ------------------------------------------------------------------ learned boundary correction
+int sbm_mlp_create(int dim, int p, int hidden, unsigned long long seed, void* stream, void** out) {
+  if (!out) return set_error(SBM_ERR_ARG, "null output");
+  *out = nullptr;
+  if ((dim != 2 && dim != 3) || p < 1 || p > 3 || hidden < 8 || hidden > 1024)
+    return set_error(SBM_ERR_ARG, "bad MLP shape");
+  return guarded([&]() -> int {
+    auto M = std::make_unique<Mlp>();
+    M->dim = dim;
+    M->p = p;
+    M->np = dim == 2 ? (p + 1) * (p + 1) : (p + 1) * (p + 1) * (p + 1);
+    const int nq = dim == 2 ? p + 1 : (p + 1) * (p + 1);
+    M->npatch = dim == 2 ? 9 : 27;
+    M->nstat = 2 * dim * nq * dim + 1 + 2 * dim;
+    M->F = M->npatch * M->np + M->nstat;
+    M->Fpad = (M->F + 31) / 32 * 32;
+    M->H = hidden;
+    M->O = M->np;
+    M->s = static_cast<cudaStream_t>(stream);
+    const size_t F = M->Fpad, H = M->H, O = M->O;
+    M->oW1 = 0;
+    M->ob1 = F * H;
+    M->oW2 = M->ob1 + H;
+    M->ob2 = M->oW2 + H * H;
+    M->oW3 = M->ob2 + H;
+    M->ob3 = M->oW3 + H * O;
+    M->nparam = M->ob3 + O;
+    M->P = M->alloc<float>(M->nparam);
+    M->G = M->alloc<float>(M->nparam);
+    M->Am = M->alloc<float>(M->nparam);
+    M->Av = M->alloc<float>(M->nparam);
+    M->Pb = M->alloc<__nv_bfloat16>(M->nparam);
+    M->loss_part = M->alloc<float>(152);
+    M->loss_tmp = M->alloc<float>(1);
+    M->loss_acc = M->alloc<float>(1);
+    // He-normal hidden layers, 1/H output layer, zero biases
+    std::vector<float> packed(packed_size(*M), 0.f);
+    uint64_t st = seed;
+    size_t o = 0;
+    for (size_t i = 0; i < (size_t)M->F * H; ++i) packed[o++] = (float)(normal01(st) * std::sqrt(2.0 / M->F));
+    o += H;
+    for (size_t i = 0; i < H * H; ++i) packed[o++] = (float)(normal01(st) * std::sqrt(2.0 / H));
+    o += H;
+    for (size_t i = 0; i < H * O; ++i) packed[o++] = (float)(normal01(st) * std::sqrt(1.0 / H));
+    set_params(*M, packed.data());
+    *out = M.release();
+    return SBM_OK;
+  });
+}
+
+void sbm_mlp_destroy(void* mlp) { delete mlp_of(mlp); }
+
+int sbm_mlp_shape(const void* mlp, int* F, int* Fpad, int* H, int* O, long long* nparam) {
+  const Mlp* M = static_cast<const Mlp*>(mlp);
+  if (!M) return set_error(SBM_ERR_ARG, "null MLP");
+  if (F) *F = M->F;
+  if (Fpad) *Fpad = M->Fpad;
+  if (H) *H = M->H;
+  if (O) *O = M->O;
+  if (nparam) *nparam = (long long)packed_size(*M);
+  return SBM_OK;
+}
+
+int sbm_mlp_set_params(void* mlp, const float* params_host) {
+  Mlp* M = mlp_of(mlp);
+  if (!M || !params_host) return set_error(SBM_ERR_ARG, "bad argument");
+  return guarded([&]() -> int {
+    set_params(*M, params_host);
+    return SBM_OK;
+  });
+}
+
+int sbm_mlp_get_params(const void* mlp, float* params_host) {
+  const Mlp* M = static_cast<const Mlp*>(mlp);
+  if (!M || !params_host) return set_error(SBM_ERR_ARG, "bad argument");
+  return guarded([&]() -> int {
+    get_packed(*M, M->P, params_host);
+    return SBM_OK;
+  });
+}
+
+int sbm_mlp_forward(void* mlp, const float* X_dev, int rows, float* Y_dev) {
+  Mlp* M = mlp_of(mlp);
+  if (!M || !X_dev || !Y_dev || rows < 0) return set_error(SBM_ERR_ARG, "bad argument");
+  return guarded([&]() -> int {
+    M->ensure_batch(std::max(rows, 1));
+    CUDA_TRY(launch_pack_bf16(rows, M->F, M->Fpad, X_dev, M->Xb, M->s));
+    M->forward(M->Xb, rows, Y_dev, M->H1, M->H2, M->s);
+    return SBM_OK;
+  });
+}
+
+int sbm_mlp_gradients(void* mlp, const float* X_dev, const float* T_dev, int rows, float* grad_host,
+                      double* loss) {
+  Mlp* M = mlp_of(mlp);
+  if (!M || !X_dev || !T_dev || rows < 1) return set_error(SBM_ERR_ARG, "bad argument");
+  return guarded([&]() -> int {
+    M->ensure_batch(rows);
+    CUDA_TRY(launch_pack_bf16(rows, M->F, M->Fpad, X_dev, M->Xb, M->s));
+    CUDA_TRY(cudaMemcpyAsync(M->Tb, T_dev, (size_t)rows * M->O * sizeof(float), cudaMemcpyDeviceToDevice, M->s));
+    M->forward(M->Xb, rows, M->Y, M->H1, M->H2, M->s);
+    M->backward(M->Xb, M->Tb, rows);
+    const double l = read_loss(*M, rows);
+    if (loss) *loss = l;
+    if (grad_host) get_packed(*M, M->G, grad_host);
+    return SBM_OK;
+  });
+}
+
+int sbm_mlp_num_samples(const void* mlp, long long* n) {
+  const Mlp* M = static_cast<const Mlp*>(mlp);
+  if (!M || !n) return set_error(SBM_ERR_ARG, "bad argument");
+  *n = (long long)M->count;
+  return SBM_OK;
+}
+
+int sbm_mlp_clear_samples(void* mlp) {
+  Mlp* M = mlp_of(mlp);
+  if (!M) return set_error(SBM_ERR_ARG, "null MLP");
+  M->count = 0;
+  return SBM_OK;
+}
+
+int sbm_mlp_train(void* mlp, int epochs, int batch, float lr, unsigned long long seed, double* loss) {
+  Mlp* M = mlp_of(mlp);
+  if (!M || epochs < 0 || batch < 1 || !(lr > 0)) return set_error(SBM_ERR_ARG, "bad argument");
+  if (M->count == 0) return set_error(SBM_ERR_ARG, "no training samples");
+  return guarded([&]() -> int {
+    M->ensure_batch(batch);
+    const size_t n = M->count;
+    std::vector<int> perm(n);
+    uint64_t st = seed;
+    double last = 0;
+    for (int e = 0; e < epochs; ++e) {
+      for (size_t i = 0; i < n; ++i) perm[i] = (int)i;
+      for (size_t i = n - 1; i > 0; --i) std::swap(perm[i], perm[splitmix64(st) % (i + 1)]);   // Fisher-Yates
+      CUDA_TRY(cudaMemcpyAsync(M->idx_all, perm.data(), n * sizeof(int), cudaMemcpyHostToDevice, M->s));
+      CUDA_TRY(cudaMemsetAsync(M->loss_acc, 0, sizeof(float), M->s));
+      int nbatch = 0;
+      for (size_t b0 = 0; b0 < n; b0 += batch) {
+        const int rows = (int)std::min<size_t>(batch, n - b0);
+        CUDA_TRY(launch_rows_gather(rows, M->Fpad, M->idx_all + b0, M->Xd, M->Xb, M->O, M->Td, M->Tb, M->s));
+        M->forward(M->Xb, rows, M->Y, M->H1, M->H2, M->s);
+        M->backward(M->Xb, M->Tb, rows);
+        M->adam_t += 1;
+        CUDA_TRY(launch_adam((int)M->nparam, M->P, M->G, M->Am, M->Av, M->Pb, lr, 0.9f, 0.999f, 1e-8f, M->adam_t, M->s));
+        CUDA_TRY(launch_colsum(152, 1, M->loss_part, M->loss_tmp, M->s));
+        CUDA_TRY(launch_axpy_f(1, 1.0f / ((float)rows * M->O), M->loss_tmp, M->loss_acc, M->s));
+        ++nbatch;
+      }
+      float acc = 0;
+      CUDA_TRY(cudaMemcpyAsync(&acc, M->loss_acc, sizeof(float), cudaMemcpyDeviceToHost, M->s));
+      CUDA_TRY(cudaStreamSynchronize(M->s));
+      last = acc / nbatch;
+    }
+    if (loss) *loss = last;
+    return SBM_OK;
+  });
+}
+
+int sbm_mlp_save(const void* mlp, const char* path) {
+  const Mlp* M = static_cast<const Mlp*>(mlp);
+  if (!M || !path) return set_error(SBM_ERR_ARG, "bad argument");
+  return guarded([&]() -> int {
+    std::vector<float> w(packed_size(*M));
+    get_packed(*M, M->P, w.data());
+    int32_t hdr[6] = {1, M->dim, M->p, M->F, M->H, M->O};
+    std::vector<unsigned char> buf(8 + sizeof(hdr) + w.size() * sizeof(float));
+    std::memcpy(buf.data(), "SBMMLP\0\0", 8);
+    std::memcpy(buf.data() + 8, hdr, sizeof(hdr));
+    std::memcpy(buf.data() + 8 + sizeof(hdr), w.data(), w.size() * sizeof(float));
+    const uint32_t crc = crc32(buf.data(), buf.size());
+    FILE* f = std::fopen(path, "wb");
+    if (!f) return set_error(SBM_ERR_ARG, std::string("cannot write ") + path);
+    const bool ok = std::fwrite(buf.data(), 1, buf.size(), f) == buf.size() && std::fwrite(&crc, 4, 1, f) == 1;
+    std::fclose(f);
+    return ok ? SBM_OK : set_error(SBM_ERR_ARG, std::string("short write to ") + path);
+  });
+}
+
+int sbm_mlp_load(void* mlp, const char* path) {
+  Mlp* M = mlp_of(mlp);
+  if (!M || !path) return set_error(SBM_ERR_ARG, "bad argument");
+  return guarded([&]() -> int {
+    FILE* f = std::fopen(path, "rb");
+    if (!f) return set_error(SBM_ERR_ARG, std::string("cannot read ") + path);
+    std::vector<unsigned char> buf;
+    unsigned char tmp[65536];
+    size_t k;
+    while ((k = std::fread(tmp, 1, sizeof(tmp), f)) > 0) buf.insert(buf.end(), tmp, tmp + k);
+    std::fclose(f);
+    const size_t want = 8 + 24 + packed_size(*M) * sizeof(float) + 4;
+    if (buf.size() != want || std::memcmp(buf.data(), "SBMMLP\0\0", 8) != 0)
+      return set_error(SBM_ERR_ARG, "not an MLP file of this shape");
+    int32_t hdr[6];
+    std::memcpy(hdr, buf.data() + 8, sizeof(hdr));
+    if (hdr[0] != 1 || hdr[1] != M->dim || hdr[2] != M->p || hdr[3] != M->F || hdr[4] != M->H || hdr[5] != M->O)
+      return set_error(SBM_ERR_ARG, "MLP file shape differs");
+    uint32_t crc;
+    std::memcpy(&crc, buf.data() + want - 4, 4);
+    if (crc != crc32(buf.data(), want - 4)) return set_error(SBM_ERR_ARG, "MLP file checksum mismatch");
+    std::vector<float> w(packed_size(*M));
+    std::memcpy(w.data(), buf.data() + 32, w.size() * sizeof(float));
+    set_params(*M, w.data());
+    return SBM_OK;
+  });
+}
+
+int sbm_learned_features(void* ctx, int dtype, const void* res_dev, float* X_dev, float* s_dev) {
+  Context* C = ctx_of(ctx);
+  if (C && C->host_only) return set_error(SBM_ERR_ARG, "host-only context");
+  if (!C || !res_dev || !X_dev || !s_dev) return set_error(SBM_ERR_ARG, "bad argument");
+  return guarded([&]() -> int {
+    ensure_learned(*C);
+    const HostLevel& H = C->lv[C->finest()].H;
+    if (dtype == SBM_F64)
+      CUDA_TRY(launch_mlp_features<double>(C->lf_nb, C->lf_npatch, H.np, C->lf_nstat, C->lf_Fpad, C->mlp_patch,
+                                           C->mlp_stat, (const double*)res_dev, C->mlp_X, s_dev, C->stream));
+    else if (dtype == SBM_F32)
+      CUDA_TRY(launch_mlp_features<float>(C->lf_nb, C->lf_npatch, H.np, C->lf_nstat, C->lf_Fpad, C->mlp_patch,
+                                          C->mlp_stat, (const float*)res_dev, C->mlp_X, s_dev, C->stream));
+    else
+      return set_error(SBM_ERR_ARG, "dtype");
+    CUDA_TRY(launch_unpack_bf16(C->lf_nb, C->lf_F, C->lf_Fpad, C->mlp_X, X_dev, C->stream));
+    return SBM_OK;
+  });
+}
+
+int sbm_learned_cells(void* ctx, int* n_bnd, int* cells_host) {
+  Context* C = ctx_of(ctx);
+  if (!C || !n_bnd) return set_error(SBM_ERR_ARG, "bad argument");
+  const HostLevel& H = C->lv[C->finest()].H;
+  *n_bnd = H.n_bnd;
+  if (cells_host && H.n_bnd) std::memcpy(cells_host, H.bnd_cell.data(), H.n_bnd * sizeof(int));
+  return SBM_OK;
+}
+
+int sbm_collect(void* ctx, void* mlp, int dtype, const void* u0_dev, int n_starts, int n_cycles,
+                long long* n_added) {
+  Context* C = ctx_of(ctx);
+  Mlp* M = mlp_of(mlp);
+  if (C && C->host_only) return set_error(SBM_ERR_ARG, "host-only context");
+  if (!C || !M || !u0_dev || n_starts < 0 || n_cycles < 0) return set_error(SBM_ERR_ARG, "bad argument");
+  const HostLevel& H = C->lv[C->finest()].H;
+  if (M->dim != H.dim || M->p != H.p) return set_error(SBM_ERR_ARG, "MLP shape does not match the finest level");
+  return guarded([&]() -> int {
+    long long n = 0;
+    if (dtype == SBM_F64) n = collect_impl<double>(*C, *M, (const double*)u0_dev, n_starts, n_cycles);
+    else if (dtype == SBM_F32) n = collect_impl<float>(*C, *M, (const float*)u0_dev, n_starts, n_cycles);
+    else return set_error(SBM_ERR_ARG, "dtype");
+    if (n_added) *n_added = n;
+    return SBM_OK;
+  });
+}
+
+int sbm_attach_mlp(void* ctx, void* mlp, float scale, double fallback_rate) {
+  Context* C = ctx_of(ctx);
+  if (C && C->host_only) return set_error(SBM_ERR_ARG, "host-only context");
+  if (!C) return set_error(SBM_ERR_ARG, "null context");
+  Mlp* M = mlp_of(mlp);
+  if (M) {
+    const HostLevel& H = C->lv[C->finest()].H;
+    if (M->dim != H.dim || M->p != H.p) return set_error(SBM_ERR_ARG, "MLP shape does not match the finest level");
+  }
+  return guarded([&]() -> int {
+    CUDA_TRY(cudaStreamSynchronize(C->stream));
+    C->drop_graphs();                               // the captured V-cycles change
+    C->mlp = M;
+    C->mlp_on = M != nullptr;
+    C->mlp_scale = scale;
+    C->mlp_rate_ref = fallback_rate;
+    if (M) {
+      ensure_learned(*C);
+      const int nb = std::max(C->lf_nb, 1);
+      if (C->mlp_bufH < M->H || C->mlp_bufO < M->O) {   // inference buffers before any capture
+        C->mlp_H1 = C->dalloc<__nv_bfloat16>((size_t)nb * M->H);
+        C->mlp_H2 = C->dalloc<__nv_bfloat16>((size_t)nb * M->H);
+        C->mlp_Y = C->dalloc<float>((size_t)nb * M->O);
+        C->mlp_bufH = M->H;
+        C->mlp_bufO = M->O;
+      }
+    }
+    return SBM_OK;
   });
 }
 

@@ -61,20 +61,56 @@ __device__ __forceinline__ void load_cell(const TI* __restrict__ x, int a, R (&v
   for (int i = 0; i < NP; ++i) v[i] = (R)ldv<COH>(x + (size_t)a * NP + i);
 }
 
-// y += (sum over interior faces of A_KN u_N) for cell a (Eq. 10 couplings); neighbours of
-// colour > col are skipped when zero_start (they hold zeros).
-template <int D, int N1, bool COH, typename TI, typename R>
-__device__ __forceinline__ void add_couplings(const LevelParams<R>& P, const TI* __restrict__ u, int a, int col,
-                                              bool zero_start, int (&nb)[2 * D], R (&y)[CD<D, N1>::NP]) {
+// Loads the 16-byte aligned values of one cell from shared memory (local or another CTA of the
+// cluster) with vector loads.
+template <int NP, typename R>
+__device__ __forceinline__ void load_np_vec(const R* p, R (&v)[NP]) {
+  static_assert((NP * sizeof(R)) % 16 == 0, "cell values must fill 16-byte words");
+  if constexpr (sizeof(R) == 4) {
+#pragma unroll
+    for (int c = 0; c < NP / 4; ++c) {
+      const float4 w = reinterpret_cast<const float4*>(p)[c];
+      v[4 * c] = w.x;
+      v[4 * c + 1] = w.y;
+      v[4 * c + 2] = w.z;
+      v[4 * c + 3] = w.w;
+    }
+  } else {
+#pragma unroll
+    for (int c = 0; c < NP / 2; ++c) {
+      const double2 w = reinterpret_cast<const double2*>(p)[c];
+      v[2 * c] = w.x;
+      v[2 * c + 1] = w.y;
+    }
+  }
+}
+
+template <int NP, typename R>
+__device__ __forceinline__ void store_np_vec(R* p, const R (&v)[NP]) {
+  if constexpr (sizeof(R) == 4) {
+#pragma unroll
+    for (int c = 0; c < NP / 4; ++c)
+      reinterpret_cast<float4*>(p)[c] = make_float4(v[4 * c], v[4 * c + 1], v[4 * c + 2], v[4 * c + 3]);
+  } else {
+#pragma unroll
+    for (int c = 0; c < NP / 2; ++c) reinterpret_cast<double2*>(p)[c] = make_double2(v[2 * c], v[2 * c + 1]);
+  }
+}
+
+// y += (sum over interior faces of A_KN u_N) for a cell of colour col (Eq. 10 couplings);
+// loadn(n, colour of n, values) fetches neighbour n.  Neighbours of colour > col are skipped
+// when zero_start (they hold zeros).
+template <int D, int N1, typename R, typename LoadN>
+__device__ __forceinline__ void add_couplings_f(const LevelConsts<R>& C, int col, bool zero_start,
+                                                const int (&nb)[2 * D], LoadN loadn, R (&y)[CD<D, N1>::NP]) {
   constexpr int NP = CD<D, N1>::NP, NQ = CD<D, N1>::NQ;
-  const LevelConsts<R>& C = P.k;
 #pragma unroll
   for (int s = 0; s < 2 * D; ++s) {
     const int dir = s >> 1;
     const int n = nb[s];
     if (n < 0 || (zero_start && (col ^ (1 << dir)) > col)) continue;
     R un[NP];
-    load_cell<D, N1, COH, TI, R>(u, n, un);
+    loadn(n, col ^ (1 << dir), un);
     const R* B = (s & 1) ? C.Bmp : C.Bpm;
 #pragma unroll
     for (int t = 0; t < NQ; ++t) {
@@ -88,6 +124,15 @@ __device__ __forceinline__ void add_couplings(const LevelParams<R>& P, const TI*
       }
     }
   }
+}
+
+// Couplings with the neighbour values read from the global vector u.
+template <int D, int N1, bool COH, typename TI, typename R>
+__device__ __forceinline__ void add_couplings(const LevelParams<R>& P, const TI* __restrict__ u, int col,
+                                              bool zero_start, const int (&nb)[2 * D], R (&y)[CD<D, N1>::NP]) {
+  constexpr int NP = CD<D, N1>::NP;
+  add_couplings_f<D, N1, R>(P.k, col, zero_start, nb,
+                            [&](int n, int, R(&un)[NP]) { load_cell<D, N1, COH, TI, R>(u, n, un); }, y);
 }
 
 // y += A_KK v (volume + own halves of interior faces + surrogate faces), reference scaling.
@@ -214,7 +259,7 @@ __device__ __forceinline__ void cell_apply(const LevelParams<R>& P, const TI* __
 #pragma unroll
   for (int i = 0; i < NP; ++i) y[i] = 0;
   add_self<D, N1, R>(P, nb, boundary_index(P, a, 1 << D), v, y);
-  add_couplings<D, N1, COH, TI, R>(P, x, a, 0, false, nb, y);
+  add_couplings<D, N1, COH, TI, R>(P, x, 0, false, nb, y);
 #pragma unroll
   for (int i = 0; i < NP; ++i) y[i] *= P.hscale;
 }
@@ -232,73 +277,82 @@ __global__ void __launch_bounds__(kCellThreads) k_apply_cell(const __grid_consta
   for (int i = 0; i < NP; ++i) y[(size_t)a * NP + i] = MODE == 1 ? f[(size_t)a * NP + i] - r[i] : r[i];
 }
 
-// One cell of one colour of the block Gauss-Seidel sweep (Eq. 16): cell a of the colour
-// starting at cs whose first nbnd cells are boundary cells (dense inverse, boundary index
-// b0 + a - cs); the others use the fast diagonalisation.  zero_start as in k_smooth.
-template <int D, int N1, bool COH, typename R>
-__device__ __forceinline__ void smooth_one(const LevelParams<R>& P, int col, int zero_start, int cs, int nbnd,
-                                           int b0, int a, const R* __restrict__ f, R* __restrict__ u) {
+// y = A_KK^{-1} t / hscale-scaled block solve of one cell: the dense inverse of boundary cell
+// bidx, or the fast diagonalisation (S^T)^(x d), 1 / (hscale sum lambda), S^(x d) when bidx < 0.
+template <int D, int N1, typename R>
+__device__ __forceinline__ void block_solve(const LevelParams<R>& P, int bidx, R (&t)[CD<D, N1>::NP],
+                                            R (&y)[CD<D, N1>::NP]) {
   constexpr int NP = CD<D, N1>::NP, NQ = CD<D, N1>::NQ;
-  const bool isB = a - cs < nbnd;
-  int nb[2 * D];
-  load_nbr<D, R>(P, a, nb);
-  R c[NP];
-#pragma unroll
-  for (int i = 0; i < NP; ++i) c[i] = 0;
-  add_couplings<D, N1, COH, R, R>(P, u, a, col, zero_start != 0, nb, c);
-  R t[NP];
-#pragma unroll
-  for (int i = 0; i < NP; ++i) t[i] = ldv<COH>(f + (size_t)a * NP + i) - P.hscale * c[i];
-  R y[NP];
-  if (isB) {
-    const R* Bi = P.binvT + (size_t)(b0 + (a - cs)) * NP * NP;
+  if (bidx >= 0) {
+    const R* Bi = P.binvT + (size_t)bidx * NP * NP;
 #pragma unroll
     for (int i = 0; i < NP; ++i) y[i] = 0;
 #pragma unroll
     for (int j = 0; j < NP; ++j)
 #pragma unroll
       for (int i = 0; i < NP; ++i) y[i] += Bi[j * NP + i] * t[j];
-  } else {
-    const LevelConsts<R>& C = P.k;
-#pragma unroll
-    for (int dir = 0; dir < D; ++dir) {            // (S^T)^(x d) t
-      R w[NP];
-#pragma unroll
-      for (int tl = 0; tl < NQ; ++tl)
-#pragma unroll
-        for (int m = 0; m < N1; ++m) {
-          R acc = 0;
-#pragma unroll
-          for (int k = 0; k < N1; ++k) acc += C.S[k * N1 + m] * t[dof<D, N1>(dir, k, tl)];
-          w[dof<D, N1>(dir, m, tl)] = acc;
-        }
-#pragma unroll
-      for (int i = 0; i < NP; ++i) t[i] = w[i];
-    }
-#pragma unroll
-    for (int i = 0; i < NP; ++i) {
-      R lsum = C.lam[i % N1] + C.lam[(i / N1) % N1];
-      if (D == 3) lsum += C.lam[i / (N1 * N1)];
-      t[i] = t[i] / (P.hscale * lsum);
-    }
-#pragma unroll
-    for (int dir = 0; dir < D; ++dir) {            // S^(x d) v
-      R w[NP];
-#pragma unroll
-      for (int tl = 0; tl < NQ; ++tl)
-#pragma unroll
-        for (int m = 0; m < N1; ++m) {
-          R acc = 0;
-#pragma unroll
-          for (int k = 0; k < N1; ++k) acc += C.S[m * N1 + k] * t[dof<D, N1>(dir, k, tl)];
-          w[dof<D, N1>(dir, m, tl)] = acc;
-        }
-#pragma unroll
-      for (int i = 0; i < NP; ++i) t[i] = w[i];
-    }
-#pragma unroll
-    for (int i = 0; i < NP; ++i) y[i] = t[i];
+    return;
   }
+  const LevelConsts<R>& C = P.k;
+#pragma unroll
+  for (int dir = 0; dir < D; ++dir) {              // (S^T)^(x d) t
+    R w[NP];
+#pragma unroll
+    for (int tl = 0; tl < NQ; ++tl)
+#pragma unroll
+      for (int m = 0; m < N1; ++m) {
+        R acc = 0;
+#pragma unroll
+        for (int k = 0; k < N1; ++k) acc += C.S[k * N1 + m] * t[dof<D, N1>(dir, k, tl)];
+        w[dof<D, N1>(dir, m, tl)] = acc;
+      }
+#pragma unroll
+    for (int i = 0; i < NP; ++i) t[i] = w[i];
+  }
+#pragma unroll
+  for (int i = 0; i < NP; ++i) {
+    R lsum = C.lam[i % N1] + C.lam[(i / N1) % N1];
+    if (D == 3) lsum += C.lam[i / (N1 * N1)];
+    t[i] = t[i] / (P.hscale * lsum);
+  }
+#pragma unroll
+  for (int dir = 0; dir < D; ++dir) {              // S^(x d) v
+    R w[NP];
+#pragma unroll
+    for (int tl = 0; tl < NQ; ++tl)
+#pragma unroll
+      for (int m = 0; m < N1; ++m) {
+        R acc = 0;
+#pragma unroll
+        for (int k = 0; k < N1; ++k) acc += C.S[m * N1 + k] * t[dof<D, N1>(dir, k, tl)];
+        w[dof<D, N1>(dir, m, tl)] = acc;
+      }
+#pragma unroll
+    for (int i = 0; i < NP; ++i) t[i] = w[i];
+  }
+#pragma unroll
+  for (int i = 0; i < NP; ++i) y[i] = t[i];
+}
+
+// One cell of one colour of the block Gauss-Seidel sweep (Eq. 16): cell a of the colour
+// starting at cs whose first nbnd cells are boundary cells (dense inverse, boundary index
+// b0 + a - cs); the others use the fast diagonalisation.  zero_start as in k_smooth.
+template <int D, int N1, bool COH, typename R>
+__device__ __forceinline__ void smooth_one(const LevelParams<R>& P, int col, int zero_start, int cs, int nbnd,
+                                           int b0, int a, const R* __restrict__ f, R* __restrict__ u) {
+  constexpr int NP = CD<D, N1>::NP;
+  const bool isB = a - cs < nbnd;
+  int nb[2 * D];
+  load_nbr<D, R>(P, a, nb);
+  R c[NP];
+#pragma unroll
+  for (int i = 0; i < NP; ++i) c[i] = 0;
+  add_couplings<D, N1, COH, R, R>(P, u, col, zero_start != 0, nb, c);
+  R t[NP];
+#pragma unroll
+  for (int i = 0; i < NP; ++i) t[i] = ldv<COH>(f + (size_t)a * NP + i) - P.hscale * c[i];
+  R y[NP];
+  block_solve<D, N1, R>(P, isB ? b0 + (a - cs) : -1, t, y);
   if (P.omega == R(1)) {
 #pragma unroll
     for (int i = 0; i < NP; ++i) u[(size_t)a * NP + i] = y[i];
@@ -398,97 +452,218 @@ __global__ void __launch_bounds__(kCellThreads) k_resid_restrict_h_cell(const __
   resid_restrict_h_one<D, false, R>(P, T, u, f, rc, cc);
 }
 
-// Prolongation into fine cell a (p = 1 on both meshes, Eq. 17): uf_a += (Ph x Ph ..) ec_parent.
+// h-transfer weight of fine node i (child o of its parent) and coarse node j, p = 1 on both
+// meshes (Eqs. 17, 18): the tensor product of the 1D child matrices.
 template <int D, typename R>
-__device__ __forceinline__ void prolong_h_one(const TransferParams<R>& T, const R* __restrict__ ec,
-                                              R* __restrict__ uf, int a) {
-  constexpr int NP = CD<D, 2>::NP;
-  const int code = T.parent_code[a];
-  if (code < 0) return;
-  const int par = code >> 3, o = code & 7;
-  R e[NP];
-#pragma unroll
-  for (int j = 0; j < NP; ++j) e[j] = ldv<true>(ec + (size_t)par * NP + j);
-#pragma unroll
-  for (int i = 0; i < NP; ++i) {
-    R acc = 0;
-#pragma unroll
-    for (int j = 0; j < NP; ++j) {
-      R wgt = T.Ph[o & 1][(i & 1) * 2 + (j & 1)] * T.Ph[(o >> 1) & 1][((i >> 1) & 1) * 2 + ((j >> 1) & 1)];
-      if (D == 3) wgt *= T.Ph[(o >> 2) & 1][((i >> 2) & 1) * 2 + ((j >> 2) & 1)];
-      acc += wgt * e[j];
-    }
-    uf[(size_t)a * NP + i] = ldv<true>(uf + (size_t)a * NP + i) + acc;
-  }
+__device__ __forceinline__ R h_weight(const TransferParams<R>& T, int o, int i, int j) {
+  R wgt = T.Ph[o & 1][(i & 1) * 2 + (j & 1)] * T.Ph[(o >> 1) & 1][((i >> 1) & 1) * 2 + ((j >> 1) & 1)];
+  if (D == 3) wgt *= T.Ph[(o >> 2) & 1][((i >> 2) & 1) * 2 + ((j >> 2) & 1)];
+  return wgt;
 }
 
+// ----------------------------------------------------------------------------------------------
 // The V-cycle below and including level `top` (all of them p = 1 h-levels) in one launch of a
-// thread-block cluster: every phase (one colour of a sweep, a fused residual/restriction, the
-// coarse solve, a prolongation) is spread over the cluster's threads and closed by a fence and
-// a hardware cluster barrier, which replaces the per-phase kernel launches.
+// thread-block cluster, with every level vector held in the cluster's shared memory.
+//
+// Layout: colour c of a level (cells [cs_c, ce_c) of the colour-major order) is cut into
+// chunks of m[c] consecutive cells, chunk k living on CTA k of the cluster; a CTA stores its
+// chunks of all colours back to back (colour c from cell slot off[c]) once for z (element
+// offset zoff) and once for the right-hand side (roff).  A CTA updates only the cells it
+// stores; neighbour, child and parent values of other CTAs are read through distributed shared
+// memory.  Every phase (one colour of a sweep, the fused residual/restriction, the coarse solve,
+// a prolongation) ends with a cluster barrier, whose release/acquire semantics order the shared
+// memory writes of the phase before the reads of the next.
+// ----------------------------------------------------------------------------------------------
+template <typename R>
+__device__ __forceinline__ int colour_of(const TailLevel<R>& L, int a, int ncol) {
+  int c = 0;
+#pragma unroll
+  for (int k = 1; k < 8; ++k)
+    if (k < ncol && a >= L.P.colour_start[k]) c = k;
+  return c;
+}
+
+// Generic address of the NP values of cell a (colour col) of vector `vo` (zoff or roff) of L.
+template <int NP, typename R>
+__device__ __forceinline__ R* tail_cell(const cooperative_groups::cluster_group& cl, R* sm, const TailLevel<R>& L,
+                                        int vo, int a, int col) {
+  const int rel = a - L.P.colour_start[col];
+  const int rk = rel / L.m[col];
+  R* p = sm + vo + (size_t)(L.off[col] + rel - rk * L.m[col]) * NP;
+  return cl.map_shared_rank(p, (unsigned)rk);
+}
+
 template <int D, typename R>
 __global__ void __launch_bounds__(kTailThreads, 1) k_vcycle_tail(const TailLevel<R>* __restrict__ TL, int top,
                                                                  const R* __restrict__ r_top, R* __restrict__ z_top,
                                                                  const double* __restrict__ coarse_inv, int pre,
-                                                                 int post) {
+                                                                 int post, int gather_off) {
   namespace cg = cooperative_groups;
-  cg::cluster_group cl = cg::this_cluster();
-  const int nthr = (int)(cl.num_blocks() * blockDim.x);
-  const int tid = (int)(cl.block_rank() * blockDim.x + threadIdx.x);
+  const cg::cluster_group cl = cg::this_cluster();
+  extern __shared__ __align__(16) unsigned char tail_smem[];
+  R* sm = reinterpret_cast<R*>(tail_smem);
+  const int rank = (int)cl.block_rank();
   constexpr int NCOL = 1 << D, NP = CD<D, 2>::NP;
-  auto phase_end = [&]() {
-    __threadfence();
-    cl.sync();
+
+  // this CTA's cells of colour col of L: fn(cell, slot)
+  auto for_own = [&](const TailLevel<R>& L, int col, auto&& fn) {
+    const int cs = L.P.colour_start[col], ce = L.P.colour_start[col + 1], m = L.m[col];
+    const int first = cs + rank * m;
+    const int cnt = min(m, ce - first);
+    for (int j = threadIdx.x; j < cnt; j += kTailThreads) fn(first + j, L.off[col] + j);
   };
+  auto loader = [&cl, sm](const TailLevel<R>& L, int vo) {
+    const TailLevel<R>* Lp = &L;
+    return [&cl, sm, Lp, vo](int n, int ncol, R(&un)[NP]) {
+      load_np_vec<NP, R>(tail_cell<NP>(cl, sm, *Lp, vo, n, ncol), un);
+    };
+  };
+  auto smooth = [&](const TailLevel<R>& L, int col, bool zs) {
+    for_own(L, col, [&](int a, int slot) {
+      const LevelParams<R>& P = L.P;
+      int nb[2 * D];
+      load_nbr<D, R>(P, a, nb);
+      R c[NP];
+#pragma unroll
+      for (int i = 0; i < NP; ++i) c[i] = 0;
+      add_couplings_f<D, 2, R>(P.k, col, zs, nb, loader(L, L.zoff), c);
+      R t[NP];
+      load_np_vec<NP, R>(sm + L.roff + (size_t)slot * NP, t);
+#pragma unroll
+      for (int i = 0; i < NP; ++i) t[i] -= P.hscale * c[i];
+      const int off = a - P.colour_start[col];
+      R y[NP];
+      block_solve<D, 2, R>(P, off < P.colour_nbnd[col] ? P.bstart[col] + off : -1, t, y);
+      R* zu = sm + L.zoff + (size_t)slot * NP;
+      if (P.omega != R(1)) {
+        R uo[NP];
+        if (zs) {
+#pragma unroll
+          for (int i = 0; i < NP; ++i) uo[i] = 0;
+        } else {
+          load_np_vec<NP, R>(zu, uo);
+        }
+#pragma unroll
+        for (int i = 0; i < NP; ++i) y[i] = (R(1) - P.omega) * uo[i] + P.omega * y[i];
+      }
+      store_np_vec<NP, R>(zu, y);
+    });
+  };
+
+  {                                                // right-hand side of the top level
+    const TailLevel<R>& L = TL[top];
+    for (int col = 0; col < NCOL; ++col)
+      for_own(L, col, [&](int a, int slot) {
+#pragma unroll
+        for (int i = 0; i < NP; ++i) sm[L.roff + (size_t)slot * NP + i] = r_top[(size_t)a * NP + i];
+      });
+    cl.sync();
+  }
   for (int l = top; l >= 1; --l) {                 // down: pre-smooth, residual, restrict
     const TailLevel<R>& L = TL[l];
-    const R* r = l == top ? r_top : L.rhs;
-    R* z = l == top ? z_top : L.z;
     if (pre == 0) {
-      for (size_t q = tid; q < (size_t)L.P.n_act * NP; q += nthr) z[q] = R(0);
-      phase_end();
+      for (int q = threadIdx.x; q < L.ncell * NP; q += kTailThreads) sm[L.zoff + q] = R(0);
+      cl.sync();
     }
     for (int k = 0; k < pre; ++k)
       for (int col = 0; col < NCOL; ++col) {
-        const int cs = L.P.colour_start[col], ce = L.P.colour_start[col + 1];
-        for (int a = cs + tid; a < ce; a += nthr)
-          smooth_one<D, 2, true, R>(L.P, col, k == 0, cs, L.P.colour_nbnd[col], L.P.bstart[col], a, r, z);
-        phase_end();
+        smooth(L, col, k == 0);
+        cl.sync();
       }
     const TailLevel<R>& Lc = TL[l - 1];
-    for (int cc = tid; cc < Lc.P.n_act; cc += nthr) resid_restrict_h_one<D, true, R>(L.P, L.T, z, r, Lc.rhs, cc);
-    phase_end();
+    for (int ccol = 0; ccol < NCOL; ++ccol)
+      for_own(Lc, ccol, [&](int cc, int slot) {
+        R out[NP];
+#pragma unroll
+        for (int j = 0; j < NP; ++j) out[j] = 0;
+#pragma unroll 1
+        for (int o = 0; o < NCOL; ++o) {
+          const int a = L.T.children[(size_t)o * L.T.n_act_c + cc];
+          if (a < 0) continue;
+          const int ca = colour_of(L, a, NCOL);
+          int nb[2 * D];
+          load_nbr<D, R>(L.P, a, nb);
+          R v[NP], y[NP], f[NP];
+          load_np_vec<NP, R>(tail_cell<NP>(cl, sm, L, L.zoff, a, ca), v);
+          load_np_vec<NP, R>(tail_cell<NP>(cl, sm, L, L.roff, a, ca), f);
+#pragma unroll
+          for (int i = 0; i < NP; ++i) y[i] = 0;
+          const int off = a - L.P.colour_start[ca];
+          add_self<D, 2, R>(L.P, nb, off < L.P.colour_nbnd[ca] ? L.P.bstart[ca] + off : -1, v, y);
+          add_couplings_f<D, 2, R>(L.P.k, ca, false, nb, loader(L, L.zoff), y);
+#pragma unroll
+          for (int i = 0; i < NP; ++i) y[i] = f[i] - L.P.hscale * y[i];
+#pragma unroll
+          for (int j = 0; j < NP; ++j) {
+            R acc = 0;
+#pragma unroll
+            for (int i = 0; i < NP; ++i) acc += h_weight<D, R>(L.T, o, i, j) * y[i];
+            out[j] += acc;
+          }
+        }
+        store_np_vec<NP, R>(sm + Lc.roff + (size_t)slot * NP, out);
+      });
+    cl.sync();
   }
   {                                                // coarse solve in FP64, one warp per row
     const TailLevel<R>& L0 = TL[0];
     const int n0 = L0.P.n_act * NP;
-    R* z0 = top == 0 ? z_top : L0.z;
-    const R* r0 = top == 0 ? r_top : L0.rhs;
+    R* g = sm + gather_off;                        // this CTA's copy of the whole coarse rhs
+    for (int a = threadIdx.x; a < L0.P.n_act; a += kTailThreads) {
+      R v[NP];
+      load_np_vec<NP, R>(tail_cell<NP>(cl, sm, L0, L0.roff, a, colour_of(L0, a, NCOL)), v);
+      store_np_vec<NP, R>(g + (size_t)a * NP, v);
+    }
+    __syncthreads();
     const int lane = threadIdx.x & 31;
-    for (int row = tid >> 5; row < n0; row += nthr >> 5) {
+    const int nwarp = (int)cl.num_blocks() * (kTailThreads / 32);
+    for (int row = rank * (kTailThreads / 32) + (threadIdx.x >> 5); row < n0; row += nwarp) {
       double acc = 0;
-      for (int c = lane; c < n0; c += 32) acc += coarse_inv[(size_t)row * n0 + c] * (double)ldv<true>(r0 + c);
+      for (int c = lane; c < n0; c += 32) acc += coarse_inv[(size_t)row * n0 + c] * (double)g[c];
 #pragma unroll
       for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
-      if (lane == 0) z0[row] = (R)acc;
+      if (lane == 0) {
+        const int cell = row / NP;
+        tail_cell<NP>(cl, sm, L0, L0.zoff, cell, colour_of(L0, cell, NCOL))[row - cell * NP] = (R)acc;
+      }
     }
-    phase_end();
+    cl.sync();
   }
   for (int l = 1; l <= top; ++l) {                 // up: prolongate, post-smooth
     const TailLevel<R>& L = TL[l];
-    const R* r = l == top ? r_top : L.rhs;
-    R* z = l == top ? z_top : L.z;
-    const R* zc = l - 1 == 0 && top == 0 ? z_top : TL[l - 1].z;
-    for (int a = tid; a < L.P.n_act; a += nthr) prolong_h_one<D, R>(L.T, zc, z, a);
-    phase_end();
+    const TailLevel<R>& Lc = TL[l - 1];
+    for (int col = 0; col < NCOL; ++col)
+      for_own(L, col, [&](int a, int slot) {
+        const int code = L.T.parent_code[a];
+        if (code < 0) return;
+        const int par = code >> 3, o = code & 7;
+        R e[NP], u[NP];
+        load_np_vec<NP, R>(tail_cell<NP>(cl, sm, Lc, Lc.zoff, par, colour_of(Lc, par, NCOL)), e);
+        R* zu = sm + L.zoff + (size_t)slot * NP;
+        load_np_vec<NP, R>(zu, u);
+#pragma unroll
+        for (int i = 0; i < NP; ++i) {
+          R acc = 0;
+#pragma unroll
+          for (int j = 0; j < NP; ++j) acc += h_weight<D, R>(L.T, o, i, j) * e[j];
+          u[i] += acc;
+        }
+        store_np_vec<NP, R>(zu, u);
+      });
+    cl.sync();
     for (int k = 0; k < post; ++k)
       for (int q = 0; q < NCOL; ++q) {
-        const int col = NCOL - 1 - q;
-        const int cs = L.P.colour_start[col], ce = L.P.colour_start[col + 1];
-        for (int a = cs + tid; a < ce; a += nthr)
-          smooth_one<D, 2, true, R>(L.P, col, 0, cs, L.P.colour_nbnd[col], L.P.bstart[col], a, r, z);
-        phase_end();
+        smooth(L, NCOL - 1 - q, false);
+        cl.sync();
       }
+  }
+  {                                                // correction of the top level out
+    const TailLevel<R>& L = TL[top];
+    for (int col = 0; col < NCOL; ++col)
+      for_own(L, col, [&](int a, int slot) {
+#pragma unroll
+        for (int i = 0; i < NP; ++i) z_top[(size_t)a * NP + i] = sm[L.zoff + (size_t)slot * NP + i];
+      });
   }
 }
 
@@ -566,55 +741,29 @@ cudaError_t launch_resid_restrict_h_cell(int dim, const LevelParams<R>& P, const
   return cudaGetLastError();
 }
 
-int tail_cluster_size(int dim, int prec) {
-  static int cached[2][2] = {{-1, -1}, {-1, -1}};
-  int& c = cached[dim == 3][prec];
-  if (c >= 0) return c;
-  c = 0;
-  for (int size : {16, 8}) {
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(size);
-    cfg.blockDim = dim3(kTailThreads);
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = size;
-    attr[0].val.clusterDim.y = 1;
-    attr[0].val.clusterDim.z = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    int nclusters = 0;
-    cudaError_t e;
-    if (dim == 2 && prec == 0) {
-      cudaFuncSetAttribute(k_vcycle_tail<2, double>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-      e = cudaOccupancyMaxActiveClusters(&nclusters, k_vcycle_tail<2, double>, &cfg);
-    } else if (dim == 2) {
-      cudaFuncSetAttribute(k_vcycle_tail<2, float>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-      e = cudaOccupancyMaxActiveClusters(&nclusters, k_vcycle_tail<2, float>, &cfg);
-    } else if (prec == 0) {
-      cudaFuncSetAttribute(k_vcycle_tail<3, double>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-      e = cudaOccupancyMaxActiveClusters(&nclusters, k_vcycle_tail<3, double>, &cfg);
-    } else {
-      cudaFuncSetAttribute(k_vcycle_tail<3, float>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-      e = cudaOccupancyMaxActiveClusters(&nclusters, k_vcycle_tail<3, float>, &cfg);
-    }
-    if (e == cudaSuccess && nclusters >= 1) {
-      c = size;
-      break;
-    }
-    cudaGetLastError();                            // clear a refused query
+size_t tail_smem_limit() {
+  static size_t limit = 0;
+  if (limit == 0) {
+    int dev = 0, optin = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    limit = optin > 1024 ? (size_t)optin - 1024 : 0;   // room for the kernels' static shared memory
   }
-  return c;
+  return limit;
 }
 
-template <typename R>
-cudaError_t launch_vcycle_tail(int dim, const TailLevel<R>* TL, int top, const R* r, R* z, const double* coarse_inv,
-                               int pre, int post, cudaStream_t s) {
-  const int size = tail_cluster_size(dim, sizeof(R) == 8 ? 0 : 1);
-  if (size == 0) return cudaErrorNotSupported;
+template <int D, typename R>
+bool tail_fits_kernel(int size, size_t smem) {
+  auto kern = k_vcycle_tail<D, R>;
+  if (cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess ||
+      cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tail_smem_limit()) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(size);
   cfg.blockDim = dim3(kTailThreads);
-  cfg.stream = s;
+  cfg.dynamicSmemBytes = smem;
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeClusterDimension;
   attr[0].val.clusterDim.x = size;
@@ -622,17 +771,45 @@ cudaError_t launch_vcycle_tail(int dim, const TailLevel<R>* TL, int top, const R
   attr[0].val.clusterDim.z = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
+  int nclusters = 0;
+  const cudaError_t e = cudaOccupancyMaxActiveClusters(&nclusters, kern, &cfg);
+  if (e != cudaSuccess) cudaGetLastError();          // clear a refused query
+  return e == cudaSuccess && nclusters >= 1;
+}
+
+bool tail_cluster_fits(int dim, int prec, int size, size_t smem) {
+  if (smem > tail_smem_limit()) return false;
+  if (dim == 2) return prec == 0 ? tail_fits_kernel<2, double>(size, smem) : tail_fits_kernel<2, float>(size, smem);
+  return prec == 0 ? tail_fits_kernel<3, double>(size, smem) : tail_fits_kernel<3, float>(size, smem);
+}
+
+template <typename R>
+cudaError_t launch_vcycle_tail(int dim, const TailLevel<R>* TL, int top, const R* r, R* z, const double* coarse_inv,
+                               int pre, int post, const TailPlan& plan, cudaStream_t s) {
+  if (plan.cluster < 1) return cudaErrorNotSupported;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(plan.cluster);
+  cfg.blockDim = dim3(kTailThreads);
+  cfg.dynamicSmemBytes = plan.smem_bytes;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = plan.cluster;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
   cudaError_t e;
-  if (dim == 2) e = cudaLaunchKernelEx(&cfg, k_vcycle_tail<2, R>, TL, top, r, z, coarse_inv, pre, post);
-  else e = cudaLaunchKernelEx(&cfg, k_vcycle_tail<3, R>, TL, top, r, z, coarse_inv, pre, post);
+  if (dim == 2) e = cudaLaunchKernelEx(&cfg, k_vcycle_tail<2, R>, TL, top, r, z, coarse_inv, pre, post, plan.gather_off);
+  else e = cudaLaunchKernelEx(&cfg, k_vcycle_tail<3, R>, TL, top, r, z, coarse_inv, pre, post, plan.gather_off);
   count_launches();
   return e;
 }
 
 template cudaError_t launch_vcycle_tail<double>(int, const TailLevel<double>*, int, const double*, double*,
-                                                const double*, int, int, cudaStream_t);
+                                                const double*, int, int, const TailPlan&, cudaStream_t);
 template cudaError_t launch_vcycle_tail<float>(int, const TailLevel<float>*, int, const float*, float*, const double*,
-                                               int, int, cudaStream_t);
+                                               int, int, const TailPlan&, cudaStream_t);
 template cudaError_t launch_apply_cell<double, double>(int, int, const LevelParams<double>&, const double*,
                                                        const double*, double*, int, cudaStream_t);
 template cudaError_t launch_apply_cell<float, float>(int, int, const LevelParams<float>&, const float*, const float*,

@@ -1,6 +1,7 @@
 // Host-side launchers of the libsbm CUDA kernels.
 #pragma once
 
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 #include "sbm_internal.h"
@@ -36,12 +37,16 @@ template <typename R>
 cudaError_t launch_resid_restrict_h_cell(int dim, const LevelParams<R>& P, const TransferParams<R>& T, const R* u,
                                         const R* f, R* rc, cudaStream_t s);
 
-// The V-cycle of levels 0..top (p = 1 h-levels) in one thread-block-cluster launch; z = M^{-1} r
-// on level top.  cudaErrorNotSupported if no cluster of 8 or more CTAs fits.
+// The V-cycle of levels 0..top (p = 1 h-levels) in one thread-block-cluster launch with the
+// level vectors in shared memory; z = M^{-1} r on level top.  cudaErrorNotSupported if the plan
+// has no cluster.
 template <typename R>
 cudaError_t launch_vcycle_tail(int dim, const TailLevel<R>* TL, int top, const R* r, R* z, const double* coarse_inv,
-                               int pre, int post, cudaStream_t s);
-int tail_cluster_size(int dim, int prec);
+                               int pre, int post, const TailPlan& plan, cudaStream_t s);
+// Largest dynamic shared memory a tail CTA may use, and whether a cluster of `size` CTAs with
+// `smem` bytes each can be resident (prec 0: FP64, 1: FP32).
+size_t tail_smem_limit();
+bool tail_cluster_fits(int dim, int prec, int size, size_t smem);
 
 // y = A x (mode 0) or y = f - A x (mode 1) on one level; TI is the input precision, R the
 // compute / output precision.
@@ -98,5 +103,36 @@ cudaError_t launch_cast(const TI* x, TO* y, size_t N, cudaStream_t s);
 // c = a + b (k <= 32 entries), c[k] = hn at index k
 cudaError_t launch_hess_column(const double* h1, const double* h2, const double* hn, int k, double* col,
                                cudaStream_t s);
+
+// ---------------------------------------------------------------- learned boundary-cell correction
+template <typename TI>
+cudaError_t launch_mlp_features(int n_bnd, int npatch, int np, int nstat, int Fpad, const int* patch,
+                                const float* stat, const TI* res, __nv_bfloat16* X, float* s, cudaStream_t st);
+// C = opA(A) opB(B) (+ bias) (relu), BF16 in, FP32 accumulate; outputs FP32 Cf and/or BF16 Cb.
+cudaError_t launch_gemm_bf16(int M, int N, int K, int ta, int tb, const __nv_bfloat16* A, int lda,
+                             const __nv_bfloat16* B, int ldb, const float* bias, int relu, float* Cf,
+                             __nv_bfloat16* Cb, int ldc, cudaStream_t s);
+cudaError_t launch_mse_grad(int rows, int O, const float* Y, const float* T, float* dYf, __nv_bfloat16* dYb,
+                            float inv_count, float* loss_partial, int nblk, cudaStream_t s);
+cudaError_t launch_relu_mask(int n, float* dH, const __nv_bfloat16* H, __nv_bfloat16* dZb, cudaStream_t s);
+cudaError_t launch_colsum(int rows, int cols, const float* D, float* g, cudaStream_t s);
+cudaError_t launch_adam(int n, float* p, const float* g, float* m, float* v, __nv_bfloat16* pb, float lr, float b1,
+                        float b2, float eps, int t, cudaStream_t s);
+cudaError_t launch_to_bf16(int n, const float* x, __nv_bfloat16* y, cudaStream_t s);
+template <typename TU>
+cudaError_t launch_mlp_targets(int n_bnd, int np, const int* cell, const TU* u, const float* s, float* T,
+                               cudaStream_t st);
+template <typename TZ>
+cudaError_t launch_mlp_scatter(int n_bnd, int np, int ldy, const int* cell, const float* Y, const float* s,
+                               float scale, TZ* z, cudaStream_t st);
+cudaError_t launch_rows_gather(int rows, int width, const int* idx, const __nv_bfloat16* X, __nv_bfloat16* Xb,
+                               int owidth, const float* T, float* Tb, cudaStream_t s);
+cudaError_t launch_axpy_f(size_t n, float a, const float* x, float* y, cudaStream_t s);
+// Xb = bf16(X) with rows padded from F to Fpad columns with zeros, and back.
+cudaError_t launch_pack_bf16(int rows, int F, int Fpad, const float* X, __nv_bfloat16* Xb, cudaStream_t s);
+cudaError_t launch_unpack_bf16(int rows, int F, int Fpad, const __nv_bfloat16* Xb, float* X, cudaStream_t s);
+// y += x
+template <typename R>
+cudaError_t launch_add(size_t n, const R* x, R* y, cudaStream_t s);
 
 }  // namespace sbm

@@ -54,6 +54,12 @@ struct HostLevel {
   double Bpp[kMaxN1 * kMaxN1] = {};  // own half of the left interior face (this cell is K+)
   double S[kMaxN1 * kMaxN1] = {}, lam[kMaxN1] = {};   // W-orthonormal eigenvectors / values of L[3]
   std::vector<double> coarse_inv;   // [N*N] on the coarsest level only
+  // learned boundary-cell correction: per boundary cell the compact indices of the 3^dim patch
+  // cells K + o (o in {-1,0,1}^dim, x fastest; -1 inactive or outside) and the static features
+  // [d/h per (slot, face point, component)], kappa, [surrogate mask per slot]
+  std::vector<int> patch;           // [n_bnd][3^dim]
+  std::vector<int> bnd_cell;        // [n_bnd] compact index of each boundary cell
+  std::vector<double> mlp_static;   // [n_bnd][2 dim nq dim + 1 + 2 dim]
   int n_dof() const { return n_act * np; }
   bool is_boundary(int a, int* bidx) const;
 };
@@ -117,14 +123,25 @@ struct TransferParams {
   R Pp[kMaxN1 * kMaxN1];           // p: Pp[i*nc + j] = l^c_j(x^f_i)
 };
 
-// One level of the cluster V-cycle tail (device memory): parameters, the transfer to the next
-// coarser level, and the level's work vectors.
+// One level of the cluster V-cycle tail (device memory): parameters, the transfer from the next
+// coarser level, and where the level's vectors live in every CTA's shared memory: colour c is
+// cut into chunks of m[c] cells (chunk k on CTA k), stored from cell slot off[c]; z and the
+// right-hand side start at element offsets zoff and roff, ncell cell slots each.
 template <typename R>
 struct TailLevel {
   LevelParams<R> P;
   TransferParams<R> T;
-  R* z;
-  R* rhs;
+  int m[8], off[8];
+  int ncell, zoff, roff;
+};
+
+// Launch shape of the cluster tail of one precision: cluster size (CTAs), dynamic shared
+// memory per CTA, and the element offset of the coarse right-hand-side gather buffer.
+struct TailPlan {
+  int top = -1;
+  int cluster = 0;
+  size_t smem_bytes = 0;
+  int gather_off = 0;
 };
 
 }  // namespace sbm

@@ -683,6 +683,7 @@ HostLevel build_level(const sbm_setup_desc& d, int n, int p) {
   const int S = ipow(s, dim);
   const size_t nbg = (size_t)ipow(n, dim);
   std::vector<unsigned char> active(nbg, 0);
+  std::vector<int> counts(nbg, 0);
   const double thr = d.lambda * S;
   parallel_for((int)nbg, [&](int b, int e) {
     for (int lin = b; lin < e; ++lin) {
@@ -697,6 +698,7 @@ HostLevel build_level(const sbm_setup_desc& d, int n, int p) {
         }
         count += sh.phi(X) < 0.0;
       }
+      counts[lin] = count;
       active[lin] = d.lambda_inclusive ? (count >= thr) : (count > thr);
     }
   });
@@ -845,6 +847,34 @@ HostLevel build_level(const sbm_setup_desc& d, int n, int p) {
     }
   }
   L.n_sface = (int)L.sf_cell.size();
+
+  // learned-correction data of boundary cells: 3^d patch table and static features
+  {
+    const int npatch = ipow(3, dim), nstat = 2 * dim * nq * dim + 1 + 2 * dim;
+    L.patch.assign((size_t)L.n_bnd * npatch, -1);
+    L.bnd_cell = bcell;
+    L.mlp_static.assign((size_t)L.n_bnd * nstat, 0.0);
+    for (int b = 0; b < L.n_bnd; ++b) {
+      const int a = bcell[b];
+      for (int o = 0; o < npatch; ++o) {
+        int j[3] = {L.cell[3 * a], L.cell[3 * a + 1], L.cell[3 * a + 2]};
+        bool inside = true;
+        for (int k = 0, oo = o; k < dim; ++k, oo /= 3) {
+          j[k] += oo % 3 - 1;
+          inside = inside && j[k] >= 0 && j[k] < n;
+        }
+        if (inside) L.patch[(size_t)b * npatch + o] = L.bg2act[lin_of(j)];
+      }
+      double* st = &L.mlp_static[(size_t)b * nstat];
+      for (int slot = 0; slot < L.nslot; ++slot)
+        for (int t = 0; t < nq; ++t)
+          for (int k = 0; k < dim; ++k)
+            st[(slot * nq + t) * dim + k] = L.dhat[(((size_t)b * L.nslot + slot) * dim + k) * nq + t];
+      st[2 * dim * nq * dim] = (double)counts[lin_of(&L.cell[3 * a])] / S;
+      for (int slot = 0; slot < L.nslot; ++slot)
+        st[2 * dim * nq * dim + 1 + slot] = L.nbr[(size_t)slot * L.n_act + a] < 0 ? 1.0 : 0.0;
+    }
+  }
 
   // dense blocks A_KK of boundary cells (Eq. 14) and their inverses, stored transposed
   L.binvT.assign((size_t)L.n_bnd * np * np, 0.0);
