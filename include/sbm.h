@@ -90,6 +90,9 @@ typedef struct {
                          /* vectors in shared memory (the largest such level that fits starts    */
                          /* it); 0: library default (none); < 0: never                            */
   int tail_cluster_ctas; /* CTAs of that cluster: 1, 2, 4, 8 or 16; 0: 16, else 8                  */
+  int launch_overlap;    /* > 0: the level and Krylov kernels use programmatic dependent launch,  */
+                         /* so each may be scheduled while its predecessor finishes; < 0: plain   */
+                         /* stream-ordered launches; 0: on with the FP32 V-cycle, off with FP64   */
   int cell_kernel_min_cells; /* launches over at least this many cells use one thread per cell   */
                          /* when (p+1)^d <= 16; 0: always in FP32, never in FP64; < 0: never       */
   void* stream;          /* cudaStream_t for every launch of this context                        */

@@ -867,7 +867,13 @@ double read_loss(Mlp& M, int rows) {
   return t / ((double)rows * M.O);
 }
 
-Context* ctx_of(void* p) { return static_cast<Context*>(p); }
+// The context handle of an ABI call; also selects, for the calling thread, whether the
+// launches of this call use programmatic dependent launch (the context's launch_overlap).
+Context* ctx_of(void* p) {
+  Context* C = static_cast<Context*>(p);
+  if (C) pdl_enabled() = C->desc.launch_overlap > 0 || (C->desc.launch_overlap == 0 && C->desc.precision == SBM_F32);
+  return C;
+}
 Mlp* mlp_of(void* p) { return static_cast<Mlp*>(p); }
 
 int check_level(const Context* C, int& level) {

@@ -268,6 +268,7 @@ template <int D, int N1, typename TI, typename R, int MODE>
 __global__ void __launch_bounds__(kCellThreads) k_apply_cell(const __grid_constant__ LevelParams<R> P,
                                                              const TI* __restrict__ x, const R* __restrict__ f,
                                                              R* __restrict__ y) {
+  pdl_entry();
   constexpr int NP = CD<D, N1>::NP;
   const int a = blockIdx.x * kCellThreads + threadIdx.x;
   if (a >= P.n_act) return;
@@ -371,6 +372,7 @@ template <int D, int N1, typename R>
 __global__ void __launch_bounds__(kCellThreads) k_smooth_cell(const __grid_constant__ LevelParams<R> P, int col,
                                                               int zero_start, int cs, int nbnd, int ce, int nblk_b,
                                                               int b0, const R* __restrict__ f, R* __restrict__ u) {
+  pdl_entry();
   const bool isB = (int)blockIdx.x < nblk_b;
   const int first = isB ? cs + blockIdx.x * kCellThreads : cs + nbnd + (blockIdx.x - nblk_b) * kCellThreads;
   const int last = isB ? cs + nbnd : ce;
@@ -385,6 +387,7 @@ __global__ void __launch_bounds__(kCellThreads) k_resid_restrict_p_cell(const __
                                                                         const __grid_constant__ TransferParams<R> T,
                                                                         const R* __restrict__ u,
                                                                         const R* __restrict__ f, R* __restrict__ rc) {
+  pdl_entry();
   constexpr int NP = CD<D, N1>::NP;
   constexpr int NPC = D == 2 ? NC * NC : NC * NC * NC;
   const int a = blockIdx.x * kCellThreads + threadIdx.x;
@@ -447,6 +450,7 @@ __global__ void __launch_bounds__(kCellThreads) k_resid_restrict_h_cell(const __
                                                                         const __grid_constant__ TransferParams<R> T,
                                                                         const R* __restrict__ u,
                                                                         const R* __restrict__ f, R* __restrict__ rc) {
+  pdl_entry();
   const int cc = blockIdx.x * kCellThreads + threadIdx.x;
   if (cc >= T.n_act_c) return;
   resid_restrict_h_one<D, false, R>(P, T, u, f, rc, cc);
@@ -688,8 +692,8 @@ cudaError_t launch_apply_cell(int dim, int p, const LevelParams<R>& P, const TI*
   if (P.n_act == 0) return cudaSuccess;
 #define SBM_AC(D, N1)                                                                           \
   {                                                                                             \
-    if (mode == 0) k_apply_cell<D, N1, TI, R, 0><<<cdiv(P.n_act, kCellThreads), kCellThreads, 0, s>>>(P, x, f, y); \
-    else k_apply_cell<D, N1, TI, R, 1><<<cdiv(P.n_act, kCellThreads), kCellThreads, 0, s>>>(P, x, f, y);          \
+    if (mode == 0) SBM_PDL((k_apply_cell<D, N1, TI, R, 0>), cdiv(P.n_act, kCellThreads), kCellThreads, 0, s, P, x, f, y); \
+    else SBM_PDL((k_apply_cell<D, N1, TI, R, 1>), cdiv(P.n_act, kCellThreads), kCellThreads, 0, s, P, x, f, y);          \
   }
   SBM_CELL_DISPATCH(dim, p, SBM_AC);
 #undef SBM_AC
@@ -708,7 +712,7 @@ cudaError_t launch_smooth_cell(int dim, int p, const LevelParams<R>& P, int reve
     const int nblk_b = (int)cdiv(nbnd, kCellThreads), nblk_i = (int)cdiv(ce - cs - nbnd, kCellThreads);
     if (nblk_b + nblk_i == 0) continue;
 #define SBM_SC(D, N1)                                                                                    \
-  k_smooth_cell<D, N1, R><<<nblk_b + nblk_i, kCellThreads, 0, s>>>(P, col, zero_start, cs, nbnd, ce, nblk_b, \
+  SBM_PDL((k_smooth_cell<D, N1, R>), nblk_b + nblk_i, kCellThreads, 0, s, P, col, zero_start, cs, nbnd, ce, nblk_b, \
                                                                    P.bstart[col], f, u);
     SBM_CELL_DISPATCH(dim, p, SBM_SC);
 #undef SBM_SC
@@ -722,8 +726,8 @@ cudaError_t launch_resid_restrict_p_cell(int dim, int pf, const LevelParams<R>& 
                                         const R* u, const R* f, R* rc, cudaStream_t s) {
   if (P.n_act == 0) return cudaSuccess;
   const unsigned g = cdiv(P.n_act, kCellThreads);
-  if (dim == 2 && pf == 2) k_resid_restrict_p_cell<2, 3, 2, R><<<g, kCellThreads, 0, s>>>(P, T, u, f, rc);
-  else if (dim == 2 && pf == 3) k_resid_restrict_p_cell<2, 4, 3, R><<<g, kCellThreads, 0, s>>>(P, T, u, f, rc);
+  if (dim == 2 && pf == 2) SBM_PDL((k_resid_restrict_p_cell<2, 3, 2, R>), g, kCellThreads, 0, s, P, T, u, f, rc);
+  else if (dim == 2 && pf == 3) SBM_PDL((k_resid_restrict_p_cell<2, 4, 3, R>), g, kCellThreads, 0, s, P, T, u, f, rc);
   else return cudaErrorInvalidValue;
   count_launches();
   return cudaGetLastError();
@@ -734,8 +738,8 @@ cudaError_t launch_resid_restrict_h_cell(int dim, const LevelParams<R>& P, const
                                         const R* f, R* rc, cudaStream_t s) {
   if (T.n_act_c == 0) return cudaSuccess;
   const unsigned g = cdiv(T.n_act_c, kCellThreads);
-  if (dim == 2) k_resid_restrict_h_cell<2, R><<<g, kCellThreads, 0, s>>>(P, T, u, f, rc);
-  else if (dim == 3) k_resid_restrict_h_cell<3, R><<<g, kCellThreads, 0, s>>>(P, T, u, f, rc);
+  if (dim == 2) SBM_PDL((k_resid_restrict_h_cell<2, R>), g, kCellThreads, 0, s, P, T, u, f, rc);
+  else if (dim == 3) SBM_PDL((k_resid_restrict_h_cell<3, R>), g, kCellThreads, 0, s, P, T, u, f, rc);
   else return cudaErrorInvalidValue;
   count_launches();
   return cudaGetLastError();

@@ -51,6 +51,7 @@ template <int NV>
 __global__ void __launch_bounds__(kDotThreads) k_multi_dot(const double* __restrict__ V, size_t ldv,
                                                            const double* __restrict__ w, size_t N,
                                                            double* __restrict__ partial) {
+  pdl_entry();
   double acc[NV];
 #pragma unroll
   for (int k = 0; k < NV; ++k) acc[k] = 0.0;
@@ -82,6 +83,7 @@ template <int NV, bool NORM>
 __global__ void __launch_bounds__(kDotThreads) k_axpy_dot(const double* __restrict__ V, size_t ldv,
                                                           const double* __restrict__ h, double* __restrict__ w,
                                                           size_t N, int nv, double* __restrict__ partial) {
+  pdl_entry();
   constexpr int NA = NORM ? 1 : NV;            // accumulators
   __shared__ double hs[kMaxVec];
   if (threadIdx.x < nv) hs[threadIdx.x] = h[threadIdx.x];
@@ -116,6 +118,7 @@ __global__ void __launch_bounds__(kDotThreads) k_axpy_dot(const double* __restri
 // order of the additions is fixed for a given number of blocks (deterministic results).
 __global__ void __launch_bounds__(1024) k_reduce_partials(const double* __restrict__ partial, int nblk, int nv,
                                                           double* __restrict__ out, int take_sqrt) {
+  pdl_entry();
   const int k = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (k >= nv) return;
   double s = 0.0;
@@ -128,6 +131,7 @@ template <typename TZ>
 __global__ void __launch_bounds__(256) k_multi_axpy(const TZ* __restrict__ Z, size_t ldz, int nv,
                                                     const double* __restrict__ coef, double sign,
                                                     double* __restrict__ w, size_t N) {
+  pdl_entry();
   __shared__ double cf[kMaxVec];
   if (threadIdx.x < nv) cf[threadIdx.x] = sign * coef[threadIdx.x];
   __syncthreads();
@@ -141,6 +145,7 @@ __global__ void __launch_bounds__(256) k_multi_axpy(const TZ* __restrict__ Z, si
 
 __global__ void k_div_scalar(const double* __restrict__ w, const double* __restrict__ s, double* __restrict__ v,
                              size_t N) {
+  pdl_entry();
   const double inv = 1.0 / s[0];
   const size_t stride = (size_t)gridDim.x * blockDim.x;
   for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += stride) v[i] = w[i] * inv;
@@ -148,11 +153,13 @@ __global__ void k_div_scalar(const double* __restrict__ w, const double* __restr
 
 template <typename TI, typename TO>
 __global__ void k_cast(const TI* __restrict__ x, TO* __restrict__ y, size_t N) {
+  pdl_entry();
   const size_t stride = (size_t)gridDim.x * blockDim.x;
   for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += stride) y[i] = (TO)x[i];
 }
 
 __global__ void k_hess_column(const double* h1, const double* h2, const double* hn, int k, double* col) {
+  pdl_entry();
   const int i = threadIdx.x;
   if (i < k) col[i] = h1[i] + h2[i];
   if (i == k) col[k] = hn[0];
@@ -175,6 +182,11 @@ unsigned grid_for(size_t N) {
 
 std::atomic<long long> g_kernel_launches{0};
 
+bool& pdl_enabled() {
+  thread_local bool on = true;
+  return on;
+}
+
 int dot_blocks(size_t N) {
   size_t g = (N + kDotChunk - 1) / kDotChunk;
   if (g < 1) g = 1;
@@ -188,7 +200,7 @@ cudaError_t launch_multi_dot(const double* V, size_t ldv, int nv, const double* 
   const int nblk = dot_blocks(N);
   switch (nv) {
 #define SBM_DOT_CASE(K) \
-  case K: k_multi_dot<K><<<nblk, kDotThreads, 0, s>>>(V, ldv, w, N, partial); break;
+  case K: SBM_PDL((k_multi_dot<K>), nblk, kDotThreads, 0, s, V, ldv, w, N, partial); break;
     SBM_DOT_CASE(1) SBM_DOT_CASE(2) SBM_DOT_CASE(3) SBM_DOT_CASE(4) SBM_DOT_CASE(5) SBM_DOT_CASE(6)
     SBM_DOT_CASE(7) SBM_DOT_CASE(8) SBM_DOT_CASE(9) SBM_DOT_CASE(10) SBM_DOT_CASE(11) SBM_DOT_CASE(12)
     SBM_DOT_CASE(13) SBM_DOT_CASE(14) SBM_DOT_CASE(15) SBM_DOT_CASE(16) SBM_DOT_CASE(17) SBM_DOT_CASE(18)
@@ -197,7 +209,7 @@ cudaError_t launch_multi_dot(const double* V, size_t ldv, int nv, const double* 
     SBM_DOT_CASE(31) SBM_DOT_CASE(32)
 #undef SBM_DOT_CASE
   }
-  k_reduce_partials<<<1, 32 * nv, 0, s>>>(partial, nblk, nv, out, take_sqrt);
+  SBM_PDL(k_reduce_partials, 1, 32 * nv, 0, s, partial, nblk, nv, out, take_sqrt);
   count_launches(2);
   return cudaGetLastError();
 }
@@ -208,7 +220,7 @@ cudaError_t launch_axpy_dot(const double* V, size_t ldv, int nv, const double* h
   const int nblk = dot_blocks(N);
   switch (nv) {
 #define SBM_AD_CASE(K) \
-  case K: k_axpy_dot<K, false><<<nblk, kDotThreads, 0, s>>>(V, ldv, h, w, N, nv, partial); break;
+  case K: SBM_PDL((k_axpy_dot<K, false>), nblk, kDotThreads, 0, s, V, ldv, h, w, N, nv, partial); break;
     SBM_AD_CASE(1) SBM_AD_CASE(2) SBM_AD_CASE(3) SBM_AD_CASE(4) SBM_AD_CASE(5) SBM_AD_CASE(6)
     SBM_AD_CASE(7) SBM_AD_CASE(8) SBM_AD_CASE(9) SBM_AD_CASE(10) SBM_AD_CASE(11) SBM_AD_CASE(12)
     SBM_AD_CASE(13) SBM_AD_CASE(14) SBM_AD_CASE(15) SBM_AD_CASE(16) SBM_AD_CASE(17) SBM_AD_CASE(18)
@@ -217,7 +229,7 @@ cudaError_t launch_axpy_dot(const double* V, size_t ldv, int nv, const double* h
     SBM_AD_CASE(31) SBM_AD_CASE(32)
 #undef SBM_AD_CASE
   }
-  k_reduce_partials<<<1, 32 * nv, 0, s>>>(partial, nblk, nv, out, 0);
+  SBM_PDL(k_reduce_partials, 1, 32 * nv, 0, s, partial, nblk, nv, out, 0);
   count_launches(2);
   return cudaGetLastError();
 }
@@ -226,8 +238,8 @@ cudaError_t launch_axpy_norm(const double* V, size_t ldv, int nv, const double* 
                              double* partial, double* out, cudaStream_t s) {
   if (nv < 1 || nv > kMaxVec) return cudaErrorInvalidValue;
   const int nblk = dot_blocks(N);
-  k_axpy_dot<0, true><<<nblk, kDotThreads, 0, s>>>(V, ldv, h, w, N, nv, partial);
-  k_reduce_partials<<<1, 32, 0, s>>>(partial, nblk, 1, out, 1);
+  SBM_PDL((k_axpy_dot<0, true>), nblk, kDotThreads, 0, s, V, ldv, h, w, N, nv, partial);
+  SBM_PDL(k_reduce_partials, 1, 32, 0, s, partial, nblk, 1, out, 1);
   count_launches(2);
   return cudaGetLastError();
 }
@@ -236,27 +248,27 @@ template <typename TZ>
 cudaError_t launch_multi_axpy(const TZ* Z, size_t ldz, int nv, const double* coef, double sign, double* w,
                               size_t N, cudaStream_t s) {
   if (nv < 1 || nv > kMaxVec) return cudaErrorInvalidValue;
-  k_multi_axpy<TZ><<<grid_for(N), 256, 0, s>>>(Z, ldz, nv, coef, sign, w, N);
+  SBM_PDL((k_multi_axpy<TZ>), grid_for(N), 256, 0, s, Z, ldz, nv, coef, sign, w, N);
   count_launches();
   return cudaGetLastError();
 }
 
 cudaError_t launch_div_scalar(const double* w, const double* sc, double* v, size_t N, cudaStream_t s) {
-  k_div_scalar<<<grid_for(N), 256, 0, s>>>(w, sc, v, N);
+  SBM_PDL(k_div_scalar, grid_for(N), 256, 0, s, w, sc, v, N);
   count_launches();
   return cudaGetLastError();
 }
 
 template <typename TI, typename TO>
 cudaError_t launch_cast(const TI* x, TO* y, size_t N, cudaStream_t s) {
-  k_cast<TI, TO><<<grid_for(N), 256, 0, s>>>(x, y, N);
+  SBM_PDL((k_cast<TI, TO>), grid_for(N), 256, 0, s, x, y, N);
   count_launches();
   return cudaGetLastError();
 }
 
 cudaError_t launch_hess_column(const double* h1, const double* h2, const double* hn, int k, double* col,
                                cudaStream_t s) {
-  k_hess_column<<<1, 64, 0, s>>>(h1, h2, hn, k, col);
+  SBM_PDL(k_hess_column, 1, 64, 0, s, h1, h2, hn, k, col);
   count_launches();
   return cudaGetLastError();
 }

@@ -219,6 +219,7 @@ __device__ __forceinline__ R apply_dof(const LevelParams<R>& P, const LevelConst
 template <int D, int N1, typename TI, typename R, int MODE>
 __global__ void __launch_bounds__(256) k_apply(const __grid_constant__ LevelParams<R> P, const TI* __restrict__ x,
                                                const R* __restrict__ f, R* __restrict__ y) {
+  pdl_entry();
   using Dm = Dims<D, N1>;
   constexpr int NP = Dm::NP, NQ = Dm::NQ, NS = Dm::NS, CPB = Dm::CPB;
   __shared__ LevelConsts<R> C;
@@ -243,6 +244,7 @@ __global__ void __launch_bounds__(256) k_resid_restrict_p(const __grid_constant_
                                                           const __grid_constant__ TransferParams<R> T,
                                                           const R* __restrict__ u, const R* __restrict__ f,
                                                           R* __restrict__ rc) {
+  pdl_entry();
   using Dm = Dims<D, N1>;
   constexpr int NP = Dm::NP, NQ = Dm::NQ, NS = Dm::NS, CPB = Dm::CPB;
   constexpr int NPC = D == 2 ? NC * NC : NC * NC * NC;
@@ -289,6 +291,7 @@ __global__ void __launch_bounds__(256) k_resid_restrict_h(const __grid_constant_
                                                           const __grid_constant__ TransferParams<R> T,
                                                           const R* __restrict__ u, const R* __restrict__ f,
                                                           R* __restrict__ rc) {
+  pdl_entry();
   using Dm = Dims<D, 2>;
   constexpr int NP = Dm::NP, NQ = Dm::NQ, NS = Dm::NS, CPB = Dm::CPB;
   constexpr int NCH = 1 << D, CPC = CPB / NCH;       // children per coarse cell, coarse cells per block
@@ -351,6 +354,7 @@ template <int D, int N1, typename R>
 __global__ void __launch_bounds__(256) k_smooth(const __grid_constant__ LevelParams<R> P, int col, int zero_start,
                                                 int cs, int nbnd, int ce, int nblk_b, int b0,
                                                 const R* __restrict__ f, R* __restrict__ u) {
+  pdl_entry();
   using Dm = Dims<D, N1>;
   constexpr int NP = Dm::NP, NS = Dm::NS, CPB = Dm::CPB;
   __shared__ LevelConsts<R> C;
@@ -456,6 +460,7 @@ __global__ void __launch_bounds__(256) k_smooth(const __grid_constant__ LevelPar
 template <int D, int NF, int NC, typename R>
 __global__ void __launch_bounds__(256) k_restrict(const __grid_constant__ TransferParams<R> T,
                                                   const R* __restrict__ rf, R* __restrict__ rc) {
+  pdl_entry();
   constexpr int NPF = D == 2 ? NF * NF : NF * NF * NF;
   constexpr int NPC = D == 2 ? NC * NC : NC * NC * NC;
   const size_t gid = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -500,6 +505,7 @@ __global__ void __launch_bounds__(256) k_restrict(const __grid_constant__ Transf
 template <int D, int NF, int NC, typename R>
 __global__ void __launch_bounds__(256) k_prolong(const __grid_constant__ TransferParams<R> T,
                                                  const R* __restrict__ ec, R* __restrict__ uf) {
+  pdl_entry();
   constexpr int NPF = D == 2 ? NF * NF : NF * NF * NF;
   constexpr int NPC = D == 2 ? NC * NC : NC * NC * NC;
   const size_t gid = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -540,6 +546,7 @@ __global__ void __launch_bounds__(256) k_prolong(const __grid_constant__ Transfe
 template <typename T>
 __global__ void __launch_bounds__(256) k_coarse(const double* __restrict__ Ainv, int N, const T* __restrict__ r,
                                                 T* __restrict__ e) {
+  pdl_entry();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int row = blockIdx.x * (blockDim.x >> 5) + warp;
   if (row >= N) return;
@@ -576,8 +583,8 @@ cudaError_t launch_apply(int dim, int p, const LevelParams<R>& P, const TI* x, c
   {                                                                                      \
     using Dm = Dims<D, N1>;                                                              \
     const unsigned grid = ceil_div(P.n_act, Dm::CPB);                                    \
-    if (mode == 0) k_apply<D, N1, TI, R, 0><<<grid, Dm::NT, 0, s>>>(P, x, f, y);         \
-    else k_apply<D, N1, TI, R, 1><<<grid, Dm::NT, 0, s>>>(P, x, f, y);                   \
+    if (mode == 0) SBM_PDL((k_apply<D, N1, TI, R, 0>), grid, Dm::NT, 0, s, P, x, f, y);         \
+    else SBM_PDL((k_apply<D, N1, TI, R, 1>), grid, Dm::NT, 0, s, P, x, f, y);                   \
     count_launches();                                                                    \
   }
   SBM_DISPATCH_DP(dim, p, SBM_APPLY);
@@ -601,7 +608,7 @@ cudaError_t launch_smooth(int dim, int p, const LevelParams<R>& P, int reverse, 
     const int nblk_b = (int)ceil_div(nbnd, Dm::CPB);                                               \
     const int nblk_i = (int)ceil_div(ce - cs - nbnd, Dm::CPB);                                     \
     if (nblk_b + nblk_i > 0) {                                                                     \
-      k_smooth<D, N1, R><<<nblk_b + nblk_i, Dm::NT, 0, s>>>(P, col, zero_start, cs, nbnd, ce, nblk_b,   \
+      SBM_PDL((k_smooth<D, N1, R>), nblk_b + nblk_i, Dm::NT, 0, s, P, col, zero_start, cs, nbnd, ce, nblk_b,   \
                                                             P.bstart[col], f, u);                    \
       count_launches();                                                                            \
     }                                                                                              \
@@ -632,7 +639,7 @@ cudaError_t launch_resid_restrict_p(int dim, int pf, const LevelParams<R>& P, co
 #define SBM_RRP(D, N1, NC)                                                                         \
   {                                                                                                \
     using Dm = Dims<D, N1>;                                                                        \
-    k_resid_restrict_p<D, N1, NC, R><<<ceil_div(P.n_act, Dm::CPB), Dm::NT, 0, s>>>(P, T, u, f, rc); \
+    SBM_PDL((k_resid_restrict_p<D, N1, NC, R>), ceil_div(P.n_act, Dm::CPB), Dm::NT, 0, s, P, T, u, f, rc); \
     count_launches();                                                                              \
   }
   if (dim == 2 && pf == 2) { SBM_RRP(2, 3, 2); }
@@ -651,10 +658,10 @@ cudaError_t launch_resid_restrict_h(int dim, const LevelParams<R>& P, const Tran
   if (P.cell_min > 0 && T.n_act_f >= P.cell_min) return launch_resid_restrict_h_cell<R>(dim, P, T, u, f, rc, s);
   if (dim == 2) {
     using Dm = Dims<2, 2>;
-    k_resid_restrict_h<2, R><<<ceil_div(T.n_act_c, Dm::CPB / 4), Dm::NT, 0, s>>>(P, T, u, f, rc);
+    SBM_PDL((k_resid_restrict_h<2, R>), ceil_div(T.n_act_c, Dm::CPB / 4), Dm::NT, 0, s, P, T, u, f, rc);
   } else if (dim == 3) {
     using Dm = Dims<3, 2>;
-    k_resid_restrict_h<3, R><<<ceil_div(T.n_act_c, Dm::CPB / 8), Dm::NT, 0, s>>>(P, T, u, f, rc);
+    SBM_PDL((k_resid_restrict_h<3, R>), ceil_div(T.n_act_c, Dm::CPB / 8), Dm::NT, 0, s, P, T, u, f, rc);
   } else {
     return cudaErrorInvalidValue;
   }
@@ -668,7 +675,7 @@ cudaError_t launch_restrict(int dim, int pf, int pc, const TransferParams<R>& T,
 #define SBM_RESTRICT(D, NF, NC)                                                   \
   {                                                                               \
     const size_t n = (size_t)T.n_act_c * (D == 2 ? NC * NC : NC * NC * NC);       \
-    k_restrict<D, NF, NC, R><<<ceil_div(n, 256), 256, 0, s>>>(T, rf, rc);         \
+    SBM_PDL((k_restrict<D, NF, NC, R>), ceil_div(n, 256), 256, 0, s, T, rf, rc);         \
     count_launches();                                                             \
   }
   SBM_DISPATCH_T(dim, pf, pc, SBM_RESTRICT);
@@ -682,7 +689,7 @@ cudaError_t launch_prolong(int dim, int pf, int pc, const TransferParams<R>& T, 
 #define SBM_PROLONG(D, NF, NC)                                                    \
   {                                                                               \
     const size_t n = (size_t)T.n_act_f * (D == 2 ? NF * NF : NF * NF * NF);       \
-    k_prolong<D, NF, NC, R><<<ceil_div(n, 256), 256, 0, s>>>(T, ec, uf);          \
+    SBM_PDL((k_prolong<D, NF, NC, R>), ceil_div(n, 256), 256, 0, s, T, ec, uf);          \
     count_launches();                                                             \
   }
   SBM_DISPATCH_T(dim, pf, pc, SBM_PROLONG);
@@ -693,7 +700,7 @@ cudaError_t launch_prolong(int dim, int pf, int pc, const TransferParams<R>& T, 
 template <typename T>
 cudaError_t launch_coarse(const double* Ainv, int N, const T* r, T* e, cudaStream_t s) {
   if (N == 0) return cudaSuccess;
-  k_coarse<T><<<ceil_div(N, 8), 256, 0, s>>>(Ainv, N, r, e);
+  SBM_PDL((k_coarse<T>), ceil_div(N, 8), 256, 0, s, Ainv, N, r, e);
   count_launches();
   return cudaGetLastError();
 }

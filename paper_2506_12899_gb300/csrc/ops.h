@@ -15,6 +15,46 @@ namespace sbm {
 extern std::atomic<long long> g_kernel_launches;
 inline void count_launches(long long n = 1) { g_kernel_launches.fetch_add(n, std::memory_order_relaxed); }
 
+// Programmatic dependent launch.  A kernel launched through SBM_PDL may be scheduled while the
+// previous kernel of its stream is still running; it starts with pdl_entry(), which waits until
+// that kernel has completed and its memory operations are visible (griddepcontrol.wait) and then
+// lets the next kernel be scheduled (griddepcontrol.launch_dependents, which takes effect once
+// every CTA of the grid has issued it or exited, so a waiting grid never holds back the blocks
+// of the one before it).  This hides the launch latency between the many short kernels of a
+// V-cycle.  pdl_enabled() is per calling thread and follows the context in use.
+bool& pdl_enabled();
+
+#ifdef __CUDACC__
+__device__ __forceinline__ void pdl_entry() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+template <typename... KArgs, typename... Args>
+cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                       Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = pdl_enabled() ? 1 : 0;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
+// Launches `kernel` (parenthesised if it has template arguments) with PDL; returns the error
+// from the enclosing launcher on failure.
+#define SBM_PDL(kernel, grid, block, smem, stream, ...)                                                \
+  do {                                                                                                \
+    const cudaError_t sbm_e_ = ::sbm::launch_pdl(kernel, dim3(grid), dim3(block), smem, stream, __VA_ARGS__); \
+    if (sbm_e_ != cudaSuccess) return sbm_e_;                                                         \
+  } while (0)
+#endif
+
 // Sets the calling thread's sbm_last_error() message and returns code.
 int record_error(int code, const std::string& msg);
 
