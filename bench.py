@@ -238,6 +238,30 @@ def run_ours(args) -> dict | None:
         ms, info = solve_step(s64)
         times64.append(ms)
         infos64.append(info)
+    # ---- learned variant: the boundary-cell MLP trained (untimed) on pairs collected from the
+    # stationary V-cycle iteration on this hierarchy, attached with the fallback rule at the
+    # plain solve's mean rate per step; the timed solves are otherwise identical
+    learned = None
+    if not args.no_learned:
+        gen = torch.Generator(device="cuda").manual_seed(1000 + rank)
+        mlp = S.Mlp(prob.dim, prob.p, 128, seed=rank)
+        u0 = (2 * torch.rand((4, N), generator=gen, device="cuda", dtype=torch.float32) - 1).contiguous()
+        pairs = s32.collect(mlp, u0, 3)
+        loss = mlp.train(epochs=20, batch=4096, lr=1e-3, seed=rank)
+        its_plain = infos32[-1].iterations
+        rate = infos32[-1].true_rel_residual ** (1.0 / max(its_plain, 1))
+        s32.attach_mlp(mlp, 1.0, fallback_rate=rate)
+        solve_step(s32)
+        tl, il = [], []
+        for _ in range(args.steps):
+            ms_, inf_ = solve_step(s32)
+            tl.append(ms_)
+            il.append(inf_)
+        s32.attach_mlp(None)
+        learned = {"ms": round(statistics.mean(tl), 4), "iterations": [i.iterations for i in il],
+                   "converged": all(i.converged for i in il), "fallback": [i.learned_fallback for i in il],
+                   "train_pairs": pairs, "train_loss": round(loss, 6), "fallback_rate": rate,
+                   "mlp": "F-128-128-n_p ReLU, BF16 tensor-core GEMMs, Adam 20 epochs, batch 4096"}
     # ---- end to end through the host-buffer C-ABI call (copies inside the timed region)
     bh = torch.empty(N, dtype=torch.float64, pin_memory=True)
     xh = torch.empty(N, dtype=torch.float64, pin_memory=True)
@@ -314,6 +338,7 @@ def run_ours(args) -> dict | None:
         "fp64_vcycle": {"ms": round(statistics.mean(times64), 4), "iterations": [i.iterations for i in infos64],
                         "converged": all(i.converged for i in infos64)},
         "speedup_fp32_over_fp64_vcycle": round(statistics.mean(times64) / ms32, 3),
+        "learned": learned,
         "solves_per_s_total": round(world * args.steps / (total_ms / 1e3), 3),
         "apply_gbs": {"fp32": list(rooflines.values())[1]["achieved"],
                       "fp64": list(rooflines.values())[2]["achieved"]},
@@ -343,7 +368,7 @@ def run_profile(args) -> None:
     import torch
     import paper_2506_12899_gb300 as S
     if args.profile == "solve":
-        g = S.Solver(WORKLOADS[args.workload](0), "f32")
+        g = S.Solver(WORKLOADS[args.workload](0), "f32", krylov_basis=args.krylov_basis)
         b = g.rhs()
         x = torch.zeros_like(b)
         l0 = S.kernel_launches()
@@ -356,7 +381,8 @@ def run_profile(args) -> None:
         print("SOLVE_LAUNCHES", S.kernel_launches() - l1, flush=True)
         print("ITERATIONS", info.iterations, "CONVERGED", info.converged, flush=True)
     else:
-        g = S.Solver(W.star2d_p2(args.profile_n, 0), "f32")
+        g = S.Solver(W.star2d_p2(args.profile_n, 0), "f32", tail_max_cells=args.tail_max_cells,
+                     tail_cluster_ctas=args.tail_cluster)
         N = g.n_dof()
         gen = torch.Generator(device="cuda").manual_seed(0)
         f = torch.rand(N, device="cuda", generator=gen)
@@ -419,8 +445,13 @@ def main():
     ap.add_argument("--workload", default="star2d_p2_n512", choices=sorted(WORKLOADS))
     ap.add_argument("--cpu-budget", type=float, default=15.0, help="seconds of oracle solve time to sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-learned", action="store_true", help="skip the learned-correction variant")
     ap.add_argument("--profile", choices=["solve", "kernels"], help="fixed launches for an ncu capture")
     ap.add_argument("--profile-n", type=int, default=2048, help="cells per direction for --profile kernels")
+    ap.add_argument("--tail-max-cells", type=int, default=0, help="--profile kernels: cluster-tail cut-off")
+    ap.add_argument("--tail-cluster", type=int, default=0, help="--profile kernels: cluster-tail CTAs")
+    ap.add_argument("--krylov-basis", type=int, default=0, choices=[0, 1],
+                    help="--profile solve: FGMRES basis storage (0 double-float, 1 FP64)")
     args = ap.parse_args()
     if args.profile:
         run_profile(args)

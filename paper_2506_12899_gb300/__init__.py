@@ -56,7 +56,7 @@ class _Desc(ctypes.Structure):
                 ("post_smooth", ctypes.c_int), ("omega", ctypes.c_double), ("omega_p3", ctypes.c_double),
                 ("vf_samples", ctypes.c_int), ("precision", ctypes.c_int), ("tail_max_cells", ctypes.c_int),
                 ("tail_cluster_ctas", ctypes.c_int), ("launch_overlap", ctypes.c_int),
-                ("cell_kernel_min_cells", ctypes.c_int), ("stream", ctypes.c_void_p)]
+                ("krylov_basis", ctypes.c_int), ("cell_kernel_min_cells", ctypes.c_int), ("stream", ctypes.c_void_p)]
 
 
 class _LevelInfo(ctypes.Structure):
@@ -158,7 +158,8 @@ def _check(code: int):
 
 
 def make_desc(prob, precision: int = SBM_F64, stream: int = 0, tail_max_cells: int = 0,
-              cell_kernel_min_cells: int = 0, tail_cluster_ctas: int = 0, launch_overlap: int = 0) -> _Desc:
+              cell_kernel_min_cells: int = 0, tail_cluster_ctas: int = 0, launch_overlap: int = 0,
+              krylov_basis: int = 0) -> _Desc:
     d = _Desc()
     d.dim, d.n, d.p = prob.dim, prob.n, prob.p
     d.lo[:] = [float(v) for v in prob.lo]
@@ -177,6 +178,7 @@ def make_desc(prob, precision: int = SBM_F64, stream: int = 0, tail_max_cells: i
     d.tail_max_cells = tail_max_cells
     d.tail_cluster_ctas = tail_cluster_ctas
     d.launch_overlap = launch_overlap
+    d.krylov_basis = krylov_basis
     d.cell_kernel_min_cells = cell_kernel_min_cells
     return d
 
@@ -185,11 +187,13 @@ class Solver:
     """One DG-SBM problem set up on the current CUDA device (a libsbm context)."""
 
     def __init__(self, prob, precision: str = "f64", stream=None, tail_max_cells: int = 0,
-                 cell_kernel_min_cells: int = 0, tail_cluster_ctas: int = 0, launch_overlap: int = 0):
+                 cell_kernel_min_cells: int = 0, tail_cluster_ctas: int = 0, launch_overlap: int = 0,
+                 krylov_basis: int = 0):
         """tail_max_cells: p = 1 levels with at most that many cells run as one cluster launch
         (0: library default, < 0: never) of tail_cluster_ctas CTAs (0: 16, else 8).
         launch_overlap: programmatic dependent launch between the solver's kernels, > 0 on, < 0 off,
-        0 on with the FP32 V-cycle and off with FP64 (measured best).  cell_kernel_min_cells: launches over at least that many
+        0 on with the FP32 V-cycle and off with FP64 (measured best).  krylov_basis: 0 double-float
+        FGMRES basis (Gram-Schmidt on the FP32 pipes), 1 FP64 basis.  cell_kernel_min_cells: launches over at least that many
         cells use one thread per cell (0: library default, < 0: never, 1: always where
         (p+1)^d <= 16)."""
         import torch
@@ -201,7 +205,7 @@ class Solver:
         self.precision = SBM_F32 if precision == "f32" else SBM_F64
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         desc = make_desc(prob, self.precision, self.stream.cuda_stream, tail_max_cells, cell_kernel_min_cells,
-                         tail_cluster_ctas, launch_overlap)
+                         tail_cluster_ctas, launch_overlap, krylov_basis)
         ctx = ctypes.c_void_p()
         _check(self.lib.sbm_setup(ctypes.byref(desc), ctypes.byref(ctx)))
         self.ctx = ctx

@@ -171,10 +171,13 @@ struct Context {
   void* tail[2] = {nullptr, nullptr};  // TailLevel<double> / TailLevel<float> arrays
   // FGMRES workspace
   int ws_m = 0, ws_prec = -1;
-  double* V = nullptr;
+  double* V = nullptr;               // FP64 basis [m+1][N] (krylov_basis = 1)
+  float2* V2 = nullptr;              // double-float basis [m+1][N] (krylov_basis = 0)
   void* Z = nullptr;
   double* w = nullptr;
   float* r32 = nullptr;
+  double* v64 = nullptr;             // FP64 copy of v_j for the FP64 V-cycle on a double-float basis
+  int ws_basis = -1;
   double* partial = nullptr;
   double* dots = nullptr;          // [0,32) h1, [32,64) h2, [64] norm, [96, 128) Hessenberg column
   double* ydev = nullptr;
@@ -347,6 +350,7 @@ void validate(const sbm_setup_desc& d) {
   if (d.pre_smooth < 0 || d.post_smooth < 0 || d.pre_smooth > 16 || d.post_smooth > 16) bad("smoothing steps");
   if (d.precision != SBM_F64 && d.precision != SBM_F32) bad("precision must be SBM_F64 or SBM_F32");
   if (d.extension != 0 && d.extension != 1) bad("extension must be 0 or 1");
+  if (d.krylov_basis != 0 && d.krylov_basis != 1) bad("krylov_basis must be 0 or 1");
   if (d.tail_cluster_ctas < 0 || d.tail_cluster_ctas > 16 || (d.tail_cluster_ctas & (d.tail_cluster_ctas - 1)))
     bad("tail_cluster_ctas must be 0, 1, 2, 4, 8 or 16");
   const double w0 = d.hi[0] - d.lo[0];
@@ -560,14 +564,21 @@ void vcycle_rec(Context& C, int l, const R* r, R* z, cudaStream_t s) {
 
 void ensure_krylov(Context& C, int m) {
   const int prec = C.desc.precision;
-  if (C.ws_m >= m && C.ws_prec == prec) return;
+  const int basis = C.desc.krylov_basis;
+  if (C.ws_m >= m && C.ws_prec == prec && C.ws_basis == basis) return;
   C.drop_graphs();                                  // captured pointers change
   const size_t N = C.lv.back().H.n_dof();
-  C.V = C.dalloc<double>((size_t)(m + 1) * N);
+  if (basis == 1) {
+    C.V = C.dalloc<double>((size_t)(m + 1) * N);
+  } else {
+    C.V2 = C.dalloc<float2>((size_t)(m + 1) * N);
+    if (prec == SBM_F64) C.v64 = C.dalloc<double>(N);
+  }
+  C.ws_basis = basis;
   C.Z = prec == SBM_F32 ? (void*)C.dalloc<float>((size_t)m * N) : (void*)C.dalloc<double>((size_t)m * N);
   C.w = C.dalloc<double>(N);
   if (prec == SBM_F32) C.r32 = C.dalloc<float>(N);
-  C.partial = C.dalloc<double>((size_t)dot_blocks(N) * 32);
+  C.partial = C.dalloc<double>((size_t)std::max(dot_blocks(N), gs_blocks(N)) * 32);   // rows of either grid
   C.dots = C.dalloc<double>(128);
   C.ydev = C.dalloc<double>(32);
   C.ws_m = m;
@@ -593,22 +604,41 @@ void arnoldi_step_work(Context& C, int j, cudaStream_t s) {
   double* h2 = C.dots + 32;
   double* hn = C.dots + 64;
   double* col = C.dots + 96;
-  double* Vj = C.V + (size_t)j * N;
-  if (prec == SBM_F32) {
-    float* Zj = static_cast<float*>(C.Z) + (size_t)j * N;
-    CUDA_TRY((launch_cast<double, float>(Vj, C.r32, N, s)));
-    vcycle_rec<float>(C, Lf, C.r32, Zj, s);
-    CUDA_TRY((launch_apply<float, double>(dim, p, F.P64, Zj, nullptr, C.w, 0, s)));
-  } else {
-    double* Zj = static_cast<double*>(C.Z) + (size_t)j * N;
-    vcycle_rec<double>(C, Lf, Vj, Zj, s);
-    CUDA_TRY((launch_apply<double, double>(dim, p, F.P64, Zj, nullptr, C.w, 0, s)));
+  if (C.desc.krylov_basis == 1) {                 // FP64 basis
+    double* Vj = C.V + (size_t)j * N;
+    if (prec == SBM_F32) {
+      float* Zj = static_cast<float*>(C.Z) + (size_t)j * N;
+      CUDA_TRY((launch_cast<double, float>(Vj, C.r32, N, s)));
+      vcycle_rec<float>(C, Lf, C.r32, Zj, s);
+      CUDA_TRY((launch_apply<float, double>(dim, p, F.P64, Zj, nullptr, C.w, 0, s)));
+    } else {
+      double* Zj = static_cast<double*>(C.Z) + (size_t)j * N;
+      vcycle_rec<double>(C, Lf, Vj, Zj, s);
+      CUDA_TRY((launch_apply<double, double>(dim, p, F.P64, Zj, nullptr, C.w, 0, s)));
+    }
+    // CGS2 in three sweeps over V: h1 = V^T w; w -= V h1 and h2 = V^T w; w -= V h2 and |w|
+    CUDA_TRY(launch_multi_dot(C.V, N, j + 1, C.w, N, C.partial, h1, 0, s));
+    CUDA_TRY(launch_axpy_dot(C.V, N, j + 1, h1, C.w, N, C.partial, h2, s));
+    CUDA_TRY(launch_axpy_norm(C.V, N, j + 1, h2, C.w, N, C.partial, hn, s));
+    CUDA_TRY(launch_div_scalar(C.w, hn, C.V + (size_t)(j + 1) * N, N, s));
+  } else {                                          // double-float basis, same three sweeps
+    const float2* Vj = C.V2 + (size_t)j * N;
+    if (prec == SBM_F32) {
+      float* Zj = static_cast<float*>(C.Z) + (size_t)j * N;
+      CUDA_TRY(launch_df_to<float>(Vj, C.r32, N, s));
+      vcycle_rec<float>(C, Lf, C.r32, Zj, s);
+      CUDA_TRY((launch_apply<float, double>(dim, p, F.P64, Zj, nullptr, C.w, 0, s)));
+    } else {
+      double* Zj = static_cast<double*>(C.Z) + (size_t)j * N;
+      CUDA_TRY(launch_df_to<double>(Vj, C.v64, N, s));
+      vcycle_rec<double>(C, Lf, C.v64, Zj, s);
+      CUDA_TRY((launch_apply<double, double>(dim, p, F.P64, Zj, nullptr, C.w, 0, s)));
+    }
+    CUDA_TRY(launch_gs_dot(C.V2, N, j + 1, C.w, N, C.partial, h1, s));
+    CUDA_TRY(launch_gs_axpy_dot(C.V2, N, j + 1, h1, C.w, N, C.partial, h2, s));
+    CUDA_TRY(launch_gs_axpy_norm(C.V2, N, j + 1, h2, C.w, N, C.partial, hn, s));
+    CUDA_TRY(launch_gs_scale(C.w, hn, C.V2 + (size_t)(j + 1) * N, N, s));
   }
-  // CGS2 in three sweeps over V: h1 = V^T w; w -= V h1 and h2 = V^T w; w -= V h2 and |w|
-  CUDA_TRY(launch_multi_dot(C.V, N, j + 1, C.w, N, C.partial, h1, 0, s));
-  CUDA_TRY(launch_axpy_dot(C.V, N, j + 1, h1, C.w, N, C.partial, h2, s));
-  CUDA_TRY(launch_axpy_norm(C.V, N, j + 1, h2, C.w, N, C.partial, hn, s));
-  CUDA_TRY(launch_div_scalar(C.w, hn, C.V + (size_t)(j + 1) * N, N, s));
   CUDA_TRY(launch_hess_column(h1, h2, hn, j + 1, col, s));
   CUDA_TRY(cudaMemcpyAsync(C.host_pinned, col, (j + 2) * sizeof(double), cudaMemcpyDeviceToHost, s));
 }
@@ -678,9 +708,9 @@ int solve_impl(Context& C, const double* b, double* x, double tol, int m, int ma
   } else {
     std::vector<double> H((size_t)(m + 1) * m), cs(m), sn(m), g(m + 1), y(m);
     while (true) {
-      double* V0 = C.V;
-      CUDA_TRY((launch_apply<double, double>(dim, p, F.P64, x, b, V0, 1, s)));
-      const double beta = device_norm(C, V0, N, hn, s);
+      double* r0 = C.desc.krylov_basis == 1 ? C.V : C.w;   // r = b - A x, FP64
+      CUDA_TRY((launch_apply<double, double>(dim, p, F.P64, x, b, r0, 1, s)));
+      const double beta = device_norm(C, r0, N, hn, s);
       loc.true_rel_residual = beta / bnorm;
       if (!std::isfinite(beta)) {
         status = SBM_ERR_NAN;
@@ -694,7 +724,8 @@ int solve_impl(Context& C, const double* b, double* x, double tol, int m, int ma
         status = SBM_ERR_NOT_CONVERGED;
         break;
       }
-      CUDA_TRY(launch_div_scalar(V0, hn, V0, N, s));
+      if (C.desc.krylov_basis == 1) CUDA_TRY(launch_div_scalar(r0, hn, r0, N, s));
+      else CUDA_TRY(launch_gs_scale(r0, hn, C.V2, N, s));
       std::fill(H.begin(), H.end(), 0.0);
       std::fill(g.begin(), g.end(), 0.0);
       g[0] = beta;

@@ -165,6 +165,167 @@ __global__ void k_hess_column(const double* h1, const double* h2, const double* 
   if (i == k) col[k] = hn[0];
 }
 
+// ------------------------------------------------------------------------------------------
+// Gram-Schmidt on a double-float Krylov basis.  A basis vector is stored as pairs (hi, lo) of
+// FP32 values with v = hi + lo and |lo| <= ulp(hi)/2 (a double-float number, Dekker 1971), 8
+// bytes per entry like FP64.  Products and sums use error-free transformations on the FP32
+// pipes: two_prod (p = a*b, e = fma(a, b, -p), so a*b = p + e exactly) and Knuth's two_sum.
+// Every operation carries about 48 significant bits (relative error ~4e-15), against FP64's
+// 53; the FP64 pipe, which bounds the plain FP64 sweeps on GB300, is not used per entry.
+// The non-contracting intrinsics (__fmul_rn, __fadd_rn, __fsub_rn) keep the compiler from
+// fusing the steps of an error-free transformation into an FMA.
+__device__ __forceinline__ float2 df_from_double(double x) {
+  const float hi = __double2float_rn(x);
+  return make_float2(hi, __double2float_rn(x - (double)hi));
+}
+
+__device__ __forceinline__ double df_to_double(float2 a) { return (double)a.x + (double)a.y; }
+
+// (s, c) += a * b: the exact product p + e of the high parts, the cross terms into e, the sum
+// s + p by two_sum with its rounding error added to the compensation c.
+__device__ __forceinline__ void df_dot_acc(float& s, float& c, float2 a, float2 b) {
+  const float p = __fmul_rn(a.x, b.x);
+  float e = fmaf(a.x, b.x, -p);
+  e = fmaf(a.x, b.y, e);
+  e = fmaf(a.y, b.x, e);
+  const float t = __fadd_rn(s, p);
+  const float z = __fsub_rn(t, s);
+  const float err = __fadd_rn(__fsub_rn(s, __fsub_rn(t, z)), __fsub_rn(p, z));
+  s = t;
+  c = __fadd_rn(c, __fadd_rn(err, e));
+}
+
+// w - h * v in double-float, renormalised.
+__device__ __forceinline__ float2 df_sub_prod(float2 w, float2 h, float2 v) {
+  const float p = __fmul_rn(h.x, v.x);
+  float e = fmaf(h.x, v.x, -p);
+  e = fmaf(h.x, v.y, e);
+  e = fmaf(h.y, v.x, e);
+  const float t = __fsub_rn(w.x, p);
+  const float z = __fsub_rn(t, w.x);
+  const float err = __fadd_rn(__fsub_rn(w.x, __fsub_rn(t, z)), __fsub_rn(__fsub_rn(0.f, p), z));
+  const float lo = __fsub_rn(__fadd_rn(w.y, err), e);
+  const float hi = __fadd_rn(t, lo);
+  return make_float2(hi, __fsub_rn(lo, __fsub_rn(hi, t)));
+}
+
+// A load the compiler may not merge with an earlier load of the same address (volatile asm):
+// the dot pass of k_gs_axpy_dot re-reads V from L1 instead of keeping NV values live.
+__device__ __forceinline__ float2 ld_again(const float2* p) {
+  float2 v;
+  asm volatile("ld.global.ca.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "l"(p));
+  return v;
+}
+
+// (s, c) += (s2, c2) for double-float partial sums held as a leading value and a compensation.
+__device__ __forceinline__ void df_acc_add(float& s, float& c, float s2, float c2) {
+  const float t = __fadd_rn(s, s2);
+  const float z = __fsub_rn(t, s);
+  const float err = __fadd_rn(__fsub_rn(s, __fsub_rn(t, z)), __fsub_rn(s2, z));
+  s = t;
+  c = __fadd_rn(__fadd_rn(c, c2), err);
+}
+
+// Block reduction of NV double-float per-thread sums into partial[blockIdx][k] (FP64): warp
+// shuffles in double-float on the FP32 pipes, one FP64 value per warp and vector, then a
+// fixed-order FP64 sum over the warps.
+template <int NV>
+__device__ __forceinline__ void block_partials_df(float (&s)[NV], float (&c)[NV], double* __restrict__ partial) {
+  __shared__ double red[kDotThreads / 32][NV > 0 ? NV : 1];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll
+  for (int k = 0; k < NV; ++k) {
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+      const float s2 = __shfl_xor_sync(0xffffffffu, s[k], off);
+      const float c2 = __shfl_xor_sync(0xffffffffu, c[k], off);
+      df_acc_add(s[k], c[k], s2, c2);
+    }
+    if (lane == 0) red[warp][k] = (double)s[k] + (double)c[k];
+  }
+  __syncthreads();
+  if (threadIdx.x < NV) {
+    double t = 0.0;
+#pragma unroll
+    for (int q = 0; q < kDotThreads / 32; ++q) t += red[q][threadIdx.x];
+    partial[(size_t)blockIdx.x * kMaxVec + threadIdx.x] = t;
+  }
+}
+
+// partial[block][k] = this block's share of V_k . w (V double-float, w FP64), k < NV; each
+// thread sweeps its elements with a grid stride, reading every V_k once.
+template <int NV>
+__global__ void __launch_bounds__(kDotThreads) k_gs_dot(const float2* __restrict__ V, size_t ldv,
+                                                        const double* __restrict__ w, size_t N,
+                                                        double* __restrict__ partial) {
+  pdl_entry();
+  float s[NV], c[NV];
+#pragma unroll
+  for (int k = 0; k < NV; ++k) s[k] = c[k] = 0.f;
+  const size_t stride = (size_t)gridDim.x * kDotThreads;
+  for (size_t i = (size_t)blockIdx.x * kDotThreads + threadIdx.x; i < N; i += stride) {
+    const float2 wi = df_from_double(w[i]);
+#pragma unroll
+    for (int k = 0; k < NV; ++k) df_dot_acc(s[k], c[k], V[k * ldv + i], wi);
+  }
+  block_partials_df<NV>(s, c, partial);
+}
+
+// w <- w - sum_k h[k] V_k in double-float (w stored back in FP64), then the partial sums of
+// V_k . w for k < NV, or of |w|^2 when NORM (nv vectors, no dots).  The dot pass reads V_k
+// again (an L1/L2 hit right after the update pass) instead of holding NV values per thread.
+template <int NV, bool NORM>
+__global__ void __launch_bounds__(kDotThreads) k_gs_axpy_dot(const float2* __restrict__ V, size_t ldv,
+                                                             const double* __restrict__ h, double* __restrict__ w,
+                                                             size_t N, int nv, double* __restrict__ partial) {
+  pdl_entry();
+  constexpr int NA = NORM ? 1 : NV;
+  __shared__ float2 hs[kMaxVec];
+  if (threadIdx.x < nv) hs[threadIdx.x] = df_from_double(h[threadIdx.x]);
+  __syncthreads();
+  float s[NA], c[NA];
+#pragma unroll
+  for (int k = 0; k < NA; ++k) s[k] = c[k] = 0.f;
+  const size_t stride = (size_t)gridDim.x * kDotThreads;
+  for (size_t i = (size_t)blockIdx.x * kDotThreads + threadIdx.x; i < N; i += stride) {
+    float2 wi = df_from_double(w[i]);
+    if (NORM) {
+      for (int k = 0; k < nv; ++k) wi = df_sub_prod(wi, hs[k], V[k * ldv + i]);
+      w[i] = df_to_double(wi);
+      df_dot_acc(s[0], c[0], wi, wi);
+    } else {
+#pragma unroll
+      for (int k = 0; k < NV; ++k) wi = df_sub_prod(wi, hs[k], V[k * ldv + i]);
+      w[i] = df_to_double(wi);
+#pragma unroll
+      for (int k = 0; k < NV; ++k) df_dot_acc(s[k], c[k], ld_again(V + k * ldv + i), wi);
+    }
+  }
+  block_partials_df<NA>(s, c, partial);
+}
+
+// v = w / s[0] as double-float.
+__global__ void k_gs_scale(const double* __restrict__ w, const double* __restrict__ sc, float2* __restrict__ v,
+                           size_t N) {
+  pdl_entry();
+  const double inv = 1.0 / sc[0];
+  const size_t stride = (size_t)gridDim.x * blockDim.x;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += stride)
+    v[i] = df_from_double(w[i] * inv);
+}
+
+// y = v rounded to FP32 or to FP64.
+template <typename TO>
+__global__ void k_df_to(const float2* __restrict__ v, TO* __restrict__ y, size_t N) {
+  pdl_entry();
+  const size_t stride = (size_t)gridDim.x * blockDim.x;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += stride) {
+    const float2 a = v[i];
+    if constexpr (sizeof(TO) == 4) y[i] = __fadd_rn(a.x, a.y);
+    else y[i] = df_to_double(a);
+  }
+}
+
 // Scratch of sbm_dots_noalloc: room for the per-block partial sums of the largest grid the dot
 // kernel uses (dot_blocks() never exceeds kNoAllocBlocks) times 32 vectors: 152 KiB per device,
 // held by every GPU that loads the library until the process exits.
@@ -272,6 +433,80 @@ cudaError_t launch_hess_column(const double* h1, const double* h2, const double*
   count_launches();
   return cudaGetLastError();
 }
+
+// Grid of the double-float sweeps: two blocks per SM at most, so that each thread handles
+// enough elements to amortise its reduction.
+int gs_blocks(size_t N) {
+  size_t g = (N + kDotThreads - 1) / kDotThreads;
+  if (g < 1) g = 1;
+  if (g > 152 * 2) g = 152 * 2;
+  return (int)g;
+}
+
+cudaError_t launch_gs_dot(const float2* V, size_t ldv, int nv, const double* w, size_t N, double* partial,
+                          double* out, cudaStream_t s) {
+  if (nv < 1 || nv > kMaxVec) return cudaErrorInvalidValue;
+  const int nblk = gs_blocks(N);
+  switch (nv) {
+#define SBM_GD_CASE(K) \
+  case K: SBM_PDL((k_gs_dot<K>), nblk, kDotThreads, 0, s, V, ldv, w, N, partial); break;
+    SBM_GD_CASE(1) SBM_GD_CASE(2) SBM_GD_CASE(3) SBM_GD_CASE(4) SBM_GD_CASE(5) SBM_GD_CASE(6)
+    SBM_GD_CASE(7) SBM_GD_CASE(8) SBM_GD_CASE(9) SBM_GD_CASE(10) SBM_GD_CASE(11) SBM_GD_CASE(12)
+    SBM_GD_CASE(13) SBM_GD_CASE(14) SBM_GD_CASE(15) SBM_GD_CASE(16) SBM_GD_CASE(17) SBM_GD_CASE(18)
+    SBM_GD_CASE(19) SBM_GD_CASE(20) SBM_GD_CASE(21) SBM_GD_CASE(22) SBM_GD_CASE(23) SBM_GD_CASE(24)
+    SBM_GD_CASE(25) SBM_GD_CASE(26) SBM_GD_CASE(27) SBM_GD_CASE(28) SBM_GD_CASE(29) SBM_GD_CASE(30)
+    SBM_GD_CASE(31) SBM_GD_CASE(32)
+#undef SBM_GD_CASE
+  }
+  SBM_PDL(k_reduce_partials, 1, 32 * nv, 0, s, partial, nblk, nv, out, 0);
+  count_launches(2);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gs_axpy_dot(const float2* V, size_t ldv, int nv, const double* h, double* w, size_t N,
+                               double* partial, double* out, cudaStream_t s) {
+  if (nv < 1 || nv > kMaxVec) return cudaErrorInvalidValue;
+  const int nblk = gs_blocks(N);
+  switch (nv) {
+#define SBM_GA_CASE(K) \
+  case K: SBM_PDL((k_gs_axpy_dot<K, false>), nblk, kDotThreads, 0, s, V, ldv, h, w, N, nv, partial); break;
+    SBM_GA_CASE(1) SBM_GA_CASE(2) SBM_GA_CASE(3) SBM_GA_CASE(4) SBM_GA_CASE(5) SBM_GA_CASE(6)
+    SBM_GA_CASE(7) SBM_GA_CASE(8) SBM_GA_CASE(9) SBM_GA_CASE(10) SBM_GA_CASE(11) SBM_GA_CASE(12)
+    SBM_GA_CASE(13) SBM_GA_CASE(14) SBM_GA_CASE(15) SBM_GA_CASE(16) SBM_GA_CASE(17) SBM_GA_CASE(18)
+    SBM_GA_CASE(19) SBM_GA_CASE(20) SBM_GA_CASE(21) SBM_GA_CASE(22) SBM_GA_CASE(23) SBM_GA_CASE(24)
+    SBM_GA_CASE(25) SBM_GA_CASE(26) SBM_GA_CASE(27) SBM_GA_CASE(28) SBM_GA_CASE(29) SBM_GA_CASE(30)
+    SBM_GA_CASE(31) SBM_GA_CASE(32)
+#undef SBM_GA_CASE
+  }
+  SBM_PDL(k_reduce_partials, 1, 32 * nv, 0, s, partial, nblk, nv, out, 0);
+  count_launches(2);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gs_axpy_norm(const float2* V, size_t ldv, int nv, const double* h, double* w, size_t N,
+                                double* partial, double* out, cudaStream_t s) {
+  if (nv < 1 || nv > kMaxVec) return cudaErrorInvalidValue;
+  const int nblk = gs_blocks(N);
+  SBM_PDL((k_gs_axpy_dot<0, true>), nblk, kDotThreads, 0, s, V, ldv, h, w, N, nv, partial);
+  SBM_PDL(k_reduce_partials, 1, 32, 0, s, partial, nblk, 1, out, 1);
+  count_launches(2);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gs_scale(const double* w, const double* sc, float2* v, size_t N, cudaStream_t s) {
+  SBM_PDL(k_gs_scale, grid_for(N), 256, 0, s, w, sc, v, N);
+  count_launches();
+  return cudaGetLastError();
+}
+
+template <typename TO>
+cudaError_t launch_df_to(const float2* v, TO* y, size_t N, cudaStream_t s) {
+  SBM_PDL((k_df_to<TO>), grid_for(N), 256, 0, s, v, y, N);
+  count_launches();
+  return cudaGetLastError();
+}
+template cudaError_t launch_df_to<float>(const float2*, float*, size_t, cudaStream_t);
+template cudaError_t launch_df_to<double>(const float2*, double*, size_t, cudaStream_t);
 
 int dots_noalloc(const double* V, long long ldv, int nv, const double* w, long long n, double* out,
                  cudaStream_t stream) {

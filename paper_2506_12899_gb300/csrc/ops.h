@@ -121,6 +121,8 @@ cudaError_t launch_coarse(const double* Ainv, int N, const T* r, T* e, cudaStrea
 // ---------------------------------------------------------------- FGMRES building blocks (FP64)
 // Number of partial-sum blocks used for vectors of length N (fixed per N: deterministic sums).
 int dot_blocks(size_t N);
+// Blocks of the double-float Gram-Schmidt sweeps (rows of their partial-sum buffer).
+int gs_blocks(size_t N);
 // out[k] = sum_i V[k*ldv + i] w[i], k < nv (nv <= 32); partial holds dot_blocks(N)*32 doubles.
 cudaError_t launch_multi_dot(const double* V, size_t ldv, int nv, const double* w, size_t N, double* partial,
                              double* out, int take_sqrt, cudaStream_t s);
@@ -141,6 +143,17 @@ cudaError_t launch_div_scalar(const double* w, const double* s, double* v, size_
 template <typename TI, typename TO>
 cudaError_t launch_cast(const TI* x, TO* y, size_t N, cudaStream_t s);
 // c = a + b (k <= 32 entries), c[k] = hn at index k
+// Gram-Schmidt on a double-float basis V (pairs hi, lo of FP32 per entry, Dekker 1971):
+// out = V^T w; w -= V h then out = V^T w; w -= V h then out = |w|; v = w / s[0]; v rounded.
+cudaError_t launch_gs_dot(const float2* V, size_t ldv, int nv, const double* w, size_t N, double* partial,
+                          double* out, cudaStream_t s);
+cudaError_t launch_gs_axpy_dot(const float2* V, size_t ldv, int nv, const double* h, double* w, size_t N,
+                               double* partial, double* out, cudaStream_t s);
+cudaError_t launch_gs_axpy_norm(const float2* V, size_t ldv, int nv, const double* h, double* w, size_t N,
+                                double* partial, double* out, cudaStream_t s);
+cudaError_t launch_gs_scale(const double* w, const double* sc, float2* v, size_t N, cudaStream_t s);
+template <typename TO>
+cudaError_t launch_df_to(const float2* v, TO* y, size_t N, cudaStream_t s);
 cudaError_t launch_hess_column(const double* h1, const double* h2, const double* hn, int k, double* col,
                                cudaStream_t s);
 

@@ -21,11 +21,11 @@ def _dof_map(solver, lev, level):
 class Pair:
     """A GPU solver and the oracle hierarchy of the same problem, with dof maps per level."""
 
-    def __init__(self, prob, precision="f64", tail_max_cells=0, cell_kernel_min_cells=0):
+    def __init__(self, prob, precision="f64", tail_max_cells=0, cell_kernel_min_cells=0, **solver_kwargs):
         import paper_2506_12899_gb300 as S
         self.prob = prob
         self.gpu = S.Solver(prob, precision, tail_max_cells=tail_max_cells,
-                            cell_kernel_min_cells=cell_kernel_min_cells)
+                            cell_kernel_min_cells=cell_kernel_min_cells, **solver_kwargs)
         self.H = MG.Hierarchy(prob)
         assert self.gpu.num_levels == len(self.H.levels)
         self.maps = [_dof_map(self.gpu, lev, l) for l, lev in enumerate(self.H.levels)]

@@ -36,12 +36,13 @@ CASES = {
 _pairs = {}
 
 
-def pair(name, precision="f64", tail=False, cell=0):
+def pair(name, precision="f64", tail=False, cell=0, basis=0):
     """tail: run the small p = 1 levels as one cluster launch; cell: thread-per-cell kernels
-    (0: size-based default, 1: always where (p+1)^d <= 16, -1: never)."""
-    key = (name, precision, tail, cell)
+    (0: size-based default, 1: always where (p+1)^d <= 16, -1: never); basis: FGMRES basis
+    storage (0 double-float, 1 FP64)."""
+    key = (name, precision, tail, cell, basis)
     if key not in _pairs:
-        _pairs[key] = Pair(CASES[name], precision, 40000 if tail else -1, cell)
+        _pairs[key] = Pair(CASES[name], precision, 40000 if tail else -1, cell, krylov_basis=basis)
     return _pairs[key]
 
 
@@ -258,10 +259,12 @@ def test_cluster_tail_is_one_launch():
             assert n > 10
 
 
-@pytest.mark.parametrize("name", ["disk2d_p1_n32", "star2d_p2_n32", "sphere3d_p1_n8"])
-def test_fgmres_fp64_per_level_launches(name):
-    """FGMRES with the cluster tail disabled: same iteration count and solution as the oracle."""
-    P = pair(name, tail=False)
+@pytest.mark.parametrize("name", ["disk2d_p1_n32", "star2d_p2_n32", "sphere3d_p2_n8", "ellipsoid3d_p3_n12"])
+@pytest.mark.parametrize("tail,basis", [(True, 0), (False, 1)], ids=["cluster_tail", "fp64_basis"])
+def test_fgmres_fp64_variants(name, tail, basis):
+    """FGMRES with the cluster V-cycle tail, and with the FP64 Krylov basis instead of the
+    double-float one: same iteration count and solution (1e-10) as the oracle."""
+    P = pair(name, tail=tail, basis=basis)
     F = P.H.finest
     L = len(P.H.levels) - 1
     bo = F.disc.rhs()
