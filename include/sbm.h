@@ -85,11 +85,14 @@ typedef struct {
   double omega_p3;       /* relaxation on levels with p_l = 3                                    */
   int vf_samples;        /* kappa sub-samples per direction; 0: 16 in 2D, 8 in 3D                 */
   int precision;         /* V-cycle precision inside sbm_solve: SBM_F64 or SBM_F32                */
-  int tail_max_cells;    /* the p = 1 h-levels with at most this many active cells run their      */
-                         /* whole V-cycle in one thread-block-cluster launch with the level       */
-                         /* vectors in shared memory (the largest such level that fits starts    */
-                         /* it); 0: library default (none); < 0: never                            */
-  int tail_cluster_ctas; /* CTAs of that cluster: 1, 2, 4, 8 or 16; 0: 16, else 8                  */
+  int tail_max_cells;    /* the coarse p = 1 h-levels with at most this many active cells run     */
+                         /* their whole V-cycle in one launch with the level data in shared       */
+                         /* memory (the largest such level that fits starts it); 0: library      */
+                         /* default = every level that fits for FP32 V-cycles, none for FP64;    */
+                         /* < 0: never                                                            */
+  int tail_cluster_ctas; /* CTAs of that launch: 1 (one CTA, __syncthreads phases; the default    */
+                         /* for 0) or 2, 4, 8, 16 (a thread-block cluster, vectors spread over    */
+                         /* the CTAs' distributed shared memory)                                  */
   int launch_overlap;    /* > 0: the level and Krylov kernels use programmatic dependent launch,  */
                          /* so each may be scheduled while its predecessor finishes; < 0: plain   */
                          /* stream-ordered launches; 0: on with the FP32 V-cycle, off with FP64   */

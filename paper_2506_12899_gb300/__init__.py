@@ -189,8 +189,9 @@ class Solver:
     def __init__(self, prob, precision: str = "f64", stream=None, tail_max_cells: int = 0,
                  cell_kernel_min_cells: int = 0, tail_cluster_ctas: int = 0, launch_overlap: int = 0,
                  krylov_basis: int = 0):
-        """tail_max_cells: p = 1 levels with at most that many cells run as one cluster launch
-        (0: library default, < 0: never) of tail_cluster_ctas CTAs (0: 16, else 8).
+        """tail_max_cells: coarse p = 1 levels with at most that many cells run as one launch
+        (0: library default, every level that fits for FP32 and none for FP64; < 0: never) of
+        tail_cluster_ctas CTAs (0 or 1: one CTA; 2..16: a thread-block cluster).
         launch_overlap: programmatic dependent launch between the solver's kernels, > 0 on, < 0 off,
         0 on with the FP32 V-cycle and off with FP64 (measured best).  krylov_basis: 0 double-float
         FGMRES basis (Gram-Schmidt on the FP32 pipes), 1 FP64 basis.  cell_kernel_min_cells: launches over at least that many

@@ -169,6 +169,8 @@ struct Context {
   int tail_cand = -1;                // highest level the cluster tail may start at (-1: none)
   TailPlan tail_plan[2];             // per precision: levels 0..top in one cluster launch
   void* tail[2] = {nullptr, nullptr};  // TailLevel<double> / TailLevel<float> arrays
+  std::unique_ptr<TailCta<double>> tail_cta64;   // one-CTA tail parameter blocks
+  std::unique_ptr<TailCta<float>> tail_cta32;
   // FGMRES workspace
   int ws_m = 0, ws_prec = -1;
   double* V = nullptr;               // FP64 basis [m+1][N] (krylov_basis = 1)
@@ -413,7 +415,7 @@ Context* build_context(const sbm_setup_desc& d, bool device) {
     C->lv[l].T32 = make_transfer<float>(C->lv[l - 1], C->lv[l]);
   }
   {
-    const long long cap = d.tail_max_cells == 0 ? -1 : d.tail_max_cells;
+    const long long cap = d.tail_max_cells == 0 ? (1LL << 40) : d.tail_max_cells;
     int top = -1;
     for (int l = 0; l < (int)C->lv.size(); ++l) {
       const HostLevel& H = C->lv[l].H;
@@ -447,8 +449,54 @@ void ensure_work(Context& C) {
   // memory of a resident cluster of 16, else 8, CTAs
   C.tail_plan[pi] = TailPlan{};
   const int NP = C.lv[0].H.dim == 2 ? 4 : 8;
-  std::vector<int> sizes = {16, 8};
-  if (C.desc.tail_cluster_ctas > 0) sizes = {C.desc.tail_cluster_ctas};
+  // default (tail_max_cells = 0): the one-CTA tail for FP32 V-cycles, none for FP64 ones (one
+  // SM's FP64 pipe makes it slower than per-level launches: measured)
+  const bool tail_default = C.desc.tail_max_cells == 0;
+  const int ctas = C.desc.tail_cluster_ctas == 0 ? 1 : C.desc.tail_cluster_ctas;
+  if (ctas == 1 && !(tail_default && sizeof(R) == 8)) {
+    // one CTA: the highest candidate level whose data (levels 0..top) fit in its shared memory
+    const int dim = C.lv[0].H.dim, ncol = 1 << dim;
+    for (int top = std::min(C.tail_cand, kMaxTailCta - 1); top >= 1; --top) {
+      auto tp = std::make_unique<TailCta<R>>();
+      std::memset(tp.get(), 0, sizeof(TailCta<R>));
+      size_t re = 0, ie = 0;                        // R elements, ints
+      for (int l = 0; l <= top; ++l) {
+        const HostLevel& H = C.lv[l].H;
+        tp->P[l] = params<R>(C.lv[l]);
+        if (l >= 1) tp->T[l] = tparams<R>(C.lv[l]);
+        tp->n_bnd[l] = H.n_bnd;
+        tp->zoff[l] = (int)re;
+        re += (size_t)H.n_act * NP;
+        tp->roff[l] = (int)re;
+        re += (size_t)H.n_act * NP;
+        tp->boff[l] = (int)re;
+        re += (size_t)H.n_bnd * NP * NP;
+        tp->noff[l] = (int)ie;
+        ie += (size_t)2 * dim * H.n_act;
+        if (l >= 1) {
+          tp->coff[l] = (int)ie;
+          ie += (size_t)ncol * C.lv[l - 1].H.n_act;
+          tp->poff[l] = (int)ie;
+          ie += (size_t)H.n_act;
+        }
+      }
+      const size_t int_base = (re * sizeof(R) + 15) / 16 * 16;
+      const size_t smem = int_base + ie * sizeof(int);
+      tp->top = top;
+      tp->pre = C.desc.pre_smooth;
+      tp->post = C.desc.post_smooth;
+      tp->int_base = (unsigned)int_base;
+      if (!tail_cta_fits(dim, pi, smem, sizeof(TailCta<R>))) continue;
+      C.tail_plan[pi].top = top;
+      C.tail_plan[pi].cluster = 1;
+      C.tail_plan[pi].smem_bytes = smem;
+      if constexpr (sizeof(R) == 8) C.tail_cta64 = std::move(tp);
+      else C.tail_cta32 = std::move(tp);
+      break;
+    }
+  }
+  std::vector<int> sizes = {ctas};
+  if (ctas == 1 || (tail_default && sizeof(R) == 8)) sizes.clear();
   for (int size : sizes) {
     if (C.tail_plan[pi].top >= 1) break;
     for (int top = C.tail_cand; top >= 1; --top) {
@@ -539,9 +587,16 @@ void vcycle_rec(Context& C, int l, const R* r, R* z, cudaStream_t s) {
     CUDA_TRY(launch_coarse<R>(L.coarse_inv, L.H.n_dof(), r, z, s));
     return;
   }
-  if (l == C.tail_plan[pi].top && !(C.mlp_on && l == C.finest())) {   // levels 0..l in one cluster launch
-    CUDA_TRY(launch_vcycle_tail<R>(L.H.dim, static_cast<const TailLevel<R>*>(C.tail[pi]), l, r, z,
-                                   C.lv[0].coarse_inv, C.desc.pre_smooth, C.desc.post_smooth, C.tail_plan[pi], s));
+  if (l == C.tail_plan[pi].top && !(C.mlp_on && l == C.finest())) {   // levels 0..l in one launch
+    if (C.tail_plan[pi].cluster == 1) {
+      const TailCta<R>* tp;
+      if constexpr (sizeof(R) == 8) tp = C.tail_cta64.get();
+      else tp = C.tail_cta32.get();
+      CUDA_TRY(launch_vcycle_tail_cta<R>(L.H.dim, *tp, r, z, C.lv[0].coarse_inv, C.tail_plan[pi].smem_bytes, s));
+    } else {
+      CUDA_TRY(launch_vcycle_tail<R>(L.H.dim, static_cast<const TailLevel<R>*>(C.tail[pi]), l, r, z,
+                                     C.lv[0].coarse_inv, C.desc.pre_smooth, C.desc.post_smooth, C.tail_plan[pi], s));
+    }
     return;
   }
   const int dim = L.H.dim;

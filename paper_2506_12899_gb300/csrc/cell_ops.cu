@@ -281,11 +281,22 @@ __global__ void __launch_bounds__(kCellThreads) k_apply_cell(const __grid_consta
 // y = A_KK^{-1} t / hscale-scaled block solve of one cell: the dense inverse of boundary cell
 // bidx, or the fast diagonalisation (S^T)^(x d), 1 / (hscale sum lambda), S^(x d) when bidx < 0.
 template <int D, int N1, typename R>
+__device__ __forceinline__ void block_solve_at(const LevelParams<R>& P, const R* Bi, R (&t)[CD<D, N1>::NP],
+                                               R (&y)[CD<D, N1>::NP]);
+
+template <int D, int N1, typename R>
 __device__ __forceinline__ void block_solve(const LevelParams<R>& P, int bidx, R (&t)[CD<D, N1>::NP],
                                             R (&y)[CD<D, N1>::NP]) {
+  constexpr int NP = CD<D, N1>::NP;
+  block_solve_at<D, N1, R>(P, bidx >= 0 ? P.binvT + (size_t)bidx * NP * NP : nullptr, t, y);
+}
+
+// Bi: the cell's transposed dense inverse, or null for the fast diagonalisation.
+template <int D, int N1, typename R>
+__device__ __forceinline__ void block_solve_at(const LevelParams<R>& P, const R* Bi, R (&t)[CD<D, N1>::NP],
+                                               R (&y)[CD<D, N1>::NP]) {
   constexpr int NP = CD<D, N1>::NP, NQ = CD<D, N1>::NQ;
-  if (bidx >= 0) {
-    const R* Bi = P.binvT + (size_t)bidx * NP * NP;
+  if (Bi) {
 #pragma unroll
     for (int i = 0; i < NP; ++i) y[i] = 0;
 #pragma unroll
@@ -671,6 +682,174 @@ __global__ void __launch_bounds__(kTailThreads, 1) k_vcycle_tail(const TailLevel
   }
 }
 
+// ----------------------------------------------------------------------------------------------
+// The V-cycle of levels 0..top (p = 1 h-levels) in one CTA: all data of those levels in shared
+// memory, phases separated by __syncthreads(); see TailCta.
+// ----------------------------------------------------------------------------------------------
+constexpr int kTailCtaThreads = 512;
+
+template <int D, typename R>
+__global__ void __launch_bounds__(kTailCtaThreads, 1) k_vcycle_tail_cta(const __grid_constant__ TailCta<R> TP,
+                                                                        const R* __restrict__ r_top,
+                                                                        R* __restrict__ z_top,
+                                                                        const double* __restrict__ coarse_inv) {
+  pdl_entry();
+  extern __shared__ __align__(16) unsigned char tcta_smem[];
+  R* sm = reinterpret_cast<R*>(tcta_smem);
+  int* si = reinterpret_cast<int*>(tcta_smem + TP.int_base);
+  constexpr int NCOL = 1 << D, NP = CD<D, 2>::NP;
+  const int top = TP.top, tid = threadIdx.x;
+  // stage the tables and inverses of every level, and the top level's right-hand side
+  for (int l = 0; l <= top; ++l) {
+    const LevelParams<R>& P = TP.P[l];
+    for (int q = tid; q < 2 * D * P.n_act; q += kTailCtaThreads) si[TP.noff[l] + q] = P.nbr[q];
+    for (int q = tid; q < TP.n_bnd[l] * NP * NP; q += kTailCtaThreads) sm[TP.boff[l] + q] = P.binvT[q];
+    if (l >= 1) {
+      const TransferParams<R>& T = TP.T[l];
+      for (int q = tid; q < NCOL * T.n_act_c; q += kTailCtaThreads) si[TP.coff[l] + q] = T.children[q];
+      for (int q = tid; q < T.n_act_f; q += kTailCtaThreads) si[TP.poff[l] + q] = T.parent_code[q];
+    }
+  }
+  for (int q = tid; q < TP.P[top].n_act * NP; q += kTailCtaThreads) sm[TP.roff[top] + q] = r_top[q];
+  __syncthreads();
+
+  auto nbr_of = [&](int l, int a, int (&nb)[2 * D]) {
+#pragma unroll
+    for (int s = 0; s < 2 * D; ++s) nb[s] = si[TP.noff[l] + s * TP.P[l].n_act + a];
+  };
+  auto smooth = [&](int l, int col, bool zs) {
+    const LevelParams<R>& P = TP.P[l];
+    const int cs = P.colour_start[col], ce = P.colour_start[col + 1], nbnd = P.colour_nbnd[col];
+    R* z = sm + TP.zoff[l];
+    const R* f = sm + TP.roff[l];
+    for (int a = cs + tid; a < ce; a += kTailCtaThreads) {
+      int nb[2 * D];
+      nbr_of(l, a, nb);
+      R c[NP];
+#pragma unroll
+      for (int i = 0; i < NP; ++i) c[i] = 0;
+      add_couplings_f<D, 2, R>(P.k, col, zs, nb, [&](int n, int, R(&un)[NP]) { load_np_vec<NP, R>(z + n * NP, un); },
+                               c);
+      R t[NP];
+      load_np_vec<NP, R>(f + a * NP, t);
+#pragma unroll
+      for (int i = 0; i < NP; ++i) t[i] -= P.hscale * c[i];
+      const int off = a - cs;
+      R y[NP];
+      block_solve_at<D, 2, R>(P, off < nbnd ? sm + TP.boff[l] + (size_t)(P.bstart[col] + off) * NP * NP : nullptr,
+                              t, y);
+      if (P.omega != R(1)) {
+        R uo[NP];
+        if (zs) {
+#pragma unroll
+          for (int i = 0; i < NP; ++i) uo[i] = 0;
+        } else {
+          load_np_vec<NP, R>(z + a * NP, uo);
+        }
+#pragma unroll
+        for (int i = 0; i < NP; ++i) y[i] = (R(1) - P.omega) * uo[i] + P.omega * y[i];
+      }
+      store_np_vec<NP, R>(z + a * NP, y);
+    }
+  };
+
+  for (int l = top; l >= 1; --l) {                 // down: pre-smooth, residual, restrict
+    const LevelParams<R>& P = TP.P[l];
+    if (TP.pre == 0) {
+      for (int q = tid; q < P.n_act * NP; q += kTailCtaThreads) sm[TP.zoff[l] + q] = R(0);
+      __syncthreads();
+    }
+    for (int k = 0; k < TP.pre; ++k)
+      for (int col = 0; col < NCOL; ++col) {
+        smooth(l, col, k == 0);
+        __syncthreads();
+      }
+    const TransferParams<R>& T = TP.T[l];
+    const R* z = sm + TP.zoff[l];
+    const R* f = sm + TP.roff[l];
+    R* rc = sm + TP.roff[l - 1];
+    for (int cc = tid; cc < T.n_act_c; cc += kTailCtaThreads) {
+      R out[NP];
+#pragma unroll
+      for (int j = 0; j < NP; ++j) out[j] = 0;
+#pragma unroll 1
+      for (int o = 0; o < NCOL; ++o) {
+        const int a = si[TP.coff[l] + o * T.n_act_c + cc];
+        if (a < 0) continue;
+        int ca = 0;
+#pragma unroll
+        for (int q = 1; q < NCOL; ++q)
+          if (a >= P.colour_start[q]) ca = q;
+        int nb[2 * D];
+        nbr_of(l, a, nb);
+        R v[NP], y[NP], fa[NP];
+        load_np_vec<NP, R>(z + a * NP, v);
+        load_np_vec<NP, R>(f + a * NP, fa);
+#pragma unroll
+        for (int i = 0; i < NP; ++i) y[i] = 0;
+        const int off = a - P.colour_start[ca];
+        add_self<D, 2, R>(P, nb, off < P.colour_nbnd[ca] ? P.bstart[ca] + off : -1, v, y);
+        add_couplings_f<D, 2, R>(P.k, ca, false, nb,
+                                 [&](int n, int, R(&un)[NP]) { load_np_vec<NP, R>(z + n * NP, un); }, y);
+#pragma unroll
+        for (int i = 0; i < NP; ++i) y[i] = fa[i] - P.hscale * y[i];
+#pragma unroll
+        for (int j = 0; j < NP; ++j) {
+          R acc = 0;
+#pragma unroll
+          for (int i = 0; i < NP; ++i) acc += h_weight<D, R>(T, o, i, j) * y[i];
+          out[j] += acc;
+        }
+      }
+      store_np_vec<NP, R>(rc + cc * NP, out);
+    }
+    __syncthreads();
+  }
+  {                                                // coarse solve in FP64, one warp per row
+    const int n0 = TP.P[0].n_act * NP;
+    const R* r0 = sm + TP.roff[0];
+    R* z0 = sm + TP.zoff[0];
+    const int lane = tid & 31;
+    for (int row = tid >> 5; row < n0; row += kTailCtaThreads / 32) {
+      double acc = 0;
+      for (int c = lane; c < n0; c += 32) acc += coarse_inv[(size_t)row * n0 + c] * (double)r0[c];
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+      if (lane == 0) z0[row] = (R)acc;
+    }
+    __syncthreads();
+  }
+  for (int l = 1; l <= top; ++l) {                 // up: prolongate, post-smooth
+    const LevelParams<R>& P = TP.P[l];
+    const TransferParams<R>& T = TP.T[l];
+    R* z = sm + TP.zoff[l];
+    const R* zc = sm + TP.zoff[l - 1];
+    for (int a = tid; a < P.n_act; a += kTailCtaThreads) {
+      const int code = si[TP.poff[l] + a];
+      if (code < 0) continue;
+      const int par = code >> 3, o = code & 7;
+      R e[NP], u[NP];
+      load_np_vec<NP, R>(zc + par * NP, e);
+      load_np_vec<NP, R>(z + a * NP, u);
+#pragma unroll
+      for (int i = 0; i < NP; ++i) {
+        R acc = 0;
+#pragma unroll
+        for (int j = 0; j < NP; ++j) acc += h_weight<D, R>(T, o, i, j) * e[j];
+        u[i] += acc;
+      }
+      store_np_vec<NP, R>(z + a * NP, u);
+    }
+    __syncthreads();
+    for (int k = 0; k < TP.post; ++k)
+      for (int q = 0; q < NCOL; ++q) {
+        smooth(l, NCOL - 1 - q, false);
+        __syncthreads();
+      }
+  }
+  for (int q = tid; q < TP.P[top].n_act * NP; q += kTailCtaThreads) z_top[q] = sm[TP.zoff[top] + q];
+}
+
 inline unsigned cdiv(size_t a, size_t b) { return (unsigned)((a + b - 1) / b); }
 
 }  // namespace
@@ -809,6 +988,35 @@ cudaError_t launch_vcycle_tail(int dim, const TailLevel<R>* TL, int top, const R
   count_launches();
   return e;
 }
+
+bool tail_cta_fits(int dim, int prec, size_t smem, size_t param_bytes) {
+  (void)param_bytes;
+  if (smem > tail_smem_limit()) return false;
+  cudaError_t e;
+  const int lim = (int)tail_smem_limit();
+  if (dim == 2) e = prec == 0 ? cudaFuncSetAttribute(k_vcycle_tail_cta<2, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim)
+                              : cudaFuncSetAttribute(k_vcycle_tail_cta<2, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+  else e = prec == 0 ? cudaFuncSetAttribute(k_vcycle_tail_cta<3, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim)
+                     : cudaFuncSetAttribute(k_vcycle_tail_cta<3, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return true;
+}
+
+template <typename R>
+cudaError_t launch_vcycle_tail_cta(int dim, const TailCta<R>& TP, const R* r, R* z, const double* coarse_inv,
+                                   size_t smem, cudaStream_t s) {
+  if (dim == 2) SBM_PDL((k_vcycle_tail_cta<2, R>), 1, kTailCtaThreads, smem, s, TP, r, z, coarse_inv);
+  else SBM_PDL((k_vcycle_tail_cta<3, R>), 1, kTailCtaThreads, smem, s, TP, r, z, coarse_inv);
+  count_launches();
+  return cudaGetLastError();
+}
+template cudaError_t launch_vcycle_tail_cta<double>(int, const TailCta<double>&, const double*, double*,
+                                                    const double*, size_t, cudaStream_t);
+template cudaError_t launch_vcycle_tail_cta<float>(int, const TailCta<float>&, const float*, float*, const double*,
+                                                   size_t, cudaStream_t);
 
 template cudaError_t launch_vcycle_tail<double>(int, const TailLevel<double>*, int, const double*, double*,
                                                 const double*, int, int, const TailPlan&, cudaStream_t);

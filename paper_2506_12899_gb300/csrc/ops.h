@@ -86,6 +86,12 @@ cudaError_t launch_vcycle_tail(int dim, const TailLevel<R>* TL, int top, const R
 // Largest dynamic shared memory a tail CTA may use, and whether a cluster of `size` CTAs with
 // `smem` bytes each can be resident (prec 0: FP64, 1: FP32).
 size_t tail_smem_limit();
+// The one-CTA tail (TailCta): whether `smem` bytes fit (sets the kernel's shared-memory limit),
+// and the launch.
+bool tail_cta_fits(int dim, int prec, size_t smem, size_t param_bytes);
+template <typename R>
+cudaError_t launch_vcycle_tail_cta(int dim, const TailCta<R>& TP, const R* r, R* z, const double* coarse_inv,
+                                   size_t smem, cudaStream_t s);
 bool tail_cluster_fits(int dim, int prec, int size, size_t smem);
 
 // y = A x (mode 0) or y = f - A x (mode 1) on one level; TI is the input precision, R the

@@ -135,11 +135,27 @@ struct TailLevel {
   int ncell, zoff, roff;
 };
 
+// One-CTA V-cycle tail: the coarse p = 1 levels 0..top in a single CTA, with every level vector,
+// neighbour table, transfer table and boundary-cell inverse staged in its shared memory.  The
+// whole block is a kernel parameter (__grid_constant__), so every level constant is a constant-
+// bank read.  Offsets are in elements of R (vectors, inverses) or of int (tables).
+constexpr int kMaxTailCta = 6;
+template <typename R>
+struct TailCta {
+  int top, pre, post;
+  int zoff[kMaxTailCta], roff[kMaxTailCta], boff[kMaxTailCta];
+  int noff[kMaxTailCta], coff[kMaxTailCta], poff[kMaxTailCta];   // nbr, children, parent codes
+  int n_bnd[kMaxTailCta];
+  unsigned int_base;               // byte offset of the int area
+  LevelParams<R> P[kMaxTailCta];
+  TransferParams<R> T[kMaxTailCta];
+};
+
 // Launch shape of the cluster tail of one precision: cluster size (CTAs), dynamic shared
 // memory per CTA, and the element offset of the coarse right-hand-side gather buffer.
 struct TailPlan {
   int top = -1;
-  int cluster = 0;
+  int cluster = 0;                 // 1: the one-CTA tail kernel
   size_t smem_bytes = 0;
   int gather_off = 0;
 };

@@ -36,13 +36,15 @@ CASES = {
 _pairs = {}
 
 
-def pair(name, precision="f64", tail=False, cell=0, basis=0):
-    """tail: run the small p = 1 levels as one cluster launch; cell: thread-per-cell kernels
-    (0: size-based default, 1: always where (p+1)^d <= 16, -1: never); basis: FGMRES basis
-    storage (0 double-float, 1 FP64)."""
+def pair(name, precision="f64", tail=0, cell=0, basis=0):
+    """tail: CTAs of the launch that runs the small p = 1 levels' V-cycle (16: a thread-block
+    cluster, 1: one CTA, 0: one launch per phase); cell: thread-per-cell kernels (0: size-based
+    default, 1: always where (p+1)^d <= 16, -1: never); basis: FGMRES basis storage (0
+    double-float, 1 FP64)."""
     key = (name, precision, tail, cell, basis)
     if key not in _pairs:
-        _pairs[key] = Pair(CASES[name], precision, 40000 if tail else -1, cell, krylov_basis=basis)
+        _pairs[key] = Pair(CASES[name], precision, 40000 if tail else -1, cell, krylov_basis=basis,
+                           tail_cluster_ctas=tail)
     return _pairs[key]
 
 
@@ -166,11 +168,12 @@ def test_coarse_solve(name):
     assert rel_max(e, x) <= 1e-11
 
 
-@pytest.mark.parametrize("tail", [True, False], ids=["cluster_tail", "per_level_launches"])
+@pytest.mark.parametrize("tail", [16, 1, 0], ids=["cluster_tail", "cta_tail", "per_level_launches"])
 @pytest.mark.parametrize("name", list(CASES))
 def test_vcycle(name, tail):
     """One V-cycle (Sec. 3) equals the oracle's; FP32 V-cycle within its rounding bound.  Run with
-    the small p = 1 levels in one thread-block-cluster launch and with one launch per phase."""
+    the small p = 1 levels in one thread-block-cluster launch, in one one-CTA launch, and with one
+    launch per phase."""
     P = pair(name, tail=tail)
     L = len(P.H.levels) - 1
     r = W.random_vector(P.H.finest.N, 21)
@@ -241,12 +244,12 @@ def test_gram_schmidt_dots(n, nv):
 
 
 def test_cluster_tail_is_one_launch():
-    """On a hierarchy of small p = 1 levels the whole V-cycle is one cluster launch; with the tail
-    disabled it is one launch per phase."""
+    """On a hierarchy of small p = 1 levels the whole V-cycle is one cluster launch or one one-CTA
+    launch; with the tail disabled it is one launch per phase."""
     import paper_2506_12899_gb300 as S
-    P, Q = pair("disk2d_p1_n32", tail=True), pair("disk2d_p1_n32", tail=False)
+    P, C, Q = pair("disk2d_p1_n32", tail=16), pair("disk2d_p1_n32", tail=1), pair("disk2d_p1_n32", tail=0)
     r = torch.tensor(W.random_vector(P.H.finest.N, 1), device="cuda")
-    for g, expect in ((P.gpu, 1), (Q.gpu, None)):
+    for g, expect in ((P.gpu, 1), (C.gpu, 1), (Q.gpu, None)):
         g.vcycle(r)
         torch.cuda.synchronize()
         n0 = S.kernel_launches()
@@ -260,7 +263,7 @@ def test_cluster_tail_is_one_launch():
 
 
 @pytest.mark.parametrize("name", ["disk2d_p1_n32", "star2d_p2_n32", "sphere3d_p2_n8", "ellipsoid3d_p3_n12"])
-@pytest.mark.parametrize("tail,basis", [(True, 0), (False, 1)], ids=["cluster_tail", "fp64_basis"])
+@pytest.mark.parametrize("tail,basis", [(16, 0), (1, 0), (0, 1)], ids=["cluster_tail", "cta_tail", "fp64_basis"])
 def test_fgmres_fp64_variants(name, tail, basis):
     """FGMRES with the cluster V-cycle tail, and with the FP64 Krylov basis instead of the
     double-float one: same iteration count and solution (1e-10) as the oracle."""
