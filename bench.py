@@ -296,10 +296,11 @@ def run_ours(args) -> dict | None:
     hbm, src = peaks()
     fp64_tflops = 152 * 2.07e9 * 2 * 2 / 1e12    # SMs x max clock x 2 FP64 FMA/clk/SM x 2 flop
     kernels = {
-        # one colour of the finest-level (p) block Gauss-Seidel sweep: f of the colour, u of the
-        # neighbouring colours, u written, dense inverses of the colour's boundary cells, face data
+        # one colour of the finest-level (p) block Gauss-Seidel sweep: f of the colour (N/2^d),
+        # u of the d neighbouring colours (d N/2^d), u written (N/2^d), the dense inverses of the
+        # colour's boundary cells and their face data
         f"k_smooth_cell<{prob.dim},{info['p'] + 1},float> (finest level, one colour)":
-            ("hbm", (4 * N + info["n_boundary"] * nb * nb * 4 + 4 * geo_bytes) / ncol, t_smooth),
+            ("hbm", ((prob.dim + 2) * 4 * N + info["n_boundary"] * nb * nb * 4 + 4 * geo_bytes) / ncol, t_smooth),
         f"k_apply_cell<{prob.dim},{info['p'] + 1},float> (FP32 operator, finest level)":
             ("hbm", 2 * 4 * N + 4 * geo_bytes, t_apply32),
         f"k_apply<{prob.dim},{info['p'] + 1},double> (FP64 operator, finest level)":

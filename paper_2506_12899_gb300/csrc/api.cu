@@ -175,6 +175,7 @@ struct Context {
   int ws_m = 0, ws_prec = -1;
   double* V = nullptr;               // FP64 basis [m+1][N] (krylov_basis = 1)
   float2* V2 = nullptr;              // double-float basis [m+1][N] (krylov_basis = 0)
+  float2* wdf = nullptr;             // w as double-float between the Gram-Schmidt sweeps
   void* Z = nullptr;
   double* w = nullptr;
   float* r32 = nullptr;
@@ -627,6 +628,7 @@ void ensure_krylov(Context& C, int m) {
     C.V = C.dalloc<double>((size_t)(m + 1) * N);
   } else {
     C.V2 = C.dalloc<float2>((size_t)(m + 1) * N);
+    C.wdf = C.dalloc<float2>(N);
     if (prec == SBM_F64) C.v64 = C.dalloc<double>(N);
   }
   C.ws_basis = basis;
@@ -677,22 +679,21 @@ void arnoldi_step_work(Context& C, int j, cudaStream_t s) {
     CUDA_TRY(launch_axpy_norm(C.V, N, j + 1, h2, C.w, N, C.partial, hn, s));
     CUDA_TRY(launch_div_scalar(C.w, hn, C.V + (size_t)(j + 1) * N, N, s));
   } else {                                          // double-float basis, same three sweeps
-    const float2* Vj = C.V2 + (size_t)j * N;
+    // v_j rounded to the V-cycle precision is in r32 / v64 (written with v_j itself)
     if (prec == SBM_F32) {
       float* Zj = static_cast<float*>(C.Z) + (size_t)j * N;
-      CUDA_TRY(launch_df_to<float>(Vj, C.r32, N, s));
       vcycle_rec<float>(C, Lf, C.r32, Zj, s);
       CUDA_TRY((launch_apply<float, double>(dim, p, F.P64, Zj, nullptr, C.w, 0, s)));
     } else {
       double* Zj = static_cast<double*>(C.Z) + (size_t)j * N;
-      CUDA_TRY(launch_df_to<double>(Vj, C.v64, N, s));
       vcycle_rec<double>(C, Lf, C.v64, Zj, s);
       CUDA_TRY((launch_apply<double, double>(dim, p, F.P64, Zj, nullptr, C.w, 0, s)));
     }
-    CUDA_TRY(launch_gs_dot(C.V2, N, j + 1, C.w, N, C.partial, h1, s));
-    CUDA_TRY(launch_gs_axpy_dot(C.V2, N, j + 1, h1, C.w, N, C.partial, h2, s));
-    CUDA_TRY(launch_gs_axpy_norm(C.V2, N, j + 1, h2, C.w, N, C.partial, hn, s));
-    CUDA_TRY(launch_gs_scale(C.w, hn, C.V2 + (size_t)(j + 1) * N, N, s));
+    CUDA_TRY(launch_gs_dot(C.V2, N, j + 1, C.w, C.wdf, N, C.partial, h1, s));
+    CUDA_TRY(launch_gs_axpy_dot(C.V2, N, j + 1, h1, C.wdf, N, C.partial, h2, s));
+    CUDA_TRY(launch_gs_axpy_norm(C.V2, N, j + 1, h2, C.wdf, N, C.partial, hn, s));
+    if (prec == SBM_F32) CUDA_TRY((launch_gs_scale<float2, float>(C.wdf, hn, C.V2 + (size_t)(j + 1) * N, C.r32, N, s)));
+    else CUDA_TRY((launch_gs_scale<float2, double>(C.wdf, hn, C.V2 + (size_t)(j + 1) * N, C.v64, N, s)));
   }
   CUDA_TRY(launch_hess_column(h1, h2, hn, j + 1, col, s));
   CUDA_TRY(cudaMemcpyAsync(C.host_pinned, col, (j + 2) * sizeof(double), cudaMemcpyDeviceToHost, s));
@@ -780,7 +781,8 @@ int solve_impl(Context& C, const double* b, double* x, double tol, int m, int ma
         break;
       }
       if (C.desc.krylov_basis == 1) CUDA_TRY(launch_div_scalar(r0, hn, r0, N, s));
-      else CUDA_TRY(launch_gs_scale(r0, hn, C.V2, N, s));
+      else if (prec == SBM_F32) CUDA_TRY((launch_gs_scale<double, float>(r0, hn, C.V2, C.r32, N, s)));
+      else CUDA_TRY((launch_gs_scale<double, double>(r0, hn, C.V2, C.v64, N, s)));
       std::fill(H.begin(), H.end(), 0.0);
       std::fill(g.begin(), g.end(), 0.0);
       g[0] = beta;

@@ -44,21 +44,47 @@ __host__ __device__ constexpr int tang_dim(int dir, int q) {
   return D == 2 ? 1 - dir : (dir == 0 ? 1 + q : (dir == 1 ? 2 * q : q));
 }
 
-// Vector loads.  COH: through L2 only (ld.global.cg), for the cluster V-cycle, where values
-// written by other CTAs in the previous phase are read after a cluster barrier and L1 is not
-// coherent; otherwise ordinary L1-cached loads (a thread reads its cell's contiguous values,
-// so consecutive load instructions of a warp hit the lines the first one brought in).
-template <bool COH, typename T>
+// Global loads are ordinary L1-cached loads (a thread reads its cell's contiguous values, so
+// consecutive load instructions of a warp hit the lines the first one brought in).
+template <typename T>
 __device__ __forceinline__ T ldv(const T* p) {
-  if (COH) return __ldcg(p);
   return *p;
 }
 
-template <int D, int N1, bool COH, typename TI, typename R>
+// The (p+1)^d values of cell a.  When a cell's values fill whole 16-byte words (2D and 3D p = 1
+// in FP32 and FP64) and the vector is 16-byte aligned, they are read with 16-byte loads.
+template <int D, int N1, typename TI, typename R>
 __device__ __forceinline__ void load_cell(const TI* __restrict__ x, int a, R (&v)[CD<D, N1>::NP]) {
   constexpr int NP = CD<D, N1>::NP;
+  if constexpr ((NP * sizeof(TI)) % 16 == 0) {
+    if ((reinterpret_cast<uintptr_t>(x) & 15) == 0) {
+      TI t[NP];
+      const uint4* q = reinterpret_cast<const uint4*>(x + (size_t)a * NP);
 #pragma unroll
-  for (int i = 0; i < NP; ++i) v[i] = (R)ldv<COH>(x + (size_t)a * NP + i);
+      for (int c = 0; c < (int)(NP * sizeof(TI) / 16); ++c) reinterpret_cast<uint4*>(t)[c] = q[c];
+#pragma unroll
+      for (int i = 0; i < NP; ++i) v[i] = (R)t[i];
+      return;
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < NP; ++i) v[i] = (R)ldv(x + (size_t)a * NP + i);
+}
+
+// Stores the values of cell a, with 16-byte stores under the same conditions as load_cell.
+template <int D, int N1, typename R>
+__device__ __forceinline__ void store_cell(R* __restrict__ x, int a, const R (&v)[CD<D, N1>::NP]) {
+  constexpr int NP = CD<D, N1>::NP;
+  if constexpr ((NP * sizeof(R)) % 16 == 0) {
+    if ((reinterpret_cast<uintptr_t>(x) & 15) == 0) {
+      uint4* q = reinterpret_cast<uint4*>(x + (size_t)a * NP);
+#pragma unroll
+      for (int c = 0; c < (int)(NP * sizeof(R) / 16); ++c) q[c] = reinterpret_cast<const uint4*>(v)[c];
+      return;
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < NP; ++i) x[(size_t)a * NP + i] = v[i];
 }
 
 // Loads the 16-byte aligned values of one cell from shared memory (local or another CTA of the
@@ -127,12 +153,12 @@ __device__ __forceinline__ void add_couplings_f(const LevelConsts<R>& C, int col
 }
 
 // Couplings with the neighbour values read from the global vector u.
-template <int D, int N1, bool COH, typename TI, typename R>
+template <int D, int N1, typename TI, typename R>
 __device__ __forceinline__ void add_couplings(const LevelParams<R>& P, const TI* __restrict__ u, int col,
                                               bool zero_start, const int (&nb)[2 * D], R (&y)[CD<D, N1>::NP]) {
   constexpr int NP = CD<D, N1>::NP;
   add_couplings_f<D, N1, R>(P.k, col, zero_start, nb,
-                            [&](int n, int, R(&un)[NP]) { load_cell<D, N1, COH, TI, R>(u, n, un); }, y);
+                            [&](int n, int, R(&un)[NP]) { load_cell<D, N1, TI, R>(u, n, un); }, y);
 }
 
 // y += A_KK v (volume + own halves of interior faces + surrogate faces), reference scaling.
@@ -248,18 +274,18 @@ __device__ __forceinline__ void load_nbr(const LevelParams<R>& P, int a, int (&n
 }
 
 // y = (A x)_a with the reference scaling h^(d-2) applied.
-template <int D, int N1, bool COH, typename TI, typename R>
+template <int D, int N1, typename TI, typename R>
 __device__ __forceinline__ void cell_apply(const LevelParams<R>& P, const TI* __restrict__ x, int a,
                                            R (&y)[CD<D, N1>::NP]) {
   constexpr int NP = CD<D, N1>::NP;
   int nb[2 * D];
   load_nbr<D, R>(P, a, nb);
   R v[NP];
-  load_cell<D, N1, COH, TI, R>(x, a, v);
+  load_cell<D, N1, TI, R>(x, a, v);
 #pragma unroll
   for (int i = 0; i < NP; ++i) y[i] = 0;
   add_self<D, N1, R>(P, nb, boundary_index(P, a, 1 << D), v, y);
-  add_couplings<D, N1, COH, TI, R>(P, x, 0, false, nb, y);
+  add_couplings<D, N1, TI, R>(P, x, 0, false, nb, y);
 #pragma unroll
   for (int i = 0; i < NP; ++i) y[i] *= P.hscale;
 }
@@ -273,7 +299,7 @@ __global__ void __launch_bounds__(kCellThreads) k_apply_cell(const __grid_consta
   const int a = blockIdx.x * kCellThreads + threadIdx.x;
   if (a >= P.n_act) return;
   R r[NP];
-  cell_apply<D, N1, false, TI, R>(P, x, a, r);
+  cell_apply<D, N1, TI, R>(P, x, a, r);
 #pragma unroll
   for (int i = 0; i < NP; ++i) y[(size_t)a * NP + i] = MODE == 1 ? f[(size_t)a * NP + i] - r[i] : r[i];
 }
@@ -349,7 +375,7 @@ __device__ __forceinline__ void block_solve_at(const LevelParams<R>& P, const R*
 // One cell of one colour of the block Gauss-Seidel sweep (Eq. 16): cell a of the colour
 // starting at cs whose first nbnd cells are boundary cells (dense inverse, boundary index
 // b0 + a - cs); the others use the fast diagonalisation.  zero_start as in k_smooth.
-template <int D, int N1, bool COH, typename R>
+template <int D, int N1, typename R>
 __device__ __forceinline__ void smooth_one(const LevelParams<R>& P, int col, int zero_start, int cs, int nbnd,
                                            int b0, int a, const R* __restrict__ f, R* __restrict__ u) {
   constexpr int NP = CD<D, N1>::NP;
@@ -359,19 +385,19 @@ __device__ __forceinline__ void smooth_one(const LevelParams<R>& P, int col, int
   R c[NP];
 #pragma unroll
   for (int i = 0; i < NP; ++i) c[i] = 0;
-  add_couplings<D, N1, COH, R, R>(P, u, col, zero_start != 0, nb, c);
+  add_couplings<D, N1, R, R>(P, u, col, zero_start != 0, nb, c);
   R t[NP];
+  load_cell<D, N1, R, R>(f, a, t);
 #pragma unroll
-  for (int i = 0; i < NP; ++i) t[i] = ldv<COH>(f + (size_t)a * NP + i) - P.hscale * c[i];
+  for (int i = 0; i < NP; ++i) t[i] -= P.hscale * c[i];
   R y[NP];
   block_solve<D, N1, R>(P, isB ? b0 + (a - cs) : -1, t, y);
   if (P.omega == R(1)) {
-#pragma unroll
-    for (int i = 0; i < NP; ++i) u[(size_t)a * NP + i] = y[i];
+    store_cell<D, N1, R>(u, a, y);
   } else {
 #pragma unroll
     for (int i = 0; i < NP; ++i) {
-      const R uo = zero_start ? R(0) : ldv<COH>(u + (size_t)a * NP + i);
+      const R uo = zero_start ? R(0) : ldv(u + (size_t)a * NP + i);
       u[(size_t)a * NP + i] = (R(1) - P.omega) * uo + P.omega * y[i];
     }
   }
@@ -389,7 +415,7 @@ __global__ void __launch_bounds__(kCellThreads) k_smooth_cell(const __grid_const
   const int last = isB ? cs + nbnd : ce;
   const int a = first + threadIdx.x;
   if (a >= last) return;
-  smooth_one<D, N1, false, R>(P, col, zero_start, cs, nbnd, b0, a, f, u);
+  smooth_one<D, N1, R>(P, col, zero_start, cs, nbnd, b0, a, f, u);
 }
 
 // Residual and p-restriction fused, one thread per cell (Eqs. 11, 18).
@@ -404,7 +430,7 @@ __global__ void __launch_bounds__(kCellThreads) k_resid_restrict_p_cell(const __
   const int a = blockIdx.x * kCellThreads + threadIdx.x;
   if (a >= P.n_act) return;
   R r[NP];
-  cell_apply<D, N1, false, R, R>(P, u, a, r);
+  cell_apply<D, N1, R, R>(P, u, a, r);
 #pragma unroll
   for (int i = 0; i < NP; ++i) r[i] = f[(size_t)a * NP + i] - r[i];
 #pragma unroll
@@ -422,51 +448,6 @@ __global__ void __launch_bounds__(kCellThreads) k_resid_restrict_p_cell(const __
   }
 }
 
-// Residual and h-restriction fused for coarse cell cc (p = 1 on both meshes): the residuals of
-// its active children are formed in registers and restricted (Eq. 18).
-template <int D, bool COH, typename R>
-__device__ __forceinline__ void resid_restrict_h_one(const LevelParams<R>& P, const TransferParams<R>& T,
-                                                     const R* __restrict__ u, const R* __restrict__ f,
-                                                     R* __restrict__ rc, int cc) {
-  constexpr int NP = CD<D, 2>::NP;
-  R out[NP];
-#pragma unroll
-  for (int j = 0; j < NP; ++j) out[j] = 0;
-#pragma unroll
-  for (int o = 0; o < (1 << D); ++o) {
-    const int a = T.children[(size_t)o * T.n_act_c + cc];
-    if (a < 0) continue;
-    R r[NP];
-    cell_apply<D, 2, COH, R, R>(P, u, a, r);
-#pragma unroll
-    for (int i = 0; i < NP; ++i) r[i] = ldv<COH>(f + (size_t)a * NP + i) - r[i];
-#pragma unroll
-    for (int j = 0; j < NP; ++j) {
-      R acc = 0;
-#pragma unroll
-      for (int i = 0; i < NP; ++i) {
-        R wgt = T.Ph[o & 1][(i & 1) * 2 + (j & 1)] * T.Ph[(o >> 1) & 1][((i >> 1) & 1) * 2 + ((j >> 1) & 1)];
-        if (D == 3) wgt *= T.Ph[(o >> 2) & 1][((i >> 2) & 1) * 2 + ((j >> 2) & 1)];
-        acc += wgt * r[i];
-      }
-      out[j] += acc;
-    }
-  }
-#pragma unroll
-  for (int j = 0; j < NP; ++j) rc[(size_t)cc * NP + j] = out[j];
-}
-
-template <int D, typename R>
-__global__ void __launch_bounds__(kCellThreads) k_resid_restrict_h_cell(const __grid_constant__ LevelParams<R> P,
-                                                                        const __grid_constant__ TransferParams<R> T,
-                                                                        const R* __restrict__ u,
-                                                                        const R* __restrict__ f, R* __restrict__ rc) {
-  pdl_entry();
-  const int cc = blockIdx.x * kCellThreads + threadIdx.x;
-  if (cc >= T.n_act_c) return;
-  resid_restrict_h_one<D, false, R>(P, T, u, f, rc, cc);
-}
-
 // h-transfer weight of fine node i (child o of its parent) and coarse node j, p = 1 on both
 // meshes (Eqs. 17, 18): the tensor product of the 1D child matrices.
 template <int D, typename R>
@@ -475,6 +456,45 @@ __device__ __forceinline__ R h_weight(const TransferParams<R>& T, int o, int i, 
   if (D == 3) wgt *= T.Ph[(o >> 2) & 1][((i >> 2) & 1) * 2 + ((j >> 2) & 1)];
   return wgt;
 }
+
+// One group of 2^D adjacent lanes per coarse cell, lane o of the group handling child o: the
+// child's residual in registers, its restriction, then a fixed butterfly sum over the group.
+template <int D, typename R>
+__global__ void __launch_bounds__(kCellThreads) k_resid_restrict_h_cell(const __grid_constant__ LevelParams<R> P,
+                                                                        const __grid_constant__ TransferParams<R> T,
+                                                                        const R* __restrict__ u,
+                                                                        const R* __restrict__ f, R* __restrict__ rc) {
+  pdl_entry();
+  constexpr int NCOL = 1 << D, NP = CD<D, 2>::NP;
+  const int t = blockIdx.x * kCellThreads + threadIdx.x;
+  const int cc = t / NCOL, o = t % NCOL;
+  R out[NP];
+#pragma unroll
+  for (int j = 0; j < NP; ++j) out[j] = 0;
+  const int a = cc < T.n_act_c ? T.children[(size_t)o * T.n_act_c + cc] : -1;
+  if (a >= 0) {
+    R r[NP], fa[NP];
+    cell_apply<D, 2, R, R>(P, u, a, r);
+    load_cell<D, 2, R, R>(f, a, fa);
+#pragma unroll
+    for (int i = 0; i < NP; ++i) r[i] = fa[i] - r[i];
+#pragma unroll
+    for (int j = 0; j < NP; ++j) {
+      R acc = 0;
+#pragma unroll
+      for (int i = 0; i < NP; ++i) acc += h_weight<D, R>(T, o, i, j) * r[i];
+      out[j] = acc;
+    }
+  }
+#pragma unroll
+  for (int off = 1; off < NCOL; off <<= 1)
+#pragma unroll
+    for (int j = 0; j < NP; ++j) out[j] += __shfl_xor_sync(0xffffffffu, out[j], off);
+  if (o == 0 && cc < T.n_act_c)
+#pragma unroll
+    for (int j = 0; j < NP; ++j) rc[(size_t)cc * NP + j] = out[j];
+}
+
 
 // ----------------------------------------------------------------------------------------------
 // The V-cycle below and including level `top` (all of them p = 1 h-levels) in one launch of a
@@ -916,7 +936,7 @@ template <typename R>
 cudaError_t launch_resid_restrict_h_cell(int dim, const LevelParams<R>& P, const TransferParams<R>& T, const R* u,
                                         const R* f, R* rc, cudaStream_t s) {
   if (T.n_act_c == 0) return cudaSuccess;
-  const unsigned g = cdiv(T.n_act_c, kCellThreads);
+  const unsigned g = cdiv((size_t)T.n_act_c << dim, kCellThreads);
   if (dim == 2) SBM_PDL((k_resid_restrict_h_cell<2, R>), g, kCellThreads, 0, s, P, T, u, f, rc);
   else if (dim == 3) SBM_PDL((k_resid_restrict_h_cell<3, R>), g, kCellThreads, 0, s, P, T, u, f, rc);
   else return cudaErrorInvalidValue;

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <mutex>
+#include <type_traits>
 
 #include "ops.h"
 
@@ -252,12 +253,13 @@ __device__ __forceinline__ void block_partials_df(float (&s)[NV], float (&c)[NV]
   }
 }
 
-// partial[block][k] = this block's share of V_k . w (V double-float, w FP64), k < NV; each
-// thread sweeps its elements with a grid stride, reading every V_k once.
+// partial[block][k] = this block's share of V_k . w (V double-float, w FP64), k < NV; w is also
+// written as double-float to wdf for the next sweeps.  Each thread sweeps its entries with a
+// grid stride, reading every V_k once.
 template <int NV>
 __global__ void __launch_bounds__(kDotThreads) k_gs_dot(const float2* __restrict__ V, size_t ldv,
-                                                        const double* __restrict__ w, size_t N,
-                                                        double* __restrict__ partial) {
+                                                        const double* __restrict__ w, float2* __restrict__ wdf,
+                                                        size_t N, double* __restrict__ partial) {
   pdl_entry();
   float s[NV], c[NV];
 #pragma unroll
@@ -265,53 +267,72 @@ __global__ void __launch_bounds__(kDotThreads) k_gs_dot(const float2* __restrict
   const size_t stride = (size_t)gridDim.x * kDotThreads;
   for (size_t i = (size_t)blockIdx.x * kDotThreads + threadIdx.x; i < N; i += stride) {
     const float2 wi = df_from_double(w[i]);
+    wdf[i] = wi;
 #pragma unroll
     for (int k = 0; k < NV; ++k) df_dot_acc(s[k], c[k], V[k * ldv + i], wi);
   }
   block_partials_df<NV>(s, c, partial);
 }
 
-// w <- w - sum_k h[k] V_k in double-float (w stored back in FP64), then the partial sums of
-// V_k . w for k < NV, or of |w|^2 when NORM (nv vectors, no dots).  The dot pass reads V_k
-// again (an L1/L2 hit right after the update pass) instead of holding NV values per thread.
+// wdf <- wdf - sum_{k<NV} h[k] V_k in double-float, then the partial sums of V_k . wdf for
+// k < NV, or of |wdf|^2 when NORM.  The dot pass reads V_k again (an L1/L2 hit right after the
+// update pass) instead of holding NV values per thread.
 template <int NV, bool NORM>
 __global__ void __launch_bounds__(kDotThreads) k_gs_axpy_dot(const float2* __restrict__ V, size_t ldv,
-                                                             const double* __restrict__ h, double* __restrict__ w,
-                                                             size_t N, int nv, double* __restrict__ partial) {
+                                                             const double* __restrict__ h, float2* __restrict__ wdf,
+                                                             size_t N, double* __restrict__ partial) {
   pdl_entry();
   constexpr int NA = NORM ? 1 : NV;
   __shared__ float2 hs[kMaxVec];
-  if (threadIdx.x < nv) hs[threadIdx.x] = df_from_double(h[threadIdx.x]);
+  if (threadIdx.x < NV) hs[threadIdx.x] = df_from_double(h[threadIdx.x]);
   __syncthreads();
   float s[NA], c[NA];
 #pragma unroll
   for (int k = 0; k < NA; ++k) s[k] = c[k] = 0.f;
   const size_t stride = (size_t)gridDim.x * kDotThreads;
   for (size_t i = (size_t)blockIdx.x * kDotThreads + threadIdx.x; i < N; i += stride) {
-    float2 wi = df_from_double(w[i]);
+    float2 wi = wdf[i];
+#pragma unroll
+    for (int k = 0; k < NV; ++k) wi = df_sub_prod(wi, hs[k], V[k * ldv + i]);
+    wdf[i] = wi;
     if (NORM) {
-      for (int k = 0; k < nv; ++k) wi = df_sub_prod(wi, hs[k], V[k * ldv + i]);
-      w[i] = df_to_double(wi);
       df_dot_acc(s[0], c[0], wi, wi);
     } else {
 #pragma unroll
-      for (int k = 0; k < NV; ++k) wi = df_sub_prod(wi, hs[k], V[k * ldv + i]);
-      w[i] = df_to_double(wi);
-#pragma unroll
-      for (int k = 0; k < NV; ++k) df_dot_acc(s[k], c[k], ld_again(V + k * ldv + i), wi);
+      for (int k = 0; k < NA; ++k) df_dot_acc(s[k], c[k], ld_again(V + k * ldv + i), wi);
     }
   }
   block_partials_df<NA>(s, c, partial);
 }
 
-// v = w / s[0] as double-float.
-__global__ void k_gs_scale(const double* __restrict__ w, const double* __restrict__ sc, float2* __restrict__ v,
-                           size_t N) {
+// v = w / sc[0] as double-float (w FP64 or double-float), and, if out is not null, v rounded to
+// TO (the next V-cycle's input).
+template <typename TW, typename TO>
+__global__ void k_gs_scale(const TW* __restrict__ w, const double* __restrict__ sc, float2* __restrict__ v,
+                           TO* __restrict__ out, size_t N) {
   pdl_entry();
   const double inv = 1.0 / sc[0];
+  const float2 g = df_from_double(inv);
   const size_t stride = (size_t)gridDim.x * blockDim.x;
-  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += stride)
-    v[i] = df_from_double(w[i] * inv);
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += stride) {
+    float2 r;
+    if constexpr (sizeof(TW) == 8 && std::is_same<TW, double>::value) {
+      r = df_from_double(w[i] * inv);
+    } else {                                        // double-float product, renormalised
+      const float2 a = w[i];
+      const float p = __fmul_rn(a.x, g.x);
+      float e = fmaf(a.x, g.x, -p);
+      e = fmaf(a.x, g.y, e);
+      e = fmaf(a.y, g.x, e);
+      const float hi = __fadd_rn(p, e);
+      r = make_float2(hi, __fsub_rn(e, __fsub_rn(hi, p)));
+    }
+    v[i] = r;
+    if (out) {
+      if constexpr (sizeof(TO) == 4) out[i] = __fadd_rn(r.x, r.y);
+      else out[i] = df_to_double(r);
+    }
+  }
 }
 
 // y = v rounded to FP32 or to FP64.
@@ -443,13 +464,13 @@ int gs_blocks(size_t N) {
   return (int)g;
 }
 
-cudaError_t launch_gs_dot(const float2* V, size_t ldv, int nv, const double* w, size_t N, double* partial,
-                          double* out, cudaStream_t s) {
+cudaError_t launch_gs_dot(const float2* V, size_t ldv, int nv, const double* w, float2* wdf, size_t N,
+                          double* partial, double* out, cudaStream_t s) {
   if (nv < 1 || nv > kMaxVec) return cudaErrorInvalidValue;
   const int nblk = gs_blocks(N);
   switch (nv) {
 #define SBM_GD_CASE(K) \
-  case K: SBM_PDL((k_gs_dot<K>), nblk, kDotThreads, 0, s, V, ldv, w, N, partial); break;
+  case K: SBM_PDL((k_gs_dot<K>), nblk, kDotThreads, 0, s, V, ldv, w, wdf, N, partial); break;
     SBM_GD_CASE(1) SBM_GD_CASE(2) SBM_GD_CASE(3) SBM_GD_CASE(4) SBM_GD_CASE(5) SBM_GD_CASE(6)
     SBM_GD_CASE(7) SBM_GD_CASE(8) SBM_GD_CASE(9) SBM_GD_CASE(10) SBM_GD_CASE(11) SBM_GD_CASE(12)
     SBM_GD_CASE(13) SBM_GD_CASE(14) SBM_GD_CASE(15) SBM_GD_CASE(16) SBM_GD_CASE(17) SBM_GD_CASE(18)
@@ -463,13 +484,14 @@ cudaError_t launch_gs_dot(const float2* V, size_t ldv, int nv, const double* w, 
   return cudaGetLastError();
 }
 
-cudaError_t launch_gs_axpy_dot(const float2* V, size_t ldv, int nv, const double* h, double* w, size_t N,
-                               double* partial, double* out, cudaStream_t s) {
+template <bool NORM>
+cudaError_t launch_gs_axpy(const float2* V, size_t ldv, int nv, const double* h, float2* wdf, size_t N,
+                           double* partial, double* out, cudaStream_t s) {
   if (nv < 1 || nv > kMaxVec) return cudaErrorInvalidValue;
   const int nblk = gs_blocks(N);
   switch (nv) {
 #define SBM_GA_CASE(K) \
-  case K: SBM_PDL((k_gs_axpy_dot<K, false>), nblk, kDotThreads, 0, s, V, ldv, h, w, N, nv, partial); break;
+  case K: SBM_PDL((k_gs_axpy_dot<K, NORM>), nblk, kDotThreads, 0, s, V, ldv, h, wdf, N, partial); break;
     SBM_GA_CASE(1) SBM_GA_CASE(2) SBM_GA_CASE(3) SBM_GA_CASE(4) SBM_GA_CASE(5) SBM_GA_CASE(6)
     SBM_GA_CASE(7) SBM_GA_CASE(8) SBM_GA_CASE(9) SBM_GA_CASE(10) SBM_GA_CASE(11) SBM_GA_CASE(12)
     SBM_GA_CASE(13) SBM_GA_CASE(14) SBM_GA_CASE(15) SBM_GA_CASE(16) SBM_GA_CASE(17) SBM_GA_CASE(18)
@@ -478,26 +500,36 @@ cudaError_t launch_gs_axpy_dot(const float2* V, size_t ldv, int nv, const double
     SBM_GA_CASE(31) SBM_GA_CASE(32)
 #undef SBM_GA_CASE
   }
-  SBM_PDL(k_reduce_partials, 1, 32 * nv, 0, s, partial, nblk, nv, out, 0);
+  const int nout = NORM ? 1 : nv;
+  SBM_PDL(k_reduce_partials, 1, 32 * nout, 0, s, partial, nblk, nout, out, NORM ? 1 : 0);
   count_launches(2);
   return cudaGetLastError();
 }
 
-cudaError_t launch_gs_axpy_norm(const float2* V, size_t ldv, int nv, const double* h, double* w, size_t N,
+cudaError_t launch_gs_axpy_dot(const float2* V, size_t ldv, int nv, const double* h, float2* wdf, size_t N,
+                               double* partial, double* out, cudaStream_t s) {
+  return launch_gs_axpy<false>(V, ldv, nv, h, wdf, N, partial, out, s);
+}
+
+cudaError_t launch_gs_axpy_norm(const float2* V, size_t ldv, int nv, const double* h, float2* wdf, size_t N,
                                 double* partial, double* out, cudaStream_t s) {
-  if (nv < 1 || nv > kMaxVec) return cudaErrorInvalidValue;
-  const int nblk = gs_blocks(N);
-  SBM_PDL((k_gs_axpy_dot<0, true>), nblk, kDotThreads, 0, s, V, ldv, h, w, N, nv, partial);
-  SBM_PDL(k_reduce_partials, 1, 32, 0, s, partial, nblk, 1, out, 1);
-  count_launches(2);
-  return cudaGetLastError();
+  return launch_gs_axpy<true>(V, ldv, nv, h, wdf, N, partial, out, s);
 }
 
-cudaError_t launch_gs_scale(const double* w, const double* sc, float2* v, size_t N, cudaStream_t s) {
-  SBM_PDL(k_gs_scale, grid_for(N), 256, 0, s, w, sc, v, N);
+template <typename TW, typename TO>
+cudaError_t launch_gs_scale(const TW* w, const double* sc, float2* v, TO* out, size_t N, cudaStream_t s) {
+  SBM_PDL((k_gs_scale<TW, TO>), grid_for(N), 256, 0, s, w, sc, v, out, N);
   count_launches();
   return cudaGetLastError();
 }
+template cudaError_t launch_gs_scale<double, float>(const double*, const double*, float2*, float*, size_t,
+                                                    cudaStream_t);
+template cudaError_t launch_gs_scale<double, double>(const double*, const double*, float2*, double*, size_t,
+                                                     cudaStream_t);
+template cudaError_t launch_gs_scale<float2, float>(const float2*, const double*, float2*, float*, size_t,
+                                                    cudaStream_t);
+template cudaError_t launch_gs_scale<float2, double>(const float2*, const double*, float2*, double*, size_t,
+                                                     cudaStream_t);
 
 template <typename TO>
 cudaError_t launch_df_to(const float2* v, TO* y, size_t N, cudaStream_t s) {

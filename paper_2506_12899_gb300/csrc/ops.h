@@ -149,15 +149,20 @@ cudaError_t launch_div_scalar(const double* w, const double* s, double* v, size_
 template <typename TI, typename TO>
 cudaError_t launch_cast(const TI* x, TO* y, size_t N, cudaStream_t s);
 // c = a + b (k <= 32 entries), c[k] = hn at index k
-// Gram-Schmidt on a double-float basis V (pairs hi, lo of FP32 per entry, Dekker 1971):
-// out = V^T w; w -= V h then out = V^T w; w -= V h then out = |w|; v = w / s[0]; v rounded.
-cudaError_t launch_gs_dot(const float2* V, size_t ldv, int nv, const double* w, size_t N, double* partial,
-                          double* out, cudaStream_t s);
-cudaError_t launch_gs_axpy_dot(const float2* V, size_t ldv, int nv, const double* h, double* w, size_t N,
+// Gram-Schmidt on a double-float basis V (pairs hi, lo of FP32 per entry, Dekker 1971), with w
+// carried between the sweeps as double-float in wdf:
+//   gs_dot:        wdf = w (FP64 in), out = V^T w
+//   gs_axpy_dot:   wdf -= V h, out = V^T wdf
+//   gs_axpy_norm:  wdf -= V h, out = |wdf|
+//   gs_scale:      v = w / s[0] (w FP64 or double-float), and out = v rounded to TO if non-null
+cudaError_t launch_gs_dot(const float2* V, size_t ldv, int nv, const double* w, float2* wdf, size_t N,
+                          double* partial, double* out, cudaStream_t s);
+cudaError_t launch_gs_axpy_dot(const float2* V, size_t ldv, int nv, const double* h, float2* wdf, size_t N,
                                double* partial, double* out, cudaStream_t s);
-cudaError_t launch_gs_axpy_norm(const float2* V, size_t ldv, int nv, const double* h, double* w, size_t N,
+cudaError_t launch_gs_axpy_norm(const float2* V, size_t ldv, int nv, const double* h, float2* wdf, size_t N,
                                 double* partial, double* out, cudaStream_t s);
-cudaError_t launch_gs_scale(const double* w, const double* sc, float2* v, size_t N, cudaStream_t s);
+template <typename TW, typename TO>
+cudaError_t launch_gs_scale(const TW* w, const double* sc, float2* v, TO* out, size_t N, cudaStream_t s);
 template <typename TO>
 cudaError_t launch_df_to(const float2* v, TO* y, size_t N, cudaStream_t s);
 cudaError_t launch_hess_column(const double* h1, const double* h2, const double* hn, int k, double* col,
