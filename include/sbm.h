@@ -96,8 +96,10 @@ typedef struct {
   int launch_overlap;    /* > 0: the level and Krylov kernels use programmatic dependent launch,  */
                          /* so each may be scheduled while its predecessor finishes; < 0: plain   */
                          /* stream-ordered launches; 0: on with the FP32 V-cycle, off with FP64   */
-  int krylov_basis;      /* FGMRES basis storage: 0 double-float pairs (hi, lo) of FP32 with the  */
-                         /* Gram-Schmidt sweeps on the FP32 pipes (~48-bit significands); 1 FP64  */
+  int krylov_basis;      /* FGMRES basis storage and Arnoldi arithmetic: 0 double-float pairs     */
+                         /* (hi, lo) of FP32, Gram-Schmidt and (FP32 V-cycle, (p+1)^d <= 16) the  */
+                         /* operator A z on the FP32 pipes (~48-bit significands); 1 FP64; 2      */
+                         /* double-float basis with the FP64 operator                             */
   int cell_kernel_min_cells; /* launches over at least this many cells use one thread per cell   */
                          /* when (p+1)^d <= 16; 0: always in FP32, never in FP64; < 0: never       */
   void* stream;          /* cudaStream_t for every launch of this context                        */

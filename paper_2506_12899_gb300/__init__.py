@@ -194,7 +194,8 @@ class Solver:
         tail_cluster_ctas CTAs (0 or 1: one CTA; 2..16: a thread-block cluster).
         launch_overlap: programmatic dependent launch between the solver's kernels, > 0 on, < 0 off,
         0 on with the FP32 V-cycle and off with FP64 (measured best).  krylov_basis: 0 double-float
-        FGMRES basis (Gram-Schmidt on the FP32 pipes), 1 FP64 basis.  cell_kernel_min_cells: launches over at least that many
+        FGMRES basis and Arnoldi operator (on the FP32 pipes), 1 FP64, 2 double-float basis with the
+        FP64 operator.  cell_kernel_min_cells: launches over at least that many
         cells use one thread per cell (0: library default, < 0: never, 1: always where
         (p+1)^d <= 16)."""
         import torch

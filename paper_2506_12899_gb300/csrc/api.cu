@@ -43,6 +43,9 @@ struct DevLevel {
   double* coarse_inv = nullptr;
   LevelParams<double> P64{};
   LevelParams<float> P32{};
+  LevelParams<dfl> Pdf{};         // double-float operator constants (finest level, thread-per-cell shapes)
+  dfl* dhat_df = nullptr;
+  bool has_df = false;
   TransferParams<double> T64{};   // transfer between level l-1 (coarse) and this level
   TransferParams<float> T32{};
   void* z[2] = {nullptr, nullptr};
@@ -353,7 +356,7 @@ void validate(const sbm_setup_desc& d) {
   if (d.pre_smooth < 0 || d.post_smooth < 0 || d.pre_smooth > 16 || d.post_smooth > 16) bad("smoothing steps");
   if (d.precision != SBM_F64 && d.precision != SBM_F32) bad("precision must be SBM_F64 or SBM_F32");
   if (d.extension != 0 && d.extension != 1) bad("extension must be 0 or 1");
-  if (d.krylov_basis != 0 && d.krylov_basis != 1) bad("krylov_basis must be 0 or 1");
+  if (d.krylov_basis < 0 || d.krylov_basis > 2) bad("krylov_basis must be 0, 1 or 2");
   if (d.tail_cluster_ctas < 0 || d.tail_cluster_ctas > 16 || (d.tail_cluster_ctas & (d.tail_cluster_ctas - 1)))
     bad("tail_cluster_ctas must be 0, 1, 2, 4, 8 or 16");
   const double w0 = d.hi[0] - d.lo[0];
@@ -402,6 +405,13 @@ Context* build_context(const sbm_setup_desc& d, bool device) {
     if (!L.H.coarse_inv.empty()) L.coarse_inv = C->upload(L.H.coarse_inv);
     L.P64 = make_params<double>(L, L.dhat64, L.binv64);
     L.P32 = make_params<float>(L, L.dhat32, L.binv32);
+    if (&L == &C->lv.back() && cell_kernels(L.H.dim, L.H.p)) {   // Arnoldi operator in double-float
+      std::vector<dfl> dh(L.H.dhat.size());
+      for (size_t i = 0; i < dh.size(); ++i) dh[i] = dfl(L.H.dhat[i]);
+      L.dhat_df = C->upload(dh);
+      L.Pdf = make_params<dfl>(L, L.dhat_df, nullptr);
+      L.has_df = true;
+    }
     // default: thread-per-cell kernels for FP32 (measured faster at every size from 512^2 to
     // 2048^2 cells), per-dof block kernels for FP64 (FP64 ALU bound; measured faster)
     if (d.cell_kernel_min_cells == 0) {
@@ -624,7 +634,7 @@ void ensure_krylov(Context& C, int m) {
   if (C.ws_m >= m && C.ws_prec == prec && C.ws_basis == basis) return;
   C.drop_graphs();                                  // captured pointers change
   const size_t N = C.lv.back().H.n_dof();
-  if (basis == 1) {
+  if (basis == 1) {                                 // FP64 basis
     C.V = C.dalloc<double>((size_t)(m + 1) * N);
   } else {
     C.V2 = C.dalloc<float2>((size_t)(m + 1) * N);
@@ -683,13 +693,19 @@ void arnoldi_step_work(Context& C, int j, cudaStream_t s) {
     if (prec == SBM_F32) {
       float* Zj = static_cast<float*>(C.Z) + (size_t)j * N;
       vcycle_rec<float>(C, Lf, C.r32, Zj, s);
-      CUDA_TRY((launch_apply<float, double>(dim, p, F.P64, Zj, nullptr, C.w, 0, s)));
+      if (C.desc.krylov_basis == 0 && F.has_df) {   // w = A z in double-float, straight into wdf
+        CUDA_TRY((launch_apply_cell<float, dfl>(dim, p, F.Pdf, Zj, nullptr, reinterpret_cast<dfl*>(C.wdf), 0, s)));
+        CUDA_TRY(launch_gs_dot_df(C.V2, N, j + 1, C.wdf, N, C.partial, h1, s));
+      } else {
+        CUDA_TRY((launch_apply<float, double>(dim, p, F.P64, Zj, nullptr, C.w, 0, s)));
+        CUDA_TRY(launch_gs_dot(C.V2, N, j + 1, C.w, C.wdf, N, C.partial, h1, s));
+      }
     } else {
       double* Zj = static_cast<double*>(C.Z) + (size_t)j * N;
       vcycle_rec<double>(C, Lf, C.v64, Zj, s);
       CUDA_TRY((launch_apply<double, double>(dim, p, F.P64, Zj, nullptr, C.w, 0, s)));
+      CUDA_TRY(launch_gs_dot(C.V2, N, j + 1, C.w, C.wdf, N, C.partial, h1, s));
     }
-    CUDA_TRY(launch_gs_dot(C.V2, N, j + 1, C.w, C.wdf, N, C.partial, h1, s));
     CUDA_TRY(launch_gs_axpy_dot(C.V2, N, j + 1, h1, C.wdf, N, C.partial, h2, s));
     CUDA_TRY(launch_gs_axpy_norm(C.V2, N, j + 1, h2, C.wdf, N, C.partial, hn, s));
     if (prec == SBM_F32) CUDA_TRY((launch_gs_scale<float2, float>(C.wdf, hn, C.V2 + (size_t)(j + 1) * N, C.r32, N, s)));

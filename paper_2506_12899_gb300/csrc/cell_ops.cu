@@ -1048,6 +1048,8 @@ template cudaError_t launch_apply_cell<float, float>(int, int, const LevelParams
                                                      float*, int, cudaStream_t);
 template cudaError_t launch_apply_cell<float, double>(int, int, const LevelParams<double>&, const float*,
                                                       const double*, double*, int, cudaStream_t);
+template cudaError_t launch_apply_cell<float, dfl>(int, int, const LevelParams<dfl>&, const float*, const dfl*,
+                                                   dfl*, int, cudaStream_t);
 template cudaError_t launch_smooth_cell<double>(int, int, const LevelParams<double>&, int, int, const double*,
                                                 double*, cudaStream_t);
 template cudaError_t launch_smooth_cell<float>(int, int, const LevelParams<float>&, int, int, const float*, float*,

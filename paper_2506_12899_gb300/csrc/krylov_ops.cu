@@ -210,6 +210,16 @@ __device__ __forceinline__ float2 df_sub_prod(float2 w, float2 h, float2 v) {
   return make_float2(hi, __fsub_rn(lo, __fsub_rn(hi, t)));
 }
 
+// a + b in double-float, renormalised.
+__device__ __forceinline__ float2 df_add(float2 a, float2 b) {
+  const float t = __fadd_rn(a.x, b.x);
+  const float z = __fsub_rn(t, a.x);
+  float e = __fadd_rn(__fsub_rn(a.x, __fsub_rn(t, z)), __fsub_rn(b.x, z));
+  e = __fadd_rn(e, __fadd_rn(a.y, b.y));
+  const float hi = __fadd_rn(t, e);
+  return make_float2(hi, __fsub_rn(e, __fsub_rn(hi, t)));
+}
+
 // A load the compiler may not merge with an earlier load of the same address (volatile asm):
 // the dot pass of k_gs_axpy_dot re-reads V from L1 instead of keeping NV values live.
 __device__ __forceinline__ float2 ld_again(const float2* p) {
@@ -256,9 +266,9 @@ __device__ __forceinline__ void block_partials_df(float (&s)[NV], float (&c)[NV]
 // partial[block][k] = this block's share of V_k . w (V double-float, w FP64), k < NV; w is also
 // written as double-float to wdf for the next sweeps.  Each thread sweeps its entries with a
 // grid stride, reading every V_k once.
-template <int NV>
+template <int NV, typename TW>
 __global__ void __launch_bounds__(kDotThreads) k_gs_dot(const float2* __restrict__ V, size_t ldv,
-                                                        const double* __restrict__ w, float2* __restrict__ wdf,
+                                                        const TW* __restrict__ w, float2* __restrict__ wdf,
                                                         size_t N, double* __restrict__ partial) {
   pdl_entry();
   float s[NV], c[NV];
@@ -266,8 +276,13 @@ __global__ void __launch_bounds__(kDotThreads) k_gs_dot(const float2* __restrict
   for (int k = 0; k < NV; ++k) s[k] = c[k] = 0.f;
   const size_t stride = (size_t)gridDim.x * kDotThreads;
   for (size_t i = (size_t)blockIdx.x * kDotThreads + threadIdx.x; i < N; i += stride) {
-    const float2 wi = df_from_double(w[i]);
-    wdf[i] = wi;
+    float2 wi;
+    if constexpr (std::is_same<TW, double>::value) {
+      wi = df_from_double(w[i]);
+      wdf[i] = wi;
+    } else {
+      wi = w[i];
+    }
 #pragma unroll
     for (int k = 0; k < NV; ++k) df_dot_acc(s[k], c[k], V[k * ldv + i], wi);
   }
@@ -292,8 +307,25 @@ __global__ void __launch_bounds__(kDotThreads) k_gs_axpy_dot(const float2* __res
   const size_t stride = (size_t)gridDim.x * kDotThreads;
   for (size_t i = (size_t)blockIdx.x * kDotThreads + threadIdx.x; i < N; i += stride) {
     float2 wi = wdf[i];
+    if (NORM) {
+      // all NV loads issued before any arithmetic; the products are summed in four independent
+      // double-float chains and the sum subtracted once, which shortens the dependent chain
+      float2 v[NORM ? NV : 1];
 #pragma unroll
-    for (int k = 0; k < NV; ++k) wi = df_sub_prod(wi, hs[k], V[k * ldv + i]);
+      for (int k = 0; k < NV; ++k) v[k] = V[k * ldv + i];
+      float2 part[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) part[q] = make_float2(0.f, 0.f);
+#pragma unroll
+      for (int k = 0; k < NV; ++k) part[k & 3] = df_sub_prod(part[k & 3], hs[k], v[NORM ? k : 0]);   // -= h v
+#pragma unroll
+      for (int q = 0; q < 4; ++q) wi = df_add(wi, part[q]);
+    } else {
+      // one chain with the loads inline: the 2 NV accumulators of the dot pass leave no room to
+      // hold the NV values as well
+#pragma unroll
+      for (int k = 0; k < NV; ++k) wi = df_sub_prod(wi, hs[k], V[k * ldv + i]);
+    }
     wdf[i] = wi;
     if (NORM) {
       df_dot_acc(s[0], c[0], wi, wi);
@@ -464,13 +496,14 @@ int gs_blocks(size_t N) {
   return (int)g;
 }
 
-cudaError_t launch_gs_dot(const float2* V, size_t ldv, int nv, const double* w, float2* wdf, size_t N,
-                          double* partial, double* out, cudaStream_t s) {
+template <typename TW>
+cudaError_t launch_gs_dot_t(const float2* V, size_t ldv, int nv, const TW* w, float2* wdf, size_t N,
+                            double* partial, double* out, cudaStream_t s) {
   if (nv < 1 || nv > kMaxVec) return cudaErrorInvalidValue;
   const int nblk = gs_blocks(N);
   switch (nv) {
 #define SBM_GD_CASE(K) \
-  case K: SBM_PDL((k_gs_dot<K>), nblk, kDotThreads, 0, s, V, ldv, w, wdf, N, partial); break;
+  case K: SBM_PDL((k_gs_dot<K, TW>), nblk, kDotThreads, 0, s, V, ldv, w, wdf, N, partial); break;
     SBM_GD_CASE(1) SBM_GD_CASE(2) SBM_GD_CASE(3) SBM_GD_CASE(4) SBM_GD_CASE(5) SBM_GD_CASE(6)
     SBM_GD_CASE(7) SBM_GD_CASE(8) SBM_GD_CASE(9) SBM_GD_CASE(10) SBM_GD_CASE(11) SBM_GD_CASE(12)
     SBM_GD_CASE(13) SBM_GD_CASE(14) SBM_GD_CASE(15) SBM_GD_CASE(16) SBM_GD_CASE(17) SBM_GD_CASE(18)
@@ -482,6 +515,16 @@ cudaError_t launch_gs_dot(const float2* V, size_t ldv, int nv, const double* w, 
   SBM_PDL(k_reduce_partials, 1, 32 * nv, 0, s, partial, nblk, nv, out, 0);
   count_launches(2);
   return cudaGetLastError();
+}
+
+cudaError_t launch_gs_dot(const float2* V, size_t ldv, int nv, const double* w, float2* wdf, size_t N,
+                          double* partial, double* out, cudaStream_t s) {
+  return launch_gs_dot_t<double>(V, ldv, nv, w, wdf, N, partial, out, s);
+}
+
+cudaError_t launch_gs_dot_df(const float2* V, size_t ldv, int nv, const float2* wdf, size_t N, double* partial,
+                             double* out, cudaStream_t s) {
+  return launch_gs_dot_t<float2>(V, ldv, nv, wdf, nullptr, N, partial, out, s);
 }
 
 template <bool NORM>

@@ -4,6 +4,7 @@
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
+#include "dfloat.h"
 #include "sbm_internal.h"
 
 #include <atomic>
@@ -157,6 +158,9 @@ cudaError_t launch_cast(const TI* x, TO* y, size_t N, cudaStream_t s);
 //   gs_scale:      v = w / s[0] (w FP64 or double-float), and out = v rounded to TO if non-null
 cudaError_t launch_gs_dot(const float2* V, size_t ldv, int nv, const double* w, float2* wdf, size_t N,
                           double* partial, double* out, cudaStream_t s);
+// gs_dot with w already double-float (wdf, read only)
+cudaError_t launch_gs_dot_df(const float2* V, size_t ldv, int nv, const float2* wdf, size_t N, double* partial,
+                             double* out, cudaStream_t s);
 cudaError_t launch_gs_axpy_dot(const float2* V, size_t ldv, int nv, const double* h, float2* wdf, size_t N,
                                double* partial, double* out, cudaStream_t s);
 cudaError_t launch_gs_axpy_norm(const float2* V, size_t ldv, int nv, const double* h, float2* wdf, size_t N,
