@@ -41,6 +41,14 @@ WORKLOADS = {
 DESCRIPTION = {
     "star2d_p2_n512": "2D star r(theta)=0.7(1+0.1 sin(5 theta+phi)), 512^2 background cells, Q2 DG-SBM, "
                       "u=exp(x)cos(2y), lambda=0.75, hp-multigrid p2->p1 then h to 8^2, FGMRES(30) tol 1e-8",
+    "disk2d_p1_n32": "2D disk r=0.7, 32^2 background cells, Q1 DG-SBM, u=sin(pi x)sin(pi y), lambda>=0.5, "
+                     "hp-multigrid h to 4^2, FGMRES(30) tol 1e-8",
+    "sphere3d_p1_n64": "3D sphere r=0.7, 64^3 background cells, Q1 DG-SBM, u=sin sin sin, lambda=0.75, "
+                       "h-multigrid to 4^3, FGMRES(30) tol 1e-8",
+    "sphere3d_p2_n64": "3D sphere r=0.7, 64^3 background cells, Q2 DG-SBM, u=sin sin sin, lambda=0.75, "
+                       "hp-multigrid p2->p1 then h to 4^3, FGMRES(30) tol 1e-8",
+    "ellipsoid3d_p3_n96": "3D rotated ellipsoid (0.75,0.6,0.5), 96^3 background cells, Q3 DG-SBM, u=sin sin sin, "
+                          "lambda=0.75, hp-multigrid p3->p2->p1 then h to 6^3, FGMRES(30) tol 1e-8",
 }
 TOL, RESTART, MAX_IT = 1e-8, 30, 300
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
@@ -142,9 +150,11 @@ def peaks():
 
 def committed_traffic(workload: str, kernel: str):
     """dram__bytes_read.sum + dram__bytes_write.sum per launch of `kernel` on `workload` from the
-    committed ncu summary profiles/<kernel family>_<workload>_traffic.txt (one line
-    'traffic_bytes_per_launch <B>'), or None when there is none."""
-    name = kernel.split("<")[0]
+    committed ncu summary profiles/<kernel instantiation>_<workload>_traffic.txt, e.g.
+    k_smooth_cell_2_2_float_star2d_p2_n512_traffic.txt (one line 'traffic_bytes_per_launch <B>'),
+    or None when there is none."""
+    import re
+    name = re.sub(r"[^A-Za-z0-9]+", "_", kernel.split(" ")[0]).strip("_")
     path = os.path.join(ROOT, "profiles", f"{name}_{workload}_traffic.txt")
     try:
         with open(path) as fh:
@@ -289,6 +299,16 @@ def run_ours(args) -> dict | None:
     V64 = torch.rand((nv, N), device="cuda", dtype=torch.float64)
     geo_bytes = info["n_sface"] * (info["p"] + 1) ** (prob.dim - 1) * prob.dim
     ncol = 2 ** prob.dim
+    # the p = 1 level on the same mesh (one below the finest), whose smoother is the kernel with
+    # the largest share of the solve (three p = 1 levels, 8 launches each per V-cycle)
+    Lp1 = s32.num_levels - 2
+    info1 = s32.info(Lp1)
+    N1 = info1["n_dof"]
+    nb1 = (info1["p"] + 1) ** prob.dim
+    r1 = torch.rand(N1, device="cuda", dtype=torch.float32)
+    u1 = torch.rand_like(r1)
+    geo1 = info1["n_sface"] * (info1["p"] + 1) ** (prob.dim - 1) * prob.dim
+    t_smooth1 = event_time(torch, lambda: s32.smooth(r1, u1, level=Lp1), 20, flush) / 2 ** prob.dim
     t_apply32 = event_time(torch, lambda: s32.apply(r32, y32), 20, flush)
     t_apply64 = event_time(torch, lambda: s64.apply(x64, y64), 20, flush)
     t_smooth = event_time(torch, lambda: s32.smooth(r32, u32), 20, flush) / ncol
@@ -296,6 +316,8 @@ def run_ours(args) -> dict | None:
     hbm, src = peaks()
     fp64_tflops = 152 * 2.07e9 * 2 * 2 / 1e12    # SMs x max clock x 2 FP64 FMA/clk/SM x 2 flop
     kernels = {
+        f"k_smooth_cell<{prob.dim},{info1['p'] + 1},float> ({info1['n']}^{prob.dim} p={info1['p']} level, one colour)":
+            ("hbm", ((prob.dim + 2) * 4 * N1 + info1["n_boundary"] * nb1 * nb1 * 4 + 4 * geo1) / ncol, t_smooth1),
         # one colour of the finest-level (p) block Gauss-Seidel sweep: f of the colour (N/2^d),
         # u of the d neighbouring colours (d N/2^d), u written (N/2^d), the dense inverses of the
         # colour's boundary cells and their face data
@@ -306,7 +328,8 @@ def run_ours(args) -> dict | None:
         f"k_apply<{prob.dim},{info['p'] + 1},double> (FP64 operator, finest level)":
             ("hbm", 2 * 8 * N + 8 * geo_bytes, t_apply64),
         # first Gram-Schmidt sweep h = V^T w at width 27, plus its partial-sum reduction
-        "k_multi_dot<27> (FP64 Gram-Schmidt sweep)": ("alu", 2 * nv * N, t_dots),
+        # sbm_dots: the FP64 multi-vector dot product (the solver's own sweeps run in double-float)
+        "k_multi_dot<27> (FP64, sbm_dots)": ("alu", 2 * nv * N, t_dots),
     }
     rooflines = {}
     for k, (bound, amount, t_) in kernels.items():
@@ -341,8 +364,8 @@ def run_ours(args) -> dict | None:
         "speedup_fp32_over_fp64_vcycle": round(statistics.mean(times64) / ms32, 3),
         "learned": learned,
         "solves_per_s_total": round(world * args.steps / (total_ms / 1e3), 3),
-        "apply_gbs": {"fp32": list(rooflines.values())[1]["achieved"],
-                      "fp64": list(rooflines.values())[2]["achieved"]},
+        "apply_gbs": {"fp32": list(rooflines.values())[2]["achieved"],
+                      "fp64": list(rooflines.values())[3]["achieved"]},
         "clocks": clk,
         "e2e": {"value": round(statistics.mean(e2e), 4), "unit": "ms", "h2d_bytes_per_step": 8 * N,
                 "d2h_bytes_per_step": 8 * N},
@@ -394,6 +417,68 @@ def run_profile(args) -> None:
         g.vcycle(f, y)
         torch.cuda.synchronize()
         print("N", N, "LEVELS", g.num_levels, flush=True)
+
+
+def run_learned_heldout(args) -> dict:
+    """a7 on a family of domains: the MLP is trained on pairs collected from the training seeds
+    (4 seeded starts x 3 stationary V-cycle steps each), then every held-out domain is solved
+    plain, with the learned correction and the fallback rule, and with the correction forced on.
+    Reports FGMRES iterations and device times (FP32 V-cycle, FP64 FGMRES, tol 1e-8)."""
+    import torch
+    import paper_2506_12899_gb300 as S
+    dim = 2 if args.family == "star2d" else 3
+    make = (lambda sd: W.random_star2d_p3(128, sd)) if dim == 2 else (lambda sd: W.random_ellipsoid3d_p3(32, sd))
+    mlp = S.Mlp(dim, 3, 128, seed=0)
+    gen = torch.Generator(device="cuda").manual_seed(0)
+    t0 = time.perf_counter()
+    pairs = 0
+    for sd in range(1000, 1000 + args.n_train):
+        g = S.Solver(make(sd), "f32")
+        u0 = (2 * torch.rand((4, g.n_dof()), generator=gen, device="cuda", dtype=torch.float32) - 1).contiguous()
+        pairs += g.collect(mlp, u0, 3)
+        g.close()
+    collect_s = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    loss = mlp.train(epochs=20, batch=4096, lr=1e-3, seed=0)
+    train_s = time.perf_counter() - t0
+
+    def timed(g, b, x):
+        x.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        info = g.solve(b, x, tol=TOL, restart=RESTART, max_it=MAX_IT)
+        e1.record()
+        e1.synchronize()
+        return info, e0.elapsed_time(e1)
+
+    rows = []
+    for sd in range(2000, 2000 + args.n_eval):
+        g = S.Solver(make(sd), "f32")
+        b = g.rhs()
+        x = torch.zeros_like(b)
+        timed(g, b, x)
+        plain, tp = timed(g, b, x)
+        rate = plain.true_rel_residual ** (1.0 / max(plain.iterations, 1))
+        g.attach_mlp(mlp, 1.0, fallback_rate=rate)
+        timed(g, b, x)
+        gated, tg = timed(g, b, x)
+        g.attach_mlp(mlp, 1.0, fallback_rate=0.0)
+        timed(g, b, x)
+        forced, tf = timed(g, b, x)
+        g.attach_mlp(None)
+        rows.append({"seed": sd, "plain": [plain.iterations, round(tp, 3)],
+                     "learned_gated": [gated.iterations, round(tg, 3), gated.learned_fallback, gated.converged],
+                     "learned_forced": [forced.iterations, round(tf, 3), forced.converged]})
+        g.close()
+    med = lambda k, i: statistics.median(r[k][i] for r in rows)
+    return {"experiment": f"learned boundary correction, held-out {args.family} p=3", "train_seeds": args.n_train,
+            "eval_seeds": args.n_eval, "train_pairs": pairs, "train_loss": loss, "collect_s": round(collect_s, 1),
+            "train_s": round(train_s, 1),
+            "median_iterations": {"plain": med("plain", 0), "learned_gated": med("learned_gated", 0),
+                                  "learned_forced": med("learned_forced", 0)},
+            "median_ms": {"plain": med("plain", 1), "learned_gated": med("learned_gated", 1),
+                          "learned_forced": med("learned_forced", 1)},
+            "fallbacks": sum(1 for r in rows if r["learned_gated"][2]), "rows": rows}
 
 
 def run_reference(args) -> dict | None:
@@ -453,7 +538,14 @@ def main():
     ap.add_argument("--tail-cluster", type=int, default=0, help="--profile kernels: cluster-tail CTAs")
     ap.add_argument("--krylov-basis", type=int, default=0, choices=[0, 1],
                     help="--profile solve: FGMRES basis storage (0 double-float, 1 FP64)")
+    ap.add_argument("--experiment", choices=["learned-heldout"], help="a7 on held-out domains (no bench line)")
+    ap.add_argument("--family", default="star2d", choices=["star2d", "ellipsoid3d"])
+    ap.add_argument("--n-train", type=int, default=256)
+    ap.add_argument("--n-eval", type=int, default=32)
     args = ap.parse_args()
+    if args.experiment:
+        print(json.dumps(run_learned_heldout(args)))
+        return
     if args.profile:
         run_profile(args)
         return

@@ -315,6 +315,12 @@ LevelParams<R> make_params(const DevLevel& D, const R* dhat, const R* binv) {
     P.k.inv_denom[k] = (R)(1.0 / den);
     P.k.lam[k] = (R)H.lam[k];
   }
+  const double hs = std::pow(H.h, H.dim - 2);
+  for (int i = 0; i < H.np; ++i) {
+    double ls = H.lam[i % n1] + H.lam[(i / n1) % n1];
+    if (H.dim == 3) ls += H.lam[i / (n1 * n1)];
+    P.k.inv_diag[i] = (R)(1.0 / (hs * ls));
+  }
   return P;
 }
 

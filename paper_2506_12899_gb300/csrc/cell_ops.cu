@@ -349,9 +349,7 @@ __device__ __forceinline__ void block_solve_at(const LevelParams<R>& P, const R*
   }
 #pragma unroll
   for (int i = 0; i < NP; ++i) {
-    R lsum = C.lam[i % N1] + C.lam[(i / N1) % N1];
-    if (D == 3) lsum += C.lam[i / (N1 * N1)];
-    t[i] = t[i] / (P.hscale * lsum);
+    t[i] = t[i] * C.inv_diag[i];
   }
 #pragma unroll
   for (int dir = 0; dir < D; ++dir) {              // S^(x d) v

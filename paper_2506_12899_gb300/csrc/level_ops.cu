@@ -427,9 +427,7 @@ __global__ void __launch_bounds__(256) k_smooth(const __grid_constant__ LevelPar
       src = dst;
       dst = tmp;
     }
-    R lsum = C.lam[ii[0]] + C.lam[ii[1]];
-    if (D == 3) lsum += C.lam[ii[2]];
-    yv = yv / (P.hscale * lsum);
+    yv = yv * C.inv_diag[i];
     dst[c * NP + i] = yv;
     __syncthreads();
     {

@@ -95,6 +95,7 @@ struct LevelConsts {
   R w[kMaxN1], e0[kMaxN1], e1[kMaxN1], d0[kMaxN1], d1[kMaxN1];
   R x[kMaxN1], inv_denom[kMaxN1];   // nodes and 1 / prod_{j != k}(x_k - x_j)
   R lam[kMaxN1];
+  R inv_diag[kMaxN1 * kMaxN1 * kMaxN1];   // 1 / (h^(d-2) (lam_i + lam_j (+ lam_k))), x fastest
 };
 
 // Device parameter block of one level for one precision (passed by value to the kernels).

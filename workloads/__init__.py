@@ -164,6 +164,19 @@ def ellipsoid3d_p3(n: int = 96, seed: int = 0) -> Problem:
                    exact=EXACT_SINPROD, coarsest_n=6 if n % 6 == 0 else 4, **HIGH_ORDER)
 
 
+def random_star2d_p3(n: int = 128, seed: int = 1000) -> Problem:
+    """Learned-correction family (2D): a seeded random star on 128^2 Q3 cells.  Training domains
+    use seeds 1000..1255, held-out domains 2000..2031."""
+    return Problem(name=f"random_star2d_p3_n{n}_s{seed}", dim=2, n=n, p=3, shape=random_star(seed),
+                   exact=EXACT_EXPCOS, coarsest_n=8 if n >= 64 else 4, **HIGH_ORDER)
+
+
+def random_ellipsoid3d_p3(n: int = 32, seed: int = 1000) -> Problem:
+    """Learned-correction family (3D): a seeded random ellipsoid on 32^3 Q3 cells."""
+    return Problem(name=f"random_ellipsoid3d_p3_n{n}_s{seed}", dim=3, n=n, p=3, shape=random_ellipsoid(seed),
+                   exact=EXACT_SINPROD, coarsest_n=4, **HIGH_ORDER)
+
+
 def paper_disk(level: int, p: int, lam: float, dim: int = 2) -> Problem:
     """Paper-replica unit disk/sphere (Sec. 5): box [-1.01,1.01]^d, 4*2^level cells per direction,
     sigma_Gamma = 5, sigma_F = 1 (scaled by (p+1)^2/h), kappa > lambda (kappa = 1 for lambda = 1),
