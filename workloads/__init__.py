@@ -152,29 +152,35 @@ def star2d_p2(n: int = 512, seed: int = 0) -> Problem:
                    exact=EXACT_EXPCOS, coarsest_n=8 if n >= 64 else 4, **HIGH_ORDER)
 
 
+# In 3D at p >= 2 the first-order Taylor extension u(x~) + d.grad u(x~) gives a V-cycle that does
+# not converge (sphere p=2: 59 FGMRES iterations at 16^3, stagnation from 32^3; ellipsoid p=3:
+# stagnation from 24^3; oracle and GPU agree), so those workloads take the full-order extension,
+# the cell polynomial evaluated at x~ + d (20 iterations at 64^3 p=2, 19 at 48^3 p=3).
 def sphere3d(n: int = 64, p: int = 1, seed: int = 0) -> Problem:
-    """3D p=1 / p=2 workload: 64^3 cells, sphere r=0.7 with seeded centre offset."""
+    """3D p=1 / p=2 workload: 64^3 cells, sphere r=0.7 with seeded centre offset (full-order
+    boundary extension at p >= 2)."""
     return Problem(name=f"sphere3d_p{p}_n{n}", dim=3, n=n, p=p, shape=disk(3, seed),
-                   exact=EXACT_SINPROD, coarsest_n=4, **HIGH_ORDER)
+                   exact=EXACT_SINPROD, coarsest_n=4, extension=1 if p >= 2 else 0, **HIGH_ORDER)
 
 
 def ellipsoid3d_p3(n: int = 96, seed: int = 0) -> Problem:
-    """3D p=3 workload: 96^3 cells, ellipsoid (0.75,0.6,0.5) rotated by seeded angles."""
+    """3D p=3 workload: 96^3 cells, ellipsoid (0.75,0.6,0.5) rotated by seeded angles (full-order
+    boundary extension)."""
     return Problem(name=f"ellipsoid3d_p3_n{n}", dim=3, n=n, p=3, shape=ellipsoid(seed),
-                   exact=EXACT_SINPROD, coarsest_n=6 if n % 6 == 0 else 4, **HIGH_ORDER)
+                   exact=EXACT_SINPROD, coarsest_n=6 if n % 6 == 0 else 4, extension=1, **HIGH_ORDER)
 
 
 def random_star2d_p3(n: int = 128, seed: int = 1000) -> Problem:
     """Learned-correction family (2D): a seeded random star on 128^2 Q3 cells.  Training domains
     use seeds 1000..1255, held-out domains 2000..2031."""
     return Problem(name=f"random_star2d_p3_n{n}_s{seed}", dim=2, n=n, p=3, shape=random_star(seed),
-                   exact=EXACT_EXPCOS, coarsest_n=8 if n >= 64 else 4, **HIGH_ORDER)
+                   exact=EXACT_EXPCOS, coarsest_n=8 if n >= 64 else 4, extension=1, **HIGH_ORDER)
 
 
 def random_ellipsoid3d_p3(n: int = 32, seed: int = 1000) -> Problem:
     """Learned-correction family (3D): a seeded random ellipsoid on 32^3 Q3 cells."""
     return Problem(name=f"random_ellipsoid3d_p3_n{n}_s{seed}", dim=3, n=n, p=3, shape=random_ellipsoid(seed),
-                   exact=EXACT_SINPROD, coarsest_n=4, **HIGH_ORDER)
+                   exact=EXACT_SINPROD, coarsest_n=4, extension=1, **HIGH_ORDER)
 
 
 def paper_disk(level: int, p: int, lam: float, dim: int = 2) -> Problem:
