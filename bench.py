@@ -37,6 +37,7 @@ WORKLOADS = {
     "sphere3d_p1_n64": lambda seed: W.sphere3d(64, 1, seed),
     "sphere3d_p2_n64": lambda seed: W.sphere3d(64, 2, seed),
     "ellipsoid3d_p3_n96": lambda seed: W.ellipsoid3d_p3(96, seed),
+    "ellipsoid3d_p3_n96_s1": lambda seed: W.ellipsoid3d_p3(96, seed, smooth=1),
 }
 DESCRIPTION = {
     "star2d_p2_n512": "2D star r(theta)=0.7(1+0.1 sin(5 theta+phi)), 512^2 background cells, Q2 DG-SBM, "
@@ -48,7 +49,9 @@ DESCRIPTION = {
     "sphere3d_p2_n64": "3D sphere r=0.7, 64^3 background cells, Q2 DG-SBM, u=sin sin sin, lambda=0.75, "
                        "hp-multigrid p2->p1 then h to 4^3, FGMRES(30) tol 1e-8",
     "ellipsoid3d_p3_n96": "3D rotated ellipsoid (0.75,0.6,0.5), 96^3 background cells, Q3 DG-SBM, u=sin sin sin, "
-                          "lambda=0.75, hp-multigrid p3->p2->p1 then h to 6^3, FGMRES(30) tol 1e-8",
+                          "lambda=0.75, hp-multigrid p3->p2->p1 then h to 6^3, 2 pre/2 post smoothing steps, "
+                          "FGMRES(30) tol 1e-8",
+    "ellipsoid3d_p3_n96_s1": "the 96^3 p=3 ellipsoid with 1 pre/1 post smoothing step (stalls without help)",
 }
 TOL, RESTART, MAX_IT = 1e-8, 30, 300
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
@@ -476,8 +479,11 @@ def run_learned_heldout(args) -> dict:
         return info, e0.elapsed_time(e1)
 
     rows = []
-    for sd in range(2000, 2000 + args.n_eval):
-        g = S.Solver(make(sd), "f32")
+    evals = [(sd, make(sd)) for sd in range(2000, 2000 + args.n_eval)]
+    if args.eval_workload:
+        evals.append((args.eval_workload, WORKLOADS[args.eval_workload](0)))
+    for sd, prob_e in evals:
+        g = S.Solver(prob_e, "f32")
         b = g.rhs()
         x = torch.zeros_like(b)
         timed(g, b, x)
@@ -494,7 +500,9 @@ def run_learned_heldout(args) -> dict:
                      "learned_gated": [gated.iterations, round(tg, 3), gated.learned_fallback, gated.converged],
                      "learned_forced": [forced.iterations, round(tf, 3), forced.converged]})
         g.close()
-    med = lambda k, i: statistics.median(r[k][i] for r in rows)
+    extra = [r for r in rows if not isinstance(r["seed"], int)]
+    rows = [r for r in rows if isinstance(r["seed"], int)]
+    med = lambda k, i: statistics.median(r[k][i] for r in rows) if rows else None
     return {"experiment": f"learned boundary correction, held-out {args.family} p=3", "train_seeds": args.n_train,
             "eval_seeds": args.n_eval, "train_pairs": pairs, "train_loss": loss, "collect_s": round(collect_s, 1),
             "train_s": round(train_s, 1),
@@ -502,7 +510,7 @@ def run_learned_heldout(args) -> dict:
                                   "learned_forced": med("learned_forced", 0)},
             "median_ms": {"plain": med("plain", 1), "learned_gated": med("learned_gated", 1),
                           "learned_forced": med("learned_forced", 1)},
-            "fallbacks": sum(1 for r in rows if r["learned_gated"][2]), "rows": rows}
+            "fallbacks": sum(1 for r in rows if r["learned_gated"][2]), "workload_eval": extra, "rows": rows}
 
 
 def run_reference(args) -> dict | None:
@@ -566,6 +574,7 @@ def main():
     ap.add_argument("--family", default="star2d", choices=["star2d", "ellipsoid3d"])
     ap.add_argument("--n-train", type=int, default=256)
     ap.add_argument("--n-eval", type=int, default=32)
+    ap.add_argument("--eval-workload", choices=sorted(WORKLOADS), help="also evaluate the trained MLP on this workload")
     args = ap.parse_args()
     if args.experiment:
         print(json.dumps(run_learned_heldout(args)))

@@ -81,6 +81,9 @@ typedef struct {
   int extension;         /* 0: u(x~) + d.grad u(x~) (Eq. 6); 1: cell polynomial at x~ + d          */
   int coarsest_n;        /* h-coarsening stops at this many cells per direction                 */
   int pre_smooth, post_smooth;
+  int ssor_each;         /* 0: a pre-smoothing step is one forward colour sweep and a post-       */
+                         /* smoothing step one reverse sweep; 1: each step is a full SSOR step,   */
+                         /* a forward then a reverse sweep, before and after the coarse correction */
   double omega;          /* block-smoother relaxation on levels with p_l <= 2                    */
   double omega_p3;       /* relaxation on levels with p_l = 3                                    */
   int vf_samples;        /* kappa sub-samples per direction; 0: 16 in 2D, 8 in 3D                 */

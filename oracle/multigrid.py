@@ -10,7 +10,9 @@ local operator A_i = R_i A R_i^T (Eq. 14), i.e. block Gauss-Seidel,
     u_K <- u_K + omega A_KK^{-1} (f - A u)_K   (most recent u).
 Visiting order: cells coloured by c(K) = sum_k (i_k mod 2) 2^k; the pre-smoother visits
 colours 0 .. 2^d - 1, the post-smoother 2^d - 1 .. 0 (together one symmetric sweep, the
-cell-wise SSOR of Sec. 4.3).  omega = 1, except on p = 3 levels where omega = 0.8 (Sec. 5.3).
+cell-wise SSOR of Sec. 4.3).  With `ssor_each`, every smoothing step is a full SSOR step, a
+forward then a reverse sweep, both before and after the coarse correction (an SSOR step is its own
+adjoint, so the V-cycle stays symmetric).  omega = 1, except on p = 3 levels where omega = 0.8 (Sec. 5.3).
 
 Transfers (Sec. 3.2): prolongation = embedding on the background mesh, realised by
 interpolating the coarse polynomial at the fine nodes (Eq. 17); restriction = its
@@ -183,12 +185,17 @@ class Hierarchy:
         if l == 0:
             return sla.lu_solve(self.coarse_lu, r)
         z = np.zeros(lev.N)
+        ssor = getattr(self.prob, "ssor_each", 0)
         for _ in range(self.prob.pre_smooth):
             lev.coloured_sweep(z, r, reverse=False)
+            if ssor:
+                lev.coloured_sweep(z, r, reverse=True)
         res = r - lev.A @ z
         zc = self.vcycle(self.R[l] @ res, l - 1)
         z += self.P[l] @ zc
         for _ in range(self.prob.post_smooth):
+            if ssor:
+                lev.coloured_sweep(z, r, reverse=False)
             lev.coloured_sweep(z, r, reverse=True)
         if correction is not None and l == top:
             correction(lev, z, r)

@@ -53,7 +53,7 @@ class _Desc(ctypes.Structure):
                 ("exact", ctypes.c_int), ("lam", ctypes.c_double), ("lam_inclusive", ctypes.c_int),
                 ("sigma_face_c", ctypes.c_double), ("sigma_bnd_c", ctypes.c_double), ("alpha", ctypes.c_double),
                 ("extension", ctypes.c_int), ("coarsest_n", ctypes.c_int), ("pre_smooth", ctypes.c_int),
-                ("post_smooth", ctypes.c_int), ("omega", ctypes.c_double), ("omega_p3", ctypes.c_double),
+                ("post_smooth", ctypes.c_int), ("ssor_each", ctypes.c_int), ("omega", ctypes.c_double), ("omega_p3", ctypes.c_double),
                 ("vf_samples", ctypes.c_int), ("precision", ctypes.c_int), ("tail_max_cells", ctypes.c_int),
                 ("tail_cluster_ctas", ctypes.c_int), ("launch_overlap", ctypes.c_int),
                 ("krylov_basis", ctypes.c_int), ("cell_kernel_min_cells", ctypes.c_int), ("stream", ctypes.c_void_p)]
@@ -174,6 +174,7 @@ def make_desc(prob, precision: int = SBM_F64, stream: int = 0, tail_max_cells: i
     d.sigma_face_c, d.sigma_bnd_c, d.alpha = prob.sigma_face_c, prob.sigma_bnd_c, prob.alpha
     d.extension, d.coarsest_n = prob.extension, prob.coarsest_n
     d.pre_smooth, d.post_smooth, d.omega, d.omega_p3 = prob.pre_smooth, prob.post_smooth, prob.omega, prob.omega_p3
+    d.ssor_each = prob.ssor_each
     d.vf_samples, d.precision, d.stream = prob.vf_samples, precision, stream
     d.tail_max_cells = tail_max_cells
     d.tail_cluster_ctas = tail_cluster_ctas

@@ -360,6 +360,7 @@ void validate(const sbm_setup_desc& d) {
   if (d.coarsest_n < 1) bad("coarsest_n must be >= 1");
   if (!(d.lambda >= 0.0 && d.lambda <= 1.0)) bad("lambda must lie in [0,1]");
   if (d.pre_smooth < 0 || d.post_smooth < 0 || d.pre_smooth > 16 || d.post_smooth > 16) bad("smoothing steps");
+  if (d.ssor_each != 0 && d.ssor_each != 1) bad("ssor_each must be 0 or 1");
   if (d.precision != SBM_F64 && d.precision != SBM_F32) bad("precision must be SBM_F64 or SBM_F32");
   if (d.extension != 0 && d.extension != 1) bad("extension must be 0 or 1");
   if (d.krylov_basis < 0 || d.krylov_basis > 2) bad("krylov_basis must be 0, 1 or 2");
@@ -502,6 +503,7 @@ void ensure_work(Context& C) {
       tp->top = top;
       tp->pre = C.desc.pre_smooth;
       tp->post = C.desc.post_smooth;
+      tp->ssor = C.desc.ssor_each;
       tp->int_base = (unsigned)int_base;
       if (!tail_cta_fits(dim, pi, smem, sizeof(TailCta<R>))) continue;
       C.tail_plan[pi].top = top;
@@ -612,14 +614,18 @@ void vcycle_rec(Context& C, int l, const R* r, R* z, cudaStream_t s) {
       CUDA_TRY(launch_vcycle_tail_cta<R>(L.H.dim, *tp, r, z, C.lv[0].coarse_inv, C.tail_plan[pi].smem_bytes, s));
     } else {
       CUDA_TRY(launch_vcycle_tail<R>(L.H.dim, static_cast<const TailLevel<R>*>(C.tail[pi]), l, r, z,
-                                     C.lv[0].coarse_inv, C.desc.pre_smooth, C.desc.post_smooth, C.tail_plan[pi], s));
+                                     C.lv[0].coarse_inv, C.desc.pre_smooth, C.desc.post_smooth, C.desc.ssor_each,
+                                     C.tail_plan[pi], s));
     }
     return;
   }
   const int dim = L.H.dim;
   const LevelParams<R>& P = params<R>(L);
   if (C.desc.pre_smooth == 0) CUDA_TRY(cudaMemsetAsync(z, 0, (size_t)L.H.n_dof() * sizeof(R), s));
-  for (int k = 0; k < C.desc.pre_smooth; ++k) CUDA_TRY(launch_smooth<R>(dim, L.H.p, P, 0, k == 0, r, z, s));
+  for (int k = 0; k < C.desc.pre_smooth; ++k) {
+    CUDA_TRY(launch_smooth<R>(dim, L.H.p, P, 0, k == 0, r, z, s));
+    if (C.desc.ssor_each) CUDA_TRY(launch_smooth<R>(dim, L.H.p, P, 1, 0, r, z, s));
+  }
   DevLevel& Lc = C.lv[l - 1];
   R* rc = static_cast<R*>(Lc.rhs[pi]);
   R* zc = static_cast<R*>(Lc.z[pi]);
@@ -630,7 +636,10 @@ void vcycle_rec(Context& C, int l, const R* r, R* z, cudaStream_t s) {
   }
   vcycle_rec<R>(C, l - 1, rc, zc, s);
   CUDA_TRY(launch_prolong<R>(dim, L.H.p, Lc.H.p, tparams<R>(L), zc, z, s));
-  for (int k = 0; k < C.desc.post_smooth; ++k) CUDA_TRY(launch_smooth<R>(dim, L.H.p, P, 1, 0, r, z, s));
+  for (int k = 0; k < C.desc.post_smooth; ++k) {
+    if (C.desc.ssor_each) CUDA_TRY(launch_smooth<R>(dim, L.H.p, P, 0, 0, r, z, s));
+    CUDA_TRY(launch_smooth<R>(dim, L.H.p, P, 1, 0, r, z, s));
+  }
   if (C.mlp_on && l == C.finest()) apply_learned<R>(C, L, r, z, s);
 }
 

@@ -530,7 +530,7 @@ template <int D, typename R>
 __global__ void __launch_bounds__(kTailThreads, 1) k_vcycle_tail(const TailLevel<R>* __restrict__ TL, int top,
                                                                  const R* __restrict__ r_top, R* __restrict__ z_top,
                                                                  const double* __restrict__ coarse_inv, int pre,
-                                                                 int post, int gather_off) {
+                                                                 int post, int ssor, int gather_off) {
   namespace cg = cooperative_groups;
   const cg::cluster_group cl = cg::this_cluster();
   extern __shared__ __align__(16) unsigned char tail_smem[];
@@ -598,11 +598,17 @@ __global__ void __launch_bounds__(kTailThreads, 1) k_vcycle_tail(const TailLevel
       for (int q = threadIdx.x; q < L.ncell * NP; q += kTailThreads) sm[L.zoff + q] = R(0);
       cl.sync();
     }
-    for (int k = 0; k < pre; ++k)
+    for (int k = 0; k < pre; ++k) {
       for (int col = 0; col < NCOL; ++col) {
         smooth(L, col, k == 0);
         cl.sync();
       }
+      if (ssor)
+        for (int q = 0; q < NCOL; ++q) {
+          smooth(L, NCOL - 1 - q, false);
+          cl.sync();
+        }
+    }
     const TailLevel<R>& Lc = TL[l - 1];
     for (int ccol = 0; ccol < NCOL; ++ccol)
       for_own(Lc, ccol, [&](int cc, int slot) {
@@ -684,11 +690,17 @@ __global__ void __launch_bounds__(kTailThreads, 1) k_vcycle_tail(const TailLevel
         store_np_vec<NP, R>(zu, u);
       });
     cl.sync();
-    for (int k = 0; k < post; ++k)
+    for (int k = 0; k < post; ++k) {
+      if (ssor)
+        for (int col = 0; col < NCOL; ++col) {
+          smooth(L, col, false);
+          cl.sync();
+        }
       for (int q = 0; q < NCOL; ++q) {
         smooth(L, NCOL - 1 - q, false);
         cl.sync();
       }
+    }
   }
   {                                                // correction of the top level out
     const TailLevel<R>& L = TL[top];
@@ -777,11 +789,17 @@ __global__ void __launch_bounds__(kTailCtaThreads, 1) k_vcycle_tail_cta(const __
       for (int q = tid; q < P.n_act * NP; q += kTailCtaThreads) sm[TP.zoff[l] + q] = R(0);
       __syncthreads();
     }
-    for (int k = 0; k < TP.pre; ++k)
+    for (int k = 0; k < TP.pre; ++k) {
       for (int col = 0; col < NCOL; ++col) {
         smooth(l, col, k == 0);
         __syncthreads();
       }
+      if (TP.ssor)
+        for (int q = 0; q < NCOL; ++q) {
+          smooth(l, NCOL - 1 - q, false);
+          __syncthreads();
+        }
+    }
     const TransferParams<R>& T = TP.T[l];
     const R* z = sm + TP.zoff[l];
     const R* f = sm + TP.roff[l];
@@ -859,11 +877,17 @@ __global__ void __launch_bounds__(kTailCtaThreads, 1) k_vcycle_tail_cta(const __
       store_np_vec<NP, R>(z + a * NP, u);
     }
     __syncthreads();
-    for (int k = 0; k < TP.post; ++k)
+    for (int k = 0; k < TP.post; ++k) {
+      if (TP.ssor)
+        for (int col = 0; col < NCOL; ++col) {
+          smooth(l, col, false);
+          __syncthreads();
+        }
       for (int q = 0; q < NCOL; ++q) {
         smooth(l, NCOL - 1 - q, false);
         __syncthreads();
       }
+    }
   }
   for (int q = tid; q < TP.P[top].n_act * NP; q += kTailCtaThreads) z_top[q] = sm[TP.zoff[top] + q];
 }
@@ -986,7 +1010,7 @@ bool tail_cluster_fits(int dim, int prec, int size, size_t smem) {
 
 template <typename R>
 cudaError_t launch_vcycle_tail(int dim, const TailLevel<R>* TL, int top, const R* r, R* z, const double* coarse_inv,
-                               int pre, int post, const TailPlan& plan, cudaStream_t s) {
+                               int pre, int post, int ssor, const TailPlan& plan, cudaStream_t s) {
   if (plan.cluster < 1) return cudaErrorNotSupported;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(plan.cluster);
@@ -1001,8 +1025,8 @@ cudaError_t launch_vcycle_tail(int dim, const TailLevel<R>* TL, int top, const R
   cfg.attrs = attr;
   cfg.numAttrs = 1;
   cudaError_t e;
-  if (dim == 2) e = cudaLaunchKernelEx(&cfg, k_vcycle_tail<2, R>, TL, top, r, z, coarse_inv, pre, post, plan.gather_off);
-  else e = cudaLaunchKernelEx(&cfg, k_vcycle_tail<3, R>, TL, top, r, z, coarse_inv, pre, post, plan.gather_off);
+  if (dim == 2) e = cudaLaunchKernelEx(&cfg, k_vcycle_tail<2, R>, TL, top, r, z, coarse_inv, pre, post, ssor, plan.gather_off);
+  else e = cudaLaunchKernelEx(&cfg, k_vcycle_tail<3, R>, TL, top, r, z, coarse_inv, pre, post, ssor, plan.gather_off);
   count_launches();
   return e;
 }
@@ -1037,9 +1061,9 @@ template cudaError_t launch_vcycle_tail_cta<float>(int, const TailCta<float>&, c
                                                    size_t, cudaStream_t);
 
 template cudaError_t launch_vcycle_tail<double>(int, const TailLevel<double>*, int, const double*, double*,
-                                                const double*, int, int, const TailPlan&, cudaStream_t);
+                                                const double*, int, int, int, const TailPlan&, cudaStream_t);
 template cudaError_t launch_vcycle_tail<float>(int, const TailLevel<float>*, int, const float*, float*, const double*,
-                                               int, int, const TailPlan&, cudaStream_t);
+                                               int, int, int, const TailPlan&, cudaStream_t);
 template cudaError_t launch_apply_cell<double, double>(int, int, const LevelParams<double>&, const double*,
                                                        const double*, double*, int, cudaStream_t);
 template cudaError_t launch_apply_cell<float, float>(int, int, const LevelParams<float>&, const float*, const float*,

@@ -83,7 +83,7 @@ cudaError_t launch_resid_restrict_h_cell(int dim, const LevelParams<R>& P, const
 // has no cluster.
 template <typename R>
 cudaError_t launch_vcycle_tail(int dim, const TailLevel<R>* TL, int top, const R* r, R* z, const double* coarse_inv,
-                               int pre, int post, const TailPlan& plan, cudaStream_t s);
+                               int pre, int post, int ssor, const TailPlan& plan, cudaStream_t s);
 // Largest dynamic shared memory a tail CTA may use, and whether a cluster of `size` CTAs with
 // `smem` bytes each can be resident (prec 0: FP64, 1: FP32).
 size_t tail_smem_limit();

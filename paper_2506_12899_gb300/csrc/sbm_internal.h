@@ -143,7 +143,7 @@ struct TailLevel {
 constexpr int kMaxTailCta = 6;
 template <typename R>
 struct TailCta {
-  int top, pre, post;
+  int top, pre, post, ssor;
   int zoff[kMaxTailCta], roff[kMaxTailCta], boff[kMaxTailCta];
   int noff[kMaxTailCta], coff[kMaxTailCta], poff[kMaxTailCta];   // nbr, children, parent codes
   int n_bnd[kMaxTailCta];

@@ -32,6 +32,7 @@ CASES = {
     "ellipsoid3d_p3_n12": W.ellipsoid3d_p3(12, 4),
     "disk2d_p2_poly": W.disk2d_p1(16, 5).replace(p=2, extension=1),
     "box2d_p2": W.Problem(dim=2, n=16, p=2, shape=W.box(0.5)),
+    "star2d_p3_n16_ssor": W.star2d_p2(16, 2).replace(p=3, ssor_each=1),
 }
 _pairs = {}
 
@@ -186,7 +187,7 @@ def test_vcycle(name, tail):
 
 
 @pytest.mark.parametrize("name", ["disk2d_p1_n32", "disk2d_p1_n32_s3", "star2d_p2_n32", "sphere3d_p1_n8",
-                                  "sphere3d_p2_n8", "box2d_p2"])
+                                  "sphere3d_p2_n8", "box2d_p2", "star2d_p3_n16_ssor"])
 def test_fgmres_fp64_matches_oracle(name):
     """a6: FP64 FGMRES(30) + FP64 V-cycle: same iteration count as the oracle and the solution
     within 1e-10 relative L2."""

@@ -287,15 +287,35 @@ def test_block_gs_converges_to_solution():
     assert np.linalg.norm(u - x) <= 1e-8 * np.linalg.norm(x)
 
 
-def test_vcycle_symmetric_on_spd_box():
+@pytest.mark.parametrize("ssor_each", [0, 1])
+def test_vcycle_symmetric_on_spd_box(ssor_each):
     """Forward pre-smoothing, backward post-smoothing and R = P^T make the V-cycle a symmetric
-    operator when A is symmetric (Secs. 3.1-3.2)."""
-    prob = W.Problem(dim=2, n=32, p=2, shape=W.box(0.5), coarsest_n=4)
+    operator when A is symmetric (Secs. 3.1-3.2); with full SSOR steps (forward then reverse,
+    before and after the coarse correction) the post-smoother is still the adjoint of the
+    pre-smoother, since an SSOR step is self-adjoint.  A wrong order breaks the symmetry by far
+    more than rounding."""
+    prob = W.Problem(dim=2, n=32, p=2, shape=W.box(0.5), coarsest_n=4, ssor_each=ssor_each)
     H = MG.Hierarchy(prob)
     rng = np.random.default_rng(0)
     r1, r2 = rng.normal(size=H.finest.N), rng.normal(size=H.finest.N)
     a, b = H.vcycle(r1) @ r2, r1 @ H.vcycle(r2)
     assert abs(a - b) <= 1e-12 * abs(a)
+
+
+def test_ssor_each_smooths_more_than_one_sweep():
+    """Two-grid error reduction on the disk: a full SSOR step per smoothing step reduces the error
+    of one V-cycle iteration at least as much as the single sweeps (the same colour order run
+    twice over)."""
+    rates = []
+    for ssor in (0, 1):
+        prob = W.disk2d_p1(16, 0).replace(ssor_each=ssor)
+        H = MG.Hierarchy(prob)
+        A = H.finest.A
+        e = np.random.default_rng(2).normal(size=H.finest.N)
+        for _ in range(3):
+            e = e - H.vcycle(A @ e)
+        rates.append(np.linalg.norm(e))
+    assert rates[1] <= rates[0]
 
 
 def test_vcycle_is_linear_and_exact_on_single_level():

@@ -67,6 +67,7 @@ class Problem:
     coarsest_n: int = 4              # h-coarsening stops at this many cells per direction
     pre_smooth: int = 1
     post_smooth: int = 1
+    ssor_each: int = 0               # 1: every smoothing step is a forward then a reverse (SSOR) sweep
     omega: float = 1.0               # block-smoother relaxation on levels with p_l <= 2
     omega_p3: float = 0.8            # relaxation on levels with p_l = 3 (Sec. 5.3)
     vf_samples: int = 0              # kappa sub-samples per direction (0: 16 in 2D, 8 in 3D)
@@ -163,11 +164,14 @@ def sphere3d(n: int = 64, p: int = 1, seed: int = 0) -> Problem:
                    exact=EXACT_SINPROD, coarsest_n=4, extension=1 if p >= 2 else 0, **HIGH_ORDER)
 
 
-def ellipsoid3d_p3(n: int = 96, seed: int = 0) -> Problem:
+def ellipsoid3d_p3(n: int = 96, seed: int = 0, smooth: int = 2) -> Problem:
     """3D p=3 workload: 96^3 cells, ellipsoid (0.75,0.6,0.5) rotated by seeded angles (full-order
-    boundary extension)."""
+    boundary extension).  Two pre- and two post-smoothing steps: with one of each the FGMRES
+    residual stalls near 5e-5 at 96^3 (measured; the paper reports the same weakness of its
+    smoother for p = 3 in 3D); with two it converges in 29 iterations."""
     return Problem(name=f"ellipsoid3d_p3_n{n}", dim=3, n=n, p=3, shape=ellipsoid(seed),
-                   exact=EXACT_SINPROD, coarsest_n=6 if n % 6 == 0 else 4, extension=1, **HIGH_ORDER)
+                   exact=EXACT_SINPROD, coarsest_n=6 if n % 6 == 0 else 4, extension=1,
+                   pre_smooth=smooth, post_smooth=smooth, **HIGH_ORDER)
 
 
 def random_star2d_p3(n: int = 128, seed: int = 1000) -> Problem:
