@@ -412,7 +412,7 @@ Context* build_context(const sbm_setup_desc& d, bool device) {
     if (!L.H.coarse_inv.empty()) L.coarse_inv = C->upload(L.H.coarse_inv);
     L.P64 = make_params<double>(L, L.dhat64, L.binv64);
     L.P32 = make_params<float>(L, L.dhat32, L.binv32);
-    if (&L == &C->lv.back() && cell_kernels(L.H.dim, L.H.p)) {   // Arnoldi operator in double-float
+    if (&L == &C->lv.back()) {                     // Arnoldi operator in double-float
       std::vector<dfl> dh(L.H.dhat.size());
       for (size_t i = 0; i < dh.size(); ++i) dh[i] = dfl(L.H.dhat[i]);
       L.dhat_df = C->upload(dh);
@@ -709,7 +709,9 @@ void arnoldi_step_work(Context& C, int j, cudaStream_t s) {
       float* Zj = static_cast<float*>(C.Z) + (size_t)j * N;
       vcycle_rec<float>(C, Lf, C.r32, Zj, s);
       if (C.desc.krylov_basis == 0 && F.has_df) {   // w = A z in double-float, straight into wdf
-        CUDA_TRY((launch_apply_cell<float, dfl>(dim, p, F.Pdf, Zj, nullptr, reinterpret_cast<dfl*>(C.wdf), 0, s)));
+        dfl* wd = reinterpret_cast<dfl*>(C.wdf);
+        if (cell_kernels(dim, p)) CUDA_TRY((launch_apply_cell<float, dfl>(dim, p, F.Pdf, Zj, nullptr, wd, 0, s)));
+        else CUDA_TRY((launch_apply<float, dfl>(dim, p, F.Pdf, Zj, nullptr, wd, 0, s)));   // one thread per DoF
         CUDA_TRY(launch_gs_dot_df(C.V2, N, j + 1, C.wdf, N, C.partial, h1, s));
       } else {
         CUDA_TRY((launch_apply<float, double>(dim, p, F.P64, Zj, nullptr, C.w, 0, s)));

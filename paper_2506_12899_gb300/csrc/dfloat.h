@@ -11,7 +11,7 @@ namespace sbm {
 
 struct __align__(8) dfl {
   float hi, lo;
-  __host__ __device__ dfl() : hi(0.f), lo(0.f) {}
+  dfl() = default;                                              // trivial: usable in __shared__ arrays
   __host__ __device__ dfl(int x) : hi((float)x), lo(0.f) {}     // small integers (exact)
   __host__ __device__ dfl(float x) : hi(x), lo(0.f) {}
   __host__ __device__ dfl(float h, float l) : hi(h), lo(l) {}

@@ -709,6 +709,8 @@ template cudaError_t launch_apply<float, float>(int, int, const LevelParams<floa
                                                 float*, int, cudaStream_t);
 template cudaError_t launch_apply<float, double>(int, int, const LevelParams<double>&, const float*, const double*,
                                                  double*, int, cudaStream_t);
+template cudaError_t launch_apply<float, dfl>(int, int, const LevelParams<dfl>&, const float*, const dfl*, dfl*, int,
+                                              cudaStream_t);
 template cudaError_t launch_smooth<double>(int, int, const LevelParams<double>&, int, int, const double*, double*,
                                            cudaStream_t);
 template cudaError_t launch_smooth<float>(int, int, const LevelParams<float>&, int, int, const float*, float*,
