@@ -170,8 +170,11 @@ def committed_traffic(workload: str, kernel: str):
 
 
 def event_time(torch, fn, reps, flush=None):
-    """Mean device time (ms) of fn() over reps launches on the current stream."""
+    """Mean device time (ms) of fn() over reps launches on the current stream, after one untimed
+    call (first calls allocate work buffers)."""
     s = torch.cuda.current_stream()
+    fn()
+    torch.cuda.synchronize()
     total = 0.0
     for _ in range(reps):
         if flush is not None:
@@ -246,11 +249,15 @@ def run_ours(args) -> dict | None:
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         total_ms = float(t.item())
     # ---- FP64 V-cycle solves (the plain variant), same workload
+    x32 = x.clone()                              # the last FP32-V-cycle solution
     times64, infos64 = [], []
     for _ in range(args.steps):
         ms, info = solve_step(s64)
         times64.append(ms)
         infos64.append(info)
+    # FP32-V-cycle solution against the FP64-V-cycle one (which matches the FP64 oracle to 1e-10
+    # on the parity-test meshes); both are solved to the same FP64 residual tolerance
+    err_vs_fp64 = float(torch.linalg.norm(x32 - x) / torch.linalg.norm(x))
     # ---- the same workload with the full-order boundary extension (cell polynomial at x~ + d)
     # instead of the first-order Taylor term, FP32 V-cycle
     full_ext = None
@@ -387,6 +394,7 @@ def run_ours(args) -> dict | None:
         "true_rel_residual": max(i.true_rel_residual for i in infos32),
         "fp64_vcycle": {"ms": round(statistics.mean(times64), 4), "iterations": [i.iterations for i in infos64],
                         "converged": all(i.converged for i in infos64)},
+        "rel_l2_error_vs_fp64_vcycle_solution": err_vs_fp64,
         "speedup_fp32_over_fp64_vcycle": round(statistics.mean(times64) / ms32, 3),
         "learned": learned,
         "full_order_extension": full_ext,
@@ -513,6 +521,78 @@ def run_learned_heldout(args) -> dict:
             "fallbacks": sum(1 for r in rows if r["learned_gated"][2]), "workload_eval": extra, "rows": rows}
 
 
+def run_roofline_sweep(args) -> dict:
+    """Operator and smoother kernels on meshes whose FP32 vectors exceed L2 several times (the
+    bench workload's fit in L2): CUDA-event time per launch after an L2 flush, algorithmic bytes
+    (every vector entry once), achieved GB/s against the measured HBM copy bandwidth."""
+    import torch
+    import paper_2506_12899_gb300 as S
+    hbm, src = peaks()
+    flush_buf = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+
+    def flush():
+        flush_buf.fill_(1.0)
+
+    rows = []
+    for label, prob in (("star2d p=2 2048^2", W.star2d_p2(2048, 0)), ("sphere3d p=2 128^3", W.sphere3d(128, 2, 0))):
+        g = S.Solver(prob, "f32")
+        L = g.num_levels - 1
+        for level in (L, L - 1):
+            inf = g.info(level)
+            N = inf["n_dof"]
+            npc = (inf["p"] + 1) ** prob.dim
+            ncol = 2 ** prob.dim
+            geo = 4 * inf["n_sface"] * (inf["p"] + 1) ** (prob.dim - 1) * prob.dim
+            f = torch.rand(N, device="cuda")
+            u = torch.rand_like(f)
+            y = torch.empty_like(f)
+            t_apply = event_time(torch, lambda: g.apply(f, y, level=level), 10, flush)
+            t_smooth = event_time(torch, lambda: g.smooth(f, u, level=level), 10, flush) / ncol
+            b_apply = 2 * 4 * N + geo
+            b_smooth = ((prob.dim + 2) * 4 * N + inf["n_boundary"] * npc * npc * 4 + geo) / ncol
+            for kern, b, t in (("apply", b_apply, t_apply), ("smoother colour", b_smooth, t_smooth)):
+                gbs = b / t / 1e6
+                rows.append({"workload": label, "level": f"{inf['n']}^{prob.dim} p={inf['p']}", "n_dof": N,
+                             "kernel": kern, "bytes": int(b), "ms": round(t, 5), "GB/s": round(gbs, 1),
+                             "frac": round(gbs / hbm, 3)})
+            del f, u, y
+        g.close()
+        torch.cuda.empty_cache()
+    return {"experiment": "FP32 operator / smoother roofline sweep (vectors > L2)", "peak_gbs": hbm,
+            "peak_source": src, "l2": "flushed (256 MB write) before every launch", "rows": rows}
+
+
+def run_paper_replica(args) -> dict:
+    """The paper's unit-disk / unit-sphere study (Sec. 5): [-1.01,1.01]^d with 4*2^level cells,
+    kappa > lambda, sigma_F = (p+1)^2/h, sigma_Gamma = 5 (p+1)^2/h, polynomial boundary extension,
+    u = 2 cos x sin y, FP64 V-cycle, GMRES tol 1e-12 and a cap of 100 iterations, with one smoothing
+    step of each kind (forward / reverse sweep) and with full SSOR steps.  Reports iteration counts
+    per (dim, p, lambda, level)."""
+    import torch
+    import paper_2506_12899_gb300 as S
+    plan = [(2, 1, range(1, 8)), (3, 1, range(1, 5)), (2, 2, range(1, 7)), (3, 2, range(1, 5)), (2, 3, range(1, 6))]
+    rows = []
+    for dim, p, levels in plan:
+        for lam in (1.0, 0.75, 0.5, 0.25):
+            for lev in levels:
+                for ssor in (0, 1):
+                    prob = W.paper_disk(lev, p, lam, dim).replace(ssor_each=ssor)
+                    if p == 3:
+                        prob = prob.replace(omega_p3=0.8)
+                    try:
+                        g = S.Solver(prob, "f64")
+                        b = g.rhs()
+                        x = torch.zeros_like(b)
+                        info = g.solve(b, x, tol=1e-12, restart=30, max_it=100)
+                        rows.append({"dim": dim, "p": p, "lambda": lam, "level": lev, "ssor_each": ssor,
+                                     "n_dof": g.n_dof(), "iterations": info.iterations, "converged": info.converged})
+                        g.close()
+                    except Exception as e:                # e.g. no active cell on a coarse level
+                        rows.append({"dim": dim, "p": p, "lambda": lam, "level": lev, "ssor_each": ssor,
+                                     "error": str(e)[:80]})
+    return {"experiment": "paper replica: unit disk/sphere iteration counts (tol 1e-12, cap 100)", "rows": rows}
+
+
 def run_reference(args) -> dict | None:
     """The reference arm: the CPU FP64 oracle on the host cores (no GPU)."""
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -570,14 +650,17 @@ def main():
     ap.add_argument("--tail-cluster", type=int, default=0, help="--profile kernels: cluster-tail CTAs")
     ap.add_argument("--krylov-basis", type=int, default=0, choices=[0, 1],
                     help="--profile solve: FGMRES basis storage (0 double-float, 1 FP64)")
-    ap.add_argument("--experiment", choices=["learned-heldout"], help="a7 on held-out domains (no bench line)")
+    ap.add_argument("--experiment", choices=["learned-heldout", "roofline-sweep", "paper-replica"],
+                    help="a7 on held-out domains, or the large-mesh roofline sweep (no bench line)")
     ap.add_argument("--family", default="star2d", choices=["star2d", "ellipsoid3d"])
     ap.add_argument("--n-train", type=int, default=256)
     ap.add_argument("--n-eval", type=int, default=32)
     ap.add_argument("--eval-workload", choices=sorted(WORKLOADS), help="also evaluate the trained MLP on this workload")
     args = ap.parse_args()
     if args.experiment:
-        print(json.dumps(run_learned_heldout(args)))
+        run = {"learned-heldout": run_learned_heldout, "roofline-sweep": run_roofline_sweep,
+               "paper-replica": run_paper_replica}[args.experiment]
+        print(json.dumps(run(args)))
         return
     if args.profile:
         run_profile(args)

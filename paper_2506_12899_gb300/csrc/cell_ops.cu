@@ -1031,20 +1031,30 @@ cudaError_t launch_vcycle_tail(int dim, const TailLevel<R>* TL, int top, const R
   return e;
 }
 
-bool tail_cta_fits(int dim, int prec, size_t smem, size_t param_bytes) {
-  (void)param_bytes;
-  if (smem > tail_smem_limit()) return false;
-  cudaError_t e;
-  const int lim = (int)tail_smem_limit();
-  if (dim == 2) e = prec == 0 ? cudaFuncSetAttribute(k_vcycle_tail_cta<2, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim)
-                              : cudaFuncSetAttribute(k_vcycle_tail_cta<2, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
-  else e = prec == 0 ? cudaFuncSetAttribute(k_vcycle_tail_cta<3, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim)
-                     : cudaFuncSetAttribute(k_vcycle_tail_cta<3, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
-  if (e != cudaSuccess) {
+template <typename K>
+bool tail_cta_fits_kernel(K kern, size_t smem) {
+  cudaFuncAttributes fa{};
+  int dev = 0, optin = 0;
+  if (cudaFuncGetAttributes(&fa, kern) != cudaSuccess || cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  const size_t room = (size_t)optin > fa.sharedSizeBytes ? (size_t)optin - fa.sharedSizeBytes : 0;
+  if (smem > room) return false;
+  if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)room) != cudaSuccess) {
     cudaGetLastError();
     return false;
   }
   return true;
+}
+
+bool tail_cta_fits(int dim, int prec, size_t smem, size_t param_bytes) {
+  (void)param_bytes;
+  if (dim == 2) return prec == 0 ? tail_cta_fits_kernel(k_vcycle_tail_cta<2, double>, smem)
+                                 : tail_cta_fits_kernel(k_vcycle_tail_cta<2, float>, smem);
+  return prec == 0 ? tail_cta_fits_kernel(k_vcycle_tail_cta<3, double>, smem)
+                   : tail_cta_fits_kernel(k_vcycle_tail_cta<3, float>, smem);
 }
 
 template <typename R>
