@@ -15,7 +15,12 @@
 namespace sbm {
 namespace {
 
-constexpr int kCellThreads = 128;
+constexpr int kCellThreads = 128;   // largest block of the thread-per-cell kernels
+
+// Block size of a thread-per-cell launch over `cells` threads: 32 for launches of up to 32 warps
+// per SM (more, smaller blocks spread a short launch over all SMs: with 32 everywhere the 2D p=2
+// 512^2 solve was 3% faster and the 3D p=1 64^3 one 16%), 128 above.
+inline unsigned cell_block(size_t cells) { return cells <= (size_t)152 * 32 * 32 ? 32u : (unsigned)kCellThreads; }
 constexpr int kTailThreads = 512;
 
 template <int D, int N1>
@@ -296,7 +301,7 @@ __global__ void __launch_bounds__(kCellThreads) k_apply_cell(const __grid_consta
                                                              R* __restrict__ y) {
   pdl_entry();
   constexpr int NP = CD<D, N1>::NP;
-  const int a = blockIdx.x * kCellThreads + threadIdx.x;
+  const int a = blockIdx.x * blockDim.x + threadIdx.x;
   if (a >= P.n_act) return;
   R r[NP];
   cell_apply<D, N1, TI, R>(P, x, a, r);
@@ -409,7 +414,7 @@ __global__ void __launch_bounds__(kCellThreads) k_smooth_cell(const __grid_const
                                                               int b0, const R* __restrict__ f, R* __restrict__ u) {
   pdl_entry();
   const bool isB = (int)blockIdx.x < nblk_b;
-  const int first = isB ? cs + blockIdx.x * kCellThreads : cs + nbnd + (blockIdx.x - nblk_b) * kCellThreads;
+  const int first = isB ? cs + blockIdx.x * blockDim.x : cs + nbnd + (blockIdx.x - nblk_b) * blockDim.x;
   const int last = isB ? cs + nbnd : ce;
   const int a = first + threadIdx.x;
   if (a >= last) return;
@@ -425,7 +430,7 @@ __global__ void __launch_bounds__(kCellThreads) k_resid_restrict_p_cell(const __
   pdl_entry();
   constexpr int NP = CD<D, N1>::NP;
   constexpr int NPC = D == 2 ? NC * NC : NC * NC * NC;
-  const int a = blockIdx.x * kCellThreads + threadIdx.x;
+  const int a = blockIdx.x * blockDim.x + threadIdx.x;
   if (a >= P.n_act) return;
   R r[NP];
   cell_apply<D, N1, R, R>(P, u, a, r);
@@ -464,7 +469,7 @@ __global__ void __launch_bounds__(kCellThreads) k_resid_restrict_h_cell(const __
                                                                         const R* __restrict__ f, R* __restrict__ rc) {
   pdl_entry();
   constexpr int NCOL = 1 << D, NP = CD<D, 2>::NP;
-  const int t = blockIdx.x * kCellThreads + threadIdx.x;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
   const int cc = t / NCOL, o = t % NCOL;
   R out[NP];
 #pragma unroll
@@ -913,8 +918,9 @@ cudaError_t launch_apply_cell(int dim, int p, const LevelParams<R>& P, const TI*
   if (P.n_act == 0) return cudaSuccess;
 #define SBM_AC(D, N1)                                                                           \
   {                                                                                             \
-    if (mode == 0) SBM_PDL((k_apply_cell<D, N1, TI, R, 0>), cdiv(P.n_act, kCellThreads), kCellThreads, 0, s, P, x, f, y); \
-    else SBM_PDL((k_apply_cell<D, N1, TI, R, 1>), cdiv(P.n_act, kCellThreads), kCellThreads, 0, s, P, x, f, y);          \
+    const unsigned bs = cell_block(P.n_act);                                                   \
+    if (mode == 0) SBM_PDL((k_apply_cell<D, N1, TI, R, 0>), cdiv(P.n_act, bs), bs, 0, s, P, x, f, y); \
+    else SBM_PDL((k_apply_cell<D, N1, TI, R, 1>), cdiv(P.n_act, bs), bs, 0, s, P, x, f, y);          \
   }
   SBM_CELL_DISPATCH(dim, p, SBM_AC);
 #undef SBM_AC
@@ -930,10 +936,11 @@ cudaError_t launch_smooth_cell(int dim, int p, const LevelParams<R>& P, int reve
   for (int q = 0; q < ncol; ++q) {   // (the launcher in level_ops.cu chose this path for the level)
     const int col = reverse ? ncol - 1 - q : q;
     const int cs = P.colour_start[col], ce = P.colour_start[col + 1], nbnd = P.colour_nbnd[col];
-    const int nblk_b = (int)cdiv(nbnd, kCellThreads), nblk_i = (int)cdiv(ce - cs - nbnd, kCellThreads);
+    const unsigned bs = cell_block(ce - cs);
+    const int nblk_b = (int)cdiv(nbnd, bs), nblk_i = (int)cdiv(ce - cs - nbnd, bs);
     if (nblk_b + nblk_i == 0) continue;
 #define SBM_SC(D, N1)                                                                                    \
-  SBM_PDL((k_smooth_cell<D, N1, R>), nblk_b + nblk_i, kCellThreads, 0, s, P, col, zero_start, cs, nbnd, ce, nblk_b, \
+  SBM_PDL((k_smooth_cell<D, N1, R>), nblk_b + nblk_i, bs, 0, s, P, col, zero_start, cs, nbnd, ce, nblk_b, \
                                                                    P.bstart[col], f, u);
     SBM_CELL_DISPATCH(dim, p, SBM_SC);
 #undef SBM_SC
@@ -946,9 +953,9 @@ template <typename R>
 cudaError_t launch_resid_restrict_p_cell(int dim, int pf, const LevelParams<R>& P, const TransferParams<R>& T,
                                         const R* u, const R* f, R* rc, cudaStream_t s) {
   if (P.n_act == 0) return cudaSuccess;
-  const unsigned g = cdiv(P.n_act, kCellThreads);
-  if (dim == 2 && pf == 2) SBM_PDL((k_resid_restrict_p_cell<2, 3, 2, R>), g, kCellThreads, 0, s, P, T, u, f, rc);
-  else if (dim == 2 && pf == 3) SBM_PDL((k_resid_restrict_p_cell<2, 4, 3, R>), g, kCellThreads, 0, s, P, T, u, f, rc);
+  const unsigned bs = cell_block(P.n_act), g = cdiv(P.n_act, bs);
+  if (dim == 2 && pf == 2) SBM_PDL((k_resid_restrict_p_cell<2, 3, 2, R>), g, bs, 0, s, P, T, u, f, rc);
+  else if (dim == 2 && pf == 3) SBM_PDL((k_resid_restrict_p_cell<2, 4, 3, R>), g, bs, 0, s, P, T, u, f, rc);
   else return cudaErrorInvalidValue;
   count_launches();
   return cudaGetLastError();
@@ -958,9 +965,9 @@ template <typename R>
 cudaError_t launch_resid_restrict_h_cell(int dim, const LevelParams<R>& P, const TransferParams<R>& T, const R* u,
                                         const R* f, R* rc, cudaStream_t s) {
   if (T.n_act_c == 0) return cudaSuccess;
-  const unsigned g = cdiv((size_t)T.n_act_c << dim, kCellThreads);
-  if (dim == 2) SBM_PDL((k_resid_restrict_h_cell<2, R>), g, kCellThreads, 0, s, P, T, u, f, rc);
-  else if (dim == 3) SBM_PDL((k_resid_restrict_h_cell<3, R>), g, kCellThreads, 0, s, P, T, u, f, rc);
+  const unsigned bs = cell_block((size_t)T.n_act_c << dim), g = cdiv((size_t)T.n_act_c << dim, bs);
+  if (dim == 2) SBM_PDL((k_resid_restrict_h_cell<2, R>), g, bs, 0, s, P, T, u, f, rc);
+  else if (dim == 3) SBM_PDL((k_resid_restrict_h_cell<3, R>), g, bs, 0, s, P, T, u, f, rc);
   else return cudaErrorInvalidValue;
   count_launches();
   return cudaGetLastError();
