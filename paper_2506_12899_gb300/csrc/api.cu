@@ -177,7 +177,8 @@ struct Context {
   // FGMRES workspace
   int ws_m = 0, ws_prec = -1;
   double* V = nullptr;               // FP64 basis [m+1][N] (krylov_basis = 1)
-  float2* V2 = nullptr;              // double-float basis [m+1][N] (krylov_basis = 0)
+  float2* V2 = nullptr;              // double-float basis [m+1][ldv] (krylov_basis = 0)
+  size_t ldv = 0;                    // leading dimension of V2: N rounded up to 32 entries
   float2* wdf = nullptr;             // w as double-float between the Gram-Schmidt sweeps
   void* Z = nullptr;
   double* w = nullptr;
@@ -649,16 +650,19 @@ void ensure_krylov(Context& C, int m) {
   if (C.ws_m >= m && C.ws_prec == prec && C.ws_basis == basis) return;
   C.drop_graphs();                                  // captured pointers change
   const size_t N = C.lv.back().H.n_dof();
+  // the staged sweeps copy whole 16-byte units from 16-byte aligned rows: rows of ldv entries,
+  // and w, wdf padded to the same length (the padding is never used in the arithmetic)
+  C.ldv = (N + 31) / 32 * 32;
   if (basis == 1) {                                 // FP64 basis
     C.V = C.dalloc<double>((size_t)(m + 1) * N);
   } else {
-    C.V2 = C.dalloc<float2>((size_t)(m + 1) * N);
-    C.wdf = C.dalloc<float2>(N);
+    C.V2 = C.dalloc<float2>((size_t)(m + 1) * C.ldv);
+    C.wdf = C.dalloc<float2>(C.ldv);
     if (prec == SBM_F64) C.v64 = C.dalloc<double>(N);
   }
   C.ws_basis = basis;
   C.Z = prec == SBM_F32 ? (void*)C.dalloc<float>((size_t)m * N) : (void*)C.dalloc<double>((size_t)m * N);
-  C.w = C.dalloc<double>(N);
+  C.w = C.dalloc<double>(C.ldv);
   if (prec == SBM_F32) C.r32 = C.dalloc<float>(N);
   C.partial = C.dalloc<double>((size_t)std::max(dot_blocks(N), gs_blocks(N)) * 32);   // rows of either grid
   C.dots = C.dalloc<double>(128);
@@ -712,21 +716,22 @@ void arnoldi_step_work(Context& C, int j, cudaStream_t s) {
         dfl* wd = reinterpret_cast<dfl*>(C.wdf);
         if (cell_kernels(dim, p)) CUDA_TRY((launch_apply_cell<float, dfl>(dim, p, F.Pdf, Zj, nullptr, wd, 0, s)));
         else CUDA_TRY((launch_apply<float, dfl>(dim, p, F.Pdf, Zj, nullptr, wd, 0, s)));   // one thread per DoF
-        CUDA_TRY(launch_gs_dot_df(C.V2, N, j + 1, C.wdf, N, C.partial, h1, s));
+        CUDA_TRY(launch_gs_dot_df(C.V2, C.ldv, j + 1, C.wdf, N, C.partial, h1, s));
       } else {
         CUDA_TRY((launch_apply<float, double>(dim, p, F.P64, Zj, nullptr, C.w, 0, s)));
-        CUDA_TRY(launch_gs_dot(C.V2, N, j + 1, C.w, C.wdf, N, C.partial, h1, s));
+        CUDA_TRY(launch_gs_dot(C.V2, C.ldv, j + 1, C.w, C.wdf, N, C.partial, h1, s));
       }
     } else {
       double* Zj = static_cast<double*>(C.Z) + (size_t)j * N;
       vcycle_rec<double>(C, Lf, C.v64, Zj, s);
       CUDA_TRY((launch_apply<double, double>(dim, p, F.P64, Zj, nullptr, C.w, 0, s)));
-      CUDA_TRY(launch_gs_dot(C.V2, N, j + 1, C.w, C.wdf, N, C.partial, h1, s));
+      CUDA_TRY(launch_gs_dot(C.V2, C.ldv, j + 1, C.w, C.wdf, N, C.partial, h1, s));
     }
-    CUDA_TRY(launch_gs_axpy_dot(C.V2, N, j + 1, h1, C.wdf, N, C.partial, h2, s));
-    CUDA_TRY(launch_gs_axpy_norm(C.V2, N, j + 1, h2, C.wdf, N, C.partial, hn, s));
-    if (prec == SBM_F32) CUDA_TRY((launch_gs_scale<float2, float>(C.wdf, hn, C.V2 + (size_t)(j + 1) * N, C.r32, N, s)));
-    else CUDA_TRY((launch_gs_scale<float2, double>(C.wdf, hn, C.V2 + (size_t)(j + 1) * N, C.v64, N, s)));
+    CUDA_TRY(launch_gs_axpy_dot(C.V2, C.ldv, j + 1, h1, C.wdf, N, C.partial, h2, s));
+    CUDA_TRY(launch_gs_axpy_norm(C.V2, C.ldv, j + 1, h2, C.wdf, N, C.partial, hn, s));
+    float2* vnext = C.V2 + (size_t)(j + 1) * C.ldv;
+    if (prec == SBM_F32) CUDA_TRY((launch_gs_scale<float2, float>(C.wdf, hn, vnext, C.r32, N, s)));
+    else CUDA_TRY((launch_gs_scale<float2, double>(C.wdf, hn, vnext, C.v64, N, s)));
   }
   CUDA_TRY(launch_hess_column(h1, h2, hn, j + 1, col, s));
   CUDA_TRY(cudaMemcpyAsync(C.host_pinned, col, (j + 2) * sizeof(double), cudaMemcpyDeviceToHost, s));
@@ -885,6 +890,8 @@ int solve_impl(Context& C, const double* b, double* x, double tol, int m, int ma
   CUDA_TRY(cudaEventElapsedTime(&ms, C.ev0, C.ev1));
   loc.ms_total = ms;
   if (info) *info = loc;
+  if (sweep_fault_take() != 0)
+    return set_error(SBM_ERR_CUDA, "Gram-Schmidt sweep: staged copies did not complete in bounded time");
   if (status == SBM_ERR_NAN) return set_error(status, "non-finite value in FGMRES");
   if (status == SBM_ERR_NOT_CONVERGED) return set_error(status, "FGMRES did not reach the tolerance");
   return SBM_OK;

@@ -3,6 +3,7 @@
 // of per-block partials), multi-vector AXPY, scaling and precision casts.
 #include <cuda_runtime.h>
 
+#include <cstdint>
 #include <mutex>
 #include <type_traits>
 
@@ -220,14 +221,6 @@ __device__ __forceinline__ float2 df_add(float2 a, float2 b) {
   return make_float2(hi, __fsub_rn(e, __fsub_rn(hi, t)));
 }
 
-// A load the compiler may not merge with an earlier load of the same address (volatile asm):
-// the dot pass of k_gs_axpy_dot re-reads V from L1 instead of keeping NV values live.
-__device__ __forceinline__ float2 ld_again(const float2* p) {
-  float2 v;
-  asm volatile("ld.global.ca.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "l"(p));
-  return v;
-}
-
 // (s, c) += (s2, c2) for double-float partial sums held as a leading value and a compensation.
 __device__ __forceinline__ void df_acc_add(float& s, float& c, float s2, float c2) {
   const float t = __fadd_rn(s, s2);
@@ -263,76 +256,157 @@ __device__ __forceinline__ void block_partials_df(float (&s)[NV], float (&c)[NV]
   }
 }
 
-// partial[block][k] = this block's share of V_k . w (V double-float, w FP64), k < NV; w is also
-// written as double-float to wdf for the next sweeps.  Each thread sweeps its entries with a
-// grid stride, reading every V_k once.
-template <int NV, typename TW>
-__global__ void __launch_bounds__(kDotThreads) k_gs_dot(const float2* __restrict__ V, size_t ldv,
-                                                        const TW* __restrict__ w, float2* __restrict__ wdf,
-                                                        size_t N, double* __restrict__ partial) {
-  pdl_entry();
-  float s[NV], c[NV];
-#pragma unroll
-  for (int k = 0; k < NV; ++k) s[k] = c[k] = 0.f;
-  const size_t stride = (size_t)gridDim.x * kDotThreads;
-  for (size_t i = (size_t)blockIdx.x * kDotThreads + threadIdx.x; i < N; i += stride) {
-    float2 wi;
-    if constexpr (std::is_same<TW, double>::value) {
-      wi = df_from_double(w[i]);
-      wdf[i] = wi;
-    } else {
-      wi = w[i];
-    }
-#pragma unroll
-    for (int k = 0; k < NV; ++k) df_dot_acc(s[k], c[k], V[k * ldv + i], wi);
-  }
-  block_partials_df<NV>(s, c, partial);
+// ---------------------------------------------------------------------------------------------
+// Gram-Schmidt sweeps staged by the Tensor Memory Accelerator.  A persistent grid (one CTA per
+// SM) walks chunks of E consecutive entries.  One elected thread copies the chunk of every V_k and
+// of w into shared memory with bulk asynchronous copies (cp.async.bulk), whose completion an
+// mbarrier counts in bytes, S chunks ahead of the arithmetic; the double-float arithmetic then
+// reads shared memory.  HBM therefore streams independently of the long dependent chains of the
+// error-free transformations, and each V_k is read as one contiguous run of E * 8 bytes per chunk.
+//
+// Requirements (checked by the launchers): V, w and wdf 16-byte aligned, ldv even, and one entry
+// of padding after the last one when N is odd (the copies move whole 16-byte units; the padding
+// entry is never used in the arithmetic).
+constexpr int kSweepThreads = 256;
+constexpr int kSweepBudget = 216 * 1024;           // shared memory of the stages, bytes
+constexpr unsigned kSweepSpin = 1u << 22;          // polls of one mbarrier phase before giving up
+
+// Set by a sweep whose staged copies did not complete within kSweepSpin polls; the solve reads and
+// clears it (sweep_fault_take) and reports SBM_ERR_CUDA.
+__device__ int g_sweep_fault;
+
+template <int NV>
+struct SweepShape {
+  static constexpr int SLOT = NV + 1;              // V_0 .. V_{NV-1}, then w
+  static constexpr int E = 2 * SLOT * 1024 * 8 <= kSweepBudget ? 1024 : (2 * SLOT * 512 * 8 <= kSweepBudget ? 512 : 256);
+  static constexpr int S0 = kSweepBudget / (SLOT * E * 8);
+  static constexpr int S = S0 > 6 ? 6 : S0;        // stages in flight
+  static constexpr size_t smem = (size_t)S * SLOT * E * sizeof(float2) + (size_t)S * sizeof(unsigned long long);
+  static_assert(S >= 2, "two stages must fit");
+};
+
+__device__ __forceinline__ unsigned smem_addr(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
 }
 
-// wdf <- wdf - sum_{k<NV} h[k] V_k in double-float, then the partial sums of V_k . wdf for
-// k < NV, or of |wdf|^2 when NORM.  The dot pass reads V_k again (an L1/L2 hit right after the
-// update pass) instead of holding NV values per thread.
-template <int NV, bool NORM>
-__global__ void __launch_bounds__(kDotThreads) k_gs_axpy_dot(const float2* __restrict__ V, size_t ldv,
-                                                             const double* __restrict__ h, float2* __restrict__ wdf,
-                                                             size_t N, double* __restrict__ partial) {
-  pdl_entry();
-  constexpr int NA = NORM ? 1 : NV;
+// One arrival that also announces `bytes` of asynchronous copies on the barrier's current phase.
+__device__ __forceinline__ void mbar_arrive_tx(unsigned long long* bar, unsigned bytes) {
+  asm volatile(
+      "{\n\t.reg .b64 st;\n\t"
+      "mbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n\t}" ::"r"(smem_addr(bar)),
+      "r"(bytes)
+      : "memory");
+}
+
+// Bulk copy of `bytes` (a multiple of 16) from global to this CTA's shared memory.
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, unsigned bytes, unsigned long long* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_addr(dst)),
+      "l"(src), "r"(bytes), "r"(smem_addr(bar))
+      : "memory");
+}
+
+// Waits for the phase of parity `parity` to complete; false after kSweepSpin unsuccessful polls.
+__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned parity) {
+  for (unsigned it = 0; it < kSweepSpin; ++it) {
+    unsigned done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(done)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+
+// MODE 0: partial[block][k] = V_k . w, k < NV.  w is FP64 (TW = double; it is also written to
+//         wdf as double-float for the next sweeps) or double-float (TW = float2).
+// MODE 1: wdf <- wdf - sum_k h[k] V_k, then partial[block][k] = V_k . wdf.
+// MODE 2: wdf <- wdf - sum_k h[k] V_k, then partial[block][0] = |wdf|^2.
+template <int NV, int MODE, typename TW>
+__global__ void __launch_bounds__(kSweepThreads) k_gs_sweep(const float2* __restrict__ V, size_t ldv, const TW* w_in,
+                                                            const double* __restrict__ h, float2* wdf, size_t N,
+                                                            double* __restrict__ partial) {
+  using Sh = SweepShape<NV>;
+  constexpr int E = Sh::E, S = Sh::S, SLOT = Sh::SLOT, EPT = E / kSweepThreads;
+  constexpr int NA = MODE == 2 ? 1 : NV;
+  extern __shared__ __align__(128) unsigned char sweep_smem[];
+  float2* stage = reinterpret_cast<float2*>(sweep_smem);
+  unsigned long long* bar = reinterpret_cast<unsigned long long*>(sweep_smem + (size_t)S * SLOT * E * sizeof(float2));
   __shared__ float2 hs[kMaxVec];
-  if (threadIdx.x < NV) hs[threadIdx.x] = df_from_double(h[threadIdx.x]);
+  const int tid = threadIdx.x;
+  if (tid == 0) {
+    for (int q = 0; q < S; ++q) mbar_init(&bar[q], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  pdl_entry();                                       // h and w come from the kernels before
+  if (MODE != 0 && tid < NV) hs[tid] = df_from_double(h[tid]);
   __syncthreads();
+  const size_t nchunk = (N + E - 1) / E;
+  const size_t mine = nchunk > blockIdx.x ? (nchunk - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+  auto issue = [&](size_t q) {                       // local chunk q into stage q % S
+    const size_t e0 = (blockIdx.x + q * gridDim.x) * (size_t)E;
+    const size_t n = N - e0 < (size_t)E ? N - e0 : (size_t)E;
+    const unsigned bytes = (unsigned)(((n + 1) & ~(size_t)1) * sizeof(float2));
+    float2* dst = stage + (size_t)(q % S) * SLOT * E;
+    unsigned long long* b = &bar[q % S];
+    mbar_arrive_tx(b, bytes * SLOT);
+#pragma unroll 1
+    for (int k = 0; k < NV; ++k) bulk_load(dst + (size_t)k * E, V + (size_t)k * ldv + e0, bytes, b);
+    bulk_load(dst + (size_t)NV * E, reinterpret_cast<const unsigned char*>(w_in) + e0 * sizeof(float2), bytes, b);
+  };
+  if (tid == 0)
+    for (size_t q = 0; q < (size_t)S && q < mine; ++q) issue(q);
   float s[NA], c[NA];
 #pragma unroll
   for (int k = 0; k < NA; ++k) s[k] = c[k] = 0.f;
-  const size_t stride = (size_t)gridDim.x * kDotThreads;
-  for (size_t i = (size_t)blockIdx.x * kDotThreads + threadIdx.x; i < N; i += stride) {
-    float2 wi = wdf[i];
-    if (NORM) {
-      // all NV loads issued before any arithmetic; the products are summed in four independent
-      // double-float chains and the sum subtracted once, which shortens the dependent chain
-      float2 v[NORM ? NV : 1];
+  for (size_t q = 0; q < mine; ++q) {
+    const bool ok = mbar_wait(&bar[q % S], (unsigned)((q / S) & 1));
+    const float2* sv = stage + (size_t)(q % S) * SLOT * E;
+    const size_t e0 = (blockIdx.x + q * gridDim.x) * (size_t)E;
 #pragma unroll
-      for (int k = 0; k < NV; ++k) v[k] = V[k * ldv + i];
-      float2 part[4];
+    for (int r = 0; r < EPT; ++r) {
+      const int t = tid + r * kSweepThreads;
+      const size_t e = e0 + t;
+      if (!ok || e >= N) continue;
+      float2 wi;
+      if constexpr (std::is_same<TW, double>::value) wi = df_from_double(reinterpret_cast<const double*>(sv + NV * E)[t]);
+      else wi = sv[NV * E + t];
+      if (MODE == 0) {
+        if constexpr (std::is_same<TW, double>::value) wdf[e] = wi;
 #pragma unroll
-      for (int q = 0; q < 4; ++q) part[q] = make_float2(0.f, 0.f);
+        for (int k = 0; k < NV; ++k) df_dot_acc(s[k], c[k], sv[k * E + t], wi);
+      } else {
+        float2 odd = make_float2(0.f, 0.f);          // two chains: even k into wi, odd k apart
 #pragma unroll
-      for (int k = 0; k < NV; ++k) part[k & 3] = df_sub_prod(part[k & 3], hs[k], v[NORM ? k : 0]);   // -= h v
+        for (int k = 0; k < NV; ++k) {
+          if (k & 1) odd = df_sub_prod(odd, hs[k], sv[k * E + t]);
+          else wi = df_sub_prod(wi, hs[k], sv[k * E + t]);
+        }
+        wi = df_add(wi, odd);
+        wdf[e] = wi;
+        if (MODE == 1) {
 #pragma unroll
-      for (int q = 0; q < 4; ++q) wi = df_add(wi, part[q]);
-    } else {
-      // one chain with the loads inline: the 2 NV accumulators of the dot pass leave no room to
-      // hold the NV values as well
-#pragma unroll
-      for (int k = 0; k < NV; ++k) wi = df_sub_prod(wi, hs[k], V[k * ldv + i]);
+          for (int k = 0; k < NA; ++k) df_dot_acc(s[k], c[k], sv[k * E + t], wi);
+        } else {
+          df_dot_acc(s[0], c[0], wi, wi);
+        }
+      }
     }
-    wdf[i] = wi;
-    if (NORM) {
-      df_dot_acc(s[0], c[0], wi, wi);
-    } else {
-#pragma unroll
-      for (int k = 0; k < NA; ++k) df_dot_acc(s[k], c[k], ld_again(V + k * ldv + i), wi);
+    if (!__syncthreads_and(ok)) {                    // stage q % S is free again from here on
+      if (tid == 0) {                                // record, then let the copies in flight land
+        atomicExch(&g_sweep_fault, 1);
+        for (size_t r = q; r < q + S && r < mine; ++r) mbar_wait(&bar[r % S], (unsigned)((r / S) & 1));
+      }
+      break;
     }
+    if (tid == 0 && q + S < mine) issue(q + S);
   }
   block_partials_df<NA>(s, c, partial);
 }
@@ -487,76 +561,83 @@ cudaError_t launch_hess_column(const double* h1, const double* h2, const double*
   return cudaGetLastError();
 }
 
-// Grid of the double-float sweeps: two blocks per SM at most, so that each thread handles
-// enough elements to amortise its reduction.
 int gs_blocks(size_t N) {
-  size_t g = (N + kDotThreads - 1) / kDotThreads;
-  if (g < 1) g = 1;
-  if (g > 152 * 2) g = 152 * 2;
-  return (int)g;
+  const size_t g = (N + kSweepThreads - 1) / kSweepThreads;
+  return (int)(g < 1 ? 1 : (g > 152 ? 152 : g));
 }
 
-template <typename TW>
-cudaError_t launch_gs_dot_t(const float2* V, size_t ldv, int nv, const TW* w, float2* wdf, size_t N,
-                            double* partial, double* out, cudaStream_t s) {
+template <int K, int MODE, typename TW>
+cudaError_t launch_sweep_k(const float2* V, size_t ldv, const TW* w, const double* h, float2* wdf, size_t N,
+                           double* partial, int* nblk_out, cudaStream_t s) {
+  using Sh = SweepShape<K>;
+  auto kern = k_gs_sweep<K, MODE, TW>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Sh::smem);
+  if (e != cudaSuccess) return e;
+  const size_t nchunk = (N + Sh::E - 1) / Sh::E;
+  const int nblk = (int)(nchunk < 1 ? 1 : (nchunk > 152 ? 152 : nchunk));
+  *nblk_out = nblk;
+  SBM_PDL(kern, nblk, kSweepThreads, Sh::smem, s, V, ldv, w, h, wdf, N, partial);
+  return cudaSuccess;
+}
+
+// One staged sweep over nv basis vectors and the reduction of its per-block partial sums into out
+// (nv values for MODE 0 and 1, the norm for MODE 2).
+template <int MODE, typename TW>
+cudaError_t launch_sweep(const float2* V, size_t ldv, int nv, const TW* w, const double* h, float2* wdf, size_t N,
+                         double* partial, double* out, cudaStream_t s) {
   if (nv < 1 || nv > kMaxVec) return cudaErrorInvalidValue;
-  const int nblk = gs_blocks(N);
+  const size_t padded = N + (N & 1);
+  if (ldv % 2 != 0 || ldv < padded || reinterpret_cast<uintptr_t>(V) % 16 != 0 ||
+      reinterpret_cast<uintptr_t>(w) % 16 != 0 || reinterpret_cast<uintptr_t>(wdf) % 16 != 0)
+    return cudaErrorInvalidValue;
+  int nblk = 1;
+  cudaError_t e = cudaSuccess;
   switch (nv) {
-#define SBM_GD_CASE(K) \
-  case K: SBM_PDL((k_gs_dot<K, TW>), nblk, kDotThreads, 0, s, V, ldv, w, wdf, N, partial); break;
-    SBM_GD_CASE(1) SBM_GD_CASE(2) SBM_GD_CASE(3) SBM_GD_CASE(4) SBM_GD_CASE(5) SBM_GD_CASE(6)
-    SBM_GD_CASE(7) SBM_GD_CASE(8) SBM_GD_CASE(9) SBM_GD_CASE(10) SBM_GD_CASE(11) SBM_GD_CASE(12)
-    SBM_GD_CASE(13) SBM_GD_CASE(14) SBM_GD_CASE(15) SBM_GD_CASE(16) SBM_GD_CASE(17) SBM_GD_CASE(18)
-    SBM_GD_CASE(19) SBM_GD_CASE(20) SBM_GD_CASE(21) SBM_GD_CASE(22) SBM_GD_CASE(23) SBM_GD_CASE(24)
-    SBM_GD_CASE(25) SBM_GD_CASE(26) SBM_GD_CASE(27) SBM_GD_CASE(28) SBM_GD_CASE(29) SBM_GD_CASE(30)
-    SBM_GD_CASE(31) SBM_GD_CASE(32)
-#undef SBM_GD_CASE
+#define SBM_SW_CASE(K) \
+  case K: e = launch_sweep_k<K, MODE, TW>(V, ldv, w, h, wdf, N, partial, &nblk, s); break;
+    SBM_SW_CASE(1) SBM_SW_CASE(2) SBM_SW_CASE(3) SBM_SW_CASE(4) SBM_SW_CASE(5) SBM_SW_CASE(6)
+    SBM_SW_CASE(7) SBM_SW_CASE(8) SBM_SW_CASE(9) SBM_SW_CASE(10) SBM_SW_CASE(11) SBM_SW_CASE(12)
+    SBM_SW_CASE(13) SBM_SW_CASE(14) SBM_SW_CASE(15) SBM_SW_CASE(16) SBM_SW_CASE(17) SBM_SW_CASE(18)
+    SBM_SW_CASE(19) SBM_SW_CASE(20) SBM_SW_CASE(21) SBM_SW_CASE(22) SBM_SW_CASE(23) SBM_SW_CASE(24)
+    SBM_SW_CASE(25) SBM_SW_CASE(26) SBM_SW_CASE(27) SBM_SW_CASE(28) SBM_SW_CASE(29) SBM_SW_CASE(30)
+    SBM_SW_CASE(31) SBM_SW_CASE(32)
+#undef SBM_SW_CASE
   }
-  SBM_PDL(k_reduce_partials, 1, 32 * nv, 0, s, partial, nblk, nv, out, 0);
+  if (e != cudaSuccess) return e;
+  const int nout = MODE == 2 ? 1 : nv;
+  SBM_PDL(k_reduce_partials, 1, 32 * nout, 0, s, partial, nblk, nout, out, MODE == 2 ? 1 : 0);
   count_launches(2);
   return cudaGetLastError();
 }
 
 cudaError_t launch_gs_dot(const float2* V, size_t ldv, int nv, const double* w, float2* wdf, size_t N,
                           double* partial, double* out, cudaStream_t s) {
-  return launch_gs_dot_t<double>(V, ldv, nv, w, wdf, N, partial, out, s);
+  return launch_sweep<0, double>(V, ldv, nv, w, nullptr, wdf, N, partial, out, s);
 }
 
 cudaError_t launch_gs_dot_df(const float2* V, size_t ldv, int nv, const float2* wdf, size_t N, double* partial,
                              double* out, cudaStream_t s) {
-  return launch_gs_dot_t<float2>(V, ldv, nv, wdf, nullptr, N, partial, out, s);
-}
-
-template <bool NORM>
-cudaError_t launch_gs_axpy(const float2* V, size_t ldv, int nv, const double* h, float2* wdf, size_t N,
-                           double* partial, double* out, cudaStream_t s) {
-  if (nv < 1 || nv > kMaxVec) return cudaErrorInvalidValue;
-  const int nblk = gs_blocks(N);
-  switch (nv) {
-#define SBM_GA_CASE(K) \
-  case K: SBM_PDL((k_gs_axpy_dot<K, NORM>), nblk, kDotThreads, 0, s, V, ldv, h, wdf, N, partial); break;
-    SBM_GA_CASE(1) SBM_GA_CASE(2) SBM_GA_CASE(3) SBM_GA_CASE(4) SBM_GA_CASE(5) SBM_GA_CASE(6)
-    SBM_GA_CASE(7) SBM_GA_CASE(8) SBM_GA_CASE(9) SBM_GA_CASE(10) SBM_GA_CASE(11) SBM_GA_CASE(12)
-    SBM_GA_CASE(13) SBM_GA_CASE(14) SBM_GA_CASE(15) SBM_GA_CASE(16) SBM_GA_CASE(17) SBM_GA_CASE(18)
-    SBM_GA_CASE(19) SBM_GA_CASE(20) SBM_GA_CASE(21) SBM_GA_CASE(22) SBM_GA_CASE(23) SBM_GA_CASE(24)
-    SBM_GA_CASE(25) SBM_GA_CASE(26) SBM_GA_CASE(27) SBM_GA_CASE(28) SBM_GA_CASE(29) SBM_GA_CASE(30)
-    SBM_GA_CASE(31) SBM_GA_CASE(32)
-#undef SBM_GA_CASE
-  }
-  const int nout = NORM ? 1 : nv;
-  SBM_PDL(k_reduce_partials, 1, 32 * nout, 0, s, partial, nblk, nout, out, NORM ? 1 : 0);
-  count_launches(2);
-  return cudaGetLastError();
+  return launch_sweep<0, float2>(V, ldv, nv, wdf, nullptr, const_cast<float2*>(wdf), N, partial, out, s);
 }
 
 cudaError_t launch_gs_axpy_dot(const float2* V, size_t ldv, int nv, const double* h, float2* wdf, size_t N,
                                double* partial, double* out, cudaStream_t s) {
-  return launch_gs_axpy<false>(V, ldv, nv, h, wdf, N, partial, out, s);
+  return launch_sweep<1, float2>(V, ldv, nv, wdf, h, wdf, N, partial, out, s);
 }
 
 cudaError_t launch_gs_axpy_norm(const float2* V, size_t ldv, int nv, const double* h, float2* wdf, size_t N,
                                 double* partial, double* out, cudaStream_t s) {
-  return launch_gs_axpy<true>(V, ldv, nv, h, wdf, N, partial, out, s);
+  return launch_sweep<2, float2>(V, ldv, nv, wdf, h, wdf, N, partial, out, s);
+}
+
+int sweep_fault_take() {
+  int f = 0;
+  if (cudaMemcpyFromSymbol(&f, g_sweep_fault, sizeof(int)) != cudaSuccess) return -1;
+  if (f) {
+    const int zero = 0;
+    if (cudaMemcpyToSymbol(g_sweep_fault, &zero, sizeof(int)) != cudaSuccess) return -1;
+  }
+  return f;
 }
 
 template <typename TW, typename TO>

@@ -128,7 +128,7 @@ cudaError_t launch_coarse(const double* Ainv, int N, const T* r, T* e, cudaStrea
 // ---------------------------------------------------------------- FGMRES building blocks (FP64)
 // Number of partial-sum blocks used for vectors of length N (fixed per N: deterministic sums).
 int dot_blocks(size_t N);
-// Blocks of the double-float Gram-Schmidt sweeps (rows of their partial-sum buffer).
+// Upper bound on the blocks of the double-float Gram-Schmidt sweeps (rows of their partial sums).
 int gs_blocks(size_t N);
 // out[k] = sum_i V[k*ldv + i] w[i], k < nv (nv <= 32); partial holds dot_blocks(N)*32 doubles.
 cudaError_t launch_multi_dot(const double* V, size_t ldv, int nv, const double* w, size_t N, double* partial,
@@ -156,6 +156,10 @@ cudaError_t launch_cast(const TI* x, TO* y, size_t N, cudaStream_t s);
 //   gs_axpy_dot:   wdf -= V h, out = V^T wdf
 //   gs_axpy_norm:  wdf -= V h, out = |wdf|
 //   gs_scale:      v = w / s[0] (w FP64 or double-float), and out = v rounded to TO if non-null
+// The first four stream V and w through shared memory with bulk asynchronous copies: V, w and
+// wdf must be 16-byte aligned, ldv even and >= N rounded up to even, and w / wdf hold that many
+// entries (cudaErrorInvalidValue otherwise).  A copy that does not complete in bounded time sets
+// a flag that sweep_fault_take() returns (1) and clears; -1 if the flag cannot be read.
 cudaError_t launch_gs_dot(const float2* V, size_t ldv, int nv, const double* w, float2* wdf, size_t N,
                           double* partial, double* out, cudaStream_t s);
 // gs_dot with w already double-float (wdf, read only)
@@ -171,6 +175,7 @@ template <typename TO>
 cudaError_t launch_df_to(const float2* v, TO* y, size_t N, cudaStream_t s);
 cudaError_t launch_hess_column(const double* h1, const double* h2, const double* hn, int k, double* col,
                                cudaStream_t s);
+int sweep_fault_take();
 
 // ---------------------------------------------------------------- learned boundary-cell correction
 template <typename TI>
