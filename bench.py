@@ -331,9 +331,9 @@ def run_ours(args) -> dict | None:
     nv = 27                                      # Gram-Schmidt width at the last step of the bench solve
     V64 = torch.rand((nv, N), device="cuda", dtype=torch.float64)
     geo_bytes = info["n_sface"] * (info["p"] + 1) ** (prob.dim - 1) * prob.dim
-    ncol = 2 ** prob.dim
+    ngrp = prob.dim + 1                          # smoother launches per sweep (colour groups)
     # the p = 1 level on the same mesh (one below the finest), whose smoother is the kernel with
-    # the largest share of the solve (three p = 1 levels, 8 launches each per V-cycle)
+    # the largest share of the solve (three p = 1 levels, two sweeps of d + 1 launches per V-cycle)
     Lp1 = s32.num_levels - 2
     info1 = s32.info(Lp1)
     N1 = info1["n_dof"]
@@ -341,21 +341,21 @@ def run_ours(args) -> dict | None:
     r1 = torch.rand(N1, device="cuda", dtype=torch.float32)
     u1 = torch.rand_like(r1)
     geo1 = info1["n_sface"] * (info1["p"] + 1) ** (prob.dim - 1) * prob.dim
-    t_smooth1 = event_time(torch, lambda: s32.smooth(r1, u1, level=Lp1), 20, flush) / 2 ** prob.dim
+    t_smooth1 = event_time(torch, lambda: s32.smooth(r1, u1, level=Lp1), 20, flush) / ngrp
     t_apply32 = event_time(torch, lambda: s32.apply(r32, y32), 20, flush)
     t_apply64 = event_time(torch, lambda: s64.apply(x64, y64), 20, flush)
-    t_smooth = event_time(torch, lambda: s32.smooth(r32, u32), 20, flush) / ncol
+    t_smooth = event_time(torch, lambda: s32.smooth(r32, u32), 20, flush) / ngrp
     t_dots = event_time(torch, lambda: s64.dots(V64, x64), 20, flush)
     hbm, src = peaks()
     fp64_tflops = 152 * 2.07e9 * 2 * 2 / 1e12    # SMs x max clock x 2 FP64 FMA/clk/SM x 2 flop
     kernels = {
-        f"k_smooth_cell<{prob.dim},{info1['p'] + 1},float> ({info1['n']}^{prob.dim} p={info1['p']} level, one colour)":
-            ("hbm", ((prob.dim + 2) * 4 * N1 + info1["n_boundary"] * nb1 * nb1 * 4 + 4 * geo1) / ncol, t_smooth1),
-        # one colour of the finest-level (p) block Gauss-Seidel sweep: f of the colour (N/2^d),
-        # u of the d neighbouring colours (d N/2^d), u written (N/2^d), the dense inverses of the
-        # colour's boundary cells and their face data
-        f"k_smooth_cell<{prob.dim},{info['p'] + 1},float> (finest level, one colour)":
-            ("hbm", ((prob.dim + 2) * 4 * N + info["n_boundary"] * nb * nb * 4 + 4 * geo_bytes) / ncol, t_smooth),
+        f"k_smooth_cell<{prob.dim},{info1['p'] + 1},float> ({info1['n']}^{prob.dim} p={info1['p']} level, mean launch of a sweep)":
+            ("hbm", ((prob.dim + 2) * 4 * N1 + info1["n_boundary"] * nb1 * nb1 * 4 + 4 * geo1) / ngrp, t_smooth1),
+        # one block Gauss-Seidel sweep of the finest level (p) moves f (N), u of the d neighbouring
+        # colours of every cell (d N), u written (N), the dense inverses of the boundary cells and
+        # their face data; it takes d + 1 launches (colour groups), and the unit is their mean
+        f"k_smooth_cell<{prob.dim},{info['p'] + 1},float> (finest level, mean launch of a sweep)":
+            ("hbm", ((prob.dim + 2) * 4 * N + info["n_boundary"] * nb * nb * 4 + 4 * geo_bytes) / ngrp, t_smooth),
         f"k_apply_cell<{prob.dim},{info['p'] + 1},float> (FP32 operator, finest level)":
             ("hbm", 2 * 4 * N + 4 * geo_bytes, t_apply32),
         f"k_apply<{prob.dim},{info['p'] + 1},double> (FP64 operator, finest level)":
@@ -543,16 +543,16 @@ def run_roofline_sweep(args) -> dict:
             inf = g.info(level)
             N = inf["n_dof"]
             npc = (inf["p"] + 1) ** prob.dim
-            ncol = 2 ** prob.dim
+            ngrp = prob.dim + 1                  # launches per sweep (colour groups)
             geo = 4 * inf["n_sface"] * (inf["p"] + 1) ** (prob.dim - 1) * prob.dim
             f = torch.rand(N, device="cuda")
             u = torch.rand_like(f)
             y = torch.empty_like(f)
             t_apply = event_time(torch, lambda: g.apply(f, y, level=level), 10, flush)
-            t_smooth = event_time(torch, lambda: g.smooth(f, u, level=level), 10, flush) / ncol
+            t_smooth = event_time(torch, lambda: g.smooth(f, u, level=level), 10, flush) / ngrp
             b_apply = 2 * 4 * N + geo
-            b_smooth = ((prob.dim + 2) * 4 * N + inf["n_boundary"] * npc * npc * 4 + geo) / ncol
-            for kern, b, t in (("apply", b_apply, t_apply), ("smoother colour", b_smooth, t_smooth)):
+            b_smooth = ((prob.dim + 2) * 4 * N + inf["n_boundary"] * npc * npc * 4 + geo) / ngrp
+            for kern, b, t in (("apply", b_apply, t_apply), ("smoother, mean launch of a sweep", b_smooth, t_smooth)):
                 gbs = b / t / 1e6
                 rows.append({"workload": label, "level": f"{inf['n']}^{prob.dim} p={inf['p']}", "n_dof": N,
                              "kernel": kern, "bytes": int(b), "ms": round(t, 5), "GB/s": round(gbs, 1),

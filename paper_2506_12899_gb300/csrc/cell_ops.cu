@@ -406,19 +406,20 @@ __device__ __forceinline__ void smooth_one(const LevelParams<R>& P, int col, int
   }
 }
 
-// One colour of the block Gauss-Seidel sweep, one thread per cell: boundary cells of the colour
-// in blocks [0, nblk_b), interior cells in the remaining blocks.
+// One colour group of the block Gauss-Seidel sweep, one thread per cell: block b updates cells of
+// the segment whose block range holds b.
 template <int D, int N1, typename R>
-__global__ void __launch_bounds__(kCellThreads) k_smooth_cell(const __grid_constant__ LevelParams<R> P, int col,
-                                                              int zero_start, int cs, int nbnd, int ce, int nblk_b,
-                                                              int b0, const R* __restrict__ f, R* __restrict__ u) {
+__global__ void __launch_bounds__(kCellThreads) k_smooth_cell(const __grid_constant__ LevelParams<R> P,
+                                                              const __grid_constant__ SmoothSegs G, int zero_start,
+                                                              const R* __restrict__ f, R* __restrict__ u) {
   pdl_entry();
-  const bool isB = (int)blockIdx.x < nblk_b;
-  const int first = isB ? cs + blockIdx.x * blockDim.x : cs + nbnd + (blockIdx.x - nblk_b) * blockDim.x;
-  const int last = isB ? cs + nbnd : ce;
-  const int a = first + threadIdx.x;
-  if (a >= last) return;
-  smooth_one<D, N1, R>(P, col, zero_start, cs, nbnd, b0, a, f, u);
+  int sg = 0;
+#pragma unroll
+  for (int k = 1; k < SmoothSegs::kMax; ++k)
+    if (k < G.n && (int)blockIdx.x >= G.blk[k]) sg = k;
+  const int a = G.first[sg] + ((int)blockIdx.x - G.blk[sg]) * (int)blockDim.x + (int)threadIdx.x;
+  if (a >= G.last[sg]) return;
+  smooth_one<D, N1, R>(P, G.col[sg], zero_start, G.cs[sg], G.nbnd[sg], G.b0[sg], a, f, u);
 }
 
 // Residual and p-restriction fused, one thread per cell (Eqs. 11, 18).
@@ -932,16 +933,12 @@ template <typename R>
 cudaError_t launch_smooth_cell(int dim, int p, const LevelParams<R>& P, int reverse, int zero_start, const R* f,
                                R* u, cudaStream_t s) {
   if (reverse) zero_start = 0;
-  const int ncol = 1 << dim;
-  for (int q = 0; q < ncol; ++q) {   // (the launcher in level_ops.cu chose this path for the level)
-    const int col = reverse ? ncol - 1 - q : q;
-    const int cs = P.colour_start[col], ce = P.colour_start[col + 1], nbnd = P.colour_nbnd[col];
-    const unsigned bs = cell_block(ce - cs);
-    const int nblk_b = (int)cdiv(nbnd, bs), nblk_i = (int)cdiv(ce - cs - nbnd, bs);
-    if (nblk_b + nblk_i == 0) continue;
-#define SBM_SC(D, N1)                                                                                    \
-  SBM_PDL((k_smooth_cell<D, N1, R>), nblk_b + nblk_i, bs, 0, s, P, col, zero_start, cs, nbnd, ce, nblk_b, \
-                                                                   P.bstart[col], f, u);
+  for (int q = 0; q <= dim; ++q) {   // (the launcher in level_ops.cu chose this path for the level)
+    const int g = reverse ? dim - q : q;
+    const unsigned bs = cell_block(group_cells(P, dim, g));
+    const SmoothSegs G = smooth_segs(P, dim, g, (int)bs);
+    if (G.n == 0 || G.blk[G.n] == 0) continue;
+#define SBM_SC(D, N1) SBM_PDL((k_smooth_cell<D, N1, R>), G.blk[G.n], bs, 0, s, P, G, zero_start, f, u);
     SBM_CELL_DISPATCH(dim, p, SBM_SC);
 #undef SBM_SC
     count_launches();

@@ -351,8 +351,8 @@ __global__ void __launch_bounds__(256) k_resid_restrict_h(const __grid_constant_
 // zero_start: u is the zero vector before this forward sweep; cells of colours not yet visited
 // (neighbour colour > col) are read as zero and u itself is not read, so no memset is needed.
 template <int D, int N1, typename R>
-__global__ void __launch_bounds__(256) k_smooth(const __grid_constant__ LevelParams<R> P, int col, int zero_start,
-                                                int cs, int nbnd, int ce, int nblk_b, int b0,
+__global__ void __launch_bounds__(256) k_smooth(const __grid_constant__ LevelParams<R> P,
+                                                const __grid_constant__ SmoothSegs G, int zero_start,
                                                 const R* __restrict__ f, R* __restrict__ u) {
   pdl_entry();
   using Dm = Dims<D, N1>;
@@ -361,9 +361,14 @@ __global__ void __launch_bounds__(256) k_smooth(const __grid_constant__ LevelPar
   __shared__ R sN[CPB * NS * NP];
   __shared__ R sT[CPB * NP], sW[CPB * NP];
   load_consts(P.k, C);
-  const bool isB = (int)blockIdx.x < nblk_b;
-  const int first = isB ? cs + blockIdx.x * CPB : cs + nbnd + (blockIdx.x - nblk_b) * CPB;
-  const int last = isB ? cs + nbnd : ce;
+  int sg = 0;                                        // the segment of this block (one colour, one kind)
+#pragma unroll
+  for (int k = 1; k < SmoothSegs::kMax; ++k)
+    if (k < G.n && (int)blockIdx.x >= G.blk[k]) sg = k;
+  const int col = G.col[sg], cs = G.cs[sg], b0 = G.b0[sg];
+  const bool isB = G.first[sg] < cs + G.nbnd[sg];
+  const int first = G.first[sg] + ((int)blockIdx.x - G.blk[sg]) * CPB;
+  const int last = G.last[sg];
   const int c = threadIdx.x / NP, i = threadIdx.x - c * NP;
   const int a = first + c;
   const bool valid = threadIdx.x < CPB * NP && a < last;
@@ -596,18 +601,14 @@ cudaError_t launch_smooth(int dim, int p, const LevelParams<R>& P, int reverse, 
   if (cell_kernels(dim, p) && P.cell_min > 0 && P.n_act >= (1 << dim) * P.cell_min)
     return launch_smooth_cell<R>(dim, p, P, reverse, zero_start, f, u, s);
   if (reverse) zero_start = 0;
-  const int ncol = 1 << dim;
-  for (int q = 0; q < ncol; ++q) {
-    const int col = reverse ? ncol - 1 - q : q;
-    const int cs = P.colour_start[col], ce = P.colour_start[col + 1], nbnd = P.colour_nbnd[col];
+  for (int q = 0; q <= dim; ++q) {
+    const int g = reverse ? dim - q : q;
 #define SBM_SMOOTH(D, N1)                                                                          \
   {                                                                                                \
     using Dm = Dims<D, N1>;                                                                        \
-    const int nblk_b = (int)ceil_div(nbnd, Dm::CPB);                                               \
-    const int nblk_i = (int)ceil_div(ce - cs - nbnd, Dm::CPB);                                     \
-    if (nblk_b + nblk_i > 0) {                                                                     \
-      SBM_PDL((k_smooth<D, N1, R>), nblk_b + nblk_i, Dm::NT, 0, s, P, col, zero_start, cs, nbnd, ce, nblk_b,   \
-                                                            P.bstart[col], f, u);                    \
+    const SmoothSegs G = smooth_segs(P, dim, g, Dm::CPB);                                          \
+    if (G.n > 0 && G.blk[G.n] > 0) {                                                               \
+      SBM_PDL((k_smooth<D, N1, R>), G.blk[G.n], Dm::NT, 0, s, P, G, zero_start, f, u);             \
       count_launches();                                                                            \
     }                                                                                              \
   }

@@ -63,6 +63,46 @@ int record_error(int code, const std::string& msg);
 int dots_noalloc(const double* V, long long ldv, int nv, const double* w, long long n, double* out,
                  cudaStream_t stream);
 
+// Colour groups of the coloured smoother.  Colour c(K) = sum_k (i_k mod 2) 2^k; face neighbours
+// differ in exactly one index parity, so a neighbour of colour c has colour c ^ 2^k: lower than c
+// (visited earlier in the forward order 0, 1, ..., 2^d - 1) exactly when it has one odd bit less.
+// Cells of colours with the same number g of odd bits therefore never neighbour one another, and
+// the forward sweep over colours equals the sweep over groups g = 0..d (reverse: d..0) with all
+// colours of a group updated by one launch: every cell reads the same neighbour values.
+// smooth_segs lists the segments of group g with cpb cells per block.
+template <typename R>
+inline SmoothSegs smooth_segs(const LevelParams<R>& P, int dim, int g, int cpb) {
+  SmoothSegs G{};
+  G.n = 0;
+  G.blk[0] = 0;
+  for (int c = 0; c < (1 << dim); ++c) {
+    if (__builtin_popcount((unsigned)c) != g) continue;
+    const int cs = P.colour_start[c], ce = P.colour_start[c + 1], nb = P.colour_nbnd[c];
+    const int lo[2] = {cs, cs + nb}, hi[2] = {cs + nb, ce};
+    for (int part = 0; part < 2; ++part) {
+      if (hi[part] <= lo[part]) continue;
+      const int k = G.n++;
+      G.first[k] = lo[part];
+      G.last[k] = hi[part];
+      G.col[k] = c;
+      G.cs[k] = cs;
+      G.nbnd[k] = nb;
+      G.b0[k] = P.bstart[c];
+      G.blk[k + 1] = G.blk[k] + (hi[part] - lo[part] + cpb - 1) / cpb;
+    }
+  }
+  return G;
+}
+
+// Cells of colour group g (colours with g odd index bits).
+template <typename R>
+inline int group_cells(const LevelParams<R>& P, int dim, int g) {
+  int n = 0;
+  for (int c = 0; c < (1 << dim); ++c)
+    if (__builtin_popcount((unsigned)c) == g) n += P.colour_start[c + 1] - P.colour_start[c];
+  return n;
+}
+
 // Thread-per-cell kernels (cell_ops.cu) serve levels with (p+1)^d <= 16: 2D, and 3D with p = 1.
 bool cell_kernels(int dim, int p);
 template <typename TI, typename R>
@@ -101,8 +141,9 @@ template <typename TI, typename R>
 cudaError_t launch_apply(int dim, int p, const LevelParams<R>& P, const TI* x, const R* f, R* y, int mode,
                          cudaStream_t s);
 
-// One coloured block Gauss-Seidel sweep (all colours, forward or reverse).  zero_start (forward
-// only): u holds zeros on entry and is not read or cleared beforehand.
+// One coloured block Gauss-Seidel sweep (all colours, forward or reverse), one launch per colour
+// group (smooth_segs).  zero_start (forward only): u holds zeros on entry and is not read or
+// cleared beforehand.
 template <typename R>
 cudaError_t launch_smooth(int dim, int p, const LevelParams<R>& P, int reverse, int zero_start, const R* f, R* u,
                           cudaStream_t s);

@@ -113,6 +113,17 @@ struct LevelParams {
   LevelConsts<R> k;
 };
 
+// The cells one smoother launch updates: the colours of one colour group (equal number of odd
+// index bits), each as a boundary segment then an interior segment.  Segment k covers cells
+// [first[k], last[k]) of colour col[k] (colour starting at cs[k], nbnd[k] boundary cells, boundary
+// index b0[k] of its first cell) and blocks [blk[k], blk[k + 1]) of the grid.
+struct SmoothSegs {
+  static constexpr int kMax = 6;
+  int n;
+  int first[kMax], last[kMax], col[kMax], cs[kMax], nbnd[kMax], b0[kMax];
+  int blk[kMax + 1];
+};
+
 // Transfer parameter block between level l-1 (coarse) and l (fine).
 template <typename R>
 struct TransferParams {
