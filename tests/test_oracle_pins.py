@@ -274,6 +274,41 @@ def test_coloured_sweep_equals_sequential_block_gs():
         assert np.linalg.norm(a - b) <= 1e-12 * np.linalg.norm(b)
 
 
+def test_colour_groups_equal_colour_order():
+    """Colour c(K) = sum_k (i_k mod 2) 2^k; face neighbours differ in one index parity, so colours
+    with the same number of odd bits never couple.  The sweep in colour order 0..2^d-1 therefore
+    equals the sweep that updates all colours with g odd bits at once, g = 0..d (reverse: d..0);
+    the GPU smoother launches one such group per launch.  The pin: no face couples two colours of
+    one group (the off-diagonal blocks of A between them vanish), and the grouped simultaneous
+    update reproduces the oracle's coloured sweep exactly."""
+    for prob in (W.star2d_p2(16, 1), W.sphere3d(6, 2, 1)):
+        lev = MG.Level(prob, prob.n, prob.p)
+        d, nb = prob.dim, lev.nb
+        pop = np.array([bin(c).count("1") for c in range(2 ** d)])
+        rows = []
+        for g in range(d + 1):
+            cells = np.concatenate([lev.cells_of_colour[c] for c in range(2 ** d) if pop[c] == g])
+            idx = (cells[:, None] * nb + np.arange(nb)[None, :]).reshape(-1)
+            rows.append((cells, idx))
+            blk = lev.A[idx][:, idx].tocoo()
+            same = (blk.row // nb) == (blk.col // nb)
+            assert np.all(blk.data[~same] == 0.0)
+        rng = np.random.default_rng(4)
+        f, u0 = rng.normal(size=lev.N), rng.normal(size=lev.N)
+        for reverse in (False, True):
+            u = u0.copy()
+            for g in (range(d, -1, -1) if reverse else range(d + 1)):
+                cells, idx = rows[g]
+                r = (f[idx] - lev.A[idx] @ u).reshape(len(cells), nb)
+                u[idx] += lev.omega * np.einsum("kij,kj->ki", lev.diag_inv[cells], r).reshape(-1)
+            ref = lev.coloured_sweep(u0.copy(), f, reverse=reverse)
+            assert np.linalg.norm(u - ref) <= 1e-14 * np.linalg.norm(ref)
+        # a colour order that is not grouped by odd-bit count gives a different map
+        bad = lev.block_gs_sequential(u0.copy(), f, np.concatenate([lev.cells_of_colour[c] for c in
+                                                                     [0, 3, 1, 2] + list(range(4, 2 ** d))]))
+        assert np.linalg.norm(bad - lev.coloured_sweep(u0.copy(), f)) > 1e-8 * np.linalg.norm(bad)
+
+
 def test_block_gs_converges_to_solution():
     """Repeated symmetric block Gauss-Seidel on an SPD system converges to A^{-1} f."""
     prob = W.Problem(dim=2, n=8, p=2, shape=W.box(0.5))
