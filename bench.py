@@ -423,7 +423,7 @@ def run_profile(args) -> None:
     solve:   one warm-up and one FP32-V-cycle FGMRES solve of --workload; prints how many of the
              library's kernels the warm-up launched (the ncu skip count) and how many the solve did.
     kernels: 2D p=2 star at --profile-n^2 cells (or the 3D sphere of degree --profile-p at
-             --profile-n^3): one FP32 operator apply, one finest-level smoother sweep (2^d colour
+             --profile-n^3): one FP32 operator apply, one finest-level smoother sweep (d+1 colour-group
              launches) and one V-cycle."""
     import torch
     import paper_2506_12899_gb300 as S
