@@ -278,13 +278,11 @@ __device__ __forceinline__ void load_nbr(const LevelParams<R>& P, int a, int (&n
   for (int s = 0; s < 2 * D; ++s) nb[s] = P.nbr[(size_t)s * P.n_act + a];
 }
 
-// y = (A x)_a with the reference scaling h^(d-2) applied.
+// y = (A x)_a with the reference scaling h^(d-2) applied; nb: the neighbours of a (load_nbr).
 template <int D, int N1, typename TI, typename R>
 __device__ __forceinline__ void cell_apply(const LevelParams<R>& P, const TI* __restrict__ x, int a,
-                                           R (&y)[CD<D, N1>::NP]) {
+                                           const int (&nb)[2 * D], R (&y)[CD<D, N1>::NP]) {
   constexpr int NP = CD<D, N1>::NP;
-  int nb[2 * D];
-  load_nbr<D, R>(P, a, nb);
   R v[NP];
   load_cell<D, N1, TI, R>(x, a, v);
 #pragma unroll
@@ -299,12 +297,15 @@ template <int D, int N1, typename TI, typename R, int MODE>
 __global__ void __launch_bounds__(kCellThreads) k_apply_cell(const __grid_constant__ LevelParams<R> P,
                                                              const TI* __restrict__ x, const R* __restrict__ f,
                                                              R* __restrict__ y) {
-  pdl_entry();
   constexpr int NP = CD<D, N1>::NP;
   const int a = blockIdx.x * blockDim.x + threadIdx.x;
+  int nb[2 * D];
+  if (a < P.n_act) load_nbr<D, R>(P, a, nb);       // set-up data: read before the wait
+  pdl_wait();
+  pdl_trigger();
   if (a >= P.n_act) return;
   R r[NP];
-  cell_apply<D, N1, TI, R>(P, x, a, r);
+  cell_apply<D, N1, TI, R>(P, x, a, nb, r);
 #pragma unroll
   for (int i = 0; i < NP; ++i) y[(size_t)a * NP + i] = MODE == 1 ? f[(size_t)a * NP + i] - r[i] : r[i];
 }
@@ -380,11 +381,10 @@ __device__ __forceinline__ void block_solve_at(const LevelParams<R>& P, const R*
 // b0 + a - cs); the others use the fast diagonalisation.  zero_start as in k_smooth.
 template <int D, int N1, typename R>
 __device__ __forceinline__ void smooth_one(const LevelParams<R>& P, int col, int zero_start, int cs, int nbnd,
-                                           int b0, int a, const R* __restrict__ f, R* __restrict__ u) {
+                                           int b0, int a, const int (&nb)[2 * D], const R* __restrict__ f,
+                                           R* __restrict__ u) {
   constexpr int NP = CD<D, N1>::NP;
   const bool isB = a - cs < nbnd;
-  int nb[2 * D];
-  load_nbr<D, R>(P, a, nb);
   R c[NP];
 #pragma unroll
   for (int i = 0; i < NP; ++i) c[i] = 0;
@@ -412,14 +412,17 @@ template <int D, int N1, typename R>
 __global__ void __launch_bounds__(kCellThreads) k_smooth_cell(const __grid_constant__ LevelParams<R> P,
                                                               const __grid_constant__ SmoothSegs G, int zero_start,
                                                               const R* __restrict__ f, R* __restrict__ u) {
-  pdl_entry();
   int sg = 0;
 #pragma unroll
   for (int k = 1; k < SmoothSegs::kMax; ++k)
     if (k < G.n && (int)blockIdx.x >= G.blk[k]) sg = k;
   const int a = G.first[sg] + ((int)blockIdx.x - G.blk[sg]) * (int)blockDim.x + (int)threadIdx.x;
+  int nb[2 * D];
+  if (a < G.last[sg]) load_nbr<D, R>(P, a, nb);     // set-up data: read before the wait
+  pdl_wait();
+  pdl_trigger();
   if (a >= G.last[sg]) return;
-  smooth_one<D, N1, R>(P, G.col[sg], zero_start, G.cs[sg], G.nbnd[sg], G.b0[sg], a, f, u);
+  smooth_one<D, N1, R>(P, G.col[sg], zero_start, G.cs[sg], G.nbnd[sg], G.b0[sg], a, nb, f, u);
 }
 
 // Residual and p-restriction fused, one thread per cell (Eqs. 11, 18).
@@ -428,13 +431,16 @@ __global__ void __launch_bounds__(kCellThreads) k_resid_restrict_p_cell(const __
                                                                         const __grid_constant__ TransferParams<R> T,
                                                                         const R* __restrict__ u,
                                                                         const R* __restrict__ f, R* __restrict__ rc) {
-  pdl_entry();
   constexpr int NP = CD<D, N1>::NP;
   constexpr int NPC = D == 2 ? NC * NC : NC * NC * NC;
   const int a = blockIdx.x * blockDim.x + threadIdx.x;
+  int nb[2 * D];
+  if (a < P.n_act) load_nbr<D, R>(P, a, nb);       // set-up data: read before the wait
+  pdl_wait();
+  pdl_trigger();
   if (a >= P.n_act) return;
   R r[NP];
-  cell_apply<D, N1, R, R>(P, u, a, r);
+  cell_apply<D, N1, R, R>(P, u, a, nb, r);
 #pragma unroll
   for (int i = 0; i < NP; ++i) r[i] = f[(size_t)a * NP + i] - r[i];
 #pragma unroll
@@ -468,17 +474,21 @@ __global__ void __launch_bounds__(kCellThreads) k_resid_restrict_h_cell(const __
                                                                         const __grid_constant__ TransferParams<R> T,
                                                                         const R* __restrict__ u,
                                                                         const R* __restrict__ f, R* __restrict__ rc) {
-  pdl_entry();
   constexpr int NCOL = 1 << D, NP = CD<D, 2>::NP;
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   const int cc = t / NCOL, o = t % NCOL;
   R out[NP];
 #pragma unroll
   for (int j = 0; j < NP; ++j) out[j] = 0;
+  // the child and its neighbours are set-up data: read before the wait
   const int a = cc < T.n_act_c ? T.children[(size_t)o * T.n_act_c + cc] : -1;
+  int nb[2 * D];
+  if (a >= 0) load_nbr<D, R>(P, a, nb);
+  pdl_wait();
+  pdl_trigger();
   if (a >= 0) {
     R r[NP], fa[NP];
-    cell_apply<D, 2, R, R>(P, u, a, r);
+    cell_apply<D, 2, R, R>(P, u, a, nb, r);
     load_cell<D, 2, R, R>(f, a, fa);
 #pragma unroll
     for (int i = 0; i < NP; ++i) r[i] = fa[i] - r[i];
@@ -722,43 +732,65 @@ __global__ void __launch_bounds__(kTailThreads, 1) k_vcycle_tail(const TailLevel
 // The V-cycle of levels 0..top (p = 1 h-levels) in one CTA: all data of those levels in shared
 // memory, phases separated by __syncthreads(); see TailCta.
 // ----------------------------------------------------------------------------------------------
-constexpr int kTailCtaThreads = 512;
+// Threads of the one-CTA tail: 1024 for 2D FP32 (a colour group of the 64^2 level in one pass), 512
+// otherwise (register budget).
+template <int D, typename R>
+constexpr int tail_cta_threads() {
+  return D == 2 && sizeof(R) == 4 ? 1024 : 512;
+}
 
 template <int D, typename R>
-__global__ void __launch_bounds__(kTailCtaThreads, 1) k_vcycle_tail_cta(const __grid_constant__ TailCta<R> TP,
+__global__ void __launch_bounds__(tail_cta_threads<D, R>(), 1) k_vcycle_tail_cta(const __grid_constant__ TailCta<R> TP,
                                                                         const R* __restrict__ r_top,
                                                                         R* __restrict__ z_top,
                                                                         const double* __restrict__ coarse_inv) {
-  pdl_entry();
   extern __shared__ __align__(16) unsigned char tcta_smem[];
   R* sm = reinterpret_cast<R*>(tcta_smem);
   int* si = reinterpret_cast<int*>(tcta_smem + TP.int_base);
-  constexpr int NCOL = 1 << D, NP = CD<D, 2>::NP;
+  constexpr int NCOL = 1 << D, NP = CD<D, 2>::NP, NT = tail_cta_threads<D, R>();
   const int top = TP.top, tid = threadIdx.x;
-  // stage the tables and inverses of every level, and the top level's right-hand side
+  // stage the tables and inverses of every level (set-up data, staged while the kernel before
+  // finishes), then, after the wait, the top level's right-hand side
   for (int l = 0; l <= top; ++l) {
     const LevelParams<R>& P = TP.P[l];
-    for (int q = tid; q < 2 * D * P.n_act; q += kTailCtaThreads) si[TP.noff[l] + q] = P.nbr[q];
-    for (int q = tid; q < TP.n_bnd[l] * NP * NP; q += kTailCtaThreads) sm[TP.boff[l] + q] = P.binvT[q];
+    for (int q = tid; q < 2 * D * P.n_act; q += NT) si[TP.noff[l] + q] = P.nbr[q];
+    for (int q = tid; q < TP.n_bnd[l] * NP * NP; q += NT) sm[TP.boff[l] + q] = P.binvT[q];
     if (l >= 1) {
       const TransferParams<R>& T = TP.T[l];
-      for (int q = tid; q < NCOL * T.n_act_c; q += kTailCtaThreads) si[TP.coff[l] + q] = T.children[q];
-      for (int q = tid; q < T.n_act_f; q += kTailCtaThreads) si[TP.poff[l] + q] = T.parent_code[q];
+      for (int q = tid; q < NCOL * T.n_act_c; q += NT) si[TP.coff[l] + q] = T.children[q];
+      for (int q = tid; q < T.n_act_f; q += NT) si[TP.poff[l] + q] = T.parent_code[q];
     }
   }
-  for (int q = tid; q < TP.P[top].n_act * NP; q += kTailCtaThreads) sm[TP.roff[top] + q] = r_top[q];
+  pdl_wait();
+  pdl_trigger();
+  for (int q = tid; q < TP.P[top].n_act * NP; q += NT) sm[TP.roff[top] + q] = r_top[q];
   __syncthreads();
 
   auto nbr_of = [&](int l, int a, int (&nb)[2 * D]) {
 #pragma unroll
     for (int s = 0; s < 2 * D; ++s) nb[s] = si[TP.noff[l] + s * TP.P[l].n_act + a];
   };
-  auto smooth = [&](int l, int col, bool zs) {
+  // one colour group g (colours with g odd index bits, which share no face): all its cells at once
+  auto smooth = [&](int l, int g, bool zs) {
     const LevelParams<R>& P = TP.P[l];
-    const int cs = P.colour_start[col], ce = P.colour_start[col + 1], nbnd = P.colour_nbnd[col];
+    // the group's colours c0 < c1 < c2 (at most three) and the running cell counts before c1, c2
+    int c0 = -1, c1 = -1, c2 = -1, n0 = 0, n1 = 0, n2 = 0;
+#pragma unroll
+    for (int c = 0; c < NCOL; ++c)
+      if (__popc(c) == g) {
+        const int n = P.colour_start[c + 1] - P.colour_start[c];
+        if (c0 < 0) { c0 = c; n0 = n; }
+        else if (c1 < 0) { c1 = c; n1 = n; }
+        else { c2 = c; n2 = n; }
+      }
     R* z = sm + TP.zoff[l];
     const R* f = sm + TP.roff[l];
-    for (int a = cs + tid; a < ce; a += kTailCtaThreads) {
+    for (int idx = tid; idx < n0 + n1 + n2; idx += NT) {
+      int col = c0, base = 0;
+      if (idx >= n0 + n1) { col = c2; base = n0 + n1; }
+      else if (idx >= n0) { col = c1; base = n0; }
+      const int cs = P.colour_start[col], nbnd = P.colour_nbnd[col];
+      const int a = cs + idx - base;
       int nb[2 * D];
       nbr_of(l, a, nb);
       R c[NP];
@@ -792,17 +824,17 @@ __global__ void __launch_bounds__(kTailCtaThreads, 1) k_vcycle_tail_cta(const __
   for (int l = top; l >= 1; --l) {                 // down: pre-smooth, residual, restrict
     const LevelParams<R>& P = TP.P[l];
     if (TP.pre == 0) {
-      for (int q = tid; q < P.n_act * NP; q += kTailCtaThreads) sm[TP.zoff[l] + q] = R(0);
+      for (int q = tid; q < P.n_act * NP; q += NT) sm[TP.zoff[l] + q] = R(0);
       __syncthreads();
     }
     for (int k = 0; k < TP.pre; ++k) {
-      for (int col = 0; col < NCOL; ++col) {
-        smooth(l, col, k == 0);
+      for (int g = 0; g <= D; ++g) {
+        smooth(l, g, k == 0);
         __syncthreads();
       }
       if (TP.ssor)
-        for (int q = 0; q < NCOL; ++q) {
-          smooth(l, NCOL - 1 - q, false);
+        for (int g = D; g >= 0; --g) {
+          smooth(l, g, false);
           __syncthreads();
         }
     }
@@ -810,7 +842,7 @@ __global__ void __launch_bounds__(kTailCtaThreads, 1) k_vcycle_tail_cta(const __
     const R* z = sm + TP.zoff[l];
     const R* f = sm + TP.roff[l];
     R* rc = sm + TP.roff[l - 1];
-    for (int cc = tid; cc < T.n_act_c; cc += kTailCtaThreads) {
+    for (int cc = tid; cc < T.n_act_c; cc += NT) {
       R out[NP];
 #pragma unroll
       for (int j = 0; j < NP; ++j) out[j] = 0;
@@ -852,7 +884,7 @@ __global__ void __launch_bounds__(kTailCtaThreads, 1) k_vcycle_tail_cta(const __
     const R* r0 = sm + TP.roff[0];
     R* z0 = sm + TP.zoff[0];
     const int lane = tid & 31;
-    for (int row = tid >> 5; row < n0; row += kTailCtaThreads / 32) {
+    for (int row = tid >> 5; row < n0; row += NT / 32) {
       double acc = 0;
       for (int c = lane; c < n0; c += 32) acc += coarse_inv[(size_t)row * n0 + c] * (double)r0[c];
 #pragma unroll
@@ -866,7 +898,7 @@ __global__ void __launch_bounds__(kTailCtaThreads, 1) k_vcycle_tail_cta(const __
     const TransferParams<R>& T = TP.T[l];
     R* z = sm + TP.zoff[l];
     const R* zc = sm + TP.zoff[l - 1];
-    for (int a = tid; a < P.n_act; a += kTailCtaThreads) {
+    for (int a = tid; a < P.n_act; a += NT) {
       const int code = si[TP.poff[l] + a];
       if (code < 0) continue;
       const int par = code >> 3, o = code & 7;
@@ -885,17 +917,17 @@ __global__ void __launch_bounds__(kTailCtaThreads, 1) k_vcycle_tail_cta(const __
     __syncthreads();
     for (int k = 0; k < TP.post; ++k) {
       if (TP.ssor)
-        for (int col = 0; col < NCOL; ++col) {
-          smooth(l, col, false);
+        for (int g = 0; g <= D; ++g) {
+          smooth(l, g, false);
           __syncthreads();
         }
-      for (int q = 0; q < NCOL; ++q) {
-        smooth(l, NCOL - 1 - q, false);
+      for (int g = D; g >= 0; --g) {
+        smooth(l, g, false);
         __syncthreads();
       }
     }
   }
-  for (int q = tid; q < TP.P[top].n_act * NP; q += kTailCtaThreads) z_top[q] = sm[TP.zoff[top] + q];
+  for (int q = tid; q < TP.P[top].n_act * NP; q += NT) z_top[q] = sm[TP.zoff[top] + q];
 }
 
 inline unsigned cdiv(size_t a, size_t b) { return (unsigned)((a + b - 1) / b); }
@@ -1064,8 +1096,8 @@ bool tail_cta_fits(int dim, int prec, size_t smem, size_t param_bytes) {
 template <typename R>
 cudaError_t launch_vcycle_tail_cta(int dim, const TailCta<R>& TP, const R* r, R* z, const double* coarse_inv,
                                    size_t smem, cudaStream_t s) {
-  if (dim == 2) SBM_PDL((k_vcycle_tail_cta<2, R>), 1, kTailCtaThreads, smem, s, TP, r, z, coarse_inv);
-  else SBM_PDL((k_vcycle_tail_cta<3, R>), 1, kTailCtaThreads, smem, s, TP, r, z, coarse_inv);
+  if (dim == 2) SBM_PDL((k_vcycle_tail_cta<2, R>), 1, (tail_cta_threads<2, R>()), smem, s, TP, r, z, coarse_inv);
+  else SBM_PDL((k_vcycle_tail_cta<3, R>), 1, (tail_cta_threads<3, R>()), smem, s, TP, r, z, coarse_inv);
   count_launches();
   return cudaGetLastError();
 }

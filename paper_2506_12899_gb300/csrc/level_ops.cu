@@ -163,23 +163,26 @@ __device__ __forceinline__ R sbm_face_terms(const LevelParams<R>& P, const Level
   return acc;
 }
 
-// (A x) at dof i of the block's cell slot c (cell a) on one level; every thread of the block calls
-// this (it contains barriers).  Stages the block's cells and their face neighbours in shared memory.
+// Face neighbours of cell a (-1 on every slot when !valid): set-up data, read before pdl_wait().
+template <int D, typename R>
+__device__ __forceinline__ void dof_nbr(const LevelParams<R>& P, int a, bool valid, int (&nb)[2 * D]) {
+#pragma unroll
+  for (int s = 0; s < 2 * D; ++s) nb[s] = valid ? P.nbr[(size_t)s * P.n_act + a] : -1;
+}
+
+// (A x) at dof i of the block's cell slot c (cell a, neighbours nb from dof_nbr) on one level;
+// every thread of the block calls this (it contains barriers).  Stages the block's cells and their
+// face neighbours in shared memory.
 template <int D, int N1, typename TI, typename R>
 __device__ __forceinline__ R apply_dof(const LevelParams<R>& P, const LevelConsts<R>& C, const TI* __restrict__ x,
-                                       int c, int i, int a, bool valid, R* sU, R* sN, R* sA, R* sB, R* sE) {
+                                       int c, int i, int a, bool valid, const int (&nb)[2 * D], R* sU, R* sN,
+                                       R* sA, R* sB, R* sE) {
   using Dm = Dims<D, N1>;
   constexpr int NP = Dm::NP, NS = Dm::NS;
-  int nb[NS];
-#pragma unroll
-  for (int s = 0; s < NS; ++s) nb[s] = -1;
   if (valid) {
     sU[c * NP + i] = (R)x[(size_t)a * NP + i];
 #pragma unroll
-    for (int s = 0; s < NS; ++s) {
-      nb[s] = P.nbr[(size_t)s * P.n_act + a];
-      sN[(c * NS + s) * NP + i] = nb[s] >= 0 ? (R)x[(size_t)nb[s] * NP + i] : R(0);
-    }
+    for (int s = 0; s < NS; ++s) sN[(c * NS + s) * NP + i] = nb[s] >= 0 ? (R)x[(size_t)nb[s] * NP + i] : R(0);
   }
   __syncthreads();
   int ii[3];
@@ -219,7 +222,6 @@ __device__ __forceinline__ R apply_dof(const LevelParams<R>& P, const LevelConst
 template <int D, int N1, typename TI, typename R, int MODE>
 __global__ void __launch_bounds__(256) k_apply(const __grid_constant__ LevelParams<R> P, const TI* __restrict__ x,
                                                const R* __restrict__ f, R* __restrict__ y) {
-  pdl_entry();
   using Dm = Dims<D, N1>;
   constexpr int NP = Dm::NP, NQ = Dm::NQ, NS = Dm::NS, CPB = Dm::CPB;
   __shared__ LevelConsts<R> C;
@@ -230,7 +232,11 @@ __global__ void __launch_bounds__(256) k_apply(const __grid_constant__ LevelPara
   const int c = threadIdx.x / NP, i = threadIdx.x - c * NP;
   const int a = blockIdx.x * CPB + c;
   const bool valid = threadIdx.x < CPB * NP && a < P.n_act;
-  R v = apply_dof<D, N1, TI, R>(P, C, x, c, i, a, valid, sU, sN, sA, sB, sE);
+  int nb[NS];
+  dof_nbr<D, R>(P, a, valid, nb);
+  pdl_wait();
+  pdl_trigger();
+  R v = apply_dof<D, N1, TI, R>(P, C, x, c, i, a, valid, nb, sU, sN, sA, sB, sE);
   if (valid) {
     if (MODE == 1) v = f[(size_t)a * NP + i] - v;
     y[(size_t)a * NP + i] = v;
@@ -244,7 +250,6 @@ __global__ void __launch_bounds__(256) k_resid_restrict_p(const __grid_constant_
                                                           const __grid_constant__ TransferParams<R> T,
                                                           const R* __restrict__ u, const R* __restrict__ f,
                                                           R* __restrict__ rc) {
-  pdl_entry();
   using Dm = Dims<D, N1>;
   constexpr int NP = Dm::NP, NQ = Dm::NQ, NS = Dm::NS, CPB = Dm::CPB;
   constexpr int NPC = D == 2 ? NC * NC : NC * NC * NC;
@@ -258,7 +263,11 @@ __global__ void __launch_bounds__(256) k_resid_restrict_p(const __grid_constant_
   const int c = threadIdx.x / NP, i = threadIdx.x - c * NP;
   const int a = blockIdx.x * CPB + c;
   const bool valid = threadIdx.x < CPB * NP && a < P.n_act;
-  R v = apply_dof<D, N1, R, R>(P, C, u, c, i, a, valid, sU, sN, sA, sB, sE);
+  int nb[NS];
+  dof_nbr<D, R>(P, a, valid, nb);
+  pdl_wait();
+  pdl_trigger();
+  R v = apply_dof<D, N1, R, R>(P, C, u, c, i, a, valid, nb, sU, sN, sA, sB, sE);
   __syncthreads();                                   // sU is reused for the residual
   sU[c * NP + i] = valid ? f[(size_t)a * NP + i] - v : R(0);
   __syncthreads();
@@ -291,7 +300,6 @@ __global__ void __launch_bounds__(256) k_resid_restrict_h(const __grid_constant_
                                                           const __grid_constant__ TransferParams<R> T,
                                                           const R* __restrict__ u, const R* __restrict__ f,
                                                           R* __restrict__ rc) {
-  pdl_entry();
   using Dm = Dims<D, 2>;
   constexpr int NP = Dm::NP, NQ = Dm::NQ, NS = Dm::NS, CPB = Dm::CPB;
   constexpr int NCH = 1 << D, CPC = CPB / NCH;       // children per coarse cell, coarse cells per block
@@ -306,7 +314,11 @@ __global__ void __launch_bounds__(256) k_resid_restrict_h(const __grid_constant_
   const int cc = blockIdx.x * CPC + c / NCH, o = c % NCH;
   const int a = (threadIdx.x < CPB * NP && cc < T.n_act_c) ? T.children[(size_t)o * T.n_act_c + cc] : -1;
   const bool valid = a >= 0;
-  R v = apply_dof<D, 2, R, R>(P, C, u, c, i, a, valid, sU, sN, sA, sB, sE);
+  int nb[NS];
+  dof_nbr<D, R>(P, a, valid, nb);
+  pdl_wait();
+  pdl_trigger();
+  R v = apply_dof<D, 2, R, R>(P, C, u, c, i, a, valid, nb, sU, sN, sA, sB, sE);
   __syncthreads();                                   // sU is reused for the residuals
   sU[c * NP + i] = valid ? f[(size_t)a * NP + i] - v : R(0);
   __syncthreads();
@@ -354,7 +366,6 @@ template <int D, int N1, typename R>
 __global__ void __launch_bounds__(256) k_smooth(const __grid_constant__ LevelParams<R> P,
                                                 const __grid_constant__ SmoothSegs G, int zero_start,
                                                 const R* __restrict__ f, R* __restrict__ u) {
-  pdl_entry();
   using Dm = Dims<D, N1>;
   constexpr int NP = Dm::NP, NS = Dm::NS, CPB = Dm::CPB;
   __shared__ LevelConsts<R> C;
@@ -373,14 +384,17 @@ __global__ void __launch_bounds__(256) k_smooth(const __grid_constant__ LevelPar
   const int a = first + c;
   const bool valid = threadIdx.x < CPB * NP && a < last;
   int nb[NS];
+  dof_nbr<D, R>(P, a, valid, nb);                    // set-up data: read before the wait
+  if (zero_start)
+#pragma unroll
+    for (int s = 0; s < NS; ++s)
+      if ((col ^ (1 << (s >> 1))) > col) nb[s] = -1;   // unvisited colour: zero
+  pdl_wait();
+  pdl_trigger();
   R uold = 0;
   if (valid) {
 #pragma unroll
-    for (int s = 0; s < NS; ++s) {
-      nb[s] = P.nbr[(size_t)s * P.n_act + a];
-      if (zero_start && (col ^ (1 << (s >> 1))) > col) nb[s] = -1;   // unvisited colour: zero
-      sN[(c * NS + s) * NP + i] = nb[s] >= 0 ? u[(size_t)nb[s] * NP + i] : R(0);
-    }
+    for (int s = 0; s < NS; ++s) sN[(c * NS + s) * NP + i] = nb[s] >= 0 ? u[(size_t)nb[s] * NP + i] : R(0);
     if (P.omega != R(1) && !zero_start) uold = u[(size_t)a * NP + i];
   }
   __syncthreads();
@@ -508,16 +522,17 @@ __global__ void __launch_bounds__(256) k_restrict(const __grid_constant__ Transf
 template <int D, int NF, int NC, typename R>
 __global__ void __launch_bounds__(256) k_prolong(const __grid_constant__ TransferParams<R> T,
                                                  const R* __restrict__ ec, R* __restrict__ uf) {
-  pdl_entry();
   constexpr int NPF = D == 2 ? NF * NF : NF * NF * NF;
   constexpr int NPC = D == 2 ? NC * NC : NC * NC * NC;
   const size_t gid = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int a = (int)(gid / NPF), i = (int)(gid % NPF);
+  const int code = T.hmode && a < T.n_act_f ? T.parent_code[a] : 0;   // set-up data: before the wait
+  pdl_wait();
+  pdl_trigger();
   if (a >= T.n_act_f) return;
   int par;
   const R *P0, *P1, *P2;
   if (T.hmode) {
-    const int code = T.parent_code[a];
     if (code < 0) return;
     par = code >> 3;
     P0 = T.Ph[code & 1];

@@ -26,9 +26,14 @@ inline void count_launches(long long n = 1) { g_kernel_launches.fetch_add(n, std
 bool& pdl_enabled();
 
 #ifdef __CUDACC__
+// The two halves of pdl_entry, for kernels that first read data no earlier kernel writes (level
+// tables, transfer maps, geometry: written once at set-up) and so overlap that latency with the
+// end of the kernel before them.  Nothing a previous kernel writes may be read before pdl_wait().
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 __device__ __forceinline__ void pdl_entry() {
-  asm volatile("griddepcontrol.wait;" ::: "memory");
-  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+  pdl_wait();
+  pdl_trigger();
 }
 
 template <typename... KArgs, typename... Args>
