@@ -2,6 +2,7 @@
 #include <cuda_runtime.h>
 
 #include <cmath>
+#include <cstdint>
 #include <cstring>
 #include <memory>
 #include <new>
@@ -479,26 +480,36 @@ void ensure_work(Context& C) {
       auto tp = std::make_unique<TailCta<R>>();
       std::memset(tp.get(), 0, sizeof(TailCta<R>));
       size_t re = 0, ie = 0;                        // R elements, ints
+      // every array starts on a 16-byte boundary, so that bulk copies can stage the tables
+      const size_t ra = 16 / sizeof(R), ia = 4;
+      auto up = [](size_t v, size_t a) { return (v + a - 1) / a * a; };
+      bool aligned = true;
+      auto al16 = [&](const void* p) { aligned = aligned && reinterpret_cast<uintptr_t>(p) % 16 == 0; };
       for (int l = 0; l <= top; ++l) {
         const HostLevel& H = C.lv[l].H;
         tp->P[l] = params<R>(C.lv[l]);
         if (l >= 1) tp->T[l] = tparams<R>(C.lv[l]);
         tp->n_bnd[l] = H.n_bnd;
         tp->zoff[l] = (int)re;
-        re += (size_t)H.n_act * NP;
+        re = up(re + (size_t)H.n_act * NP, ra);
         tp->roff[l] = (int)re;
-        re += (size_t)H.n_act * NP;
+        re = up(re + (size_t)H.n_act * NP, ra);
         tp->boff[l] = (int)re;
-        re += (size_t)H.n_bnd * NP * NP;
+        re = up(re + (size_t)H.n_bnd * NP * NP, ra);
         tp->noff[l] = (int)ie;
-        ie += (size_t)2 * dim * H.n_act;
+        ie = up(ie + (size_t)2 * dim * H.n_act, ia);
+        al16(tp->P[l].nbr);
+        al16(tp->P[l].binvT);
         if (l >= 1) {
           tp->coff[l] = (int)ie;
-          ie += (size_t)ncol * C.lv[l - 1].H.n_act;
+          ie = up(ie + (size_t)ncol * C.lv[l - 1].H.n_act, ia);
           tp->poff[l] = (int)ie;
-          ie += (size_t)H.n_act;
+          ie = up(ie + (size_t)H.n_act, ia);
+          al16(tp->T[l].children);
+          al16(tp->T[l].parent_code);
         }
       }
+      tp->bulk = aligned ? 1 : 0;
       const size_t int_base = (re * sizeof(R) + 15) / 16 * 16;
       const size_t smem = int_base + ie * sizeof(int);
       tp->top = top;
@@ -892,6 +903,8 @@ int solve_impl(Context& C, const double* b, double* x, double tol, int m, int ma
   if (info) *info = loc;
   if (sweep_fault_take() != 0)
     return set_error(SBM_ERR_CUDA, "Gram-Schmidt sweep: staged copies did not complete in bounded time");
+  if (tail_fault_take() != 0)
+    return set_error(SBM_ERR_CUDA, "V-cycle tail: staging copies did not complete in bounded time");
   if (status == SBM_ERR_NAN) return set_error(status, "non-finite value in FGMRES");
   if (status == SBM_ERR_NOT_CONVERGED) return set_error(status, "FGMRES did not reach the tolerance");
   return SBM_OK;

@@ -10,6 +10,8 @@
 #include <cooperative_groups.h>
 #include <cuda_runtime.h>
 
+#include <cstdint>
+
 #include "ops.h"
 
 namespace sbm {
@@ -739,6 +741,10 @@ constexpr int tail_cta_threads() {
   return D == 2 && sizeof(R) == 4 ? 1024 : 512;
 }
 
+// Set when the tail's staging copies did not complete within kAsyncSpin polls (the tail then
+// copied the data itself); tail_fault_take() reads and clears it.
+__device__ int g_tail_fault;
+
 template <int D, typename R>
 __global__ void __launch_bounds__(tail_cta_threads<D, R>(), 1) k_vcycle_tail_cta(const __grid_constant__ TailCta<R> TP,
                                                                         const R* __restrict__ r_top,
@@ -749,21 +755,75 @@ __global__ void __launch_bounds__(tail_cta_threads<D, R>(), 1) k_vcycle_tail_cta
   int* si = reinterpret_cast<int*>(tcta_smem + TP.int_base);
   constexpr int NCOL = 1 << D, NP = CD<D, 2>::NP, NT = tail_cta_threads<D, R>();
   const int top = TP.top, tid = threadIdx.x;
-  // stage the tables and inverses of every level (set-up data, staged while the kernel before
-  // finishes), then, after the wait, the top level's right-hand side
-  for (int l = 0; l <= top; ++l) {
-    const LevelParams<R>& P = TP.P[l];
-    for (int q = tid; q < 2 * D * P.n_act; q += NT) si[TP.noff[l] + q] = P.nbr[q];
-    for (int q = tid; q < TP.n_bnd[l] * NP * NP; q += NT) sm[TP.boff[l] + q] = P.binvT[q];
-    if (l >= 1) {
-      const TransferParams<R>& T = TP.T[l];
-      for (int q = tid; q < NCOL * T.n_act_c; q += NT) si[TP.coff[l] + q] = T.children[q];
-      for (int q = tid; q < T.n_act_f; q += NT) si[TP.poff[l] + q] = T.parent_code[q];
+  // Stage the tables and inverses of every level (set-up data, staged while the kernel before
+  // finishes), then, after the wait, the top level's right-hand side.  With TP.bulk, thread 0
+  // moves the 16-byte multiple part of every array with bulk asynchronous copies (all sources and
+  // slots are 16-byte aligned) and the threads copy the few entries past it; otherwise (or if a
+  // copy does not complete in bounded time) the threads copy everything.
+  __shared__ __align__(8) unsigned long long tbar[2];
+  const int nr = TP.P[top].n_act * NP;
+  const bool rbulk = TP.bulk && reinterpret_cast<uintptr_t>(r_top) % 16 == 0;
+  // visits every staged table: f(dst, src, count, element size)
+  auto tables = [&](auto&& f) {
+    for (int l = 0; l <= top; ++l) {
+      const LevelParams<R>& P = TP.P[l];
+      f(static_cast<void*>(si + TP.noff[l]), static_cast<const void*>(P.nbr), 2 * D * P.n_act, (int)sizeof(int));
+      f(static_cast<void*>(sm + TP.boff[l]), static_cast<const void*>(P.binvT), TP.n_bnd[l] * NP * NP,
+        (int)sizeof(R));
+      if (l >= 1) {
+        const TransferParams<R>& T = TP.T[l];
+        f(static_cast<void*>(si + TP.coff[l]), static_cast<const void*>(T.children), NCOL * T.n_act_c, (int)sizeof(int));
+        f(static_cast<void*>(si + TP.poff[l]), static_cast<const void*>(T.parent_code), T.n_act_f, (int)sizeof(int));
+      }
     }
+  };
+  auto plain = [&](void* dst, const void* src, int n, int es, int from) {   // entries [from, n)
+    if (es == 4)
+      for (int q = from + tid; q < n; q += NT) static_cast<int*>(dst)[q] = static_cast<const int*>(src)[q];
+    else
+      for (int q = from + tid; q < n; q += NT) static_cast<double*>(dst)[q] = static_cast<const double*>(src)[q];
+  };
+  if (TP.bulk) {
+    if (tid == 0) {
+      mbar_init(&tbar[0], 1);
+      mbar_init(&tbar[1], 1);
+      mbar_fence_init();
+      unsigned total = 0;
+      tables([&](void*, const void*, int n, int es) { total += (unsigned)(n * es) & ~15u; });
+      mbar_arrive_tx(&tbar[0], total);
+      tables([&](void* dst, const void* src, int n, int es) {
+        const unsigned b = (unsigned)(n * es) & ~15u;
+        if (b) bulk_load(dst, src, b, &tbar[0]);
+      });
+    }
+    tables([&](void* dst, const void* src, int n, int es) { plain(dst, src, n, es, (int)(((unsigned)(n * es) & ~15u) / es)); });
+    __syncthreads();                                 // barriers initialised before anyone polls them
+  } else {
+    tables([&](void* dst, const void* src, int n, int es) { plain(dst, src, n, es, 0); });
   }
   pdl_wait();
   pdl_trigger();
-  for (int q = tid; q < TP.P[top].n_act * NP; q += NT) sm[TP.roff[top] + q] = r_top[q];
+  if (rbulk) {
+    if (tid == 0) {
+      mbar_arrive_tx(&tbar[1], (unsigned)(nr * sizeof(R)));
+      bulk_load(sm + TP.roff[top], r_top, (unsigned)(nr * sizeof(R)), &tbar[1]);
+    }
+  } else {
+    for (int q = tid; q < nr; q += NT) sm[TP.roff[top] + q] = r_top[q];
+  }
+  if (TP.bulk) {
+    const bool ok = mbar_wait(&tbar[0], 0) && (!rbulk || mbar_wait(&tbar[1], 0));
+    if (!__syncthreads_and(ok)) {                    // record, let the copies land, copy by hand
+      if (tid == 0) {
+        atomicExch(&g_tail_fault, 1);
+        mbar_wait(&tbar[0], 0);
+        if (rbulk) mbar_wait(&tbar[1], 0);
+      }
+      __syncthreads();
+      tables([&](void* dst, const void* src, int n, int es) { plain(dst, src, n, es, 0); });
+      for (int q = tid; q < nr; q += NT) sm[TP.roff[top] + q] = r_top[q];
+    }
+  }
   __syncthreads();
 
   auto nbr_of = [&](int l, int a, int (&nb)[2 * D]) {
@@ -1091,6 +1151,16 @@ bool tail_cta_fits(int dim, int prec, size_t smem, size_t param_bytes) {
                                  : tail_cta_fits_kernel(k_vcycle_tail_cta<2, float>, smem);
   return prec == 0 ? tail_cta_fits_kernel(k_vcycle_tail_cta<3, double>, smem)
                    : tail_cta_fits_kernel(k_vcycle_tail_cta<3, float>, smem);
+}
+
+int tail_fault_take() {
+  int f = 0;
+  if (cudaMemcpyFromSymbol(&f, g_tail_fault, sizeof(int)) != cudaSuccess) return -1;
+  if (f) {
+    const int zero = 0;
+    if (cudaMemcpyToSymbol(g_tail_fault, &zero, sizeof(int)) != cudaSuccess) return -1;
+  }
+  return f;
 }
 
 template <typename R>

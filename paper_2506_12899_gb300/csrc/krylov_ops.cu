@@ -269,9 +269,8 @@ __device__ __forceinline__ void block_partials_df(float (&s)[NV], float (&c)[NV]
 // entry is never used in the arithmetic).
 constexpr int kSweepThreads = 256;
 constexpr int kSweepBudget = 216 * 1024;           // shared memory of the stages, bytes
-constexpr unsigned kSweepSpin = 1u << 22;          // polls of one mbarrier phase before giving up
 
-// Set by a sweep whose staged copies did not complete within kSweepSpin polls; the solve reads and
+// Set by a sweep whose staged copies did not complete within kAsyncSpin polls; the solve reads and
 // clears it (sweep_fault_take) and reports SBM_ERR_CUDA.
 __device__ int g_sweep_fault;
 
@@ -284,46 +283,6 @@ struct SweepShape {
   static constexpr size_t smem = (size_t)S * SLOT * E * sizeof(float2) + (size_t)S * sizeof(unsigned long long);
   static_assert(S >= 2, "two stages must fit");
 };
-
-__device__ __forceinline__ unsigned smem_addr(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
-}
-
-// One arrival that also announces `bytes` of asynchronous copies on the barrier's current phase.
-__device__ __forceinline__ void mbar_arrive_tx(unsigned long long* bar, unsigned bytes) {
-  asm volatile(
-      "{\n\t.reg .b64 st;\n\t"
-      "mbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n\t}" ::"r"(smem_addr(bar)),
-      "r"(bytes)
-      : "memory");
-}
-
-// Bulk copy of `bytes` (a multiple of 16) from global to this CTA's shared memory.
-__device__ __forceinline__ void bulk_load(void* dst, const void* src, unsigned bytes, unsigned long long* bar) {
-  asm volatile(
-      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-          smem_addr(dst)),
-      "l"(src), "r"(bytes), "r"(smem_addr(bar))
-      : "memory");
-}
-
-// Waits for the phase of parity `parity` to complete; false after kSweepSpin unsuccessful polls.
-__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned parity) {
-  for (unsigned it = 0; it < kSweepSpin; ++it) {
-    unsigned done;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(done)
-        : "r"(smem_addr(bar)), "r"(parity)
-        : "memory");
-    if (done) return true;
-  }
-  return false;
-}
 
 // MODE 0: partial[block][k] = V_k . w, k < NV.  w is FP64 (TW = double; it is also written to
 //         wdf as double-float for the next sweeps) or double-float (TW = float2).
@@ -343,7 +302,7 @@ __global__ void __launch_bounds__(kSweepThreads) k_gs_sweep(const float2* __rest
   const int tid = threadIdx.x;
   if (tid == 0) {
     for (int q = 0; q < S; ++q) mbar_init(&bar[q], 1);
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    mbar_fence_init();
   }
   pdl_entry();                                       // h and w come from the kernels before
   if (MODE != 0 && tid < NV) hs[tid] = df_from_double(h[tid]);

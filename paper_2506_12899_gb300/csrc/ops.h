@@ -36,6 +36,55 @@ __device__ __forceinline__ void pdl_entry() {
   pdl_trigger();
 }
 
+// Bulk asynchronous copies into shared memory (cp.async.bulk), completion counted in bytes on an
+// mbarrier.  Every wait is bounded: mbar_wait gives up after kAsyncSpin polls and returns false,
+// and the caller records the failure in a flag the host reads.
+constexpr unsigned kAsyncSpin = 1u << 22;
+
+__device__ __forceinline__ unsigned smem_addr(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+
+// Makes initialised mbarriers visible to the asynchronous proxy; call before the CTA syncs.
+__device__ __forceinline__ void mbar_fence_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+
+// One arrival that also announces `bytes` of asynchronous copies on the barrier's current phase.
+__device__ __forceinline__ void mbar_arrive_tx(unsigned long long* bar, unsigned bytes) {
+  asm volatile(
+      "{\n\t.reg .b64 st;\n\t"
+      "mbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n\t}" ::"r"(smem_addr(bar)),
+      "r"(bytes)
+      : "memory");
+}
+
+// Bulk copy of `bytes` (a multiple of 16; both addresses 16-byte aligned) from global memory to
+// this CTA's shared memory.
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, unsigned bytes, unsigned long long* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_addr(dst)),
+      "l"(src), "r"(bytes), "r"(smem_addr(bar))
+      : "memory");
+}
+
+// Waits for the phase of parity `parity` to complete; false after kAsyncSpin unsuccessful polls.
+__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned parity) {
+  for (unsigned it = 0; it < kAsyncSpin; ++it) {
+    unsigned done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(done)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+
 template <typename... KArgs, typename... Args>
 cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
                        Args... args) {
@@ -222,6 +271,9 @@ cudaError_t launch_df_to(const float2* v, TO* y, size_t N, cudaStream_t s);
 cudaError_t launch_hess_column(const double* h1, const double* h2, const double* hn, int k, double* col,
                                cudaStream_t s);
 int sweep_fault_take();
+// 1 if a one-CTA tail's staging copies timed out since the last call (the tail then copied the data
+// itself, so results stay valid), and clears the flag; -1 if it cannot be read.
+int tail_fault_take();
 
 // ---------------------------------------------------------------- learned boundary-cell correction
 template <typename TI>

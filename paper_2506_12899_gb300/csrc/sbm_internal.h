@@ -159,6 +159,8 @@ struct TailCta {
   int noff[kMaxTailCta], coff[kMaxTailCta], poff[kMaxTailCta];   // nbr, children, parent codes
   int n_bnd[kMaxTailCta];
   unsigned int_base;               // byte offset of the int area
+  int bulk;                        // 1: tables staged by bulk asynchronous copies (every table and
+                                   // its shared-memory slot 16-byte aligned), 0: by plain loads
   LevelParams<R> P[kMaxTailCta];
   TransferParams<R> T[kMaxTailCta];
 };
