@@ -42,6 +42,8 @@ struct DevLevel {
   int* parent_code = nullptr;
   int* children = nullptr;
   double* coarse_inv = nullptr;
+  double* coarse_invT = nullptr;     // its transpose (the one-CTA tail reads it a row per thread)
+  dfl* coarse_invT_df = nullptr;     // the transpose rounded to double-float (FP32 tail)
   LevelParams<double> P64{};
   LevelParams<float> P32{};
   LevelParams<dfl> Pdf{};         // double-float operator constants (finest level, thread-per-cell shapes)
@@ -411,7 +413,17 @@ Context* build_context(const sbm_setup_desc& d, bool device) {
     L.binv32 = C->upload(to_f32(L.H.binvT));
     if (!L.H.parent_code.empty()) L.parent_code = C->upload(L.H.parent_code);
     if (!L.H.children.empty()) L.children = C->upload(L.H.children);
-    if (!L.H.coarse_inv.empty()) L.coarse_inv = C->upload(L.H.coarse_inv);
+    if (!L.H.coarse_inv.empty()) {
+      L.coarse_inv = C->upload(L.H.coarse_inv);
+      const size_t n = L.H.n_dof();
+      std::vector<double> t(n * n);
+      for (size_t i = 0; i < n; ++i)
+        for (size_t j = 0; j < n; ++j) t[j * n + i] = L.H.coarse_inv[i * n + j];
+      L.coarse_invT = C->upload(t);
+      std::vector<dfl> tdf(t.size());
+      for (size_t i = 0; i < t.size(); ++i) tdf[i] = dfl(t[i]);
+      L.coarse_invT_df = C->upload(tdf);
+    }
     L.P64 = make_params<double>(L, L.dhat64, L.binv64);
     L.P32 = make_params<float>(L, L.dhat32, L.binv32);
     if (&L == &C->lv.back()) {                     // Arnoldi operator in double-float
@@ -511,7 +523,18 @@ void ensure_work(Context& C) {
       }
       tp->bulk = aligned ? 1 : 0;
       const size_t int_base = (re * sizeof(R) + 15) / 16 * 16;
-      const size_t smem = int_base + ie * sizeof(int);
+      size_t smem = int_base + ie * sizeof(int);
+      // the coarse inverse (FP64, n0 x n0) joins the staged data when it fits
+      const size_t n0 = (size_t)C.lv[0].H.n_act * NP;
+      const size_t cinv_off = up(smem, 16), smem_c = cinv_off + n0 * n0 * sizeof(double);
+      tp->cinv_off = 0;
+      const void* cinvT = sizeof(R) == 4 ? static_cast<const void*>(C.lv[0].coarse_invT_df)
+                                         : static_cast<const void*>(C.lv[0].coarse_invT);
+      if (cinvT && reinterpret_cast<uintptr_t>(cinvT) % 16 == 0 &&
+          tail_cta_fits(dim, pi, smem_c, sizeof(TailCta<R>))) {
+        tp->cinv_off = (unsigned)cinv_off;
+        smem = smem_c;
+      }
       tp->top = top;
       tp->pre = C.desc.pre_smooth;
       tp->post = C.desc.post_smooth;
@@ -623,7 +646,9 @@ void vcycle_rec(Context& C, int l, const R* r, R* z, cudaStream_t s) {
       const TailCta<R>* tp;
       if constexpr (sizeof(R) == 8) tp = C.tail_cta64.get();
       else tp = C.tail_cta32.get();
-      CUDA_TRY(launch_vcycle_tail_cta<R>(L.H.dim, *tp, r, z, C.lv[0].coarse_inv, C.tail_plan[pi].smem_bytes, s));
+      const void* cinvT = sizeof(R) == 4 ? static_cast<const void*>(C.lv[0].coarse_invT_df)
+                                         : static_cast<const void*>(C.lv[0].coarse_invT);
+      CUDA_TRY(launch_vcycle_tail_cta<R>(L.H.dim, *tp, r, z, C.lv[0].coarse_inv, cinvT, C.tail_plan[pi].smem_bytes, s));
     } else {
       CUDA_TRY(launch_vcycle_tail<R>(L.H.dim, static_cast<const TailLevel<R>*>(C.tail[pi]), l, r, z,
                                      C.lv[0].coarse_inv, C.desc.pre_smooth, C.desc.post_smooth, C.desc.ssor_each,

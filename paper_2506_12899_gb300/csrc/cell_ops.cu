@@ -749,7 +749,8 @@ template <int D, typename R>
 __global__ void __launch_bounds__(tail_cta_threads<D, R>(), 1) k_vcycle_tail_cta(const __grid_constant__ TailCta<R> TP,
                                                                         const R* __restrict__ r_top,
                                                                         R* __restrict__ z_top,
-                                                                        const double* __restrict__ coarse_inv) {
+                                                                        const double* __restrict__ coarse_inv,
+                                                                        const void* __restrict__ coarse_invT) {
   extern __shared__ __align__(16) unsigned char tcta_smem[];
   R* sm = reinterpret_cast<R*>(tcta_smem);
   int* si = reinterpret_cast<int*>(tcta_smem + TP.int_base);
@@ -775,6 +776,10 @@ __global__ void __launch_bounds__(tail_cta_threads<D, R>(), 1) k_vcycle_tail_cta
         f(static_cast<void*>(si + TP.coff[l]), static_cast<const void*>(T.children), NCOL * T.n_act_c, (int)sizeof(int));
         f(static_cast<void*>(si + TP.poff[l]), static_cast<const void*>(T.parent_code), T.n_act_f, (int)sizeof(int));
       }
+    }
+    if (TP.cinv_off) {
+      const int n0 = TP.P[0].n_act * NP;
+      f(static_cast<void*>(tcta_smem + TP.cinv_off), coarse_invT, n0 * n0, 8);
     }
   };
   auto plain = [&](void* dst, const void* src, int n, int es, int from) {   // entries [from, n)
@@ -902,14 +907,16 @@ __global__ void __launch_bounds__(tail_cta_threads<D, R>(), 1) k_vcycle_tail_cta
     const R* z = sm + TP.zoff[l];
     const R* f = sm + TP.roff[l];
     R* rc = sm + TP.roff[l - 1];
-    for (int cc = tid; cc < T.n_act_c; cc += NT) {
+    // one thread per child: group of NCOL adjacent lanes per coarse cell (lane o: child o), the
+    // child's residual restricted in registers, then a fixed butterfly sum over the group (every
+    // lane of a warp takes part: the pass count is the same for the whole block)
+    for (int base = 0; base < T.n_act_c * NCOL; base += NT) {
+      const int t = base + tid, cc = t / NCOL, o = t % NCOL;
+      const int a = cc < T.n_act_c ? si[TP.coff[l] + o * T.n_act_c + cc] : -1;
       R out[NP];
 #pragma unroll
       for (int j = 0; j < NP; ++j) out[j] = 0;
-#pragma unroll 1
-      for (int o = 0; o < NCOL; ++o) {
-        const int a = si[TP.coff[l] + o * T.n_act_c + cc];
-        if (a < 0) continue;
+      if (a >= 0) {
         int ca = 0;
 #pragma unroll
         for (int q = 1; q < NCOL; ++q)
@@ -932,10 +939,14 @@ __global__ void __launch_bounds__(tail_cta_threads<D, R>(), 1) k_vcycle_tail_cta
           R acc = 0;
 #pragma unroll
           for (int i = 0; i < NP; ++i) acc += h_weight<D, R>(T, o, i, j) * y[i];
-          out[j] += acc;
+          out[j] = acc;
         }
       }
-      store_np_vec<NP, R>(rc + cc * NP, out);
+#pragma unroll
+      for (int sh = 1; sh < NCOL; sh <<= 1)
+#pragma unroll
+        for (int j = 0; j < NP; ++j) out[j] += __shfl_xor_sync(0xffffffffu, out[j], sh);
+      if (o == 0 && cc < T.n_act_c) store_np_vec<NP, R>(rc + cc * NP, out);
     }
     __syncthreads();
   }
@@ -943,13 +954,43 @@ __global__ void __launch_bounds__(tail_cta_threads<D, R>(), 1) k_vcycle_tail_cta
     const int n0 = TP.P[0].n_act * NP;
     const R* r0 = sm + TP.roff[0];
     R* z0 = sm + TP.zoff[0];
-    const int lane = tid & 31;
-    for (int row = tid >> 5; row < n0; row += NT / 32) {
-      double acc = 0;
-      for (int c = lane; c < n0; c += 32) acc += coarse_inv[(size_t)row * n0 + c] * (double)r0[c];
+    if (TP.cinv_off) {
+      // the transpose staged in shared memory, one thread per row, four accumulation chains;
+      // consecutive threads read consecutive entries and r0[c] is a broadcast.  FP32 tail: the
+      // inverse is stored as double-float and every product is exact (two_prod) and summed in
+      // double-float on the FP32 pipes (about 48 bits; the input and the result are FP32), since
+      // one SM's FP64 pipe made this the tail's longest phase.  FP64 tail: FP64 throughout.
+      for (int row = tid; row < n0; row += NT) {
+        if constexpr (sizeof(R) == 4) {
+          const dfl* aT = reinterpret_cast<const dfl*>(tcta_smem + TP.cinv_off);
+          dfl acc[4] = {dfl(0.f), dfl(0.f), dfl(0.f), dfl(0.f)};
+          int c = 0;
+          for (; c + 4 <= n0; c += 4)
 #pragma unroll
-      for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
-      if (lane == 0) z0[row] = (R)acc;
+            for (int k = 0; k < 4; ++k) acc[k] += aT[(size_t)(c + k) * n0 + row] * dfl((float)r0[c + k]);
+          for (; c < n0; ++c) acc[0] += aT[(size_t)c * n0 + row] * dfl((float)r0[c]);
+          const dfl sum = (acc[0] + acc[1]) + (acc[2] + acc[3]);
+          z0[row] = (R)__fadd_rn(sum.hi, sum.lo);
+        } else {
+          const double* aT = reinterpret_cast<const double*>(tcta_smem + TP.cinv_off);
+          double acc[4] = {0.0, 0.0, 0.0, 0.0};
+          int c = 0;
+          for (; c + 4 <= n0; c += 4)
+#pragma unroll
+            for (int k = 0; k < 4; ++k) acc[k] += aT[(size_t)(c + k) * n0 + row] * (double)r0[c + k];
+          for (; c < n0; ++c) acc[0] += aT[(size_t)c * n0 + row] * (double)r0[c];
+          z0[row] = (R)((acc[0] + acc[1]) + (acc[2] + acc[3]));
+        }
+      }
+    } else {                                       // from global memory, one warp per row
+      const int lane = tid & 31;
+      for (int row = tid >> 5; row < n0; row += NT / 32) {
+        double acc = 0;
+        for (int c = lane; c < n0; c += 32) acc += coarse_inv[(size_t)row * n0 + c] * (double)r0[c];
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+        if (lane == 0) z0[row] = (R)acc;
+      }
     }
     __syncthreads();
   }
@@ -1165,16 +1206,18 @@ int tail_fault_take() {
 
 template <typename R>
 cudaError_t launch_vcycle_tail_cta(int dim, const TailCta<R>& TP, const R* r, R* z, const double* coarse_inv,
-                                   size_t smem, cudaStream_t s) {
-  if (dim == 2) SBM_PDL((k_vcycle_tail_cta<2, R>), 1, (tail_cta_threads<2, R>()), smem, s, TP, r, z, coarse_inv);
-  else SBM_PDL((k_vcycle_tail_cta<3, R>), 1, (tail_cta_threads<3, R>()), smem, s, TP, r, z, coarse_inv);
+                                   const void* coarse_invT, size_t smem, cudaStream_t s) {
+  if (dim == 2)
+    SBM_PDL((k_vcycle_tail_cta<2, R>), 1, (tail_cta_threads<2, R>()), smem, s, TP, r, z, coarse_inv, coarse_invT);
+  else
+    SBM_PDL((k_vcycle_tail_cta<3, R>), 1, (tail_cta_threads<3, R>()), smem, s, TP, r, z, coarse_inv, coarse_invT);
   count_launches();
   return cudaGetLastError();
 }
 template cudaError_t launch_vcycle_tail_cta<double>(int, const TailCta<double>&, const double*, double*,
-                                                    const double*, size_t, cudaStream_t);
+                                                    const double*, const void*, size_t, cudaStream_t);
 template cudaError_t launch_vcycle_tail_cta<float>(int, const TailCta<float>&, const float*, float*, const double*,
-                                                   size_t, cudaStream_t);
+                                                   const void*, size_t, cudaStream_t);
 
 template cudaError_t launch_vcycle_tail<double>(int, const TailLevel<double>*, int, const double*, double*,
                                                 const double*, int, int, int, const TailPlan&, cudaStream_t);

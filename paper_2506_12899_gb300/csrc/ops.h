@@ -182,11 +182,12 @@ cudaError_t launch_vcycle_tail(int dim, const TailLevel<R>* TL, int top, const R
 // `smem` bytes each can be resident (prec 0: FP64, 1: FP32).
 size_t tail_smem_limit();
 // The one-CTA tail (TailCta): whether `smem` bytes fit (sets the kernel's shared-memory limit),
-// and the launch.
+// and the launch.  coarse_inv: the FP64 coarse inverse, row-major; coarse_invT: its transpose,
+// FP64 for R = double and double-float (dfl) for R = float, staged when TP.cinv_off != 0.
 bool tail_cta_fits(int dim, int prec, size_t smem, size_t param_bytes);
 template <typename R>
 cudaError_t launch_vcycle_tail_cta(int dim, const TailCta<R>& TP, const R* r, R* z, const double* coarse_inv,
-                                   size_t smem, cudaStream_t s);
+                                   const void* coarse_invT, size_t smem, cudaStream_t s);
 bool tail_cluster_fits(int dim, int prec, int size, size_t smem);
 
 // y = A x (mode 0) or y = f - A x (mode 1) on one level; TI is the input precision, R the

@@ -161,6 +161,7 @@ struct TailCta {
   unsigned int_base;               // byte offset of the int area
   int bulk;                        // 1: tables staged by bulk asynchronous copies (every table and
                                    // its shared-memory slot 16-byte aligned), 0: by plain loads
+  unsigned cinv_off;               // byte offset of the staged FP64 coarse inverse, 0: read from global
   LevelParams<R> P[kMaxTailCta];
   TransferParams<R> T[kMaxTailCta];
 };
