@@ -300,28 +300,48 @@ __global__ void __launch_bounds__(kSweepThreads) k_gs_sweep(const float2* __rest
   unsigned long long* bar = reinterpret_cast<unsigned long long*>(sweep_smem + (size_t)S * SLOT * E * sizeof(float2));
   __shared__ float2 hs[kMaxVec];
   const int tid = threadIdx.x;
-  if (tid == 0) {
-    for (int q = 0; q < S; ++q) mbar_init(&bar[q], 1);
-    mbar_fence_init();
-  }
-  pdl_entry();                                       // h and w come from the kernels before
-  if (MODE != 0 && tid < NV) hs[tid] = df_from_double(h[tid]);
-  __syncthreads();
   const size_t nchunk = (N + E - 1) / E;
   const size_t mine = nchunk > blockIdx.x ? (nchunk - 1 - blockIdx.x) / gridDim.x + 1 : 0;
-  auto issue = [&](size_t q) {                       // local chunk q into stage q % S
-    const size_t e0 = (blockIdx.x + q * gridDim.x) * (size_t)E;
+  auto chunk = [&](size_t q, size_t& e0, unsigned& bytes) {   // local chunk q: first entry, bytes per row
+    e0 = (blockIdx.x + q * gridDim.x) * (size_t)E;
     const size_t n = N - e0 < (size_t)E ? N - e0 : (size_t)E;
-    const unsigned bytes = (unsigned)(((n + 1) & ~(size_t)1) * sizeof(float2));
+    bytes = (unsigned)(((n + 1) & ~(size_t)1) * sizeof(float2));
+  };
+  auto issue_v = [&](size_t q) {                     // arm stage q % S for all rows, copy the V rows
+    size_t e0;
+    unsigned bytes;
+    chunk(q, e0, bytes);
     float2* dst = stage + (size_t)(q % S) * SLOT * E;
     unsigned long long* b = &bar[q % S];
     mbar_arrive_tx(b, bytes * SLOT);
 #pragma unroll 1
     for (int k = 0; k < NV; ++k) bulk_load(dst + (size_t)k * E, V + (size_t)k * ldv + e0, bytes, b);
-    bulk_load(dst + (size_t)NV * E, reinterpret_cast<const unsigned char*>(w_in) + e0 * sizeof(float2), bytes, b);
   };
-  if (tid == 0)
-    for (size_t q = 0; q < (size_t)S && q < mine; ++q) issue(q);
+  auto issue_w = [&](size_t q) {
+    size_t e0;
+    unsigned bytes;
+    chunk(q, e0, bytes);
+    bulk_load(stage + (size_t)(q % S) * SLOT * E + (size_t)NV * E,
+              reinterpret_cast<const unsigned char*>(w_in) + e0 * sizeof(float2), bytes, &bar[q % S]);
+  };
+  // The first S chunks are copied before the dependency wait where that is safe: the V rows, and
+  // w for the update sweeps, were written at least two launches back, and this grid starts only
+  // after the kernel before it has passed its own griddepcontrol.wait, i.e. after everything
+  // before that kernel has completed and become visible.  h, and w of the dot sweep (the operator
+  // writes it just before), are read after the wait.
+  if (tid == 0) {
+    for (int q = 0; q < S; ++q) mbar_init(&bar[q], 1);
+    mbar_fence_init();
+    for (size_t q = 0; q < (size_t)S && q < mine; ++q) {
+      issue_v(q);
+      if (MODE != 0) issue_w(q);
+    }
+  }
+  pdl_entry();
+  if (tid == 0 && MODE == 0)
+    for (size_t q = 0; q < (size_t)S && q < mine; ++q) issue_w(q);
+  if (MODE != 0 && tid < NV) hs[tid] = df_from_double(h[tid]);
+  __syncthreads();
   float s[NA], c[NA];
 #pragma unroll
   for (int k = 0; k < NA; ++k) s[k] = c[k] = 0.f;
@@ -365,7 +385,10 @@ __global__ void __launch_bounds__(kSweepThreads) k_gs_sweep(const float2* __rest
       }
       break;
     }
-    if (tid == 0 && q + S < mine) issue(q + S);
+    if (tid == 0 && q + S < mine) {
+      issue_v(q + S);
+      issue_w(q + S);
+    }
   }
   block_partials_df<NA>(s, c, partial);
 }
