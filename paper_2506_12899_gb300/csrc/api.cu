@@ -658,24 +658,28 @@ void vcycle_rec(Context& C, int l, const R* r, R* z, cudaStream_t s) {
   }
   const int dim = L.H.dim;
   const LevelParams<R>& P = params<R>(L);
+  // `early` (the last launcher argument): r, resp. the fine z, was written two or more launches
+  // before, so the kernels read it before their dependency wait.  Only the first pre-smoothing
+  // sweep may follow r's writer directly (the restriction from the level above); the residual
+  // comes after the pre-smoothing sweeps or the memset of z, the prolongation after the residual.
   if (C.desc.pre_smooth == 0) CUDA_TRY(cudaMemsetAsync(z, 0, (size_t)L.H.n_dof() * sizeof(R), s));
   for (int k = 0; k < C.desc.pre_smooth; ++k) {
-    CUDA_TRY(launch_smooth<R>(dim, L.H.p, P, 0, k == 0, r, z, s));
-    if (C.desc.ssor_each) CUDA_TRY(launch_smooth<R>(dim, L.H.p, P, 1, 0, r, z, s));
+    CUDA_TRY(launch_smooth<R>(dim, L.H.p, P, 0, k == 0, r, z, s, k > 0));
+    if (C.desc.ssor_each) CUDA_TRY(launch_smooth<R>(dim, L.H.p, P, 1, 0, r, z, s, 1));
   }
   DevLevel& Lc = C.lv[l - 1];
   R* rc = static_cast<R*>(Lc.rhs[pi]);
   R* zc = static_cast<R*>(Lc.z[pi]);
   if (Lc.H.n == L.H.n) {                          // p-transfer: residual restricted in the same kernel
-    CUDA_TRY(launch_resid_restrict_p<R>(dim, L.H.p, P, tparams<R>(L), z, r, rc, s));
+    CUDA_TRY(launch_resid_restrict_p<R>(dim, L.H.p, P, tparams<R>(L), z, r, rc, s, 1));
   } else {                                        // h-transfer: coarse cells gather their children
-    CUDA_TRY(launch_resid_restrict_h<R>(dim, P, tparams<R>(L), z, r, rc, s));
+    CUDA_TRY(launch_resid_restrict_h<R>(dim, P, tparams<R>(L), z, r, rc, s, 1));
   }
   vcycle_rec<R>(C, l - 1, rc, zc, s);
-  CUDA_TRY(launch_prolong<R>(dim, L.H.p, Lc.H.p, tparams<R>(L), zc, z, s));
+  CUDA_TRY(launch_prolong<R>(dim, L.H.p, Lc.H.p, tparams<R>(L), zc, z, s, 1));
   for (int k = 0; k < C.desc.post_smooth; ++k) {
-    if (C.desc.ssor_each) CUDA_TRY(launch_smooth<R>(dim, L.H.p, P, 0, 0, r, z, s));
-    CUDA_TRY(launch_smooth<R>(dim, L.H.p, P, 1, 0, r, z, s));
+    if (C.desc.ssor_each) CUDA_TRY(launch_smooth<R>(dim, L.H.p, P, 0, 0, r, z, s, 1));
+    CUDA_TRY(launch_smooth<R>(dim, L.H.p, P, 1, 0, r, z, s, 1));
   }
   if (C.mlp_on && l == C.finest()) apply_learned<R>(C, L, r, z, s);
 }

@@ -380,10 +380,11 @@ __device__ __forceinline__ void block_solve_at(const LevelParams<R>& P, const R*
 
 // One cell of one colour of the block Gauss-Seidel sweep (Eq. 16): cell a of the colour
 // starting at cs whose first nbnd cells are boundary cells (dense inverse, boundary index
-// b0 + a - cs); the others use the fast diagonalisation.  zero_start as in k_smooth.
+// b0 + a - cs); the others use the fast diagonalisation.  t: f of the cell on entry (overwritten).
+// zero_start as in k_smooth.
 template <int D, int N1, typename R>
 __device__ __forceinline__ void smooth_one(const LevelParams<R>& P, int col, int zero_start, int cs, int nbnd,
-                                           int b0, int a, const int (&nb)[2 * D], const R* __restrict__ f,
+                                           int b0, int a, const int (&nb)[2 * D], R (&t)[CD<D, N1>::NP],
                                            R* __restrict__ u) {
   constexpr int NP = CD<D, N1>::NP;
   const bool isB = a - cs < nbnd;
@@ -391,8 +392,6 @@ __device__ __forceinline__ void smooth_one(const LevelParams<R>& P, int col, int
 #pragma unroll
   for (int i = 0; i < NP; ++i) c[i] = 0;
   add_couplings<D, N1, R, R>(P, u, col, zero_start != 0, nb, c);
-  R t[NP];
-  load_cell<D, N1, R, R>(f, a, t);
 #pragma unroll
   for (int i = 0; i < NP; ++i) t[i] -= P.hscale * c[i];
   R y[NP];
@@ -413,18 +412,24 @@ __device__ __forceinline__ void smooth_one(const LevelParams<R>& P, int col, int
 template <int D, int N1, typename R>
 __global__ void __launch_bounds__(kCellThreads) k_smooth_cell(const __grid_constant__ LevelParams<R> P,
                                                               const __grid_constant__ SmoothSegs G, int zero_start,
-                                                              const R* __restrict__ f, R* __restrict__ u) {
+                                                              const R* __restrict__ f, R* __restrict__ u, int early) {
+  constexpr int NP = CD<D, N1>::NP;
   int sg = 0;
 #pragma unroll
   for (int k = 1; k < SmoothSegs::kMax; ++k)
     if (k < G.n && (int)blockIdx.x >= G.blk[k]) sg = k;
   const int a = G.first[sg] + ((int)blockIdx.x - G.blk[sg]) * (int)blockDim.x + (int)threadIdx.x;
   int nb[2 * D];
-  if (a < G.last[sg]) load_nbr<D, R>(P, a, nb);     // set-up data: read before the wait
+  R t[NP];
+  if (a < G.last[sg]) {
+    load_nbr<D, R>(P, a, nb);                        // set-up data: read before the wait
+    if (early) load_cell<D, N1, R, R>(f, a, t);      // f written two or more launches back
+  }
   pdl_wait();
   pdl_trigger();
   if (a >= G.last[sg]) return;
-  smooth_one<D, N1, R>(P, G.col[sg], zero_start, G.cs[sg], G.nbnd[sg], G.b0[sg], a, nb, f, u);
+  if (!early) load_cell<D, N1, R, R>(f, a, t);
+  smooth_one<D, N1, R>(P, G.col[sg], zero_start, G.cs[sg], G.nbnd[sg], G.b0[sg], a, nb, t, u);
 }
 
 // Residual and p-restriction fused, one thread per cell (Eqs. 11, 18).
@@ -432,19 +437,25 @@ template <int D, int N1, int NC, typename R>
 __global__ void __launch_bounds__(kCellThreads) k_resid_restrict_p_cell(const __grid_constant__ LevelParams<R> P,
                                                                         const __grid_constant__ TransferParams<R> T,
                                                                         const R* __restrict__ u,
-                                                                        const R* __restrict__ f, R* __restrict__ rc) {
+                                                                        const R* __restrict__ f, R* __restrict__ rc,
+                                                                        int early) {
   constexpr int NP = CD<D, N1>::NP;
   constexpr int NPC = D == 2 ? NC * NC : NC * NC * NC;
   const int a = blockIdx.x * blockDim.x + threadIdx.x;
   int nb[2 * D];
-  if (a < P.n_act) load_nbr<D, R>(P, a, nb);       // set-up data: read before the wait
+  R fa[NP];
+  if (a < P.n_act) {
+    load_nbr<D, R>(P, a, nb);                        // set-up data: read before the wait
+    if (early) load_cell<D, N1, R, R>(f, a, fa);     // f written two or more launches back
+  }
   pdl_wait();
   pdl_trigger();
   if (a >= P.n_act) return;
+  if (!early) load_cell<D, N1, R, R>(f, a, fa);
   R r[NP];
   cell_apply<D, N1, R, R>(P, u, a, nb, r);
 #pragma unroll
-  for (int i = 0; i < NP; ++i) r[i] = f[(size_t)a * NP + i] - r[i];
+  for (int i = 0; i < NP; ++i) r[i] = fa[i] - r[i];
 #pragma unroll
   for (int j = 0; j < NPC; ++j) {
     const int j0 = j % NC, j1 = (j / NC) % NC, j2 = D == 3 ? j / (NC * NC) : 0;
@@ -475,7 +486,8 @@ template <int D, typename R>
 __global__ void __launch_bounds__(kCellThreads) k_resid_restrict_h_cell(const __grid_constant__ LevelParams<R> P,
                                                                         const __grid_constant__ TransferParams<R> T,
                                                                         const R* __restrict__ u,
-                                                                        const R* __restrict__ f, R* __restrict__ rc) {
+                                                                        const R* __restrict__ f, R* __restrict__ rc,
+                                                                        int early) {
   constexpr int NCOL = 1 << D, NP = CD<D, 2>::NP;
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   const int cc = t / NCOL, o = t % NCOL;
@@ -485,13 +497,17 @@ __global__ void __launch_bounds__(kCellThreads) k_resid_restrict_h_cell(const __
   // the child and its neighbours are set-up data: read before the wait
   const int a = cc < T.n_act_c ? T.children[(size_t)o * T.n_act_c + cc] : -1;
   int nb[2 * D];
-  if (a >= 0) load_nbr<D, R>(P, a, nb);
+  R fa[NP];
+  if (a >= 0) {
+    load_nbr<D, R>(P, a, nb);
+    if (early) load_cell<D, 2, R, R>(f, a, fa);      // f written two or more launches back
+  }
   pdl_wait();
   pdl_trigger();
   if (a >= 0) {
-    R r[NP], fa[NP];
+    R r[NP];
+    if (!early) load_cell<D, 2, R, R>(f, a, fa);
     cell_apply<D, 2, R, R>(P, u, a, nb, r);
-    load_cell<D, 2, R, R>(f, a, fa);
 #pragma unroll
     for (int i = 0; i < NP; ++i) r[i] = fa[i] - r[i];
 #pragma unroll
@@ -1064,28 +1080,31 @@ cudaError_t launch_apply_cell(int dim, int p, const LevelParams<R>& P, const TI*
 
 template <typename R>
 cudaError_t launch_smooth_cell(int dim, int p, const LevelParams<R>& P, int reverse, int zero_start, const R* f,
-                               R* u, cudaStream_t s) {
+                               R* u, cudaStream_t s, int early) {
   if (reverse) zero_start = 0;
+  int launched = 0;
   for (int q = 0; q <= dim; ++q) {   // (the launcher in level_ops.cu chose this path for the level)
     const int g = reverse ? dim - q : q;
     const unsigned bs = cell_block(group_cells(P, dim, g));
     const SmoothSegs G = smooth_segs(P, dim, g, (int)bs);
     if (G.n == 0 || G.blk[G.n] == 0) continue;
-#define SBM_SC(D, N1) SBM_PDL((k_smooth_cell<D, N1, R>), G.blk[G.n], bs, 0, s, P, G, zero_start, f, u);
+    const int fe = launched > 0 || early;            // after the sweep's first launch f is two back
+#define SBM_SC(D, N1) SBM_PDL((k_smooth_cell<D, N1, R>), G.blk[G.n], bs, 0, s, P, G, zero_start, f, u, fe);
     SBM_CELL_DISPATCH(dim, p, SBM_SC);
 #undef SBM_SC
     count_launches();
+    ++launched;
   }
   return cudaGetLastError();
 }
 
 template <typename R>
 cudaError_t launch_resid_restrict_p_cell(int dim, int pf, const LevelParams<R>& P, const TransferParams<R>& T,
-                                        const R* u, const R* f, R* rc, cudaStream_t s) {
+                                        const R* u, const R* f, R* rc, cudaStream_t s, int early) {
   if (P.n_act == 0) return cudaSuccess;
   const unsigned bs = cell_block(P.n_act), g = cdiv(P.n_act, bs);
-  if (dim == 2 && pf == 2) SBM_PDL((k_resid_restrict_p_cell<2, 3, 2, R>), g, bs, 0, s, P, T, u, f, rc);
-  else if (dim == 2 && pf == 3) SBM_PDL((k_resid_restrict_p_cell<2, 4, 3, R>), g, bs, 0, s, P, T, u, f, rc);
+  if (dim == 2 && pf == 2) SBM_PDL((k_resid_restrict_p_cell<2, 3, 2, R>), g, bs, 0, s, P, T, u, f, rc, early);
+  else if (dim == 2 && pf == 3) SBM_PDL((k_resid_restrict_p_cell<2, 4, 3, R>), g, bs, 0, s, P, T, u, f, rc, early);
   else return cudaErrorInvalidValue;
   count_launches();
   return cudaGetLastError();
@@ -1093,11 +1112,11 @@ cudaError_t launch_resid_restrict_p_cell(int dim, int pf, const LevelParams<R>& 
 
 template <typename R>
 cudaError_t launch_resid_restrict_h_cell(int dim, const LevelParams<R>& P, const TransferParams<R>& T, const R* u,
-                                        const R* f, R* rc, cudaStream_t s) {
+                                        const R* f, R* rc, cudaStream_t s, int early) {
   if (T.n_act_c == 0) return cudaSuccess;
   const unsigned bs = cell_block((size_t)T.n_act_c << dim), g = cdiv((size_t)T.n_act_c << dim, bs);
-  if (dim == 2) SBM_PDL((k_resid_restrict_h_cell<2, R>), g, bs, 0, s, P, T, u, f, rc);
-  else if (dim == 3) SBM_PDL((k_resid_restrict_h_cell<3, R>), g, bs, 0, s, P, T, u, f, rc);
+  if (dim == 2) SBM_PDL((k_resid_restrict_h_cell<2, R>), g, bs, 0, s, P, T, u, f, rc, early);
+  else if (dim == 3) SBM_PDL((k_resid_restrict_h_cell<3, R>), g, bs, 0, s, P, T, u, f, rc, early);
   else return cudaErrorInvalidValue;
   count_launches();
   return cudaGetLastError();
@@ -1232,19 +1251,19 @@ template cudaError_t launch_apply_cell<float, double>(int, int, const LevelParam
 template cudaError_t launch_apply_cell<float, dfl>(int, int, const LevelParams<dfl>&, const float*, const dfl*,
                                                    dfl*, int, cudaStream_t);
 template cudaError_t launch_smooth_cell<double>(int, int, const LevelParams<double>&, int, int, const double*,
-                                                double*, cudaStream_t);
+                                                double*, cudaStream_t, int);
 template cudaError_t launch_smooth_cell<float>(int, int, const LevelParams<float>&, int, int, const float*, float*,
-                                               cudaStream_t);
+                                               cudaStream_t, int);
 template cudaError_t launch_resid_restrict_p_cell<double>(int, int, const LevelParams<double>&,
                                                           const TransferParams<double>&, const double*, const double*,
-                                                          double*, cudaStream_t);
+                                                          double*, cudaStream_t, int);
 template cudaError_t launch_resid_restrict_p_cell<float>(int, int, const LevelParams<float>&,
                                                          const TransferParams<float>&, const float*, const float*,
-                                                         float*, cudaStream_t);
+                                                         float*, cudaStream_t, int);
 template cudaError_t launch_resid_restrict_h_cell<double>(int, const LevelParams<double>&,
                                                           const TransferParams<double>&, const double*, const double*,
-                                                          double*, cudaStream_t);
+                                                          double*, cudaStream_t, int);
 template cudaError_t launch_resid_restrict_h_cell<float>(int, const LevelParams<float>&, const TransferParams<float>&,
-                                                         const float*, const float*, float*, cudaStream_t);
+                                                         const float*, const float*, float*, cudaStream_t, int);
 
 }  // namespace sbm

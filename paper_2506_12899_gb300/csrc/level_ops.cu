@@ -249,7 +249,7 @@ template <int D, int N1, int NC, typename R>
 __global__ void __launch_bounds__(256) k_resid_restrict_p(const __grid_constant__ LevelParams<R> P,
                                                           const __grid_constant__ TransferParams<R> T,
                                                           const R* __restrict__ u, const R* __restrict__ f,
-                                                          R* __restrict__ rc) {
+                                                          R* __restrict__ rc, int early) {
   using Dm = Dims<D, N1>;
   constexpr int NP = Dm::NP, NQ = Dm::NQ, NS = Dm::NS, CPB = Dm::CPB;
   constexpr int NPC = D == 2 ? NC * NC : NC * NC * NC;
@@ -265,11 +265,14 @@ __global__ void __launch_bounds__(256) k_resid_restrict_p(const __grid_constant_
   const bool valid = threadIdx.x < CPB * NP && a < P.n_act;
   int nb[NS];
   dof_nbr<D, R>(P, a, valid, nb);
+  R fv = 0;
+  if (valid && early) fv = f[(size_t)a * NP + i];   // f written two or more launches back
   pdl_wait();
   pdl_trigger();
+  if (valid && !early) fv = f[(size_t)a * NP + i];
   R v = apply_dof<D, N1, R, R>(P, C, u, c, i, a, valid, nb, sU, sN, sA, sB, sE);
   __syncthreads();                                   // sU is reused for the residual
-  sU[c * NP + i] = valid ? f[(size_t)a * NP + i] - v : R(0);
+  sU[c * NP + i] = valid ? fv - v : R(0);
   __syncthreads();
   if (valid && i < NPC) {
     const int j0 = i % NC, j1 = (i / NC) % NC, j2 = D == 3 ? i / (NC * NC) : 0;
@@ -299,7 +302,7 @@ template <int D, typename R>
 __global__ void __launch_bounds__(256) k_resid_restrict_h(const __grid_constant__ LevelParams<R> P,
                                                           const __grid_constant__ TransferParams<R> T,
                                                           const R* __restrict__ u, const R* __restrict__ f,
-                                                          R* __restrict__ rc) {
+                                                          R* __restrict__ rc, int early) {
   using Dm = Dims<D, 2>;
   constexpr int NP = Dm::NP, NQ = Dm::NQ, NS = Dm::NS, CPB = Dm::CPB;
   constexpr int NCH = 1 << D, CPC = CPB / NCH;       // children per coarse cell, coarse cells per block
@@ -316,11 +319,14 @@ __global__ void __launch_bounds__(256) k_resid_restrict_h(const __grid_constant_
   const bool valid = a >= 0;
   int nb[NS];
   dof_nbr<D, R>(P, a, valid, nb);
+  R fv = 0;
+  if (valid && early) fv = f[(size_t)a * NP + i];   // f written two or more launches back
   pdl_wait();
   pdl_trigger();
+  if (valid && !early) fv = f[(size_t)a * NP + i];
   R v = apply_dof<D, 2, R, R>(P, C, u, c, i, a, valid, nb, sU, sN, sA, sB, sE);
   __syncthreads();                                   // sU is reused for the residuals
-  sU[c * NP + i] = valid ? f[(size_t)a * NP + i] - v : R(0);
+  sU[c * NP + i] = valid ? fv - v : R(0);
   __syncthreads();
   const int t = threadIdx.x;
   if (t < CPC * NP) {                               // coarse dof j of coarse cell t / NP (NPC = NP for p = 1)
@@ -365,7 +371,7 @@ __global__ void __launch_bounds__(256) k_resid_restrict_h(const __grid_constant_
 template <int D, int N1, typename R>
 __global__ void __launch_bounds__(256) k_smooth(const __grid_constant__ LevelParams<R> P,
                                                 const __grid_constant__ SmoothSegs G, int zero_start,
-                                                const R* __restrict__ f, R* __restrict__ u) {
+                                                const R* __restrict__ f, R* __restrict__ u, int early) {
   using Dm = Dims<D, N1>;
   constexpr int NP = Dm::NP, NS = Dm::NS, CPB = Dm::CPB;
   __shared__ LevelConsts<R> C;
@@ -389,8 +395,11 @@ __global__ void __launch_bounds__(256) k_smooth(const __grid_constant__ LevelPar
 #pragma unroll
     for (int s = 0; s < NS; ++s)
       if ((col ^ (1 << (s >> 1))) > col) nb[s] = -1;   // unvisited colour: zero
+  R fv = 0;
+  if (valid && early) fv = f[(size_t)a * NP + i];   // f written two or more launches back
   pdl_wait();
   pdl_trigger();
+  if (valid && !early) fv = f[(size_t)a * NP + i];
   R uold = 0;
   if (valid) {
 #pragma unroll
@@ -419,7 +428,7 @@ __global__ void __launch_bounds__(256) k_smooth(const __grid_constant__ LevelPar
       }
       acc += wt * s;
     }
-    t = f[(size_t)a * NP + i] - P.hscale * acc;
+    t = fv - P.hscale * acc;
   }
   sT[c * NP + i] = t;
   __syncthreads();
@@ -521,15 +530,18 @@ __global__ void __launch_bounds__(256) k_restrict(const __grid_constant__ Transf
 // Prolongation uf += P ec (Eq. 17) per fine dof; fine cells without an active parent get 0.
 template <int D, int NF, int NC, typename R>
 __global__ void __launch_bounds__(256) k_prolong(const __grid_constant__ TransferParams<R> T,
-                                                 const R* __restrict__ ec, R* __restrict__ uf) {
+                                                 const R* __restrict__ ec, R* __restrict__ uf, int early) {
   constexpr int NPF = D == 2 ? NF * NF : NF * NF * NF;
   constexpr int NPC = D == 2 ? NC * NC : NC * NC * NC;
   const size_t gid = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int a = (int)(gid / NPF), i = (int)(gid % NPF);
   const int code = T.hmode && a < T.n_act_f ? T.parent_code[a] : 0;   // set-up data: before the wait
+  R uv = 0;
+  if (early && a < T.n_act_f && code >= 0) uv = uf[(size_t)a * NPF + i];   // uf two or more launches back
   pdl_wait();
   pdl_trigger();
   if (a >= T.n_act_f) return;
+  if (!early && code >= 0) uv = uf[(size_t)a * NPF + i];
   int par;
   const R *P0, *P1, *P2;
   if (T.hmode) {
@@ -557,7 +569,7 @@ __global__ void __launch_bounds__(256) k_prolong(const __grid_constant__ Transfe
     }
     s2 += (D == 3 ? P2[i2 * NC + j2] : R(1)) * s1;
   }
-  uf[(size_t)a * NPF + i] += s2;
+  uf[(size_t)a * NPF + i] = uv + s2;
 }
 
 // e = Ainv r in FP64; one warp per row.
@@ -612,19 +624,22 @@ cudaError_t launch_apply(int dim, int p, const LevelParams<R>& P, const TI* x, c
 
 template <typename R>
 cudaError_t launch_smooth(int dim, int p, const LevelParams<R>& P, int reverse, int zero_start, const R* f, R* u,
-                          cudaStream_t s) {
+                          cudaStream_t s, int early) {
   if (cell_kernels(dim, p) && P.cell_min > 0 && P.n_act >= (1 << dim) * P.cell_min)
-    return launch_smooth_cell<R>(dim, p, P, reverse, zero_start, f, u, s);
+    return launch_smooth_cell<R>(dim, p, P, reverse, zero_start, f, u, s, early);
   if (reverse) zero_start = 0;
+  int launched = 0;
   for (int q = 0; q <= dim; ++q) {
     const int g = reverse ? dim - q : q;
+    const int fe = launched > 0 || early;            // after the sweep's first launch f is two back
 #define SBM_SMOOTH(D, N1)                                                                          \
   {                                                                                                \
     using Dm = Dims<D, N1>;                                                                        \
     const SmoothSegs G = smooth_segs(P, dim, g, Dm::CPB);                                          \
     if (G.n > 0 && G.blk[G.n] > 0) {                                                               \
-      SBM_PDL((k_smooth<D, N1, R>), G.blk[G.n], Dm::NT, 0, s, P, G, zero_start, f, u);             \
+      SBM_PDL((k_smooth<D, N1, R>), G.blk[G.n], Dm::NT, 0, s, P, G, zero_start, f, u, fe);         \
       count_launches();                                                                            \
+      ++launched;                                                                                  \
     }                                                                                              \
   }
     SBM_DISPATCH_DP(dim, p, SBM_SMOOTH);
@@ -646,14 +661,14 @@ cudaError_t launch_smooth(int dim, int p, const LevelParams<R>& P, int reverse, 
 
 template <typename R>
 cudaError_t launch_resid_restrict_p(int dim, int pf, const LevelParams<R>& P, const TransferParams<R>& T, const R* u,
-                                   const R* f, R* rc, cudaStream_t s) {
+                                   const R* f, R* rc, cudaStream_t s, int early) {
   if (P.n_act == 0) return cudaSuccess;
   if (cell_kernels(dim, pf) && P.cell_min > 0 && P.n_act >= P.cell_min)
-    return launch_resid_restrict_p_cell<R>(dim, pf, P, T, u, f, rc, s);
+    return launch_resid_restrict_p_cell<R>(dim, pf, P, T, u, f, rc, s, early);
 #define SBM_RRP(D, N1, NC)                                                                         \
   {                                                                                                \
     using Dm = Dims<D, N1>;                                                                        \
-    SBM_PDL((k_resid_restrict_p<D, N1, NC, R>), ceil_div(P.n_act, Dm::CPB), Dm::NT, 0, s, P, T, u, f, rc); \
+    SBM_PDL((k_resid_restrict_p<D, N1, NC, R>), ceil_div(P.n_act, Dm::CPB), Dm::NT, 0, s, P, T, u, f, rc, early); \
     count_launches();                                                                              \
   }
   if (dim == 2 && pf == 2) { SBM_RRP(2, 3, 2); }
@@ -667,15 +682,16 @@ cudaError_t launch_resid_restrict_p(int dim, int pf, const LevelParams<R>& P, co
 
 template <typename R>
 cudaError_t launch_resid_restrict_h(int dim, const LevelParams<R>& P, const TransferParams<R>& T, const R* u,
-                                   const R* f, R* rc, cudaStream_t s) {
+                                   const R* f, R* rc, cudaStream_t s, int early) {
   if (T.n_act_c == 0) return cudaSuccess;
-  if (P.cell_min > 0 && T.n_act_f >= P.cell_min) return launch_resid_restrict_h_cell<R>(dim, P, T, u, f, rc, s);
+  if (P.cell_min > 0 && T.n_act_f >= P.cell_min)
+    return launch_resid_restrict_h_cell<R>(dim, P, T, u, f, rc, s, early);
   if (dim == 2) {
     using Dm = Dims<2, 2>;
-    SBM_PDL((k_resid_restrict_h<2, R>), ceil_div(T.n_act_c, Dm::CPB / 4), Dm::NT, 0, s, P, T, u, f, rc);
+    SBM_PDL((k_resid_restrict_h<2, R>), ceil_div(T.n_act_c, Dm::CPB / 4), Dm::NT, 0, s, P, T, u, f, rc, early);
   } else if (dim == 3) {
     using Dm = Dims<3, 2>;
-    SBM_PDL((k_resid_restrict_h<3, R>), ceil_div(T.n_act_c, Dm::CPB / 8), Dm::NT, 0, s, P, T, u, f, rc);
+    SBM_PDL((k_resid_restrict_h<3, R>), ceil_div(T.n_act_c, Dm::CPB / 8), Dm::NT, 0, s, P, T, u, f, rc, early);
   } else {
     return cudaErrorInvalidValue;
   }
@@ -698,12 +714,13 @@ cudaError_t launch_restrict(int dim, int pf, int pc, const TransferParams<R>& T,
 }
 
 template <typename R>
-cudaError_t launch_prolong(int dim, int pf, int pc, const TransferParams<R>& T, const R* ec, R* uf, cudaStream_t s) {
+cudaError_t launch_prolong(int dim, int pf, int pc, const TransferParams<R>& T, const R* ec, R* uf, cudaStream_t s,
+                           int early) {
   if (T.n_act_f == 0) return cudaSuccess;
 #define SBM_PROLONG(D, NF, NC)                                                    \
   {                                                                               \
     const size_t n = (size_t)T.n_act_f * (D == 2 ? NF * NF : NF * NF * NF);       \
-    SBM_PDL((k_prolong<D, NF, NC, R>), ceil_div(n, 256), 256, 0, s, T, ec, uf);          \
+    SBM_PDL((k_prolong<D, NF, NC, R>), ceil_div(n, 256), 256, 0, s, T, ec, uf, early);   \
     count_launches();                                                             \
   }
   SBM_DISPATCH_T(dim, pf, pc, SBM_PROLONG);
@@ -728,26 +745,26 @@ template cudaError_t launch_apply<float, double>(int, int, const LevelParams<dou
 template cudaError_t launch_apply<float, dfl>(int, int, const LevelParams<dfl>&, const float*, const dfl*, dfl*, int,
                                               cudaStream_t);
 template cudaError_t launch_smooth<double>(int, int, const LevelParams<double>&, int, int, const double*, double*,
-                                           cudaStream_t);
+                                           cudaStream_t, int);
 template cudaError_t launch_smooth<float>(int, int, const LevelParams<float>&, int, int, const float*, float*,
-                                          cudaStream_t);
+                                          cudaStream_t, int);
 template cudaError_t launch_resid_restrict_p<double>(int, int, const LevelParams<double>&,
                                                      const TransferParams<double>&, const double*, const double*,
-                                                     double*, cudaStream_t);
+                                                     double*, cudaStream_t, int);
 template cudaError_t launch_resid_restrict_p<float>(int, int, const LevelParams<float>&, const TransferParams<float>&,
-                                                    const float*, const float*, float*, cudaStream_t);
+                                                    const float*, const float*, float*, cudaStream_t, int);
 template cudaError_t launch_resid_restrict_h<double>(int, const LevelParams<double>&, const TransferParams<double>&,
-                                                     const double*, const double*, double*, cudaStream_t);
+                                                     const double*, const double*, double*, cudaStream_t, int);
 template cudaError_t launch_resid_restrict_h<float>(int, const LevelParams<float>&, const TransferParams<float>&,
-                                                    const float*, const float*, float*, cudaStream_t);
+                                                    const float*, const float*, float*, cudaStream_t, int);
 template cudaError_t launch_restrict<double>(int, int, int, const TransferParams<double>&, const double*, double*,
                                              cudaStream_t);
 template cudaError_t launch_restrict<float>(int, int, int, const TransferParams<float>&, const float*, float*,
                                             cudaStream_t);
 template cudaError_t launch_prolong<double>(int, int, int, const TransferParams<double>&, const double*, double*,
-                                            cudaStream_t);
+                                            cudaStream_t, int);
 template cudaError_t launch_prolong<float>(int, int, int, const TransferParams<float>&, const float*, float*,
-                                           cudaStream_t);
+                                           cudaStream_t, int);
 template cudaError_t launch_coarse<double>(const double*, int, const double*, double*, cudaStream_t);
 template cudaError_t launch_coarse<float>(const double*, int, const float*, float*, cudaStream_t);
 

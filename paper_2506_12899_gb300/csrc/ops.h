@@ -164,13 +164,13 @@ cudaError_t launch_apply_cell(int dim, int p, const LevelParams<R>& P, const TI*
                               cudaStream_t s);
 template <typename R>
 cudaError_t launch_smooth_cell(int dim, int p, const LevelParams<R>& P, int reverse, int zero_start, const R* f,
-                               R* u, cudaStream_t s);
+                               R* u, cudaStream_t s, int early);
 template <typename R>
 cudaError_t launch_resid_restrict_p_cell(int dim, int pf, const LevelParams<R>& P, const TransferParams<R>& T,
-                                        const R* u, const R* f, R* rc, cudaStream_t s);
+                                        const R* u, const R* f, R* rc, cudaStream_t s, int early);
 template <typename R>
 cudaError_t launch_resid_restrict_h_cell(int dim, const LevelParams<R>& P, const TransferParams<R>& T, const R* u,
-                                        const R* f, R* rc, cudaStream_t s);
+                                        const R* f, R* rc, cudaStream_t s, int early);
 
 // The V-cycle of levels 0..top (p = 1 h-levels) in one thread-block-cluster launch with the
 // level vectors in shared memory; z = M^{-1} r on level top.  cudaErrorNotSupported if the plan
@@ -196,26 +196,32 @@ template <typename TI, typename R>
 cudaError_t launch_apply(int dim, int p, const LevelParams<R>& P, const TI* x, const R* f, R* y, int mode,
                          cudaStream_t s);
 
+// `early` (smoother, residual + restriction, prolongation): 1 when f, respectively uf, was written
+// two or more launches before the call, so the kernels may read it before griddepcontrol.wait
+// (the kernel before them has then passed its own wait, and everything earlier is complete).
+// 0 (the default) is always safe.
+//
 // One coloured block Gauss-Seidel sweep (all colours, forward or reverse), one launch per colour
 // group (smooth_segs).  zero_start (forward only): u holds zeros on entry and is not read or
 // cleared beforehand.
 template <typename R>
 cudaError_t launch_smooth(int dim, int p, const LevelParams<R>& P, int reverse, int zero_start, const R* f, R* u,
-                          cudaStream_t s);
+                          cudaStream_t s, int early = 0);
 
 // rc = P^T (f - A u) for a p-transfer (same mesh, degree pf -> pf - 1), residual not stored.
 template <typename R>
 cudaError_t launch_resid_restrict_p(int dim, int pf, const LevelParams<R>& P, const TransferParams<R>& T, const R* u,
-                                   const R* f, R* rc, cudaStream_t s);
+                                   const R* f, R* rc, cudaStream_t s, int early = 0);
 // rc = P^T (f - A u) for an h-transfer (p = 1, coarse cells gather their children).
 template <typename R>
 cudaError_t launch_resid_restrict_h(int dim, const LevelParams<R>& P, const TransferParams<R>& T, const R* u,
-                                   const R* f, R* rc, cudaStream_t s);
+                                   const R* f, R* rc, cudaStream_t s, int early = 0);
 // rc = P^T rf (restriction) and uf += P ec (prolongation) between level l-1 and l.
 template <typename R>
 cudaError_t launch_restrict(int dim, int pf, int pc, const TransferParams<R>& T, const R* rf, R* rc, cudaStream_t s);
 template <typename R>
-cudaError_t launch_prolong(int dim, int pf, int pc, const TransferParams<R>& T, const R* ec, R* uf, cudaStream_t s);
+cudaError_t launch_prolong(int dim, int pf, int pc, const TransferParams<R>& T, const R* ec, R* uf, cudaStream_t s,
+                           int early = 0);
 
 // e = Ainv r, dense FP64 matrix, N x N row-major.
 template <typename T>
