@@ -230,6 +230,16 @@ int sbm_dots(void* ctx, const double* V_dev, long long ldv, int nv, const double
 int sbm_dots_noalloc(const double* V_dev, long long ldv, int nv, const double* w_dev, long long n,
                      double* out_dev, void* stream);
 
+/* Failure-path check of the bounded waits.  The staged kernels (Gram-Schmidt sweeps, V-cycle
+ * tail) wait on mbarriers for bulk asynchronous copies; each wait gives up after a bounded number
+ * of polls, records the failure in a device flag and lets its kernel finish, and sbm_solve then
+ * returns SBM_ERR_CUDA.  This entry point runs one such wait in a one-block kernel on `stream`
+ * (a cudaStream_t, NULL for the legacy default stream), synchronises and reads the flag:
+ * starve = 0 announces 16 bytes and copies them (returns SBM_OK); starve = 1 announces 16 bytes
+ * and copies nothing, so the wait runs out after 4096 polls and the call returns SBM_ERR_CUDA
+ * with that reason.  The device context stays usable either way.  No counterpart in the paper. */
+int sbm_async_wait_selftest(int starve, void* stream);
+
 /* Solve A x = b by FGMRES(restart), right-preconditioned by one V-cycle in the precision of
  * sbm_setup_desc.precision; Arnoldi, Gram-Schmidt (two classical passes), the update of x and
  * the true residual are FP64.  x_dev holds the initial guess on entry.  Stops when the

@@ -32,7 +32,7 @@ SYMBOLS = ("sbm_setup", "sbm_setup_host", "sbm_host_apply", "sbm_host_rhs", "sbm
            "sbm_solve_host", "sbm_mlp_create", "sbm_mlp_destroy", "sbm_mlp_shape", "sbm_mlp_set_params",
            "sbm_mlp_get_params", "sbm_mlp_forward", "sbm_mlp_gradients", "sbm_mlp_num_samples",
            "sbm_mlp_clear_samples", "sbm_mlp_train", "sbm_mlp_save", "sbm_mlp_load", "sbm_learned_features",
-           "sbm_learned_cells", "sbm_collect", "sbm_attach_mlp")
+           "sbm_learned_cells", "sbm_collect", "sbm_attach_mlp", "sbm_async_wait_selftest")
 
 
 class SbmError(RuntimeError):
@@ -140,6 +140,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.sbm_learned_cells.argtypes = [vp, ctypes.POINTER(ctypes.c_int), vp]
     lib.sbm_collect.argtypes = [vp, vp, ip, vp, ip, ip, llp]
     lib.sbm_attach_mlp.argtypes = [vp, vp, ctypes.c_float, dp]
+    lib.sbm_async_wait_selftest.argtypes = [ip, vp]
     for name in SYMBOLS:
         if name not in ("sbm_destroy", "sbm_last_error", "sbm_kernel_launches", "sbm_mlp_destroy"):
             getattr(lib, name).restype = ctypes.c_int
@@ -150,6 +151,14 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
 def kernel_launches() -> int:
     """Kernel launches issued by libsbm since it was loaded."""
     return int(load_library().sbm_kernel_launches())
+
+
+def async_wait_selftest(starve: bool, stream=None) -> None:
+    """One bounded mbarrier wait on the GPU (sbm_async_wait_selftest): returns when the announced
+    copy arrived, raises SbmError (SBM_ERR_CUDA) when the wait ran out (starve=True)."""
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    _check(load_library().sbm_async_wait_selftest(1 if starve else 0, ctypes.c_void_p(s.cuda_stream)))
 
 
 def _check(code: int):

@@ -682,6 +682,44 @@ template cudaError_t launch_cast<float, double>(const float*, double*, size_t, c
 
 }  // namespace sbm
 
+namespace sbm {
+namespace {
+
+__device__ __align__(16) float4 g_selftest_src;
+
+// One bounded mbarrier wait: 16 bytes announced, then copied (starve = 0) or never copied
+// (starve = 1, the phase cannot complete and the wait gives up after `spin` polls).
+__global__ void k_async_selftest(int starve, unsigned spin) {
+  __shared__ __align__(16) float4 dst;
+  __shared__ __align__(8) unsigned long long bar;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    mbar_fence_init();
+    mbar_arrive_tx(&bar, 16);
+    if (!starve) bulk_load(&dst, &g_selftest_src, 16, &bar);
+  }
+  __syncthreads();
+  const bool ok = mbar_wait(&bar, 0, spin);
+  if (!__syncthreads_and(ok) && threadIdx.x == 0) atomicExch(&g_sweep_fault, 1);
+}
+
+}  // namespace
+}  // namespace sbm
+
+extern "C" int sbm_async_wait_selftest(int starve, void* stream) {
+  const cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (sbm::sweep_fault_take() < 0) return sbm::record_error(SBM_ERR_CUDA, "cannot read the fault flag");
+  sbm::k_async_selftest<<<1, 32, 0, s>>>(starve ? 1 : 0, 1u << 12);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return sbm::record_error(SBM_ERR_CUDA, std::string("selftest: ") + cudaGetErrorString(e));
+  sbm::count_launches();
+  const int f = sbm::sweep_fault_take();
+  if (f < 0) return sbm::record_error(SBM_ERR_CUDA, "cannot read the fault flag");
+  if (f) return sbm::record_error(SBM_ERR_CUDA, "bounded mbarrier wait gave up: the announced copy never completed");
+  return SBM_OK;
+}
+
 extern "C" int sbm_dots_noalloc(const double* V_dev, long long ldv, int nv, const double* w_dev, long long n,
                                 double* out_dev, void* stream) {
   return sbm::dots_noalloc(V_dev, ldv, nv, w_dev, n, out_dev, static_cast<cudaStream_t>(stream));

@@ -69,9 +69,9 @@ __device__ __forceinline__ void bulk_load(void* dst, const void* src, unsigned b
       : "memory");
 }
 
-// Waits for the phase of parity `parity` to complete; false after kAsyncSpin unsuccessful polls.
-__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned parity) {
-  for (unsigned it = 0; it < kAsyncSpin; ++it) {
+// Waits for the phase of parity `parity` to complete; false after `limit` unsuccessful polls.
+__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned parity, unsigned limit = kAsyncSpin) {
+  for (unsigned it = 0; it < limit; ++it) {
     unsigned done;
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
