@@ -768,12 +768,12 @@ void arnoldi_step_work(Context& C, int j, cudaStream_t s) {
       CUDA_TRY(launch_gs_dot(C.V2, C.ldv, j + 1, C.w, C.wdf, N, C.partial, h1, s));
     }
     CUDA_TRY(launch_gs_axpy_dot(C.V2, C.ldv, j + 1, h1, C.wdf, N, C.partial, h2, s));
-    CUDA_TRY(launch_gs_axpy_norm(C.V2, C.ldv, j + 1, h2, C.wdf, N, C.partial, hn, s));
+    CUDA_TRY(launch_gs_axpy_norm(C.V2, C.ldv, j + 1, h2, C.wdf, N, C.partial, hn, s, h1, col));   // + column
     float2* vnext = C.V2 + (size_t)(j + 1) * C.ldv;
     if (prec == SBM_F32) CUDA_TRY((launch_gs_scale<float2, float>(C.wdf, hn, vnext, C.r32, N, s)));
     else CUDA_TRY((launch_gs_scale<float2, double>(C.wdf, hn, vnext, C.v64, N, s)));
   }
-  CUDA_TRY(launch_hess_column(h1, h2, hn, j + 1, col, s));
+  if (C.desc.krylov_basis == 1) CUDA_TRY(launch_hess_column(h1, h2, hn, j + 1, col, s));
   CUDA_TRY(cudaMemcpyAsync(C.host_pinned, col, (j + 2) * sizeof(double), cudaMemcpyDeviceToHost, s));
 }
 

@@ -160,6 +160,27 @@ __global__ void k_cast(const TI* __restrict__ x, TO* __restrict__ y, size_t N) {
   for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += stride) y[i] = (TO)x[i];
 }
 
+// The norm sweep's reduction fused with the Hessenberg column: warp 0 sums the partial squares
+// (same order as k_reduce_partials) into hn[0] = |w| and col[k]; threads i < k write
+// col[i] = h1[i] + h2[i].
+__global__ void __launch_bounds__(64) k_reduce_norm_column(const double* __restrict__ partial, int nblk,
+                                                          double* __restrict__ hn, const double* __restrict__ h1,
+                                                          const double* __restrict__ h2, int k, double* __restrict__ col) {
+  pdl_entry();
+  const int i = threadIdx.x;
+  if (i < k) col[i] = h1[i] + h2[i];
+  if (i < 32) {
+    double s = 0.0;
+    for (int b = i; b < nblk; b += 32) s += partial[(size_t)b * kMaxVec];
+    s = warp_sum(s);
+    if (i == 0) {
+      const double r = sqrt(s);
+      hn[0] = r;
+      col[k] = r;
+    }
+  }
+}
+
 __global__ void k_hess_column(const double* h1, const double* h2, const double* hn, int k, double* col) {
   pdl_entry();
   const int i = threadIdx.x;
@@ -566,7 +587,8 @@ cudaError_t launch_sweep_k(const float2* V, size_t ldv, const TW* w, const doubl
 // (nv values for MODE 0 and 1, the norm for MODE 2).
 template <int MODE, typename TW>
 cudaError_t launch_sweep(const float2* V, size_t ldv, int nv, const TW* w, const double* h, float2* wdf, size_t N,
-                         double* partial, double* out, cudaStream_t s) {
+                         double* partial, double* out, cudaStream_t s, const double* h1 = nullptr,
+                         double* col = nullptr) {
   if (nv < 1 || nv > kMaxVec) return cudaErrorInvalidValue;
   const size_t padded = N + (N & 1);
   if (ldv % 2 != 0 || ldv < padded || reinterpret_cast<uintptr_t>(V) % 16 != 0 ||
@@ -586,8 +608,13 @@ cudaError_t launch_sweep(const float2* V, size_t ldv, int nv, const TW* w, const
 #undef SBM_SW_CASE
   }
   if (e != cudaSuccess) return e;
-  const int nout = MODE == 2 ? 1 : nv;
-  SBM_PDL(k_reduce_partials, 1, 32 * nout, 0, s, partial, nblk, nout, out, MODE == 2 ? 1 : 0);
+  if (MODE == 2 && col) {                            // |w| and the Hessenberg column in one launch
+    if (nv + 1 > 64) return cudaErrorInvalidValue;
+    SBM_PDL(k_reduce_norm_column, 1, 64, 0, s, partial, nblk, out, h1, h, nv, col);
+  } else {
+    const int nout = MODE == 2 ? 1 : nv;
+    SBM_PDL(k_reduce_partials, 1, 32 * nout, 0, s, partial, nblk, nout, out, MODE == 2 ? 1 : 0);
+  }
   count_launches(2);
   return cudaGetLastError();
 }
@@ -608,8 +635,8 @@ cudaError_t launch_gs_axpy_dot(const float2* V, size_t ldv, int nv, const double
 }
 
 cudaError_t launch_gs_axpy_norm(const float2* V, size_t ldv, int nv, const double* h, float2* wdf, size_t N,
-                                double* partial, double* out, cudaStream_t s) {
-  return launch_sweep<2, float2>(V, ldv, nv, wdf, h, wdf, N, partial, out, s);
+                                double* partial, double* out, cudaStream_t s, const double* h1, double* col) {
+  return launch_sweep<2, float2>(V, ldv, nv, wdf, h, wdf, N, partial, out, s, h1, col);
 }
 
 int sweep_fault_take() {

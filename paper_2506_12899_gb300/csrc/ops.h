@@ -269,8 +269,11 @@ cudaError_t launch_gs_dot_df(const float2* V, size_t ldv, int nv, const float2* 
                              double* out, cudaStream_t s);
 cudaError_t launch_gs_axpy_dot(const float2* V, size_t ldv, int nv, const double* h, float2* wdf, size_t N,
                                double* partial, double* out, cudaStream_t s);
+// With col: also col[i] = h1[i] + h[i] (i < nv) and col[nv] = |wdf| (the Hessenberg column), in
+// the same reduction launch.
 cudaError_t launch_gs_axpy_norm(const float2* V, size_t ldv, int nv, const double* h, float2* wdf, size_t N,
-                                double* partial, double* out, cudaStream_t s);
+                                double* partial, double* out, cudaStream_t s, const double* h1 = nullptr,
+                                double* col = nullptr);
 template <typename TW, typename TO>
 cudaError_t launch_gs_scale(const TW* w, const double* sc, float2* v, TO* out, size_t N, cudaStream_t s);
 template <typename TO>
