@@ -754,7 +754,7 @@ void arnoldi_step_work(Context& C, int j, cudaStream_t s) {
       vcycle_rec<float>(C, Lf, C.r32, Zj, s);
       if (C.desc.krylov_basis == 0 && F.has_df) {   // w = A z in double-float, straight into wdf
         dfl* wd = reinterpret_cast<dfl*>(C.wdf);
-        if (cell_kernels(dim, p)) CUDA_TRY((launch_apply_cell<float, dfl>(dim, p, F.Pdf, Zj, nullptr, wd, 0, s)));
+        if (cell_smoother(dim, p)) CUDA_TRY((launch_apply_cell<float, dfl>(dim, p, F.Pdf, Zj, nullptr, wd, 0, s)));
         else CUDA_TRY((launch_apply<float, dfl>(dim, p, F.Pdf, Zj, nullptr, wd, 0, s)));   // one thread per DoF
         CUDA_TRY(launch_gs_dot_df(C.V2, C.ldv, j + 1, C.wdf, N, C.partial, h1, s));
       } else {

@@ -11,6 +11,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <type_traits>
 
 #include "ops.h"
 
@@ -1051,8 +1052,10 @@ inline unsigned cdiv(size_t a, size_t b) { return (unsigned)((a + b - 1) / b); }
 
 }  // namespace
 
-bool cell_kernels(int dim, int p) { return dim == 2 || (dim == 3 && p == 1); }
+bool cell_kernels(int dim, int p) { return dim == 2 || (dim == 3 && p <= 2); }
+bool cell_smoother(int dim, int p) { return dim == 2 || (dim == 3 && p == 1); }
 
+// (p+1)^d <= 16: every thread-per-cell kernel; SBM_CELL_DISPATCH3 adds 3D p = 2 (FP32 operator).
 #define SBM_CELL_DISPATCH(dim, p, MACRO)            \
   do {                                              \
     if (dim == 2 && p == 1) { MACRO(2, 2); }        \
@@ -1060,6 +1063,11 @@ bool cell_kernels(int dim, int p) { return dim == 2 || (dim == 3 && p == 1); }
     else if (dim == 2 && p == 3) { MACRO(2, 4); }   \
     else if (dim == 3 && p == 1) { MACRO(3, 2); }   \
     else return cudaErrorInvalidValue;              \
+  } while (0)
+#define SBM_CELL_DISPATCH3(dim, p, MACRO)           \
+  do {                                              \
+    if (dim == 3 && p == 2) { MACRO(3, 3); }        \
+    else SBM_CELL_DISPATCH(dim, p, MACRO);          \
   } while (0)
 
 template <typename TI, typename R>
@@ -1072,7 +1080,8 @@ cudaError_t launch_apply_cell(int dim, int p, const LevelParams<R>& P, const TI*
     if (mode == 0) SBM_PDL((k_apply_cell<D, N1, TI, R, 0>), cdiv(P.n_act, bs), bs, 0, s, P, x, f, y); \
     else SBM_PDL((k_apply_cell<D, N1, TI, R, 1>), cdiv(P.n_act, bs), bs, 0, s, P, x, f, y);          \
   }
-  SBM_CELL_DISPATCH(dim, p, SBM_AC);
+  if constexpr (std::is_same<TI, float>::value && std::is_same<R, float>::value) SBM_CELL_DISPATCH3(dim, p, SBM_AC);
+  else SBM_CELL_DISPATCH(dim, p, SBM_AC);
 #undef SBM_AC
   count_launches();
   return cudaGetLastError();
@@ -1105,6 +1114,7 @@ cudaError_t launch_resid_restrict_p_cell(int dim, int pf, const LevelParams<R>& 
   const unsigned bs = cell_block(P.n_act), g = cdiv(P.n_act, bs);
   if (dim == 2 && pf == 2) SBM_PDL((k_resid_restrict_p_cell<2, 3, 2, R>), g, bs, 0, s, P, T, u, f, rc, early);
   else if (dim == 2 && pf == 3) SBM_PDL((k_resid_restrict_p_cell<2, 4, 3, R>), g, bs, 0, s, P, T, u, f, rc, early);
+  else if (dim == 3 && pf == 2) SBM_PDL((k_resid_restrict_p_cell<3, 3, 2, R>), g, bs, 0, s, P, T, u, f, rc, early);
   else return cudaErrorInvalidValue;
   count_launches();
   return cudaGetLastError();

@@ -625,7 +625,7 @@ cudaError_t launch_apply(int dim, int p, const LevelParams<R>& P, const TI* x, c
 template <typename R>
 cudaError_t launch_smooth(int dim, int p, const LevelParams<R>& P, int reverse, int zero_start, const R* f, R* u,
                           cudaStream_t s, int early) {
-  if (cell_kernels(dim, p) && P.cell_min > 0 && P.n_act >= (1 << dim) * P.cell_min)
+  if (cell_smoother(dim, p) && P.cell_min > 0 && P.n_act >= (1 << dim) * P.cell_min)
     return launch_smooth_cell<R>(dim, p, P, reverse, zero_start, f, u, s, early);
   if (reverse) zero_start = 0;
   int launched = 0;

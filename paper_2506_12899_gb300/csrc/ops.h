@@ -157,8 +157,13 @@ inline int group_cells(const LevelParams<R>& P, int dim, int g) {
   return n;
 }
 
-// Thread-per-cell kernels (cell_ops.cu) serve levels with (p+1)^d <= 16: 2D, and 3D with p = 1.
+// Thread-per-cell kernels (cell_ops.cu): cell_kernels covers the FP32 operator and the fused
+// residual + restriction (2D, 3D p <= 2); cell_smoother the smoother and the double-float Arnoldi
+// operator ((p+1)^d <= 16: 2D, 3D p = 1).  For 3D p = 2 the thread-per-DoF family is faster for
+// those two (measured: smoother sweep 38.6 against 154 us at 64^3; the double-float operator
+// needs 255 registers per thread there), the thread-per-cell one for the others at large sizes.
 bool cell_kernels(int dim, int p);
+bool cell_smoother(int dim, int p);
 template <typename TI, typename R>
 cudaError_t launch_apply_cell(int dim, int p, const LevelParams<R>& P, const TI* x, const R* f, R* y, int mode,
                               cudaStream_t s);
