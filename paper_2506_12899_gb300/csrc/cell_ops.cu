@@ -59,11 +59,41 @@ __device__ __forceinline__ T ldv(const T* p) {
   return *p;
 }
 
-// The (p+1)^d values of cell a.  When a cell's values fill whole 16-byte words (2D and 3D p = 1
-// in FP32 and FP64) and the vector is 16-byte aligned, they are read with 16-byte loads.
+// 32-byte global load / store (sm_100 and later), p 32-byte aligned.
+__device__ __forceinline__ void ld32B(const void* p, unsigned (&r)[8]) {
+  asm volatile("ld.global.v8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+               : "l"(p));
+}
+__device__ __forceinline__ void st32B(void* p, const unsigned (&r)[8]) {
+  asm volatile("st.global.v8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"l"(p), "r"(r[0]), "r"(r[1]), "r"(r[2]),
+               "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7])
+               : "memory");
+}
+
+// The (p+1)^d values of cell a.  When a cell's values fill whole 32-byte words (3D p = 1 and 2D
+// p = 3 in FP32, 3D p = 1 in FP64) and the vector is 32-byte aligned, they are read with 32-byte
+// loads (one L1 request per warp and word instead of two); when they fill 16-byte words (2D p = 1
+// as well), with 16-byte loads.
 template <int D, int N1, typename TI, typename R>
 __device__ __forceinline__ void load_cell(const TI* __restrict__ x, int a, R (&v)[CD<D, N1>::NP]) {
   constexpr int NP = CD<D, N1>::NP;
+  if constexpr ((NP * sizeof(TI)) % 32 == 0) {
+    if ((reinterpret_cast<uintptr_t>(x) & 31) == 0) {
+      TI t[NP];
+      const unsigned char* q = reinterpret_cast<const unsigned char*>(x + (size_t)a * NP);
+#pragma unroll
+      for (int c = 0; c < (int)(NP * sizeof(TI) / 32); ++c) {
+        unsigned r[8];
+        ld32B(q + 32 * c, r);
+#pragma unroll
+        for (int k = 0; k < 8; ++k) reinterpret_cast<unsigned*>(t)[8 * c + k] = r[k];
+      }
+#pragma unroll
+      for (int i = 0; i < NP; ++i) v[i] = (R)t[i];
+      return;
+    }
+  }
   if constexpr ((NP * sizeof(TI)) % 16 == 0) {
     if ((reinterpret_cast<uintptr_t>(x) & 15) == 0) {
       TI t[NP];
@@ -79,10 +109,23 @@ __device__ __forceinline__ void load_cell(const TI* __restrict__ x, int a, R (&v
   for (int i = 0; i < NP; ++i) v[i] = (R)ldv(x + (size_t)a * NP + i);
 }
 
-// Stores the values of cell a, with 16-byte stores under the same conditions as load_cell.
+// Stores the values of cell a, with 32- or 16-byte stores under the same conditions as load_cell.
 template <int D, int N1, typename R>
 __device__ __forceinline__ void store_cell(R* __restrict__ x, int a, const R (&v)[CD<D, N1>::NP]) {
   constexpr int NP = CD<D, N1>::NP;
+  if constexpr ((NP * sizeof(R)) % 32 == 0) {
+    if ((reinterpret_cast<uintptr_t>(x) & 31) == 0) {
+      unsigned char* q = reinterpret_cast<unsigned char*>(x + (size_t)a * NP);
+#pragma unroll
+      for (int c = 0; c < (int)(NP * sizeof(R) / 32); ++c) {
+        unsigned r[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) r[k] = reinterpret_cast<const unsigned*>(v)[8 * c + k];
+        st32B(q + 32 * c, r);
+      }
+      return;
+    }
+  }
   if constexpr ((NP * sizeof(R)) % 16 == 0) {
     if ((reinterpret_cast<uintptr_t>(x) & 15) == 0) {
       uint4* q = reinterpret_cast<uint4*>(x + (size_t)a * NP);

@@ -11,6 +11,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <type_traits>
 
 #include "ops.h"
 
@@ -607,7 +608,9 @@ template <typename TI, typename R>
 cudaError_t launch_apply(int dim, int p, const LevelParams<R>& P, const TI* x, const R* f, R* y, int mode,
                          cudaStream_t s) {
   if (P.n_act == 0) return cudaSuccess;
-  if (cell_kernels(dim, p) && P.cell_min > 0 && P.n_act >= P.cell_min)
+  // 3D p = 2 has a thread-per-cell operator for FP32 only (cell_kernels / cell_smoother)
+  constexpr bool f32 = std::is_same<TI, float>::value && std::is_same<R, float>::value;
+  if ((f32 ? cell_kernels(dim, p) : cell_smoother(dim, p)) && P.cell_min > 0 && P.n_act >= P.cell_min)
     return launch_apply_cell<TI, R>(dim, p, P, x, f, y, mode, s);
 #define SBM_APPLY(D, N1)                                                                 \
   {                                                                                      \
