@@ -203,7 +203,9 @@ int sbm_coarse_solve(void* ctx, int dtype, const void* r_dev, void* e_dev);
 /* One V-cycle z = M^{-1} r on the finest level (Sec. 3): zero initial guess, pre-smoothing
  * (forward colours), residual, restriction, recursion, prolongation, post-smoothing (reverse
  * colours); coarse direct solve.  dtype selects the V-cycle precision (FP32: every level
- * operation in FP32 except the FP64 coarse solve). */
+ * operation in FP32 except the coarse solve, which applies the FP64 inverse; inside the one-CTA
+ * tail of an FP32 V-cycle its products are formed exactly and summed in double-float, about 48
+ * significant bits, on FP32 input and output). */
 int sbm_vcycle(void* ctx, int dtype, const void* r_dev, void* z_dev);
 
 /* Gram-Schmidt projections of the FGMRES Arnoldi step (Sec. 3): out[k] = sum_i V[k*ldv + i] w[i]
