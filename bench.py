@@ -188,6 +188,18 @@ def event_time(torch, fn, reps, flush=None):
     return total / reps
 
 
+def reduce_max(value: float, device: str = "cuda") -> float:
+    """Max of `value` over the ranks of the default process group (the job's time is the slowest
+    rank's); the value itself without a process group or with one rank."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return value
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def run_ours(args) -> dict | None:
     import torch
     import torch.distributed as dist
@@ -243,11 +255,7 @@ def run_ours(args) -> dict | None:
     clk = clocks.stop()
     if world > 1:
         dist.barrier()
-    total_ms = sum(times32)
-    if world > 1:
-        t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = reduce_max(sum(times32), "cuda")
     # ---- FP64 V-cycle solves (the plain variant), same workload
     x32 = x.clone()                              # the last FP32-V-cycle solution
     times64, infos64 = [], []
