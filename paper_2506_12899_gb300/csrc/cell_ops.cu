@@ -109,6 +109,46 @@ __device__ __forceinline__ void load_cell(const TI* __restrict__ x, int a, R (&v
   for (int i = 0; i < NP; ++i) v[i] = (R)ldv(x + (size_t)a * NP + i);
 }
 
+// load_cell for data that earlier kernels wrote, read before griddepcontrol.wait (the `early`
+// reads): every access goes to L2 only (ld.global.cg), the coherence point that the writer's
+// completion has reached, so a line another kernel left in this SM's L1 is never used.
+template <int D, int N1, typename TI, typename R>
+__device__ __forceinline__ void load_cell_l2(const TI* __restrict__ x, int a, R (&v)[CD<D, N1>::NP]) {
+  constexpr int NP = CD<D, N1>::NP;
+  const TI* p = x + (size_t)a * NP;
+  if constexpr ((NP * sizeof(TI)) % 32 == 0) {
+    if ((reinterpret_cast<uintptr_t>(x) & 31) == 0) {
+      TI t[NP];
+#pragma unroll
+      for (int c = 0; c < (int)(NP * sizeof(TI) / 32); ++c) {
+        unsigned r[8];
+        asm volatile("ld.global.cg.v8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                     : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+                       "=r"(r[7])
+                     : "l"(reinterpret_cast<const unsigned char*>(p) + 32 * c));
+#pragma unroll
+        for (int k = 0; k < 8; ++k) reinterpret_cast<unsigned*>(t)[8 * c + k] = r[k];
+      }
+#pragma unroll
+      for (int i = 0; i < NP; ++i) v[i] = (R)t[i];
+      return;
+    }
+  }
+  if constexpr ((NP * sizeof(TI)) % 16 == 0) {
+    if ((reinterpret_cast<uintptr_t>(x) & 15) == 0) {
+      TI t[NP];
+#pragma unroll
+      for (int c = 0; c < (int)(NP * sizeof(TI) / 16); ++c)
+        reinterpret_cast<uint4*>(t)[c] = __ldcg(reinterpret_cast<const uint4*>(p) + c);
+#pragma unroll
+      for (int i = 0; i < NP; ++i) v[i] = (R)t[i];
+      return;
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < NP; ++i) v[i] = (R)__ldcg(p + i);
+}
+
 // Stores the values of cell a, with 32- or 16-byte stores under the same conditions as load_cell.
 template <int D, int N1, typename R>
 __device__ __forceinline__ void store_cell(R* __restrict__ x, int a, const R (&v)[CD<D, N1>::NP]) {
@@ -467,7 +507,7 @@ __global__ void __launch_bounds__(kCellThreads) k_smooth_cell(const __grid_const
   R t[NP];
   if (a < G.last[sg]) {
     load_nbr<D, R>(P, a, nb);                        // set-up data: read before the wait
-    if (early) load_cell<D, N1, R, R>(f, a, t);      // f written two or more launches back
+    if (early) load_cell_l2<D, N1, R, R>(f, a, t);   // f written two or more launches back
   }
   pdl_wait();
   pdl_trigger();
@@ -490,7 +530,7 @@ __global__ void __launch_bounds__(kCellThreads) k_resid_restrict_p_cell(const __
   R fa[NP];
   if (a < P.n_act) {
     load_nbr<D, R>(P, a, nb);                        // set-up data: read before the wait
-    if (early) load_cell<D, N1, R, R>(f, a, fa);     // f written two or more launches back
+    if (early) load_cell_l2<D, N1, R, R>(f, a, fa);  // f written two or more launches back
   }
   pdl_wait();
   pdl_trigger();
@@ -544,7 +584,7 @@ __global__ void __launch_bounds__(kCellThreads) k_resid_restrict_h_cell(const __
   R fa[NP];
   if (a >= 0) {
     load_nbr<D, R>(P, a, nb);
-    if (early) load_cell<D, 2, R, R>(f, a, fa);      // f written two or more launches back
+    if (early) load_cell_l2<D, 2, R, R>(f, a, fa);   // f written two or more launches back
   }
   pdl_wait();
   pdl_trigger();

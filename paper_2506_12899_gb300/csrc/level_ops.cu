@@ -267,7 +267,7 @@ __global__ void __launch_bounds__(256) k_resid_restrict_p(const __grid_constant_
   int nb[NS];
   dof_nbr<D, R>(P, a, valid, nb);
   R fv = 0;
-  if (valid && early) fv = f[(size_t)a * NP + i];   // f written two or more launches back
+  if (valid && early) fv = __ldcg(f + (size_t)a * NP + i);   // f written two or more launches back (L2)
   pdl_wait();
   pdl_trigger();
   if (valid && !early) fv = f[(size_t)a * NP + i];
@@ -321,7 +321,7 @@ __global__ void __launch_bounds__(256) k_resid_restrict_h(const __grid_constant_
   int nb[NS];
   dof_nbr<D, R>(P, a, valid, nb);
   R fv = 0;
-  if (valid && early) fv = f[(size_t)a * NP + i];   // f written two or more launches back
+  if (valid && early) fv = __ldcg(f + (size_t)a * NP + i);   // f written two or more launches back (L2)
   pdl_wait();
   pdl_trigger();
   if (valid && !early) fv = f[(size_t)a * NP + i];
@@ -397,7 +397,7 @@ __global__ void __launch_bounds__(256) k_smooth(const __grid_constant__ LevelPar
     for (int s = 0; s < NS; ++s)
       if ((col ^ (1 << (s >> 1))) > col) nb[s] = -1;   // unvisited colour: zero
   R fv = 0;
-  if (valid && early) fv = f[(size_t)a * NP + i];   // f written two or more launches back
+  if (valid && early) fv = __ldcg(f + (size_t)a * NP + i);   // f written two or more launches back (L2)
   pdl_wait();
   pdl_trigger();
   if (valid && !early) fv = f[(size_t)a * NP + i];
@@ -538,7 +538,7 @@ __global__ void __launch_bounds__(256) k_prolong(const __grid_constant__ Transfe
   const int a = (int)(gid / NPF), i = (int)(gid % NPF);
   const int code = T.hmode && a < T.n_act_f ? T.parent_code[a] : 0;   // set-up data: before the wait
   R uv = 0;
-  if (early && a < T.n_act_f && code >= 0) uv = uf[(size_t)a * NPF + i];   // uf two or more launches back
+  if (early && a < T.n_act_f && code >= 0) uv = __ldcg(uf + (size_t)a * NPF + i);   // uf two launches back (L2)
   pdl_wait();
   pdl_trigger();
   if (a >= T.n_act_f) return;
