@@ -295,11 +295,18 @@ constexpr int kSweepBudget = 216 * 1024;           // shared memory of the stage
 // clears it (sweep_fault_take) and reports SBM_ERR_CUDA.
 __device__ int g_sweep_fault;
 
+constexpr int kSweepBudgetNoW = 224 * 1024;        // stage budget when w is read directly
+
 template <int NV>
 struct SweepShape {
-  static constexpr int SLOT = NV + 1;              // V_0 .. V_{NV-1}, then w
-  static constexpr int E = 2 * SLOT * 1024 * 8 <= kSweepBudget ? 1024 : (2 * SLOT * 512 * 8 <= kSweepBudget ? 512 : 256);
-  static constexpr int S0 = kSweepBudget / (SLOT * E * 8);
+  static constexpr int SLOTW = NV + 1;             // V_0 .. V_{NV-1}, then w
+  static constexpr int EW = 2 * SLOTW * 1024 * 8 <= kSweepBudget ? 1024 : (2 * SLOTW * 512 * 8 <= kSweepBudget ? 512 : 256);
+  // when the w slot would force 256-entry chunks, w is read with plain coalesced loads instead and
+  // the V rows alone fill two 512-entry stages (widths 26..28)
+  static constexpr bool WIN = !(EW == 256 && 2 * NV * 512 * 8 <= kSweepBudgetNoW);
+  static constexpr int SLOT = WIN ? SLOTW : NV;
+  static constexpr int E = WIN ? EW : 512;
+  static constexpr int S0 = (WIN ? kSweepBudget : kSweepBudgetNoW) / (SLOT * E * 8);
   static constexpr int S = S0 > 6 ? 6 : S0;        // stages in flight
   static constexpr size_t smem = (size_t)S * SLOT * E * sizeof(float2) + (size_t)S * sizeof(unsigned long long);
   static_assert(S >= 2, "two stages must fit");
@@ -338,12 +345,14 @@ __global__ void __launch_bounds__(kSweepThreads) k_gs_sweep(const float2* __rest
 #pragma unroll 1
     for (int k = 0; k < NV; ++k) bulk_load(dst + (size_t)k * E, V + (size_t)k * ldv + e0, bytes, b);
   };
-  auto issue_w = [&](size_t q) {
-    size_t e0;
-    unsigned bytes;
-    chunk(q, e0, bytes);
-    bulk_load(stage + (size_t)(q % S) * SLOT * E + (size_t)NV * E,
-              reinterpret_cast<const unsigned char*>(w_in) + e0 * sizeof(float2), bytes, &bar[q % S]);
+  auto issue_w = [&](size_t q) {                     // (without a w slot, w is read from global memory)
+    if constexpr (Sh::WIN) {
+      size_t e0;
+      unsigned bytes;
+      chunk(q, e0, bytes);
+      bulk_load(stage + (size_t)(q % S) * SLOT * E + (size_t)NV * E,
+                reinterpret_cast<const unsigned char*>(w_in) + e0 * sizeof(float2), bytes, &bar[q % S]);
+    }
   };
   // The first S chunks are copied before the dependency wait where that is safe: the V rows, and
   // w for the update sweeps, were written at least two launches back, and this grid starts only
@@ -376,8 +385,14 @@ __global__ void __launch_bounds__(kSweepThreads) k_gs_sweep(const float2* __rest
       const size_t e = e0 + t;
       if (!ok || e >= N) continue;
       float2 wi;
-      if constexpr (std::is_same<TW, double>::value) wi = df_from_double(reinterpret_cast<const double*>(sv + NV * E)[t]);
-      else wi = sv[NV * E + t];
+      if constexpr (!Sh::WIN) {
+        if constexpr (std::is_same<TW, double>::value) wi = df_from_double(reinterpret_cast<const double*>(w_in)[e]);
+        else wi = reinterpret_cast<const float2*>(w_in)[e];
+      } else if constexpr (std::is_same<TW, double>::value) {
+        wi = df_from_double(reinterpret_cast<const double*>(sv + NV * E)[t]);
+      } else {
+        wi = sv[NV * E + t];
+      }
       if (MODE == 0) {
         if constexpr (std::is_same<TW, double>::value) wdf[e] = wi;
 #pragma unroll
