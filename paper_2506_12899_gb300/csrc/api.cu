@@ -1517,10 +1517,14 @@ int sbm_mlp_save(const void* mlp, const char* path) {
     std::vector<float> w(packed_size(*M));
     get_packed(*M, M->P, w.data());
     int32_t hdr[6] = {1, M->dim, M->p, M->F, M->H, M->O};
-    std::vector<unsigned char> buf(8 + sizeof(hdr) + w.size() * sizeof(float));
-    std::memcpy(buf.data(), "SBMMLP\0\0", 8);
-    std::memcpy(buf.data() + 8, hdr, sizeof(hdr));
-    std::memcpy(buf.data() + 8 + sizeof(hdr), w.data(), w.size() * sizeof(float));
+    static const unsigned char magic[8] = {'S', 'B', 'M', 'M', 'L', 'P', 0, 0};
+    std::vector<unsigned char> buf;
+    buf.reserve(8 + sizeof(hdr) + w.size() * sizeof(float));
+    buf.insert(buf.end(), magic, magic + 8);
+    const unsigned char* hb = reinterpret_cast<const unsigned char*>(hdr);
+    buf.insert(buf.end(), hb, hb + sizeof(hdr));
+    const unsigned char* wb = reinterpret_cast<const unsigned char*>(w.data());
+    buf.insert(buf.end(), wb, wb + w.size() * sizeof(float));
     const uint32_t crc = crc32(buf.data(), buf.size());
     FILE* f = std::fopen(path, "wb");
     if (!f) return set_error(SBM_ERR_ARG, std::string("cannot write ") + path);
