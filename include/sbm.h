@@ -216,6 +216,22 @@ int sbm_vcycle(void* ctx, int dtype, const void* r_dev, void* z_dev);
 int sbm_dots(void* ctx, const double* V_dev, long long ldv, int nv, const double* w_dev, long long n,
              double* out_dev);
 
+/* The three Gram-Schmidt sweeps of one FGMRES Arnoldi step (Sec. 3; two classical passes, CGS2)
+ * on caller data, by the kernels sbm_solve uses:
+ *   h1 = V w;  w1 = w - V^T h1;  h2 = V w1;  w2 = w1 - V^T h2;  norm = |w2|_2.
+ * V_dev holds nv (1..32) FP64 vectors of the finest level's length N (row-major, [nv][N]), w_dev
+ * one; outputs: h_dev[0..nv) = h1, h_dev[nv..2nv) = h2 (FP64), w_out_dev = w2 (N doubles),
+ * norm_dev = |w2| (one double).  variant 0: the double-float basis of krylov_basis = 0/2 (V rounded
+ * to FP32 pairs, ~48-bit significands, staged bulk-copy sweeps), w given in FP64 and converted by
+ * the first sweep (FP64-V-cycle solves); 1: the same with w first rounded to double-float (the
+ * path of FP32-V-cycle solves, where A z is formed in double-float); 2: the FP64 sweeps of
+ * krylov_basis = 1.  The context keeps its own copy of the rows and of w (allocated on first use:
+ * 32 padded rows of N double-floats) and does not touch the solve's workspace.  Synchronises.
+ * Errors: SBM_ERR_ARG for null pointers, nv outside 1..32 or an unknown variant; SBM_ERR_CUDA if a
+ * launch fails or a bounded wait of a staged sweep gave up. */
+int sbm_gram_schmidt(void* ctx, int variant, const double* V_dev, int nv, const double* w_dev, double* h_dev,
+                     double* w_out_dev, double* norm_dev);
+
 /* sbm_dots without any allocation, for callers that cannot call cudaMalloc: for example a
  * process whose caching allocator has already reserved the device memory (a cudaMalloc would
  * fail), or a latency-critical loop that cannot accept the device-wide synchronisation a
@@ -223,12 +239,20 @@ int sbm_dots(void* ctx, const double* V_dev, long long ldv, int nv, const double
  * computed by the same kernels and in the same order as sbm_dots, on `stream` (a cudaStream_t,
  * NULL for the legacy default stream, current device).  The per-block partial sums live in a
  * file-scope __device__ array of 608 x 32 doubles (152 KiB) that every GPU loading the library
- * holds until the process exits.  The first call on a device looks up that array's device
- * address (cudaGetSymbolAddress) and should come before any stream capture.  Every call reuses
- * the same array: each call overwrites the partial sums it reads, so nothing carries over, but
- * calls that overlap on the GPU (other streams, other host threads) race on the array.
- * Errors: SBM_ERR_ARG for null pointers, nv outside 1..32, n < 0 or ldv < n; SBM_ERR_CUDA if
- * the address lookup or the launch fails.  The paper has no counterpart to this entry point. */
+ * holds until the process exits.  That array is created when the library's Krylov module is
+ * loaded into a device's context.  Under CUDA's lazy module loading (the default) that happens on
+ * the first use of the module there (this call, or any solve), and that one load allocates the
+ * array: make the first call on each device at a point where 152 KiB can still be had, e.g.
+ * before a caching allocator reserves the memory.  Later calls allocate nothing.  Every call
+ * made outside stream capture looks the array's address up again in the current context
+ * (cudaGetSymbolAddress), so a reset or replaced context is followed; inside a capture the
+ * address of the last call outside capture on this device is used, so the first call on a
+ * device must come before any stream capture.  Every call reuses the same array: each call
+ * overwrites the partial sums it reads, so nothing carries over, but calls that overlap on the
+ * GPU (other streams, other host threads) race on the array.
+ * Errors: SBM_ERR_ARG for null pointers, nv outside 1..32, n < 0, ldv < n, or a first call
+ * inside a capture; SBM_ERR_CUDA if the address lookup or the launch fails.  The paper has no
+ * counterpart to this entry point. */
 int sbm_dots_noalloc(const double* V_dev, long long ldv, int nv, const double* w_dev, long long n,
                      double* out_dev, void* stream);
 

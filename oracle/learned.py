@@ -157,14 +157,17 @@ def correction(net: MLP, cells):
     return apply
 
 
-def training_pairs(H: MG.Hierarchy, n_starts: int, n_cycles: int, seed: int):
+def training_pairs(H: MG.Hierarchy, n_starts: int, n_cycles: int, seed: int, u0s=None, cells=None):
     """(X, T) from the stationary V-cycle iteration u <- u + V(-A u) on A u = 0 from seeded random
-    u0 in U[-1, 1]: the exact solution is 0, so after each finest-level post-smoothing the error of
-    the finest iterate is -u.  Features use r = -A u; targets are -u_K / s."""
+    u0 in U[-1, 1] (or the given starts u0s): the exact solution is 0, so after each finest-level
+    post-smoothing the error of the finest iterate is -u.  Features use r = -A u; targets are
+    -u_K / s.  Rows: for each start, for each step, one per boundary cell (`cells`, default the
+    boundary cells in natural order)."""
     F = H.finest
-    cells = boundary_cells(F)
+    cells = boundary_cells(F) if cells is None else cells
     nb = F.nb
     rng = np.random.default_rng(seed)
+    starts = list(u0s) if u0s is not None else [2.0 * rng.random(F.N) - 1.0 for _ in range(n_starts)]
     Xs, Ts = [], []
 
     def record(level, z, rhs):
@@ -177,8 +180,8 @@ def training_pairs(H: MG.Hierarchy, n_starts: int, n_cycles: int, seed: int):
         Ts.append(T)
 
     state = {}
-    for _ in range(n_starts):
-        u = 2.0 * rng.random(F.N) - 1.0
+    for u in starts:
+        u = np.array(u, dtype=np.float64)
         for _ in range(n_cycles):
             state["u"] = u
             z = H.vcycle(-(F.A @ u), correction=record)

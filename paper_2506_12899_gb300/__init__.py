@@ -28,7 +28,7 @@ ERRORS = {-1: "SBM_ERR_ARG", -2: "SBM_ERR_CUDA", -3: "SBM_ERR_SINGULAR_BLOCK", -
 # exported C symbols (checked by the tests against include/sbm.h)
 SYMBOLS = ("sbm_setup", "sbm_setup_host", "sbm_host_apply", "sbm_host_rhs", "sbm_destroy", "sbm_last_error", "sbm_kernel_launches", "sbm_num_levels", "sbm_info", "sbm_layout",
            "sbm_export_geometry", "sbm_rhs", "sbm_apply", "sbm_residual", "sbm_smooth", "sbm_restrict",
-           "sbm_prolong_add", "sbm_coarse_solve", "sbm_vcycle", "sbm_dots", "sbm_dots_noalloc", "sbm_solve",
+           "sbm_prolong_add", "sbm_coarse_solve", "sbm_vcycle", "sbm_dots", "sbm_dots_noalloc", "sbm_gram_schmidt", "sbm_solve",
            "sbm_solve_host", "sbm_mlp_create", "sbm_mlp_destroy", "sbm_mlp_shape", "sbm_mlp_set_params",
            "sbm_mlp_get_params", "sbm_mlp_forward", "sbm_mlp_gradients", "sbm_mlp_num_samples",
            "sbm_mlp_clear_samples", "sbm_mlp_train", "sbm_mlp_save", "sbm_mlp_load", "sbm_learned_features",
@@ -119,6 +119,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.sbm_coarse_solve.argtypes = [vp, ip, vp, vp]
     lib.sbm_vcycle.argtypes = [vp, ip, vp, vp]
     lib.sbm_dots.argtypes = [vp, vp, ctypes.c_longlong, ip, vp, ctypes.c_longlong, vp]
+    lib.sbm_gram_schmidt.argtypes = [vp, ip, vp, ip, vp, vp, vp, vp]
     lib.sbm_dots_noalloc.argtypes = [vp, ctypes.c_longlong, ip, vp, ctypes.c_longlong, vp, vp]
     lib.sbm_solve.argtypes = [vp, vp, vp, dp, ip, ip, ctypes.POINTER(_SolveInfo)]
     lib.sbm_solve_host.argtypes = [vp, vp, vp, dp, ip, ip, ctypes.POINTER(_SolveInfo)]
@@ -327,6 +328,22 @@ class Solver:
         _check(self.lib.sbm_dots(self.ctx, self._vec(V), V.shape[1], V.shape[0], self._vec(w, torch.float64),
                                  w.numel(), self._vec(out, torch.float64)))
         return out
+
+    def gram_schmidt(self, V, w, variant: int = 0):
+        """(h1, h2, w2, |w2|) of the two classical Gram-Schmidt passes of an Arnoldi step, by the
+        solver's own sweeps: V (nv, N) and w (N,) contiguous float64 CUDA tensors, N the finest
+        level's length; variant 0/1 double-float basis (w in FP64 / rounded to double-float first),
+        2 FP64 basis."""
+        torch = self._torch
+        if V.dim() != 2 or V.dtype != torch.float64 or not V.is_contiguous() or not V.is_cuda:
+            raise ValueError("V must be a contiguous (nv, N) float64 CUDA tensor")
+        nv = V.shape[0]
+        h = torch.empty(2 * nv, dtype=torch.float64, device="cuda")
+        wout = torch.empty_like(w)
+        nrm = torch.empty(1, dtype=torch.float64, device="cuda")
+        _check(self.lib.sbm_gram_schmidt(self.ctx, variant, self._vec(V), nv, self._vec(w, torch.float64),
+                                         self._vec(h), self._vec(wout), self._vec(nrm)))
+        return h[:nv], h[nv:], wout, float(nrm.item())
 
     def solve(self, b, x, tol: float = 1e-8, restart: int = 30, max_it: int = 300, check: bool = True) -> SolveInfo:
         inf = _SolveInfo()

@@ -198,6 +198,12 @@ struct Context {
   bool host_only = false;
   double* dots_scratch = nullptr;  // partial sums of sbm_dots
   size_t dots_scratch_len = 0;
+  // sbm_gram_schmidt: its own copy of the basis and of w (padded rows), partial sums and results
+  float2* gsV2 = nullptr;          // [32][ldv] double-float basis rows
+  double* gsw = nullptr;           // [ldv] w, FP64
+  float2* gswdf = nullptr;         // [ldv] w, double-float
+  double* gspartial = nullptr;
+  double* gsdots = nullptr;        // [0,32) h1, [32,64) h2, [64] |w|, [65] 1.0, [128,161) column
   // FGMRES runs on an internal non-blocking stream (the legacy default stream cannot be captured
   // into a graph), joined to the caller's stream with events.  Each Arnoldi step j of each
   // V-cycle precision is captured once into a CUDA graph and replayed.
@@ -1317,6 +1323,69 @@ int sbm_dots(void* ctx, const double* V_dev, long long ldv, int nv, const double
       C->dots_scratch_len = need;
     }
     CUDA_TRY(launch_multi_dot(V_dev, (size_t)ldv, nv, w_dev, (size_t)n, C->dots_scratch, out_dev, 0, C->stream));
+    return SBM_OK;
+  });
+}
+
+int sbm_gram_schmidt(void* ctx, int variant, const double* V_dev, int nv, const double* w_dev, double* h_dev,
+                     double* w_out_dev, double* norm_dev) {
+  Context* C = ctx_of(ctx);
+  if (C && C->host_only) return set_error(SBM_ERR_ARG, "host-only context");
+  if (!C || !V_dev || !w_dev || !h_dev || !w_out_dev || !norm_dev || nv < 1 || nv > 32 || variant < 0 ||
+      variant > 2)
+    return set_error(SBM_ERR_ARG, "bad argument");
+  return guarded([&]() -> int {
+    const size_t N = C->lv.back().H.n_dof();
+    const size_t ldv = (N + 31) / 32 * 32;           // the solve's padded row length
+    const cudaStream_t s = C->stream;
+    if (!C->gsw) {
+      C->gsw = C->dalloc<double>(ldv);
+      C->gswdf = C->dalloc<float2>(ldv);
+      C->gspartial = C->dalloc<double>((size_t)std::max(dot_blocks(N), gs_blocks(N)) * 32);
+      C->gsdots = C->dalloc<double>(256);
+      const double one = 1.0;
+      CUDA_TRY(cudaMemcpy(C->gsdots + 65, &one, sizeof(double), cudaMemcpyHostToDevice));
+    }
+    if (sweep_fault_take() < 0) return set_error(SBM_ERR_CUDA, "cannot read the fault flag");
+    double* h1 = C->gsdots;
+    double* h2 = C->gsdots + 32;
+    double* hn = C->gsdots + 64;
+    const double* one = C->gsdots + 65;
+    double* col = C->gsdots + 128;
+    // w into the padded buffer (the staged copies read whole 16-byte units past an odd N)
+    CUDA_TRY(cudaMemsetAsync(C->gsw, 0, ldv * sizeof(double), s));
+    CUDA_TRY(cudaMemcpyAsync(C->gsw, w_dev, N * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    if (variant == 2) {                              // FP64 basis: the sweeps of krylov_basis = 1
+      CUDA_TRY(launch_multi_dot(V_dev, N, nv, C->gsw, N, C->gspartial, h1, 0, s));
+      CUDA_TRY(launch_axpy_dot(V_dev, N, nv, h1, C->gsw, N, C->gspartial, h2, s));
+      CUDA_TRY(launch_axpy_norm(V_dev, N, nv, h2, C->gsw, N, C->gspartial, hn, s));
+      CUDA_TRY(cudaMemcpyAsync(w_out_dev, C->gsw, N * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    } else {                                         // double-float basis: the staged sweeps
+      if (!C->gsV2) {
+        C->gsV2 = C->dalloc<float2>(32 * ldv);
+        CUDA_TRY(cudaMemsetAsync(C->gsV2, 0, 32 * ldv * sizeof(float2), s));
+      }
+      for (int k = 0; k < nv; ++k)                   // rows rounded to double-float (exact split)
+        CUDA_TRY((launch_gs_scale<double, double>(V_dev + (size_t)k * N, one, C->gsV2 + (size_t)k * ldv,
+                                                  (double*)nullptr, N, s)));
+      if (variant == 1) {                            // w handed over as double-float (FP32-V-cycle solves)
+        CUDA_TRY(cudaMemsetAsync(C->gswdf, 0, ldv * sizeof(float2), s));
+        CUDA_TRY((launch_gs_scale<double, double>(C->gsw, one, C->gswdf, (double*)nullptr, N, s)));
+        CUDA_TRY(launch_gs_dot_df(C->gsV2, ldv, nv, C->gswdf, N, C->gspartial, h1, s));
+      } else {                                       // w in FP64, converted by the first sweep
+        CUDA_TRY(launch_gs_dot(C->gsV2, ldv, nv, C->gsw, C->gswdf, N, C->gspartial, h1, s));
+      }
+      CUDA_TRY(launch_gs_axpy_dot(C->gsV2, ldv, nv, h1, C->gswdf, N, C->gspartial, h2, s));
+      CUDA_TRY(launch_gs_axpy_norm(C->gsV2, ldv, nv, h2, C->gswdf, N, C->gspartial, hn, s, h1, col));
+      CUDA_TRY(launch_df_to<double>(C->gswdf, w_out_dev, N, s));
+    }
+    CUDA_TRY(cudaMemcpyAsync(h_dev, h1, nv * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    CUDA_TRY(cudaMemcpyAsync(h_dev + nv, h2, nv * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    CUDA_TRY(cudaMemcpyAsync(norm_dev, hn, sizeof(double), cudaMemcpyDeviceToDevice, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    const int f = sweep_fault_take();
+    if (f < 0) return set_error(SBM_ERR_CUDA, "cannot read the fault flag");
+    if (f) return set_error(SBM_ERR_CUDA, "a bounded mbarrier wait of a Gram-Schmidt sweep gave up");
     return SBM_OK;
   });
 }

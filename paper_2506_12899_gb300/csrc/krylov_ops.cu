@@ -15,6 +15,7 @@ namespace {
 
 constexpr int kDotThreads = 256;
 constexpr int kMaxVec = 32;
+constexpr int kDotMaxBlocks = 152 * 4;     // grid cap of the multi-vector dot kernels (4 CTAs per SM)
 
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
@@ -472,12 +473,13 @@ __global__ void k_df_to(const float2* __restrict__ v, TO* __restrict__ y, size_t
 }
 
 // Scratch of sbm_dots_noalloc: room for the per-block partial sums of the largest grid the dot
-// kernel uses (dot_blocks() never exceeds kNoAllocBlocks) times 32 vectors: 152 KiB per device,
+// kernel uses (dot_blocks() caps its grid at kDotMaxBlocks) times 32 vectors: 152 KiB per device,
 // held by every GPU that loads the library until the process exits.
-constexpr int kNoAllocBlocks = 152 * 4;
+constexpr int kNoAllocBlocks = kDotMaxBlocks;
+static_assert(kNoAllocBlocks >= kDotMaxBlocks, "the static scratch must hold the largest dot grid");
 static __device__ __align__(256) double g_dots_scratch[kNoAllocBlocks * kMaxVec];
 std::mutex g_dots_scratch_mu;
-double* g_dots_scratch_dev[256] = {};      // device address of g_dots_scratch, per device ordinal
+double* g_dots_scratch_dev[256] = {};      // last resolved address of g_dots_scratch, per device ordinal
 
 unsigned grid_for(size_t N) {
   size_t g = (N + 255) / 256;
@@ -496,7 +498,7 @@ bool& pdl_enabled() {
 int dot_blocks(size_t N) {
   size_t g = (N + kDotChunk - 1) / kDotChunk;
   if (g < 1) g = 1;
-  if (g > 152 * 4) g = 152 * 4;
+  if (g > kDotMaxBlocks) g = kDotMaxBlocks;
   return (int)g;
 }
 
@@ -698,15 +700,27 @@ int dots_noalloc(const double* V, long long ldv, int nv, const double* w, long l
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return record_error(SBM_ERR_CUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
   if (dev < 0 || dev >= 256) return record_error(SBM_ERR_ARG, "sbm_dots_noalloc: device ordinal out of range");
+  // The array's device address belongs to the context current on this thread, and it changes when
+  // that context is replaced (cudaDeviceReset, a primary-context reset, another driver context).
+  // So it is looked up again on every call made outside stream capture, where the lookup is an
+  // ordinary host call; only inside a capture, where a lookup that has to load the module could
+  // break the capture, the address resolved by the last call outside capture is used.
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  e = cudaStreamIsCapturing(stream, &cap);
+  if (e != cudaSuccess)
+    return record_error(SBM_ERR_CUDA, std::string("cudaStreamIsCapturing: ") + cudaGetErrorString(e));
   double* scratch = nullptr;
   {
     std::lock_guard<std::mutex> lock(g_dots_scratch_mu);
-    if (!g_dots_scratch_dev[dev]) {          // first call on this device: resolve the array's address
+    if (cap == cudaStreamCaptureStatusNone) {
       void* p = nullptr;
       e = cudaGetSymbolAddress(&p, g_dots_scratch);
       if (e != cudaSuccess)
         return record_error(SBM_ERR_CUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
       g_dots_scratch_dev[dev] = static_cast<double*>(p);
+    } else if (!g_dots_scratch_dev[dev]) {
+      return record_error(SBM_ERR_ARG, "sbm_dots_noalloc: the first call on a device must come before any "
+                                       "stream capture");
     }
     scratch = g_dots_scratch_dev[dev];
   }

@@ -135,10 +135,10 @@ def test_collect_matches_oracle_targets():
     n = P.gpu.collect(gm, P.to_gpu(u0, L)[None, :].contiguous(), 1)
     cells = bnd_cells_oracle(P)
     assert n == len(cells) and gm.num_samples() == n
-    # oracle: one step of u <- u + V(-A u); then the pair of each boundary cell
-    u1 = u0 + P.H.vcycle(-(lev.A @ u0))
-    Xo, so = OL.features(lev, -(lev.A @ u1), cells)
-    To = np.stack([-u1[a * lev.nb:(a + 1) * lev.nb] for a in cells]) / so[:, None]
+    # oracle: one step of u <- u + V(-A u) from the same start, the pair of each boundary cell in
+    # the library's cell order
+    Xo, To = OL.training_pairs(P.H, 1, 1, 0, u0s=[u0], cells=cells)
+    assert Xo.shape[0] == n
     # the library keeps the pairs internally; train for zero epochs is a no-op, so read them back
     # through the loss of an MLP whose output is exactly zero: loss = mean(T^2)
     zero = [np.zeros_like(a) for a in OL.MLP(gm.F, gm.H, gm.O).params()]

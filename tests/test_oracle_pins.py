@@ -446,3 +446,49 @@ def test_learned_features_layout():
         assert set(np.nonzero(mask)[0]) == slots
         for slot in range(4):
             assert (np.abs(d[slot]).max() > 0) == (slot in slots)
+
+
+def _vcycle_matrix(H):
+    """The V-cycle as a matrix, by brute force: column j is V(e_j) (V is linear, Sec. 3)."""
+    N = H.finest.N
+    M = np.zeros((N, N))
+    for j in range(N):
+        e = np.zeros(N)
+        e[j] = 1.0
+        M[:, j] = H.vcycle(e)
+    return M
+
+
+def test_training_pairs_follow_the_error_propagation():
+    """The learned part's training pairs: after k steps of u <- u + V(-A u) on A u = 0 the iterate is
+    (I - V A)^k u0 (error propagation of a stationary iteration with a linear preconditioner), so
+    the k-th block of rows must hold targets -u_K / s_K of that iterate and residual features of
+    -A u.  Checked against the explicit matrix power on a tiny mesh; a sign, a stale iterate or
+    the correction z alone in place of u + z fails it."""
+    from oracle import learned as OL
+    H = MG.Hierarchy(W.disk2d_p1(8, 1).replace(coarsest_n=4))
+    F = H.finest
+    assert len(H.levels) == 2
+    cells = OL.boundary_cells(F)
+    nb = F.nb
+    rng = np.random.default_rng(3)
+    u0s = [2.0 * rng.random(F.N) - 1.0 for _ in range(2)]
+    X, T = OL.training_pairs(H, 2, 3, 0, u0s=u0s)
+    nc = len(cells)
+    assert X.shape == (2 * 3 * nc, OL.feature_size(2, 1)) and T.shape == (2 * 3 * nc, nb)
+    E = np.eye(F.N) - _vcycle_matrix(H) @ F.A.toarray()
+    row = 0
+    for u0 in u0s:
+        u = u0.copy()
+        for _ in range(3):
+            u = E @ u
+            Xo, so = OL.features(F, -(F.A @ u), cells)
+            To = np.stack([-u[a * nb:(a + 1) * nb] for a in cells]) / so[:, None]
+            assert np.allclose(X[row:row + nc], Xo, rtol=1e-9, atol=1e-12)
+            assert np.allclose(T[row:row + nc], To, rtol=1e-9, atol=1e-12)
+            row += nc
+    # the centre block of the patch (offset (0, 0), the fifth of nine) times s is -(A u)_K
+    _, so = OL.features(F, -(F.A @ u), cells)
+    r = -(F.A @ u)
+    assert np.allclose(X[-nc:, 4 * nb:5 * nb] * so[:, None], np.stack([r[a * nb:(a + 1) * nb] for a in cells]),
+                       rtol=1e-9, atol=1e-12)
