@@ -24,6 +24,11 @@ import sys
 import tempfile
 import time
 
+# the oracle arms run on one host core: pin the BLAS thread pools before numpy is first imported
+if "--cpu-worker" in sys.argv or "reference" in sys.argv:
+    for _v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ[_v] = "1"
+
 ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
@@ -58,10 +63,12 @@ PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 
 
 # ----------------------------------------------------------------------------- CPU oracle worker
-def cpu_worker(workload: str, seed: int, budget_s: float, full: bool) -> dict:
-    """Times the CPU FP64 oracle (set-up untimed) on the same workload: FGMRES iterations until
-    `budget_s` of solve time is spent; returns ms per Arnoldi step and, if `full`, the oracle's
-    own iteration count to 1e-8."""
+def cpu_worker(workload: str, seed: int, budget_s: float) -> dict:
+    """Times the CPU FP64 oracle (set-up untimed) on the same workload: whole FGMRES(30) solves to
+    1e-8 from x = 0, repeated until `budget_s` of solve time is spent (at least one).  Writes the
+    oracle's solution and the background cell of every oracle cell to an .npz file (for the error
+    of the GPU solutions against the oracle) and returns its path with the timings."""
+    import numpy as np
     from oracle import krylov as K
     from oracle import multigrid as MG
     prob = WORKLOADS[workload](seed)
@@ -70,26 +77,23 @@ def cpu_worker(workload: str, seed: int, budget_s: float, full: bool) -> dict:
     F = H.finest
     b = F.disc.rhs()
     setup_s = time.perf_counter() - t0
-    steps, spent = 0, 0.0
-    while spent < budget_s:
+    times, its, x, info = [], [], None, None
+    while not times or sum(times) < budget_s:
         t0 = time.perf_counter()
-        K.fgmres(lambda v: F.A @ v, H.vcycle, b, tol=TOL, m=RESTART, max_it=2)
-        spent += time.perf_counter() - t0
-        steps += 2
-    out = dict(ms_per_iteration=1e3 * spent / steps, iterations_sampled=steps, setup_s=setup_s, n_dof=F.N)
-    if full:
-        t0 = time.perf_counter()
-        _x, info = K.fgmres(lambda v: F.A @ v, H.vcycle, b, tol=TOL, m=RESTART, max_it=MAX_IT)
-        out.update(full_iterations=info.iterations, full_solve_ms=1e3 * (time.perf_counter() - t0),
-                   converged=info.converged)
-    return out
+        x, info = K.fgmres(lambda v: F.A @ v, H.vcycle, b, tol=TOL, m=RESTART, max_it=MAX_IT)
+        times.append(time.perf_counter() - t0)
+        its.append(info.iterations)
+    fd, path = tempfile.mkstemp(suffix=".npz")
+    os.close(fd)
+    np.savez(path, x=x, active_cells=F.geom.active_cells, nb=F.nb)
+    return dict(solve_ms=1e3 * statistics.mean(times), solves=len(times), iterations=its, setup_s=setup_s,
+                n_dof=F.N, converged=bool(info.converged), solution=path)
 
 
-def start_cpu_worker(workload, seed, budget_s, full=False):
+def start_cpu_worker(workload, seed, budget_s):
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
                CUDA_VISIBLE_DEVICES="")
-    cmd = [sys.executable, os.path.abspath(__file__), "--cpu-worker", workload, str(seed), str(budget_s),
-           "1" if full else "0"]
+    cmd = [sys.executable, os.path.abspath(__file__), "--cpu-worker", workload, str(seed), str(budget_s)]
     return subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.PIPE, env=env, cwd=ROOT)
 
 
@@ -200,6 +204,121 @@ def reduce_max(value: float, device: str = "cuda") -> float:
     return float(t.item())
 
 
+def timed_solves(torch, solver, b, x, n, flush):
+    """n solves from x = 0 after an L2 flush each, CUDA events on the current stream: (ms list,
+    info list)."""
+    ts, infos = [], []
+    for _ in range(n):
+        x.zero_()
+        flush()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        info = solver.solve(b, x, tol=TOL, restart=RESTART, max_it=MAX_IT)
+        e1.record()
+        e1.synchronize()
+        ts.append(e0.elapsed_time(e1))
+        infos.append(info)
+    return ts, infos
+
+
+def settings(prob) -> dict:
+    """The discretisation and solver settings a workload runs with."""
+    return {"sigma_F": f"{prob.sigma_face_c} (p_l+1)^2/h_l", "sigma_Gamma": f"{prob.sigma_bnd_c} (p_l+1)^2/h_l",
+            "lambda": prob.lam, "active_test": ">=" if prob.lam_inclusive else ">", "alpha": prob.alpha,
+            "extension": "u(x~)+d.grad u(x~) (first-order Taylor)" if prob.extension == 0
+            else "cell polynomial at x~+d (full order)",
+            "pre_smooth": prob.pre_smooth, "post_smooth": prob.post_smooth, "ssor_each": prob.ssor_each,
+            "omega": prob.omega, "omega_p3": prob.omega_p3, "coarsest_n": prob.coarsest_n}
+
+
+def smoother_bytes(w: int, N: int, n_bnd: int, npc: int, n_sface: int, nq: int, dim: int) -> float:
+    """Algorithmic bytes of one full block Gauss-Seidel sweep: f read, u read, u written (3wN; the
+    neighbours' values are counted once), the boundary cells' dense inverses and the shift vectors
+    of the surrogate faces."""
+    return 3 * w * N + n_bnd * npc * npc * w + n_sface * nq * dim * w
+
+
+def apply_bytes(w: int, N: int, n_sface: int, nq: int, dim: int) -> float:
+    """Algorithmic bytes of one operator apply: x read, y written, the surrogate-face shift vectors."""
+    return 2 * w * N + n_sface * nq * dim * w
+
+
+def large_mesh_rooflines(torch, S, hbm, flush, reps=10) -> list:
+    """FP32 operator and smoother kernels on meshes whose vectors exceed L2, each launch after an L2
+    flush: achieved GB/s from the algorithmic bytes, against the measured HBM copy bandwidth."""
+    rows = []
+    cases = (("star2d p=2 2048^2", W.star2d_p2(2048, 0), 2), ("sphere3d p=2 128^3", W.sphere3d(128, 2, 0), 2),
+             ("ellipsoid3d p=3 96^3", W.ellipsoid3d_p3(96, 0), 1))
+    for label, prob, nlev in cases:
+        g = S.Solver(prob, "f32")
+        L = g.num_levels - 1
+        for level in range(L, L - nlev, -1):
+            inf = g.info(level)
+            N = inf["n_dof"]
+            npc = (inf["p"] + 1) ** prob.dim
+            nq = (inf["p"] + 1) ** (prob.dim - 1)
+            ngrp = prob.dim + 1                  # launches per sweep (colour groups)
+            f = torch.rand(N, device="cuda")
+            u = torch.rand_like(f)
+            y = torch.empty_like(f)
+            t_apply = event_time(torch, lambda: g.apply(f, y, level=level), reps, flush)
+            t_smooth = event_time(torch, lambda: g.smooth(f, u, level=level), reps, flush) / ngrp
+            b_apply = apply_bytes(4, N, inf["n_sface"], nq, prob.dim)
+            b_smooth = smoother_bytes(4, N, inf["n_boundary"], npc, inf["n_sface"], nq, prob.dim) / ngrp
+            for kern, b, t in (("apply", b_apply, t_apply), ("smoother, mean launch of a sweep", b_smooth, t_smooth)):
+                gbs = b / t / 1e6
+                rows.append({"workload": label, "level": f"{inf['n']}^{prob.dim} p={inf['p']}", "n_dof": N,
+                             "kernel": kern, "bytes": int(b), "ms": round(t, 5), "GB/s": round(gbs, 1),
+                             "frac": round(gbs / hbm, 3)})
+            del f, u, y
+        g.close()
+        torch.cuda.empty_cache()
+    return rows
+
+
+def other_workloads(torch, S, flush, n) -> dict:
+    """The other benchmark configurations at full size: FP32-V-cycle and FP64-V-cycle solves (n
+    timed each after one warm-up), iterations and residuals."""
+    out = {}
+    for name in ("disk2d_p1_n32", "sphere3d_p1_n64", "sphere3d_p2_n64", "ellipsoid3d_p3_n96"):
+        prob = WORKLOADS[name](0)
+        res = {"description": DESCRIPTION[name], "settings": settings(prob)}
+        for prec in ("f32", "f64"):
+            g = S.Solver(prob, prec)
+            b = g.rhs()
+            x = torch.zeros_like(b)
+            timed_solves(torch, g, b, x, 1, flush)
+            ts, infos = timed_solves(torch, g, b, x, n, flush)
+            res["n_dof"] = b.numel()
+            res[prec] = {"ms": round(statistics.mean(ts), 4), "iterations": infos[-1].iterations,
+                         "converged": all(i.converged for i in infos),
+                         "true_rel_residual": max(i.true_rel_residual for i in infos)}
+            g.close()
+        res["speedup_fp32_over_fp64_vcycle"] = round(res["f64"]["ms"] / res["f32"]["ms"], 3)
+        out[name] = res
+        torch.cuda.empty_cache()
+    return out
+
+
+def error_vs_oracle(solver, x, path) -> float | None:
+    """||x - x_oracle|| / ||x_oracle|| with the oracle's solution from the CPU worker's file, mapped
+    from the library's compact layout to the oracle's cell order by background cell index."""
+    import numpy as np
+    try:
+        d = np.load(path)
+    except OSError:
+        return None
+    xo, act, nb = d["x"], d["active_cells"], int(d["nb"])
+    n, dim = solver.prob.n, solver.prob.dim
+    c = solver.layout()
+    lin = c[:, 0].astype(np.int64) + n * c[:, 1].astype(np.int64) + (n * n * c[:, 2].astype(np.int64) if dim == 3 else 0)
+    pos = {int(v): i for i, v in enumerate(act)}
+    cells = np.array([pos[int(v)] for v in lin])
+    xg = x.cpu().numpy().reshape(-1, nb)
+    xo = xo.reshape(-1, nb)[cells]
+    return float(np.linalg.norm(xg - xo) / np.linalg.norm(xo))
+
+
 def run_ours(args) -> dict | None:
     import torch
     import torch.distributed as dist
@@ -226,46 +345,37 @@ def run_ours(args) -> dict | None:
     def flush():
         flush_buf.fill_(1.0)
 
-    def solve_step(solver):
-        x.zero_()
-        flush()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record()
-        info = solver.solve(b, x, tol=TOL, restart=RESTART, max_it=MAX_IT)
-        e1.record()
-        e1.synchronize()
-        return e0.elapsed_time(e1), info
-
     for _ in range(args.warmup):
-        solve_step(s32)
-        solve_step(s64)
+        timed_solves(torch, s32, b, x, 1, flush)
+        timed_solves(torch, s64, b, x, 1, flush)
     # ---- timed region: K FP32-V-cycle solves
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
     clocks = ClockSampler(local)
     launches0 = S.kernel_launches()
-    times32, infos32 = [], []
-    for _ in range(args.steps):
-        ms, info = solve_step(s32)
-        times32.append(ms)
-        infos32.append(info)
+    times32, infos32 = timed_solves(torch, s32, b, x, args.steps, flush)
     launches = S.kernel_launches() - launches0
     torch.cuda.synchronize()
     clk = clocks.stop()
     if world > 1:
         dist.barrier()
     total_ms = reduce_max(sum(times32), "cuda")
-    # ---- FP64 V-cycle solves (the plain variant), same workload
     x32 = x.clone()                              # the last FP32-V-cycle solution
-    times64, infos64 = [], []
-    for _ in range(args.steps):
-        ms, info = solve_step(s64)
-        times64.append(ms)
-        infos64.append(info)
-    # FP32-V-cycle solution against the FP64-V-cycle one (which matches the FP64 oracle to 1e-10
-    # on the parity-test meshes); both are solved to the same FP64 residual tolerance
-    err_vs_fp64 = float(torch.linalg.norm(x32 - x) / torch.linalg.norm(x))
+    # ---- FP64 V-cycle solves (the plain variant), same workload
+    times64, infos64 = timed_solves(torch, s64, b, x, args.steps, flush)
+    x64 = x.clone()
+    # FP32-V-cycle solution against the FP64-V-cycle one; both are solved to the same FP64 residual
+    err_vs_fp64 = float(torch.linalg.norm(x32 - x64) / torch.linalg.norm(x64))
+    # ---- the FP32 V-cycle under FGMRES with the plain FP64 basis and FP64 operator (krylov_basis 1)
+    sb1 = S.Solver(prob, "f32", krylov_basis=1)
+    timed_solves(torch, sb1, b, x, 1, flush)
+    tb1, ib1 = timed_solves(torch, sb1, b, x, args.steps, flush)
+    fp64_basis = {"ms": round(statistics.mean(tb1), 4), "iterations": [i.iterations for i in ib1],
+                  "converged": all(i.converged for i in ib1),
+                  "true_rel_residual": max(i.true_rel_residual for i in ib1),
+                  "variant": "FP32 V-cycle, FGMRES(30) with FP64 basis, FP64 Gram-Schmidt and FP64 operator"}
+    sb1.close()
     # ---- the same workload with the full-order boundary extension (cell polynomial at x~ + d)
     # instead of the first-order Taylor term, FP32 V-cycle
     full_ext = None
@@ -273,21 +383,11 @@ def run_ours(args) -> dict | None:
         sfe = S.Solver(prob.replace(extension=1), "f32")
         bfe = sfe.rhs()
         xfe = torch.zeros_like(bfe)
-
-        def fe_step():
-            xfe.zero_()
-            flush()
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record()
-            inf = sfe.solve(bfe, xfe, tol=TOL, restart=RESTART, max_it=MAX_IT)
-            e1.record()
-            e1.synchronize()
-            return e0.elapsed_time(e1), inf
-        fe_step()
-        fe = [fe_step() for _ in range(args.steps)]
-        full_ext = {"ms": round(statistics.mean(t for t, _ in fe), 4), "iterations": [i.iterations for _, i in fe],
-                    "converged": all(i.converged for _, i in fe),
-                    "true_rel_residual": max(i.true_rel_residual for _, i in fe)}
+        timed_solves(torch, sfe, bfe, xfe, 1, flush)
+        tf, fe = timed_solves(torch, sfe, bfe, xfe, args.steps, flush)
+        full_ext = {"ms": round(statistics.mean(tf), 4), "iterations": [i.iterations for i in fe],
+                    "converged": all(i.converged for i in fe),
+                    "true_rel_residual": max(i.true_rel_residual for i in fe)}
         sfe.close()
     # ---- learned variant: the boundary-cell MLP trained (untimed) on pairs collected from the
     # stationary V-cycle iteration on this hierarchy, attached with the fallback rule at the
@@ -302,12 +402,8 @@ def run_ours(args) -> dict | None:
         its_plain = infos32[-1].iterations
         rate = infos32[-1].true_rel_residual ** (1.0 / max(its_plain, 1))
         s32.attach_mlp(mlp, 1.0, fallback_rate=rate)
-        solve_step(s32)
-        tl, il = [], []
-        for _ in range(args.steps):
-            ms_, inf_ = solve_step(s32)
-            tl.append(ms_)
-            il.append(inf_)
+        timed_solves(torch, s32, b, x, 1, flush)
+        tl, il = timed_solves(torch, s32, b, x, args.steps, flush)
         s32.attach_mlp(None)
         learned = {"ms": round(statistics.mean(tl), 4), "iterations": [i.iterations for i in il],
                    "converged": all(i.converged for i in il), "fallback": [i.learned_fallback for i in il],
@@ -331,14 +427,14 @@ def run_ours(args) -> dict | None:
     # FGMRES).  Algorithmic bytes count every vector once; flops are the method's FMAs x 2.
     info = s32.info()
     nb = (info["p"] + 1) ** prob.dim
+    nq = (info["p"] + 1) ** (prob.dim - 1)
     r32 = torch.rand(N, device="cuda", dtype=torch.float32)
     u32 = torch.rand_like(r32)
     y32 = torch.empty_like(r32)
-    x64 = torch.rand(N, device="cuda", dtype=torch.float64)
-    y64 = torch.empty_like(x64)
+    xr64 = torch.rand(N, device="cuda", dtype=torch.float64)
+    y64 = torch.empty_like(xr64)
     nv = 27                                      # Gram-Schmidt width at the last step of the bench solve
     V64 = torch.rand((nv, N), device="cuda", dtype=torch.float64)
-    geo_bytes = info["n_sface"] * (info["p"] + 1) ** (prob.dim - 1) * prob.dim
     ngrp = prob.dim + 1                          # smoother launches per sweep (colour groups)
     # the p = 1 level on the same mesh (one below the finest), whose smoother is the kernel with
     # the largest share of the solve (three p = 1 levels, two sweeps of d + 1 launches per V-cycle)
@@ -346,29 +442,28 @@ def run_ours(args) -> dict | None:
     info1 = s32.info(Lp1)
     N1 = info1["n_dof"]
     nb1 = (info1["p"] + 1) ** prob.dim
+    nq1 = (info1["p"] + 1) ** (prob.dim - 1)
     r1 = torch.rand(N1, device="cuda", dtype=torch.float32)
     u1 = torch.rand_like(r1)
-    geo1 = info1["n_sface"] * (info1["p"] + 1) ** (prob.dim - 1) * prob.dim
     t_smooth1 = event_time(torch, lambda: s32.smooth(r1, u1, level=Lp1), 20, flush) / ngrp
     t_apply32 = event_time(torch, lambda: s32.apply(r32, y32), 20, flush)
-    t_apply64 = event_time(torch, lambda: s64.apply(x64, y64), 20, flush)
+    t_apply64 = event_time(torch, lambda: s64.apply(xr64, y64), 20, flush)
     t_smooth = event_time(torch, lambda: s32.smooth(r32, u32), 20, flush) / ngrp
-    t_dots = event_time(torch, lambda: s64.dots(V64, x64), 20, flush)
+    t_dots = event_time(torch, lambda: s64.dots(V64, xr64), 20, flush)
     hbm, src = peaks()
     fp64_tflops = 152 * 2.07e9 * 2 * 2 / 1e12    # SMs x max clock x 2 FP64 FMA/clk/SM x 2 flop
     kernels = {
+        # one block Gauss-Seidel sweep moves f, u read, u written (3wN), the dense inverses of the
+        # boundary cells and their face data; it takes d + 1 launches (colour groups), and the unit
+        # is their mean
         f"k_smooth_cell<{prob.dim},{info1['p'] + 1},float> ({info1['n']}^{prob.dim} p={info1['p']} level, mean launch of a sweep)":
-            ("hbm", ((prob.dim + 2) * 4 * N1 + info1["n_boundary"] * nb1 * nb1 * 4 + 4 * geo1) / ngrp, t_smooth1),
-        # one block Gauss-Seidel sweep of the finest level (p) moves f (N), u of the d neighbouring
-        # colours of every cell (d N), u written (N), the dense inverses of the boundary cells and
-        # their face data; it takes d + 1 launches (colour groups), and the unit is their mean
+            ("hbm", smoother_bytes(4, N1, info1["n_boundary"], nb1, info1["n_sface"], nq1, prob.dim) / ngrp, t_smooth1),
         f"k_smooth_cell<{prob.dim},{info['p'] + 1},float> (finest level, mean launch of a sweep)":
-            ("hbm", ((prob.dim + 2) * 4 * N + info["n_boundary"] * nb * nb * 4 + 4 * geo_bytes) / ngrp, t_smooth),
+            ("hbm", smoother_bytes(4, N, info["n_boundary"], nb, info["n_sface"], nq, prob.dim) / ngrp, t_smooth),
         f"k_apply_cell<{prob.dim},{info['p'] + 1},float> (FP32 operator, finest level)":
-            ("hbm", 2 * 4 * N + 4 * geo_bytes, t_apply32),
+            ("hbm", apply_bytes(4, N, info["n_sface"], nq, prob.dim), t_apply32),
         f"k_apply<{prob.dim},{info['p'] + 1},double> (FP64 operator, finest level)":
-            ("hbm", 2 * 8 * N + 8 * geo_bytes, t_apply64),
-        # first Gram-Schmidt sweep h = V^T w at width 27, plus its partial-sum reduction
+            ("hbm", apply_bytes(8, N, info["n_sface"], nq, prob.dim), t_apply64),
         # sbm_dots: the FP64 multi-vector dot product (the solver's own sweeps run in double-float)
         "k_multi_dot<27> (FP64, sbm_dots)": ("alu", 2 * nv * N, t_dots),
     }
@@ -386,6 +481,13 @@ def run_ours(args) -> dict | None:
     dominant = next(iter(kernels))
     roof = dict(rooflines[dominant])
     roof.update(kernel=dominant, peak_source=src, traffic=committed_traffic(args.workload, dominant))
+    del r32, u32, y32, xr64, y64, V64, r1, u1
+    torch.cuda.empty_cache()
+    # ---- the other benchmark configurations, and the kernels on meshes larger than L2
+    others = large = None
+    if not args.no_extra:
+        others = other_workloads(torch, S, flush, 5)
+        large = large_mesh_rooflines(torch, S, hbm, flush)
     if rank != 0:
         return None
     cpu = finish_cpu_worker(cpu_proc) if cpu_proc is not None else None
@@ -396,12 +498,16 @@ def run_ours(args) -> dict | None:
         "warmup": args.warmup, "ms_per_step": round(ms32, 4), "higher_is_better": False, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
         "config": {"workload": args.workload, "description": DESCRIPTION.get(args.workload, args.workload),
-                   "n_dof": N, "levels": s32.num_levels, "variant": "FP32 V-cycle, FP64 FGMRES(30)",
+                   "n_dof": N, "levels": s32.num_levels,
+                   "variant": "FP32 V-cycle; FGMRES(30) with a double-float basis (FP32 pairs, ~48-bit "
+                              "significands), Gram-Schmidt and Arnoldi operator on the FP32 pipes; FP64 true residual",
+                   "settings": settings(prob),
                    "l2": "flushed (256 MB write) before every step", "parallelism": f"replicas x{world}"},
         "iterations": its32, "converged": all(i.converged for i in infos32),
         "true_rel_residual": max(i.true_rel_residual for i in infos32),
         "fp64_vcycle": {"ms": round(statistics.mean(times64), 4), "iterations": [i.iterations for i in infos64],
                         "converged": all(i.converged for i in infos64)},
+        "fp64_basis": fp64_basis,
         "rel_l2_error_vs_fp64_vcycle_solution": err_vs_fp64,
         "speedup_fp32_over_fp64_vcycle": round(statistics.mean(times64) / ms32, 3),
         "learned": learned,
@@ -415,14 +521,19 @@ def run_ours(args) -> dict | None:
         "gpu_launches": int(launches),
         "roofline": roof,
         "rooflines": rooflines,
+        "rooflines_large_meshes": large,
+        "other_workloads": others,
     }
     if cpu is not None:
-        solve_ms = cpu["ms_per_iteration"] * statistics.mean(its32)
-        out["cpu_baseline"] = {"value": round(solve_ms, 1), "unit": "ms", "cores": 1, "kind": "oracle",
-                               "sample": f"{cpu['iterations_sampled']} FGMRES iterations of the FP64 oracle on the "
-                                         f"same workload ({cpu['ms_per_iteration']:.1f} ms each), scaled to the "
-                                         f"{statistics.mean(its32):.1f} iterations of the GPU solve; oracle set-up "
-                                         f"{cpu['setup_s']:.0f} s not timed"}
+        path = cpu["solution"]
+        out["rel_l2_error_vs_oracle"] = {"fp32_vcycle": error_vs_oracle(s32, x32, path),
+                                         "fp64_vcycle": error_vs_oracle(s32, x64, path),
+                                         "oracle_iterations": cpu["iterations"][-1]}
+        os.unlink(path)
+        out["cpu_baseline"] = {"value": round(cpu["solve_ms"], 1), "unit": "ms", "cores": 1, "kind": "oracle",
+                               "sample": f"{cpu['solves']} whole FGMRES(30) solves to 1e-8 of the same workload "
+                                         f"by the FP64 oracle on one host core ({cpu['iterations'][-1]} iterations "
+                                         f"each), mean; oracle set-up {cpu['setup_s']:.0f} s not timed"}
     return out
 
 
@@ -532,42 +643,14 @@ def run_learned_heldout(args) -> dict:
 
 
 def run_roofline_sweep(args) -> dict:
-    """Operator and smoother kernels on meshes whose FP32 vectors exceed L2 several times (the
-    bench workload's fit in L2): CUDA-event time per launch after an L2 flush, algorithmic bytes
-    (every vector entry once), achieved GB/s against the measured HBM copy bandwidth."""
+    """Operator and smoother kernels on meshes whose FP32 vectors exceed L2 (the bench workload's
+    fit in L2): CUDA-event time per launch after an L2 flush, algorithmic bytes (every vector
+    entry once), achieved GB/s against the measured HBM copy bandwidth."""
     import torch
     import paper_2506_12899_gb300 as S
     hbm, src = peaks()
     flush_buf = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
-
-    def flush():
-        flush_buf.fill_(1.0)
-
-    rows = []
-    for label, prob in (("star2d p=2 2048^2", W.star2d_p2(2048, 0)), ("sphere3d p=2 128^3", W.sphere3d(128, 2, 0))):
-        g = S.Solver(prob, "f32")
-        L = g.num_levels - 1
-        for level in (L, L - 1):
-            inf = g.info(level)
-            N = inf["n_dof"]
-            npc = (inf["p"] + 1) ** prob.dim
-            ngrp = prob.dim + 1                  # launches per sweep (colour groups)
-            geo = 4 * inf["n_sface"] * (inf["p"] + 1) ** (prob.dim - 1) * prob.dim
-            f = torch.rand(N, device="cuda")
-            u = torch.rand_like(f)
-            y = torch.empty_like(f)
-            t_apply = event_time(torch, lambda: g.apply(f, y, level=level), 10, flush)
-            t_smooth = event_time(torch, lambda: g.smooth(f, u, level=level), 10, flush) / ngrp
-            b_apply = 2 * 4 * N + geo
-            b_smooth = ((prob.dim + 2) * 4 * N + inf["n_boundary"] * npc * npc * 4 + geo) / ngrp
-            for kern, b, t in (("apply", b_apply, t_apply), ("smoother, mean launch of a sweep", b_smooth, t_smooth)):
-                gbs = b / t / 1e6
-                rows.append({"workload": label, "level": f"{inf['n']}^{prob.dim} p={inf['p']}", "n_dof": N,
-                             "kernel": kern, "bytes": int(b), "ms": round(t, 5), "GB/s": round(gbs, 1),
-                             "frac": round(gbs / hbm, 3)})
-            del f, u, y
-        g.close()
-        torch.cuda.empty_cache()
+    rows = large_mesh_rooflines(torch, S, hbm, lambda: flush_buf.fill_(1.0))
     return {"experiment": "FP32 operator / smoother roofline sweep (vectors > L2)", "peak_gbs": hbm,
             "peak_source": src, "l2": "flushed (256 MB write) before every launch", "rows": rows}
 
@@ -604,46 +687,43 @@ def run_paper_replica(args) -> dict:
 
 
 def run_reference(args) -> dict | None:
-    """The reference arm: the CPU FP64 oracle on the host cores (no GPU)."""
+    """The reference arm: the CPU FP64 oracle on the host cores (no GPU); each step is one whole
+    FGMRES(30) solve to 1e-8 from x = 0 (set-up untimed)."""
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return None
-    os.environ.setdefault("OMP_NUM_THREADS", "1")
     from oracle import krylov as K
     from oracle import multigrid as MG
     prob = WORKLOADS[args.workload](0)
     H = MG.Hierarchy(prob)
     F = H.finest
     b = F.disc.rhs()
-    # the oracle's own iteration count to 1e-8 is measured once (not timed), then each step times
-    # a bounded sample of two FGMRES iterations and scales it to that count
-    _x, info = K.fgmres(lambda v: F.A @ v, H.vcycle, b, tol=TOL, m=RESTART, max_it=MAX_IT)
-    its = info.iterations
-    per_it = []
+    times, info = [], None
     for k in range(args.warmup + args.steps):
         t0 = time.perf_counter()
-        K.fgmres(lambda v: F.A @ v, H.vcycle, b, tol=TOL, m=RESTART, max_it=2)
+        _x, info = K.fgmres(lambda v: F.A @ v, H.vcycle, b, tol=TOL, m=RESTART, max_it=MAX_IT)
         if k >= args.warmup:
-            per_it.append((time.perf_counter() - t0) / 2)
-    ms = 1e3 * statistics.mean(per_it) * its
+            times.append(time.perf_counter() - t0)
+    ms = 1e3 * statistics.mean(times)
+    cores = 1                                    # single-threaded BLAS, scalar Python loops
     return {"impl": "reference", "metric": METRIC, "value": round(ms, 1), "unit": "ms", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 1), "higher_is_better": False,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": args.workload, "description": DESCRIPTION.get(args.workload, args.workload),
-                       "n_dof": F.N, "variant": "CPU FP64 oracle: assembled CSR, coloured block GS V-cycle, "
-                                                "FGMRES(30)"},
-            "iterations": its, "converged": info.converged,
-            "cpu_baseline": {"value": round(ms, 1), "unit": "ms", "cores": 1, "kind": "oracle",
-                             "sample": f"each step: 2 FGMRES iterations of the oracle scaled to its {its} "
-                                       f"iterations to 1e-8"},
+                       "n_dof": F.N, "settings": settings(prob),
+                       "variant": "CPU FP64 oracle: assembled CSR, coloured block GS V-cycle, FGMRES(30)"},
+            "iterations": info.iterations, "converged": info.converged,
+            "cpu_baseline": {"value": round(ms, 1), "unit": "ms", "cores": cores, "kind": "oracle",
+                             "sample": f"each step one whole FGMRES(30) solve of the workload to 1e-8 "
+                                       f"({info.iterations} iterations); oracle set-up not timed"},
             "e2e": {"value": round(ms, 1), "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
 def main():
     if len(sys.argv) > 1 and sys.argv[1] == "--cpu-worker":
-        workload, seed, budget, full = sys.argv[2], int(sys.argv[3]), float(sys.argv[4]), sys.argv[5] == "1"
-        print(json.dumps(cpu_worker(workload, seed, budget, full)))
+        workload, seed, budget = sys.argv[2], int(sys.argv[3]), float(sys.argv[4])
+        print(json.dumps(cpu_worker(workload, seed, budget)))
         return
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -651,9 +731,11 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="star2d_p2_n512", choices=sorted(WORKLOADS))
-    ap.add_argument("--cpu-budget", type=float, default=15.0, help="seconds of oracle solve time to sample")
+    ap.add_argument("--cpu-budget", type=float, default=10.0, help="seconds of whole oracle solves to time")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-correction variant")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="skip the other workloads and the large-mesh rooflines in the bench line")
     ap.add_argument("--profile", choices=["solve", "kernels"], help="fixed launches for an ncu capture")
     ap.add_argument("--profile-n", type=int, default=2048, help="cells per direction for --profile kernels")
     ap.add_argument("--profile-shape", default="star2d", choices=["star2d", "sphere3d"],

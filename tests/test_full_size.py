@@ -13,7 +13,8 @@ the one-CTA tail for the small p = 1 levels, the staged Gram-Schmidt sweeps).
 
 Tolerances are the ones of tests/test_gpu_parity.py: FP64 operator 1e-12 relative; FP32 operator
 2e-6 |A||x|; FP32 smoother 2e-4 relative (inputs rounded to FP32 and block inverses amplified by
-cond(A_KK)); FP64 smoother n_p eps cond(A_KK) (floor 1e-12); FP32 V-cycle 1e-4 relative L2; FP64
+cond(A_KK)); FP64 smoother sweep (d+1) 2 n_p eps cond(A_KK) over the whole level (`sweep_tol`),
+n_p eps cond(A_KK) for a single cell update (floor 1e-12); FP32 V-cycle 1e-4 relative L2; FP64
 FGMRES equal iteration counts and 1e-10 relative L2.
 """
 import numpy as np
@@ -37,6 +38,16 @@ def block_tol(levels):
     kap = max(np.linalg.cond(lev.disc.diag).max() for lev in levels)
     nb = max(lev.nb for lev in levels)
     return max(1e-12, nb * 2.2e-16 * kap)
+
+
+def sweep_tol(lev):
+    """FP64 bound of one colour sweep (Eq. 16) over the d + 1 colour groups: each group forms the
+    residual of its cells and applies the block inverses (rounding ~ 2 n_p eps cond(A_KK), the
+    interior cells by fast diagonalisation on the GPU and by LU on the oracle side), and passes its
+    error on to the later groups through the couplings A_KN; at full size the largest block
+    condition number (about 2.4e4 at 512^2 p = 2) is met in some cell of every group."""
+    kap = np.linalg.cond(lev.disc.diag).max()
+    return max(1e-12, (lev.prob.dim + 1) * 2 * lev.nb * 2.2e-16 * kap)
 
 
 @pytest.fixture(scope="module")
@@ -72,7 +83,7 @@ def test_star512_smoother_sweeps(star512):
             assert err32 <= 2e-4, (l, reverse, err32)
             u64 = P.gpu.smooth(P.to_gpu(f, l), P.to_gpu(u0, l), level=l, reverse=reverse)
             err64 = rel_max(P.to_oracle(u64, l), uo)
-            assert err64 <= block_tol([lev]), (l, reverse, err64)
+            assert err64 <= sweep_tol(lev), (l, reverse, err64, sweep_tol(lev))
 
 
 def test_star512_vcycle(star512):
