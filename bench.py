@@ -541,9 +541,9 @@ def run_profile(args) -> None:
     """Fixed launch sequences for ncu captures (numbers printed under ncu are not bench values).
     solve:   one warm-up and one FP32-V-cycle FGMRES solve of --workload; prints how many of the
              library's kernels the warm-up launched (the ncu skip count) and how many the solve did.
-    kernels: 2D p=2 star at --profile-n^2 cells (or the 3D sphere of degree --profile-p at
-             --profile-n^3): one FP32 operator apply, one finest-level smoother sweep (d+1 colour-group
-             launches) and one V-cycle."""
+    kernels: 2D p=2 star at --profile-n^2 cells (or the 3D sphere of degree --profile-p, or the
+             3D p=3 ellipsoid, at --profile-n^3): one FP32 operator apply, one finest-level smoother
+             sweep (d+1 colour-group launches) and one V-cycle."""
     import torch
     import paper_2506_12899_gb300 as S
     if args.profile == "solve":
@@ -560,9 +560,11 @@ def run_profile(args) -> None:
         print("SOLVE_LAUNCHES", S.kernel_launches() - l1, flush=True)
         print("ITERATIONS", info.iterations, "CONVERGED", info.converged, flush=True)
     else:
-        prob = (W.star2d_p2(args.profile_n, 0) if args.profile_shape == "star2d"
-                else W.sphere3d(args.profile_n, args.profile_p, 0))
-        g = S.Solver(prob, "f32", tail_max_cells=args.tail_max_cells, tail_cluster_ctas=args.tail_cluster)
+        prob = {"star2d": lambda: W.star2d_p2(args.profile_n, 0),
+                "sphere3d": lambda: W.sphere3d(args.profile_n, args.profile_p, 0),
+                "ellipsoid3d": lambda: W.ellipsoid3d_p3(args.profile_n, 0)}[args.profile_shape]()
+        g = S.Solver(prob, "f32", tail_max_cells=args.tail_max_cells, tail_cluster_ctas=args.tail_cluster,
+                     staged_min_cells=args.staged_min)
         N = g.n_dof()
         gen = torch.Generator(device="cuda").manual_seed(0)
         f = torch.rand(N, device="cuda", generator=gen)
@@ -738,8 +740,10 @@ def main():
                     help="skip the other workloads and the large-mesh rooflines in the bench line")
     ap.add_argument("--profile", choices=["solve", "kernels"], help="fixed launches for an ncu capture")
     ap.add_argument("--profile-n", type=int, default=2048, help="cells per direction for --profile kernels")
-    ap.add_argument("--profile-shape", default="star2d", choices=["star2d", "sphere3d"],
-                    help="--profile kernels: 2D p=2 star or 3D sphere (degree --profile-p)")
+    ap.add_argument("--profile-shape", default="star2d", choices=["star2d", "sphere3d", "ellipsoid3d"],
+                    help="--profile kernels: 2D p=2 star, 3D sphere (degree --profile-p) or 3D p=3 ellipsoid")
+    ap.add_argument("--staged-min", type=int, default=0,
+                    help="--profile kernels: staged thread-per-cell kernels from this many cells (<0 never)")
     ap.add_argument("--profile-p", type=int, default=2)
     ap.add_argument("--tail-max-cells", type=int, default=0, help="--profile kernels: cluster-tail cut-off")
     ap.add_argument("--tail-cluster", type=int, default=0, help="--profile kernels: cluster-tail CTAs")

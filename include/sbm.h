@@ -105,6 +105,10 @@ typedef struct {
                          /* double-float basis with the FP64 operator                             */
   int cell_kernel_min_cells; /* launches over at least this many cells use one thread per cell   */
                          /* when (p+1)^d <= 16; 0: always in FP32, never in FP64; < 0: never       */
+  int staged_min_cells;  /* FP32 operator and smoother launches over at least this many cells     */
+                         /* (2D p <= 3, 3D p <= 2) use the staged thread-per-cell kernels, whose  */
+                         /* CTA copies its cells and their face neighbours into shared memory     */
+                         /* first; 0: library default; < 0: never                                  */
   void* stream;          /* cudaStream_t for every launch of this context                        */
 } sbm_setup_desc;
 
@@ -215,6 +219,13 @@ int sbm_vcycle(void* ctx, int dtype, const void* r_dev, void* z_dev);
  * out_dev holds nv doubles. */
 int sbm_dots(void* ctx, const double* V_dev, long long ldv, int nv, const double* w_dev, long long n,
              double* out_dev);
+
+/* L2 error ||u - u_h||_{L2} over the active cells of the finest level (the surrogate domain), the
+ * error measure of the paper's convergence studies (Sec. 5.1, Sec. 5.4): u is the manufactured
+ * solution of sbm_setup_desc.exact, u_h the FP64 solution x_dev (compact layout, n_dof doubles),
+ * integrated cell by cell with the (p+3)-point tensor Gauss-Legendre rule.  Runs on the device
+ * (deterministic fixed-order sums), synchronises and writes the error to *err_host. */
+int sbm_l2_error(void* ctx, const double* x_dev, double* err_host);
 
 /* The three Gram-Schmidt sweeps of one FGMRES Arnoldi step (Sec. 3; two classical passes, CGS2)
  * on caller data, by the kernels sbm_solve uses:

@@ -28,7 +28,7 @@ ERRORS = {-1: "SBM_ERR_ARG", -2: "SBM_ERR_CUDA", -3: "SBM_ERR_SINGULAR_BLOCK", -
 # exported C symbols (checked by the tests against include/sbm.h)
 SYMBOLS = ("sbm_setup", "sbm_setup_host", "sbm_host_apply", "sbm_host_rhs", "sbm_destroy", "sbm_last_error", "sbm_kernel_launches", "sbm_num_levels", "sbm_info", "sbm_layout",
            "sbm_export_geometry", "sbm_rhs", "sbm_apply", "sbm_residual", "sbm_smooth", "sbm_restrict",
-           "sbm_prolong_add", "sbm_coarse_solve", "sbm_vcycle", "sbm_dots", "sbm_dots_noalloc", "sbm_gram_schmidt", "sbm_solve",
+           "sbm_prolong_add", "sbm_coarse_solve", "sbm_vcycle", "sbm_dots", "sbm_dots_noalloc", "sbm_gram_schmidt", "sbm_l2_error", "sbm_solve",
            "sbm_solve_host", "sbm_mlp_create", "sbm_mlp_destroy", "sbm_mlp_shape", "sbm_mlp_set_params",
            "sbm_mlp_get_params", "sbm_mlp_forward", "sbm_mlp_gradients", "sbm_mlp_num_samples",
            "sbm_mlp_clear_samples", "sbm_mlp_train", "sbm_mlp_save", "sbm_mlp_load", "sbm_learned_features",
@@ -56,7 +56,8 @@ class _Desc(ctypes.Structure):
                 ("post_smooth", ctypes.c_int), ("ssor_each", ctypes.c_int), ("omega", ctypes.c_double), ("omega_p3", ctypes.c_double),
                 ("vf_samples", ctypes.c_int), ("precision", ctypes.c_int), ("tail_max_cells", ctypes.c_int),
                 ("tail_cluster_ctas", ctypes.c_int), ("launch_overlap", ctypes.c_int),
-                ("krylov_basis", ctypes.c_int), ("cell_kernel_min_cells", ctypes.c_int), ("stream", ctypes.c_void_p)]
+                ("krylov_basis", ctypes.c_int), ("cell_kernel_min_cells", ctypes.c_int),
+                ("staged_min_cells", ctypes.c_int), ("stream", ctypes.c_void_p)]
 
 
 class _LevelInfo(ctypes.Structure):
@@ -120,6 +121,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.sbm_vcycle.argtypes = [vp, ip, vp, vp]
     lib.sbm_dots.argtypes = [vp, vp, ctypes.c_longlong, ip, vp, ctypes.c_longlong, vp]
     lib.sbm_gram_schmidt.argtypes = [vp, ip, vp, ip, vp, vp, vp, vp]
+    lib.sbm_l2_error.argtypes = [vp, vp, ctypes.POINTER(ctypes.c_double)]
     lib.sbm_dots_noalloc.argtypes = [vp, ctypes.c_longlong, ip, vp, ctypes.c_longlong, vp, vp]
     lib.sbm_solve.argtypes = [vp, vp, vp, dp, ip, ip, ctypes.POINTER(_SolveInfo)]
     lib.sbm_solve_host.argtypes = [vp, vp, vp, dp, ip, ip, ctypes.POINTER(_SolveInfo)]
@@ -169,7 +171,7 @@ def _check(code: int):
 
 def make_desc(prob, precision: int = SBM_F64, stream: int = 0, tail_max_cells: int = 0,
               cell_kernel_min_cells: int = 0, tail_cluster_ctas: int = 0, launch_overlap: int = 0,
-              krylov_basis: int = 0) -> _Desc:
+              krylov_basis: int = 0, staged_min_cells: int = 0) -> _Desc:
     d = _Desc()
     d.dim, d.n, d.p = prob.dim, prob.n, prob.p
     d.lo[:] = [float(v) for v in prob.lo]
@@ -191,6 +193,7 @@ def make_desc(prob, precision: int = SBM_F64, stream: int = 0, tail_max_cells: i
     d.launch_overlap = launch_overlap
     d.krylov_basis = krylov_basis
     d.cell_kernel_min_cells = cell_kernel_min_cells
+    d.staged_min_cells = staged_min_cells
     return d
 
 
@@ -199,7 +202,7 @@ class Solver:
 
     def __init__(self, prob, precision: str = "f64", stream=None, tail_max_cells: int = 0,
                  cell_kernel_min_cells: int = 0, tail_cluster_ctas: int = 0, launch_overlap: int = 0,
-                 krylov_basis: int = 0):
+                 krylov_basis: int = 0, staged_min_cells: int = 0):
         """tail_max_cells: coarse p = 1 levels with at most that many cells run as one launch
         (0: library default, every level that fits for FP32 and none for FP64; < 0: never) of
         tail_cluster_ctas CTAs (0 or 1: one CTA; 2..16: a thread-block cluster).
@@ -208,7 +211,8 @@ class Solver:
         FGMRES basis and Arnoldi operator (on the FP32 pipes), 1 FP64, 2 double-float basis with the
         FP64 operator.  cell_kernel_min_cells: launches over at least that many
         cells use one thread per cell (0: library default, < 0: never, 1: always where
-        (p+1)^d <= 16)."""
+        (p+1)^d <= 16).  staged_min_cells: FP32 operator and smoother launches over at least that
+        many cells use the staged thread-per-cell kernels (0: library default, < 0: never)."""
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("libsbm needs a CUDA device; no CPU fallback exists")
@@ -218,7 +222,7 @@ class Solver:
         self.precision = SBM_F32 if precision == "f32" else SBM_F64
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         desc = make_desc(prob, self.precision, self.stream.cuda_stream, tail_max_cells, cell_kernel_min_cells,
-                         tail_cluster_ctas, launch_overlap, krylov_basis)
+                         tail_cluster_ctas, launch_overlap, krylov_basis, staged_min_cells)
         ctx = ctypes.c_void_p()
         _check(self.lib.sbm_setup(ctypes.byref(desc), ctypes.byref(ctx)))
         self.ctx = ctx
@@ -328,6 +332,12 @@ class Solver:
         _check(self.lib.sbm_dots(self.ctx, self._vec(V), V.shape[1], V.shape[0], self._vec(w, torch.float64),
                                  w.numel(), self._vec(out, torch.float64)))
         return out
+
+    def l2_error(self, x) -> float:
+        """||u - u_h||_L2 over the finest active cells of the FP64 solution x (device)."""
+        e = ctypes.c_double()
+        _check(self.lib.sbm_l2_error(self.ctx, self._vec(x, self._torch.float64), ctypes.byref(e)))
+        return e.value
 
     def gram_schmidt(self, V, w, variant: int = 0):
         """(h1, h2, w2, |w2|) of the two classical Gram-Schmidt passes of an Arnoldi step, by the

@@ -204,6 +204,10 @@ struct Context {
   float2* gswdf = nullptr;         // [ldv] w, double-float
   double* gspartial = nullptr;
   double* gsdots = nullptr;        // [0,32) h1, [32,64) h2, [64] |w|, [65] 1.0, [128,161) column
+  // sbm_l2_error: background indices of the finest cells, partial sums, result
+  int* l2cell = nullptr;
+  double* l2partial = nullptr;
+  double* l2out = nullptr;
   // FGMRES runs on an internal non-blocking stream (the legacy default stream cannot be captured
   // into a graph), joined to the caller's stream with events.  Each Arnoldi step j of each
   // V-cycle precision is captured once into a CUDA graph and replayed.
@@ -447,6 +451,8 @@ Context* build_context(const sbm_setup_desc& d, bool device) {
     } else {
       L.P64.cell_min = L.P32.cell_min = d.cell_kernel_min_cells < 0 ? 0 : d.cell_kernel_min_cells;
     }
+    // staged thread-per-cell kernels (FP32): launches over at least staged_min cells
+    L.P32.staged_min = d.staged_min_cells == 0 ? 0 : (d.staged_min_cells < 0 ? 0 : d.staged_min_cells);
   }
   for (size_t l = 1; l < C->lv.size(); ++l) {
     C->lv[l].T64 = make_transfer<double>(C->lv[l - 1], C->lv[l]);
@@ -1323,6 +1329,35 @@ int sbm_dots(void* ctx, const double* V_dev, long long ldv, int nv, const double
       C->dots_scratch_len = need;
     }
     CUDA_TRY(launch_multi_dot(V_dev, (size_t)ldv, nv, w_dev, (size_t)n, C->dots_scratch, out_dev, 0, C->stream));
+    return SBM_OK;
+  });
+}
+
+int sbm_l2_error(void* ctx, const double* x_dev, double* err_host) {
+  Context* C = ctx_of(ctx);
+  if (C && C->host_only) return set_error(SBM_ERR_ARG, "host-only context");
+  if (!C || !x_dev || !err_host) return set_error(SBM_ERR_ARG, "bad argument");
+  return guarded([&]() -> int {
+    const HostLevel& H = C->lv.back().H;
+    const cudaStream_t s = C->stream;
+    if (!C->l2cell) {
+      C->l2cell = C->upload(H.cell);
+      C->l2partial = C->dalloc<double>((size_t)l2_error_blocks(H.n_act));
+      C->l2out = C->dalloc<double>(1);
+    }
+    L2ErrorParams E;
+    std::memset(&E, 0, sizeof(E));
+    E.n_act = H.n_act;
+    E.kind = C->desc.exact;
+    E.h = H.h;
+    for (int k = 0; k < 3; ++k) E.lo[k] = C->desc.lo[k];
+    const int m1 = H.p + 3;
+    gauss_legendre01(m1, E.xq, E.wq);
+    for (int q = 0; q < m1; ++q) lagrange_eval(H.n1, H.B.x, E.xq[q], E.V + q * kMaxN1, nullptr);
+    CUDA_TRY(launch_l2_error(H.dim, H.p, E, C->l2cell, x_dev, C->l2partial, C->l2out, s));
+    CUDA_TRY(cudaMemcpyAsync(C->host_pinned, C->l2out, sizeof(double), cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    *err_host = C->host_pinned[0];
     return SBM_OK;
   });
 }

@@ -610,6 +610,10 @@ cudaError_t launch_apply(int dim, int p, const LevelParams<R>& P, const TI* x, c
   if (P.n_act == 0) return cudaSuccess;
   // 3D p = 2 has a thread-per-cell operator for FP32 only (cell_kernels / cell_smoother)
   constexpr bool f32 = std::is_same<TI, float>::value && std::is_same<R, float>::value;
+  if constexpr (f32) {
+    if (staged_kernels(dim, p) && P.staged_min > 0 && P.n_act >= P.staged_min)
+      return launch_apply_staged(dim, p, P, x, f, y, mode, s);
+  }
   if ((f32 ? cell_kernels(dim, p) : cell_smoother(dim, p)) && P.cell_min > 0 && P.n_act >= P.cell_min)
     return launch_apply_cell<TI, R>(dim, p, P, x, f, y, mode, s);
 #define SBM_APPLY(D, N1)                                                                 \
@@ -628,6 +632,10 @@ cudaError_t launch_apply(int dim, int p, const LevelParams<R>& P, const TI* x, c
 template <typename R>
 cudaError_t launch_smooth(int dim, int p, const LevelParams<R>& P, int reverse, int zero_start, const R* f, R* u,
                           cudaStream_t s, int early) {
+  if constexpr (std::is_same<R, float>::value) {
+    if (staged_kernels(dim, p) && P.staged_min > 0 && P.n_act >= (1 << dim) * P.staged_min)
+      return launch_smooth_staged(dim, p, P, reverse, zero_start, f, u, s, early);
+  }
   if (cell_smoother(dim, p) && P.cell_min > 0 && P.n_act >= (1 << dim) * P.cell_min)
     return launch_smooth_cell<R>(dim, p, P, reverse, zero_start, f, u, s, early);
   if (reverse) zero_start = 0;

@@ -177,6 +177,15 @@ template <typename R>
 cudaError_t launch_resid_restrict_h_cell(int dim, const LevelParams<R>& P, const TransferParams<R>& T, const R* u,
                                         const R* f, R* rc, cudaStream_t s, int early);
 
+// Staged thread-per-cell kernels (staged_ops.cu), FP32 only: the CTA copies its cells and their
+// face neighbours into shared memory with coalesced asynchronous copies before the per-cell
+// arithmetic (2D p <= 3, 3D p <= 2).  Used for launches over >= LevelParams::staged_min cells.
+bool staged_kernels(int dim, int p);
+cudaError_t launch_apply_staged(int dim, int p, const LevelParams<float>& P, const float* x, const float* f,
+                                float* y, int mode, cudaStream_t s);
+cudaError_t launch_smooth_staged(int dim, int p, const LevelParams<float>& P, int reverse, int zero_start,
+                                 const float* f, float* u, cudaStream_t s, int early);
+
 // The V-cycle of levels 0..top (p = 1 h-levels) in one thread-block-cluster launch with the
 // level vectors in shared memory; z = M^{-1} r on level top.  cudaErrorNotSupported if the plan
 // has no cluster.
@@ -227,6 +236,13 @@ cudaError_t launch_restrict(int dim, int pf, int pc, const TransferParams<R>& T,
 template <typename R>
 cudaError_t launch_prolong(int dim, int pf, int pc, const TransferParams<R>& T, const R* ec, R* uf, cudaStream_t s,
                            int early = 0);
+
+// ||u - u_h||_L2 over the active cells of a level (error_ops.cu): per-block partial sums into
+// partial (l2_error_blocks(n_act) doubles), then out[0] on the device.  cell: [n_act][3] background
+// indices, x: FP64 solution in compact layout.
+int l2_error_blocks(int n_act);
+cudaError_t launch_l2_error(int dim, int p, const L2ErrorParams& E, const int* cell, const double* x,
+                            double* partial, double* out, cudaStream_t s);
 
 // e = Ainv r, dense FP64 matrix, N x N row-major.
 template <typename T>

@@ -98,6 +98,15 @@ struct LevelConsts {
   R inv_diag[kMaxN1 * kMaxN1 * kMaxN1];   // 1 / (h^(d-2) (lam_i + lam_j (+ lam_k))), x fastest
 };
 
+// Parameters of the L2-error kernel (error_ops.cu): finest level, (p+3)-point Gauss-Legendre rule on
+// [0, 1], the 1D Lagrange values V[q * kMaxN1 + k] = l_k(xq[q]) of the cell basis at its points.
+struct L2ErrorParams {
+  int n_act, kind;
+  double h, lo[3];
+  double xq[8], wq[8];
+  double V[8 * kMaxN1];
+};
+
 // Device parameter block of one level for one precision (passed by value to the kernels).
 template <typename R>
 struct LevelParams {
@@ -110,6 +119,7 @@ struct LevelParams {
   R sigG, alpha, omega;
   int extension;
   int cell_min;                    // launches over >= cell_min cells use thread-per-cell kernels (0: never)
+  int staged_min;                  // FP32 launches over >= staged_min cells use the staged kernels (0: never)
   LevelConsts<R> k;
 };
 

@@ -86,6 +86,28 @@ def test_star512_smoother_sweeps(star512):
             assert err64 <= sweep_tol(lev), (l, reverse, err64, sweep_tol(lev))
 
 
+def test_star512_staged_kernels(star512):
+    """The staged thread-per-cell operator and smoother at the benchmark size, forced on every
+    level: operator on every level and both sweep directions above the coarsest, FP32 bounds."""
+    import paper_2506_12899_gb300 as S
+    P = star512
+    g = S.Solver(P.prob, "f32", staged_min_cells=1)
+    for l, lev in enumerate(P.H.levels):
+        x = W.random_vector(lev.N, 131 + l)
+        yo = lev.A @ x
+        scale = np.abs(abs(lev.A) @ np.abs(x)).max()
+        y32 = P.to_oracle(g.apply(P.to_gpu(x, l, torch.float32), level=l), l)
+        assert np.abs(y32 - yo).max() <= 2e-6 * scale, (l, np.abs(y32 - yo).max() / scale)
+        if l == 0:
+            continue
+        f, u0 = W.random_vector(lev.N, 140 + l), W.random_vector(lev.N, 150 + l)
+        for reverse in (False, True):
+            uo = lev.coloured_sweep(u0.copy(), f, reverse=reverse)
+            u32 = g.smooth(P.to_gpu(f, l, torch.float32), P.to_gpu(u0, l, torch.float32), level=l, reverse=reverse)
+            assert rel_max(P.to_oracle(u32, l), uo) <= 2e-4, (l, reverse, rel_max(P.to_oracle(u32, l), uo))
+    g.close()
+
+
 def test_star512_vcycle(star512):
     """One V-cycle of the benchmark hierarchy (512^2 p=2 -> p=1 -> ... -> 64^2, then the one-CTA
     tail over 64^2 .. 8^2 and the coarse solve) in FP32, and the FP64 V-cycle with one launch per

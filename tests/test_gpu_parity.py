@@ -33,6 +33,10 @@ CASES = {
     "disk2d_p2_poly": W.disk2d_p1(16, 5).replace(p=2, extension=1),
     "box2d_p2": W.Problem(dim=2, n=16, p=2, shape=W.box(0.5)),
     "star2d_p3_n16_ssor": W.star2d_p2(16, 2).replace(p=3, ssor_each=1),
+    "complex2d_p1_l3": W.paper_complex2d(3, 1, 0.5),
+    "complex2d_p2_l2": W.paper_complex2d(2, 2, 0.75),
+    "complex2d_p3_l2": W.paper_complex2d(2, 3, 0.5),
+    "paper_disk_p2_l3": W.paper_disk(3, 2, 0.5),
 }
 _pairs = {}
 
@@ -188,7 +192,8 @@ def test_vcycle(name, tail):
 
 
 @pytest.mark.parametrize("name", ["disk2d_p1_n32", "disk2d_p1_n32_s3", "star2d_p2_n32", "sphere3d_p1_n8",
-                                  "sphere3d_p2_n8", "box2d_p2", "star2d_p3_n16_ssor"])
+                                  "sphere3d_p2_n8", "box2d_p2", "star2d_p3_n16_ssor", "complex2d_p1_l3",
+                                  "complex2d_p2_l2", "complex2d_p3_l2", "paper_disk_p2_l3"])
 def test_fgmres_fp64_matches_oracle(name):
     """a6: FP64 FGMRES(30) + FP64 V-cycle: same iteration count as the oracle and the solution
     within 1e-10 relative L2."""
@@ -385,3 +390,79 @@ def test_full_size_star512_p2_sampled():
     assert info.converged and info.true_rel_residual <= 1e-8
     res = bo[sample] - rows(xs.cpu().numpy())
     assert np.abs(res).max() <= 1e-7 * np.abs(bo).max()
+
+
+@pytest.mark.parametrize("name", ["disk2d_p1_n32", "star2d_p2_n32", "star2d_p3_n16", "sphere3d_p1_n8", "sphere3d_p2_n8",
+                                  "ellipsoid3d_p3_n12"])
+def test_staged_kernels(name):
+    """The staged thread-per-cell kernels (cells and face neighbours copied into shared memory by
+    the CTA before the per-cell arithmetic), forced on every FP32 launch they cover (2D p <= 3,
+    3D p <= 2): operator, residual, both sweep directions on every level above the coarsest, and
+    the V-cycle, against the oracle with the FP32 bounds used above."""
+    import paper_2506_12899_gb300 as S
+    P = pair(name)
+    g = S.Solver(P.prob, "f32", staged_min_cells=1)
+    for l, lev in enumerate(P.H.levels):
+        x = W.random_vector(lev.N, 70 + l)
+        yo = lev.A @ x
+        scale = np.abs(abs(lev.A) @ np.abs(x)).max()
+        y32 = P.to_oracle(g.apply(P.to_gpu(x, l, torch.float32), level=l), l)
+        assert np.abs(y32 - yo).max() <= 2e-6 * scale, (l, np.abs(y32 - yo).max() / scale)
+        f = W.random_vector(lev.N, 80 + l)
+        r32 = P.to_oracle(g.residual(P.to_gpu(f, l, torch.float32), P.to_gpu(x, l, torch.float32), level=l), l)
+        assert np.abs(r32 - (f - yo)).max() <= 2e-6 * (scale + np.abs(f).max())
+        if l == 0:
+            continue
+        u0 = W.random_vector(lev.N, 90 + l)
+        for reverse in (False, True):
+            uo = lev.coloured_sweep(u0.copy(), f, reverse=reverse)
+            u32 = g.smooth(P.to_gpu(f, l, torch.float32), P.to_gpu(u0, l, torch.float32), level=l, reverse=reverse)
+            assert rel_max(P.to_oracle(u32, l), uo) <= 2e-4, (l, reverse, rel_max(P.to_oracle(u32, l), uo))
+    L = len(P.H.levels) - 1
+    r = W.random_vector(P.H.finest.N, 23)
+    zo = P.H.vcycle(r)
+    z32 = P.to_oracle(g.vcycle(P.to_gpu(r, L, torch.float32)), L)
+    assert np.linalg.norm(z32 - zo) <= 1e-4 * np.linalg.norm(zo), np.linalg.norm(z32 - zo) / np.linalg.norm(zo)
+    b = g.rhs()
+    xs = torch.zeros_like(b)
+    info = g.solve(b, xs, tol=1e-8)
+    assert info.converged and info.true_rel_residual <= 1e-8
+    g.close()
+
+
+@pytest.mark.parametrize("name", ["disk2d_p1_n32", "star2d_p3_n16", "sphere3d_p2_n8", "ellipsoid3d_p3_n12",
+                                  "complex2d_p1_l3", "complex2d_p2_l2", "complex2d_p3_l2"])
+def test_l2_error_matches_oracle(name):
+    """sbm_l2_error (Sec. 5.1 / 5.4 error measure) against the oracle's l2_error, on the oracle's own
+    direct solution mapped to the library layout and on a random vector."""
+    import scipy.sparse.linalg as spla
+    P = pair(name)
+    F = P.H.finest
+    L = len(P.H.levels) - 1
+    xo = spla.spsolve(F.A.tocsc(), F.disc.rhs())
+    for x in (xo, W.random_vector(F.N, 3)):
+        eo = F.disc.l2_error(x)
+        eg = P.gpu.l2_error(P.to_gpu(x, L))
+        assert abs(eg - eo) <= 1e-10 * eo, (eg, eo)
+
+
+@pytest.mark.parametrize("p,level,lam", [(1, 3, 1.0), (2, 2, 0.5), (3, 2, 0.75)])
+def test_complex2d_solution_and_error(p, level, lam):
+    """The complex deformed domain of Sec. 5.4 (Newton closest points on a non-convex level set):
+    the GPU FP64 solve reproduces the oracle's direct solution and its L2 error, with the paper's
+    tolerance 1e-12."""
+    import scipy.sparse.linalg as spla
+    import paper_2506_12899_gb300 as S
+    prob = W.paper_complex2d(level, p, lam)
+    P = Pair(prob)
+    F = P.H.finest
+    L = len(P.H.levels) - 1
+    xo = spla.spsolve(F.A.tocsc(), F.disc.rhs())
+    b = P.gpu.rhs()
+    x = torch.zeros_like(b)
+    info = P.gpu.solve(b, x, tol=1e-12, restart=30, max_it=300)
+    assert info.converged
+    xg = P.to_oracle(x, L)
+    assert np.linalg.norm(xg - xo) <= 1e-9 * np.linalg.norm(xo)
+    eo = F.disc.l2_error(xo)
+    assert abs(P.gpu.l2_error(x) - eo) <= 1e-6 * eo

@@ -197,6 +197,16 @@ def paper_disk(level: int, p: int, lam: float, dim: int = 2) -> Problem:
                    extension=1, coarsest_n=4)
 
 
+def paper_complex2d(level: int, p: int, lam: float) -> Problem:
+    """The paper's complex deformed 2D domain (Sec. 5.4): phi = (1 - 3/4 sin^2(pi x))(x^2 + y^2) - 1/5,
+    u = phi + 1 (g = 1 on the true boundary), background [-1.01,1.01]^2 with 4*2^level cells per
+    direction, the paper-replica penalties and activity test of paper_disk, polynomial extension."""
+    return Problem(name=f"paper_complex2d_p{p}_l{level}_lam{lam}", dim=2, n=4 * 2 ** level, p=p,
+                   lo=(-1.01,) * 3, hi=(1.01,) * 3, shape=complex2d(), exact=EXACT_PHIP1, lam=lam,
+                   lam_inclusive=1 if lam >= 1.0 else 0, sigma_face_c=1.0, sigma_bnd_c=5.0, extension=1,
+                   coarsest_n=4)
+
+
 def random_vector(n: int, seed: int, dtype=np.float64) -> np.ndarray:
     """Seeded U[-1,1] vector (used as an apply / smoother / V-cycle input)."""
     return (2.0 * np.random.default_rng(seed).random(n) - 1.0).astype(dtype)
