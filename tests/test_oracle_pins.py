@@ -325,6 +325,136 @@ def test_coloured_sweep_equals_sequential_block_gs():
         assert np.linalg.norm(a - b) <= 1e-12 * np.linalg.norm(b)
 
 
+def test_red_black_sweep_equals_sequential_block_gs():
+    """Red-black ordering: cells of equal index-sum parity share no face (a face changes one index
+    by one), so the sweep over the even-parity colours, then the odd ones, equals the cell-by-cell
+    successive correction (Eq. 16) in that cell order, differs from the 2^d-colour sweep, and a
+    colouring that mixes parities within a step would not be a valid simultaneous update."""
+    for prob in (W.disk2d_p1(16, 2).replace(p=2, ordering=1), W.sphere3d(6, 1, 1).replace(ordering=1)):
+        lev = MG.Level(prob, prob.n, prob.p)
+        par = lev.geom.cell_idx.sum(axis=1) % 2
+        # no coupling between two cells of the same parity
+        A = lev.A.tocoo()
+        ca, cb = A.row // lev.nb, A.col // lev.nb
+        off = ca != cb
+        assert np.all(par[ca[off]] != par[cb[off]])
+        rng = np.random.default_rng(4)
+        f, u0 = rng.normal(size=lev.N), rng.normal(size=lev.N)
+        order = np.concatenate([np.nonzero(par == 0)[0], np.nonzero(par == 1)[0]])
+        for reverse in (False, True):
+            a = lev.coloured_sweep(u0.copy(), f, reverse=reverse)
+            o = order[::-1] if reverse else order
+            b = lev.block_gs_sequential(u0.copy(), f, o)
+            assert np.linalg.norm(a - b) <= 1e-12 * np.linalg.norm(b)
+        c = MG.Level(prob.replace(ordering=0), prob.n, prob.p).coloured_sweep(u0.copy(), f)
+        assert np.linalg.norm(lev.coloured_sweep(u0.copy(), f) - c) > 1e-6 * np.linalg.norm(c)
+
+
+def test_block_jacobi_step_and_convergence():
+    """Additive block Jacobi: one step equals u + omega D^-1 (f - A u) with D the principal cell
+    blocks of the dense matrix, and damped steps converge to A^-1 f on the SPD box."""
+    prob = W.Problem(dim=2, n=8, p=2, shape=W.box(0.5), smoother=1, omega=0.6)
+    lev = MG.Level(prob, 8, 2)
+    A = lev.A.toarray()
+    rng = np.random.default_rng(5)
+    f, u0 = rng.normal(size=lev.N), rng.normal(size=lev.N)
+    r = f - A @ u0
+    expect = u0.copy()
+    for a in range(lev.geom.n_active):
+        s = lev.dofs(a)
+        expect[s] += 0.6 * np.linalg.solve(A[s, s], r[s])
+    got = lev.block_jacobi_step(u0.copy(), f)
+    assert np.linalg.norm(got - expect) <= 1e-12 * np.linalg.norm(expect)
+    # k steps multiply the error by (I - omega D^-1 A)^k, whose spectral radius is below 1 on the
+    # SPD box for omega < 2 / lambda_max(D^-1 A): the iteration converges to A^-1 f
+    Dinv = np.zeros_like(A)
+    for a in range(lev.geom.n_active):
+        s = lev.dofs(a)
+        Dinv[s, s] = np.linalg.inv(A[s, s])
+    E = np.eye(lev.N) - 0.6 * Dinv @ A
+    assert np.abs(np.linalg.eigvals(E)).max() < 1.0
+    x = np.linalg.solve(A, f)
+    u = u0.copy()
+    for _ in range(7):
+        lev.block_jacobi_step(u, f)
+    assert np.linalg.norm((u - x) - np.linalg.matrix_power(E, 7) @ (u0 - x)) <= 1e-10 * np.linalg.norm(u0 - x)
+
+
+def test_power_iteration_estimates_lambda_max():
+    """The power-iteration estimate of lambda_max(D^-1 A) lies below the spectral radius and within
+    10% of it on the SPD box (where D^-1 A has a real positive spectrum); the start vector depends on
+    the background cell index only."""
+    prob = W.Problem(dim=2, n=8, p=2, shape=W.box(0.5), smoother=2)
+    lev = MG.Level(prob, 8, 2)
+    A = lev.A.toarray()
+    Dinv = np.zeros_like(A)
+    for a in range(lev.geom.n_active):
+        s = lev.dofs(a)
+        Dinv[s, s] = np.linalg.inv(A[s, s])
+    ev = np.linalg.eigvals(Dinv @ A)
+    rho = np.abs(ev).max()
+    assert np.abs(ev.imag).max() < 1e-8 and ev.real.min() > 0
+    lam = lev.lambda_max()
+    assert lam <= rho * (1 + 1e-12) and lam >= 0.9 * rho, (lam, rho)
+    v = MG.chebyshev_start(lev.geom.cell_idx, lev.nb).reshape(-1, lev.nb)
+    perm = np.random.default_rng(0).permutation(lev.geom.n_active)
+    assert np.array_equal(MG.chebyshev_start(lev.geom.cell_idx[perm], lev.nb).reshape(-1, lev.nb), v[perm])
+
+
+def test_chebyshev_error_polynomial():
+    """The Chebyshev smoother multiplies the error by the scaled Chebyshev polynomial
+    p_m(t) = T_m((theta - t) / delta) / T_m(theta / delta) of t = D^-1 A (textbook Chebyshev
+    semi-iteration), checked through the eigen-decomposition of D^-1 A on the SPD box, for degrees
+    1 to 5; every eigencomponent inside the interval is damped by at least 1 / T_m(theta/delta)."""
+    prob = W.Problem(dim=2, n=8, p=2, shape=W.box(0.5), smoother=2)
+    lev = MG.Level(prob, 8, 2)
+    A = lev.A.toarray()
+    Dinv = np.zeros_like(A)
+    for a in range(lev.geom.n_active):
+        s = lev.dofs(a)
+        Dinv[s, s] = np.linalg.inv(A[s, s])
+    T = Dinv @ A
+    b = MG.CHEB_SAFETY * lev.lambda_max()
+    a_ = b / prob.cheb_ratio
+    theta, delta = 0.5 * (b + a_), 0.5 * (b - a_)
+    X = (theta * np.eye(lev.N) - T) / delta
+    rng = np.random.default_rng(6)
+    x = rng.normal(size=lev.N)
+    f = A @ x
+    u0 = rng.normal(size=lev.N)
+    Tkm1, Tk = np.eye(lev.N), X.copy()                     # T_0(X), T_1(X) (three-term recurrence)
+    for m in range(1, 6):
+        if m > 1:
+            Tkm1, Tk = Tk, 2 * X @ Tk - Tkm1
+        scale = np.cosh(m * np.arccosh(theta / delta))     # T_m(theta / delta), theta / delta > 1
+        u = lev.chebyshev(u0.copy(), f, degree=m)
+        e0, e = u0 - x, u - x
+        expect = Tk @ e0 / scale
+        assert np.linalg.norm(e - expect) <= 1e-9 * np.linalg.norm(e0), (m, np.linalg.norm(e - expect))
+        # eigencomponents of D^-1 A inside [a, b] are damped by at least 1 / T_m(theta / delta)
+        w = np.linalg.eigvals(T).real
+        inside = w[(w >= a_) & (w <= b)]
+        pm = np.cos(m * np.arccos(np.clip((theta - inside) / delta, -1, 1))) / scale
+        assert np.all(np.abs(pm) <= 1.0 / scale * (1 + 1e-9))
+
+
+@pytest.mark.parametrize("dim,p", [(2, 1), (2, 2), (3, 1)])
+def test_penalty_free_variant_reproduces_linear(dim, p):
+    """The penalty-free form alpha = -1, sigma_Gamma = 0 (Sec. 2.1) is still consistent: the linear
+    solution is reproduced exactly for any shift d (the SBM terms vanish on it with the Taylor
+    extension), and the matrix is not symmetric on a curved boundary."""
+    prob = (W.disk2d_p1(16, 1) if dim == 2 else W.sphere3d(8, 1, 4)).replace(p=p, alpha=-1.0, sigma_bnd_c=0.0,
+                                                                              exact=W.EXACT_LINEAR)
+    g = G.LevelGeometry(prob, prob.n, p)
+    D = Discretisation(prob, g)
+    uI = D.interpolate(W.EXACT_LINEAR)
+    b = D.rhs()
+    assert np.linalg.norm(D.A @ uI - b) <= 1e-12 * np.linalg.norm(b)
+    x = spla.spsolve(D.A.tocsc(), b)
+    assert np.linalg.norm(x - uI) <= 1e-10 * np.linalg.norm(uI)
+    assert abs(D.A - D.A.T).max() > 1e-6 * abs(D.A).max()
+
+
 def test_colour_groups_equal_colour_order():
     """Colour c(K) = sum_k (i_k mod 2) 2^k; face neighbours differ in one index parity, so colours
     with the same number of odd bits never couple.  The sweep in colour order 0..2^d-1 therefore

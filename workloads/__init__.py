@@ -71,6 +71,12 @@ class Problem:
     omega: float = 1.0               # block-smoother relaxation on levels with p_l <= 2
     omega_p3: float = 0.8            # relaxation on levels with p_l = 3 (Sec. 5.3)
     vf_samples: int = 0              # kappa sub-samples per direction (0: 16 in 2D, 8 in 3D)
+    smoother: int = 0                # 0: coloured block Gauss-Seidel (multiplicative, Eq. 16); 1: additive
+                                     # block Jacobi damped by omega; 2: Chebyshev-accelerated block Jacobi
+    ordering: int = 0                # Gauss-Seidel colours: 0 the 2^d colours c = sum (i_k mod 2) 2^k;
+                                     # 1 red-black, (sum_k i_k) mod 2
+    cheb_degree: int = 4             # Chebyshev steps per smoothing step
+    cheb_ratio: float = 20.0         # Chebyshev interval [lambda_max / ratio, lambda_max]
 
     def replace(self, **kw) -> "Problem":
         return dataclasses.replace(self, **kw)
