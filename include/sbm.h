@@ -109,6 +109,15 @@ typedef struct {
                          /* (2D p <= 3, 3D p <= 2) use the staged thread-per-cell kernels, whose  */
                          /* CTA copies its cells and their face neighbours into shared memory     */
                          /* first; 0: library default; < 0: never                                  */
+  int smoother;          /* 0: coloured multiplicative block Gauss-Seidel (Eq. 16, the default);   */
+                         /* 1: additive cell-wise block Jacobi u += omega_l D^-1 (f - A u) (the     */
+                         /* additive form of Sec. 3.1); 2: block Jacobi inside a Chebyshev          */
+                         /* iteration of cheb_degree steps on [b / cheb_ratio, b], b = 1.1 times a  */
+                         /* power-iteration estimate of lambda_max(D^-1 A) (Sec. 5.3)               */
+  int ordering;          /* Gauss-Seidel colours: 0 the 2^d colours c = sum (i_k mod 2) 2^k; 1     */
+                         /* red-black, (sum_k i_k) mod 2 (even parity first in a forward sweep)     */
+  int cheb_degree;       /* Chebyshev steps per smoothing step (smoother 2), 1..16                  */
+  double cheb_ratio;     /* lambda_max / lambda_min of the Chebyshev interval (smoother 2), > 1      */
   void* stream;          /* cudaStream_t for every launch of this context                        */
 } sbm_setup_desc;
 

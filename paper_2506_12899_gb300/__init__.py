@@ -57,7 +57,8 @@ class _Desc(ctypes.Structure):
                 ("vf_samples", ctypes.c_int), ("precision", ctypes.c_int), ("tail_max_cells", ctypes.c_int),
                 ("tail_cluster_ctas", ctypes.c_int), ("launch_overlap", ctypes.c_int),
                 ("krylov_basis", ctypes.c_int), ("cell_kernel_min_cells", ctypes.c_int),
-                ("staged_min_cells", ctypes.c_int), ("stream", ctypes.c_void_p)]
+                ("staged_min_cells", ctypes.c_int), ("smoother", ctypes.c_int), ("ordering", ctypes.c_int),
+                ("cheb_degree", ctypes.c_int), ("cheb_ratio", ctypes.c_double), ("stream", ctypes.c_void_p)]
 
 
 class _LevelInfo(ctypes.Structure):
@@ -194,6 +195,10 @@ def make_desc(prob, precision: int = SBM_F64, stream: int = 0, tail_max_cells: i
     d.krylov_basis = krylov_basis
     d.cell_kernel_min_cells = cell_kernel_min_cells
     d.staged_min_cells = staged_min_cells
+    d.smoother = getattr(prob, "smoother", 0)
+    d.ordering = getattr(prob, "ordering", 0)
+    d.cheb_degree = getattr(prob, "cheb_degree", 4)
+    d.cheb_ratio = getattr(prob, "cheb_ratio", 20.0)
     return d
 
 

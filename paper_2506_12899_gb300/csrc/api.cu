@@ -54,6 +54,9 @@ struct DevLevel {
   void* z[2] = {nullptr, nullptr};
   void* rhs[2] = {nullptr, nullptr};
   void* res[2] = {nullptr, nullptr};
+  void* tmp[2] = {nullptr, nullptr};   // additive smoothers: y = D^-1 r
+  void* dir[2] = {nullptr, nullptr};   // Chebyshev: the update direction d
+  double lam_max = 0.0;                // Chebyshev: estimate of lambda_max(D^-1 A) (set-up)
 };
 
 
@@ -378,6 +381,10 @@ void validate(const sbm_setup_desc& d) {
   if (d.precision != SBM_F64 && d.precision != SBM_F32) bad("precision must be SBM_F64 or SBM_F32");
   if (d.extension != 0 && d.extension != 1) bad("extension must be 0 or 1");
   if (d.krylov_basis < 0 || d.krylov_basis > 2) bad("krylov_basis must be 0, 1 or 2");
+  if (d.smoother < 0 || d.smoother > 2) bad("smoother must be 0, 1 or 2");
+  if (d.ordering != 0 && d.ordering != 1) bad("ordering must be 0 or 1");
+  if (d.smoother == 2 && (d.cheb_degree < 1 || d.cheb_degree > 16 || !(d.cheb_ratio > 1.0)))
+    bad("Chebyshev smoother: 1 <= cheb_degree <= 16 and cheb_ratio > 1");
   if (d.tail_cluster_ctas < 0 || d.tail_cluster_ctas > 16 || (d.tail_cluster_ctas & (d.tail_cluster_ctas - 1)))
     bad("tail_cluster_ctas must be 0, 1, 2, 4, 8 or 16");
   const double w0 = d.hi[0] - d.lo[0];
@@ -389,6 +396,53 @@ void validate(const sbm_setup_desc& d) {
   if (d.shape.kind == SBM_SHAPE_STAR && d.dim != 2) bad("star shape is 2D");
   if (d.shape.kind == SBM_SHAPE_COMPLEX2D && d.dim != 2) bad("complex2d shape is 2D");
   if (d.shape.kind == SBM_SHAPE_ELLIPSOID && d.dim != 3) bad("ellipsoid shape is 3D");
+}
+
+// Start vector of the power iteration: entry (cell, node l) = 1 + 0.5 sin(0.7 (i + 2.1 j + 3.3 k) +
+// 1.3 l) from the cell's background index, the same vector in any cell order.
+std::vector<double> power_start(const HostLevel& H) {
+  std::vector<double> v((size_t)H.n_dof());
+  for (int a = 0; a < H.n_act; ++a) {
+    const double base = H.cell[3 * a] + 2.1 * H.cell[3 * a + 1] + (H.dim == 3 ? 3.3 * H.cell[3 * a + 2] : 0.0);
+    for (int l = 0; l < H.np; ++l) v[(size_t)a * H.np + l] = 1.0 + 0.5 * std::sin(0.7 * base + 1.3 * l);
+  }
+  return v;
+}
+
+constexpr int kPowerSteps = 15;       // power-iteration steps for lambda_max(D^-1 A)
+constexpr double kChebSafety = 1.1;   // upper end of the Chebyshev interval: 1.1 times the estimate
+
+// lambda_max(D^-1 A) of every level above the coarsest by kPowerSteps power-iteration steps in FP64
+// on the device: w = D^-1 (A v) (the operator, then the block solves of the smoother kernels with
+// every neighbour read as zero and omega = 1), lambda = |w| / |v|, v <- w (the normalisation of v
+// before each step is folded into the quotient).
+void estimate_lambda_max(Context& C) {
+  const cudaStream_t s = C.stream;
+  for (size_t l = 1; l < C.lv.size(); ++l) {
+    DevLevel& L = C.lv[l];
+    const size_t N = L.H.n_dof();
+    double* v = C.dalloc<double>(N);
+    double* av = C.dalloc<double>(N);
+    double* w = C.dalloc<double>(N);
+    double* part = C.dalloc<double>((size_t)dot_blocks(N) * 32);
+    double* nrm = C.dalloc<double>(2);
+    const std::vector<double> v0 = power_start(L.H);
+    CUDA_TRY(cudaMemcpy(v, v0.data(), N * sizeof(double), cudaMemcpyHostToDevice));
+    LevelParams<double> P1 = L.P64;
+    P1.omega = 1.0;
+    double lam = 0.0;
+    for (int it = 0; it < kPowerSteps; ++it) {
+      CUDA_TRY((launch_apply<double, double>(L.H.dim, L.H.p, L.P64, v, nullptr, av, 0, s)));
+      CUDA_TRY(launch_smooth<double>(L.H.dim, L.H.p, P1, 0, kZeroAll, av, w, s));
+      CUDA_TRY(launch_multi_dot(v, N, 1, v, N, part, nrm, 1, s));
+      CUDA_TRY(launch_multi_dot(w, N, 1, w, N, part, nrm + 1, 1, s));
+      CUDA_TRY(cudaMemcpyAsync(C.host_pinned, nrm, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
+      CUDA_TRY(cudaStreamSynchronize(s));
+      lam = C.host_pinned[1] / C.host_pinned[0];
+      std::swap(v, w);
+    }
+    L.lam_max = lam;
+  }
 }
 
 Context* build_context(const sbm_setup_desc& d, bool device) {
@@ -436,6 +490,7 @@ Context* build_context(const sbm_setup_desc& d, bool device) {
     }
     L.P64 = make_params<double>(L, L.dhat64, L.binv64);
     L.P32 = make_params<float>(L, L.dhat32, L.binv32);
+    L.P64.ordering = L.P32.ordering = d.ordering;
     if (&L == &C->lv.back()) {                     // Arnoldi operator in double-float
       std::vector<dfl> dh(L.H.dhat.size());
       for (size_t i = 0; i < dh.size(); ++i) dh[i] = dfl(L.H.dhat[i]);
@@ -467,9 +522,11 @@ Context* build_context(const sbm_setup_desc& d, bool device) {
       if (H.p != 1 || !h_level || H.n_act > cap) break;
       top = l;
     }
-    C->tail_cand = cap > 0 && top >= 1 ? top : -1;
+    // the one-launch tail runs the coloured Gauss-Seidel of the 2^d-colour ordering only
+    C->tail_cand = cap > 0 && top >= 1 && d.smoother == 0 && d.ordering == 0 ? top : -1;
   }
   CUDA_TRY(cudaMallocHost(&C->host_pinned, 64 * sizeof(double)));
+  if (d.smoother == 2) estimate_lambda_max(*C);
   CUDA_TRY(cudaEventCreate(&C->ev0));
   CUDA_TRY(cudaEventCreate(&C->ev1));
   CUDA_TRY(cudaStreamCreateWithFlags(&C->ws, cudaStreamNonBlocking));
@@ -488,6 +545,10 @@ void ensure_work(Context& C) {
     L.z[pi] = C.dalloc<R>(N);
     L.rhs[pi] = C.dalloc<R>(N);
     L.res[pi] = C.dalloc<R>(N);
+    if (C.desc.smoother != 0) {
+      L.tmp[pi] = C.dalloc<R>(N);
+      if (C.desc.smoother == 2) L.dir[pi] = C.dalloc<R>(N);
+    }
   }
   // cluster tail: the highest candidate level whose vectors (levels 0..top) fit in the shared
   // memory of a resident cluster of 16, else 8, CTAs
@@ -642,6 +703,56 @@ void apply_learned(Context& C, DevLevel& L, const R* r, R* z, cudaStream_t s) {
   CUDA_TRY(launch_mlp_scatter<R>(nb, M.np, M.O, C.mlp_cells, C.mlp_Y, C.mlp_s, C.mlp_scale, z, s));
 }
 
+// y = D^-1 t on level L: the smoother kernels with every neighbour read as zero and omega = 1 apply
+// the cell-block inverses of Eq. 14 (dense for boundary cells, fast diagonalisation otherwise).
+template <typename R>
+void block_inverse(const DevLevel& L, const R* t, R* y, cudaStream_t s) {
+  LevelParams<R> P1 = params<R>(L);
+  P1.omega = R(1);
+  CUDA_TRY(launch_smooth<R>(L.H.dim, L.H.p, P1, 0, kZeroAll, t, y, s));
+}
+
+// One step of the additive smoothers on z for the right-hand side r (zero: z = 0 on entry):
+// block Jacobi z += omega_l D^-1 (r - A z), or cheb_degree Chebyshev steps with D^-1 on the
+// interval [b / cheb_ratio, b], b = 1.1 lambda_max (three-term recurrence: rho_0 = 1 / sigma,
+// d_0 = D^-1 r_0 / theta, rho_k = 1 / (2 sigma - rho_(k-1)), d_k = rho_k rho_(k-1) d_(k-1)
+// + (2 rho_k / delta) D^-1 r_k, z += d_k).
+template <typename R>
+void additive_smooth(Context& C, DevLevel& L, const R* r, R* z, bool zero, cudaStream_t s) {
+  const int pi = prec_index<R>();
+  const size_t N = L.H.n_dof();
+  const int dim = L.H.dim, p = L.H.p;
+  R* res = static_cast<R*>(L.res[pi]);
+  R* y = static_cast<R*>(L.tmp[pi]);
+  const LevelParams<R>& P = params<R>(L);
+  auto residual_inverse = [&](bool from_zero) {      // y = D^-1 (r - A z)
+    if (from_zero) {
+      block_inverse<R>(L, r, y, s);
+    } else {
+      CUDA_TRY((launch_apply<R, R>(dim, p, P, z, r, res, 1, s)));
+      block_inverse<R>(L, res, y, s);
+    }
+  };
+  if (C.desc.smoother == 1) {
+    const R omega = (R)(p == 3 ? C.desc.omega_p3 : C.desc.omega);
+    residual_inverse(zero);
+    CUDA_TRY(launch_smoother_update<R>(N, R(0), omega, y, nullptr, z, zero ? 0 : 1, s));
+    return;
+  }
+  R* d = static_cast<R*>(L.dir[pi]);
+  const double b = kChebSafety * L.lam_max, a = b / C.desc.cheb_ratio;
+  const double theta = 0.5 * (b + a), delta = 0.5 * (b - a), sigma = theta / delta;
+  double rho = 1.0 / sigma;
+  residual_inverse(zero);
+  CUDA_TRY(launch_smoother_update<R>(N, R(0), (R)(1.0 / theta), y, d, z, zero ? 2 : 3, s));
+  for (int k = 1; k < C.desc.cheb_degree; ++k) {
+    const double rho_new = 1.0 / (2.0 * sigma - rho);
+    residual_inverse(false);
+    CUDA_TRY(launch_smoother_update<R>(N, (R)(rho_new * rho), (R)(2.0 * rho_new / delta), y, d, z, 4, s));
+    rho = rho_new;
+  }
+}
+
 // One V-cycle on level l (Sec. 3): zero initial guess, pre-smoothing with forward colour order,
 // residual, restriction (Eq. 18), recursion, prolongation (Eq. 17), post-smoothing with reverse
 // colour order; level 0 is solved with the dense coarse inverse.
@@ -676,6 +787,10 @@ void vcycle_rec(Context& C, int l, const R* r, R* z, cudaStream_t s) {
   // comes after the pre-smoothing sweeps or the memset of z, the prolongation after the residual.
   if (C.desc.pre_smooth == 0) CUDA_TRY(cudaMemsetAsync(z, 0, (size_t)L.H.n_dof() * sizeof(R), s));
   for (int k = 0; k < C.desc.pre_smooth; ++k) {
+    if (C.desc.smoother != 0) {
+      additive_smooth<R>(C, L, r, z, k == 0, s);
+      continue;
+    }
     CUDA_TRY(launch_smooth<R>(dim, L.H.p, P, 0, k == 0, r, z, s, k > 0));
     if (C.desc.ssor_each) CUDA_TRY(launch_smooth<R>(dim, L.H.p, P, 1, 0, r, z, s, 1));
   }
@@ -690,6 +805,10 @@ void vcycle_rec(Context& C, int l, const R* r, R* z, cudaStream_t s) {
   vcycle_rec<R>(C, l - 1, rc, zc, s);
   CUDA_TRY(launch_prolong<R>(dim, L.H.p, Lc.H.p, tparams<R>(L), zc, z, s, 1));
   for (int k = 0; k < C.desc.post_smooth; ++k) {
+    if (C.desc.smoother != 0) {
+      additive_smooth<R>(C, L, r, z, false, s);
+      continue;
+    }
     if (C.desc.ssor_each) CUDA_TRY(launch_smooth<R>(dim, L.H.p, P, 0, 0, r, z, s, 1));
     CUDA_TRY(launch_smooth<R>(dim, L.H.p, P, 1, 0, r, z, s, 1));
   }

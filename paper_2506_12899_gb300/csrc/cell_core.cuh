@@ -435,7 +435,7 @@ __device__ __forceinline__ void block_solve_at(const LevelParams<R>& P, const R*
 // One cell of one colour of the block Gauss-Seidel sweep (Eq. 16): cell a of the colour
 // starting at cs whose first nbnd cells are boundary cells (dense inverse, boundary index
 // b0 + a - cs); the others use the fast diagonalisation.  t: f of the cell on entry (overwritten).
-// zero_start as in k_smooth.
+// zero_start: a kZero* mode (ops.h).
 template <int D, int N1, typename R>
 __device__ __forceinline__ void smooth_one(const LevelParams<R>& P, int col, int zero_start, int cs, int nbnd,
                                            int b0, int a, const int (&nb)[2 * D], R (&t)[CD<D, N1>::NP],
@@ -445,7 +445,10 @@ __device__ __forceinline__ void smooth_one(const LevelParams<R>& P, int col, int
   R c[NP];
 #pragma unroll
   for (int i = 0; i < NP; ++i) c[i] = 0;
-  add_couplings<D, N1, R, R>(P, u, col, zero_start != 0, nb, c);
+  int nbz[2 * D];                                   // kZeroAll: every neighbour reads as zero
+#pragma unroll
+  for (int q = 0; q < 2 * D; ++q) nbz[q] = zero_start == kZeroAll ? -1 : nb[q];
+  add_couplings<D, N1, R, R>(P, u, col, zero_start == kZeroLater, nbz, c);
 #pragma unroll
   for (int i = 0; i < NP; ++i) t[i] -= P.hscale * c[i];
   R y[NP];

@@ -722,13 +722,15 @@ cudaError_t launch_smooth_cell(int dim, int p, const LevelParams<R>& P, int reve
                                R* u, cudaStream_t s, int early) {
   if (reverse) zero_start = 0;
   int launched = 0;
-  for (int q = 0; q <= dim; ++q) {   // (the launcher in level_ops.cu chose this path for the level)
-    const int g = reverse ? dim - q : q;
+  const int ng = n_colour_groups(P, dim);
+  for (int q = 0; q < ng; ++q) {     // (the launcher in level_ops.cu chose this path for the level)
+    const int g = reverse ? ng - 1 - q : q;
+    const int zm = group_zero_mode(P, zero_start, q);
     const unsigned bs = cell_block(group_cells(P, dim, g));
     const SmoothSegs G = smooth_segs(P, dim, g, (int)bs);
     if (G.n == 0 || G.blk[G.n] == 0) continue;
     const int fe = launched > 0 || early;            // after the sweep's first launch f is two back
-#define SBM_SC(D, N1) SBM_PDL((k_smooth_cell<D, N1, R>), G.blk[G.n], bs, 0, s, P, G, zero_start, f, u, fe);
+#define SBM_SC(D, N1) SBM_PDL((k_smooth_cell<D, N1, R>), G.blk[G.n], bs, 0, s, P, G, zm, f, u, fe);
     SBM_CELL_DISPATCH(dim, p, SBM_SC);
 #undef SBM_SC
     count_launches();

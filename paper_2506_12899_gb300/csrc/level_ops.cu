@@ -392,10 +392,9 @@ __global__ void __launch_bounds__(256) k_smooth(const __grid_constant__ LevelPar
   const bool valid = threadIdx.x < CPB * NP && a < last;
   int nb[NS];
   dof_nbr<D, R>(P, a, valid, nb);                    // set-up data: read before the wait
-  if (zero_start)
 #pragma unroll
-    for (int s = 0; s < NS; ++s)
-      if ((col ^ (1 << (s >> 1))) > col) nb[s] = -1;   // unvisited colour: zero
+  for (int s = 0; s < NS; ++s)                       // neighbours that read as zero (kZero* modes)
+    if ((zero_start == kZeroLater && (col ^ (1 << (s >> 1))) > col) || zero_start == kZeroAll) nb[s] = -1;
   R fv = 0;
   if (valid && early) fv = __ldcg(f + (size_t)a * NP + i);   // f written two or more launches back (L2)
   pdl_wait();
@@ -640,15 +639,17 @@ cudaError_t launch_smooth(int dim, int p, const LevelParams<R>& P, int reverse, 
     return launch_smooth_cell<R>(dim, p, P, reverse, zero_start, f, u, s, early);
   if (reverse) zero_start = 0;
   int launched = 0;
-  for (int q = 0; q <= dim; ++q) {
-    const int g = reverse ? dim - q : q;
+  const int ng = n_colour_groups(P, dim);
+  for (int q = 0; q < ng; ++q) {
+    const int g = reverse ? ng - 1 - q : q;
+    const int zm = group_zero_mode(P, zero_start, q);
     const int fe = launched > 0 || early;            // after the sweep's first launch f is two back
 #define SBM_SMOOTH(D, N1)                                                                          \
   {                                                                                                \
     using Dm = Dims<D, N1>;                                                                        \
     const SmoothSegs G = smooth_segs(P, dim, g, Dm::CPB);                                          \
     if (G.n > 0 && G.blk[G.n] > 0) {                                                               \
-      SBM_PDL((k_smooth<D, N1, R>), G.blk[G.n], Dm::NT, 0, s, P, G, zero_start, f, u, fe);         \
+      SBM_PDL((k_smooth<D, N1, R>), G.blk[G.n], Dm::NT, 0, s, P, G, zm, f, u, fe);                 \
       count_launches();                                                                            \
       ++launched;                                                                                  \
     }                                                                                              \
@@ -658,6 +659,45 @@ cudaError_t launch_smooth(int dim, int p, const LevelParams<R>& P, int reverse, 
   }
   return cudaGetLastError();
 }
+
+namespace {
+// The update of the additive smoothers (block Jacobi, Chebyshev) after y = D^-1 (f - A z):
+//   mode 0: z = b y (first Jacobi step from z = 0)      mode 1: z += b y
+//   mode 2: d = b y, z = d (first Chebyshev step from 0) mode 3: d = b y, z += d
+//   mode 4: d = a d + b y, z += d
+template <typename R>
+__global__ void k_smoother_update(size_t n, R a, R b, const R* __restrict__ y, R* __restrict__ d, R* __restrict__ z,
+                                  int mode) {
+  pdl_entry();
+  const size_t stride = (size_t)gridDim.x * blockDim.x;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+    const R by = b * y[i];
+    if (mode == 0) {
+      z[i] = by;
+    } else if (mode == 1) {
+      z[i] += by;
+    } else {
+      const R di = mode == 4 ? a * d[i] + by : by;
+      d[i] = di;
+      z[i] = mode == 2 ? di : z[i] + di;
+    }
+  }
+}
+}  // namespace
+
+template <typename R>
+cudaError_t launch_smoother_update(size_t n, R a, R b, const R* y, R* d, R* z, int mode, cudaStream_t s) {
+  size_t g = (n + 255) / 256;
+  if (g < 1) g = 1;
+  if (g > 152 * 8) g = 152 * 8;
+  SBM_PDL((k_smoother_update<R>), (unsigned)g, 256, 0, s, n, a, b, y, d, z, mode);
+  count_launches();
+  return cudaGetLastError();
+}
+template cudaError_t launch_smoother_update<double>(size_t, double, double, const double*, double*, double*, int,
+                                                    cudaStream_t);
+template cudaError_t launch_smoother_update<float>(size_t, float, float, const float*, float*, float*, int,
+                                                   cudaStream_t);
 
 #define SBM_DISPATCH_T(dim, pf, pc, MACRO)                          \
   do {                                                              \

@@ -123,14 +123,34 @@ int dots_noalloc(const double* V, long long ldv, int nv, const double* w, long l
 // Cells of colours with the same number g of odd bits therefore never neighbour one another, and
 // the forward sweep over colours equals the sweep over groups g = 0..d (reverse: d..0) with all
 // colours of a group updated by one launch: every cell reads the same neighbour values.
+// With red-black ordering (LevelParams::ordering = 1) the groups are the two index-sum parities,
+// popcount(c) mod 2: a face changes one index by one, so cells of equal parity never neighbour.
 // smooth_segs lists the segments of group g with cpb cells per block.
+template <typename R>
+inline int colour_group(const LevelParams<R>& P, int c) {
+  const int pc = __builtin_popcount((unsigned)c);
+  return P.ordering == 1 ? (pc & 1) : pc;
+}
+template <typename R>
+inline int n_colour_groups(const LevelParams<R>& P, int dim) {
+  return P.ordering == 1 ? 2 : dim + 1;
+}
+
+// Modes of the smoother kernels' zero_start argument: which values of u a launch may treat as zero.
+//   0: none (u holds the current iterate);
+//   1: a forward colour-group sweep from u = 0: the cell's own u and its neighbours of later groups
+//      (colour with one more odd bit) are zero;
+//   2: every neighbour and the cell's own u are zero (the launch applies omega A_KK^-1 f);
+//   3: the cell's own u is zero, every neighbour is current (later red-black group from u = 0).
+enum { kZeroNone = 0, kZeroLater = 1, kZeroAll = 2, kZeroSelf = 3 };
+
 template <typename R>
 inline SmoothSegs smooth_segs(const LevelParams<R>& P, int dim, int g, int cpb) {
   SmoothSegs G{};
   G.n = 0;
   G.blk[0] = 0;
   for (int c = 0; c < (1 << dim); ++c) {
-    if (__builtin_popcount((unsigned)c) != g) continue;
+    if (colour_group(P, c) != g) continue;
     const int cs = P.colour_start[c], ce = P.colour_start[c + 1], nb = P.colour_nbnd[c];
     const int lo[2] = {cs, cs + nb}, hi[2] = {cs + nb, ce};
     for (int part = 0; part < 2; ++part) {
@@ -148,13 +168,23 @@ inline SmoothSegs smooth_segs(const LevelParams<R>& P, int dim, int g, int cpb) 
   return G;
 }
 
-// Cells of colour group g (colours with g odd index bits).
+// Cells of colour group g.
 template <typename R>
 inline int group_cells(const LevelParams<R>& P, int dim, int g) {
   int n = 0;
   for (int c = 0; c < (1 << dim); ++c)
-    if (__builtin_popcount((unsigned)c) == g) n += P.colour_start[c + 1] - P.colour_start[c];
+    if (colour_group(P, c) == g) n += P.colour_start[c + 1] - P.colour_start[c];
   return n;
+}
+
+// Zero mode of the launch of group index q (0-based in sweep order) of a forward sweep started from
+// u = 0: colour groups skip the later groups' neighbours; red-black treats every neighbour as zero
+// in its first group and none in its second.
+template <typename R>
+inline int group_zero_mode(const LevelParams<R>& P, int zero_start, int q) {
+  if (zero_start != kZeroLater) return zero_start;
+  if (P.ordering == 1) return q == 0 ? kZeroAll : kZeroSelf;
+  return kZeroLater;
 }
 
 // Thread-per-cell kernels (cell_ops.cu): cell_kernels covers the FP32 operator and the fused
@@ -221,6 +251,11 @@ cudaError_t launch_apply(int dim, int p, const LevelParams<R>& P, const TI* x, c
 template <typename R>
 cudaError_t launch_smooth(int dim, int p, const LevelParams<R>& P, int reverse, int zero_start, const R* f, R* u,
                           cudaStream_t s, int early = 0);
+
+// Update step of the additive smoothers after y = D^-1 r (modes in level_ops.cu: z = b y, z += b y,
+// and the Chebyshev d = a d + b y, z += d forms).
+template <typename R>
+cudaError_t launch_smoother_update(size_t n, R a, R b, const R* y, R* d, R* z, int mode, cudaStream_t s);
 
 // rc = P^T (f - A u) for a p-transfer (same mesh, degree pf -> pf - 1), residual not stored.
 template <typename R>

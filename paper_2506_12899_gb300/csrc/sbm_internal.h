@@ -120,6 +120,7 @@ struct LevelParams {
   int extension;
   int cell_min;                    // launches over >= cell_min cells use thread-per-cell kernels (0: never)
   int staged_min;                  // FP32 launches over >= staged_min cells use the staged kernels (0: never)
+  int ordering;                    // smoother colour groups: 0 by odd-bit count of the colour, 1 red-black
   LevelConsts<R> k;
 };
 
@@ -128,7 +129,7 @@ struct LevelParams {
 // [first[k], last[k]) of colour col[k] (colour starting at cs[k], nbnd[k] boundary cells, boundary
 // index b0[k] of its first cell) and blocks [blk[k], blk[k + 1]) of the grid.
 struct SmoothSegs {
-  static constexpr int kMax = 6;
+  static constexpr int kMax = 8;
   int n;
   int first[kMax], last[kMax], col[kMax], cs[kMax], nbnd[kMax], b0[kMax];
   int blk[kMax + 1];

@@ -187,7 +187,7 @@ __global__ void __launch_bounds__(CB) k_smooth_staged(const __grid_constant__ Le
   if (own) load_nbr<D, float>(P, a, nb);                               // set-up data: before the wait
 #pragma unroll
   for (int s = 0; s < NS; ++s) {
-    const bool later = zero_start && (col ^ (1 << (s >> 1))) > col;     // not visited yet: zero
+    const bool later = (zero_start == kZeroLater && (col ^ (1 << (s >> 1))) > col) || zero_start == kZeroAll;
     sNb[s * CB + threadIdx.x] = later ? -1 : nb[s];
   }
   if (early) {                                 // f written two or more launches back: L2-only loads
@@ -308,8 +308,10 @@ cudaError_t launch_smooth_staged(int dim, int p, const LevelParams<float>& P, in
                                  const float* f, float* u, cudaStream_t s, int early) {
   if (reverse) zero_start = 0;
   int launched = 0;
-  for (int q = 0; q <= dim; ++q) {
-    const int g = reverse ? dim - q : q;
+  const int ng = n_colour_groups(P, dim);
+  for (int q = 0; q < ng; ++q) {
+    const int g = reverse ? ng - 1 - q : q;
+    const int zm = group_zero_mode(P, zero_start, q);
     const int cells = group_cells(P, dim, g);
     const bool small = (size_t)cells <= (size_t)152 * 32 * 32;
     const int fe = launched > 0 || early;            // after the sweep's first launch f is two back
@@ -322,8 +324,8 @@ cudaError_t launch_smooth_staged(int dim, int p, const LevelParams<float>& P, in
     const SmoothSegs G = smooth_segs(P, dim, g, cb);                                               \
     if (G.n > 0 && G.blk[G.n] > 0) {                                                               \
       any = true;                                                                                  \
-      e = small ? launch_smooth_staged_cb<D, N1, 32>(P, G, zero_start, f, u, fe, s)                \
-                : launch_smooth_staged_cb<D, N1, CBL>(P, G, zero_start, f, u, fe, s);              \
+      e = small ? launch_smooth_staged_cb<D, N1, 32>(P, G, zm, f, u, fe, s)                        \
+                : launch_smooth_staged_cb<D, N1, CBL>(P, G, zm, f, u, fe, s);                      \
     }                                                                                              \
   }
     SBM_STAGED_DISPATCH(dim, p, SBM_SS);

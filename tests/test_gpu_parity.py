@@ -37,6 +37,14 @@ CASES = {
     "complex2d_p2_l2": W.paper_complex2d(2, 2, 0.75),
     "complex2d_p3_l2": W.paper_complex2d(2, 3, 0.5),
     "paper_disk_p2_l3": W.paper_disk(3, 2, 0.5),
+    # smoother and formulation variants (Sec. 2.1, Sec. 3.1, Sec. 5.3)
+    "star2d_p2_n32_redblack": W.star2d_p2(32, 1).replace(ordering=1),
+    "sphere3d_p2_n8_redblack": W.sphere3d(8, 2, 3).replace(ordering=1),
+    "disk2d_p1_n32_jacobi": W.disk2d_p1(32, 0).replace(smoother=1, omega=0.7),
+    "ellipsoid3d_p3_n12_jacobi": W.ellipsoid3d_p3(12, 4).replace(smoother=1, omega=0.7, omega_p3=0.6),
+    "star2d_p3_n16_chebyshev": W.star2d_p2(16, 2).replace(p=3, smoother=2),
+    "sphere3d_p1_n8_chebyshev": W.sphere3d(8, 1, 2).replace(smoother=2, cheb_degree=3),
+    "disk2d_p2_penalty_free": W.disk2d_p1(16, 5).replace(p=2, extension=1, alpha=-1.0, sigma_bnd_c=0.0),
 }
 _pairs = {}
 
@@ -193,7 +201,9 @@ def test_vcycle(name, tail):
 
 @pytest.mark.parametrize("name", ["disk2d_p1_n32", "disk2d_p1_n32_s3", "star2d_p2_n32", "sphere3d_p1_n8",
                                   "sphere3d_p2_n8", "box2d_p2", "star2d_p3_n16_ssor", "complex2d_p1_l3",
-                                  "complex2d_p2_l2", "complex2d_p3_l2", "paper_disk_p2_l3"])
+                                  "complex2d_p2_l2", "complex2d_p3_l2", "paper_disk_p2_l3", "star2d_p2_n32_redblack",
+                                  "sphere3d_p2_n8_redblack", "disk2d_p1_n32_jacobi", "ellipsoid3d_p3_n12_jacobi",
+                                  "star2d_p3_n16_chebyshev", "sphere3d_p1_n8_chebyshev", "disk2d_p2_penalty_free"])
 def test_fgmres_fp64_matches_oracle(name):
     """a6: FP64 FGMRES(30) + FP64 V-cycle: same iteration count as the oracle and the solution
     within 1e-10 relative L2."""
@@ -466,3 +476,33 @@ def test_complex2d_solution_and_error(p, level, lam):
     assert np.linalg.norm(xg - xo) <= 1e-9 * np.linalg.norm(xo)
     eo = F.disc.l2_error(xo)
     assert abs(P.gpu.l2_error(x) - eo) <= 1e-6 * eo
+
+
+@pytest.mark.parametrize("name", ["star2d_p2_n32_redblack", "disk2d_p1_n32_jacobi", "star2d_p3_n16_chebyshev",
+                                  "ellipsoid3d_p3_n12_jacobi"])
+def test_smoother_variant_launches(name):
+    """Launch counts of one V-cycle follow the variant: red-black takes 2 smoother launches per
+    sweep instead of d+1; the additive smoothers take no one-launch tail; every variant's FP32
+    V-cycle agrees with the oracle's V-cycle within the FP32 bound."""
+    import paper_2506_12899_gb300 as S
+    P = pair(name)
+    L = len(P.H.levels) - 1
+    r = W.random_vector(P.H.finest.N, 5)
+    g = S.Solver(P.prob, "f32")
+    rt = P.to_gpu(r, L, torch.float32)
+    g.vcycle(rt)
+    torch.cuda.synchronize()
+    n0 = S.kernel_launches()
+    z = g.vcycle(rt)
+    torch.cuda.synchronize()
+    n = S.kernel_launches() - n0
+    zo = P.H.vcycle(r)
+    assert np.linalg.norm(P.to_oracle(z, L) - zo) <= 1e-4 * np.linalg.norm(zo)
+    assert n > 2 * (len(P.H.levels) - 1)                 # per-level launches, no one-launch tail
+    if P.prob.ordering == 1 and P.prob.smoother == 0:
+        u = P.to_gpu(W.random_vector(P.H.finest.N, 6), L, torch.float32)
+        f = P.to_gpu(W.random_vector(P.H.finest.N, 7), L, torch.float32)
+        n0 = S.kernel_launches()
+        g.smooth(f, u)
+        assert S.kernel_launches() - n0 == 2
+    g.close()
