@@ -300,6 +300,23 @@ def other_workloads(torch, S, flush, n) -> dict:
     return out
 
 
+def setup_times(S, reps=2) -> dict:
+    """Wall time of sbm_setup (host build of every level, device uploads) for the 96^3 p=3 ellipsoid
+    with the volume fractions and closest points on the device, and on the host cores."""
+    out = {}
+    prob = WORKLOADS["ellipsoid3d_p3_n96"](0)
+    for label, flag in (("device_geometry", 1), ("host_geometry", -1)):
+        ts = []
+        for _ in range(reps):
+            t0 = time.perf_counter()
+            g = S.Solver(prob, "f32", device_geometry=flag)
+            ts.append(time.perf_counter() - t0)
+            g.close()
+        out[label + "_s"] = round(min(ts), 3)
+    out["workload"] = "ellipsoid3d_p3_n96"
+    return out
+
+
 def error_vs_oracle(solver, x, path) -> float | None:
     """||x - x_oracle|| / ||x_oracle|| with the oracle's solution from the CPU worker's file, mapped
     from the library's compact layout to the oracle's cell order by background cell index."""
@@ -484,10 +501,11 @@ def run_ours(args) -> dict | None:
     del r32, u32, y32, xr64, y64, V64, r1, u1
     torch.cuda.empty_cache()
     # ---- the other benchmark configurations, and the kernels on meshes larger than L2
-    others = large = None
+    others = large = setup = None
     if not args.no_extra:
         others = other_workloads(torch, S, flush, 5)
         large = large_mesh_rooflines(torch, S, hbm, flush)
+        setup = setup_times(S)
     if rank != 0:
         return None
     cpu = finish_cpu_worker(cpu_proc) if cpu_proc is not None else None
@@ -523,6 +541,7 @@ def run_ours(args) -> dict | None:
         "rooflines": rooflines,
         "rooflines_large_meshes": large,
         "other_workloads": others,
+        "setup_time": setup,
     }
     if cpu is not None:
         path = cpu["solution"]

@@ -118,6 +118,9 @@ typedef struct {
                          /* red-black, (sum_k i_k) mod 2 (even parity first in a forward sweep)     */
   int cheb_degree;       /* Chebyshev steps per smoothing step (smoother 2), 1..16                  */
   double cheb_ratio;     /* lambda_max / lambda_min of the Chebyshev interval (smoother 2), > 1      */
+  int device_geometry;   /* sbm_setup: the volume fractions (s^d sub-cell samples of phi per cell)  */
+                         /* and the closest-point Newton solves of the surrogate-face points run   */
+                         /* as device kernels (0: default, on; < 0: on the host cores)              */
   void* stream;          /* cudaStream_t for every launch of this context                        */
 } sbm_setup_desc;
 

@@ -58,7 +58,8 @@ class _Desc(ctypes.Structure):
                 ("tail_cluster_ctas", ctypes.c_int), ("launch_overlap", ctypes.c_int),
                 ("krylov_basis", ctypes.c_int), ("cell_kernel_min_cells", ctypes.c_int),
                 ("staged_min_cells", ctypes.c_int), ("smoother", ctypes.c_int), ("ordering", ctypes.c_int),
-                ("cheb_degree", ctypes.c_int), ("cheb_ratio", ctypes.c_double), ("stream", ctypes.c_void_p)]
+                ("cheb_degree", ctypes.c_int), ("cheb_ratio", ctypes.c_double), ("device_geometry", ctypes.c_int),
+                ("stream", ctypes.c_void_p)]
 
 
 class _LevelInfo(ctypes.Structure):
@@ -172,7 +173,7 @@ def _check(code: int):
 
 def make_desc(prob, precision: int = SBM_F64, stream: int = 0, tail_max_cells: int = 0,
               cell_kernel_min_cells: int = 0, tail_cluster_ctas: int = 0, launch_overlap: int = 0,
-              krylov_basis: int = 0, staged_min_cells: int = 0) -> _Desc:
+              krylov_basis: int = 0, staged_min_cells: int = 0, device_geometry: int = 0) -> _Desc:
     d = _Desc()
     d.dim, d.n, d.p = prob.dim, prob.n, prob.p
     d.lo[:] = [float(v) for v in prob.lo]
@@ -199,6 +200,7 @@ def make_desc(prob, precision: int = SBM_F64, stream: int = 0, tail_max_cells: i
     d.ordering = getattr(prob, "ordering", 0)
     d.cheb_degree = getattr(prob, "cheb_degree", 4)
     d.cheb_ratio = getattr(prob, "cheb_ratio", 20.0)
+    d.device_geometry = device_geometry
     return d
 
 
@@ -207,7 +209,7 @@ class Solver:
 
     def __init__(self, prob, precision: str = "f64", stream=None, tail_max_cells: int = 0,
                  cell_kernel_min_cells: int = 0, tail_cluster_ctas: int = 0, launch_overlap: int = 0,
-                 krylov_basis: int = 0, staged_min_cells: int = 0):
+                 krylov_basis: int = 0, staged_min_cells: int = 0, device_geometry: int = 0):
         """tail_max_cells: coarse p = 1 levels with at most that many cells run as one launch
         (0: library default, every level that fits for FP32 and none for FP64; < 0: never) of
         tail_cluster_ctas CTAs (0 or 1: one CTA; 2..16: a thread-block cluster).
@@ -217,7 +219,9 @@ class Solver:
         FP64 operator.  cell_kernel_min_cells: launches over at least that many
         cells use one thread per cell (0: library default, < 0: never, 1: always where
         (p+1)^d <= 16).  staged_min_cells: FP32 operator and smoother launches over at least that
-        many cells use the staged thread-per-cell kernels (0: library default, < 0: never)."""
+        many cells use the staged thread-per-cell kernels (0: library default, < 0: never).
+        device_geometry: volume fractions and closest points on the device (0: default, on; < 0:
+        on the host cores)."""
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("libsbm needs a CUDA device; no CPU fallback exists")
@@ -227,7 +231,7 @@ class Solver:
         self.precision = SBM_F32 if precision == "f32" else SBM_F64
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         desc = make_desc(prob, self.precision, self.stream.cuda_stream, tail_max_cells, cell_kernel_min_cells,
-                         tail_cluster_ctas, launch_overlap, krylov_basis, staged_min_cells)
+                         tail_cluster_ctas, launch_overlap, krylov_basis, staged_min_cells, device_geometry)
         ctx = ctypes.c_void_p()
         _check(self.lib.sbm_setup(ctypes.byref(desc), ctypes.byref(ctx)))
         self.ctx = ctx

@@ -457,7 +457,7 @@ Context* build_context(const sbm_setup_desc& d, bool device) {
   for (int q = 2; q <= d.p; ++q) seq.emplace_back(d.n, q);
   for (auto& np : seq) {
     DevLevel L;
-    L.H = build_level(d, np.first, np.second);
+    L.H = build_level(d, np.first, np.second, device);
     if (L.H.n_act == 0) {
       C->lv.clear();                       // an empty level: everything coarser is dropped
       continue;

@@ -70,7 +70,13 @@ struct SetupError {
 };
 
 // Builds one level; throws SetupError.  (Geometry of Sec. 2.1 / Sec. 4.2, element data of Eq. 11.)
-HostLevel build_level(const sbm_setup_desc& d, int n, int p);
+// device: the volume fractions and the closest points run as device kernels (geometry_ops.cu)
+// unless d.device_geometry < 0.
+HostLevel build_level(const sbm_setup_desc& d, int n, int p, bool device = false);
+// Device set-up kernels (geometry_ops.cu); throw SetupError on CUDA failures.
+void device_volume_counts(const sbm_setup_desc& d, int n, double h, int s, std::vector<int>& counts);
+void device_closest_points(const sbm_setup_desc& d, const std::vector<double>& samples, const std::vector<double>& X,
+                           std::vector<double>& C, std::vector<int>& ok);
 // Links a coarse and the next finer level (parent / children tables for h-transfers).
 void link_levels(HostLevel& coarse, HostLevel& fine);
 // Dense coarse inverse (host LU with partial pivoting).
