@@ -678,19 +678,28 @@ def run_roofline_sweep(args) -> dict:
 
 def run_paper_replica(args) -> dict:
     """The paper's unit-disk / unit-sphere study (Sec. 5): [-1.01,1.01]^d with 4*2^level cells,
-    kappa > lambda, sigma_F = (p+1)^2/h, sigma_Gamma = 5 (p+1)^2/h, polynomial boundary extension,
-    u = 2 cos x sin y, FP64 V-cycle, GMRES tol 1e-12 and a cap of 100 iterations, with one smoothing
-    step of each kind (forward / reverse sweep) and with full SSOR steps.  Reports iteration counts
-    per (dim, p, lambda, level)."""
+    kappa > lambda, polynomial boundary extension, u = 2 cos x sin y, FP64 V-cycle, GMRES tolerance
+    1e-12 and a cap of 100 iterations, omega = 0.8 at p = 3.  Reports iteration counts per
+    (dim, p, lambda, level) for three readings of the paper's solver settings:
+      base:       sigma_F = (p+1)^2/h, sigma_Gamma = 5 (p+1)^2/h, one forward sweep before and one
+                  reverse sweep after the coarse correction (the cell-wise SSOR split over the V);
+      ssor:       the same penalties, a full SSOR step (forward + reverse) before and after;
+      sipg_ssor:  full SSOR steps with the interior penalty sigma_F = p(p+1)/h (p^2/h at p >= 2),
+                  sigma_Gamma = 5 (p+1)^2/h."""
     import torch
     import paper_2506_12899_gb300 as S
     plan = [(2, 1, range(1, 8)), (3, 1, range(1, 5)), (2, 2, range(1, 7)), (3, 2, range(1, 5)), (2, 3, range(1, 6))]
+    readings = {"base": dict(ssor_each=0), "ssor": dict(ssor_each=1), "sipg_ssor": dict(ssor_each=1, sipg=True)}
     rows = []
     for dim, p, levels in plan:
         for lam in (1.0, 0.75, 0.5, 0.25):
-            for lev in levels:
-                for ssor in (0, 1):
-                    prob = W.paper_disk(lev, p, lam, dim).replace(ssor_each=ssor)
+            for name, rd in readings.items():
+                its = []
+                for lev in levels:
+                    prob = W.paper_disk(lev, p, lam, dim).replace(ssor_each=rd["ssor_each"])
+                    if rd.get("sipg"):
+                        cf = (p * (p + 1) if p == 1 else p * p) / (p + 1) ** 2
+                        prob = prob.replace(sigma_face_c=cf)
                     if p == 3:
                         prob = prob.replace(omega_p3=0.8)
                     try:
@@ -698,13 +707,43 @@ def run_paper_replica(args) -> dict:
                         b = g.rhs()
                         x = torch.zeros_like(b)
                         info = g.solve(b, x, tol=1e-12, restart=30, max_it=100)
-                        rows.append({"dim": dim, "p": p, "lambda": lam, "level": lev, "ssor_each": ssor,
-                                     "n_dof": g.n_dof(), "iterations": info.iterations, "converged": info.converged})
+                        its.append(info.iterations if info.converged else 100)
                         g.close()
                     except Exception as e:                # e.g. no active cell on a coarse level
-                        rows.append({"dim": dim, "p": p, "lambda": lam, "level": lev, "ssor_each": ssor,
-                                     "error": str(e)[:80]})
+                        its.append(str(e)[:40])
+                rows.append({"dim": dim, "p": p, "lambda": lam, "reading": name, "iterations_by_level": its})
     return {"experiment": "paper replica: unit disk/sphere iteration counts (tol 1e-12, cap 100)", "rows": rows}
+
+
+def run_complex2d(args) -> dict:
+    """The complex deformed domain of Sec. 5.4 on the GPU: phi = (1 - 3/4 sin^2(pi x))(x^2 + y^2) - 1/5,
+    u = phi + 1, [-1.01,1.01]^2 with 4*2^level cells, lambda in {1, .75, .5, .25}, p = 1..3; FP64
+    V-cycle, GMRES tolerance 1e-12 and a cap of 100 iterations; the iteration count and the L2 error
+    ||u - u_h|| over the surrogate domain (sbm_l2_error) of each solve."""
+    import torch
+    import paper_2506_12899_gb300 as S
+    rows = []
+    for p, levels in ((1, range(1, 8)), (2, range(1, 8)), (3, range(1, 7))):
+        for lam in (1.0, 0.75, 0.5, 0.25):
+            its, errs = [], []
+            for lev in levels:
+                prob = W.paper_complex2d(lev, p, lam)
+                if p == 3:
+                    prob = prob.replace(omega_p3=0.8)
+                try:
+                    g = S.Solver(prob, "f64")
+                    b = g.rhs()
+                    x = torch.zeros_like(b)
+                    info = g.solve(b, x, tol=1e-12, restart=30, max_it=100)
+                    its.append(info.iterations if info.converged else 100)
+                    errs.append(float(f"{g.l2_error(x):.4e}"))
+                    g.close()
+                except Exception as e:
+                    its.append(str(e)[:40])
+                    errs.append(None)
+            rows.append({"p": p, "lambda": lam, "iterations_by_level": its, "l2_error_by_level": errs})
+    return {"experiment": "complex deformed 2D domain (Sec. 5.4): iterations (tol 1e-12, cap 100) and L2 errors",
+            "rows": rows}
 
 
 def run_reference(args) -> dict | None:
@@ -768,7 +807,7 @@ def main():
     ap.add_argument("--tail-cluster", type=int, default=0, help="--profile kernels: cluster-tail CTAs")
     ap.add_argument("--krylov-basis", type=int, default=0, choices=[0, 1],
                     help="--profile solve: FGMRES basis storage (0 double-float, 1 FP64)")
-    ap.add_argument("--experiment", choices=["learned-heldout", "roofline-sweep", "paper-replica"],
+    ap.add_argument("--experiment", choices=["learned-heldout", "roofline-sweep", "paper-replica", "complex2d"],
                     help="a7 on held-out domains, or the large-mesh roofline sweep (no bench line)")
     ap.add_argument("--family", default="star2d", choices=["star2d", "ellipsoid3d"])
     ap.add_argument("--n-train", type=int, default=256)
@@ -777,7 +816,7 @@ def main():
     args = ap.parse_args()
     if args.experiment:
         run = {"learned-heldout": run_learned_heldout, "roofline-sweep": run_roofline_sweep,
-               "paper-replica": run_paper_replica}[args.experiment]
+               "paper-replica": run_paper_replica, "complex2d": run_complex2d}[args.experiment]
         print(json.dumps(run(args)))
         return
     if args.profile:
