@@ -415,16 +415,18 @@ def run_ours(args) -> dict | None:
         mlp = S.Mlp(prob.dim, prob.p, 128, seed=rank)
         u0 = (2 * torch.rand((4, N), generator=gen, device="cuda", dtype=torch.float32) - 1).contiguous()
         pairs = s32.collect(mlp, u0, 3)
+        rms = mlp.target_scale()                 # train on unit-RMS targets, attach with scale = RMS
         loss = mlp.train(epochs=20, batch=4096, lr=1e-3, seed=rank)
         its_plain = infos32[-1].iterations
         rate = infos32[-1].true_rel_residual ** (1.0 / max(its_plain, 1))
-        s32.attach_mlp(mlp, 1.0, fallback_rate=rate)
+        s32.attach_mlp(mlp, rms, fallback_rate=rate)
         timed_solves(torch, s32, b, x, 1, flush)
         tl, il = timed_solves(torch, s32, b, x, args.steps, flush)
         s32.attach_mlp(None)
         learned = {"ms": round(statistics.mean(tl), 4), "iterations": [i.iterations for i in il],
                    "converged": all(i.converged for i in il), "fallback": [i.learned_fallback for i in il],
-                   "train_pairs": pairs, "train_loss": round(loss, 6), "fallback_rate": rate,
+                   "train_pairs": pairs, "train_loss_relative_to_target_power": round(loss, 6),
+                   "target_rms": rms, "fallback_rate": rate,
                    "mlp": "F-128-128-n_p ReLU, BF16 tensor-core GEMMs, Adam 20 epochs, batch 4096"}
     # ---- end to end through the host-buffer C-ABI call (copies inside the timed region)
     bh = torch.empty(N, dtype=torch.float64, pin_memory=True)
@@ -615,6 +617,7 @@ def run_learned_heldout(args) -> dict:
         pairs += g.collect(mlp, u0, 3)
         g.close()
     collect_s = time.perf_counter() - t0
+    rms = mlp.target_scale()                     # unit-RMS targets; the correction is attached with scale = RMS
     t0 = time.perf_counter()
     loss = mlp.train(epochs=20, batch=4096, lr=1e-3, seed=0)
     train_s = time.perf_counter() - t0
@@ -639,10 +642,10 @@ def run_learned_heldout(args) -> dict:
         timed(g, b, x)
         plain, tp = timed(g, b, x)
         rate = plain.true_rel_residual ** (1.0 / max(plain.iterations, 1))
-        g.attach_mlp(mlp, 1.0, fallback_rate=rate)
+        g.attach_mlp(mlp, rms, fallback_rate=rate)
         timed(g, b, x)
         gated, tg = timed(g, b, x)
-        g.attach_mlp(mlp, 1.0, fallback_rate=0.0)
+        g.attach_mlp(mlp, rms, fallback_rate=0.0)
         timed(g, b, x)
         forced, tf = timed(g, b, x)
         g.attach_mlp(None)
@@ -654,7 +657,8 @@ def run_learned_heldout(args) -> dict:
     rows = [r for r in rows if isinstance(r["seed"], int)]
     med = lambda k, i: statistics.median(r[k][i] for r in rows) if rows else None
     return {"experiment": f"learned boundary correction, held-out {args.family} p=3", "train_seeds": args.n_train,
-            "eval_seeds": args.n_eval, "train_pairs": pairs, "train_loss": loss, "collect_s": round(collect_s, 1),
+            "eval_seeds": args.n_eval, "train_pairs": pairs, "target_rms": rms,
+            "train_loss_relative_to_target_power": loss, "collect_s": round(collect_s, 1),
             "train_s": round(train_s, 1),
             "median_iterations": {"plain": med("plain", 0), "learned_gated": med("learned_gated", 0),
                                   "learned_forced": med("learned_forced", 0)},

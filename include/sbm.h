@@ -306,7 +306,8 @@ int sbm_solve_host(void* ctx, const double* b_host, double* x_host, double tol, 
  * Learned boundary-cell correction.  The paper has no learned component; this is a learned
  * variant of the V-cycle smoother built on its method (the p = 3 smoother weakens near the
  * surrogate boundary, Sec. 5.3).  After the finest level's post-smoothing every boundary cell K
- * (a cell owning a surrogate face) gets u_K += scale * s_K * MLP(x_K), where
+ * (a cell owning a surrogate face) gets u_K += scale * s_K * h^(2-d) * MLP(x_K) (h^(2-d): the
+ * operator scales like h^(d-2), so the network's outputs are mesh-independent), where
  *   x_K = [ patch residual / s_K, d / h at every face point, kappa(K), surrogate-face mask ],
  *   s_K = |patch residual|_2 (1 if zero),
  * the patch being the 3^d cells K + o, o in {-1,0,1}^d (x fastest), their residual r - A u with
@@ -338,6 +339,13 @@ int sbm_mlp_forward(void* mlp, const float* X_dev, int rows, float* Y_dev);
  * packed layout (host), and the loss.  X_dev [rows][F], T_dev [rows][O] device FP32. */
 int sbm_mlp_gradients(void* mlp, const float* X_dev, const float* T_dev, int rows, float* grad_host,
                       double* loss);
+/* Normalises the stored training targets to unit root mean square: computes rms = sqrt(mean T^2)
+ * over every stored target entry (device, deterministic), divides the stored targets by it and
+ * returns it in *rms (1 and no change if the targets are all zero).  A network trained afterwards
+ * predicts targets / rms; attach it with scale = rms (sbm_attach_mlp) to restore the units.  The
+ * training loss is then the mean squared error relative to the targets' mean square.
+ * SBM_ERR_ARG if the set is empty. */
+int sbm_mlp_target_scale(void* mlp, double* rms);
 /* The MLP's training set (filled by sbm_collect): number of stored rows; empty it. */
 int sbm_mlp_num_samples(const void* mlp, long long* n);
 int sbm_mlp_clear_samples(void* mlp);
@@ -360,7 +368,7 @@ int sbm_learned_cells(void* ctx, int* n_bnd, int* cells_host);
 /* Training pairs: from each of the n_starts initial vectors u0_dev[k][N] (dtype, the V-cycle
  * precision used), run n_cycles steps of u <- u + V(-A u) on A u = 0 (plain V-cycles, exact
  * solution 0) and after each step append, for every boundary cell, (x_K from r = -A u,
- * target -u_K / s_K) to the MLP's training set.  *n_added = rows appended. */
+ * target -u_K / (s_K h^(2-d))) to the MLP's training set.  *n_added = rows appended. */
 int sbm_collect(void* ctx, void* mlp, int dtype, const void* u0_dev, int n_starts, int n_cycles,
                 long long* n_added);
 /* Attach (mlp non-NULL) or detach (NULL) the correction to the context's V-cycle with the given

@@ -3,7 +3,7 @@
 The paper has no learned component; this is the learned variant of the V-cycle smoother built on
 the paper's method (its p = 3 smoother weakens near the surrogate boundary, Sec. 5.3).  After
 the finest-level post-smoothing, every boundary cell K (a cell owning a surrogate face) gets a
-correction u_K += s * MLP(x_K), where
+correction u_K += s * h^(2-d) * MLP(x_K), where
 
   x_K = [ patch residual / s , d / h on every face point , kappa(K) , surrogate-face mask ]
   s   = || patch residual ||_2  (1 if the patch residual is zero)
@@ -17,7 +17,8 @@ correction u_K += s * MLP(x_K), where
 
 MLP: two hidden layers with ReLU, y = W3^T relu(W2^T relu(W1^T x + b1) + b2) + b3 (weights
 stored input-major, W1: F x H).  Training minimises the mean squared error between y and
-target / s, where the target is the cell's error (exact solution minus u).
+target / (s h^(2-d)), where the target is the cell's error (exact solution minus u); h^(2-d) is the
+scale of A^-1 (the operator scales like h^(d-2)), which makes the targets mesh-independent.
 """
 from __future__ import annotations
 
@@ -145,12 +146,19 @@ def boundary_cells(level: MG.Level):
     return level.geom.boundary_cells()
 
 
-def correction(net: MLP, cells):
-    """V-cycle hook: z_K += s * MLP(x_K) for the boundary cells, x from r - A z (finest level)."""
+def correction_unit(level: MG.Level) -> float:
+    """Unit of the network's outputs, h^(2-d): the operator scales like h^(d-2), so the error of a
+    cell relative to its patch residual norm scales like h^(2-d)."""
+    return level.geom.h ** (2 - level.prob.dim)
+
+
+def correction(net: MLP, cells, scale: float = 1.0):
+    """V-cycle hook: z_K += scale * s * h^(2-d) * MLP(x_K) for the boundary cells, x from r - A z
+    (finest level)."""
     def apply(level: MG.Level, z: np.ndarray, r: np.ndarray):
         res = r - level.A @ z
         X, s = features(level, res, cells)
-        Y = net.forward(X) * s[:, None]
+        Y = net.forward(X) * (scale * correction_unit(level)) * s[:, None]
         nb = level.nb
         for row, a in enumerate(cells):
             z[a * nb:(a + 1) * nb] += Y[row]
@@ -161,8 +169,8 @@ def training_pairs(H: MG.Hierarchy, n_starts: int, n_cycles: int, seed: int, u0s
     """(X, T) from the stationary V-cycle iteration u <- u + V(-A u) on A u = 0 from seeded random
     u0 in U[-1, 1] (or the given starts u0s): the exact solution is 0, so after each finest-level
     post-smoothing the error of the finest iterate is -u.  Features use r = -A u; targets are
-    -u_K / s.  Rows: for each start, for each step, one per boundary cell (`cells`, default the
-    boundary cells in natural order)."""
+    -u_K / (s h^(2-d)).  Rows: for each start, for each step, one per boundary cell (`cells`, default
+    the boundary cells in natural order)."""
     F = H.finest
     cells = boundary_cells(F) if cells is None else cells
     nb = F.nb
@@ -175,7 +183,7 @@ def training_pairs(H: MG.Hierarchy, n_starts: int, n_cycles: int, seed: int, u0s
         u_new = state["u"] + z
         res = -(level.A @ u_new)
         X, s = features(level, res, cells)
-        T = np.stack([-u_new[a * nb:(a + 1) * nb] for a in cells]) / s[:, None]
+        T = np.stack([-u_new[a * nb:(a + 1) * nb] for a in cells]) / (s[:, None] * correction_unit(level))
         Xs.append(X)
         Ts.append(T)
 

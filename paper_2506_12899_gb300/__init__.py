@@ -31,7 +31,7 @@ SYMBOLS = ("sbm_setup", "sbm_setup_host", "sbm_host_apply", "sbm_host_rhs", "sbm
            "sbm_prolong_add", "sbm_coarse_solve", "sbm_vcycle", "sbm_dots", "sbm_dots_noalloc", "sbm_gram_schmidt", "sbm_l2_error", "sbm_solve",
            "sbm_solve_host", "sbm_mlp_create", "sbm_mlp_destroy", "sbm_mlp_shape", "sbm_mlp_set_params",
            "sbm_mlp_get_params", "sbm_mlp_forward", "sbm_mlp_gradients", "sbm_mlp_num_samples",
-           "sbm_mlp_clear_samples", "sbm_mlp_train", "sbm_mlp_save", "sbm_mlp_load", "sbm_learned_features",
+           "sbm_mlp_clear_samples", "sbm_mlp_target_scale", "sbm_mlp_train", "sbm_mlp_save", "sbm_mlp_load", "sbm_learned_features",
            "sbm_learned_cells", "sbm_collect", "sbm_attach_mlp", "sbm_async_wait_selftest")
 
 
@@ -138,6 +138,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.sbm_mlp_gradients.argtypes = [vp, vp, vp, ip, vp, ctypes.POINTER(ctypes.c_double)]
     lib.sbm_mlp_num_samples.argtypes = [vp, llp]
     lib.sbm_mlp_clear_samples.argtypes = [vp]
+    lib.sbm_mlp_target_scale.argtypes = [vp, ctypes.POINTER(ctypes.c_double)]
     lib.sbm_mlp_train.argtypes = [vp, ip, ip, ctypes.c_float, ctypes.c_ulonglong, ctypes.POINTER(ctypes.c_double)]
     lib.sbm_mlp_save.argtypes = [vp, ctypes.c_char_p]
     lib.sbm_mlp_load.argtypes = [vp, ctypes.c_char_p]
@@ -505,6 +506,12 @@ class Mlp:
 
     def clear_samples(self) -> None:
         _check(self.lib.sbm_mlp_clear_samples(self.h))
+
+    def target_scale(self) -> float:
+        """Normalise the stored targets to unit RMS; returns the RMS (attach with scale=RMS)."""
+        r = ctypes.c_double()
+        _check(self.lib.sbm_mlp_target_scale(self.h, ctypes.byref(r)))
+        return r.value
 
     def train(self, epochs: int = 20, batch: int = 4096, lr: float = 1e-3, seed: int = 0) -> float:
         loss = ctypes.c_double()

@@ -700,7 +700,9 @@ void apply_learned(Context& C, DevLevel& L, const R* r, R* z, cudaStream_t s) {
   CUDA_TRY(launch_mlp_features<R>(nb, C.lf_npatch, L.H.np, C.lf_nstat, C.lf_Fpad, C.mlp_patch, C.mlp_stat, res,
                                   C.mlp_X, C.mlp_s, s));
   M.forward(C.mlp_X, nb, C.mlp_Y, C.mlp_H1, C.mlp_H2, s);
-  CUDA_TRY(launch_mlp_scatter<R>(nb, M.np, M.O, C.mlp_cells, C.mlp_Y, C.mlp_s, C.mlp_scale, z, s));
+  // the network predicts the correction in units of s h^(2-d) (A scales like h^(d-2))
+  const float hs = (float)std::pow(L.H.h, 2 - L.H.dim);
+  CUDA_TRY(launch_mlp_scatter<R>(nb, M.np, M.O, C.mlp_cells, C.mlp_Y, C.mlp_s, C.mlp_scale * hs, z, s));
 }
 
 // y = D^-1 t on level L: the smoother kernels with every neighbour read as zero and omega = 1 apply
@@ -1104,7 +1106,8 @@ long long collect_impl(Context& C, Mlp& M, const R* u0, int n_starts, int n_cycl
       __nv_bfloat16* X = M.Xd + M.count * M.Fpad;
       CUDA_TRY(launch_mlp_features<R>(nb, C.lf_npatch, F.H.np, C.lf_nstat, C.lf_Fpad, C.mlp_patch, C.mlp_stat, rhs, X,
                                       C.mlp_s, s));
-      CUDA_TRY(launch_mlp_targets<R>(nb, F.H.np, C.mlp_cells, u, C.mlp_s, M.Td + M.count * M.O, s));
+      const float hfac = (float)std::pow(F.H.h, F.H.dim - 2);     // targets -u_K / (s h^(2-d))
+      CUDA_TRY(launch_mlp_targets<R>(nb, F.H.np, C.mlp_cells, u, C.mlp_s, hfac, M.Td + M.count * M.O, s));
       M.count += nb;
     }
   }
@@ -1729,6 +1732,29 @@ int sbm_mlp_train(void* mlp, int epochs, int batch, float lr, unsigned long long
       last = acc / nbatch;
     }
     if (loss) *loss = last;
+    return SBM_OK;
+  });
+}
+
+int sbm_mlp_target_scale(void* mlp, double* rms) {
+  Mlp* M = mlp_of(mlp);
+  if (!M || !rms) return set_error(SBM_ERR_ARG, "bad argument");
+  if (M->count == 0) return set_error(SBM_ERR_ARG, "no training samples");
+  return guarded([&]() -> int {
+    const size_t n = M->count * (size_t)M->O;
+    const int nblk = 152 * 4;
+    double* part = M->alloc<double>(nblk + 1);
+    double sum = 0.0;
+    cudaError_t e = launch_sumsq(n, M->Td, part, nblk, part + nblk, M->s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&sum, part + nblk, sizeof(double), cudaMemcpyDeviceToHost, M->s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(M->s);
+    M->release(part);
+    CUDA_TRY(e);
+    double r = std::sqrt(sum / (double)n);
+    if (!(r > 0.0) || !std::isfinite(r)) r = 1.0;
+    else CUDA_TRY(launch_scale_f(n, (float)(1.0 / r), M->Td, M->s));
+    CUDA_TRY(cudaStreamSynchronize(M->s));
+    *rms = r;
     return SBM_OK;
   });
 }

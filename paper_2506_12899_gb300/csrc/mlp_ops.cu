@@ -214,11 +214,38 @@ __global__ void k_to_bf16(int n, const float* __restrict__ x, __nv_bfloat16* __r
 // T[b][i] = -u[cell(b)][i] / s[b]  (training target: the error of u for the zero solution).
 template <typename TU>
 __global__ void k_mlp_targets(int n_bnd, int np, const int* __restrict__ cell, const TU* __restrict__ u,
-                              const float* __restrict__ s, float* __restrict__ T) {
+                              const float* __restrict__ s, float hfac, float* __restrict__ T) {
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n_bnd * np; e += gridDim.x * blockDim.x) {
     const int b = e / np, i = e % np;
-    T[e] = -(float)u[(size_t)cell[b] * np + i] / s[b];
+    T[e] = -(float)u[(size_t)cell[b] * np + i] * hfac / s[b];
   }
+}
+
+// Sum of squares of x[0..n) in per-block FP64 partial sums, then one fixed-order sum (deterministic).
+__global__ void __launch_bounds__(256) k_sumsq_partial(size_t n, const float* __restrict__ x, double* __restrict__ part) {
+  double acc = 0.0;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    const double v = x[i];
+    acc += v * v;
+  }
+  __shared__ double red[256];
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) part[blockIdx.x] = red[0];
+}
+__global__ void k_sum_final(int nblk, const double* __restrict__ part, double* __restrict__ out) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    double s = 0.0;
+    for (int b = 0; b < nblk; ++b) s += part[b];
+    out[0] = s;
+  }
+}
+__global__ void k_scale_f(size_t n, float a, float* __restrict__ x) {
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) x[i] *= a;
 }
 
 // z[cell(b)][i] += scale * s[b] * Y[b][i]
@@ -348,9 +375,9 @@ cudaError_t launch_to_bf16(int n, const float* x, __nv_bfloat16* y, cudaStream_t
 }
 
 template <typename TU>
-cudaError_t launch_mlp_targets(int n_bnd, int np, const int* cell, const TU* u, const float* s, float* T,
-                               cudaStream_t st) {
-  k_mlp_targets<TU><<<g1(n_bnd * np), 256, 0, st>>>(n_bnd, np, cell, u, s, T);
+cudaError_t launch_mlp_targets(int n_bnd, int np, const int* cell, const TU* u, const float* s, float hfac,
+                               float* T, cudaStream_t st) {
+  k_mlp_targets<TU><<<g1(n_bnd * np), 256, 0, st>>>(n_bnd, np, cell, u, s, hfac, T);
   count_launches();
   return cudaGetLastError();
 }
@@ -391,12 +418,27 @@ template cudaError_t launch_mlp_features<float>(int, int, int, int, int, const i
                                                 __nv_bfloat16*, float*, cudaStream_t);
 template cudaError_t launch_mlp_features<double>(int, int, int, int, int, const int*, const float*, const double*,
                                                  __nv_bfloat16*, float*, cudaStream_t);
-template cudaError_t launch_mlp_targets<float>(int, int, const int*, const float*, const float*, float*, cudaStream_t);
-template cudaError_t launch_mlp_targets<double>(int, int, const int*, const double*, const float*, float*,
+template cudaError_t launch_mlp_targets<float>(int, int, const int*, const float*, const float*, float, float*, cudaStream_t);
+template cudaError_t launch_mlp_targets<double>(int, int, const int*, const double*, const float*, float, float*,
                                                 cudaStream_t);
 template cudaError_t launch_mlp_scatter<float>(int, int, int, const int*, const float*, const float*, float, float*,
                                                cudaStream_t);
 template cudaError_t launch_mlp_scatter<double>(int, int, int, const int*, const float*, const float*, float, double*,
                                                 cudaStream_t);
 
+}  // namespace sbm
+
+namespace sbm {
+cudaError_t launch_sumsq(size_t n, const float* x, double* part, int nblk, double* out, cudaStream_t st) {
+  k_sumsq_partial<<<nblk, 256, 0, st>>>(n, x, part);
+  k_sum_final<<<1, 32, 0, st>>>(nblk, part, out);
+  count_launches(2);
+  return cudaGetLastError();
+}
+cudaError_t launch_scale_f(size_t n, float a, float* x, cudaStream_t st) {
+  size_t g = (n + 255) / 256;
+  k_scale_f<<<(unsigned)(g < 1 ? 1 : (g > 1216 ? 1216 : g)), 256, 0, st>>>(n, a, x);
+  count_launches();
+  return cudaGetLastError();
+}
 }  // namespace sbm

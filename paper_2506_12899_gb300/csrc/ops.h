@@ -357,8 +357,11 @@ cudaError_t launch_adam(int n, float* p, const float* g, float* m, float* v, __n
                         float b2, float eps, int t, cudaStream_t s);
 cudaError_t launch_to_bf16(int n, const float* x, __nv_bfloat16* y, cudaStream_t s);
 template <typename TU>
-cudaError_t launch_mlp_targets(int n_bnd, int np, const int* cell, const TU* u, const float* s, float* T,
+cudaError_t launch_mlp_targets(int n_bnd, int np, const int* cell, const TU* u, const float* s, float hfac, float* T,
                                cudaStream_t st);
+// out[0] = sum of x[i]^2 (part: nblk doubles of per-block sums); x *= a.
+cudaError_t launch_sumsq(size_t n, const float* x, double* part, int nblk, double* out, cudaStream_t st);
+cudaError_t launch_scale_f(size_t n, float a, float* x, cudaStream_t st);
 template <typename TZ>
 cudaError_t launch_mlp_scatter(int n_bnd, int np, int ldy, const int* cell, const float* Y, const float* s,
                                float scale, TZ* z, cudaStream_t st);

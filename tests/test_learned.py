@@ -100,9 +100,11 @@ def test_gradients_match_oracle():
     assert np.linalg.norm(g - go) <= 2e-2 * np.linalg.norm(go)
 
 
-def test_vcycle_with_correction_matches_oracle():
-    """z = V(r) with the correction after the finest post-smoothing, against the oracle hook."""
-    P = pair("star2d_p2_n32")
+@pytest.mark.parametrize("name", ["star2d_p2_n32", "sphere3d_p1_n8"])
+def test_vcycle_with_correction_matches_oracle(name):
+    """z = V(r) with the correction after the finest post-smoothing (in units of s h^(2-d)), against
+    the oracle hook."""
+    P = pair(name)
     net, gm = mlp_pair(P, seed=7)
     for a in (net.W3, net.b3):                           # keep the correction a modest fraction of z
         a *= 0.05
@@ -124,13 +126,15 @@ def test_vcycle_with_correction_matches_oracle():
     assert np.linalg.norm(d - do) <= 2e-2 * np.linalg.norm(do)
 
 
-def test_collect_matches_oracle_targets():
-    """Collected pairs: features of r = -A u and targets -u_K / s_K after one plain V-cycle step."""
+@pytest.mark.parametrize("name", ["disk2d_p1_n32", "sphere3d_p1_n8"])
+def test_collect_matches_oracle_targets(name):
+    """Collected pairs: features of r = -A u and targets -u_K / (s_K h^(2-d)) after one plain V-cycle
+    step; then the targets normalised to unit RMS (sbm_mlp_target_scale)."""
     import paper_2506_12899_gb300 as S
-    P = pair("disk2d_p1_n32")
+    P = pair(name)
     lev = P.H.finest
     L = len(P.H.levels) - 1
-    gm = S.Mlp(2, lev.p, 16)
+    gm = S.Mlp(P.prob.dim, lev.p, 16)
     u0 = W.random_vector(lev.N, 21)
     n = P.gpu.collect(gm, P.to_gpu(u0, L)[None, :].contiguous(), 1)
     cells = bnd_cells_oracle(P)
@@ -145,6 +149,11 @@ def test_collect_matches_oracle_targets():
     gm.set_params(zero)
     loss = gm.train(epochs=1, batch=n, lr=1e-12)
     assert abs(loss - np.mean(To ** 2)) <= 1e-4 * np.mean(To ** 2)
+    rms = gm.target_scale()
+    assert abs(rms - np.sqrt(np.mean(To ** 2))) <= 1e-5 * rms
+    gm.set_params(zero)
+    loss = gm.train(epochs=1, batch=n, lr=1e-12)
+    assert abs(loss - 1.0) <= 1e-4
 
 
 def test_training_reduces_loss():

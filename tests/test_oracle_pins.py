@@ -640,23 +640,26 @@ def _vcycle_matrix(H):
     return M
 
 
-def test_training_pairs_follow_the_error_propagation():
+@pytest.mark.parametrize("prob", [W.disk2d_p1(8, 1).replace(coarsest_n=4), W.sphere3d(8, 1, 2).replace(coarsest_n=4)],
+                         ids=["disk2d", "sphere3d"])
+def test_training_pairs_follow_the_error_propagation(prob):
     """The learned part's training pairs: after k steps of u <- u + V(-A u) on A u = 0 the iterate is
     (I - V A)^k u0 (error propagation of a stationary iteration with a linear preconditioner), so
-    the k-th block of rows must hold targets -u_K / s_K of that iterate and residual features of
-    -A u.  Checked against the explicit matrix power on a tiny mesh; a sign, a stale iterate or
+    the k-th block of rows must hold targets -u_K / (s_K h^(2-d)) of that iterate and residual
+    features of -A u.  Checked against the explicit matrix power on a tiny mesh; a sign, a stale iterate or
     the correction z alone in place of u + z fails it."""
     from oracle import learned as OL
-    H = MG.Hierarchy(W.disk2d_p1(8, 1).replace(coarsest_n=4))
+    H = MG.Hierarchy(prob)
     F = H.finest
     assert len(H.levels) == 2
     cells = OL.boundary_cells(F)
+    dim = prob.dim
     nb = F.nb
     rng = np.random.default_rng(3)
     u0s = [2.0 * rng.random(F.N) - 1.0 for _ in range(2)]
     X, T = OL.training_pairs(H, 2, 3, 0, u0s=u0s)
     nc = len(cells)
-    assert X.shape == (2 * 3 * nc, OL.feature_size(2, 1)) and T.shape == (2 * 3 * nc, nb)
+    assert X.shape == (2 * 3 * nc, OL.feature_size(dim, 1)) and T.shape == (2 * 3 * nc, nb)
     E = np.eye(F.N) - _vcycle_matrix(H) @ F.A.toarray()
     row = 0
     for u0 in u0s:
@@ -664,12 +667,13 @@ def test_training_pairs_follow_the_error_propagation():
         for _ in range(3):
             u = E @ u
             Xo, so = OL.features(F, -(F.A @ u), cells)
-            To = np.stack([-u[a * nb:(a + 1) * nb] for a in cells]) / so[:, None]
+            To = np.stack([-u[a * nb:(a + 1) * nb] for a in cells]) / so[:, None] / F.geom.h ** (2 - F.prob.dim)
             assert np.allclose(X[row:row + nc], Xo, rtol=1e-9, atol=1e-12)
             assert np.allclose(T[row:row + nc], To, rtol=1e-9, atol=1e-12)
             row += nc
-    # the centre block of the patch (offset (0, 0), the fifth of nine) times s is -(A u)_K
+    # the centre block of the patch (offset 0, the middle of the 3^d blocks) times s is -(A u)_K
     _, so = OL.features(F, -(F.A @ u), cells)
     r = -(F.A @ u)
-    assert np.allclose(X[-nc:, 4 * nb:5 * nb] * so[:, None], np.stack([r[a * nb:(a + 1) * nb] for a in cells]),
+    c = (3 ** dim) // 2
+    assert np.allclose(X[-nc:, c * nb:(c + 1) * nb] * so[:, None], np.stack([r[a * nb:(a + 1) * nb] for a in cells]),
                        rtol=1e-9, atol=1e-12)
