@@ -759,7 +759,7 @@ void additive_smooth(Context& C, DevLevel& L, const R* r, R* z, bool zero, cudaS
 // residual, restriction (Eq. 18), recursion, prolongation (Eq. 17), post-smoothing with reverse
 // colour order; level 0 is solved with the dense coarse inverse.
 template <typename R>
-void vcycle_rec(Context& C, int l, const R* r, R* z, cudaStream_t s) {
+void vcycle_rec(Context& C, int l, const R* r, R* z, cudaStream_t s, bool first_group_done = false) {
   DevLevel& L = C.lv[l];
   const int pi = prec_index<R>();
   if (l == 0) {
@@ -793,18 +793,28 @@ void vcycle_rec(Context& C, int l, const R* r, R* z, cudaStream_t s) {
       additive_smooth<R>(C, L, r, z, k == 0, s);
       continue;
     }
-    CUDA_TRY(launch_smooth<R>(dim, L.H.p, P, 0, k == 0, r, z, s, k > 0));
+    // the first sweep's first colour group may have been done by the restriction from the level above
+    CUDA_TRY(launch_smooth<R>(dim, L.H.p, P, 0, k == 0, r, z, s, k > 0, k == 0 && first_group_done ? 1 : 0));
     if (C.desc.ssor_each) CUDA_TRY(launch_smooth<R>(dim, L.H.p, P, 1, 0, r, z, s, 1));
   }
   DevLevel& Lc = C.lv[l - 1];
   R* rc = static_cast<R*>(Lc.rhs[pi]);
   R* zc = static_cast<R*>(Lc.z[pi]);
+  // The coarse level's first colour group (colour 0) of its first pre-smoothing sweep from zero
+  // needs only its own restricted residual (every neighbour is still zero): the restriction kernel
+  // does it too, unless the coarse level is solved directly or by the one-launch tail.
+  const LevelParams<R>& Pc = params<R>(Lc);
+  const bool fuse = C.desc.smoother == 0 && C.desc.ordering == 0 && C.desc.pre_smooth >= 1 && l - 1 >= 1 &&
+                    l - 1 != C.tail_plan[pi].top &&
+                    restrict_fuses_first_group<R>(dim, L.H.p, P, tparams<R>(L), Lc.H.p, Pc);
   if (Lc.H.n == L.H.n) {                          // p-transfer: residual restricted in the same kernel
-    CUDA_TRY(launch_resid_restrict_p<R>(dim, L.H.p, P, tparams<R>(L), z, r, rc, s, 1));
+    CUDA_TRY(launch_resid_restrict_p<R>(dim, L.H.p, P, tparams<R>(L), z, r, rc, s, 1, fuse ? &Pc : nullptr,
+                                        fuse ? zc : nullptr));
   } else {                                        // h-transfer: coarse cells gather their children
-    CUDA_TRY(launch_resid_restrict_h<R>(dim, P, tparams<R>(L), z, r, rc, s, 1));
+    CUDA_TRY(launch_resid_restrict_h<R>(dim, P, tparams<R>(L), z, r, rc, s, 1, fuse ? &Pc : nullptr,
+                                        fuse ? zc : nullptr));
   }
-  vcycle_rec<R>(C, l - 1, rc, zc, s);
+  vcycle_rec<R>(C, l - 1, rc, zc, s, fuse);
   CUDA_TRY(launch_prolong<R>(dim, L.H.p, Lc.H.p, tparams<R>(L), zc, z, s, 1));
   for (int k = 0; k < C.desc.post_smooth; ++k) {
     if (C.desc.smoother != 0) {

@@ -64,12 +64,17 @@ __global__ void __launch_bounds__(kCellThreads) k_smooth_cell(const __grid_const
 }
 
 // Residual and p-restriction fused, one thread per cell (Eqs. 11, 18).
-template <int D, int N1, int NC, typename R>
+// SM0: also the first colour group (colour 0) of the coarse level's first pre-smoothing sweep from
+// zero, zc_K = omega A_KK^-1 rc_K for coarse cells K of colour 0 (their neighbours, of later
+// colours, are still zero), with the coarse level's parameters Pc; that sweep then starts at group 1.
+template <int D, int N1, int NC, typename R, bool SM0>
 __global__ void __launch_bounds__(kCellThreads) k_resid_restrict_p_cell(const __grid_constant__ LevelParams<R> P,
                                                                         const __grid_constant__ TransferParams<R> T,
                                                                         const R* __restrict__ u,
                                                                         const R* __restrict__ f, R* __restrict__ rc,
-                                                                        int early) {
+                                                                        int early,
+                                                                        const __grid_constant__ LevelParams<R> Pc,
+                                                                        R* __restrict__ zc) {
   constexpr int NP = CD<D, N1>::NP;
   constexpr int NPC = D == 2 ? NC * NC : NC * NC * NC;
   const int a = blockIdx.x * blockDim.x + threadIdx.x;
@@ -87,6 +92,7 @@ __global__ void __launch_bounds__(kCellThreads) k_resid_restrict_p_cell(const __
   cell_apply<D, N1, R, R>(P, u, a, nb, r);
 #pragma unroll
   for (int i = 0; i < NP; ++i) r[i] = fa[i] - r[i];
+  R out[NPC];
 #pragma unroll
   for (int j = 0; j < NPC; ++j) {
     const int j0 = j % NC, j1 = (j / NC) % NC, j2 = D == 3 ? j / (NC * NC) : 0;
@@ -98,7 +104,17 @@ __global__ void __launch_bounds__(kCellThreads) k_resid_restrict_p_cell(const __
       if (D == 3) wgt *= T.Pp[i2 * NC + j2];
       acc += wgt * r[i];
     }
+    out[j] = acc;
     rc[(size_t)a * NPC + j] = acc;
+  }
+  if constexpr (SM0) {
+    if (a < Pc.colour_start[1]) {                    // same mesh: the coarse cell has index a
+      R y[NPC];
+      block_solve<D, NC, R>(Pc, a < Pc.colour_nbnd[0] ? Pc.bstart[0] + a : -1, out, y);
+#pragma unroll
+      for (int j = 0; j < NPC; ++j) y[j] = Pc.omega == R(1) ? y[j] : Pc.omega * y[j];
+      store_cell<D, NC, R>(zc, a, y);
+    }
   }
 }
 
@@ -113,12 +129,16 @@ __device__ __forceinline__ R h_weight(const TransferParams<R>& T, int o, int i, 
 
 // One group of 2^D adjacent lanes per coarse cell, lane o of the group handling child o: the
 // child's residual in registers, its restriction, then a fixed butterfly sum over the group.
-template <int D, typename R>
+// SM0: also the first colour group of the coarse level's first pre-smoothing sweep from zero (see
+// k_resid_restrict_p_cell), computed by lane 0 of each coarse cell's group.
+template <int D, typename R, bool SM0>
 __global__ void __launch_bounds__(kCellThreads) k_resid_restrict_h_cell(const __grid_constant__ LevelParams<R> P,
                                                                         const __grid_constant__ TransferParams<R> T,
                                                                         const R* __restrict__ u,
                                                                         const R* __restrict__ f, R* __restrict__ rc,
-                                                                        int early) {
+                                                                        int early,
+                                                                        const __grid_constant__ LevelParams<R> Pc,
+                                                                        R* __restrict__ zc) {
   constexpr int NCOL = 1 << D, NP = CD<D, 2>::NP;
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   const int cc = t / NCOL, o = t % NCOL;
@@ -153,9 +173,19 @@ __global__ void __launch_bounds__(kCellThreads) k_resid_restrict_h_cell(const __
   for (int off = 1; off < NCOL; off <<= 1)
 #pragma unroll
     for (int j = 0; j < NP; ++j) out[j] += __shfl_xor_sync(0xffffffffu, out[j], off);
-  if (o == 0 && cc < T.n_act_c)
+  if (o == 0 && cc < T.n_act_c) {
 #pragma unroll
     for (int j = 0; j < NP; ++j) rc[(size_t)cc * NP + j] = out[j];
+    if constexpr (SM0) {
+      if (cc < Pc.colour_start[1]) {
+        R y[NP];
+        block_solve<D, 2, R>(Pc, cc < Pc.colour_nbnd[0] ? Pc.bstart[0] + cc : -1, out, y);
+#pragma unroll
+        for (int j = 0; j < NP; ++j) y[j] = Pc.omega == R(1) ? y[j] : Pc.omega * y[j];
+        store_cell<D, 2, R>(zc, cc, y);
+      }
+    }
+  }
 }
 
 
@@ -719,11 +749,11 @@ cudaError_t launch_apply_cell(int dim, int p, const LevelParams<R>& P, const TI*
 
 template <typename R>
 cudaError_t launch_smooth_cell(int dim, int p, const LevelParams<R>& P, int reverse, int zero_start, const R* f,
-                               R* u, cudaStream_t s, int early) {
+                               R* u, cudaStream_t s, int early, int first_group) {
   if (reverse) zero_start = 0;
   int launched = 0;
   const int ng = n_colour_groups(P, dim);
-  for (int q = 0; q < ng; ++q) {     // (the launcher in level_ops.cu chose this path for the level)
+  for (int q = first_group; q < ng; ++q) {   // (the launcher in level_ops.cu chose this path for the level)
     const int g = reverse ? ng - 1 - q : q;
     const int zm = group_zero_mode(P, zero_start, q);
     const unsigned bs = cell_block(group_cells(P, dim, g));
@@ -741,25 +771,43 @@ cudaError_t launch_smooth_cell(int dim, int p, const LevelParams<R>& P, int reve
 
 template <typename R>
 cudaError_t launch_resid_restrict_p_cell(int dim, int pf, const LevelParams<R>& P, const TransferParams<R>& T,
-                                        const R* u, const R* f, R* rc, cudaStream_t s, int early) {
+                                        const R* u, const R* f, R* rc, cudaStream_t s, int early,
+                                        const LevelParams<R>* Pc, R* zc) {
   if (P.n_act == 0) return cudaSuccess;
   const unsigned bs = cell_block(P.n_act), g = cdiv(P.n_act, bs);
-  if (dim == 2 && pf == 2) SBM_PDL((k_resid_restrict_p_cell<2, 3, 2, R>), g, bs, 0, s, P, T, u, f, rc, early);
-  else if (dim == 2 && pf == 3) SBM_PDL((k_resid_restrict_p_cell<2, 4, 3, R>), g, bs, 0, s, P, T, u, f, rc, early);
-  else if (dim == 3 && pf == 2) SBM_PDL((k_resid_restrict_p_cell<3, 3, 2, R>), g, bs, 0, s, P, T, u, f, rc, early);
+  const bool sm0 = Pc != nullptr && zc != nullptr;
+  const LevelParams<R>& Q = sm0 ? *Pc : P;           // unused without the fused first group
+#define SBM_RRPC(D, N1, NC)                                                                                \
+  {                                                                                                        \
+    if (sm0) SBM_PDL((k_resid_restrict_p_cell<D, N1, NC, R, true>), g, bs, 0, s, P, T, u, f, rc, early, Q, zc); \
+    else SBM_PDL((k_resid_restrict_p_cell<D, N1, NC, R, false>), g, bs, 0, s, P, T, u, f, rc, early, Q, zc);    \
+  }
+  if (dim == 2 && pf == 2) SBM_RRPC(2, 3, 2)
+  else if (dim == 2 && pf == 3) SBM_RRPC(2, 4, 3)
+  else if (dim == 3 && pf == 2) SBM_RRPC(3, 3, 2)
   else return cudaErrorInvalidValue;
+#undef SBM_RRPC
   count_launches();
   return cudaGetLastError();
 }
 
 template <typename R>
 cudaError_t launch_resid_restrict_h_cell(int dim, const LevelParams<R>& P, const TransferParams<R>& T, const R* u,
-                                        const R* f, R* rc, cudaStream_t s, int early) {
+                                        const R* f, R* rc, cudaStream_t s, int early, const LevelParams<R>* Pc,
+                                        R* zc) {
   if (T.n_act_c == 0) return cudaSuccess;
   const unsigned bs = cell_block((size_t)T.n_act_c << dim), g = cdiv((size_t)T.n_act_c << dim, bs);
-  if (dim == 2) SBM_PDL((k_resid_restrict_h_cell<2, R>), g, bs, 0, s, P, T, u, f, rc, early);
-  else if (dim == 3) SBM_PDL((k_resid_restrict_h_cell<3, R>), g, bs, 0, s, P, T, u, f, rc, early);
-  else return cudaErrorInvalidValue;
+  const bool sm0 = Pc != nullptr && zc != nullptr;
+  const LevelParams<R>& Q = sm0 ? *Pc : P;
+  if (dim == 2) {
+    if (sm0) SBM_PDL((k_resid_restrict_h_cell<2, R, true>), g, bs, 0, s, P, T, u, f, rc, early, Q, zc);
+    else SBM_PDL((k_resid_restrict_h_cell<2, R, false>), g, bs, 0, s, P, T, u, f, rc, early, Q, zc);
+  } else if (dim == 3) {
+    if (sm0) SBM_PDL((k_resid_restrict_h_cell<3, R, true>), g, bs, 0, s, P, T, u, f, rc, early, Q, zc);
+    else SBM_PDL((k_resid_restrict_h_cell<3, R, false>), g, bs, 0, s, P, T, u, f, rc, early, Q, zc);
+  } else {
+    return cudaErrorInvalidValue;
+  }
   count_launches();
   return cudaGetLastError();
 }
@@ -893,19 +941,22 @@ template cudaError_t launch_apply_cell<float, double>(int, int, const LevelParam
 template cudaError_t launch_apply_cell<float, dfl>(int, int, const LevelParams<dfl>&, const float*, const dfl*,
                                                    dfl*, int, cudaStream_t);
 template cudaError_t launch_smooth_cell<double>(int, int, const LevelParams<double>&, int, int, const double*,
-                                                double*, cudaStream_t, int);
+                                                double*, cudaStream_t, int, int);
 template cudaError_t launch_smooth_cell<float>(int, int, const LevelParams<float>&, int, int, const float*, float*,
-                                               cudaStream_t, int);
+                                               cudaStream_t, int, int);
 template cudaError_t launch_resid_restrict_p_cell<double>(int, int, const LevelParams<double>&,
                                                           const TransferParams<double>&, const double*, const double*,
-                                                          double*, cudaStream_t, int);
+                                                          double*, cudaStream_t, int, const LevelParams<double>*,
+                                                          double*);
 template cudaError_t launch_resid_restrict_p_cell<float>(int, int, const LevelParams<float>&,
                                                          const TransferParams<float>&, const float*, const float*,
-                                                         float*, cudaStream_t, int);
+                                                         float*, cudaStream_t, int, const LevelParams<float>*, float*);
 template cudaError_t launch_resid_restrict_h_cell<double>(int, const LevelParams<double>&,
                                                           const TransferParams<double>&, const double*, const double*,
-                                                          double*, cudaStream_t, int);
+                                                          double*, cudaStream_t, int, const LevelParams<double>*,
+                                                          double*);
 template cudaError_t launch_resid_restrict_h_cell<float>(int, const LevelParams<float>&, const TransferParams<float>&,
-                                                         const float*, const float*, float*, cudaStream_t, int);
+                                                         const float*, const float*, float*, cudaStream_t, int,
+                                                         const LevelParams<float>*, float*);
 
 }  // namespace sbm

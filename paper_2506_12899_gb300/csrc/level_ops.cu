@@ -630,13 +630,16 @@ cudaError_t launch_apply(int dim, int p, const LevelParams<R>& P, const TI* x, c
 
 template <typename R>
 cudaError_t launch_smooth(int dim, int p, const LevelParams<R>& P, int reverse, int zero_start, const R* f, R* u,
-                          cudaStream_t s, int early) {
+                          cudaStream_t s, int early, int first_group) {
   if constexpr (std::is_same<R, float>::value) {
-    if (staged_kernels(dim, p) && P.staged_min > 0 && P.n_act >= (1 << dim) * P.staged_min)
+    if (staged_kernels(dim, p) && P.staged_min > 0 && P.n_act >= (1 << dim) * P.staged_min) {
+      if (first_group != 0) return cudaErrorInvalidValue;
       return launch_smooth_staged(dim, p, P, reverse, zero_start, f, u, s, early);
+    }
   }
   if (cell_smoother(dim, p) && P.cell_min > 0 && P.n_act >= (1 << dim) * P.cell_min)
-    return launch_smooth_cell<R>(dim, p, P, reverse, zero_start, f, u, s, early);
+    return launch_smooth_cell<R>(dim, p, P, reverse, zero_start, f, u, s, early, first_group);
+  if (first_group != 0) return cudaErrorInvalidValue;
   if (reverse) zero_start = 0;
   int launched = 0;
   const int ng = n_colour_groups(P, dim);
@@ -699,6 +702,22 @@ template cudaError_t launch_smoother_update<double>(size_t, double, double, cons
 template cudaError_t launch_smoother_update<float>(size_t, float, float, const float*, float*, float*, int,
                                                    cudaStream_t);
 
+template <typename R>
+bool restrict_fuses_first_group(int dim, int pf, const LevelParams<R>& P, const TransferParams<R>& T, int pc,
+                                const LevelParams<R>& Pc) {
+  const bool fine_cell = T.hmode ? (P.cell_min > 0 && T.n_act_f >= P.cell_min)
+                                 : (cell_kernels(dim, pf) && P.cell_min > 0 && P.n_act >= P.cell_min);
+  bool coarse_cell = cell_smoother(dim, pc) && Pc.cell_min > 0 && Pc.n_act >= (1 << dim) * Pc.cell_min &&
+                     Pc.ordering == 0;
+  if constexpr (std::is_same<R, float>::value)
+    coarse_cell = coarse_cell && !(staged_kernels(dim, pc) && Pc.staged_min > 0 && Pc.n_act >= (1 << dim) * Pc.staged_min);
+  return fine_cell && coarse_cell;
+}
+template bool restrict_fuses_first_group<double>(int, int, const LevelParams<double>&, const TransferParams<double>&,
+                                                 int, const LevelParams<double>&);
+template bool restrict_fuses_first_group<float>(int, int, const LevelParams<float>&, const TransferParams<float>&, int,
+                                                const LevelParams<float>&);
+
 #define SBM_DISPATCH_T(dim, pf, pc, MACRO)                          \
   do {                                                              \
     if (dim == 2 && pf == 1 && pc == 1) { MACRO(2, 2, 2); }         \
@@ -712,10 +731,11 @@ template cudaError_t launch_smoother_update<float>(size_t, float, float, const f
 
 template <typename R>
 cudaError_t launch_resid_restrict_p(int dim, int pf, const LevelParams<R>& P, const TransferParams<R>& T, const R* u,
-                                   const R* f, R* rc, cudaStream_t s, int early) {
+                                   const R* f, R* rc, cudaStream_t s, int early, const LevelParams<R>* Pc, R* zc) {
   if (P.n_act == 0) return cudaSuccess;
   if (cell_kernels(dim, pf) && P.cell_min > 0 && P.n_act >= P.cell_min)
-    return launch_resid_restrict_p_cell<R>(dim, pf, P, T, u, f, rc, s, early);
+    return launch_resid_restrict_p_cell<R>(dim, pf, P, T, u, f, rc, s, early, Pc, zc);
+  if (Pc || zc) return cudaErrorInvalidValue;       // the fused first group exists on the cell path only
 #define SBM_RRP(D, N1, NC)                                                                         \
   {                                                                                                \
     using Dm = Dims<D, N1>;                                                                        \
@@ -733,10 +753,11 @@ cudaError_t launch_resid_restrict_p(int dim, int pf, const LevelParams<R>& P, co
 
 template <typename R>
 cudaError_t launch_resid_restrict_h(int dim, const LevelParams<R>& P, const TransferParams<R>& T, const R* u,
-                                   const R* f, R* rc, cudaStream_t s, int early) {
+                                   const R* f, R* rc, cudaStream_t s, int early, const LevelParams<R>* Pc, R* zc) {
   if (T.n_act_c == 0) return cudaSuccess;
   if (P.cell_min > 0 && T.n_act_f >= P.cell_min)
-    return launch_resid_restrict_h_cell<R>(dim, P, T, u, f, rc, s, early);
+    return launch_resid_restrict_h_cell<R>(dim, P, T, u, f, rc, s, early, Pc, zc);
+  if (Pc || zc) return cudaErrorInvalidValue;       // the fused first group exists on the cell path only
   if (dim == 2) {
     using Dm = Dims<2, 2>;
     SBM_PDL((k_resid_restrict_h<2, R>), ceil_div(T.n_act_c, Dm::CPB / 4), Dm::NT, 0, s, P, T, u, f, rc, early);
@@ -796,18 +817,21 @@ template cudaError_t launch_apply<float, double>(int, int, const LevelParams<dou
 template cudaError_t launch_apply<float, dfl>(int, int, const LevelParams<dfl>&, const float*, const dfl*, dfl*, int,
                                               cudaStream_t);
 template cudaError_t launch_smooth<double>(int, int, const LevelParams<double>&, int, int, const double*, double*,
-                                           cudaStream_t, int);
+                                               cudaStream_t, int, int);
 template cudaError_t launch_smooth<float>(int, int, const LevelParams<float>&, int, int, const float*, float*,
-                                          cudaStream_t, int);
+                                               cudaStream_t, int, int);
 template cudaError_t launch_resid_restrict_p<double>(int, int, const LevelParams<double>&,
                                                      const TransferParams<double>&, const double*, const double*,
-                                                     double*, cudaStream_t, int);
+                                                     double*, cudaStream_t, int, const LevelParams<double>*, double*);
 template cudaError_t launch_resid_restrict_p<float>(int, int, const LevelParams<float>&, const TransferParams<float>&,
-                                                    const float*, const float*, float*, cudaStream_t, int);
+                                                    const float*, const float*, float*, cudaStream_t, int,
+                                                    const LevelParams<float>*, float*);
 template cudaError_t launch_resid_restrict_h<double>(int, const LevelParams<double>&, const TransferParams<double>&,
-                                                     const double*, const double*, double*, cudaStream_t, int);
+                                                     const double*, const double*, double*, cudaStream_t, int,
+                                                     const LevelParams<double>*, double*);
 template cudaError_t launch_resid_restrict_h<float>(int, const LevelParams<float>&, const TransferParams<float>&,
-                                                    const float*, const float*, float*, cudaStream_t, int);
+                                                    const float*, const float*, float*, cudaStream_t, int,
+                                                    const LevelParams<float>*, float*);
 template cudaError_t launch_restrict<double>(int, int, int, const TransferParams<double>&, const double*, double*,
                                              cudaStream_t);
 template cudaError_t launch_restrict<float>(int, int, int, const TransferParams<float>&, const float*, float*,

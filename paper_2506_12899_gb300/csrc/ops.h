@@ -199,13 +199,17 @@ cudaError_t launch_apply_cell(int dim, int p, const LevelParams<R>& P, const TI*
                               cudaStream_t s);
 template <typename R>
 cudaError_t launch_smooth_cell(int dim, int p, const LevelParams<R>& P, int reverse, int zero_start, const R* f,
-                               R* u, cudaStream_t s, int early);
+                               R* u, cudaStream_t s, int early, int first_group = 0);
+// Pc, zc non-null: the launch also performs the first colour group (colour 0) of the coarse level's
+// first pre-smoothing sweep from zero, zc_K = omega A_KK^-1 rc_K (Pc: the coarse level's parameters).
 template <typename R>
 cudaError_t launch_resid_restrict_p_cell(int dim, int pf, const LevelParams<R>& P, const TransferParams<R>& T,
-                                        const R* u, const R* f, R* rc, cudaStream_t s, int early);
+                                        const R* u, const R* f, R* rc, cudaStream_t s, int early,
+                                        const LevelParams<R>* Pc = nullptr, R* zc = nullptr);
 template <typename R>
 cudaError_t launch_resid_restrict_h_cell(int dim, const LevelParams<R>& P, const TransferParams<R>& T, const R* u,
-                                        const R* f, R* rc, cudaStream_t s, int early);
+                                        const R* f, R* rc, cudaStream_t s, int early,
+                                        const LevelParams<R>* Pc = nullptr, R* zc = nullptr);
 
 // Staged thread-per-cell kernels (staged_ops.cu), FP32 only: the CTA copies its cells and their
 // face neighbours into shared memory with coalesced asynchronous copies before the per-cell
@@ -248,9 +252,11 @@ cudaError_t launch_apply(int dim, int p, const LevelParams<R>& P, const TI* x, c
 // One coloured block Gauss-Seidel sweep (all colours, forward or reverse), one launch per colour
 // group (smooth_segs).  zero_start (forward only): u holds zeros on entry and is not read or
 // cleared beforehand.
+// first_group > 0 (forward sweeps only): the sweep starts at that colour group, the earlier ones
+// having been done by a fused kernel (launch_resid_restrict_*_cell with Pc, zc).
 template <typename R>
 cudaError_t launch_smooth(int dim, int p, const LevelParams<R>& P, int reverse, int zero_start, const R* f, R* u,
-                          cudaStream_t s, int early = 0);
+                          cudaStream_t s, int early = 0, int first_group = 0);
 
 // Update step of the additive smoothers after y = D^-1 r (modes in level_ops.cu: z = b y, z += b y,
 // and the Chebyshev d = a d + b y, z += d forms).
@@ -260,11 +266,18 @@ cudaError_t launch_smoother_update(size_t n, R a, R b, const R* y, R* d, R* z, i
 // rc = P^T (f - A u) for a p-transfer (same mesh, degree pf -> pf - 1), residual not stored.
 template <typename R>
 cudaError_t launch_resid_restrict_p(int dim, int pf, const LevelParams<R>& P, const TransferParams<R>& T, const R* u,
-                                   const R* f, R* rc, cudaStream_t s, int early = 0);
+                                   const R* f, R* rc, cudaStream_t s, int early = 0, const LevelParams<R>* Pc = nullptr,
+                                   R* zc = nullptr);
 // rc = P^T (f - A u) for an h-transfer (p = 1, coarse cells gather their children).
 template <typename R>
 cudaError_t launch_resid_restrict_h(int dim, const LevelParams<R>& P, const TransferParams<R>& T, const R* u,
-                                   const R* f, R* rc, cudaStream_t s, int early = 0);
+                                   const R* f, R* rc, cudaStream_t s, int early = 0, const LevelParams<R>* Pc = nullptr,
+                                   R* zc = nullptr);
+// Whether launch_resid_restrict_{p,h} can fuse the coarse level's first colour group (it takes the
+// thread-per-cell path there and the coarse level's smoother would take it too).
+template <typename R>
+bool restrict_fuses_first_group(int dim, int pf, const LevelParams<R>& P, const TransferParams<R>& T, int pc,
+                                const LevelParams<R>& Pc);
 // rc = P^T rf (restriction) and uf += P ec (prolongation) between level l-1 and l.
 template <typename R>
 cudaError_t launch_restrict(int dim, int pf, int pc, const TransferParams<R>& T, const R* rf, R* rc, cudaStream_t s);
