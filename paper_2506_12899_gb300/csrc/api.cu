@@ -815,10 +815,21 @@ void vcycle_rec(Context& C, int l, const R* r, R* z, cudaStream_t s, bool first_
                                         fuse ? zc : nullptr));
   }
   vcycle_rec<R>(C, l - 1, rc, zc, s, fuse);
-  CUDA_TRY(launch_prolong<R>(dim, L.H.p, Lc.H.p, tparams<R>(L), zc, z, s, 1));
+  // The prolongation z += P zc is folded into the first post-smoothing sweep where that sweep takes
+  // the thread-per-cell Gauss-Seidel path (launch_smooth_cell_pend), else it is its own launch.
+  const bool pend = C.desc.smoother == 0 && C.desc.ordering == 0 && C.desc.post_smooth >= 1 &&
+                    smooth_takes_cell_path<R>(dim, L.H.p, P) &&
+                    ((dim == 2 && L.H.p <= 3) || (dim == 3 && L.H.p == 1));
+  if (!pend) CUDA_TRY(launch_prolong<R>(dim, L.H.p, Lc.H.p, tparams<R>(L), zc, z, s, 1));
   for (int k = 0; k < C.desc.post_smooth; ++k) {
     if (C.desc.smoother != 0) {
       additive_smooth<R>(C, L, r, z, false, s);
+      continue;
+    }
+    if (k == 0 && pend) {
+      CUDA_TRY(launch_smooth_cell_pend<R>(dim, L.H.p, Lc.H.p, P, tparams<R>(L), zc, C.desc.ssor_each ? 0 : 1, r, z,
+                                          s, 1));
+      if (C.desc.ssor_each) CUDA_TRY(launch_smooth<R>(dim, L.H.p, P, 1, 0, r, z, s, 1));
       continue;
     }
     if (C.desc.ssor_each) CUDA_TRY(launch_smooth<R>(dim, L.H.p, P, 0, 0, r, z, s, 1));
