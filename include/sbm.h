@@ -333,6 +333,11 @@ int sbm_mlp_shape(const void* mlp, int* F, int* Fpad, int* H, int* O, long long*
 /* Host FP32 packed parameters in / out; setting them also resets the Adam state. */
 int sbm_mlp_set_params(void* mlp, const float* params_host);
 int sbm_mlp_get_params(const void* mlp, float* params_host);
+/* GEMM implementation of the MLP: 0 (default) the tcgen05 tensor-core kernel (128 x 128 tiles,
+ * FP32 accumulators in tensor memory), 1 the warp-level mma.sync kernel.  Both compute the same
+ * BF16 x BF16 -> FP32 products (summation order differs).  A tensor-core commit that does not arrive
+ * within a bounded wait makes the next synchronising MLP call return SBM_ERR_CUDA. */
+int sbm_mlp_gemm_backend(void* mlp, int backend);
 /* Y_dev[rows][O] = MLP(X_dev[rows][F]) (device FP32 buffers; X is rounded to BF16). */
 int sbm_mlp_forward(void* mlp, const float* X_dev, int rows, float* Y_dev);
 /* Gradient of the mean squared error mean((MLP(X) - T)^2) over the rows x O entries, in the

@@ -30,7 +30,7 @@ SYMBOLS = ("sbm_setup", "sbm_setup_host", "sbm_host_apply", "sbm_host_rhs", "sbm
            "sbm_export_geometry", "sbm_rhs", "sbm_apply", "sbm_residual", "sbm_smooth", "sbm_restrict",
            "sbm_prolong_add", "sbm_coarse_solve", "sbm_vcycle", "sbm_dots", "sbm_dots_noalloc", "sbm_gram_schmidt", "sbm_l2_error", "sbm_solve",
            "sbm_solve_host", "sbm_mlp_create", "sbm_mlp_destroy", "sbm_mlp_shape", "sbm_mlp_set_params",
-           "sbm_mlp_get_params", "sbm_mlp_forward", "sbm_mlp_gradients", "sbm_mlp_num_samples",
+           "sbm_mlp_get_params", "sbm_mlp_gemm_backend", "sbm_mlp_forward", "sbm_mlp_gradients", "sbm_mlp_num_samples",
            "sbm_mlp_clear_samples", "sbm_mlp_target_scale", "sbm_mlp_train", "sbm_mlp_save", "sbm_mlp_load", "sbm_learned_features",
            "sbm_learned_cells", "sbm_collect", "sbm_attach_mlp", "sbm_async_wait_selftest")
 
@@ -135,6 +135,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.sbm_mlp_set_params.argtypes = [vp, vp]
     lib.sbm_mlp_get_params.argtypes = [vp, vp]
     lib.sbm_mlp_forward.argtypes = [vp, vp, ip, vp]
+    lib.sbm_mlp_gemm_backend.argtypes = [vp, ip]
     lib.sbm_mlp_gradients.argtypes = [vp, vp, vp, ip, vp, ctypes.POINTER(ctypes.c_double)]
     lib.sbm_mlp_num_samples.argtypes = [vp, llp]
     lib.sbm_mlp_clear_samples.argtypes = [vp]
@@ -483,6 +484,10 @@ class Mlp:
         if flat.size != self.nparam:
             raise ValueError(f"expected {self.nparam} parameters, got {flat.size}")
         _check(self.lib.sbm_mlp_set_params(self.h, flat.ctypes.data))
+
+    def gemm_backend(self, backend: int) -> None:
+        """0: tcgen05 tensor-core GEMMs (default), 1: warp-level mma.sync GEMMs."""
+        _check(self.lib.sbm_mlp_gemm_backend(self.h, backend))
 
     def forward(self, X):
         rows = X.shape[0]

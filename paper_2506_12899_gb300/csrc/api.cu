@@ -65,6 +65,14 @@ struct DevLevel {
 // per-batch activation buffers.  Parameters are packed W1[Fpad][H] b1[H] W2[H][H] b2[H]
 // W3[H][O] b3[O] (input-major); rows F..Fpad-1 of W1 are zero and stay zero (their gradient
 // is zero because the padded feature columns are zero).
+// The MLP's GEMMs: tcgen05 (backend 0) or mma.sync (1).
+inline cudaError_t gemm_bf16(int backend, int M, int N, int K, int ta, int tb, const __nv_bfloat16* A, int lda,
+                             const __nv_bfloat16* B, int ldb, const float* bias, int relu, float* Cf,
+                             __nv_bfloat16* Cb, int ldc, cudaStream_t s) {
+  return backend == 0 ? launch_gemm_tc(M, N, K, ta, tb, A, lda, B, ldb, bias, relu, Cf, Cb, ldc, s)
+                      : launch_gemm_bf16(M, N, K, ta, tb, A, lda, B, ldb, bias, relu, Cf, Cb, ldc, s);
+}
+
 struct Mlp {
   int dim = 2, p = 1, np = 4, npatch = 9, nstat = 0, F = 0, Fpad = 0, H = 128, O = 4;
   size_t nparam = 0, oW1 = 0, ob1 = 0, oW2 = 0, ob2 = 0, oW3 = 0, ob3 = 0;
@@ -76,6 +84,7 @@ struct Mlp {
   float* Av = nullptr;               // Adam second moments
   __nv_bfloat16* Pb = nullptr;       // BF16 copy of the parameters
   int adam_t = 0;
+  int gemm = 0;                      // 0: tcgen05 tensor cores (tc_gemm.cu), 1: warp-level mma.sync
   size_t cap = 0, count = 0;         // training set rows
   __nv_bfloat16* Xd = nullptr;       // [cap][Fpad]
   float* Td = nullptr;               // [cap][O]
@@ -147,23 +156,23 @@ struct Mlp {
   // Yout[rows][O] = MLP(X) with the BF16 weights, hidden activations into h1, h2 ([rows][H]).
   void forward(const __nv_bfloat16* X, int rows, float* Yout, __nv_bfloat16* h1, __nv_bfloat16* h2,
                cudaStream_t st) const {
-    CUDA_TRY(launch_gemm_bf16(rows, H, Fpad, 0, 0, X, Fpad, W1b(), H, P + ob1, 1, nullptr, h1, H, st));
-    CUDA_TRY(launch_gemm_bf16(rows, H, H, 0, 0, h1, H, W2b(), H, P + ob2, 1, nullptr, h2, H, st));
-    CUDA_TRY(launch_gemm_bf16(rows, O, H, 0, 0, h2, H, W3b(), O, P + ob3, 0, Yout, nullptr, O, st));
+    CUDA_TRY(gemm_bf16(gemm, rows, H, Fpad, 0, 0, X, Fpad, W1b(), H, P + ob1, 1, nullptr, h1, H, st));
+    CUDA_TRY(gemm_bf16(gemm, rows, H, H, 0, 0, h1, H, W2b(), H, P + ob2, 1, nullptr, h2, H, st));
+    CUDA_TRY(gemm_bf16(gemm, rows, O, H, 0, 0, h2, H, W3b(), O, P + ob3, 0, Yout, nullptr, O, st));
   }
   // G = gradient of the mean squared error over the rows of (X, T), after forward(X, rows, Y,
   // H1, H2); loss_part receives per-block partial sums of the squared errors.
   void backward(const __nv_bfloat16* X, const float* T, int rows) {
     CUDA_TRY(launch_mse_grad(rows, O, Y, T, dYf, dYb, 1.0f / ((float)rows * O), loss_part, 152, s));
-    CUDA_TRY(launch_gemm_bf16(H, O, rows, 1, 0, H2, H, dYb, O, nullptr, 0, G + oW3, nullptr, O, s));
+    CUDA_TRY(gemm_bf16(gemm, H, O, rows, 1, 0, H2, H, dYb, O, nullptr, 0, G + oW3, nullptr, O, s));
     CUDA_TRY(launch_colsum(rows, O, dYf, G + ob3, s));
-    CUDA_TRY(launch_gemm_bf16(rows, H, O, 0, 1, dYb, O, W3b(), O, nullptr, 0, dH2, nullptr, H, s));
+    CUDA_TRY(gemm_bf16(gemm, rows, H, O, 0, 1, dYb, O, W3b(), O, nullptr, 0, dH2, nullptr, H, s));
     CUDA_TRY(launch_relu_mask(rows * H, dH2, H2, dZ2b, s));
-    CUDA_TRY(launch_gemm_bf16(H, H, rows, 1, 0, H1, H, dZ2b, H, nullptr, 0, G + oW2, nullptr, H, s));
+    CUDA_TRY(gemm_bf16(gemm, H, H, rows, 1, 0, H1, H, dZ2b, H, nullptr, 0, G + oW2, nullptr, H, s));
     CUDA_TRY(launch_colsum(rows, H, dH2, G + ob2, s));
-    CUDA_TRY(launch_gemm_bf16(rows, H, H, 0, 1, dZ2b, H, W2b(), H, nullptr, 0, dH1, nullptr, H, s));
+    CUDA_TRY(gemm_bf16(gemm, rows, H, H, 0, 1, dZ2b, H, W2b(), H, nullptr, 0, dH1, nullptr, H, s));
     CUDA_TRY(launch_relu_mask(rows * H, dH1, H1, dZ1b, s));
-    CUDA_TRY(launch_gemm_bf16(Fpad, H, rows, 1, 0, X, Fpad, dZ1b, H, nullptr, 0, G + oW1, nullptr, H, s));
+    CUDA_TRY(gemm_bf16(gemm, Fpad, H, rows, 1, 0, X, Fpad, dZ1b, H, nullptr, 0, G + oW1, nullptr, H, s));
     CUDA_TRY(launch_colsum(rows, H, dH1, G + ob1, s));
   }
 };
@@ -815,21 +824,10 @@ void vcycle_rec(Context& C, int l, const R* r, R* z, cudaStream_t s, bool first_
                                         fuse ? zc : nullptr));
   }
   vcycle_rec<R>(C, l - 1, rc, zc, s, fuse);
-  // The prolongation z += P zc is folded into the first post-smoothing sweep where that sweep takes
-  // the thread-per-cell Gauss-Seidel path (launch_smooth_cell_pend), else it is its own launch.
-  const bool pend = C.desc.smoother == 0 && C.desc.ordering == 0 && C.desc.post_smooth >= 1 &&
-                    smooth_takes_cell_path<R>(dim, L.H.p, P) &&
-                    ((dim == 2 && L.H.p <= 3) || (dim == 3 && L.H.p == 1));
-  if (!pend) CUDA_TRY(launch_prolong<R>(dim, L.H.p, Lc.H.p, tparams<R>(L), zc, z, s, 1));
+  CUDA_TRY(launch_prolong<R>(dim, L.H.p, Lc.H.p, tparams<R>(L), zc, z, s, 1));
   for (int k = 0; k < C.desc.post_smooth; ++k) {
     if (C.desc.smoother != 0) {
       additive_smooth<R>(C, L, r, z, false, s);
-      continue;
-    }
-    if (k == 0 && pend) {
-      CUDA_TRY(launch_smooth_cell_pend<R>(dim, L.H.p, Lc.H.p, P, tparams<R>(L), zc, C.desc.ssor_each ? 0 : 1, r, z,
-                                          s, 1));
-      if (C.desc.ssor_each) CUDA_TRY(launch_smooth<R>(dim, L.H.p, P, 1, 0, r, z, s, 1));
       continue;
     }
     if (C.desc.ssor_each) CUDA_TRY(launch_smooth<R>(dim, L.H.p, P, 0, 0, r, z, s, 1));
@@ -1678,6 +1676,13 @@ int sbm_mlp_get_params(const void* mlp, float* params_host) {
   });
 }
 
+int sbm_mlp_gemm_backend(void* mlp, int backend) {
+  Mlp* M = mlp_of(mlp);
+  if (!M || backend < 0 || backend > 1) return set_error(SBM_ERR_ARG, "bad argument");
+  M->gemm = backend;
+  return SBM_OK;
+}
+
 int sbm_mlp_forward(void* mlp, const float* X_dev, int rows, float* Y_dev) {
   Mlp* M = mlp_of(mlp);
   if (!M || !X_dev || !Y_dev || rows < 0) return set_error(SBM_ERR_ARG, "bad argument");
@@ -1700,6 +1705,7 @@ int sbm_mlp_gradients(void* mlp, const float* X_dev, const float* T_dev, int row
     M->forward(M->Xb, rows, M->Y, M->H1, M->H2, M->s);
     M->backward(M->Xb, M->Tb, rows);
     const double l = read_loss(*M, rows);
+    if (tc_fault_take() != 0) return set_error(SBM_ERR_CUDA, "a tensor-core GEMM commit did not arrive in time");
     if (loss) *loss = l;
     if (grad_host) get_packed(*M, M->G, grad_host);
     return SBM_OK;
@@ -1750,6 +1756,7 @@ int sbm_mlp_train(void* mlp, int epochs, int batch, float lr, unsigned long long
       float acc = 0;
       CUDA_TRY(cudaMemcpyAsync(&acc, M->loss_acc, sizeof(float), cudaMemcpyDeviceToHost, M->s));
       CUDA_TRY(cudaStreamSynchronize(M->s));
+      if (tc_fault_take() != 0) return set_error(SBM_ERR_CUDA, "a tensor-core GEMM commit did not arrive in time");
       last = acc / nbatch;
     }
     if (loss) *loss = last;

@@ -63,103 +63,6 @@ __global__ void __launch_bounds__(kCellThreads) k_smooth_cell(const __grid_const
   smooth_one<D, N1, R>(P, G.col[sg], zero_start, G.cs[sg], G.nbnd[sg], G.b0[sg], a, nb, t, u);
 }
 
-// v += (P ec)|_a (Eq. 17) for fine cell a: the coarse polynomial of its parent (h-transfer, parent
-// code; none for a fine cell without an active parent) or of the same cell (p-transfer) at the fine
-// nodes.
-template <int D, int NF, int NC, typename R>
-__device__ __forceinline__ void add_prolongation(const TransferParams<R>& T, const R* __restrict__ ec, int a,
-                                                 R (&v)[CD<D, NF>::NP]) {
-  constexpr int NPF = CD<D, NF>::NP, NPC = CD<D, NC>::NP;
-  int par;
-  const R *P0, *P1, *P2;
-  if (T.hmode) {
-    const int code = T.parent_code[a];
-    if (code < 0) return;
-    par = code >> 3;
-    P0 = T.Ph[code & 1];
-    P1 = T.Ph[(code >> 1) & 1];
-    P2 = T.Ph[(code >> 2) & 1];
-  } else {
-    par = a;
-    P0 = P1 = P2 = T.Pp;
-  }
-  R e[NPC];
-  load_cell<D, NC, R, R>(ec, par, e);
-#pragma unroll
-  for (int i = 0; i < NPF; ++i) {
-    const int i0 = i % NF, i1 = (i / NF) % NF, i2 = D == 3 ? i / (NF * NF) : 0;
-    R s2 = 0;
-#pragma unroll
-    for (int j2 = 0; j2 < (D == 3 ? NC : 1); ++j2) {
-      R s1 = 0;
-#pragma unroll
-      for (int j1 = 0; j1 < NC; ++j1) {
-        R s0 = 0;
-#pragma unroll
-        for (int j0 = 0; j0 < NC; ++j0) s0 += P0[i0 * NC + j0] * e[j0 + NC * j1 + NC * NC * j2];
-        s1 += P1[i1 * NC + j1] * s0;
-      }
-      s2 += (D == 3 ? P2[i2 * NC + j2] : R(1)) * s1;
-    }
-    v[i] += s2;
-  }
-}
-
-// k_smooth_cell for the first post-smoothing sweep with the prolongation u += P ec still pending
-// (Eq. 17 folded into the sweep, which then needs no separate prolongation launch): a cell of a
-// group not yet visited in this sweep still holds its pre-prolongation value, so a neighbour of
-// such a group is read as u_N + (P ec)_N, and the cell's own value as u_K + (P ec)_K; every cell is
-// visited exactly once in the sweep, and its update writes its prolongated and smoothed value.
-// reverse: the sweep visits the groups d .. 0 (a neighbour of colour c ^ 2^k is unvisited when it
-// has fewer odd bits), else 0 .. d.
-template <int D, int N1, int NC, typename R>
-__global__ void __launch_bounds__(kCellThreads) k_smooth_cell_pend(const __grid_constant__ LevelParams<R> P,
-                                                                   const __grid_constant__ SmoothSegs G,
-                                                                   const __grid_constant__ TransferParams<R> T,
-                                                                   const R* __restrict__ ec, int reverse,
-                                                                   const R* __restrict__ f, R* __restrict__ u,
-                                                                   int early) {
-  constexpr int NP = CD<D, N1>::NP;
-  int sg = 0;
-#pragma unroll
-  for (int k = 1; k < SmoothSegs::kMax; ++k)
-    if (k < G.n && (int)blockIdx.x >= G.blk[k]) sg = k;
-  const int a = G.first[sg] + ((int)blockIdx.x - G.blk[sg]) * (int)blockDim.x + (int)threadIdx.x;
-  const int col = G.col[sg];
-  int nb[2 * D];
-  R t[NP];
-  if (a < G.last[sg]) {
-    load_nbr<D, R>(P, a, nb);                        // set-up data: read before the wait
-    if (early) load_cell_l2<D, N1, R, R>(f, a, t);   // f written two or more launches back
-  }
-  pdl_wait();
-  pdl_trigger();
-  if (a >= G.last[sg]) return;
-  if (!early) load_cell<D, N1, R, R>(f, a, t);
-  R c[NP];
-#pragma unroll
-  for (int i = 0; i < NP; ++i) c[i] = 0;
-  add_couplings_f<D, N1, R>(P.k, col, false, nb,
-                            [&](int n, int ncol, R(&un)[NP]) {
-                              load_cell<D, N1, R, R>(u, n, un);
-                              if (reverse ? ncol < col : ncol > col) add_prolongation<D, N1, NC, R>(T, ec, n, un);
-                            },
-                            c);
-#pragma unroll
-  for (int i = 0; i < NP; ++i) t[i] -= P.hscale * c[i];
-  const bool isB = a - G.cs[sg] < G.nbnd[sg];
-  R y[NP];
-  block_solve<D, N1, R>(P, isB ? G.b0[sg] + (a - G.cs[sg]) : -1, t, y);
-  if (P.omega != R(1)) {
-    R uo[NP];
-    load_cell<D, N1, R, R>(u, a, uo);
-    add_prolongation<D, N1, NC, R>(T, ec, a, uo);
-#pragma unroll
-    for (int i = 0; i < NP; ++i) y[i] = (R(1) - P.omega) * uo[i] + P.omega * y[i];
-  }
-  store_cell<D, N1, R>(u, a, y);
-}
-
 // Residual and p-restriction fused, one thread per cell (Eqs. 11, 18).
 // SM0: also the first colour group (colour 0) of the coarse level's first pre-smoothing sweep from
 // zero, zc_K = omega A_KK^-1 rc_K for coarse cells K of colour 0 (their neighbours, of later
@@ -843,37 +746,6 @@ cudaError_t launch_apply_cell(int dim, int p, const LevelParams<R>& P, const TI*
   count_launches();
   return cudaGetLastError();
 }
-
-template <typename R>
-cudaError_t launch_smooth_cell_pend(int dim, int p, int pc, const LevelParams<R>& P, const TransferParams<R>& T,
-                                   const R* ec, int reverse, const R* f, R* u, cudaStream_t s, int early) {
-  int launched = 0;
-  const int ng = n_colour_groups(P, dim);
-  for (int q = 0; q < ng; ++q) {
-    const int g = reverse ? ng - 1 - q : q;
-    const unsigned bs = cell_block(group_cells(P, dim, g));
-    const SmoothSegs G = smooth_segs(P, dim, g, (int)bs);
-    if (G.n == 0 || G.blk[G.n] == 0) continue;
-    const int fe = launched > 0 || early;
-#define SBM_SCP(D, N1, NC) \
-  SBM_PDL((k_smooth_cell_pend<D, N1, NC, R>), G.blk[G.n], bs, 0, s, P, G, T, ec, reverse, f, u, fe);
-    if (dim == 2 && p == 1 && pc == 1) { SBM_SCP(2, 2, 2) }
-    else if (dim == 2 && p == 2 && pc == 1) { SBM_SCP(2, 3, 2) }
-    else if (dim == 2 && p == 3 && pc == 2) { SBM_SCP(2, 4, 3) }
-    else if (dim == 3 && p == 1 && pc == 1) { SBM_SCP(3, 2, 2) }
-    else return cudaErrorInvalidValue;
-#undef SBM_SCP
-    count_launches();
-    ++launched;
-  }
-  return cudaGetLastError();
-}
-template cudaError_t launch_smooth_cell_pend<double>(int, int, int, const LevelParams<double>&,
-                                                     const TransferParams<double>&, const double*, int, const double*,
-                                                     double*, cudaStream_t, int);
-template cudaError_t launch_smooth_cell_pend<float>(int, int, int, const LevelParams<float>&,
-                                                    const TransferParams<float>&, const float*, int, const float*,
-                                                    float*, cudaStream_t, int);
 
 template <typename R>
 cudaError_t launch_smooth_cell(int dim, int p, const LevelParams<R>& P, int reverse, int zero_start, const R* f,

@@ -703,16 +703,6 @@ template cudaError_t launch_smoother_update<float>(size_t, float, float, const f
                                                    cudaStream_t);
 
 template <typename R>
-bool smooth_takes_cell_path(int dim, int p, const LevelParams<R>& P) {
-  if constexpr (std::is_same<R, float>::value) {
-    if (staged_kernels(dim, p) && P.staged_min > 0 && P.n_act >= (1 << dim) * P.staged_min) return false;
-  }
-  return cell_smoother(dim, p) && P.cell_min > 0 && P.n_act >= (1 << dim) * P.cell_min;
-}
-template bool smooth_takes_cell_path<double>(int, int, const LevelParams<double>&);
-template bool smooth_takes_cell_path<float>(int, int, const LevelParams<float>&);
-
-template <typename R>
 bool restrict_fuses_first_group(int dim, int pf, const LevelParams<R>& P, const TransferParams<R>& T, int pc,
                                 const LevelParams<R>& Pc) {
   const bool fine_cell = T.hmode ? (P.cell_min > 0 && T.n_act_f >= P.cell_min)

@@ -200,12 +200,6 @@ cudaError_t launch_apply_cell(int dim, int p, const LevelParams<R>& P, const TI*
 template <typename R>
 cudaError_t launch_smooth_cell(int dim, int p, const LevelParams<R>& P, int reverse, int zero_start, const R* f,
                                R* u, cudaStream_t s, int early, int first_group = 0);
-// One colour-group sweep (forward or reverse) with the prolongation u += P ec (Eq. 17, transfer T
-// from the level of degree pc) folded in: the separate prolongation launch is not needed.  The
-// 2^d-colour ordering and the thread-per-cell path only ((p+1)^d <= 16).
-template <typename R>
-cudaError_t launch_smooth_cell_pend(int dim, int p, int pc, const LevelParams<R>& P, const TransferParams<R>& T,
-                                   const R* ec, int reverse, const R* f, R* u, cudaStream_t s, int early);
 // Pc, zc non-null: the launch also performs the first colour group (colour 0) of the coarse level's
 // first pre-smoothing sweep from zero, zc_K = omega A_KK^-1 rc_K (Pc: the coarse level's parameters).
 template <typename R>
@@ -279,9 +273,6 @@ template <typename R>
 cudaError_t launch_resid_restrict_h(int dim, const LevelParams<R>& P, const TransferParams<R>& T, const R* u,
                                    const R* f, R* rc, cudaStream_t s, int early = 0, const LevelParams<R>* Pc = nullptr,
                                    R* zc = nullptr);
-// Whether launch_smooth on this level takes the thread-per-cell path (cell_ops.cu).
-template <typename R>
-bool smooth_takes_cell_path(int dim, int p, const LevelParams<R>& P);
 // Whether launch_resid_restrict_{p,h} can fuse the coarse level's first colour group (it takes the
 // thread-per-cell path there and the coarse level's smoother would take it too).
 template <typename R>
@@ -371,6 +362,13 @@ cudaError_t launch_mlp_features(int n_bnd, int npatch, int np, int nstat, int Fp
 cudaError_t launch_gemm_bf16(int M, int N, int K, int ta, int tb, const __nv_bfloat16* A, int lda,
                              const __nv_bfloat16* B, int ldb, const float* bias, int relu, float* Cf,
                              __nv_bfloat16* Cb, int ldc, cudaStream_t s);
+// The same GEMM on the tcgen05 tensor cores (tc_gemm.cu): 128 x 128 tiles, FP32 accumulators in
+// tensor memory.  A commit that does not arrive in bounded time sets a flag that tc_fault_take()
+// returns (1) and clears; -1 if it cannot be read.
+cudaError_t launch_gemm_tc(int M, int N, int K, int ta, int tb, const __nv_bfloat16* A, int lda,
+                           const __nv_bfloat16* B, int ldb, const float* bias, int relu, float* Cf,
+                           __nv_bfloat16* Cb, int ldc, cudaStream_t s);
+int tc_fault_take();
 cudaError_t launch_mse_grad(int rows, int O, const float* Y, const float* T, float* dYf, __nv_bfloat16* dYb,
                             float inv_count, float* loss_partial, int nblk, cudaStream_t s);
 cudaError_t launch_relu_mask(int n, float* dH, const __nv_bfloat16* H, __nv_bfloat16* dZb, cudaStream_t s);

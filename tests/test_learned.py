@@ -219,3 +219,24 @@ def test_checkpoint_roundtrip_and_corruption():
         gm.save(path)
         with pytest.raises(S.SbmError):
             wrong.load(path)
+
+
+@pytest.mark.parametrize("dim,p,hidden,rows", [(2, 2, 128, 1000), (2, 1, 32, 77), (3, 1, 128, 300), (2, 3, 64, 4096)])
+def test_tensor_core_gemm_matches_mma_sync(dim, p, hidden, rows):
+    """The tcgen05 tensor-core GEMMs (default) and the warp-level mma.sync GEMMs compute the same
+    BF16 products with FP32 sums: forward outputs and gradients agree within the FP32 summation
+    differences (1e-4 relative), on ragged shapes (rows, F, O not multiples of the tiles)."""
+    import paper_2506_12899_gb300 as S
+    gm = S.Mlp(dim, p, hidden, seed=11)
+    rng = np.random.default_rng(rows)
+    X = torch.tensor(rng.uniform(-1, 1, size=(rows, gm.F)), dtype=torch.float32, device="cuda")
+    T = torch.tensor(rng.normal(size=(rows, gm.O)), dtype=torch.float32, device="cuda")
+    gm.gemm_backend(0)
+    y_tc = gm.forward(X).cpu().numpy()
+    l_tc, g_tc = gm.gradients(X, T)
+    gm.gemm_backend(1)
+    y_ws = gm.forward(X).cpu().numpy()
+    l_ws, g_ws = gm.gradients(X, T)
+    assert np.linalg.norm(y_tc - y_ws) <= 1e-4 * np.linalg.norm(y_ws)
+    assert abs(l_tc - l_ws) <= 1e-4 * l_ws
+    assert np.linalg.norm(g_tc - g_ws) <= 1e-3 * np.linalg.norm(g_ws)
