@@ -562,11 +562,24 @@ def run_profile(args) -> None:
     """Fixed launch sequences for ncu captures (numbers printed under ncu are not bench values).
     solve:   one warm-up and one FP32-V-cycle FGMRES solve of --workload; prints how many of the
              library's kernels the warm-up launched (the ncu skip count) and how many the solve did.
+    mlp:     the 3D p=3 MLP (F = 2023, H = 128, O = 64): one forward and one gradient pass on
+             --profile-n random rows.
     kernels: 2D p=2 star at --profile-n^2 cells (or the 3D sphere of degree --profile-p, or the
              3D p=3 ellipsoid, at --profile-n^3): one FP32 operator apply, one finest-level smoother
              sweep (d+1 colour-group launches) and one V-cycle."""
     import torch
     import paper_2506_12899_gb300 as S
+    if args.profile == "mlp":                    # the learned part's GEMMs: one forward and one gradient pass
+        mlp = S.Mlp(3, 3, 128, seed=0)
+        gen = torch.Generator(device="cuda").manual_seed(0)
+        rows = args.profile_n
+        X = (2 * torch.rand((rows, mlp.F), generator=gen, device="cuda") - 1).contiguous()
+        T = torch.randn((rows, mlp.O), generator=gen, device="cuda").contiguous()
+        mlp.forward(X)
+        loss, _ = mlp.gradients(X, T)
+        torch.cuda.synchronize()
+        print("ROWS", rows, "F", mlp.F, "H", mlp.H, "O", mlp.O, "LOSS", loss, flush=True)
+        return
     if args.profile == "solve":
         g = S.Solver(WORKLOADS[args.workload](0), "f32", krylov_basis=args.krylov_basis)
         b = g.rhs()
@@ -800,7 +813,7 @@ def main():
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-correction variant")
     ap.add_argument("--no-extra", action="store_true",
                     help="skip the other workloads and the large-mesh rooflines in the bench line")
-    ap.add_argument("--profile", choices=["solve", "kernels"], help="fixed launches for an ncu capture")
+    ap.add_argument("--profile", choices=["solve", "kernels", "mlp"], help="fixed launches for an ncu capture")
     ap.add_argument("--profile-n", type=int, default=2048, help="cells per direction for --profile kernels")
     ap.add_argument("--profile-shape", default="star2d", choices=["star2d", "sphere3d", "ellipsoid3d"],
                     help="--profile kernels: 2D p=2 star, 3D sphere (degree --profile-p) or 3D p=3 ellipsoid")
