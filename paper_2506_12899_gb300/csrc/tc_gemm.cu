@@ -6,10 +6,11 @@
 // K-major layout without swizzle: 8-row x 16-byte core matrices, K-adjacent core matrices 128 bytes
 // apart, 8-row groups 1024 bytes apart; out-of-range rows, columns and K entries are zero.  One
 // thread then issues four tcgen05.mma (M = 128, N = 128, K = 16 each) that accumulate into a
-// 128 x 128 FP32 tile in tensor memory, and commits them to an mbarrier; the CTA waits on it (at
-// most kAsyncSpin polls, then it records the failure in a device flag and stops issuing) before the
-// shared tiles are overwritten.  Finally each warp reads its 32 rows of the accumulator with
-// tcgen05.ld and applies bias and ReLU.
+// 128 x 128 FP32 tile in tensor memory, and commits them to the stage's mbarrier.  Two stages
+// alternate, so the threads stage chunk i + 1 while the tensor core works on chunk i; a stage is
+// overwritten only after its commit arrived (at most kAsyncSpin polls per wait; a wait that runs out
+// records the failure in a device flag, lets the MMAs in flight land and skips the epilogue).
+// Finally each warp reads its 32 rows of the accumulator with tcgen05.ld and applies bias and ReLU.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -43,18 +44,67 @@ __device__ __forceinline__ uint32_t tile_off(int r, int k) {
   return (uint32_t)(((r >> 3) * 8 + (k >> 3)) * 128 + (r & 7) * 16 + (k & 7) * 2);
 }
 
+// Stages the K chunk k0 .. k0+63 of rows r0 .. r0+127 of the operand X (op(X)(r, k) = X[r*ld + k] when
+// KMAJ, else X[k*ld + r]) into the 128 x 64 K-major tile T.  16-byte pieces (8 consecutive k of one
+// row, one row of a core matrix) are loaded with 16-byte loads where the piece lies inside the
+// matrix and is 16-byte aligned (KMAJ); otherwise (MN-major storage: 8 consecutive r of one k, or the
+// ragged edges) element by element.  Entries outside R x K are zero.
+template <bool KMAJ>
+__device__ __forceinline__ void stage_tile(unsigned char* T, const __nv_bfloat16* __restrict__ X, int ld, int R,
+                                           int K, int r0, int k0, bool vec_ok) {
+  const __nv_bfloat16 zero = __float2bfloat16_rn(0.f);
+  if (KMAJ) {
+    for (int q = threadIdx.x; q < 128 * 8; q += kTcThreads) {   // piece q: row q / 8, k chunk q % 8
+      const int r = q >> 3, c = q & 7;
+      const int gr = r0 + r, gk = k0 + 8 * c;
+      uint4 v = make_uint4(0u, 0u, 0u, 0u);
+      if (gr < R) {
+        const __nv_bfloat16* src = X + (size_t)gr * ld + gk;
+        if (vec_ok && gk + 8 <= K) {
+          v = *reinterpret_cast<const uint4*>(src);
+        } else {
+          __nv_bfloat16 t[8];
+#pragma unroll
+          for (int j = 0; j < 8; ++j) t[j] = gk + j < K ? src[j] : zero;
+          v = *reinterpret_cast<const uint4*>(t);
+        }
+      }
+      *reinterpret_cast<uint4*>(T + tile_off(r, 8 * c)) = v;
+    }
+  } else {
+    for (int q = threadIdx.x; q < 64 * 16; q += kTcThreads) {   // piece q: k = q / 16, rows 8 (q % 16) ..
+      const int kk = q >> 4, rc = (q & 15) * 8;
+      const int gk = k0 + kk, gr = r0 + rc;
+      __nv_bfloat16 t[8];
+      if (gk < K) {
+        const __nv_bfloat16* src = X + (size_t)gk * ld + gr;
+        if (vec_ok && gr + 8 <= R) {
+          *reinterpret_cast<uint4*>(t) = *reinterpret_cast<const uint4*>(src);
+        } else {
+#pragma unroll
+          for (int j = 0; j < 8; ++j) t[j] = gr + j < R ? src[j] : zero;
+        }
+      } else {
+#pragma unroll
+        for (int j = 0; j < 8; ++j) t[j] = zero;
+      }
+#pragma unroll
+      for (int j = 0; j < 8; ++j) *reinterpret_cast<__nv_bfloat16*>(T + tile_off(rc + j, kk)) = t[j];
+    }
+  }
+}
+
 template <int TA, int TB>
 __global__ void __launch_bounds__(kTcThreads) k_gemm_tc(int M, int N, int K, const __nv_bfloat16* __restrict__ A,
                                                         int lda, const __nv_bfloat16* __restrict__ B, int ldb,
                                                         const float* __restrict__ bias, int relu,
                                                         float* __restrict__ Cf, __nv_bfloat16* __restrict__ Cb,
                                                         int ldc) {
-  __shared__ __align__(1024) unsigned char As[TBM * TBK * 2];
-  __shared__ __align__(1024) unsigned char Bs[TBN * TBK * 2];
-  __shared__ __align__(8) unsigned long long bar;
+  // two stages of (A tile, B tile), 32 KB each, in dynamic shared memory (1024-byte aligned)
+  extern __shared__ __align__(1024) unsigned char tc_smem[];
+  __shared__ __align__(8) unsigned long long bar[2];
   __shared__ uint32_t tmem_base;
   __shared__ int stop;
-  extern __shared__ unsigned char occupancy_pad[];  // residency cap only (launch_tc), never touched
   const int m0 = blockIdx.y * TBM, n0 = blockIdx.x * TBN;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (warp == 0) {                                   // 128 FP32 columns of tensor memory
@@ -63,7 +113,8 @@ __global__ void __launch_bounds__(kTcThreads) k_gemm_tc(int M, int N, int K, con
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
   if (threadIdx.x == 0) {
-    mbar_init(&bar, 1);
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
     mbar_fence_init();
     stop = 0;
   }
@@ -71,63 +122,67 @@ __global__ void __launch_bounds__(kTcThreads) k_gemm_tc(int M, int N, int K, con
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = tmem_base;
-  const __nv_bfloat16 zero = __float2bfloat16_rn(0.f);
   const uint32_t idesc = idesc_bf16(TBM, TBN);
-  unsigned phase = 0;
-  int issued = 0;
-  for (int k0 = 0; k0 < K; k0 += TBK) {
-    // stage A (rows m0.., K chunk) and B (columns n0.., K chunk), both K-major
-    for (int e = threadIdx.x; e < TBM * TBK; e += kTcThreads) {
-      const int r = TA ? e % TBM : e / TBK, kk = TA ? e / TBM : e % TBK;
-      const int m = m0 + r, k = k0 + kk;
-      const __nv_bfloat16 v = (m < M && k < K) ? (TA ? A[(size_t)k * lda + m] : A[(size_t)m * lda + k]) : zero;
-      *reinterpret_cast<__nv_bfloat16*>(As + tile_off(r, kk)) = v;
+  // 16-byte loads need 16-byte aligned rows
+  const bool va = (reinterpret_cast<uintptr_t>(A) & 15) == 0 && ((size_t)lda * 2) % 16 == 0;
+  const bool vb = (reinterpret_cast<uintptr_t>(B) & 15) == 0 && ((size_t)ldb * 2) % 16 == 0;
+  unsigned phase[2] = {0u, 0u};
+  int it = 0;
+  bool failed = false;
+  for (int k0 = 0; k0 < K; k0 += TBK, ++it) {
+    const int b = it & 1;
+    unsigned char* As = tc_smem + b * 2 * (TBM * TBK * 2);
+    unsigned char* Bs = As + TBM * TBK * 2;
+    if (it >= 2) {                                   // the MMAs of chunk it - 2 read this stage
+      const bool ok = stop ? true : mbar_wait(&bar[b], phase[b]);
+      phase[b] ^= 1u;
+      if (!__syncthreads_and(ok)) {
+        failed = true;
+        break;
+      }
     }
-    for (int e = threadIdx.x; e < TBN * TBK; e += kTcThreads) {
-      const int c = TB ? e / TBK : e % TBN, kk = TB ? e % TBK : e / TBN;
-      const int n = n0 + c, k = k0 + kk;
-      const __nv_bfloat16 v = (n < N && k < K) ? (TB ? B[(size_t)n * ldb + k] : B[(size_t)k * ldb + n]) : zero;
-      *reinterpret_cast<__nv_bfloat16*>(Bs + tile_off(c, kk)) = v;
-    }
+    stage_tile<TA == 0>(As, A, lda, M, K, m0, k0, va);
+    stage_tile<TB == 1>(Bs, B, ldb, N, K, n0, k0, vb);
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // generic writes -> tensor core
     __syncthreads();
-    if (threadIdx.x == 0 && !stop) {
+    if (threadIdx.x == 0) {
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 #pragma unroll
       for (int ks = 0; ks < TBK / 16; ++ks) {        // K = 16 per instruction: two core matrices
         const uint64_t ad = smem_desc(As + ks * 256, 128, 1024);
         const uint64_t bd = smem_desc(Bs + ks * 256, 128, 1024);
-        const uint32_t acc = issued > 0 ? 1u : 0u;
+        const uint32_t acc = (it > 0 || ks > 0) ? 1u : 0u;
         asm volatile(
             "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
             "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
             "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
             : "memory");
-        ++issued;
       }
       asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                       smem_addr(&bar))
+                       smem_addr(&bar[b]))
                    : "memory");
     }
-    // every thread waits until the MMAs have read the tiles (bounded)
-    const bool ok = stop ? true : mbar_wait(&bar, phase);
-    if (!__syncthreads_and(ok)) {
-      // the commit did not arrive in time: record it, give the MMAs in flight a second bounded wait
-      // before the tensor memory is released, and stop issuing
-      if (threadIdx.x == 0) {
-        atomicExch(&g_tc_fault, 1);
-        stop = 1;
-        mbar_wait(&bar, phase);
-      }
-      __syncthreads();
-      break;
-    }
-    phase ^= 1u;
   }
+  // wait for the commits still outstanding (the last one or two chunks), bounded
+  if (!failed) {
+    bool ok = true;
+    for (int j = (it >= 2 ? it - 2 : 0); j < it; ++j) {
+      const int b = j & 1;
+      ok = ok && mbar_wait(&bar[b], phase[b]);
+      phase[b] ^= 1u;
+    }
+    failed = !__syncthreads_and(ok);
+  }
+  if (failed && threadIdx.x == 0) {                  // record it and let the MMAs in flight land
+    atomicExch(&g_tc_fault, 1);
+    mbar_wait(&bar[0], phase[0]);
+    mbar_wait(&bar[1], phase[1]);
+  }
+  __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   // epilogue: warp w owns accumulator rows (TMEM lanes) 32 w .. 32 w + 31
   const int m = m0 + warp * 32 + lane;
-  if (!stop && K > 0) {
+  if (!failed && K > 0) {
 #pragma unroll 1
     for (int c0 = 0; c0 < TBN; c0 += 32) {
       uint32_t r[32];
@@ -171,17 +226,17 @@ __global__ void __launch_bounds__(kTcThreads) k_gemm_tc(int M, int N, int K, con
 
 }  // namespace
 
-// Unused dynamic shared memory that caps the residency at 3 CTAs per SM, so that the CTAs of an SM
-// never ask for more than 3 x 128 of its 512 tensor-memory columns (tcgen05.alloc would wait).
-constexpr size_t kTcPad = 44 * 1024;
+// Two stages of 32 KB: at most 3 CTAs per SM, so the CTAs of an SM never ask for more than 3 x 128
+// of its 512 tensor-memory columns (tcgen05.alloc would wait).
+constexpr size_t kTcSmem = 2 * 2 * (size_t)TBM * TBK * 2;
 
 template <int TA, int TB>
 cudaError_t launch_tc(dim3 grid, int M, int N, int K, const __nv_bfloat16* A, int lda, const __nv_bfloat16* B,
                       int ldb, const float* bias, int relu, float* Cf, __nv_bfloat16* Cb, int ldc, cudaStream_t s) {
   const cudaError_t e = cudaFuncSetAttribute(k_gemm_tc<TA, TB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)kTcPad);
+                                             (int)kTcSmem);
   if (e != cudaSuccess) return e;
-  k_gemm_tc<TA, TB><<<grid, kTcThreads, kTcPad, s>>>(M, N, K, A, lda, B, ldb, bias, relu, Cf, Cb, ldc);
+  k_gemm_tc<TA, TB><<<grid, kTcThreads, kTcSmem, s>>>(M, N, K, A, lda, B, ldb, bias, relu, Cf, Cb, ldc);
   return cudaSuccess;
 }
 
