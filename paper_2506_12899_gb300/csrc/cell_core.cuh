@@ -57,12 +57,62 @@ __device__ __forceinline__ void st32B(void* p, const unsigned (&r)[8]) {
                : "memory");
 }
 
-// The (p+1)^d values of cell a.  When a cell's values fill whole 32-byte words (3D p = 1 and 2D
-// p = 3 in FP32, 3D p = 1 in FP64) and the vector is 32-byte aligned, they are read with 32-byte
-// loads (one L1 request per warp and word instead of two); when they fill 16-byte words (2D p = 1
-// as well), with 16-byte loads.
+// The NP values of cell a when they do not fill whole 16-byte words (an odd (p+1)^d, i.e. 2D and 3D
+// p = 2): the thread reads the 16-byte-aligned window of the vector that holds them, with
+// 16-byte loads, and moves its values to the front by two word-shift selects.  A warp's scalar
+// loads of such cells each touch as many 128-byte lines as the cells span (27 for 3D p = 2 in
+// FP32), and the L1 request stream, not DRAM, then bounds the kernel; the window loads touch the
+// same lines with a fraction of the requests.  The window may cover words of the adjacent cells,
+// which are read and discarded.  Returns false, loading nothing, when the window would pass the
+// end of the vector (n_act cells) or the vector is not 16-byte aligned; the caller then loads the
+// values one by one.  CG: loads that go to L2 only (see load_cell_l2).
+template <int NP, typename T, bool CG>
+__device__ __forceinline__ bool load_window(const T* __restrict__ x, int a, int n_act, T (&v)[NP]) {
+  static_assert(sizeof(T) == 4 || sizeof(T) == 8, "4- or 8-byte elements");
+  constexpr int NW = NP * (int)sizeof(T) / 4;                 // 32-bit words of one cell
+  constexpr int MAXSH = sizeof(T) == 8 ? 2 : 3;               // largest word shift of a cell start
+  constexpr int NV = (NW + MAXSH + 3) / 4;                    // 16-byte loads of the window
+  if ((reinterpret_cast<uintptr_t>(x) & 15) != 0) return false;
+  const size_t g = (size_t)a * NW;
+  const size_t st = g & ~(size_t)3;
+  if (st + 4 * NV > (size_t)n_act * NW) return false;
+  const int sh = (int)(g - st);
+  const uint4* q = reinterpret_cast<const uint4*>(reinterpret_cast<const unsigned*>(x) + st);
+  unsigned w[4 * NV];
+#pragma unroll
+  for (int c = 0; c < NV; ++c) {
+    const uint4 u4 = CG ? __ldcg(q + c) : q[c];
+    w[4 * c] = u4.x;
+    w[4 * c + 1] = u4.y;
+    w[4 * c + 2] = u4.z;
+    w[4 * c + 3] = u4.w;
+  }
+  if constexpr (sizeof(T) == 4) {
+#pragma unroll
+    for (int i = 0; i + 1 < 4 * NV; ++i) w[i] = (sh & 1) ? w[i + 1] : w[i];
+  }
+  unsigned o[NW];
+#pragma unroll
+  for (int i = 0; i < NW; ++i) o[i] = (sh & 2) ? w[i + 2] : w[i];
+#pragma unroll
+  for (int i = 0; i < NP; ++i) {
+    if constexpr (sizeof(T) == 4) {
+      v[i] = __uint_as_float(o[i]);
+    } else {
+      const unsigned pair[2] = {o[2 * i], o[2 * i + 1]};
+      memcpy(&v[i], pair, sizeof(T));
+    }
+  }
+  return true;
+}
+
+// The (p+1)^d values of cell a (of a vector of n_act cells).  When a cell's values fill whole
+// 32-byte words (3D p = 1 and 2D p = 3 in FP32, 3D p = 1 in FP64) and the vector is 32-byte
+// aligned, they are read with 32-byte loads (one L1 request per warp and word instead of two);
+// when they fill 16-byte words (2D p = 1 as well), with 16-byte loads; otherwise through their
+// 16-byte-aligned window (load_window).
 template <int D, int N1, typename TI, typename R>
-__device__ __forceinline__ void load_cell(const TI* __restrict__ x, int a, R (&v)[CD<D, N1>::NP]) {
+__device__ __forceinline__ void load_cell(const TI* __restrict__ x, int a, int n_act, R (&v)[CD<D, N1>::NP]) {
   constexpr int NP = CD<D, N1>::NP;
   if constexpr ((NP * sizeof(TI)) % 32 == 0) {
     if ((reinterpret_cast<uintptr_t>(x) & 31) == 0) {
@@ -90,6 +140,13 @@ __device__ __forceinline__ void load_cell(const TI* __restrict__ x, int a, R (&v
       for (int i = 0; i < NP; ++i) v[i] = (R)t[i];
       return;
     }
+  } else if constexpr (sizeof(TI) == 4 || sizeof(TI) == 8) {
+    TI t[NP];
+    if (load_window<NP, TI, false>(x, a, n_act, t)) {
+#pragma unroll
+      for (int i = 0; i < NP; ++i) v[i] = (R)t[i];
+      return;
+    }
   }
 #pragma unroll
   for (int i = 0; i < NP; ++i) v[i] = (R)ldv(x + (size_t)a * NP + i);
@@ -99,7 +156,7 @@ __device__ __forceinline__ void load_cell(const TI* __restrict__ x, int a, R (&v
 // reads): every access goes to L2 only (ld.global.cg), the coherence point that the writer's
 // completion has reached, so a line another kernel left in this SM's L1 is never used.
 template <int D, int N1, typename TI, typename R>
-__device__ __forceinline__ void load_cell_l2(const TI* __restrict__ x, int a, R (&v)[CD<D, N1>::NP]) {
+__device__ __forceinline__ void load_cell_l2(const TI* __restrict__ x, int a, int n_act, R (&v)[CD<D, N1>::NP]) {
   constexpr int NP = CD<D, N1>::NP;
   const TI* p = x + (size_t)a * NP;
   if constexpr ((NP * sizeof(TI)) % 32 == 0) {
@@ -130,9 +187,51 @@ __device__ __forceinline__ void load_cell_l2(const TI* __restrict__ x, int a, R 
       for (int i = 0; i < NP; ++i) v[i] = (R)t[i];
       return;
     }
+  } else if constexpr (sizeof(TI) == 4 || sizeof(TI) == 8) {
+    TI t[NP];
+    if (load_window<NP, TI, true>(x, a, n_act, t)) {
+#pragma unroll
+      for (int i = 0; i < NP; ++i) v[i] = (R)t[i];
+      return;
+    }
   }
 #pragma unroll
   for (int i = 0; i < NP; ++i) v[i] = (R)__ldcg(p + i);
+}
+
+// Whether the values of a cell fill whole 16-byte words (then stored with vector stores by each
+// thread; otherwise warp_store_cells).
+template <int NP, typename R>
+constexpr bool cell_vec16() {
+  return (NP * sizeof(R)) % 16 == 0;
+}
+
+// Shared-memory staging buffer of warp_store_cells: 32 cells per warp of a kCellThreads block.
+template <int NP, typename R>
+struct WarpStage {
+  R v[kCellThreads / 32][cell_vec16<NP, R>() ? 1 : 32 * NP];
+};
+
+// Stores the values v of cells a0 + lane, for the lanes lane < m, of a warp whose lanes own
+// consecutive cells: through the warp's slice sw of shared memory, so that the global stores are
+// coalesced (lane k of every store instruction writes word k of a 128-byte run) instead of one
+// scattered 4- or 8-byte store per value and thread.  Every lane of the warp must call it.
+template <int NP, typename R>
+__device__ __forceinline__ void warp_store_cells(R* __restrict__ y, int a0, int m, const R (&v)[NP], R* sw) {
+  const int lane = threadIdx.x & 31;
+  __syncwarp();                                   // earlier readers of sw are done
+  if (lane < m) {
+#pragma unroll
+    for (int i = 0; i < NP; ++i) sw[lane * NP + i] = v[i];
+  }
+  __syncwarp();
+  R* dst = y + (size_t)a0 * NP;
+  const int cnt = m * NP;
+#pragma unroll
+  for (int k = 0; k < NP; ++k) {
+    const int e = lane + 32 * k;
+    if (e < cnt) dst[e] = sw[e];
+  }
 }
 
 // Stores the values of cell a, with 32- or 16-byte stores under the same conditions as load_cell.
@@ -235,7 +334,7 @@ __device__ __forceinline__ void add_couplings(const LevelParams<R>& P, const TI*
                                               bool zero_start, const int (&nb)[2 * D], R (&y)[CD<D, N1>::NP]) {
   constexpr int NP = CD<D, N1>::NP;
   add_couplings_f<D, N1, R>(P.k, col, zero_start, nb,
-                            [&](int n, int, R(&un)[NP]) { load_cell<D, N1, TI, R>(u, n, un); }, y);
+                            [&](int n, int, R(&un)[NP]) { load_cell<D, N1, TI, R>(u, n, P.n_act, un); }, y);
 }
 
 // y += A_KK v (volume + own halves of interior faces + surrogate faces), reference scaling.
@@ -356,7 +455,7 @@ __device__ __forceinline__ void cell_apply(const LevelParams<R>& P, const TI* __
                                            const int (&nb)[2 * D], R (&y)[CD<D, N1>::NP]) {
   constexpr int NP = CD<D, N1>::NP;
   R v[NP];
-  load_cell<D, N1, TI, R>(x, a, v);
+  load_cell<D, N1, TI, R>(x, a, P.n_act, v);
 #pragma unroll
   for (int i = 0; i < NP; ++i) y[i] = 0;
   add_self<D, N1, R>(P, nb, boundary_index(P, a, 1 << D), v, y);
@@ -434,12 +533,12 @@ __device__ __forceinline__ void block_solve_at(const LevelParams<R>& P, const R*
 
 // One cell of one colour of the block Gauss-Seidel sweep (Eq. 16): cell a of the colour
 // starting at cs whose first nbnd cells are boundary cells (dense inverse, boundary index
-// b0 + a - cs); the others use the fast diagonalisation.  t: f of the cell on entry (overwritten).
-// zero_start: a kZero* mode (ops.h).
+// b0 + a - cs); the others use the fast diagonalisation.  t: f of the cell on entry (overwritten);
+// un: the cell's new values, which the caller stores.  zero_start: a kZero* mode (ops.h).
 template <int D, int N1, typename R>
 __device__ __forceinline__ void smooth_one(const LevelParams<R>& P, int col, int zero_start, int cs, int nbnd,
                                            int b0, int a, const int (&nb)[2 * D], R (&t)[CD<D, N1>::NP],
-                                           R* __restrict__ u) {
+                                           const R* __restrict__ u, R (&un)[CD<D, N1>::NP]) {
   constexpr int NP = CD<D, N1>::NP;
   const bool isB = a - cs < nbnd;
   R c[NP];
@@ -451,15 +550,16 @@ __device__ __forceinline__ void smooth_one(const LevelParams<R>& P, int col, int
   add_couplings<D, N1, R, R>(P, u, col, zero_start == kZeroLater, nbz, c);
 #pragma unroll
   for (int i = 0; i < NP; ++i) t[i] -= P.hscale * c[i];
-  R y[NP];
-  block_solve<D, N1, R>(P, isB ? b0 + (a - cs) : -1, t, y);
-  if (P.omega == R(1)) {
-    store_cell<D, N1, R>(u, a, y);
-  } else {
+  block_solve<D, N1, R>(P, isB ? b0 + (a - cs) : -1, t, un);
+  if (P.omega != R(1)) {
+    R uo[NP];
+    if (zero_start) {
 #pragma unroll
-    for (int i = 0; i < NP; ++i) {
-      const R uo = zero_start ? R(0) : ldv(u + (size_t)a * NP + i);
-      u[(size_t)a * NP + i] = (R(1) - P.omega) * uo + P.omega * y[i];
+      for (int i = 0; i < NP; ++i) uo[i] = R(0);
+    } else {
+      load_cell<D, N1, R, R>(u, a, P.n_act, uo);
     }
+#pragma unroll
+    for (int i = 0; i < NP; ++i) un[i] = (R(1) - P.omega) * uo[i] + P.omega * un[i];
   }
 }

@@ -10,6 +10,7 @@
 #include <cooperative_groups.h>
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstdint>
 #include <type_traits>
 
@@ -20,21 +21,51 @@ namespace {
 
 #include "cell_core.cuh"
 
+// Launches over all cells of a level interleave the colours: block b takes chunk b / 2^D (of
+// blockDim.x consecutive cells) of colour b mod 2^D.  The face neighbours of a cell all have
+// other colours, so with the colours taken one after another every colour's values would be read
+// from DRAM once for its own pass and again in the passes of the colours next to it; interleaved,
+// the blocks in flight cover the same stretch of the mesh in every colour and the neighbours'
+// values are found in L2.  Sets the first cell of the calling thread's warp and the end of its
+// colour (the warp holds min(32, end - a0w) cells, none if that is <= 0).
+template <int D, typename R>
+__device__ __forceinline__ void interleaved_warp(const LevelParams<R>& P, int& a0w, int& end) {
+  constexpr int NCOL = 1 << D;
+  const int c = (int)blockIdx.x % NCOL;
+  a0w = P.colour_start[c] + ((int)blockIdx.x / NCOL) * (int)blockDim.x + ((int)threadIdx.x & ~31);
+  end = P.colour_start[c + 1];
+}
+
+// y = A x (MODE 0) or y = f - A x (MODE 1), one thread per cell, colours interleaved.
 template <int D, int N1, typename TI, typename R, int MODE>
 __global__ void __launch_bounds__(kCellThreads) k_apply_cell(const __grid_constant__ LevelParams<R> P,
                                                              const TI* __restrict__ x, const R* __restrict__ f,
                                                              R* __restrict__ y) {
   constexpr int NP = CD<D, N1>::NP;
-  const int a = blockIdx.x * blockDim.x + threadIdx.x;
+  int a0w, end;
+  interleaved_warp<D, R>(P, a0w, end);
+  const int a = a0w + ((int)threadIdx.x & 31);
+  const bool valid = a < end;
   int nb[2 * D];
-  if (a < P.n_act) load_nbr<D, R>(P, a, nb);       // set-up data: read before the wait
+  if (valid) load_nbr<D, R>(P, a, nb);             // set-up data: read before the wait
   pdl_wait();
   pdl_trigger();
-  if (a >= P.n_act) return;
   R r[NP];
-  cell_apply<D, N1, TI, R>(P, x, a, nb, r);
+  if (valid) {
+    cell_apply<D, N1, TI, R>(P, x, a, nb, r);
+    if (MODE == 1) {
+      R fv[NP];
+      load_cell<D, N1, R, R>(f, a, P.n_act, fv);
 #pragma unroll
-  for (int i = 0; i < NP; ++i) y[(size_t)a * NP + i] = MODE == 1 ? f[(size_t)a * NP + i] - r[i] : r[i];
+      for (int i = 0; i < NP; ++i) r[i] = fv[i] - r[i];
+    }
+  }
+  if constexpr (cell_vec16<NP, R>()) {
+    if (valid) store_cell<D, N1, R>(y, a, r);
+  } else {
+    __shared__ WarpStage<NP, R> stage;
+    if (a0w < end) warp_store_cells<NP, R>(y, a0w, min(32, end - a0w), r, stage.v[threadIdx.x >> 5]);
+  }
 }
 
 
@@ -49,18 +80,29 @@ __global__ void __launch_bounds__(kCellThreads) k_smooth_cell(const __grid_const
 #pragma unroll
   for (int k = 1; k < SmoothSegs::kMax; ++k)
     if (k < G.n && (int)blockIdx.x >= G.blk[k]) sg = k;
-  const int a = G.first[sg] + ((int)blockIdx.x - G.blk[sg]) * (int)blockDim.x + (int)threadIdx.x;
+  const int a0w = G.first[sg] + ((int)blockIdx.x - G.blk[sg]) * (int)blockDim.x + ((int)threadIdx.x & ~31);
+  const int end = G.last[sg];
+  const int a = a0w + ((int)threadIdx.x & 31);
+  const bool valid = a < end;
   int nb[2 * D];
   R t[NP];
-  if (a < G.last[sg]) {
+  if (valid) {
     load_nbr<D, R>(P, a, nb);                        // set-up data: read before the wait
-    if (early) load_cell_l2<D, N1, R, R>(f, a, t);   // f written two or more launches back
+    if (early) load_cell_l2<D, N1, R, R>(f, a, P.n_act, t);   // f written two or more launches back
   }
   pdl_wait();
   pdl_trigger();
-  if (a >= G.last[sg]) return;
-  if (!early) load_cell<D, N1, R, R>(f, a, t);
-  smooth_one<D, N1, R>(P, G.col[sg], zero_start, G.cs[sg], G.nbnd[sg], G.b0[sg], a, nb, t, u);
+  R y[NP];
+  if (valid) {
+    if (!early) load_cell<D, N1, R, R>(f, a, P.n_act, t);
+    smooth_one<D, N1, R>(P, G.col[sg], zero_start, G.cs[sg], G.nbnd[sg], G.b0[sg], a, nb, t, u, y);
+  }
+  if constexpr (cell_vec16<NP, R>()) {
+    if (valid) store_cell<D, N1, R>(u, a, y);
+  } else {
+    __shared__ WarpStage<NP, R> stage;
+    if (a0w < end) warp_store_cells<NP, R>(u, a0w, min(32, end - a0w), y, stage.v[threadIdx.x >> 5]);
+  }
 }
 
 // Residual and p-restriction fused, one thread per cell (Eqs. 11, 18).
@@ -77,17 +119,19 @@ __global__ void __launch_bounds__(kCellThreads) k_resid_restrict_p_cell(const __
                                                                         R* __restrict__ zc) {
   constexpr int NP = CD<D, N1>::NP;
   constexpr int NPC = D == 2 ? NC * NC : NC * NC * NC;
-  const int a = blockIdx.x * blockDim.x + threadIdx.x;
+  int a0w, end;
+  interleaved_warp<D, R>(P, a0w, end);               // colours interleaved
+  const int a = a0w + ((int)threadIdx.x & 31);
   int nb[2 * D];
   R fa[NP];
-  if (a < P.n_act) {
+  if (a < end) {
     load_nbr<D, R>(P, a, nb);                        // set-up data: read before the wait
-    if (early) load_cell_l2<D, N1, R, R>(f, a, fa);  // f written two or more launches back
+    if (early) load_cell_l2<D, N1, R, R>(f, a, P.n_act, fa);  // f written two or more launches back
   }
   pdl_wait();
   pdl_trigger();
-  if (a >= P.n_act) return;
-  if (!early) load_cell<D, N1, R, R>(f, a, fa);
+  if (a >= end) return;
+  if (!early) load_cell<D, N1, R, R>(f, a, P.n_act, fa);
   R r[NP];
   cell_apply<D, N1, R, R>(P, u, a, nb, r);
 #pragma unroll
@@ -151,13 +195,13 @@ __global__ void __launch_bounds__(kCellThreads) k_resid_restrict_h_cell(const __
   R fa[NP];
   if (a >= 0) {
     load_nbr<D, R>(P, a, nb);
-    if (early) load_cell_l2<D, 2, R, R>(f, a, fa);   // f written two or more launches back
+    if (early) load_cell_l2<D, 2, R, R>(f, a, P.n_act, fa);   // f written two or more launches back
   }
   pdl_wait();
   pdl_trigger();
   if (a >= 0) {
     R r[NP];
-    if (!early) load_cell<D, 2, R, R>(f, a, fa);
+    if (!early) load_cell<D, 2, R, R>(f, a, P.n_act, fa);
     cell_apply<D, 2, R, R>(P, u, a, nb, r);
 #pragma unroll
     for (int i = 0; i < NP; ++i) r[i] = fa[i] - r[i];
@@ -710,6 +754,16 @@ __global__ void __launch_bounds__(tail_cta_threads<D, R>(), 1) k_vcycle_tail_cta
 
 inline unsigned cdiv(size_t a, size_t b) { return (unsigned)((a + b - 1) / b); }
 
+// Grid of an interleaved launch (interleaved_warp) over all cells of a level: 2^dim blocks per
+// chunk, as many chunks as the largest colour needs.
+template <typename R>
+unsigned interleaved_grid(const LevelParams<R>& P, int dim, unsigned bs) {
+  const int ncol = 1 << dim;
+  int longest = 0;
+  for (int c = 0; c < ncol; ++c) longest = std::max(longest, P.colour_start[c + 1] - P.colour_start[c]);
+  return (unsigned)ncol * cdiv((size_t)longest, bs);
+}
+
 }  // namespace
 
 bool cell_kernels(int dim, int p) { return dim == 2 || (dim == 3 && p <= 2); }
@@ -736,9 +790,9 @@ cudaError_t launch_apply_cell(int dim, int p, const LevelParams<R>& P, const TI*
   if (P.n_act == 0) return cudaSuccess;
 #define SBM_AC(D, N1)                                                                           \
   {                                                                                             \
-    const unsigned bs = cell_block(P.n_act);                                                   \
-    if (mode == 0) SBM_PDL((k_apply_cell<D, N1, TI, R, 0>), cdiv(P.n_act, bs), bs, 0, s, P, x, f, y); \
-    else SBM_PDL((k_apply_cell<D, N1, TI, R, 1>), cdiv(P.n_act, bs), bs, 0, s, P, x, f, y);          \
+    const unsigned bs = cell_block(P.n_act), g = interleaved_grid(P, dim, bs);                 \
+    if (mode == 0) SBM_PDL((k_apply_cell<D, N1, TI, R, 0>), g, bs, 0, s, P, x, f, y);          \
+    else SBM_PDL((k_apply_cell<D, N1, TI, R, 1>), g, bs, 0, s, P, x, f, y);                    \
   }
   if constexpr (std::is_same<TI, float>::value && std::is_same<R, float>::value) SBM_CELL_DISPATCH3(dim, p, SBM_AC);
   else SBM_CELL_DISPATCH(dim, p, SBM_AC);
@@ -774,7 +828,7 @@ cudaError_t launch_resid_restrict_p_cell(int dim, int pf, const LevelParams<R>& 
                                         const R* u, const R* f, R* rc, cudaStream_t s, int early,
                                         const LevelParams<R>* Pc, R* zc) {
   if (P.n_act == 0) return cudaSuccess;
-  const unsigned bs = cell_block(P.n_act), g = cdiv(P.n_act, bs);
+  const unsigned bs = cell_block(P.n_act), g = interleaved_grid(P, dim, bs);
   const bool sm0 = Pc != nullptr && zc != nullptr;
   const LevelParams<R>& Q = sm0 ? *Pc : P;           // unused without the fused first group
 #define SBM_RRPC(D, N1, NC)                                                                                \
