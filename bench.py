@@ -565,8 +565,9 @@ def run_profile(args) -> None:
     mlp:     the 3D p=3 MLP (F = 2023, H = 128, O = 64): one forward and one gradient pass on
              --profile-n random rows.
     kernels: 2D p=2 star at --profile-n^2 cells (or the 3D sphere of degree --profile-p, or the
-             3D p=3 ellipsoid, at --profile-n^3): one FP32 operator apply, one finest-level smoother
-             sweep (d+1 colour-group launches) and one V-cycle."""
+             3D p=3 ellipsoid, at --profile-n^3): one FP32 operator apply and one smoother sweep
+             (d+1 colour-group launches) on the level --profile-level below the finest, and one
+             V-cycle when that is the finest."""
     import torch
     import paper_2506_12899_gb300 as S
     if args.profile == "mlp":                    # the learned part's GEMMs: one forward and one gradient pass
@@ -599,16 +600,18 @@ def run_profile(args) -> None:
                 "ellipsoid3d": lambda: W.ellipsoid3d_p3(args.profile_n, 0)}[args.profile_shape]()
         g = S.Solver(prob, "f32", tail_max_cells=args.tail_max_cells, tail_cluster_ctas=args.tail_cluster,
                      staged_min_cells=args.staged_min)
-        N = g.n_dof()
+        lev = g.num_levels - 1 - args.profile_level
+        N = g.info(lev)["n_dof"]
         gen = torch.Generator(device="cuda").manual_seed(0)
         f = torch.rand(N, device="cuda", generator=gen)
         u = torch.rand(N, device="cuda", generator=gen)
         y = torch.empty_like(f)
-        g.apply(f, y)
-        g.smooth(f, u)
-        g.vcycle(f, y)
+        g.apply(f, y, level=lev)
+        g.smooth(f, u, level=lev)
+        if lev == g.num_levels - 1:
+            g.vcycle(f, y)
         torch.cuda.synchronize()
-        print("N", N, "LEVELS", g.num_levels, flush=True)
+        print("N", N, "LEVELS", g.num_levels, "LEVEL", lev, flush=True)
 
 
 def run_learned_heldout(args) -> dict:
@@ -820,6 +823,8 @@ def main():
     ap.add_argument("--staged-min", type=int, default=0,
                     help="--profile kernels: staged thread-per-cell kernels from this many cells (<0 never)")
     ap.add_argument("--profile-p", type=int, default=2)
+    ap.add_argument("--profile-level", type=int, default=0,
+                    help="--profile kernels: level below the finest (0: finest, with one V-cycle)")
     ap.add_argument("--tail-max-cells", type=int, default=0, help="--profile kernels: cluster-tail cut-off")
     ap.add_argument("--tail-cluster", type=int, default=0, help="--profile kernels: cluster-tail CTAs")
     ap.add_argument("--krylov-basis", type=int, default=0, choices=[0, 1],

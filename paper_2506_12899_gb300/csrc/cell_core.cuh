@@ -531,16 +531,14 @@ __device__ __forceinline__ void block_solve_at(const LevelParams<R>& P, const R*
   for (int i = 0; i < NP; ++i) y[i] = t[i];
 }
 
-// One cell of one colour of the block Gauss-Seidel sweep (Eq. 16): cell a of the colour
-// starting at cs whose first nbnd cells are boundary cells (dense inverse, boundary index
-// b0 + a - cs); the others use the fast diagonalisation.  t: f of the cell on entry (overwritten);
-// un: the cell's new values, which the caller stores.  zero_start: a kZero* mode (ops.h).
+// One cell of one colour of the block Gauss-Seidel sweep (Eq. 16), in three steps: smooth_rhs
+// forms t_K = f_K - sum over interior faces of A_KN u_N (t: f_K on entry; the SBM terms lie in
+// A_KK), the caller solves A_KK y = t (dense inverse for boundary cells, fast diagonalisation
+// otherwise), and smooth_relax applies the relaxation factor.  zero_start: a kZero* mode (ops.h).
 template <int D, int N1, typename R>
-__device__ __forceinline__ void smooth_one(const LevelParams<R>& P, int col, int zero_start, int cs, int nbnd,
-                                           int b0, int a, const int (&nb)[2 * D], R (&t)[CD<D, N1>::NP],
-                                           const R* __restrict__ u, R (&un)[CD<D, N1>::NP]) {
+__device__ __forceinline__ void smooth_rhs(const LevelParams<R>& P, int col, int zero_start, const int (&nb)[2 * D],
+                                           R (&t)[CD<D, N1>::NP], const R* __restrict__ u) {
   constexpr int NP = CD<D, N1>::NP;
-  const bool isB = a - cs < nbnd;
   R c[NP];
 #pragma unroll
   for (int i = 0; i < NP; ++i) c[i] = 0;
@@ -550,16 +548,21 @@ __device__ __forceinline__ void smooth_one(const LevelParams<R>& P, int col, int
   add_couplings<D, N1, R, R>(P, u, col, zero_start == kZeroLater, nbz, c);
 #pragma unroll
   for (int i = 0; i < NP; ++i) t[i] -= P.hscale * c[i];
-  block_solve<D, N1, R>(P, isB ? b0 + (a - cs) : -1, t, un);
-  if (P.omega != R(1)) {
-    R uo[NP];
-    if (zero_start) {
+}
+
+// un = (1 - omega) u_K + omega un for cell a (u_K = 0 when zero_start).
+template <int D, int N1, typename R>
+__device__ __forceinline__ void smooth_relax(const LevelParams<R>& P, int zero_start, int a, const R* __restrict__ u,
+                                             R (&un)[CD<D, N1>::NP]) {
+  constexpr int NP = CD<D, N1>::NP;
+  if (P.omega == R(1)) return;
+  R uo[NP];
+  if (zero_start) {
 #pragma unroll
-      for (int i = 0; i < NP; ++i) uo[i] = R(0);
-    } else {
-      load_cell<D, N1, R, R>(u, a, P.n_act, uo);
-    }
-#pragma unroll
-    for (int i = 0; i < NP; ++i) un[i] = (R(1) - P.omega) * uo[i] + P.omega * un[i];
+    for (int i = 0; i < NP; ++i) uo[i] = R(0);
+  } else {
+    load_cell<D, N1, R, R>(u, a, P.n_act, uo);
   }
+#pragma unroll
+  for (int i = 0; i < NP; ++i) un[i] = (R(1) - P.omega) * uo[i] + P.omega * un[i];
 }

@@ -95,7 +95,10 @@ __global__ void __launch_bounds__(kCellThreads) k_smooth_cell(const __grid_const
   R y[NP];
   if (valid) {
     if (!early) load_cell<D, N1, R, R>(f, a, P.n_act, t);
-    smooth_one<D, N1, R>(P, G.col[sg], zero_start, G.cs[sg], G.nbnd[sg], G.b0[sg], a, nb, t, u, y);
+    smooth_rhs<D, N1, R>(P, G.col[sg], zero_start, nb, t, u);
+    const int off = a - G.cs[sg];
+    block_solve<D, N1, R>(P, off < G.nbnd[sg] ? G.b0[sg] + off : -1, t, y);
+    smooth_relax<D, N1, R>(P, zero_start, a, u, y);
   }
   if constexpr (cell_vec16<NP, R>()) {
     if (valid) store_cell<D, N1, R>(u, a, y);

@@ -190,8 +190,10 @@ inline int group_zero_mode(const LevelParams<R>& P, int zero_start, int q) {
 // Thread-per-cell kernels (cell_ops.cu): cell_kernels covers the FP32 operator and the fused
 // residual + restriction (2D, 3D p <= 2); cell_smoother the smoother and the double-float Arnoldi
 // operator ((p+1)^d <= 16: 2D, 3D p = 1).  For 3D p = 2 the thread-per-DoF family is faster for
-// those two (measured: smoother sweep 38.6 against 154 us at 64^3; the double-float operator
-// needs 255 registers per thread there), the thread-per-cell one for the others at large sizes.
+// those two (measured: smoother sweep 38.6 against 154 us at 64^3; with the 16-byte window loads
+// the thread-per-cell smoother still reached 0.09 of HBM at 128^3 against 0.14, and the 64^3 p=2
+// solve took 10.65 against 9.30 ms; the double-float operator needs 255 registers per thread
+// there), the thread-per-cell one for the others at large sizes.
 bool cell_kernels(int dim, int p);
 bool cell_smoother(int dim, int p);
 template <typename TI, typename R>
