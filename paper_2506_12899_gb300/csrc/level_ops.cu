@@ -615,6 +615,12 @@ cudaError_t launch_apply(int dim, int p, const LevelParams<R>& P, const TI* x, c
   }
   if ((f32 ? cell_kernels(dim, p) : cell_smoother(dim, p)) && P.cell_min > 0 && P.n_act >= P.cell_min)
     return launch_apply_cell<TI, R>(dim, p, P, x, f, y, mode, s);
+  if constexpr (f32) {
+    auto al16 = [](const void* q) { return (reinterpret_cast<uintptr_t>(q) & 15) == 0; };
+    if (line_kernels(dim, p) && P.cell_min > 0 && P.n_act >= P.cell_min && al16(x) && al16(y) &&
+        (mode == 0 || al16(f)))
+      return launch_apply_line(P, x, f, y, mode, s);
+  }
 #define SBM_APPLY(D, N1)                                                                 \
   {                                                                                      \
     using Dm = Dims<D, N1>;                                                              \

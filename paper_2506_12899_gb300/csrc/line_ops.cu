@@ -1,0 +1,249 @@
+// Thread-per-line operator for 3D p = 3 cells (Eqs. 7, 10, 11), FP32.
+//
+// A p = 3 cell holds 64 values (4 x 4 x 4, dof i + 4 j + 16 k).  The thread-per-DoF kernels of
+// level_ops.cu give every value its own thread and spend about 470 instructions per value on
+// index arithmetic and scalar shared-memory reads; a thread per cell would need some 200
+// registers.  Here a cell's 16 threads each own one line along x, (j, k) = (l mod 4, l / 4) for
+// thread l, and compute the operator at its four values i = 0..3:
+//   - the block copies its 8 cells and their 6 face neighbours into shared memory, one 16-byte
+//     word per thread and cell (a cell's 256 bytes are contiguous, so the copies are coalesced);
+//   - x terms (volume, both x faces): the thread's own line, 4 x 4 matrices;
+//   - y terms: plane k of the cell and of its y neighbours (the lines through (i, ., k));
+//   - z terms: the (i, j, .) lines, rows j of the cell and its z neighbours;
+// every read is a 16-byte shared-memory word, and the 1D matrices come from the kernel's
+// parameter block.  Surrogate faces (Eq. 7) follow in three barrier-separated phases per face
+// slot: the 16 threads of a cell take the 16 points of the face (trace and normal derivative,
+// then the extended value), then every thread adds the face terms at its own four values.
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <type_traits>
+
+#include "ops.h"
+
+namespace sbm {
+namespace {
+
+#include "cell_core.cuh"
+
+constexpr int kLineCells = 8;                    // cells per block
+constexpr int kLineThreads = 16 * kLineCells;    // 16 lines per cell
+constexpr int kLineStride = 68;                  // staged row of a cell: 64 values, padded (banks)
+
+__device__ __forceinline__ float4 lds4(const float* p) { return *reinterpret_cast<const float4*>(p); }
+
+// s[i] += sum_m M[r(i) * 4 + m] * v[m], v one 16-byte word (rows r(i) = i: full matrix).
+__device__ __forceinline__ void mat4(const float* M, const float4 v, float (&s)[4]) {
+#pragma unroll
+  for (int i = 0; i < 4; ++i) s[i] += M[4 * i] * v.x + M[4 * i + 1] * v.y + M[4 * i + 2] * v.z + M[4 * i + 3] * v.w;
+}
+
+// Surrogate-face terms (Eq. 7) of the block's boundary cells at the calling thread's four
+// values, reference scaling; every thread of the block calls it (barriers).
+__device__ __forceinline__ void line_sbm_terms(const LevelParams<float>& P, float (*sX)[7][kLineStride],
+                                               float (*sU)[16], float (*sG)[16], float (*sE)[16], int c, int l,
+                                               int j, int k, int bidx, const int (&nb)[6], float (&acc)[4]) {
+  const LevelConsts<float>& C = P.k;
+  const float* own = sX[c][0];
+#pragma unroll 1
+  for (int slot = 0; slot < 6; ++slot) {
+    const bool sf = bidx >= 0 && nb[slot] < 0;
+    if (!__syncthreads_or(sf)) continue;
+    const int dir = slot >> 1, side = slot & 1;
+    const float* es = side ? C.e1 : C.e0;
+    const float* ds = side ? C.d1 : C.d0;
+    const float* dh = sf ? P.dhat + ((size_t)bidx * 6 + slot) * 3 * 16 : nullptr;
+    const int t = l;                             // this thread's face point
+    if (sf) {                                    // trace and normal derivative at face point t
+      float su = 0.f, sd = 0.f;
+#pragma unroll
+      for (int kn = 0; kn < 4; ++kn) {
+        const float v = own[dof<3, 4>(dir, kn, t)];
+        su += es[kn] * v;
+        sd += ds[kn] * v;
+      }
+      sU[c][t] = su;
+      sG[c][t] = sd;
+    }
+    __syncthreads();
+    if (sf) {                                    // extended value at face point t
+      float E;
+      if (P.extension == 0) {
+        E = sU[c][t] + dh[dir * 16 + t] * sG[c][t];
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {            // tangential derivatives of the trace
+          const int m = tang_dim<3>(dir, q);
+          const int stride = q == 0 ? 1 : 4;
+          const int tm = (t / stride) % 4;
+          float g = 0.f;
+#pragma unroll
+          for (int r = 0; r < 4; ++r) g += C.Dm[tm * 4 + r] * sU[c][t + (r - tm) * stride];
+          E += dh[m * 16 + t] * g;
+        }
+      } else {                                   // cell polynomial at x~ + d
+        float lv[3][4];
+#pragma unroll
+        for (int m = 0; m < 3; ++m) {
+          float xi;
+          if (m == dir) {
+            xi = (float)side;
+          } else {
+            const int q = m < dir ? m : m - 1;
+            xi = C.x[(t / (q == 0 ? 1 : 4)) % 4];
+          }
+          const float yv = xi + dh[m * 16 + t];
+#pragma unroll
+          for (int kk = 0; kk < 4; ++kk) {
+            float val = C.inv_denom[kk];
+#pragma unroll
+            for (int jj = 0; jj < 4; ++jj)
+              if (jj != kk) val *= (yv - C.x[jj]);
+            lv[m][kk] = val;
+          }
+        }
+        E = 0.f;
+#pragma unroll
+        for (int q = 0; q < 64; ++q) E += lv[0][q % 4] * lv[1][(q / 4) % 4] * lv[2][q / 16] * own[q];
+      }
+      sE[c][t] = E;
+    }
+    __syncthreads();
+    if (sf) {                                    // terms at the thread's values (i, j, k), i = 0..3
+      const float sg = side ? 1.f : -1.f;
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        int tp, kn;                              // face point and normal position of value (i, j, k)
+        if (dir == 0) {
+          tp = j + 4 * k;
+          kn = i;
+        } else if (dir == 1) {
+          tp = i + 4 * k;
+          kn = j;
+        } else {
+          tp = i + 4 * j;
+          kn = k;
+        }
+        const float wt = C.w[tp % 4] * C.w[tp / 4];
+        const float E = sE[c][tp], G = sG[c][tp];
+        acc[i] += wt * (es[kn] * (-sg * G + P.sigG * E) - P.alpha * sg * ds[kn] * E);
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// y = A x (MODE 0) or y = f - A x (MODE 1) for a 3D p = 3 level, FP32.
+template <int MODE>
+__global__ void __launch_bounds__(kLineThreads) k_apply_line(const __grid_constant__ LevelParams<float> P,
+                                                             const float* __restrict__ x,
+                                                             const float* __restrict__ f, float* __restrict__ y) {
+  __shared__ __align__(16) float sX[kLineCells][7][kLineStride];
+  __shared__ float sU[kLineCells][16], sG[kLineCells][16], sE[kLineCells][16];
+  const int c = threadIdx.x >> 4, l = threadIdx.x & 15, j = l & 3, k = l >> 2;
+  const int a = blockIdx.x * kLineCells + c;
+  const bool valid = a < P.n_act;
+  int nb[6];
+#pragma unroll
+  for (int s = 0; s < 6; ++s) nb[s] = valid ? P.nbr[(size_t)s * P.n_act + a] : -1;   // set-up data
+  pdl_wait();
+  pdl_trigger();
+  if (valid) {                                   // word l of the cell and of each neighbour
+    reinterpret_cast<float4*>(sX[c][0])[l] = reinterpret_cast<const float4*>(x + (size_t)a * 64)[l];
+#pragma unroll
+    for (int s = 0; s < 6; ++s)
+      if (nb[s] >= 0)
+        reinterpret_cast<float4*>(sX[c][1 + s])[l] = reinterpret_cast<const float4*>(x + (size_t)nb[s] * 64)[l];
+  }
+  __syncthreads();
+  const LevelConsts<float>& C = P.k;
+  float acc[4] = {0.f, 0.f, 0.f, 0.f};
+  if (valid) {
+    const float* own = sX[c][0];
+    {                                            // x: the thread's own line (j, k)
+      float s[4] = {0.f, 0.f, 0.f, 0.f};
+      mat4(C.L[(nb[0] >= 0) + 2 * (nb[1] >= 0)], lds4(own + 4 * j + 16 * k), s);
+      if (nb[0] >= 0) mat4(C.Bpm, lds4(sX[c][1] + 4 * j + 16 * k), s);
+      if (nb[1] >= 0) mat4(C.Bmp, lds4(sX[c][2] + 4 * j + 16 * k), s);
+      const float wt = C.w[j] * C.w[k];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) acc[i] += wt * s[i];
+    }
+    {                                            // y: lines (i, ., k), row j of the 1D matrices
+      const float* Lm = C.L[(nb[2] >= 0) + 2 * (nb[3] >= 0)];
+      float s[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+      for (int m = 0; m < 4; ++m) {
+        const float4 v = lds4(own + 4 * m + 16 * k);
+        const float cm = Lm[4 * j + m];
+        s[0] += cm * v.x; s[1] += cm * v.y; s[2] += cm * v.z; s[3] += cm * v.w;
+      }
+#pragma unroll
+      for (int q = 0; q < 2; ++q) {
+        if (nb[2 + q] < 0) continue;
+        const float* B = q == 0 ? C.Bpm : C.Bmp;
+        const float* un = sX[c][3 + q];
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+          const float4 v = lds4(un + 4 * m + 16 * k);
+          const float cm = B[4 * j + m];
+          s[0] += cm * v.x; s[1] += cm * v.y; s[2] += cm * v.z; s[3] += cm * v.w;
+        }
+      }
+      const float wk = C.w[k];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) acc[i] += C.w[i] * wk * s[i];
+    }
+    {                                            // z: lines (i, j, .), row k of the 1D matrices
+      const float* Lm = C.L[(nb[4] >= 0) + 2 * (nb[5] >= 0)];
+      float s[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+      for (int m = 0; m < 4; ++m) {
+        const float4 v = lds4(own + 4 * j + 16 * m);
+        const float cm = Lm[4 * k + m];
+        s[0] += cm * v.x; s[1] += cm * v.y; s[2] += cm * v.z; s[3] += cm * v.w;
+      }
+#pragma unroll
+      for (int q = 0; q < 2; ++q) {
+        if (nb[4 + q] < 0) continue;
+        const float* B = q == 0 ? C.Bpm : C.Bmp;
+        const float* un = sX[c][5 + q];
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+          const float4 v = lds4(un + 4 * j + 16 * m);
+          const float cm = B[4 * k + m];
+          s[0] += cm * v.x; s[1] += cm * v.y; s[2] += cm * v.z; s[3] += cm * v.w;
+        }
+      }
+      const float wj = C.w[j];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) acc[i] += C.w[i] * wj * s[i];
+    }
+  }
+  const int bidx = valid ? boundary_index(P, a, 8) : -1;
+  if (__syncthreads_or(bidx >= 0)) line_sbm_terms(P, sX, sU, sG, sE, c, l, j, k, bidx, nb, acc);
+  if (valid) {
+    float4 out = make_float4(P.hscale * acc[0], P.hscale * acc[1], P.hscale * acc[2], P.hscale * acc[3]);
+    const size_t o = (size_t)a * 64 + 4 * j + 16 * k;
+    if (MODE == 1) {
+      const float4 fv = *reinterpret_cast<const float4*>(f + o);
+      out = make_float4(fv.x - out.x, fv.y - out.y, fv.z - out.z, fv.w - out.w);
+    }
+    *reinterpret_cast<float4*>(y + o) = out;
+  }
+}
+
+}  // namespace
+
+bool line_kernels(int dim, int p) { return dim == 3 && p == 3; }
+
+cudaError_t launch_apply_line(const LevelParams<float>& P, const float* x, const float* f, float* y, int mode,
+                              cudaStream_t s) {
+  if (P.n_act == 0) return cudaSuccess;
+  const unsigned grid = (unsigned)((P.n_act + kLineCells - 1) / kLineCells);
+  if (mode == 0) SBM_PDL((k_apply_line<0>), grid, kLineThreads, 0, s, P, x, f, y);
+  else SBM_PDL((k_apply_line<1>), grid, kLineThreads, 0, s, P, x, f, y);
+  count_launches();
+  return cudaGetLastError();
+}
+
+}  // namespace sbm

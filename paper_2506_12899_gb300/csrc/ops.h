@@ -195,6 +195,10 @@ inline int group_zero_mode(const LevelParams<R>& P, int zero_start, int q) {
 // solve took 10.65 against 9.30 ms; the double-float operator needs 255 registers per thread
 // there), the thread-per-cell one for the others at large sizes.
 bool cell_kernels(int dim, int p);
+// Thread-per-line FP32 operator (line_ops.cu): 3D p = 3; x, y (and f for mode 1) 16-byte aligned.
+bool line_kernels(int dim, int p);
+cudaError_t launch_apply_line(const LevelParams<float>& P, const float* x, const float* f, float* y, int mode,
+                              cudaStream_t s);
 bool cell_smoother(int dim, int p);
 template <typename TI, typename R>
 cudaError_t launch_apply_cell(int dim, int p, const LevelParams<R>& P, const TI* x, const R* f, R* y, int mode,

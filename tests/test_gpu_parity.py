@@ -102,11 +102,13 @@ def test_apply_unit_columns_tiny(name):
 
 
 @pytest.mark.parametrize("cell", [1, -1], ids=["thread_per_cell", "thread_per_dof"])
-@pytest.mark.parametrize("name", ["disk2d_p1_n32", "star2d_p2_n32", "star2d_p3_n16", "sphere3d_p1_n8", "sphere3d_p2_n8"])
+@pytest.mark.parametrize("name", ["disk2d_p1_n32", "star2d_p2_n32", "star2d_p3_n16", "sphere3d_p1_n8", "sphere3d_p2_n8",
+                                  "ellipsoid3d_p3_n12"])
 def test_kernel_variants(name, cell):
     """Both kernel families (one thread per cell, one thread per dof) for the operator, the
     smoother and the V-cycle, in FP64 and FP32, against the oracle (3D p = 2: the FP32 operator
-    and the residual + restriction of the V-cycle; its smoother is thread-per-DoF either way)."""
+    and the residual + restriction of the V-cycle; its smoother is thread-per-DoF either way;
+    3D p = 3: the FP32 operator with one thread per line of a cell, against thread per DoF)."""
     P = pair(name, cell=cell)
     L = len(P.H.levels) - 1
     lev = P.H.finest
