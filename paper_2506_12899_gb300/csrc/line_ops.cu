@@ -232,6 +232,161 @@ __global__ void __launch_bounds__(kLineThreads) k_apply_line(const __grid_consta
   }
 }
 
+
+// One colour group of the block Gauss-Seidel sweep (Eq. 16) on a 3D p = 3 level, FP32, one thread
+// per x-line, 8 cells of one segment per block:
+//   t_K = f_K - sum over interior faces of A_KN u_N (the SBM terms lie in A_KK),
+//   u_K <- (1 - omega) u_K + omega A_KK^-1 t_K.
+// The couplings take the same line, plane and row reads as the operator.  Boundary cells apply
+// their dense inverse (each thread four rows, 16-byte reads of the transposed inverse, t from
+// shared memory); interior cells the fast diagonalisation (S^T)^(x3), 1 / (h^(d-2) sum lambda),
+// S^(x3): the x contractions on the thread's own line in registers, the y and z contractions
+// after an exchange of the cell's values through shared memory.  A cell's 16 threads lie in one
+// warp, so the exchanges need only warp barriers.  zero_start: a kZero* mode (ops.h).
+__global__ void __launch_bounds__(kLineThreads) k_smooth_line(const __grid_constant__ LevelParams<float> P,
+                                                              const __grid_constant__ SmoothSegs G, int zero_start,
+                                                              const float* __restrict__ f, float* __restrict__ u,
+                                                              int early) {
+  __shared__ __align__(16) float sN[kLineCells][6][kLineStride];
+  __shared__ __align__(16) float sT[kLineCells][kLineStride], sW[kLineCells][kLineStride];
+  const int c = threadIdx.x >> 4, l = threadIdx.x & 15, j = l & 3, k = l >> 2;
+  int sg = 0;
+#pragma unroll
+  for (int q = 1; q < SmoothSegs::kMax; ++q)
+    if (q < G.n && (int)blockIdx.x >= G.blk[q]) sg = q;
+  const int col = G.col[sg], cs = G.cs[sg];
+  const bool isB = G.first[sg] < cs + G.nbnd[sg];    // segments are all-boundary or all-interior
+  const int a = G.first[sg] + ((int)blockIdx.x - G.blk[sg]) * kLineCells + c;
+  const bool valid = a < G.last[sg];
+  const size_t o = (size_t)a * 64 + 4 * j + 16 * k;  // the thread's line
+  int nb[6];
+#pragma unroll
+  for (int s = 0; s < 6; ++s) {                      // set-up data: read before the wait
+    nb[s] = valid ? P.nbr[(size_t)s * P.n_act + a] : -1;
+    if ((zero_start == kZeroLater && (col ^ (1 << (s >> 1))) > col) || zero_start == kZeroAll) nb[s] = -1;
+  }
+  float4 fv = make_float4(0.f, 0.f, 0.f, 0.f);
+  if (valid && early) fv = __ldcg(reinterpret_cast<const float4*>(f + o));   // f written two or more launches back
+  pdl_wait();
+  pdl_trigger();
+  float4 uold = make_float4(0.f, 0.f, 0.f, 0.f);
+  if (valid) {
+    if (!early) fv = *reinterpret_cast<const float4*>(f + o);
+#pragma unroll
+    for (int s = 0; s < 6; ++s)
+      if (nb[s] >= 0)
+        reinterpret_cast<float4*>(sN[c][s])[l] = reinterpret_cast<const float4*>(u + (size_t)nb[s] * 64)[l];
+    if (P.omega != 1.f && zero_start == kZeroNone) uold = *reinterpret_cast<const float4*>(u + o);
+  }
+  __syncthreads();
+  const LevelConsts<float>& C = P.k;
+  float t[4];
+  {                                                  // couplings (Eq. 10, interior faces)
+    float acc[4] = {0.f, 0.f, 0.f, 0.f};
+    if (valid) {
+      float s[4] = {0.f, 0.f, 0.f, 0.f};
+      if (nb[0] >= 0) mat4(C.Bpm, lds4(sN[c][0] + 4 * j + 16 * k), s);
+      if (nb[1] >= 0) mat4(C.Bmp, lds4(sN[c][1] + 4 * j + 16 * k), s);
+      const float wt = C.w[j] * C.w[k];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) acc[i] += wt * s[i];
+#pragma unroll
+      for (int dir = 1; dir < 3; ++dir) {
+        float r[4] = {0.f, 0.f, 0.f, 0.f};
+        const int row = dir == 1 ? j : k;            // the thread's position along dir
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+          if (nb[2 * dir + q] < 0) continue;
+          const float* B = q == 0 ? C.Bpm : C.Bmp;
+          const float* un = sN[c][2 * dir + q];
+#pragma unroll
+          for (int m = 0; m < 4; ++m) {
+            const float4 v = lds4(un + (dir == 1 ? 4 * m + 16 * k : 4 * j + 16 * m));
+            const float cm = B[4 * row + m];
+            r[0] += cm * v.x; r[1] += cm * v.y; r[2] += cm * v.z; r[3] += cm * v.w;
+          }
+        }
+        const float wo = C.w[dir == 1 ? k : j];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) acc[i] += C.w[i] * wo * r[i];
+      }
+    }
+    t[0] = fv.x - P.hscale * acc[0];
+    t[1] = fv.y - P.hscale * acc[1];
+    t[2] = fv.z - P.hscale * acc[2];
+    t[3] = fv.w - P.hscale * acc[3];
+  }
+  float y[4] = {0.f, 0.f, 0.f, 0.f};
+  float* lt = sT[c] + 4 * j + 16 * k;
+  float* lw = sW[c] + 4 * j + 16 * k;
+  if (isB) {                                         // dense inverse: y = Binv t
+    *reinterpret_cast<float4*>(lt) = make_float4(t[0], t[1], t[2], t[3]);
+    __syncwarp();
+    if (valid) {
+      const float* Bi = P.binvT + (size_t)(G.b0[sg] + (a - cs)) * 64 * 64 + 4 * j + 16 * k;
+#pragma unroll 8
+      for (int q = 0; q < 64; ++q) {
+        const float4 b = *reinterpret_cast<const float4*>(Bi + (size_t)q * 64);
+        const float tq = sT[c][q];
+        y[0] += b.x * tq; y[1] += b.y * tq; y[2] += b.z * tq; y[3] += b.w * tq;
+      }
+    }
+  } else {                                           // fast diagonalisation
+    float w[4];
+#pragma unroll
+    for (int m = 0; m < 4; ++m) w[m] = C.S[m] * t[0] + C.S[4 + m] * t[1] + C.S[8 + m] * t[2] + C.S[12 + m] * t[3];
+    *reinterpret_cast<float4*>(lt) = make_float4(w[0], w[1], w[2], w[3]);
+    __syncwarp();
+    float v[4] = {0.f, 0.f, 0.f, 0.f};               // y: (S^T) along the lines (i, ., k)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const float4 r = lds4(sT[c] + 4 * q + 16 * k);
+      const float cq = C.S[4 * q + j];
+      v[0] += cq * r.x; v[1] += cq * r.y; v[2] += cq * r.z; v[3] += cq * r.w;
+    }
+    *reinterpret_cast<float4*>(lw) = make_float4(v[0], v[1], v[2], v[3]);
+    __syncwarp();
+    float z[4] = {0.f, 0.f, 0.f, 0.f};               // z: (S^T) along the lines (i, j, .)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const float4 r = lds4(sW[c] + 4 * j + 16 * q);
+      const float cq = C.S[4 * q + k];
+      z[0] += cq * r.x; z[1] += cq * r.y; z[2] += cq * r.z; z[3] += cq * r.w;
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) z[i] *= C.inv_diag[i + 4 * j + 16 * k];
+#pragma unroll
+    for (int m = 0; m < 4; ++m) w[m] = C.S[4 * m] * z[0] + C.S[4 * m + 1] * z[1] + C.S[4 * m + 2] * z[2] + C.S[4 * m + 3] * z[3];
+    *reinterpret_cast<float4*>(lt) = make_float4(w[0], w[1], w[2], w[3]);
+    __syncwarp();
+#pragma unroll
+    for (int i = 0; i < 4; ++i) v[i] = 0.f;          // y: S along (i, ., k)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const float4 r = lds4(sT[c] + 4 * q + 16 * k);
+      const float cq = C.S[4 * j + q];
+      v[0] += cq * r.x; v[1] += cq * r.y; v[2] += cq * r.z; v[3] += cq * r.w;
+    }
+    *reinterpret_cast<float4*>(lw) = make_float4(v[0], v[1], v[2], v[3]);
+    __syncwarp();
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {                    // z: S along (i, j, .)
+      const float4 r = lds4(sW[c] + 4 * j + 16 * q);
+      const float cq = C.S[4 * k + q];
+      y[0] += cq * r.x; y[1] += cq * r.y; y[2] += cq * r.z; y[3] += cq * r.w;
+    }
+  }
+  if (valid) {
+    float4 out = make_float4(y[0], y[1], y[2], y[3]);
+    if (P.omega != 1.f) {
+      const float om = P.omega, rm = 1.f - P.omega;
+      out = make_float4(rm * uold.x + om * y[0], rm * uold.y + om * y[1], rm * uold.z + om * y[2],
+                        rm * uold.w + om * y[3]);
+    }
+    *reinterpret_cast<float4*>(u + o) = out;
+  }
+}
+
 }  // namespace
 
 bool line_kernels(int dim, int p) { return dim == 3 && p == 3; }
@@ -243,6 +398,23 @@ cudaError_t launch_apply_line(const LevelParams<float>& P, const float* x, const
   if (mode == 0) SBM_PDL((k_apply_line<0>), grid, kLineThreads, 0, s, P, x, f, y);
   else SBM_PDL((k_apply_line<1>), grid, kLineThreads, 0, s, P, x, f, y);
   count_launches();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_smooth_line(const LevelParams<float>& P, int reverse, int zero_start, const float* f, float* u,
+                               cudaStream_t s, int early, int first_group) {
+  if (reverse) zero_start = 0;
+  int launched = 0;
+  const int ng = n_colour_groups(P, 3);
+  for (int q = first_group; q < ng; ++q) {
+    const int g = reverse ? ng - 1 - q : q;
+    const SmoothSegs G = smooth_segs(P, 3, g, kLineCells);
+    if (G.n == 0 || G.blk[G.n] == 0) continue;
+    const int fe = launched > 0 || early;            // after the sweep's first launch f is two back
+    SBM_PDL(k_smooth_line, G.blk[G.n], kLineThreads, 0, s, P, G, group_zero_mode(P, zero_start, q), f, u, fe);
+    count_launches();
+    ++launched;
+  }
   return cudaGetLastError();
 }
 

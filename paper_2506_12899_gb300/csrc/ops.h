@@ -199,6 +199,8 @@ bool cell_kernels(int dim, int p);
 bool line_kernels(int dim, int p);
 cudaError_t launch_apply_line(const LevelParams<float>& P, const float* x, const float* f, float* y, int mode,
                               cudaStream_t s);
+cudaError_t launch_smooth_line(const LevelParams<float>& P, int reverse, int zero_start, const float* f, float* u,
+                               cudaStream_t s, int early, int first_group);
 bool cell_smoother(int dim, int p);
 template <typename TI, typename R>
 cudaError_t launch_apply_cell(int dim, int p, const LevelParams<R>& P, const TI* x, const R* f, R* y, int mode,
