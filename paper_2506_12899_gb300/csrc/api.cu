@@ -515,6 +515,7 @@ Context* build_context(const sbm_setup_desc& d, bool device) {
     } else {
       L.P64.cell_min = L.P32.cell_min = d.cell_kernel_min_cells < 0 ? 0 : d.cell_kernel_min_cells;
     }
+    L.Pdf.cell_min = L.P32.cell_min;               // the double-float operator follows the FP32 choice
     // staged thread-per-cell kernels (FP32): launches over at least staged_min cells
     L.P32.staged_min = d.staged_min_cells == 0 ? 0 : (d.staged_min_cells < 0 ? 0 : d.staged_min_cells);
   }

@@ -615,11 +615,11 @@ cudaError_t launch_apply(int dim, int p, const LevelParams<R>& P, const TI* x, c
   }
   if ((f32 ? cell_kernels(dim, p) : cell_smoother(dim, p)) && P.cell_min > 0 && P.n_act >= P.cell_min)
     return launch_apply_cell<TI, R>(dim, p, P, x, f, y, mode, s);
-  if constexpr (f32) {
+  if constexpr (std::is_same<TI, float>::value && (std::is_same<R, float>::value || std::is_same<R, dfl>::value)) {
     auto al16 = [](const void* q) { return (reinterpret_cast<uintptr_t>(q) & 15) == 0; };
     if (line_kernels(dim, p) && P.cell_min > 0 && P.n_act >= P.cell_min && al16(x) && al16(y) &&
         (mode == 0 || al16(f)))
-      return launch_apply_line(P, x, f, y, mode, s);
+      return launch_apply_line<R>(P, x, f, y, mode, s);
   }
 #define SBM_APPLY(D, N1)                                                                 \
   {                                                                                      \
@@ -747,6 +747,11 @@ cudaError_t launch_resid_restrict_p(int dim, int pf, const LevelParams<R>& P, co
   if (cell_kernels(dim, pf) && P.cell_min > 0 && P.n_act >= P.cell_min)
     return launch_resid_restrict_p_cell<R>(dim, pf, P, T, u, f, rc, s, early, Pc, zc);
   if (Pc || zc) return cudaErrorInvalidValue;       // the fused first group exists on the cell path only
+  if constexpr (std::is_same<R, float>::value) {
+    auto al16 = [](const void* q) { return (reinterpret_cast<uintptr_t>(q) & 15) == 0; };
+    if (line_kernels(dim, pf) && P.cell_min > 0 && P.n_act >= P.cell_min && al16(u) && al16(f))
+      return launch_resid_restrict_line(P, T, u, f, rc, s, early);
+  }
 #define SBM_RRP(D, N1, NC)                                                                         \
   {                                                                                                \
     using Dm = Dims<D, N1>;                                                                        \
