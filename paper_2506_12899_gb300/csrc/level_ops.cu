@@ -613,14 +613,14 @@ cudaError_t launch_apply(int dim, int p, const LevelParams<R>& P, const TI* x, c
     if (staged_kernels(dim, p) && P.staged_min > 0 && P.n_act >= P.staged_min)
       return launch_apply_staged(dim, p, P, x, f, y, mode, s);
   }
-  if ((f32 ? cell_kernels(dim, p) : cell_smoother(dim, p)) && P.cell_min > 0 && P.n_act >= P.cell_min)
-    return launch_apply_cell<TI, R>(dim, p, P, x, f, y, mode, s);
   if constexpr (std::is_same<TI, float>::value && (std::is_same<R, float>::value || std::is_same<R, dfl>::value)) {
     auto al16 = [](const void* q) { return (reinterpret_cast<uintptr_t>(q) & 15) == 0; };
-    if (line_kernels(dim, p) && P.cell_min > 0 && P.n_act >= P.cell_min && al16(x) && al16(y) &&
-        (mode == 0 || al16(f)))
-      return launch_apply_line<R>(P, x, f, y, mode, s);
+    const bool use = std::is_same<R, dfl>::value ? line_kernels_df(dim, p) : line_kernels(dim, p);
+    if (use && P.cell_min > 0 && P.n_act >= P.cell_min && al16(x) && al16(y) && (mode == 0 || al16(f)))
+      return launch_apply_line<R>(p, P, x, f, y, mode, s);
   }
+  if ((f32 ? cell_kernels(dim, p) : cell_smoother(dim, p)) && P.cell_min > 0 && P.n_act >= P.cell_min)
+    return launch_apply_cell<TI, R>(dim, p, P, x, f, y, mode, s);
 #define SBM_APPLY(D, N1)                                                                 \
   {                                                                                      \
     using Dm = Dims<D, N1>;                                                              \
@@ -648,7 +648,7 @@ cudaError_t launch_smooth(int dim, int p, const LevelParams<R>& P, int reverse, 
   if constexpr (std::is_same<R, float>::value) {
     auto al16 = [](const void* q) { return (reinterpret_cast<uintptr_t>(q) & 15) == 0; };
     if (line_kernels(dim, p) && P.cell_min > 0 && P.n_act >= (1 << dim) * P.cell_min && al16(f) && al16(u))
-      return launch_smooth_line(P, reverse, zero_start, f, u, s, early, first_group);
+      return launch_smooth_line(p, P, reverse, zero_start, f, u, s, early, first_group);
   }
   if (first_group != 0) return cudaErrorInvalidValue;
   if (reverse) zero_start = 0;
@@ -749,7 +749,7 @@ cudaError_t launch_resid_restrict_p(int dim, int pf, const LevelParams<R>& P, co
   if (Pc || zc) return cudaErrorInvalidValue;       // the fused first group exists on the cell path only
   if constexpr (std::is_same<R, float>::value) {
     auto al16 = [](const void* q) { return (reinterpret_cast<uintptr_t>(q) & 15) == 0; };
-    if (line_kernels(dim, pf) && P.cell_min > 0 && P.n_act >= P.cell_min && al16(u) && al16(f))
+    if (dim == 3 && pf == 3 && P.cell_min > 0 && P.n_act >= P.cell_min && al16(u) && al16(f))
       return launch_resid_restrict_line(P, T, u, f, rc, s, early);
   }
 #define SBM_RRP(D, N1, NC)                                                                         \

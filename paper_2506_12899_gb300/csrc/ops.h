@@ -195,16 +195,18 @@ inline int group_zero_mode(const LevelParams<R>& P, int zero_start, int q) {
 // solve took 10.65 against 9.30 ms; the double-float operator needs 255 registers per thread
 // there), the thread-per-cell one for the others at large sizes.
 bool cell_kernels(int dim, int p);
-// Thread-per-line kernels (line_ops.cu), 3D p = 3: the operator (x FP32, arithmetic and y FP32 or
-// double-float), the FP32 smoother and the FP32 fused residual + restriction to p = 2.  Vectors
-// 16-byte aligned.
-bool line_kernels(int dim, int p);
+// Thread-per-line kernels (line_ops.cu), 3D p = 2 and 3: the operator (x FP32, arithmetic and y
+// FP32 or double-float), the FP32 smoother, and (p = 3) the FP32 fused residual + restriction to
+// p = 2.  Vectors 16-byte aligned.
+bool line_kernels(int dim, int p);      // FP32 operator, smoother, residual + restriction
+bool line_kernels_df(int dim, int p);   // double-float operator
 template <typename R>
-cudaError_t launch_apply_line(const LevelParams<R>& P, const float* x, const R* f, R* y, int mode, cudaStream_t s);
+cudaError_t launch_apply_line(int p, const LevelParams<R>& P, const float* x, const R* f, R* y, int mode,
+                              cudaStream_t s);
 cudaError_t launch_resid_restrict_line(const LevelParams<float>& P, const TransferParams<float>& T, const float* u,
                                        const float* f, float* rc, cudaStream_t s, int early);
-cudaError_t launch_smooth_line(const LevelParams<float>& P, int reverse, int zero_start, const float* f, float* u,
-                               cudaStream_t s, int early, int first_group);
+cudaError_t launch_smooth_line(int p, const LevelParams<float>& P, int reverse, int zero_start, const float* f,
+                               float* u, cudaStream_t s, int early, int first_group);
 bool cell_smoother(int dim, int p);
 template <typename TI, typename R>
 cudaError_t launch_apply_cell(int dim, int p, const LevelParams<R>& P, const TI* x, const R* f, R* y, int mode,
