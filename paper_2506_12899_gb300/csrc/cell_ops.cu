@@ -1,12 +1,15 @@
-// Thread-per-cell CUDA kernels for small cells ((p+1)^d <= 16: 2D p = 1..3 and 3D p = 1).
+// Thread-per-cell CUDA kernels for small cells ((p+1)^d <= 16: 2D p = 1..3 and 3D p = 1; the FP32
+// operator and residual + restriction also for 3D p = 2).
 //
 // One thread owns one cell: its (p+1)^d values, the interior-face couplings to its 2d
 // neighbours, its surrogate-face terms and its block inverse live in registers.  Every loop
 // over nodes, lines and directions is unrolled, so each 1D-matrix coefficient is a uniform,
-// immediate-offset read of the kernel parameter block (constant cache broadcast) and no
-// shared memory or barrier is needed.  The per-DoF kernels of level_ops.cu issue about 175
-// instructions per DoF, mostly shared-memory traffic; here the arithmetic is the same
-// (Eqs. 7, 10, 11, 14, 16, 18) but the instruction stream is a fraction of that.
+// immediate-offset read of the kernel parameter block (constant cache broadcast).  The per-DoF
+// kernels of level_ops.cu issue about 175 instructions per DoF, mostly shared-memory traffic;
+// here the arithmetic is the same (Eqs. 7, 10, 11, 14, 16, 18) but the instruction stream is a
+// fraction of that.  Cells of an odd number of values are read through their 16-byte-aligned
+// window and stored through shared memory (cell_core.cuh); launches over a whole level take the
+// colours interleaved (interleaved_warp).
 #include <cooperative_groups.h>
 #include <cuda_runtime.h>
 
