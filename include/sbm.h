@@ -100,11 +100,14 @@ typedef struct {
                          /* so each may be scheduled while its predecessor finishes; < 0: plain   */
                          /* stream-ordered launches; 0: on with the FP32 V-cycle, off with FP64   */
   int krylov_basis;      /* FGMRES basis storage and Arnoldi arithmetic: 0 double-float pairs     */
-                         /* (hi, lo) of FP32, Gram-Schmidt and (FP32 V-cycle, (p+1)^d <= 16) the  */
-                         /* operator A z on the FP32 pipes (~48-bit significands); 1 FP64; 2      */
-                         /* double-float basis with the FP64 operator                             */
+                         /* (hi, lo) of FP32, Gram-Schmidt and (FP32 V-cycle) the operator A z on */
+                         /* the FP32 pipes (~48-bit significands); 1 FP64; 2 double-float basis   */
+                         /* with the FP64 operator                                                */
   int cell_kernel_min_cells; /* launches over at least this many cells use one thread per cell   */
-                         /* when (p+1)^d <= 16; 0: always in FP32, never in FP64; < 0: never       */
+                         /* when (p+1)^d <= 16 (and the FP32 operator at 3D p = 2), and one thread */
+                         /* per line of a cell at 3D p = 3 (FP32; the double-float Arnoldi          */
+                         /* operator at 3D p = 2 and 3); 0: always in FP32, never in FP64; < 0:     */
+                         /* never (one thread per DoF everywhere)                                   */
   int staged_min_cells;  /* FP32 operator and smoother launches over at least this many cells     */
                          /* (2D p <= 3, 3D p <= 2) use the staged thread-per-cell kernels, whose  */
                          /* CTA copies its cells and their face neighbours into shared memory     */

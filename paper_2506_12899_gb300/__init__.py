@@ -219,8 +219,8 @@ class Solver:
         0 on with the FP32 V-cycle and off with FP64 (measured best).  krylov_basis: 0 double-float
         FGMRES basis and Arnoldi operator (on the FP32 pipes), 1 FP64, 2 double-float basis with the
         FP64 operator.  cell_kernel_min_cells: launches over at least that many
-        cells use one thread per cell (0: library default, < 0: never, 1: always where
-        (p+1)^d <= 16).  staged_min_cells: FP32 operator and smoother launches over at least that
+        cells use one thread per cell, or at 3D p = 3 one thread per line of a cell (0: library
+        default, < 0: never, 1: always where those kernels exist).  staged_min_cells: FP32 operator and smoother launches over at least that
         many cells use the staged thread-per-cell kernels (0: library default, < 0: never).
         device_geometry: volume fractions and closest points on the device (0: default, on; < 0:
         on the host cores)."""

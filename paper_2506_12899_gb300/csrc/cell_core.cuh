@@ -63,7 +63,8 @@ __device__ __forceinline__ void st32B(void* p, const unsigned (&r)[8]) {
 // loads of such cells each touch as many 128-byte lines as the cells span (27 for 3D p = 2 in
 // FP32), and the L1 request stream, not DRAM, then bounds the kernel; the window loads touch the
 // same lines with a fraction of the requests.  The window may cover words of the adjacent cells,
-// which are read and discarded.  Returns false, loading nothing, when the window would pass the
+// which are read and discarded (in a smoother launch those words can belong to cells another
+// thread is updating; no value taken from them is used).  Returns false, loading nothing, when the window would pass the
 // end of the vector (n_act cells) or the vector is not 16-byte aligned; the caller then loads the
 // values one by one.  CG: loads that go to L2 only (see load_cell_l2).
 template <int NP, typename T, bool CG>
