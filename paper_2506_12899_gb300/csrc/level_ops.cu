@@ -647,7 +647,7 @@ cudaError_t launch_smooth(int dim, int p, const LevelParams<R>& P, int reverse, 
     return launch_smooth_cell<R>(dim, p, P, reverse, zero_start, f, u, s, early, first_group);
   if constexpr (std::is_same<R, float>::value) {
     auto al16 = [](const void* q) { return (reinterpret_cast<uintptr_t>(q) & 15) == 0; };
-    if (line_kernels(dim, p) && P.cell_min > 0 && P.n_act >= (1 << dim) * P.cell_min && al16(f) && al16(u))
+    if (line_smoother(dim, p) && P.cell_min > 0 && P.n_act >= (1 << dim) * P.cell_min && al16(f) && al16(u))
       return launch_smooth_line(p, P, reverse, zero_start, f, u, s, early, first_group);
   }
   if (first_group != 0) return cudaErrorInvalidValue;

@@ -29,15 +29,32 @@ namespace {
 
 #include "cell_core.cuh"
 
-constexpr int kLineCells = 8;                    // cells per block
-constexpr int kLineThreads = 16 * kLineCells;    // 16 threads per cell
+constexpr int kLineThreads = 128;                // 4 warps per block
 
+// A cell's lanes: LPC consecutive lanes of one warp (16 at p = 3, 9 at p = 2, so that a warp holds
+// CPW = 2 or 3 cells and a cell's exchanges need only warp barriers; at p = 2 lanes 27-31 idle).
 template <int N1>
 struct LD {
   static constexpr int NP = N1 * N1 * N1;        // values of a cell
   static constexpr int NL = N1 * N1;             // lines (and face points) of a cell
   static constexpr int ST = N1 == 4 ? 68 : 28;   // staged row of a cell (floats, 16-byte multiple; banks)
+  static constexpr int LPC = N1 == 4 ? 16 : 9;   // lanes per cell
+  static constexpr int CPW = 32 / LPC;           // cells per warp
+  static constexpr int CPB = 4 * CPW;            // cells per block
 };
+
+// The calling thread's cell slot c in the block and lane l within the cell; false for the idle
+// lanes past the warp's last cell (they take slot and lane of the warp's first line and must
+// not write).
+template <int N1>
+__device__ __forceinline__ bool line_lane(int& c, int& l) {
+  constexpr int LPC = LD<N1>::LPC, CPW = LD<N1>::CPW;
+  const int w = (int)threadIdx.x >> 5, L = (int)threadIdx.x & 31;
+  const bool ok = L < CPW * LPC;
+  c = w * CPW + (ok ? L / LPC : 0);
+  l = ok ? L % LPC : 0;
+  return ok;
+}
 
 // acc += a b and a b in the arithmetic R: FP32, or double-float (the Arnoldi operator's).
 __device__ __forceinline__ void madd(float& acc, float a, float b) { acc = fmaf(a, b, acc); }
@@ -105,7 +122,7 @@ __device__ __forceinline__ void stg_line(dfl* __restrict__ y, size_t o, const df
 }
 
 // Copies the values of cell a (row X0, unless null) and of its face neighbours nb (rows N[s])
-// into shared memory; thread l of the cell's 16 copies its share of every row.
+// into shared memory; lane l of the cell's LPC copies its share of every row.
 template <int N1>
 __device__ __forceinline__ void line_stage(const float* __restrict__ x, int a, const int (&nb)[6], int l, float* X0,
                                            float (*N)[LD<N1>::ST]) {
@@ -117,7 +134,7 @@ __device__ __forceinline__ void line_stage(const float* __restrict__ x, int a, c
       if (nb[s] >= 0) reinterpret_cast<float4*>(N[s])[l] = reinterpret_cast<const float4*>(x + (size_t)nb[s] * NP)[l];
   } else {
 #pragma unroll
-    for (int w = l; w < NP; w += 16) {
+    for (int w = l; w < NP; w += LD<N1>::LPC) {
       if (X0) X0[w] = x[(size_t)a * NP + w];
 #pragma unroll
       for (int s = 0; s < 6; ++s)
@@ -287,12 +304,14 @@ template <int N1, typename R, int MODE>
 __global__ void __launch_bounds__(kLineThreads) k_apply_line(const __grid_constant__ LevelParams<R> P,
                                                              const float* __restrict__ x, const R* __restrict__ f,
                                                              R* __restrict__ y) {
-  constexpr int NP = LD<N1>::NP, NL = LD<N1>::NL, ST = LD<N1>::ST;
-  __shared__ __align__(16) float sX[kLineCells][7][ST];
-  __shared__ R sU[kLineCells][16], sG[kLineCells][16], sE[kLineCells][16];
-  const int c = threadIdx.x >> 4, l = threadIdx.x & 15, j = l % N1, k = l / N1;
-  const int a = blockIdx.x * kLineCells + c;
-  const bool valid = a < P.n_act;
+  constexpr int NP = LD<N1>::NP, NL = LD<N1>::NL, ST = LD<N1>::ST, CPB = LD<N1>::CPB;
+  __shared__ __align__(16) float sX[CPB][7][ST];
+  __shared__ R sU[CPB][16], sG[CPB][16], sE[CPB][16];
+  int c, l;
+  const bool lane_ok = line_lane<N1>(c, l);
+  const int j = l % N1, k = l / N1;
+  const int a = blockIdx.x * CPB + c;
+  const bool valid = lane_ok && a < P.n_act;
   const bool line = valid && l < NL;
   int nb[6];
 #pragma unroll
@@ -330,11 +349,12 @@ __global__ void __launch_bounds__(kLineThreads) k_resid_restrict_line(const __gr
                                                                       const float* __restrict__ u,
                                                                       const float* __restrict__ f,
                                                                       float* __restrict__ rc, int early) {
-  __shared__ __align__(16) float sX[kLineCells][7][LD<4>::ST];
-  __shared__ float sU[kLineCells][16], sG[kLineCells][16], sE[kLineCells][16];
-  __shared__ float sR1[kLineCells][48], sR2[kLineCells][36];
+  constexpr int CPB = LD<4>::CPB;
+  __shared__ __align__(16) float sX[CPB][7][LD<4>::ST];
+  __shared__ float sU[CPB][16], sG[CPB][16], sE[CPB][16];
+  __shared__ float sR1[CPB][48], sR2[CPB][36];
   const int c = threadIdx.x >> 4, l = threadIdx.x & 15, j = l & 3, k = l >> 2;
-  const int a = blockIdx.x * kLineCells + c;
+  const int a = blockIdx.x * CPB + c;
   const bool valid = a < P.n_act;
   const size_t o = (size_t)a * 64 + 4 * j + 16 * k;
   int nb[6];
@@ -397,20 +417,20 @@ __global__ void __launch_bounds__(kLineThreads) k_smooth_line(const __grid_const
                                                               const __grid_constant__ SmoothSegs G, int zero_start,
                                                               const float* __restrict__ f, float* __restrict__ u,
                                                               int early) {
-  constexpr int NP = LD<N1>::NP, NL = LD<N1>::NL, ST = LD<N1>::ST, Q = N1 * N1;
-  __shared__ __align__(16) float sN[kLineCells][6][ST];
-  __shared__ __align__(16) float sT[kLineCells][ST], sW[kLineCells][ST];
-  const int c = threadIdx.x >> 4, l = threadIdx.x & 15;
-  const int lc = l < NL ? l : 0;                     // threads without a line mirror line 0 (no stores)
-  const int j = lc % N1, k = lc / N1;
+  constexpr int NP = LD<N1>::NP, NL = LD<N1>::NL, ST = LD<N1>::ST, Q = N1 * N1, CPB = LD<N1>::CPB;
+  __shared__ __align__(16) float sN[CPB][6][ST];
+  __shared__ __align__(16) float sT[CPB][ST], sW[CPB][ST];
+  int c, l;
+  const bool lane_ok = line_lane<N1>(c, l);          // idle lanes mirror line 0 of the warp (no stores)
+  const int j = l % N1, k = l / N1;
   int sg = 0;
 #pragma unroll
   for (int q = 1; q < SmoothSegs::kMax; ++q)
     if (q < G.n && (int)blockIdx.x >= G.blk[q]) sg = q;
   const int col = G.col[sg], cs = G.cs[sg];
   const bool isB = G.first[sg] < cs + G.nbnd[sg];    // segments are all-boundary or all-interior
-  const int a = G.first[sg] + ((int)blockIdx.x - G.blk[sg]) * kLineCells + c;
-  const bool valid = a < G.last[sg];
+  const int a = G.first[sg] + ((int)blockIdx.x - G.blk[sg]) * CPB + c;
+  const bool valid = lane_ok && a < G.last[sg];
   const bool line = valid && l < NL;
   const size_t o = (size_t)a * NP + N1 * j + Q * k;  // the thread's line
   int nb[6];
@@ -446,7 +466,7 @@ __global__ void __launch_bounds__(kLineThreads) k_smooth_line(const __grid_const
   for (int i = 0; i < N1; ++i) y[i] = 0.f;
   float* lt = sT[c] + N1 * j + Q * k;
   float* lw = sW[c] + N1 * j + Q * k;
-  const bool owner = l < NL;                         // writes its line in the exchanges
+  const bool owner = lane_ok && l < NL;              // writes its line in the exchanges
   if (isB) {                                         // dense inverse: y = Binv t
     if (owner) sts_line<N1>(lt, t);
     __syncwarp();
@@ -539,11 +559,11 @@ __global__ void __launch_bounds__(kLineThreads) k_smooth_line(const __grid_const
 }  // namespace
 
 // Where the thread-per-line kernels run (measured at 128^3 p = 2 and 96^3 p = 3 against the
-// thread-per-cell FP32 operator and the thread-per-DoF smoother): the FP32 operator, smoother and
-// residual + restriction at p = 3; the double-float Arnoldi operator at p = 2 and 3.  At p = 2 the
-// line operator took 135 us against 53 us for the thread-per-cell one, and the line smoother
-// matched the thread-per-DoF one (48.1 against 46.9 us per launch).
+// thread-per-cell FP32 operator and the thread-per-DoF smoother): the FP32 operator and residual +
+// restriction at p = 3 (at p = 2 the line operator took 135 us against 53 us for the thread-per-
+// cell one); the FP32 smoother and the double-float Arnoldi operator at p = 2 and 3.
 bool line_kernels(int dim, int p) { return dim == 3 && p == 3; }
+bool line_smoother(int dim, int p) { return dim == 3 && (p == 2 || p == 3); }
 bool line_kernels_df(int dim, int p) { return dim == 3 && (p == 2 || p == 3); }
 
 #define SBM_LINE_DISPATCH(p, MACRO)     \
@@ -557,9 +577,9 @@ template <typename R>
 cudaError_t launch_apply_line(int p, const LevelParams<R>& P, const float* x, const R* f, R* y, int mode,
                               cudaStream_t s) {
   if (P.n_act == 0) return cudaSuccess;
-  const unsigned grid = (unsigned)((P.n_act + kLineCells - 1) / kLineCells);
 #define SBM_AL(N1)                                                                          \
   {                                                                                         \
+    const unsigned grid = (unsigned)((P.n_act + LD<N1>::CPB - 1) / LD<N1>::CPB);            \
     if (mode == 0) SBM_PDL((k_apply_line<N1, R, 0>), grid, kLineThreads, 0, s, P, x, f, y); \
     else SBM_PDL((k_apply_line<N1, R, 1>), grid, kLineThreads, 0, s, P, x, f, y);           \
   }
@@ -576,7 +596,7 @@ template cudaError_t launch_apply_line<dfl>(int, const LevelParams<dfl>&, const 
 cudaError_t launch_resid_restrict_line(const LevelParams<float>& P, const TransferParams<float>& T, const float* u,
                                        const float* f, float* rc, cudaStream_t s, int early) {
   if (P.n_act == 0) return cudaSuccess;
-  const unsigned grid = (unsigned)((P.n_act + kLineCells - 1) / kLineCells);
+  const unsigned grid = (unsigned)((P.n_act + LD<4>::CPB - 1) / LD<4>::CPB);
   SBM_PDL(k_resid_restrict_line, grid, kLineThreads, 0, s, P, T, u, f, rc, early);
   count_launches();
   return cudaGetLastError();
@@ -590,7 +610,7 @@ cudaError_t launch_smooth_line(int p, const LevelParams<float>& P, int reverse, 
   const int ng = n_colour_groups(P, 3);
   for (int q = first_group; q < ng; ++q) {
     const int g = reverse ? ng - 1 - q : q;
-    const SmoothSegs G = smooth_segs(P, 3, g, kLineCells);
+    const SmoothSegs G = smooth_segs(P, 3, g, p == 3 ? LD<4>::CPB : LD<3>::CPB);
     if (G.n == 0 || G.blk[G.n] == 0) continue;
     const int fe = launched > 0 || early;            // after the sweep's first launch f is two back
     const int zm = group_zero_mode(P, zero_start, q);

@@ -198,7 +198,8 @@ bool cell_kernels(int dim, int p);
 // Thread-per-line kernels (line_ops.cu), 3D p = 2 and 3: the operator (x FP32, arithmetic and y
 // FP32 or double-float), the FP32 smoother, and (p = 3) the FP32 fused residual + restriction to
 // p = 2.  Vectors 16-byte aligned.
-bool line_kernels(int dim, int p);      // FP32 operator, smoother, residual + restriction
+bool line_kernels(int dim, int p);      // FP32 operator, residual + restriction
+bool line_smoother(int dim, int p);     // FP32 smoother
 bool line_kernels_df(int dim, int p);   // double-float operator
 template <typename R>
 cudaError_t launch_apply_line(int p, const LevelParams<R>& P, const float* x, const R* f, R* y, int mode,
