@@ -189,15 +189,14 @@ inline int group_zero_mode(const LevelParams<R>& P, int zero_start, int q) {
 
 // Thread-per-cell kernels (cell_ops.cu): cell_kernels covers the FP32 operator and the fused
 // residual + restriction (2D, 3D p <= 2); cell_smoother the smoother and the double-float Arnoldi
-// operator ((p+1)^d <= 16: 2D, 3D p = 1).  For 3D p = 2 the thread-per-DoF family is faster for
-// those two (measured: smoother sweep 38.6 against 154 us at 64^3; with the 16-byte window loads
-// the thread-per-cell smoother still reached 0.09 of HBM at 128^3 against 0.14, and the 64^3 p=2
-// solve took 10.65 against 9.30 ms; the double-float operator needs 255 registers per thread
-// there), the thread-per-cell one for the others at large sizes.
+// operator ((p+1)^d <= 16: 2D, 3D p = 1).  At 3D p = 2 one thread per cell is slower for those two
+// (smoother 0.09 of HBM at 128^3 even with the 16-byte window loads; the double-float operator
+// needs 255 registers per thread), and the thread-per-line kernels below take them.
 bool cell_kernels(int dim, int p);
 // Thread-per-line kernels (line_ops.cu), 3D p = 2 and 3: the operator (x FP32, arithmetic and y
 // FP32 or double-float), the FP32 smoother, and (p = 3) the FP32 fused residual + restriction to
-// p = 2.  Vectors 16-byte aligned.
+// p = 2; line_kernels, line_smoother and line_kernels_df say where each runs.  Vectors 16-byte
+// aligned.
 bool line_kernels(int dim, int p);      // FP32 operator, residual + restriction
 bool line_smoother(int dim, int p);     // FP32 smoother
 bool line_kernels_df(int dim, int p);   // double-float operator

@@ -107,9 +107,9 @@ def test_apply_unit_columns_tiny(name):
 def test_kernel_variants(name, cell):
     """Both kernel families (one thread per cell, one thread per dof) for the operator, the
     smoother and the V-cycle, in FP64 and FP32, against the oracle (3D p = 2: the FP32 operator
-    and the residual + restriction of the V-cycle; its smoother is thread-per-DoF either way;
-    3D p = 3: the FP32 operator and smoother with one thread per line of a cell, against thread per
-    DoF)."""
+    and the residual + restriction of the V-cycle one thread per cell, the FP32 smoother one thread
+    per line of a cell; 3D p = 3: the FP32 operator and smoother one thread per line; against
+    thread per DoF)."""
     P = pair(name, cell=cell)
     L = len(P.H.levels) - 1
     lev = P.H.finest
