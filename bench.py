@@ -264,7 +264,10 @@ def large_mesh_rooflines(torch, S, hbm, flush, reps=10) -> list:
     flush: achieved GB/s from the algorithmic bytes, against the measured HBM copy bandwidth."""
     rows = []
     cases = (("star2d p=2 2048^2", W.star2d_p2(2048, 0), 2), ("sphere3d p=2 128^3", W.sphere3d(128, 2, 0), 2),
-             ("ellipsoid3d p=3 96^3", W.ellipsoid3d_p3(96, 0), 1))
+             ("ellipsoid3d p=3 96^3", W.ellipsoid3d_p3(96, 0), 1),
+             # finest levels whose FP32 vectors are one to two times L2 and more
+             ("star2d p=2 4096^2", W.star2d_p2(4096, 0), 1), ("sphere3d p=2 192^3", W.sphere3d(192, 2, 0), 1),
+             ("ellipsoid3d p=3 128^3", W.ellipsoid3d_p3(128, 0), 1))
     for label, prob, nlev in cases:
         g = S.Solver(prob, "f32")
         L = g.num_levels - 1
