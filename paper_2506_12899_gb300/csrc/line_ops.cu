@@ -37,11 +37,19 @@ template <int N1>
 struct LD {
   static constexpr int NP = N1 * N1 * N1;        // values of a cell
   static constexpr int NL = N1 * N1;             // lines (and face points) of a cell
-  static constexpr int ST = N1 == 4 ? 68 : 28;   // staged row of a cell (floats, 16-byte multiple; banks)
+  static constexpr int ST = N1 == 4 ? 68 : 40;   // staged row of a cell (floats, 16-byte multiple; banks)
   static constexpr int LPC = N1 == 4 ? 16 : 9;   // lanes per cell
   static constexpr int CPW = 32 / LPC;           // cells per warp
   static constexpr int CPB = 4 * CPW;            // cells per block
 };
+
+// Staged rows keep every line of a cell in its own 16-byte word: value (i, j, k) at
+// i + 4 (j + N1 k), so that a line, and a row of a plane, is one 16-byte shared-memory access (at
+// p = 2 the fourth word of a line is padding); sp(q) maps the dense index q = i + N1 j + N1^2 k.
+template <int N1>
+__host__ __device__ constexpr int sp(int q) {
+  return (q % N1) + 4 * (q / N1);
+}
 
 // The calling thread's cell slot c in the block and lane l within the cell; false for the idle
 // lanes past the warp's last cell (they take slot and lane of the warp's first line and must
@@ -62,28 +70,18 @@ __device__ __forceinline__ void madd(dfl& acc, dfl a, dfl b) { acc += a * b; }
 __device__ __forceinline__ float mul(float a, float b) { return a * b; }
 __device__ __forceinline__ dfl mul(dfl a, dfl b) { return dfl(a * b); }
 
-// N1 consecutive staged values (16-byte aligned for N1 = 4).
+// One staged line (a 16-byte word, see sp).
 template <int N1>
 __device__ __forceinline__ void lds_line(const float* p, float (&v)[N1]) {
-  if constexpr (N1 == 4) {
-    const float4 q = *reinterpret_cast<const float4*>(p);
-    v[0] = q.x;
-    v[1] = q.y;
-    v[2] = q.z;
-    v[3] = q.w;
-  } else {
-#pragma unroll
-    for (int i = 0; i < N1; ++i) v[i] = p[i];
-  }
+  const float4 q = *reinterpret_cast<const float4*>(p);
+  v[0] = q.x;
+  v[1] = q.y;
+  v[2] = q.z;
+  if constexpr (N1 == 4) v[3] = q.w;
 }
 template <int N1>
 __device__ __forceinline__ void sts_line(float* p, const float (&v)[N1]) {
-  if constexpr (N1 == 4) {
-    *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
-  } else {
-#pragma unroll
-    for (int i = 0; i < N1; ++i) p[i] = v[i];
-  }
+  *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], N1 == 4 ? v[3] : 0.f);
 }
 
 // The thread's line of a global FP32 vector (at offset o); CG: L2-only loads (data written two or
@@ -135,10 +133,10 @@ __device__ __forceinline__ void line_stage(const float* __restrict__ x, int a, c
   } else {
 #pragma unroll
     for (int w = l; w < NP; w += LD<N1>::LPC) {
-      if (X0) X0[w] = x[(size_t)a * NP + w];
+      if (X0) X0[sp<N1>(w)] = x[(size_t)a * NP + w];
 #pragma unroll
       for (int s = 0; s < 6; ++s)
-        if (nb[s] >= 0) N[s][w] = x[(size_t)nb[s] * NP + w];
+        if (nb[s] >= 0) N[s][sp<N1>(w)] = x[(size_t)nb[s] * NP + w];
     }
   }
 }
@@ -162,7 +160,7 @@ __device__ __forceinline__ void line_interior(const LevelConsts<R>& C, const flo
       if (q >= 0 && nb[q] < 0) continue;
       const R* M = q < 0 ? C.L[(nb[0] >= 0) + 2 * (nb[1] >= 0)] : (q == 0 ? C.Bpm : C.Bmp);
       float v[N1];
-      lds_line<N1>((q < 0 ? own : N[q]) + N1 * j + Q * k, v);
+      lds_line<N1>((q < 0 ? own : N[q]) + 4 * (j + N1 * k), v);
 #pragma unroll
       for (int i = 0; i < N1; ++i)
 #pragma unroll
@@ -186,7 +184,7 @@ __device__ __forceinline__ void line_interior(const LevelConsts<R>& C, const flo
 #pragma unroll
       for (int m = 0; m < N1; ++m) {
         float v[N1];
-        lds_line<N1>(xs + (dir == 1 ? N1 * m + Q * k : N1 * j + Q * m), v);
+        lds_line<N1>(xs + 4 * (dir == 1 ? m + N1 * k : j + N1 * m), v);
         const R cm = M[N1 * row + m];
 #pragma unroll
         for (int i = 0; i < N1; ++i) madd(s[i], cm, R(v[i]));
@@ -220,7 +218,7 @@ __device__ __forceinline__ void line_sbm_terms(const LevelParams<R>& P, const fl
       R su = R(0.f), sd = R(0.f);
 #pragma unroll
       for (int kn = 0; kn < N1; ++kn) {
-        const R v = R(own[dof<3, N1>(dir, kn, t)]);
+        const R v = R(own[sp<N1>(dof<3, N1>(dir, kn, t))]);
         madd(su, es[kn], v);
         madd(sd, ds[kn], v);
       }
@@ -267,7 +265,7 @@ __device__ __forceinline__ void line_sbm_terms(const LevelParams<R>& P, const fl
         E = R(0.f);
 #pragma unroll
         for (int q = 0; q < N1 * NQ; ++q)
-          madd(E, mul(mul(lv[0][q % N1], lv[1][(q / N1) % N1]), lv[2][q / NQ]), R(own[q]));
+          madd(E, mul(mul(lv[0][q % N1], lv[1][(q / N1) % N1]), lv[2][q / NQ]), R(own[sp<N1>(q)]));
       }
       sE[c][t] = E;
     }
@@ -464,8 +462,8 @@ __global__ void __launch_bounds__(kLineThreads) k_smooth_line(const __grid_const
   float y[N1];
 #pragma unroll
   for (int i = 0; i < N1; ++i) y[i] = 0.f;
-  float* lt = sT[c] + N1 * j + Q * k;
-  float* lw = sW[c] + N1 * j + Q * k;
+  float* lt = sT[c] + 4 * (j + N1 * k);
+  float* lw = sW[c] + 4 * (j + N1 * k);
   const bool owner = lane_ok && l < NL;              // writes its line in the exchanges
   if (isB) {                                         // dense inverse: y = Binv t
     if (owner) sts_line<N1>(lt, t);
@@ -476,7 +474,7 @@ __global__ void __launch_bounds__(kLineThreads) k_smooth_line(const __grid_const
       for (int q = 0; q < NP; ++q) {
         float b[N1];
         ldg_line<N1, false>(Bi, (size_t)q * NP, b);
-        const float tq = sT[c][q];
+        const float tq = sT[c][sp<N1>(q)];
 #pragma unroll
         for (int i = 0; i < N1; ++i) y[i] = fmaf(b[i], tq, y[i]);
       }
@@ -496,7 +494,7 @@ __global__ void __launch_bounds__(kLineThreads) k_smooth_line(const __grid_const
 #pragma unroll
     for (int q = 0; q < N1; ++q) {
       float r[N1];
-      lds_line<N1>(sT[c] + N1 * q + Q * k, r);
+      lds_line<N1>(sT[c] + 4 * (q + N1 * k), r);
       const float cq = C.S[N1 * q + j];
 #pragma unroll
       for (int i = 0; i < N1; ++i) v[i] = fmaf(cq, r[i], v[i]);
@@ -509,7 +507,7 @@ __global__ void __launch_bounds__(kLineThreads) k_smooth_line(const __grid_const
 #pragma unroll
     for (int q = 0; q < N1; ++q) {
       float r[N1];
-      lds_line<N1>(sW[c] + N1 * j + Q * q, r);
+      lds_line<N1>(sW[c] + 4 * (j + N1 * q), r);
       const float cq = C.S[N1 * q + k];
 #pragma unroll
       for (int i = 0; i < N1; ++i) z[i] = fmaf(cq, r[i], z[i]);
@@ -530,7 +528,7 @@ __global__ void __launch_bounds__(kLineThreads) k_smooth_line(const __grid_const
 #pragma unroll
     for (int q = 0; q < N1; ++q) {
       float r[N1];
-      lds_line<N1>(sT[c] + N1 * q + Q * k, r);
+      lds_line<N1>(sT[c] + 4 * (q + N1 * k), r);
       const float cq = C.S[N1 * j + q];
 #pragma unroll
       for (int i = 0; i < N1; ++i) v[i] = fmaf(cq, r[i], v[i]);
@@ -541,7 +539,7 @@ __global__ void __launch_bounds__(kLineThreads) k_smooth_line(const __grid_const
 #pragma unroll
     for (int q = 0; q < N1; ++q) {                   // z: S along (i, j, .)
       float r[N1];
-      lds_line<N1>(sW[c] + N1 * j + Q * q, r);
+      lds_line<N1>(sW[c] + 4 * (j + N1 * q), r);
       const float cq = C.S[N1 * k + q];
 #pragma unroll
       for (int i = 0; i < N1; ++i) y[i] = fmaf(cq, r[i], y[i]);
