@@ -3,20 +3,21 @@
 // A 3D cell holds N1^3 values (N1 = p + 1, dof i + N1 j + N1^2 k).  The thread-per-DoF kernels of
 // level_ops.cu give every value its own thread and spend hundreds of instructions per value on
 // index arithmetic and scalar shared-memory reads; one thread per cell needs 100-200 registers.
-// Here 16 threads serve a cell, thread l < N1^2 owning the line along x (j, k) = (l mod N1,
-// l / N1) and computing at its N1 values i = 0..N1-1 (p = 2: 9 of the 16 threads own a line;
-// all 16 copy data):
-//   - the block copies its 8 cells and their 6 face neighbours into shared memory (a cell's
-//     values are contiguous, so the copies are coalesced: 16-byte words at p = 3, 4-byte at p = 2);
+// Here a cell's N1^2 lines along x take N1^2 consecutive lanes of one warp (16 at p = 3, two cells
+// per warp; 9 at p = 2, three cells per warp and lanes 27-31 idle); lane l owns the line
+// (j, k) = (l mod N1, l / N1) and computes at its N1 values i = 0..N1-1:
+//   - the block copies its cells and their 6 face neighbours into shared memory (a cell's values
+//     are contiguous, so the copies are coalesced: 16-byte words at p = 3, 4-byte at p = 2), every
+//     line in its own 16-byte word;
 //   - x terms (volume, both x faces): the thread's own line, N1 x N1 matrices;
 //   - y terms: plane k of the cell and of its y neighbours (the lines through (i, ., k));
 //   - z terms: the (i, j, .) rows of the cell and of its z neighbours;
 // the 1D matrices come from the kernel's parameter block.  Surrogate faces (Eq. 7) follow in three
-// barrier-separated phases per face slot: the cell's threads take the N1^2 points of the face
-// (trace and normal derivative, then the extended value), then every thread adds the face terms
-// at its own values.  The smoother's fast diagonalisation contracts x on the thread's line and y,
-// z after exchanges through shared memory; a cell's 16 threads lie in one warp, so those
-// exchanges need only warp barriers.
+// barrier-separated phases per face slot: the cell's lanes take the N1^2 points of the face (trace
+// and normal derivative, then the extended value), then every lane adds the face terms at its own
+// values.  The smoother's fast diagonalisation contracts x on the thread's line and y, z after
+// exchanges through shared memory; a cell's lanes lie in one warp, so those exchanges need only
+// warp barriers.
 #include <cuda_runtime.h>
 
 #include <cstdint>
