@@ -146,6 +146,25 @@ __global__ void __launch_bounds__(256) k_multi_axpy(const TZ* __restrict__ Z, si
   }
 }
 
+// x += sum_k c_k Z_k for FP32 Z (the FP32 V-cycle's preconditioned vectors).  The increment is
+// accumulated in double-float on the FP32 pipes (each product c_k Z_k[i] formed exactly in two
+// FP32 parts, the sum to about 48 bits) and added to the FP64 x once: 27 dependent FP64 FMAs per
+// entry made the plain form FP64-pipe bound (1/64 of the FP32 rate on this GPU).
+__global__ void __launch_bounds__(256) k_multi_axpy_df(const float* __restrict__ Z, size_t ldz, int nv,
+                                                       const double* __restrict__ coef, double sign,
+                                                       double* __restrict__ w, size_t N) {
+  pdl_entry();
+  __shared__ dfl cf[kMaxVec];
+  if (threadIdx.x < nv) cf[threadIdx.x] = dfl(sign * coef[threadIdx.x]);
+  __syncthreads();
+  const size_t stride = (size_t)gridDim.x * blockDim.x;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += stride) {
+    dfl s(0.f);
+    for (int k = 0; k < nv; ++k) s += cf[k] * dfl(Z[k * ldz + i]);
+    w[i] += (double)s.hi + (double)s.lo;
+  }
+}
+
 __global__ void k_div_scalar(const double* __restrict__ w, const double* __restrict__ s, double* __restrict__ v,
                              size_t N) {
   pdl_entry();
@@ -556,7 +575,10 @@ template <typename TZ>
 cudaError_t launch_multi_axpy(const TZ* Z, size_t ldz, int nv, const double* coef, double sign, double* w,
                               size_t N, cudaStream_t s) {
   if (nv < 1 || nv > kMaxVec) return cudaErrorInvalidValue;
-  SBM_PDL((k_multi_axpy<TZ>), grid_for(N), 256, 0, s, Z, ldz, nv, coef, sign, w, N);
+  if constexpr (std::is_same<TZ, float>::value)
+    SBM_PDL(k_multi_axpy_df, grid_for(N), 256, 0, s, Z, ldz, nv, coef, sign, w, N);
+  else
+    SBM_PDL((k_multi_axpy<TZ>), grid_for(N), 256, 0, s, Z, ldz, nv, coef, sign, w, N);
   count_launches();
   return cudaGetLastError();
 }
