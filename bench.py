@@ -531,7 +531,8 @@ def run_ours(args) -> dict | None:
     its32 = [i.iterations for i in infos32]
     out = {
         "metric": METRIC, "value": round(ms32, 4), "unit": "ms", "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": round(ms32, 4), "higher_is_better": False, "scaling": "weak",
+        "warmup": args.warmup, "ms_per_step": round(ms32, 4), "step_ms": [round(t, 3) for t in times32],
+        "higher_is_better": False, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
         "config": {"workload": args.workload, "description": DESCRIPTION.get(args.workload, args.workload),
                    "n_dof": N, "levels": s32.num_levels,

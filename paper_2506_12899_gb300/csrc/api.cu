@@ -205,8 +205,10 @@ struct Context {
   double* ydev = nullptr;
   double* bbuf = nullptr;
   double* xbuf = nullptr;
-  double* host_pinned = nullptr;   // 64 doubles
+  double* host_pinned = nullptr;   // 192 doubles: [0,64) scalars and y; [64,128), [128,192) the
+                                   // Hessenberg columns of even and odd Arnoldi steps
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  cudaEvent_t step_done[2] = {};   // end of the last even / odd Arnoldi step launched
   bool host_only = false;
   double* dots_scratch = nullptr;  // partial sums of sbm_dots
   size_t dots_scratch_len = 0;
@@ -262,6 +264,8 @@ struct Context {
     if (join_out) cudaEventDestroy(join_out);
     for (void* p : allocs) cudaFree(p);
     if (host_pinned) cudaFreeHost(host_pinned);
+    for (cudaEvent_t e : step_done)
+      if (e) cudaEventDestroy(e);
     if (ev0) cudaEventDestroy(ev0);
     if (ev1) cudaEventDestroy(ev1);
   }
@@ -535,13 +539,14 @@ Context* build_context(const sbm_setup_desc& d, bool device) {
     // the one-launch tail runs the coloured Gauss-Seidel of the 2^d-colour ordering only
     C->tail_cand = cap > 0 && top >= 1 && d.smoother == 0 && d.ordering == 0 ? top : -1;
   }
-  CUDA_TRY(cudaMallocHost(&C->host_pinned, 64 * sizeof(double)));
+  CUDA_TRY(cudaMallocHost(&C->host_pinned, 192 * sizeof(double)));
   if (d.smoother == 2) estimate_lambda_max(*C);
   CUDA_TRY(cudaEventCreate(&C->ev0));
   CUDA_TRY(cudaEventCreate(&C->ev1));
   CUDA_TRY(cudaStreamCreateWithFlags(&C->ws, cudaStreamNonBlocking));
   CUDA_TRY(cudaEventCreateWithFlags(&C->join_in, cudaEventDisableTiming));
   CUDA_TRY(cudaEventCreateWithFlags(&C->join_out, cudaEventDisableTiming));
+  for (cudaEvent_t& e : C->step_done) CUDA_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
   CUDA_TRY(cudaDeviceSynchronize());
   return C.release();
 }
@@ -871,6 +876,10 @@ double device_norm(Context& C, const double* v, size_t N, double* out_dev, cudaS
   return C.host_pinned[0];
 }
 
+// Pinned host slot of the Hessenberg column of Arnoldi step j (two slots, so that step j + 1 can
+// be in flight while the host reads column j).
+double* column_slot(Context& C, int j) { return C.host_pinned + 64 * (1 + (j & 1)); }
+
 // All device work of Arnoldi step j (Sec. 3: one V-cycle, then the FP64 operator and two
 // classical Gram-Schmidt passes), ending with the copy of Hessenberg column j to pinned memory.
 void arnoldi_step_work(Context& C, int j, cudaStream_t s) {
@@ -927,7 +936,7 @@ void arnoldi_step_work(Context& C, int j, cudaStream_t s) {
     else CUDA_TRY((launch_gs_scale<float2, double>(C.wdf, hn, vnext, C.v64, N, s)));
   }
   if (C.desc.krylov_basis == 1) CUDA_TRY(launch_hess_column(h1, h2, hn, j + 1, col, s));
-  CUDA_TRY(cudaMemcpyAsync(C.host_pinned, col, (j + 2) * sizeof(double), cudaMemcpyDeviceToHost, s));
+  CUDA_TRY(cudaMemcpyAsync(column_slot(C, j), col, (j + 2) * sizeof(double), cudaMemcpyDeviceToHost, s));
 }
 
 // Runs step j from its captured graph (captured on first use).
@@ -958,8 +967,15 @@ void run_arnoldi_step(Context& C, int j, cudaStream_t s) {
     g_kernel_launches.fetch_sub(nkern);             // captured, not executed
   }
   CUDA_TRY(cudaGraphLaunch(graph, s));
+  CUDA_TRY(cudaEventRecord(C.step_done[j & 1], s));
   count_launches(nkern);
 }
+
+// Step j + 1 is queued before the host has read column j when the residual after step j, predicted
+// from the smallest of the last two per-step reduction factors, stays this many times above the
+// tolerance.  A step queued in vain (the cycle ended at step j) costs one step; iterates and
+// results do not depend on it.
+constexpr double kQueueMargin = 8.0;
 
 // Right-preconditioned flexible GMRES(m) with two classical Gram-Schmidt passes, FP64.
 int solve_impl(Context& C, const double* b, double* x, double tol, int m, int max_it, sbm_solve_info* info) {
@@ -994,6 +1010,7 @@ int solve_impl(Context& C, const double* b, double* x, double tol, int m, int ma
     loc.true_rel_residual = 0.0;
   } else {
     std::vector<double> H((size_t)(m + 1) * m), cs(m), sn(m), g(m + 1), y(m);
+    double q_last = 0.0, q_prev = 0.0;              // |sn| of the last two steps: their residual factors
     while (true) {
       double* r0 = C.desc.krylov_basis == 1 ? C.V : C.w;   // r = b - A x, FP64
       CUDA_TRY((launch_apply<double, double>(dim, p, F.P64, x, b, r0, 1, s)));
@@ -1019,14 +1036,29 @@ int solve_impl(Context& C, const double* b, double* x, double tol, int m, int ma
       g[0] = beta;
       int k = 0;
       bool nan = false;
+      int queued = -1;                              // last step launched in this cycle
       for (int j = 0; j < m; ++j) {
-        run_arnoldi_step(C, j, s);
-        CUDA_TRY(cudaStreamSynchronize(s));
-        for (int i = 0; i <= j + 1; ++i) {
-          H[(size_t)i * m + j] = C.host_pinned[i];
-          if (!std::isfinite(C.host_pinned[i])) nan = true;
+        if (queued < j) {
+          run_arnoldi_step(C, j, s);
+          queued = j;
         }
-        const double hnorm = C.host_pinned[j + 1];
+        // queue step j + 1 behind step j when step j will not end the cycle: the next steps exist,
+        // the learned-correction decision (after the third step of the first cycle) is not
+        // pending, and the predicted residual stays well above the tolerance
+        const double q_lo = std::min(q_last, q_prev);
+        if (j + 1 < m && loc.iterations + 1 < max_it && q_lo > 0.0 &&
+            !(C.mlp_on && loc.restarts == 0 && loc.iterations + 1 == 3) &&
+            std::fabs(g[j]) * q_lo > kQueueMargin * tol * bnorm) {
+          run_arnoldi_step(C, j + 1, s);
+          queued = j + 1;
+        }
+        CUDA_TRY(cudaEventSynchronize(C.step_done[j & 1]));
+        const double* colh = column_slot(C, j);
+        for (int i = 0; i <= j + 1; ++i) {
+          H[(size_t)i * m + j] = colh[i];
+          if (!std::isfinite(colh[i])) nan = true;
+        }
+        const double hnorm = colh[j + 1];
         for (int i = 0; i < j; ++i) {              // previous Givens rotations
           const double t = cs[i] * H[(size_t)i * m + j] + sn[i] * H[(size_t)(i + 1) * m + j];
           H[(size_t)(i + 1) * m + j] = -sn[i] * H[(size_t)i * m + j] + cs[i] * H[(size_t)(i + 1) * m + j];
@@ -1039,6 +1071,8 @@ int solve_impl(Context& C, const double* b, double* x, double tol, int m, int ma
         H[(size_t)(j + 1) * m + j] = 0.0;
         g[j + 1] = -sn[j] * g[j];
         g[j] = cs[j] * g[j];
+        q_prev = q_last;
+        q_last = std::isfinite(sn[j]) ? std::fabs(sn[j]) : 0.0;
         k = j + 1;
         if (loc.iterations < 512) loc.history[loc.iterations] = std::fabs(g[j + 1]) / bnorm;
         loc.iterations += 1;

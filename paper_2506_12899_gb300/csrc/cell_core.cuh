@@ -338,28 +338,15 @@ __device__ __forceinline__ void add_couplings(const LevelParams<R>& P, const TI*
                             [&](int n, int, R(&un)[NP]) { load_cell<D, N1, TI, R>(u, n, P.n_act, un); }, y);
 }
 
-// y += A_KK v (volume + own halves of interior faces + surrogate faces), reference scaling.
-template <int D, int N1, typename R>
-__device__ __forceinline__ void add_self(const LevelParams<R>& P, const int (&nb)[2 * D], int bidx,
-                                         const R (&v)[CD<D, N1>::NP], R (&y)[CD<D, N1>::NP]) {
+// y += the surrogate-face terms of boundary cell bidx (Eq. 7) with the line weights wq (the
+// quadrature weights of the face points, times any scale folded into them); nothing when bidx < 0.
+// V: the type of the cell values v (FP32 values under a double-float R are exact in it).
+template <int D, int N1, typename R, typename V>
+__device__ __forceinline__ void add_surrogate(const LevelParams<R>& P, const int (&nb)[2 * D], int bidx,
+                                              const R (&wq)[CD<D, N1>::NQ], const V (&v)[CD<D, N1>::NP],
+                                              R (&y)[CD<D, N1>::NP]) {
   constexpr int NQ = CD<D, N1>::NQ;
   const LevelConsts<R>& C = P.k;
-#pragma unroll
-  for (int dir = 0; dir < D; ++dir) {
-    // self matrix by neighbour mask; the mask is uniform over a warp of interior cells
-    const R* Lm = C.L[(nb[2 * dir] >= 0) + 2 * (nb[2 * dir + 1] >= 0)];
-#pragma unroll
-    for (int t = 0; t < NQ; ++t) {
-      const R wt = line_weight<D, N1, R>(C, t);
-#pragma unroll
-      for (int i = 0; i < N1; ++i) {
-        R acc = 0;
-#pragma unroll
-        for (int k = 0; k < N1; ++k) acc += Lm[i * N1 + k] * v[dof<D, N1>(dir, k, t)];
-        y[dof<D, N1>(dir, i, t)] += wt * acc;
-      }
-    }
-  }
   if (bidx < 0) return;
   // surrogate faces (Eq. 7): U_t, normal derivative G_t, extended value E_t per face point
 #pragma unroll
@@ -426,12 +413,39 @@ __device__ __forceinline__ void add_self(const LevelParams<R>& P, const int (&nb
           E += ph * v[j];
         }
       }
-      const R wt = line_weight<D, N1, R>(C, t);
+      const R wt = wq[t];
 #pragma unroll
       for (int k = 0; k < N1; ++k)
         y[dof<D, N1>(dir, k, t)] += wt * (es[k] * (-sg * G[t] + P.sigG * E) - P.alpha * sg * ds[k] * E);
     }
   }
+}
+
+// y += A_KK v (volume + own halves of interior faces + surrogate faces), reference scaling.
+template <int D, int N1, typename R>
+__device__ __forceinline__ void add_self(const LevelParams<R>& P, const int (&nb)[2 * D], int bidx,
+                                         const R (&v)[CD<D, N1>::NP], R (&y)[CD<D, N1>::NP]) {
+  constexpr int NQ = CD<D, N1>::NQ;
+  const LevelConsts<R>& C = P.k;
+  R wq[NQ];
+#pragma unroll
+  for (int t = 0; t < NQ; ++t) wq[t] = line_weight<D, N1, R>(C, t);
+#pragma unroll
+  for (int dir = 0; dir < D; ++dir) {
+    // self matrix by neighbour mask; the mask is uniform over a warp of interior cells
+    const R* Lm = C.L[(nb[2 * dir] >= 0) + 2 * (nb[2 * dir + 1] >= 0)];
+#pragma unroll
+    for (int t = 0; t < NQ; ++t) {
+#pragma unroll
+      for (int i = 0; i < N1; ++i) {
+        R acc = 0;
+#pragma unroll
+        for (int k = 0; k < N1; ++k) acc += Lm[i * N1 + k] * v[dof<D, N1>(dir, k, t)];
+        y[dof<D, N1>(dir, i, t)] += wq[t] * acc;
+      }
+    }
+  }
+  add_surrogate<D, N1, R, R>(P, nb, bidx, wq, v, y);
 }
 
 template <typename R>
@@ -451,18 +465,69 @@ __device__ __forceinline__ void load_nbr(const LevelParams<R>& P, int a, int (&n
 }
 
 // y = (A x)_a with the reference scaling h^(d-2) applied; nb: the neighbours of a (load_nbr).
+//
+// Double-float accumulation (the Arnoldi operator on the FP32 V-cycle output): the FP32 values
+// stay FP32 (exact, and the double-float x FP32 products are the shorter form), and per direction
+// the self line matrix and the couplings to the two neighbours across the faces normal to it act
+// on the lines along that direction, their sum weighted once per line point by the face-point
+// weight times h^(d-2); a missing neighbour contributes zeros.  This executes about a quarter
+// fewer FP32 instructions than the face-by-face form.  FP32 and FP64 keep the face-by-face form,
+// which holds one neighbour at a time in registers.
 template <int D, int N1, typename TI, typename R>
 __device__ __forceinline__ void cell_apply(const LevelParams<R>& P, const TI* __restrict__ x, int a,
                                            const int (&nb)[2 * D], R (&y)[CD<D, N1>::NP]) {
-  constexpr int NP = CD<D, N1>::NP;
-  R v[NP];
-  load_cell<D, N1, TI, R>(x, a, P.n_act, v);
+  constexpr int NP = CD<D, N1>::NP, NQ = CD<D, N1>::NQ;
+  const LevelConsts<R>& C = P.k;
+  if constexpr (std::is_same<R, dfl>::value && std::is_same<TI, float>::value) {
+    R wq[NQ];
 #pragma unroll
-  for (int i = 0; i < NP; ++i) y[i] = 0;
-  add_self<D, N1, R>(P, nb, boundary_index(P, a, 1 << D), v, y);
-  add_couplings<D, N1, TI, R>(P, x, 0, false, nb, y);
+    for (int t = 0; t < NQ; ++t) wq[t] = R(line_weight<D, N1, R>(C, t) * P.hscale);
+    float v[NP];
+    load_cell<D, N1, TI, float>(x, a, P.n_act, v);
 #pragma unroll
-  for (int i = 0; i < NP; ++i) y[i] *= P.hscale;
+    for (int dir = 0; dir < D; ++dir) {
+      const int nm = nb[2 * dir], npl = nb[2 * dir + 1];
+      float um[NP], up[NP];
+      if (nm >= 0) {
+        load_cell<D, N1, TI, float>(x, nm, P.n_act, um);
+      } else {
+#pragma unroll
+        for (int i = 0; i < NP; ++i) um[i] = 0.f;
+      }
+      if (npl >= 0) {
+        load_cell<D, N1, TI, float>(x, npl, P.n_act, up);
+      } else {
+#pragma unroll
+        for (int i = 0; i < NP; ++i) up[i] = 0.f;
+      }
+      const R* Lm = C.L[(nm >= 0) + 2 * (npl >= 0)];   // self matrix by neighbour mask
+#pragma unroll
+      for (int t = 0; t < NQ; ++t) {
+#pragma unroll
+        for (int i = 0; i < N1; ++i) {
+          R acc = R(Lm[i * N1] * v[dof<D, N1>(dir, 0, t)]);
+#pragma unroll
+          for (int k = 1; k < N1; ++k) acc += Lm[i * N1 + k] * v[dof<D, N1>(dir, k, t)];
+#pragma unroll
+          for (int k = 0; k < N1; ++k) acc += C.Bpm[i * N1 + k] * um[dof<D, N1>(dir, k, t)];
+#pragma unroll
+          for (int k = 0; k < N1; ++k) acc += C.Bmp[i * N1 + k] * up[dof<D, N1>(dir, k, t)];
+          if (dir == 0) y[dof<D, N1>(dir, i, t)] = R(wq[t] * acc);   // dir 0 visits every dof once
+          else y[dof<D, N1>(dir, i, t)] += wq[t] * acc;
+        }
+      }
+    }
+    add_surrogate<D, N1, R, float>(P, nb, boundary_index(P, a, 1 << D), wq, v, y);
+  } else {
+    R v[NP];
+    load_cell<D, N1, TI, R>(x, a, P.n_act, v);
+#pragma unroll
+    for (int i = 0; i < NP; ++i) y[i] = 0;
+    add_self<D, N1, R>(P, nb, boundary_index(P, a, 1 << D), v, y);
+    add_couplings<D, N1, TI, R>(P, x, 0, false, nb, y);
+#pragma unroll
+    for (int i = 0; i < NP; ++i) y[i] *= P.hscale;
+  }
 }
 
 

@@ -41,9 +41,8 @@ __device__ __forceinline__ void interleaved_warp(const LevelParams<R>& P, int& a
 
 // y = A x (MODE 0) or y = f - A x (MODE 1), one thread per cell, colours interleaved.
 template <int D, int N1, typename TI, typename R, int MODE>
-__global__ void __launch_bounds__(kCellThreads) k_apply_cell(const __grid_constant__ LevelParams<R> P,
-                                                             const TI* __restrict__ x, const R* __restrict__ f,
-                                                             R* __restrict__ y) {
+__device__ __forceinline__ void apply_cell_body(const LevelParams<R>& P, const TI* __restrict__ x,
+                                                const R* __restrict__ f, R* __restrict__ y) {
   constexpr int NP = CD<D, N1>::NP;
   int a0w, end;
   interleaved_warp<D, R>(P, a0w, end);
@@ -69,6 +68,24 @@ __global__ void __launch_bounds__(kCellThreads) k_apply_cell(const __grid_consta
     __shared__ WarpStage<NP, R> stage;
     if (a0w < end) warp_store_cells<NP, R>(y, a0w, min(32, end - a0w), r, stage.v[threadIdx.x >> 5]);
   }
+}
+
+template <int D, int N1, typename TI, typename R, int MODE>
+__global__ void __launch_bounds__(kCellThreads) k_apply_cell(const __grid_constant__ LevelParams<R> P,
+                                                             const TI* __restrict__ x, const R* __restrict__ f,
+                                                             R* __restrict__ y) {
+  apply_cell_body<D, N1, TI, R, MODE>(P, x, f, y);
+}
+
+// The same, compiled for 24 resident warps per SM (80 registers).  Used for the double-float
+// operator of 2D p = 2: at its natural 96 registers an SM holds 20 warps, and the 512^2 p = 2 grid
+// of 3164 warps then runs as 1.04 waves whose last warps run alone; at 80 every warp is resident
+// at once.  (2D p = 3 spills heavily at 80; p = 1 needs fewer than 80.)
+template <int D, int N1, typename TI, typename R, int MODE>
+__global__ void __launch_bounds__(kCellThreads, 6) k_apply_cell_occ(const __grid_constant__ LevelParams<R> P,
+                                                                    const TI* __restrict__ x,
+                                                                    const R* __restrict__ f, R* __restrict__ y) {
+  apply_cell_body<D, N1, TI, R, MODE>(P, x, f, y);
 }
 
 
@@ -797,8 +814,13 @@ cudaError_t launch_apply_cell(int dim, int p, const LevelParams<R>& P, const TI*
 #define SBM_AC(D, N1)                                                                           \
   {                                                                                             \
     const unsigned bs = cell_block(P.n_act), g = interleaved_grid(P, dim, bs);                 \
-    if (mode == 0) SBM_PDL((k_apply_cell<D, N1, TI, R, 0>), g, bs, 0, s, P, x, f, y);          \
-    else SBM_PDL((k_apply_cell<D, N1, TI, R, 1>), g, bs, 0, s, P, x, f, y);                    \
+    if constexpr (std::is_same<R, dfl>::value && D == 2 && N1 == 3) {                           \
+      if (mode == 0) SBM_PDL((k_apply_cell_occ<D, N1, TI, R, 0>), g, bs, 0, s, P, x, f, y);    \
+      else SBM_PDL((k_apply_cell_occ<D, N1, TI, R, 1>), g, bs, 0, s, P, x, f, y);              \
+    } else {                                                                                    \
+      if (mode == 0) SBM_PDL((k_apply_cell<D, N1, TI, R, 0>), g, bs, 0, s, P, x, f, y);        \
+      else SBM_PDL((k_apply_cell<D, N1, TI, R, 1>), g, bs, 0, s, P, x, f, y);                  \
+    }                                                                                           \
   }
   if constexpr (std::is_same<TI, float>::value && std::is_same<R, float>::value) SBM_CELL_DISPATCH3(dim, p, SBM_AC);
   else SBM_CELL_DISPATCH(dim, p, SBM_AC);

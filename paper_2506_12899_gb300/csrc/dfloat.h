@@ -54,6 +54,15 @@ __device__ __forceinline__ dfl_prod operator*(dfl a, dfl b) {
   return dfl_prod{p, e};
 }
 
+// Product with an FP32 value (a double-float with a zero low part): the b.lo term drops out.
+__device__ __forceinline__ dfl_prod operator*(dfl a, float b) {
+  const float p = __fmul_rn(a.hi, b);
+  float e = fmaf(a.hi, b, -p);
+  e = fmaf(a.lo, b, e);
+  return dfl_prod{p, e};
+}
+__device__ __forceinline__ dfl_prod operator*(float a, dfl b) { return b * a; }
+
 __device__ __forceinline__ dfl& operator+=(dfl& a, dfl b) { return a = a + b; }
 __device__ __forceinline__ dfl& operator-=(dfl& a, dfl b) { return a = a - b; }
 __device__ __forceinline__ dfl& operator*=(dfl& a, dfl b) { return a = dfl(a * b); }

@@ -479,19 +479,29 @@ HostLevel build_level(const sbm_setup_desc& d, int n, int p, bool device) {
     return lin_of(j);
   };
 
-  // compact order: colour-major; within a colour, boundary cells then interior cells
+  // compact order: colour-major; within a colour, boundary cells then interior cells.  The
+  // boundary cells are ordered by the set of their faces without a neighbour (the surrogate
+  // faces), then by background index: a warp of boundary cells then mostly evaluates one set of
+  // surrogate-face terms, not the union of its lanes' sets.  Cells of one colour do not couple,
+  // so the order within a colour changes no result of the smoother or the operator.
+  std::vector<std::vector<std::pair<int, int>>> bnd_keyed(L.ncol);
   std::vector<std::vector<int>> bnd(L.ncol), inner(L.ncol);
   for (size_t lin = 0; lin < nbg; ++lin) {
     if (!active[lin]) continue;
     int idx[3] = {(int)(lin % n), (int)((lin / n) % n), dim > 2 ? (int)(lin / ((size_t)n * n)) : 0};
     int col = 0;
     for (int k = 0; k < dim; ++k) col |= (idx[k] & 1) << k;
-    bool isb = false;
+    int mask = 0;
     for (int slot = 0; slot < 2 * dim; ++slot) {
       int nl = nb_lin(idx, slot);
-      if (nl < 0 || !active[nl]) isb = true;
+      if (nl < 0 || !active[nl]) mask |= 1 << slot;
     }
-    (isb ? bnd : inner)[col].push_back((int)lin);
+    if (mask) bnd_keyed[col].push_back({mask, (int)lin});
+    else inner[col].push_back((int)lin);
+  }
+  for (int c = 0; c < L.ncol; ++c) {
+    std::sort(bnd_keyed[c].begin(), bnd_keyed[c].end());
+    for (const auto& e : bnd_keyed[c]) bnd[c].push_back(e.second);
   }
   L.bg2act.assign(nbg, -1);
   std::vector<int> order;
