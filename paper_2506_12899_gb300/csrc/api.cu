@@ -48,6 +48,7 @@ struct DevLevel {
   LevelParams<float> P32{};
   LevelParams<dfl> Pdf{};         // double-float operator constants (finest level, thread-per-cell shapes)
   dfl* dhat_df = nullptr;
+  dfl* bself_df = nullptr;        // dense boundary self blocks of the double-float operator
   bool has_df = false;
   TransferParams<double> T64{};   // transfer between level l-1 (coarse) and this level
   TransferParams<float> T32{};
@@ -510,6 +511,29 @@ Context* build_context(const sbm_setup_desc& d, bool device) {
       L.dhat_df = C->upload(dh);
       L.Pdf = make_params<dfl>(L, L.dhat_df, nullptr);
       L.has_df = true;
+      // the boundary cells' self blocks h^(d-2) A_KK, assembled in FP64 column by column with the
+      // host operator and rounded to double-float: the thread-per-cell operator applies them
+      // densely instead of evaluating the surrogate-face terms, for up to 9 values per cell
+      // (blocks padded to an even length so that every block starts on a 16-byte boundary)
+      const HostLevel& H = L.H;
+      if (H.dim == 3 && H.p == 1 && H.n_bnd > 0) {
+        const int np = H.np, ld = (np * np + 1) & ~1;
+        std::vector<dfl> bs((size_t)H.n_bnd * ld, dfl(0.0));
+        std::vector<double> e(np), col(np);
+        for (int c = 0; c < H.ncol; ++c)
+          for (int off = 0; off < H.colour_nbnd[c]; ++off) {
+            const int a = H.colour_start[c] + off, b = H.bstart[c] + off;
+            for (int j = 0; j < np; ++j) {
+              std::fill(e.begin(), e.end(), 0.0);
+              e[j] = 1.0;
+              cell_self_apply(H, a, b, e.data(), col.data());
+              for (int i = 0; i < np; ++i) bs[(size_t)b * ld + (size_t)j * np + i] = dfl(col[i]);
+            }
+          }
+        L.bself_df = C->upload(bs);
+        L.Pdf.bself = L.bself_df;
+        L.Pdf.bself_ld = ld;
+      }
     }
     // default: thread-per-cell kernels for FP32 (measured faster at every size from 512^2 to
     // 2048^2 cells), per-dof block kernels for FP64 (FP64 ALU bound; measured faster)

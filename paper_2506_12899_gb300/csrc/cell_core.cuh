@@ -482,8 +482,21 @@ __device__ __forceinline__ void cell_apply(const LevelParams<R>& P, const TI* __
     R wq[NQ];
 #pragma unroll
     for (int t = 0; t < NQ; ++t) wq[t] = R(line_weight<D, N1, R>(C, t) * P.hscale);
+    // 3D p = 1: a boundary cell applies its stored self block (bself) instead of the self line
+    // matrices and the surrogate-face terms
+    constexpr bool kDenseSelf = D == 3 && N1 == 2;
+    int bidx = -1;
+    bool dense = false;
+    if constexpr (kDenseSelf) {
+      bidx = boundary_index(P, a, 1 << D);
+      dense = bidx >= 0 && P.bself != nullptr;
+    }
     float v[NP];
     load_cell<D, N1, TI, float>(x, a, P.n_act, v);
+    if (dense) {                                   // the self terms come from the dense block below
+#pragma unroll
+      for (int i = 0; i < NP; ++i) v[i] = 0.f;
+    }
 #pragma unroll
     for (int dir = 0; dir < D; ++dir) {
       const int nm = nb[2 * dir], npl = nb[2 * dir + 1];
@@ -517,7 +530,22 @@ __device__ __forceinline__ void cell_apply(const LevelParams<R>& P, const TI* __
         }
       }
     }
-    add_surrogate<D, N1, R, float>(P, nb, boundary_index(P, a, 1 << D), wq, v, y);
+    if constexpr (kDenseSelf) {
+      if (dense) {                                 // y += h^(d-2) A_KK v, two block entries per 16-byte load
+        load_cell<D, N1, TI, float>(x, a, P.n_act, v);
+        const float4* Ab = reinterpret_cast<const float4*>(P.bself + (size_t)bidx * P.bself_ld);
+#pragma unroll
+        for (int e = 0; e < (NP * NP + 1) / 2; ++e) {
+          const float4 q = Ab[e];
+          y[(2 * e) % NP] += dfl(q.x, q.y) * v[(2 * e) / NP];
+          if (2 * e + 1 < NP * NP) y[(2 * e + 1) % NP] += dfl(q.z, q.w) * v[(2 * e + 1) / NP];
+        }
+      } else {
+        add_surrogate<D, N1, R, float>(P, nb, bidx, wq, v, y);
+      }
+    } else {
+      add_surrogate<D, N1, R, float>(P, nb, boundary_index(P, a, 1 << D), wq, v, y);
+    }
   } else {
     R v[NP];
     load_cell<D, N1, TI, R>(x, a, P.n_act, v);
