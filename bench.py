@@ -319,6 +319,45 @@ def other_workloads(torch, S, flush, n) -> dict:
     return out
 
 
+SEED_CONFIGS = ("disk2d_p1_n32", "star2d_p2_n512", "sphere3d_p1_n64", "sphere3d_p2_n64", "ellipsoid3d_p3_n96")
+
+
+def seed_study(torch, S, flush, seeds=5, n=5) -> dict:
+    """Every benchmark configuration over seeds 0..seeds-1 (the seed moves the disk's and the
+    sphere's centre, the star's phase and the ellipsoid's rotation): per seed the median of n timed
+    solves after two warm-ups, FP32- and FP64-V-cycle; per configuration the median over the seeds,
+    the spread (min, max) and the iteration counts per seed."""
+    out = {}
+    for name in SEED_CONFIGS:
+        ms = {"f32": [], "f64": []}
+        its = {"f32": [], "f64": []}
+        converged = True
+        for sd in range(seeds):
+            prob = WORKLOADS[name](sd)
+            for prec in ("f32", "f64"):
+                g = S.Solver(prob, prec)
+                b = g.rhs()
+                x = torch.zeros_like(b)
+                timed_solves(torch, g, b, x, 2, flush)
+                ts, infos = timed_solves(torch, g, b, x, n, flush)
+                ms[prec].append(statistics.median(ts))
+                its[prec].append(infos[-1].iterations)
+                converged = converged and all(i.converged for i in infos)
+                g.close()
+            torch.cuda.empty_cache()
+        out[name] = {prec: {"median_ms": round(statistics.median(ms[prec]), 4), "min_ms": round(min(ms[prec]), 4),
+                            "max_ms": round(max(ms[prec]), 4), "iterations": its[prec]} for prec in ("f32", "f64")}
+        out[name]["converged"] = converged
+    return {"seeds": list(range(seeds)), "timed_solves_per_seed": n, "configs": out}
+
+
+def run_seed_study(args) -> dict:
+    import torch
+    import paper_2506_12899_gb300 as S
+    return {"experiment": "solve time over seeds 0..4 per benchmark configuration",
+            **seed_study(torch, S, make_flush(torch))}
+
+
 def setup_times(S, reps=2) -> dict:
     """Wall time of sbm_setup (host build of every level, device uploads) for the 96^3 p=3 ellipsoid
     with the volume fractions and closest points on the device, and on the host cores."""
@@ -519,11 +558,12 @@ def run_ours(args) -> dict | None:
     del r32, u32, y32, xr64, y64, V64, r1, u1
     torch.cuda.empty_cache()
     # ---- the other benchmark configurations, and the kernels on meshes larger than L2
-    others = large = setup = None
+    others = large = setup = seeds = None
     if not args.no_extra:
         others = other_workloads(torch, S, flush, 5)
         large = large_mesh_rooflines(torch, S, hbm, flush)
         setup = setup_times(S)
+        seeds = seed_study(torch, S, flush)
     if rank != 0:
         return None
     cpu = finish_cpu_worker(cpu_proc) if cpu_proc is not None else None
@@ -560,6 +600,7 @@ def run_ours(args) -> dict | None:
         "rooflines": rooflines,
         "rooflines_large_meshes": large,
         "other_workloads": others,
+        "seed_study": seeds,
         "setup_time": setup,
     }
     if cpu is not None:
@@ -845,7 +886,7 @@ def main():
     ap.add_argument("--tail-cluster", type=int, default=0, help="--profile kernels: cluster-tail CTAs")
     ap.add_argument("--krylov-basis", type=int, default=0, choices=[0, 1],
                     help="--profile solve: FGMRES basis storage (0 double-float, 1 FP64)")
-    ap.add_argument("--experiment", choices=["learned-heldout", "roofline-sweep", "paper-replica", "complex2d"],
+    ap.add_argument("--experiment", choices=["learned-heldout", "roofline-sweep", "paper-replica", "complex2d", "seeds"],
                     help="a7 on held-out domains, or the large-mesh roofline sweep (no bench line)")
     ap.add_argument("--family", default="star2d", choices=["star2d", "ellipsoid3d"])
     ap.add_argument("--n-train", type=int, default=256)
@@ -854,7 +895,8 @@ def main():
     args = ap.parse_args()
     if args.experiment:
         run = {"learned-heldout": run_learned_heldout, "roofline-sweep": run_roofline_sweep,
-               "paper-replica": run_paper_replica, "complex2d": run_complex2d}[args.experiment]
+               "paper-replica": run_paper_replica, "complex2d": run_complex2d,
+               "seeds": run_seed_study}[args.experiment]
         print(json.dumps(run(args)))
         return
     if args.profile:
