@@ -293,10 +293,14 @@ int sbm_dots_noalloc(const double* V_dev, long long ldv, int nv, const double* w
 int sbm_async_wait_selftest(int starve, void* stream);
 
 /* Solve A x = b by FGMRES(restart), right-preconditioned by one V-cycle in the precision of
- * sbm_setup_desc.precision; Arnoldi, Gram-Schmidt (two classical passes), the update of x and
- * the true residual are FP64.  x_dev holds the initial guess on entry.  Stops when the
- * Hessenberg residual estimate <= tol ||b|| and the recomputed ||b - A x|| <= tol ||b||, or
- * at max_it Arnoldi steps (SBM_ERR_NOT_CONVERGED).  Synchronises; fills *info if non-NULL. */
+ * sbm_setup_desc.precision (Sec. 3); the Hessenberg matrix, the Givens rotations, the update of x
+ * and the true residual are FP64, and the basis, Gram-Schmidt (two classical passes) and the
+ * Arnoldi operator are FP64 or double-float as sbm_setup_desc.krylov_basis selects.  x_dev holds
+ * the initial guess on entry.  Stops when the Hessenberg residual estimate <= tol ||b|| and the
+ * recomputed ||b - A x|| <= tol ||b||, or at max_it Arnoldi steps (SBM_ERR_NOT_CONVERGED).
+ * The host reads each Hessenberg column; while the residual stays well above the tolerance the
+ * next Arnoldi step is already queued behind the current one, and a step queued in vain is
+ * discarded (the iterates do not depend on the queuing).  Synchronises; fills *info if non-NULL. */
 int sbm_solve(void* ctx, const double* b_dev, double* x_dev, double tol, int restart, int max_it,
               sbm_solve_info* info);
 
