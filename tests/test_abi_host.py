@@ -116,3 +116,33 @@ def test_host_setup_all_levels_match_oracle(libsbm):
         xo[dof] = x
         y, yo = hs.host_apply(x, l), (lev.A @ xo)[dof]
         assert np.linalg.norm(y - yo) <= 1e-13 * np.linalg.norm(yo)
+
+
+@pytest.mark.parametrize("prob", [W.disk2d_p1(32, 0), W.star2d_p2(64, 1), W.sphere3d(16, 1, 2), W.ellipsoid3d_p3(12, 0)],
+                         ids=["disk2d_p1_n32", "star2d_p2_n64", "sphere3d_p1_n16", "ellipsoid3d_p3_n12"])
+def test_compact_order_colour_major_boundary_cells_by_face_set(libsbm, prob):
+    """Every level's compact order: colour-major (colour = parity bits of the cell index); within a
+    colour the cells with surrogate faces first, ordered by their set of surrogate-face slots and
+    then by background index, then the interior cells by background index."""
+    hs = libsbm.HostSetup(prob)
+    dim = prob.dim
+    for level in range(hs.num_levels):
+        info = hs.info(level)
+        n, na = info["n"], info["n_active"]
+        coords = hs.layout(level).astype(np.int64)
+        lin = libsbm.compact_to_natural(coords, n, dim)
+        colour = sum(((coords[:, k] & 1) << k) for k in range(dim))
+        cell, slot, _ = hs.export_geometry(level)
+        mask = np.zeros(na, dtype=np.int64)
+        np.bitwise_or.at(mask, cell, 1 << slot.astype(np.int64))
+        cs = info["colour_start"]
+        for c in range(2 ** dim):
+            a0, a1, nb = cs[c], cs[c + 1], info["colour_nbnd"][c]
+            assert np.all(colour[a0:a1] == c)
+            bnd, inner = slice(a0, a0 + nb), slice(a0 + nb, a1)
+            assert np.all(mask[bnd] != 0) and np.all(mask[inner] == 0)
+            key = mask[bnd] * (n ** dim) + lin[bnd]
+            assert np.all(np.diff(key) > 0)
+            assert np.all(np.diff(lin[inner]) > 0)
+        assert cs[2 ** dim] == na
+    hs.close()
