@@ -469,9 +469,13 @@ Context* build_context(const sbm_setup_desc& d, bool device) {
   std::vector<std::pair<int, int>> seq;
   for (auto it = ns.rbegin(); it != ns.rend(); ++it) seq.emplace_back(*it, 1);
   for (int q = 2; q <= d.p; ++q) seq.emplace_back(d.n, q);
+  std::vector<int> counts;                 // volume-fraction counts of the last mesh size built
+  int counts_n = -1;
   for (auto& np : seq) {
     DevLevel L;
-    L.H = build_level(d, np.first, np.second, device);
+    if (np.first != counts_n) counts.clear();
+    counts_n = np.first;
+    L.H = build_level(d, np.first, np.second, device, &counts);
     if (L.H.n_act == 0) {
       C->lv.clear();                       // an empty level: everything coarser is dropped
       continue;

@@ -72,7 +72,10 @@ struct SetupError {
 // Builds one level; throws SetupError.  (Geometry of Sec. 2.1 / Sec. 4.2, element data of Eq. 11.)
 // device: the volume fractions and the closest points run as device kernels (geometry_ops.cu)
 // unless d.device_geometry < 0.
-HostLevel build_level(const sbm_setup_desc& d, int n, int p, bool device = false);
+// counts_cache: the sub-cell sample counts of the volume fractions on an n-cell mesh, shared by the
+// levels of one mesh size (the p-levels): used when it holds n^dim entries, else filled.
+HostLevel build_level(const sbm_setup_desc& d, int n, int p, bool device = false,
+                      std::vector<int>* counts_cache = nullptr);
 // Device set-up kernels (geometry_ops.cu); throw SetupError on CUDA failures.
 void device_volume_counts(const sbm_setup_desc& d, int n, double h, int s, std::vector<int>& counts);
 void device_closest_points(const sbm_setup_desc& d, const std::vector<double>& samples, const std::vector<double>& X,

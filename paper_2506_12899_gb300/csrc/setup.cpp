@@ -415,7 +415,7 @@ void cell_self_apply(const HostLevel& L, int a, int bidx, const double* u, doubl
 }
 
 // ------------------------------------------------------------------------------ level set-up
-HostLevel build_level(const sbm_setup_desc& d, int n, int p, bool device) {
+HostLevel build_level(const sbm_setup_desc& d, int n, int p, bool device, std::vector<int>* counts_cache) {
   HostLevel L;
   L.dim = d.dim;
   L.n = n;
@@ -444,7 +444,11 @@ HostLevel build_level(const sbm_setup_desc& d, int n, int p, bool device) {
   std::vector<int> counts(nbg, 0);
   const double thr = d.lambda * S;
   const bool dev_geo = device && d.device_geometry >= 0;
-  if (dev_geo) {                                   // counts on the device (geometry_ops.cu)
+  if (counts_cache && counts_cache->size() == nbg) {   // a level of the same mesh counted them
+    counts = *counts_cache;
+    for (size_t lin = 0; lin < nbg; ++lin)
+      active[lin] = d.lambda_inclusive ? (counts[lin] >= thr) : (counts[lin] > thr);
+  } else if (dev_geo) {                            // counts on the device (geometry_ops.cu)
     device_volume_counts(d, n, L.h, s, counts);
     for (size_t lin = 0; lin < nbg; ++lin)
       active[lin] = d.lambda_inclusive ? (counts[lin] >= thr) : (counts[lin] > thr);
@@ -465,6 +469,7 @@ HostLevel build_level(const sbm_setup_desc& d, int n, int p, bool device) {
       active[lin] = d.lambda_inclusive ? (count >= thr) : (count > thr);
     }
   });
+  if (counts_cache && counts_cache->size() != nbg) *counts_cache = counts;
 
   auto lin_of = [&](const int* idx) {
     int lin = 0;
