@@ -515,10 +515,11 @@ Context* build_context(const sbm_setup_desc& d, bool device) {
       L.dhat_df = C->upload(dh);
       L.Pdf = make_params<dfl>(L, L.dhat_df, nullptr);
       L.has_df = true;
-      // the boundary cells' self blocks h^(d-2) A_KK, assembled in FP64 column by column with the
-      // host operator and rounded to double-float: the thread-per-cell operator applies them
-      // densely instead of evaluating the surrogate-face terms, for up to 9 values per cell
-      // (blocks padded to an even length so that every block starts on a 16-byte boundary)
+      // 3D p = 1: the boundary cells' self blocks h^(d-2) A_KK, assembled in FP64 column by column
+      // with the host operator and rounded to double-float; the thread-per-cell operator applies
+      // them densely instead of evaluating the surrogate-face terms (blocks padded to an even
+      // length so that every block starts on a 16-byte boundary).  2D keeps the surrogate-face
+      // terms: there the dense blocks made the solve slower.
       const HostLevel& H = L.H;
       if (H.dim == 3 && H.p == 1 && H.n_bnd > 0) {
         const int np = H.np, ld = (np * np + 1) & ~1;

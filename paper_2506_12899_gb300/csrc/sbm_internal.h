@@ -125,7 +125,7 @@ struct LevelParams {
   const R* dhat;
   const R* binvT;
   // dense self blocks h^(d-2) A_KK of the boundary cells (Eqs. 10, 7), column j at bself_ld * b + np * j
-  // (double-float operator of the finest level only; null elsewhere)
+  // (double-float operator of a 3D p = 1 finest level only; null elsewhere)
   const R* bself;
   int bself_ld;
   R hscale;                        // h^(dim-2)
