@@ -151,7 +151,6 @@ template <bool SELF, int N1, typename R>
 __device__ __forceinline__ void line_interior(const LevelConsts<R>& C, const float* own,
                                               const float (*N)[LD<N1>::ST], const int (&nb)[6], int j, int k,
                                               R (&acc)[N1]) {
-  constexpr int Q = N1 * N1;
   {                                                // x: the thread's own line (j, k)
     R s[N1];
 #pragma unroll
